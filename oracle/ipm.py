@@ -1,0 +1,378 @@
+"""Primal-dual barrier IPM around the condensed KKT step -- oracle side.
+
+Test infrastructure.  The outer loop follows the published primal-dual
+barrier method of Wachter and Biegler (2006), which the paper defers to
+(Sec. 4.3): monotone barrier update, fraction-to-the-boundary rule, bound
+multipliers eliminated into Sigma, Ipopt's scaled optimality error with
+tolerance 1e-8, and y0 = 0.  The step comes from the condensed system
+(Theorems 1-2), with inertia correction by a primal regularization on the
+control block until K_cond is positive definite (Theorem 3; Sec. 4.3).  Step
+acceptance uses backtracking on the l1 exact-penalty merit function
+(Nocedal and Wright, Sec. 19.4) instead of Ipopt's filter.
+
+linred(net)  -- Algorithm 1 (linearize-then-reduce).
+redlin(net)  -- Algorithm 2 (reduce-then-linearize): Newton-Raphson projection
+                to 1e-10 on the state equation at every trial control
+                (Sec. 4.4), adjoint solve for lambda, state bounds moved into
+                h_r (Eq. reduced:problem).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import kkt, model
+
+TAU_MIN = 0.99
+KAPPA_EPS = 10.0
+KAPPA_MU = 0.2
+THETA_MU = 1.5
+ETA = 1e-4
+KAPPA_SIGMA = 1e10
+
+
+@dataclasses.dataclass
+class Result:
+    status: str
+    iters: int
+    obj: float
+    w: np.ndarray
+    s: np.ndarray
+    lam: np.ndarray
+    y: np.ndarray
+    zl: np.ndarray
+    zu: np.ndarray
+    mu: float
+    sig_w: np.ndarray = None
+    sig_s: np.ndarray = None
+    err: float = np.inf
+    history: list = dataclasses.field(default_factory=list)
+
+
+def _push(v, lo, hi, k1=1e-2, k2=1e-2):
+    """Ipopt's initial bound push (Wachter-Biegler 2006, Sec. 3.6)."""
+    v = v.copy()
+    fl, fu = np.isfinite(lo), np.isfinite(hi)
+    both = fl & fu
+    pl = np.where(fl, k1 * np.maximum(1.0, np.abs(np.where(fl, lo, 0.0))), 0.0)
+    pu = np.where(fu, k1 * np.maximum(1.0, np.abs(np.where(fu, hi, 0.0))), 0.0)
+    rng = np.where(both, hi - lo, np.inf)
+    pl = np.where(both, np.minimum(pl, k2 * rng), pl)
+    pu = np.where(both, np.minimum(pu, k2 * rng), pu)
+    v = np.where(fl, np.maximum(v, lo + pl), v)
+    v = np.where(fu, np.minimum(v, hi - pu), v)
+    return v
+
+
+class _Bounds:
+    """Finite-bound bookkeeping for a vector v with lo <= v <= hi."""
+
+    def __init__(self, lo, hi):
+        self.lo, self.hi = lo, hi
+        self.fl, self.fu = np.isfinite(lo), np.isfinite(hi)
+
+    def dl(self, v):
+        return np.where(self.fl, v - np.where(self.fl, self.lo, 0.0), 1.0)
+
+    def du(self, v):
+        return np.where(self.fu, np.where(self.fu, self.hi, 0.0) - v, 1.0)
+
+    def sigma(self, v, zl, zu):
+        return np.where(self.fl, zl / self.dl(v), 0.0) + np.where(self.fu, zu / self.du(v), 0.0)
+
+    def barrier_grad(self, v, mu):
+        return np.where(self.fl, -mu / self.dl(v), 0.0) + np.where(self.fu, mu / self.du(v), 0.0)
+
+    def barrier(self, v, mu):
+        return -mu * (np.sum(np.log(self.dl(v)[self.fl])) + np.sum(np.log(self.du(v)[self.fu])))
+
+    def dz(self, v, zl, zu, dv, mu):
+        dzl = np.where(self.fl, mu / self.dl(v) - zl - zl / self.dl(v) * dv, 0.0)
+        dzu = np.where(self.fu, mu / self.du(v) - zu + zu / self.du(v) * dv, 0.0)
+        return dzl, dzu
+
+    def max_step(self, v, dv, tau):
+        a = 1.0
+        m = self.fl & (dv < 0)
+        if m.any():
+            a = min(a, np.min(-tau * self.dl(v)[m] / dv[m]))
+        m = self.fu & (dv > 0)
+        if m.any():
+            a = min(a, np.min(tau * self.du(v)[m] / dv[m]))
+        return a
+
+    def compl(self, v, zl, zu, mu):
+        return np.concatenate([(self.dl(v) * zl - mu)[self.fl], (self.du(v) * zu - mu)[self.fu]])
+
+    def safeguard(self, v, zl, zu, mu):
+        zl = np.where(self.fl, np.clip(zl, mu / (KAPPA_SIGMA * self.dl(v)), KAPPA_SIGMA * mu / self.dl(v)), 0.0)
+        zu = np.where(self.fu, np.clip(zu, mu / (KAPPA_SIGMA * self.du(v)), KAPPA_SIGMA * mu / self.du(v)), 0.0)
+        return zl, zu
+
+
+def _max_step_z(z, dz, mask, tau):
+    m = mask & (dz < 0)
+    if not m.any():
+        return 1.0
+    return min(1.0, np.min(-tau * z[m] / dz[m]))
+
+
+def _opt_error(dual, primal, compl, mults, smax=100.0):
+    n = max(1, sum(len(x) for x in mults))
+    sd = max(smax, sum(np.abs(x).sum() for x in mults) / n) / smax
+    e = max(np.abs(dual).max(initial=0.0) / sd, np.abs(primal).max(initial=0.0),
+            np.abs(compl).max(initial=0.0) / sd)
+    return e
+
+
+def _regularized(step_fn, delta_last):
+    """Inertia correction: delta_w = 0, then 1e-4 (or delta_last/3) x 8 until PD."""
+    out = step_fn(0.0)
+    if out[-1]:
+        return out, 0.0
+    d = 1e-4 if delta_last == 0.0 else max(1e-20, delta_last / 3.0)
+    while d < 1e40:
+        out = step_fn(d)
+        if out[-1]:
+            return out, d
+        d *= 8.0
+    raise RuntimeError("inertia correction failed")
+
+
+# ------------------------------------------------------------------ LinRed
+def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False):
+    """Algorithm 1.  record_at: iteration index whose iterate (and the step
+    inputs) is stored in Result.history as a dict."""
+    lay = model.Layout(net)
+    nu, nx, m, nw = lay.nu, lay.nx, lay.m, lay.nw
+    bw = _Bounds(lay.wl, lay.wu)
+    bs = _Bounds(-lay.hu, -lay.hl)
+    w = _push(lay.flat_start(), lay.wl, lay.wu)
+    s = _push(-model.cons_h(lay, w), bs.lo, bs.hi)
+    lam = np.zeros(nx)
+    y = np.zeros(m)
+    zwl, zwu = bw.fl.astype(float), bw.fu.astype(float)
+    zsl, zsu = bs.fl.astype(float), bs.fu.astype(float)
+    mu = mu0
+    nu_pen = 1.0
+    delta = 0.0
+    hist = []
+    for it in range(max_iter + 1):
+        gf, G, A = model.jacobians(lay, w)
+        g = model.cons_g(lay, w)
+        h = model.cons_h(lay, w)
+        grad_w = gf + G.T @ lam + A.T @ y
+        dual_w = grad_w - zwl + zwu
+        dual_s = y - zsl + zsu
+        primal = np.concatenate([g, h + s])
+        mults = [lam, y, zwl[bw.fl], zwu[bw.fu], zsl[bs.fl], zsu[bs.fu]]
+        err0 = _opt_error(np.concatenate([dual_w, dual_s]), primal,
+                          np.concatenate([bw.compl(w, zwl, zwu, 0.0), bs.compl(s, zsl, zsu, 0.0)]), mults)
+        if verbose:
+            print(f"it {it:3d} obj {model.objective(lay, w):.10f} err {err0:.2e} mu {mu:.1e} "
+                  f"inf_pr {np.abs(primal).max():.2e} delta {delta:.1e}")
+        if err0 <= tol:
+            return Result("converged", it, float(model.objective(lay, w)), w, s, lam, y,
+                          (zwl, zsl), (zwu, zsu), mu, err=err0, history=hist)
+        if it == max_iter:
+            break
+        while True:
+            errmu = _opt_error(np.concatenate([dual_w, dual_s]), primal,
+                               np.concatenate([bw.compl(w, zwl, zwu, mu), bs.compl(s, zsl, zsu, mu)]), mults)
+            if errmu > KAPPA_EPS * mu or mu <= tol / 10:
+                break
+            mu = max(tol / 10, min(KAPPA_MU * mu, mu ** THETA_MU))
+        tau = max(TAU_MIN, 1.0 - mu)
+        W = model.lagrangian_hessian(lay, w, lam, y)
+        sig_w = bw.sigma(w, zwl, zwu)
+        sig_s = bs.sigma(s, zsl, zsu)
+        r = np.concatenate([grad_w + bw.barrier_grad(w, mu), y + bs.barrier_grad(s, mu), g, h + s])
+        (pw, ps, plam, py, Kc, ok), delta = _regularized(
+            lambda d: kkt.condensed_step(G, A, W, sig_w, sig_s, r, nu, delta_w=d), delta)
+        if record_at is not None and it == record_at:
+            hist.append(dict(it=it, w=w.copy(), s=s.copy(), lam=lam.copy(), y=y.copy(),
+                             sig_w=sig_w.copy(), sig_s=sig_s.copy(), r=r.copy(), mu=mu,
+                             delta=delta, pw=pw, ps=ps, plam=plam, py=py, Kc=Kc))
+        phi0 = None
+        for attempt in range(40):
+            dzwl, dzwu = bw.dz(w, zwl, zwu, pw, mu)
+            dzsl, dzsu = bs.dz(s, zsl, zsu, ps, mu)
+            amax = min(bw.max_step(w, pw, tau), bs.max_step(s, ps, tau))
+            az = min(_max_step_z(zwl, dzwl, bw.fl, tau), _max_step_z(zwu, dzwu, bw.fu, tau),
+                     _max_step_z(zsl, dzsl, bs.fl, tau), _max_step_z(zsu, dzsu, bs.fu, tau))
+            # l1 merit  phi = f + barrier + nu ||c||_1
+            nu_pen = max(nu_pen, 1.1 * max(np.abs(lam + plam).max(initial=0), np.abs(y + py).max(initial=0)))
+
+            def merit(wt, st):
+                c = np.concatenate([model.cons_g(lay, wt), model.cons_h(lay, wt) + st])
+                return model.objective(lay, wt) + bw.barrier(wt, mu) + bs.barrier(st, mu) + nu_pen * np.abs(c).sum()
+            phi0 = merit(w, s)
+            dphi = (gf + bw.barrier_grad(w, mu)) @ pw + bs.barrier_grad(s, mu) @ ps - nu_pen * np.abs(primal).sum()
+            a = amax
+            while a > 1e-4 * amax:
+                if merit(w + a * pw, s + a * ps) <= phi0 + ETA * a * min(dphi, 0.0):
+                    break
+                a *= 0.5
+            if verbose:
+                print(f"    amax {amax:.2e} a {a:.2e} dphi {dphi:.3e} |pw| {np.abs(pw).max():.2e}")
+            if a > 1e-4 * amax:
+                break
+            # backtracking failed: shorten the step by a larger primal regularization
+            delta = max(1e-8, 10.0 * delta)
+            pw, ps, plam, py, Kc, ok = kkt.condensed_step(G, A, W, sig_w, sig_s, r, nu, delta_w=delta)
+            if not ok:
+                (pw, ps, plam, py, Kc, ok), delta = _regularized(
+                    lambda d: kkt.condensed_step(G, A, W, sig_w, sig_s, r, nu, delta_w=d), delta)
+        w = w + a * pw
+        s = s + a * ps
+        lam = lam + a * plam
+        y = y + a * py
+        zwl, zwu = zwl + az * dzwl, zwu + az * dzwu
+        zsl, zsu = zsl + az * dzsl, zsu + az * dzsu
+        zwl, zwu = bw.safeguard(w, zwl, zwu, mu)
+        zsl, zsu = bs.safeguard(s, zsl, zsu, mu)
+    return Result("max_iter", max_iter, float(model.objective(lay, w)), w, s, lam, y,
+                  (zwl, zsl), (zwu, zsu), mu, err=err0, history=hist)
+
+
+# ------------------------------------------------------------------ RedLin
+def newton_projection(lay, w, tol=1e-10, max_iter=30):
+    """Solve g(x, u) = 0 for x at fixed u by Newton-Raphson (Sec. 4.4).
+    Returns (w with projected x, iterations, converged)."""
+    w = w.copy()
+    nu = lay.nu
+    import scipy.sparse.linalg as spla
+    for k in range(max_iter + 1):
+        g = model.cons_g(lay, w)
+        if np.abs(g).max() <= tol:
+            return w, k, True
+        if k == max_iter or not np.all(np.isfinite(g)):
+            break
+        _, G, _ = model.jacobians(lay, w)
+        dx = spla.splu(G[:, nu:].tocsc()).solve(-g)
+        w[nu:] += dx
+    return w, max_iter, False
+
+
+def redlin(net, tol=1e-8, max_iter=300, mu0=0.1, verbose=False, record_at=None):
+    """Algorithm 2.  State bounds (Vm at load buses) become rows -x_b of h_r."""
+    lay = model.Layout(net)
+    nu, nx, m = lay.nu, lay.nx, lay.m
+    xb = np.nonzero(np.isfinite(lay.wl[nu:]))[0]           # bounded states
+    nb_ = len(xb)
+    mr = m + nb_
+    bu = _Bounds(lay.wl[:nu], lay.wu[:nu])
+    bs = _Bounds(np.concatenate([-lay.hu, lay.wl[nu:][xb]]),
+                 np.concatenate([-lay.hl, lay.wu[nu:][xb]]))
+    w = _push(lay.flat_start(), lay.wl, lay.wu)
+    w, _, ok = newton_projection(lay, w)
+    if not ok:
+        raise RuntimeError("initial power flow failed")
+
+    def hr(wt):
+        return np.concatenate([model.cons_h(lay, wt), -wt[nu:][xb]])
+
+    s = _push(-hr(w), bs.lo, bs.hi)
+    y = np.zeros(mr)
+    zul, zuu = bu.fl.astype(float), bu.fu.astype(float)
+    zsl, zsu = bs.fl.astype(float), bs.fu.astype(float)
+    mu = mu0
+    nu_pen = 1.0
+    delta = 0.0
+    hist = []
+    import scipy.sparse as sp
+    Eb = sp.coo_matrix((-np.ones(nb_), (np.arange(nb_), xb)), shape=(nb_, nx)).tocsr()
+    for it in range(max_iter + 1):
+        gf, G, A = model.jacobians(lay, w)
+        blk = kkt.split_blocks(G, A, sp.csr_matrix((lay.nw, lay.nw)), nu)
+        _, solveT = kkt._gx_solver(blk["Gx"])
+        yh, yb = y[:m], y[m:]
+        # adjoint step: lambda = -G_x^{-T} grad_x L
+        lam = -solveT(gf[nu:] + blk["Ax"].T @ yh + Eb.T @ yb)
+        grad_u = gf[:nu] + blk["Gu"].T @ lam + blk["Au"].T @ yh
+        dual_u = grad_u - zul + zuu
+        dual_s = y - zsl + zsu
+        primal = hr(w) + s
+        mults = [y, zul[bu.fl], zuu[bu.fu], zsl[bs.fl], zsu[bs.fu]]
+        err0 = _opt_error(np.concatenate([dual_u, dual_s]), primal,
+                          np.concatenate([bu.compl(w[:nu], zul, zuu, 0.0), bs.compl(s, zsl, zsu, 0.0)]), mults)
+        if verbose:
+            print(f"it {it:3d} obj {model.objective(lay, w):.10f} err {err0:.2e} mu {mu:.1e} delta {delta:.1e}")
+        if err0 <= tol:
+            return Result("converged", it, float(model.objective(lay, w)), w, s, lam, y,
+                          (zul, zsl), (zuu, zsu), mu, err=err0, history=hist)
+        if it == max_iter:
+            break
+        while True:
+            errmu = _opt_error(np.concatenate([dual_u, dual_s]), primal,
+                               np.concatenate([bu.compl(w[:nu], zul, zuu, mu), bs.compl(s, zsl, zsu, mu)]), mults)
+            if errmu > KAPPA_EPS * mu or mu <= tol / 10:
+                break
+            mu = max(tol / 10, min(KAPPA_MU * mu, mu ** THETA_MU))
+        tau = max(TAU_MIN, 1.0 - mu)
+        W = model.lagrangian_hessian(lay, w, lam, yh)
+        Ar = sp.vstack([A, sp.hstack([sp.csr_matrix((nb_, nu)), Eb])]).tocsr()
+        sig_u = bu.sigma(w[:nu], zul, zuu)
+        sig_s = bs.sigma(s, zsl, zsu)
+        r1 = grad_u + bu.barrier_grad(w[:nu], mu)
+        r2 = y + bs.barrier_grad(s, mu)
+        r3 = primal
+
+        def step(d):
+            # Eq. reduced:kktsystem condensed by Theorem 2; W_hat without Sigma_x
+            sig_w = np.concatenate([sig_u, np.zeros(nx)])
+            W_hat, A_hat, _, _, _ = kkt.reduced_blocks(G, Ar, W, sig_w, nu)
+            Kc = W_hat + np.diag(sig_u) + A_hat.T @ (sig_s[:, None] * A_hat) + d * np.eye(nu)
+            try:
+                L = np.linalg.cholesky(Kc)
+            except np.linalg.LinAlgError:
+                return None, None, None, Kc, False
+            import scipy.linalg as sla
+            rhs = -(r1 + A_hat.T @ (sig_s * r3) - A_hat.T @ r2)
+            pu = sla.cho_solve((L, True), rhs)
+            py = sig_s * (A_hat @ pu + r3) - r2
+            ps = -(A_hat @ pu + r3)
+            return pu, ps, py, Kc, True
+        (pu, ps, py, Kc, ok), delta = _regularized(step, delta)
+        if record_at is not None and it == record_at:
+            hist.append(dict(it=it, w=w.copy(), s=s.copy(), lam=lam.copy(), y=y.copy(),
+                             sig_u=sig_u.copy(), sig_s=sig_s.copy(), mu=mu, delta=delta,
+                             pu=pu, ps=ps, py=py, Kc=Kc))
+        dzul, dzuu = bu.dz(w[:nu], zul, zuu, pu, mu)
+        dzsl, dzsu = bs.dz(s, zsl, zsu, ps, mu)
+        amax = min(bu.max_step(w[:nu], pu, tau), bs.max_step(s, ps, tau))
+        az = min(_max_step_z(zul, dzul, bu.fl, tau), _max_step_z(zuu, dzuu, bu.fu, tau),
+                 _max_step_z(zsl, dzsl, bs.fl, tau), _max_step_z(zsu, dzsu, bs.fu, tau))
+        nu_pen = max(nu_pen, 1.1 * np.abs(y + py).max(initial=0))
+
+        def merit(wt, st):
+            return (model.objective(lay, wt) + bu.barrier(wt[:nu], mu) + bs.barrier(st, mu)
+                    + nu_pen * np.abs(hr(wt) + st).sum())
+        phi0 = merit(w, s)
+        # directional derivative of f_r along p_u: grad f_r = g_u - G_u^T G_x^{-T} g_x
+        gfr = gf[:nu] - blk["Gu"].T @ solveT(gf[nu:])
+        dphi = (gfr + bu.barrier_grad(w[:nu], mu)) @ pu + bs.barrier_grad(s, mu) @ ps \
+            - nu_pen * np.abs(primal).sum()
+        a = amax
+        wn = None
+        while a > 1e-12:
+            wt = w.copy()
+            wt[:nu] += a * pu
+            wt, _, okp = newton_projection(lay, wt)
+            if okp and merit(wt, s + a * ps) <= phi0 + ETA * a * min(dphi, 0.0):
+                wn = wt
+                break
+            a *= 0.5
+        if wn is None:
+            return Result("line_search_failed", it, float(model.objective(lay, w)), w, s, lam, y,
+                          (zul, zsl), (zuu, zsu), mu, err=err0, history=hist)
+        w = wn
+        s = s + a * ps
+        y = y + a * py
+        zul, zuu = zul + az * dzul, zuu + az * dzuu
+        zsl, zsu = zsl + az * dzsl, zsu + az * dzsu
+        zul, zuu = bu.safeguard(w[:nu], zul, zuu, mu)
+        zsl, zsu = bs.safeguard(s, zsl, zsu, mu)
+    return Result("max_iter", max_iter, float(model.objective(lay, w)), w, s, None, y,
+                  (zul, zsl), (zuu, zsu), mu, err=err0, history=hist)

@@ -1,0 +1,291 @@
+"""Pins for the CPU oracle: each check ties an oracle function to something
+other than itself (a printed table, a different formulation, the complex step,
+finite differences, a library factorisation, a closed form, an independent
+optimiser).  No GPU needed."""
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+
+import gridgen
+from oracle import ipm, kkt, model
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _ring_net(nb, ng):
+    """Minimal ring network with ng generators on buses 0..ng-1 (counting only)."""
+    z = np.zeros
+    lf = np.arange(nb, dtype=np.int32)
+    lt = ((np.arange(nb) + 1) % nb).astype(np.int32)
+    one = np.ones(nb)
+    return gridgen.Network(
+        name="ring", nb=nb, slack=0, Pd=z(nb), Qd=z(nb), Vmin=0.9 * one, Vmax=1.1 * one,
+        lf=lf, lt=lt, r=0.01 * one, x=0.1 * one, b=z(nb), rate=z(nb),
+        gbus=np.arange(ng, dtype=np.int32), Pmin=z(ng), Pmax=np.ones(ng), Qmin=-np.ones(ng),
+        Qmax=np.ones(ng), c2=np.ones(ng), c1=np.ones(ng))
+
+
+# ----------------------------------------------------------------- sizes
+def test_table1_variable_split():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "table1_counts.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 7
+    for name, nb, ng, nx, nu in rows:
+        lay = model.Layout(_ring_net(int(nb), int(ng)))
+        assert (lay.nx, lay.nu) == (int(nx), int(nu)), name
+
+
+def test_ring30_sizes():
+    # the 30-bus workload: 11 controls and 53 states, every one of 41 lines limited
+    lay = model.Layout(gridgen.ring30())
+    assert (lay.nu, lay.nx, lay.nl, lay.m) == (11, 53, 41, 1 + 6 + 2 * 41)
+
+
+# ------------------------------------------------------------ the model
+def _ybus(net):
+    """Nodal admittance matrix from the pi-model, by plain loops."""
+    Y = np.zeros((net.nb, net.nb), complex)
+    for l in range(net.nl):
+        f, t = net.lf[l], net.lt[l]
+        ys = 1.0 / complex(net.r[l], net.x[l])
+        Y[f, f] += ys + 0.5j * net.b[l]
+        Y[t, t] += ys + 0.5j * net.b[l]
+        Y[f, t] -= ys
+        Y[t, f] -= ys
+    return Y
+
+
+@pytest.mark.parametrize("make", [gridgen.tiny3, gridgen.ring30])
+def test_injections_match_nodal_form(make):
+    net = make()
+    lay = model.Layout(net)
+    rng = np.random.default_rng(3)
+    w = lay.flat_start() + 0.05 * rng.standard_normal(lay.nw)
+    Vm, Va = lay.voltages(w)
+    P, Q = model.injections(lay, Vm, Va)
+    V = Vm * np.exp(1j * Va)
+    S = V * np.conj(_ybus(net) @ V)
+    np.testing.assert_allclose(P, S.real, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(Q, S.imag, rtol=0, atol=1e-12)
+
+
+def _complex_step_jac(fun, w, n_out, h=1e-30):
+    J = np.zeros((n_out, len(w)))
+    for j in range(len(w)):
+        wc = w.astype(complex)
+        wc[j] += 1j * h
+        J[:, j] = np.atleast_1d(fun(wc)).imag / h
+    return J
+
+
+@pytest.mark.parametrize("make", [gridgen.tiny3, gridgen.ring30])
+def test_first_derivatives_complex_step(make):
+    lay = model.Layout(make())
+    rng = np.random.default_rng(5)
+    w = lay.flat_start() + 0.05 * rng.standard_normal(lay.nw)
+    gf, G, A = model.jacobians(lay, w)
+    Gcs = _complex_step_jac(lambda v: model.cons_g(lay, v), w, lay.nx)
+    Acs = _complex_step_jac(lambda v: model.cons_h(lay, v), w, lay.m)
+    fcs = _complex_step_jac(lambda v: model.objective(lay, v), w, 1)[0]
+    assert np.abs(G.toarray() - Gcs).max() <= 1e-12 * max(1, np.abs(Gcs).max())
+    assert np.abs(A.toarray() - Acs).max() <= 1e-12 * max(1, np.abs(Acs).max())
+    assert np.abs(gf - fcs).max() <= 1e-12 * max(1, np.abs(fcs).max())
+
+
+@pytest.mark.parametrize("make", [gridgen.tiny3, gridgen.ring30])
+def test_hessian_matches_fd_of_gradient(make):
+    lay = model.Layout(make())
+    rng = np.random.default_rng(7)
+    w = lay.flat_start() + 0.05 * rng.standard_normal(lay.nw)
+    lam = rng.standard_normal(lay.nx)
+    y = rng.standard_normal(lay.m)
+    W = model.lagrangian_hessian(lay, w, lam, y).toarray()
+    # gradient of f + lam^T g + y^T h by the complex step, differenced centrally
+    def grad(v):
+        return _complex_step_jac(
+            lambda z: model.objective(lay, z) + lam @ model.cons_g(lay, z) + y @ model.cons_h(lay, z),
+            v, 1)[0]
+    h = 1e-5
+    Wfd = np.zeros_like(W)
+    for j in range(lay.nw):
+        e = np.zeros(lay.nw)
+        e[j] = h
+        Wfd[:, j] = (grad(w + e) - grad(w - e)) / (2 * h)
+    assert np.abs(W - W.T).max() <= 1e-12 * np.abs(W).max()
+    assert np.abs(W - Wfd).max() <= 1e-7 * np.abs(W).max()
+
+
+# ------------------------------------------------------------- the KKT
+def _random_point(make, seed, scale_sig=(0.1, 10.0)):
+    lay = model.Layout(make())
+    rng = np.random.default_rng(seed)
+    w = lay.flat_start() + 0.02 * rng.standard_normal(lay.nw)
+    lam = rng.standard_normal(lay.nx)
+    y = rng.standard_normal(lay.m)
+    _, G, A = model.jacobians(lay, w)
+    W = model.lagrangian_hessian(lay, w, lam, y)
+    sw = rng.uniform(*scale_sig, lay.nw)
+    ss = rng.uniform(*scale_sig, lay.m)
+    r = rng.standard_normal(lay.nw + 2 * lay.m + lay.nx)
+    return lay, G, A, W, sw, ss, r
+
+
+@pytest.mark.parametrize("make,seed", [(gridgen.tiny3, 1), (gridgen.ring30, 2), (gridgen.ring30, 3)])
+def test_condensed_step_equals_full_space_ldl(make, seed):
+    """Theorems 1 and 2: the condensed route reaches the full-space Newton step."""
+    lay, G, A, W, sw, ss, r = _random_point(make, seed)
+    d = 0.0
+    while True:
+        out = kkt.condensed_step(G, A, W, sw, ss, r, lay.nu, delta_w=d)
+        if out[-1]:
+            break
+        d = 1e-2 if d == 0 else d * 8
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, d), np.zeros(lay.nx)])
+    Kfull = kkt.kaug(G, A, Wd, sw, ss).toarray()
+    # full-space step through scipy's Bunch-Kaufman LDL^T: K = L D L^T, L[perm] lower
+    import scipy.linalg as sla
+    lu, dd, perm = sla.ldl(Kfull)
+    tl = lu[perm]
+    z = sla.solve_triangular(tl, -r[perm], lower=True, unit_diagonal=True)
+    v = np.linalg.solve(dd, z)
+    q = sla.solve_triangular(tl.T, v, lower=False, unit_diagonal=True)
+    p_ref = np.empty_like(q)
+    p_ref[perm] = q
+    assert np.abs(Kfull @ p_ref + r).max() <= 1e-9 * np.abs(r).max()
+    p = np.concatenate(out[:4])
+    assert np.abs(p - p_ref).max() <= 1e-10 * np.abs(p_ref).max()
+
+
+@pytest.mark.parametrize("make,seed", [(gridgen.tiny3, 4), (gridgen.ring30, 5)])
+def test_kred_definition_is_symmetric_and_matches_theorem1(make, seed):
+    lay, G, A, W, sw, ss, r = _random_point(make, seed)
+    Kr = kkt.kred_definition(G, A, W, sw, ss, lay.nu)
+    assert np.abs(Kr - Kr.T).max() <= 1e-13 * np.abs(Kr).max()
+    W_hat, A_hat, _, _, _ = kkt.reduced_blocks(G, A, W, sw, lay.nu)
+    Kc = W_hat + np.diag(sw[:lay.nu]) + A_hat.T @ (ss[:, None] * A_hat)
+    assert np.abs(Kr - Kc).max() <= 1e-12 * np.abs(Kr).max()
+
+
+@pytest.mark.parametrize("delta", [0.0, 1.0, 10.0, 100.0, 1e3])
+def test_inertia_theorem3(delta):
+    """K_cond positive definite <=> inertia(K_aug) = (nx+nu+m, nx+m, 0)."""
+    lay, G, A, W, sw, ss, r = _random_point(gridgen.ring30, 11)
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, delta), np.zeros(lay.nx)])
+    Kr = kkt.kred_definition(G, A, Wd, sw, ss, lay.nu)
+    pd = np.linalg.eigvalsh(Kr).min() > 0
+    inert = kkt.inertia_dense(kkt.kaug(G, A, Wd, sw, ss))
+    assert pd == (inert == (lay.nw + lay.m, lay.nx + lay.m, 0))
+
+
+def test_inertia_both_outcomes_occur():
+    lay, G, A, W, sw, ss, r = _random_point(gridgen.ring30, 11)
+    outs = set()
+    for delta in (0.0, 1e3):
+        Wd = W + sp.diags(np.r_[np.full(lay.nu, delta), np.zeros(lay.nx)])
+        outs.add(bool(np.linalg.eigvalsh(kkt.kred_definition(G, A, Wd, sw, ss, lay.nu)).min() > 0))
+    assert outs == {True, False}
+
+
+# ------------------------------------------------------------- the IPM
+def _economic_dispatch(net):
+    """min sum c2 P^2 + c1 P  s.t. sum P = sum Pd, Pmin <= P <= Pmax, by bisection
+    on the marginal price."""
+    def total(lmb):
+        return np.clip((lmb - net.c1) / (2 * net.c2), net.Pmin, net.Pmax).sum()
+    lo, hi = 0.0, 1e4
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if total(mid) < net.Pd.sum() else (lo, mid)
+    P = np.clip((0.5 * (lo + hi) - net.c1) / (2 * net.c2), net.Pmin, net.Pmax)
+    return float(np.sum(net.c2 * P * P + net.c1 * P))
+
+
+@pytest.mark.parametrize("variant", ["linred", "redlin"])
+def test_lossless_network_is_economic_dispatch(variant):
+    # Losses vanish for every voltage profile, so the optimal voltages form a
+    # continuum and the reduced Hessian is singular along it: near mu = 1e-9 the
+    # infeasible-path variant can stall just above 1e-8 on the voltage continuum.
+    # The objective, which the continuum does not move, is what is pinned.
+    net = gridgen.lossless(gridgen.ring30())
+    res = getattr(ipm, variant)(net, max_iter=60)
+    assert res.err <= 1e-6
+    ed = _economic_dispatch(net)
+    assert abs(res.obj - ed) <= 1e-8 * abs(ed)
+
+
+def test_tiny3_matches_independent_optimizer():
+    net = gridgen.tiny3()
+    lay = model.Layout(net)
+    res = ipm.linred(net)
+    assert res.status == "converged"
+    cons = [dict(type="eq", fun=lambda v: model.cons_g(lay, v)),
+            dict(type="ineq", fun=lambda v: lay.hu[np.isfinite(lay.hu)] - model.cons_h(lay, v)[np.isfinite(lay.hu)]),
+            dict(type="ineq", fun=lambda v: model.cons_h(lay, v)[np.isfinite(lay.hl)] - lay.hl[np.isfinite(lay.hl)])]
+    bounds = [(None if not np.isfinite(a) else a, None if not np.isfinite(b) else b)
+              for a, b in zip(lay.wl, lay.wu)]
+    best = np.inf
+    rng = np.random.default_rng(0)
+    for k in range(4):
+        w0 = lay.flat_start() + (0 if k == 0 else 0.02 * rng.standard_normal(lay.nw))
+        out = so.minimize(lambda v: model.objective(lay, v), w0, method="SLSQP", bounds=bounds,
+                          constraints=cons, options=dict(ftol=1e-14, maxiter=500))
+        if out.success and np.abs(model.cons_g(lay, out.x)).max() < 1e-9:
+            best = min(best, out.fun)
+    assert np.isfinite(best)
+    assert abs(res.obj - best) <= 1e-6 * abs(best)
+
+
+def test_variants_agree_and_power_balance_holds():
+    net = gridgen.ring30()
+    lay = model.Layout(net)
+    a = ipm.linred(net)
+    b = ipm.redlin(net)
+    assert a.status == b.status == "converged"
+    assert abs(a.obj - b.obj) <= 1e-8 * abs(a.obj)
+    assert np.abs(model.cons_g(lay, a.w)).max() <= 1e-8
+    assert np.abs(model.cons_g(lay, b.w)).max() <= 1e-10
+
+
+def test_reduced_derivatives_through_projection():
+    """Reduced-derivative theorem (Sec. 2.3): grad f_r and W_hat_uu against
+    finite differences of f_r and of grad_u L_r through the Newton projection."""
+    import scipy.sparse.linalg as spla
+    net = gridgen.ring30()
+    lay = model.Layout(net)
+    nu = lay.nu
+    w, _, ok = ipm.newton_projection(lay, lay.flat_start())
+    assert ok
+    rng = np.random.default_rng(9)
+    y = rng.uniform(-1, 1, lay.m)
+
+    def reduced(u):
+        wt = w.copy()
+        wt[:nu] = u
+        wt, _, okp = ipm.newton_projection(lay, wt, tol=1e-14)
+        assert okp
+        gf, G, A = model.jacobians(lay, wt)
+        Gx = G[:, nu:].tocsc()
+        lam = -spla.splu(Gx).solve(gf[nu:] + A[:, nu:].T @ y, trans="T")
+        grad = gf[:nu] + G[:, :nu].T @ lam + A[:, :nu].T @ y
+        return wt, lam, grad, gf, G, A
+    u0 = w[:nu].copy()
+    wt, lam, grad0, gf, G, A = reduced(u0)
+    W = model.lagrangian_hessian(lay, wt, lam, y)
+    W_hat, _, _, _, _ = kkt.reduced_blocks(G, A, W, np.zeros(lay.nw), nu)
+    Hfd = np.zeros((nu, nu))
+    gfr_fd = np.zeros(nu)
+    h = 1e-6
+    for j in range(nu):
+        e = np.zeros(nu)
+        e[j] = h
+        Hfd[:, j] = (reduced(u0 + e)[2] - reduced(u0 - e)[2]) / (2 * h)
+        fp = model.objective(lay, reduced(u0 + e)[0])
+        fm = model.objective(lay, reduced(u0 - e)[0])
+        gfr_fd[j] = (fp - fm) / (2 * h)
+    Gx = G[:, nu:].tocsc()
+    gfr = gf[:nu] - G[:, :nu].T @ spla.splu(Gx).solve(gf[nu:], trans="T")
+    assert np.abs(gfr - gfr_fd).max() <= 1e-6 * np.abs(gfr).max()
+    assert np.abs(W_hat - Hfd).max() <= 1e-5 * np.abs(W_hat).max()
