@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the condensed-IPM hot path on GB300.
+
+Metric: condense + Cholesky milliseconds per IPM iteration (FP64), on the
+seeded 2,000-bus lattice workload (nu = 399 controls, nx = 3,799 states).  One
+step is one pass of the per-iteration hot path at a fixed mid-solve-like
+iterate: model derivatives, G_x refactorisation, multi-right-hand-side
+triangular solves over all nu columns, K assembly and H = K Z, the condensed
+matrix, its Cholesky factor, and the Newton-step recovery.  ``value`` is the
+condense + Cholesky part (the metric); ``ms_per_step`` the whole step.
+
+L2 (129 MB) holds the whole working set of this workload, so a 256 MB buffer is
+written on the stream between timed steps.  Device time comes from CUDA events
+on the library's stream.  ``--impl reference`` times the CPU FP64 oracle on the
+host cores for the same metric and workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gridgen  # noqa: E402
+
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flop/DFMA x GHz (max SM clock)
+METRIC = "condense+Cholesky ms/IPM iter"
+UNIT = "ms/iter"
+WORKLOAD = "grid2000: 2,000-bus lattice, 200 generators, nu=399, nx=3,799, FP64, LinRed iterate"
+
+
+def synthetic_iterate(net, nx, nu, m, seed=2203):
+    """Flat-start-like primal point with moderate multipliers and barrier terms."""
+    rng = np.random.default_rng(seed)
+    is_gen = np.zeros(net.nb, bool)
+    is_gen[net.gbus] = True
+    n_ns = net.nb - 1
+    x = np.concatenate([0.02 * rng.standard_normal(n_ns), 1.0 + 0.01 * rng.standard_normal(net.nb - net.ng)])
+    u = np.concatenate([np.clip(1.05, net.Vmin[net.gbus], net.Vmax[net.gbus]),
+                        0.5 * (net.Pmin[1:] + net.Pmax[1:])])
+    lam = 20.0 + rng.standard_normal(nx)
+    y = 0.1 * rng.random(m)
+    sig_u = rng.uniform(1.0, 10.0, nu)
+    sig_x = np.where(np.arange(nx) < n_ns, 0.0, rng.uniform(1.0, 10.0, nx))
+    sig_s = rng.uniform(1.0, 10.0, m)
+    r = rng.standard_normal(nu + nx + 2 * m + nx)
+    return dict(x=x, u=u, lam=lam, y=y, sig_u=sig_u, sig_x=sig_x, sig_s=sig_s, r=r)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for ln in open(self.path):
+            p = [c.strip() for c in ln.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(p[1]) for p in rows if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in rows if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in rows for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_condense(net, it, budget_s=15.0):
+    """Oracle condense + Cholesky per iteration at the same iterate (host cores)."""
+    from oracle import kkt, model
+    lay = model.Layout(net)
+    w = np.concatenate([it["u"], it["x"]])
+    sw = np.concatenate([it["sig_u"], it["sig_x"]])
+    reps, t0 = 0, time.perf_counter()
+    times = []
+    while time.perf_counter() - t0 < budget_s or reps < 1:
+        t1 = time.perf_counter()
+        _, G, A = model.jacobians(lay, w)
+        W = model.lagrangian_hessian(lay, w, it["lam"], it["y"])
+        t2 = time.perf_counter()
+        K = kkt.kred_definition(G, A, W, sw, it["sig_s"], lay.nu)
+        np.linalg.cholesky(K + 1e-8 * np.eye(lay.nu))
+        times.append((time.perf_counter() - t2) * 1e3)
+        reps += 1
+        if reps >= 200:
+            break
+    return float(np.median(times)), reps
+
+
+def run_reference(args):
+    """The oracle as the reference arm: same metric, workload and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    net = gridgen.grid2000()
+    from oracle import model
+    lay = model.Layout(net)
+    it = synthetic_iterate(net, lay.nx, lay.nu, lay.m)
+    for _ in range(args.warmup):
+        cpu_oracle_condense(net, it, budget_s=0.0)
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ms, _ = cpu_oracle_condense(net, it, budget_s=0.0)
+        per.append(ms)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(per))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{args.steps} oracle condense+Cholesky evaluations of the same iterate"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 10,000-bus measurement")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2203_11875_gb300 import binding, build
+    build.build()
+    dev = torch.device("cuda", local)
+    net = gridgen.grid2000()
+    h = binding.Handle(net)
+    stream = torch.cuda.Stream(device=dev)
+    h.set_stream(stream)
+    it = synthetic_iterate(net, h.nx, h.nu, h.m)
+    D = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in it.items()}
+    step = torch.zeros(h.n_kkt, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def hot_step(delta):
+        h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        col = h.kkt_factor(delta)
+        return col
+
+    torch.cuda.synchronize()
+    delta = 0.0
+    for _ in range(max(args.warmup, 3)):
+        while hot_step(delta) >= 0:
+            delta = max(1e-4, 8 * delta)
+        h.kkt_solve(D["r"], step)
+    torch.cuda.synchronize()
+    n_launch0 = binding.launch_count()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    h.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+        h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+        ev[k][1].record(stream)
+        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        assert h.kkt_factor(delta) == -1
+        ev[k][2].record(stream)
+        h.kkt_solve(D["r"], step)
+        ev[k][3].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    n_launch = binding.launch_count() - n_launch0
+    phases = h.phase_times()
+    h.profile(False)
+    cf = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    full = [ev[k][0].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    t_cf, t_full = float(np.mean(cf)), float(np.mean(full))
+    if dist:
+        t = torch.tensor([t_cf, t_full], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_cf, t_full = t.tolist()
+    # roofline of the dominant kernel: the multi-RHS triangular solves
+    st = h.stats()
+    S = (st["nnz_lu"] - h.nx) // 2           # strict lower = strict upper entries
+    flops_trsm = (4 * 2 * S * h.nu + 2 * h.nx * h.nu)  # L, U, U^T, L^T over nu columns; 2 diagonal scalings
+    trsm_ms, trsm_n = phases["trsm"]
+    per_launch_ms = trsm_ms / max(1, trsm_n)
+    achieved = (flops_trsm / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
+    # end-to-end through the public API with pinned host buffers
+    host = {k: torch.as_tensor(v, dtype=torch.float64).pin_memory() for k, v in it.items()}
+    step_h = torch.zeros(h.n_kkt, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = step_h.numel() * 8
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2e = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            for key in host:
+                D[key].copy_(host[key], non_blocking=True)
+        h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        h.kkt_factor(delta)
+        h.kkt_solve(D["r"], step)
+        with torch.cuda.stream(stream):
+            step_h.copy_(step, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e))
+    out = {"metric": METRIC, "value": t_cf / max(1, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_full, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "l2": "256 MB flush written between timed steps",
+                      "route": "adjoint", "rhs_block": None, "delta_w": delta},
+           "clocks": clocks, "gpu_launches": int(n_launch),
+           "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "includes": "H2D of x,u,lambda,y,Sigma,r + derivatives + condense + Cholesky + step + D2H of the step"},
+           "phases_ms_per_step": {p: v[0] / args.steps for p, v in phases.items()},
+           "roofline": {"bound": "alu", "kernel": "k_trsm (multi-RHS triangular solve)",
+                        "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                        "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None, "traffic": None,
+                        "flops_per_launch": flops_trsm / 4, "ms_per_launch": per_launch_ms,
+                        "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+           "symbolic": st}
+    if world > 1:
+        out["value"] = t_cf / world
+    if not args.no_scale:
+        n10 = gridgen.grid10k()
+        h10 = binding.Handle(n10)
+        h10.set_stream(stream)
+        i10 = synthetic_iterate(n10, h10.nx, h10.nu, h10.m)
+        D10 = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in i10.items()}
+        d10 = 0.0
+        for _ in range(2):
+            h10.eval_derivatives(D10["x"], D10["u"], D10["lam"], D10["y"])
+            h10.condense(D10["sig_u"], D10["sig_x"], D10["sig_s"])
+            while h10.kkt_factor(d10) >= 0:
+                d10 = max(1e-4, 8 * d10)
+        h10.profile(True)
+        t10 = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h10.eval_derivatives(D10["x"], D10["u"], D10["lam"], D10["y"])
+            with torch.cuda.stream(stream):
+                a.record(stream)
+            h10.condense(D10["sig_u"], D10["sig_x"], D10["sig_s"])
+            h10.kkt_factor(d10)
+            with torch.cuda.stream(stream):
+                b.record(stream)
+            b.synchronize()
+            t10.append(a.elapsed_time(b))
+        ph10 = h10.phase_times()
+        out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)),
+                          "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
+                          "symbolic": h10.stats()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms, reps = cpu_oracle_condense(net, it)
+        out["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"{reps} oracle condense+Cholesky evaluations of the same grid2000 "
+                                         "iterate (SciPy splu + BLAS, all host threads)"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

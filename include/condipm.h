@@ -1,0 +1,191 @@
+/*
+ * condipm.h -- C ABI of the condensed interior-point hot path (FP64, sm_103a).
+ *
+ * The library condenses the augmented KKT system of a state-control AC optimal
+ * power flow into the dense nu x nu matrix
+ *
+ *     Kred = Z^T (W + diag(Sigma_u, Sigma_x) + A^T Sigma_s A) Z,  Z = [I; -G_x^{-1} G_u]
+ *
+ * (Eq. algo:reduction, Sec. 3.3; Theorems 1-2, Sec. 2.2), factors it by dense
+ * Cholesky (Algorithm 1, "control step"; Theorem 3 makes positive definiteness the
+ * inertia test) and recovers the full Newton step (Theorem 1 and 2 recoveries).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * FP64 everywhere; indices are 0-based int32.
+ *  * Variables: u = [Vm at the ng generator buses (generator order);
+ *                    Pg of generators 1..ng-1]                       (nu = 2 ng - 1)
+ *               x = [theta at the non-slack buses (ascending bus index);
+ *                    Vm at the buses without a generator (ascending)] (nx = 2 nb - ng - 1)
+ *    Generators must sit on distinct buses; generator 0's bus is the slack bus.
+ *  * g(x,u) (state equation, Eq. 1) = [P balance at non-slack buses; Q balance at
+ *    load buses], in the order of x.  h(x,u) = [Pg of generator 0; Qg of every
+ *    generator; |S|^2 at the from-end of every flow-limited line (rate > 0,
+ *    ascending line index); |S|^2 at their to-ends]  (m = 1 + ng + 2 nlim).
+ *    The slack form is h + s = 0 (Eq. 3), so slack bounds are [-hU, -hL].
+ *  * Full-space right-hand sides and steps use the block order of
+ *    Eq. kktmatrix:normal: [r1 (nu) | r2 (nx) | r3 (m) | r4 (nx) | r5 (m)], i.e.
+ *    n_kkt = nu + 2 nx + 2 m doubles per right-hand side, and the coupling between
+ *    p_s and p_y is +I (the sign that h + s = 0 implies).
+ *  * Pointers documented "device" are CUDA device pointers owned by the caller;
+ *    "host" pointers are ordinary host memory.  The library never frees caller
+ *    memory.  Device work is issued on the handle's stream (opf_set_stream).
+ *  * Every call returns an OPF_* status; none aborts.  Device-side failures
+ *    (non-positive pivot, tiny LU pivot, expired bounded wait) are recorded in a
+ *    device status word and reported by the next call that synchronises.
+ */
+#ifndef CONDIPM_H
+#define CONDIPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define OPF_OK                 0
+#define OPF_ERR_INVALID_ARG   -1   /* bad pointer, size or call order            */
+#define OPF_ERR_CUDA          -2   /* a CUDA runtime call failed                 */
+#define OPF_ERR_NOT_PD        -3   /* Cholesky met a non-positive pivot          */
+#define OPF_ERR_SINGULAR      -4   /* G_x refactorisation met a tiny pivot       */
+#define OPF_ERR_PF_FAILED     -5   /* Newton-Raphson power flow did not converge */
+#define OPF_ERR_TIMEOUT       -6   /* a bounded device wait expired              */
+#define OPF_ERR_OOM           -7   /* device allocation failed                   */
+#define OPF_ERR_NO_CONVERGENCE -8  /* interior-point loop hit its iteration cap  */
+
+/* ---- network (host arrays, copied by opf_create) ---------------------------- */
+typedef struct opf_network {
+    int nb, nl, ng, slack;                 /* slack must equal gbus[0]                */
+    const double *Pd, *Qd, *Vmin, *Vmax;   /* [nb] loads (p.u.) and voltage bounds     */
+    const int *lf, *lt;                    /* [nl] from / to bus                       */
+    const double *r, *x, *b, *rate;        /* [nl] pi-model; rate = 0 means unlimited  */
+    const int *gbus;                       /* [ng] generator bus (distinct)            */
+    const double *Pmin, *Pmax, *Qmin, *Qmax, *c2, *c1; /* [ng]                         */
+} opf_network;
+
+/* Condensation route (Sec. 3.3). ADJOINT: Kred = H_u - G_u^T G_x^{-T} H_x with
+ * H = K Z (the paper's batched adjoint-adjoint product, N = nu).  EXPLICIT:
+ * Kred = H_u + S_x^T H_x as a dense product (the route Sec. 3.3 calls naive). */
+#define OPF_ROUTE_ADJOINT  0
+#define OPF_ROUTE_EXPLICIT 1
+
+typedef struct opf_options {
+    int route;            /* OPF_ROUTE_*                                               */
+    int rhs_block;        /* right-hand-side columns per CTA in the multi-RHS solves:
+                             1, 2, 4, 8, 16 or 32; 0 picks one from nu                 */
+    long long spin_limit; /* iteration cap of every device-side wait; 0 = 1<<26        */
+} opf_options;
+
+typedef struct opf_handle opf_handle;
+
+/* Copy the network, build the variable layout, the fixed sparsity patterns of
+ * G, A, W and K, the fill-reducing ordering and symbolic LU of G_x (its pattern
+ * is fixed by the network, Sec. 3.2), the level schedules of the triangular
+ * solves, and allocate every device workspace.  opt may be NULL (defaults).
+ * Errors: INVALID_ARG (inconsistent network), CUDA, OOM. */
+int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out);
+void opf_destroy(opf_handle* h);
+const char* opf_strerror(int code);
+
+/* Sizes (host outputs, any may be NULL). */
+int opf_sizes(const opf_handle* h, int* nx, int* nu, int* m);
+/* Statistics of the symbolic analysis (host outputs, any may be NULL):
+ * nnz of L+U (strict parts plus diagonal), levels of the forward and backward
+ * solves, nnz of K. */
+int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* levels_bwd,
+              long long* nnz_k, long long* lu_flops);
+/* Stream for all device work (a cudaStream_t, NULL = legacy default stream). */
+int opf_set_stream(opf_handle* h, void* stream);
+
+/* ---- A1-A3: model evaluation (Sec. 3.2) ------------------------------------- */
+/* Evaluate f, g, h, grad f, G = [G_u G_x], A = [A_u A_x] and the Lagrangian
+ * Hessian W = hess(f + lam^T g + y^T h) at device vectors x[nx], u[nu],
+ * lam[nx], y[m]; lam and y may be NULL (then W is not evaluated).
+ * Results stay in the handle (read them with opf_get_*). */
+int opf_eval_derivatives(opf_handle* h, const double* x, const double* u,
+                         const double* lam, const double* y);
+/* Evaluate only f, g, h (line-search trial points).  Same arguments. */
+int opf_eval_functions(opf_handle* h, const double* x, const double* u);
+
+#define OPF_VEC_F     0   /* 1 double: objective                      */
+#define OPF_VEC_G     1   /* nx: state equation g                     */
+#define OPF_VEC_H     2   /* m : inequality functions h               */
+#define OPF_VEC_GRADF 3   /* nu+nx: grad f, ordered [u; x]            */
+/* Copy a vector result to device memory dst. */
+int opf_get_vector(opf_handle* h, int which, double* dst);
+
+#define OPF_MAT_G 0       /* nx x (nu+nx), columns [u; x]             */
+#define OPF_MAT_A 1       /* m  x (nu+nx)                             */
+#define OPF_MAT_W 2       /* (nu+nx) x (nu+nx), stored in K's pattern */
+#define OPF_MAT_K 3       /* K of the last opf_condense               */
+/* CSR pattern of a matrix (host outputs: rowptr[nrows+1], colind[nnz]); pass
+ * NULL arrays to query nrows/ncols/nnz first.  Columns use the [u; x] order. */
+int opf_get_csr_pattern(const opf_handle* h, int which, int* nrows, int* ncols,
+                        long long* nnz, int* rowptr, int* colind);
+/* CSR values of a matrix in that pattern (device dst[nnz]). */
+int opf_get_csr_values(opf_handle* h, int which, double* dst);
+
+/* ---- A5/A6: G_x refactorisation and solves (Sec. 3.1, 3.3) ------------------- */
+/* Numeric LU of P G_x P^T = L U in the fixed pattern at the last evaluation point
+ * (static pivots from the ordering).  Errors: SINGULAR when a pivot is below
+ * 1e-14 times its row's largest entry. */
+int opf_gx_factor(opf_handle* h);
+/* Solve G_x X = B (trans = 0) or G_x^T X = B (trans = 1) for nrhs right-hand
+ * sides stored one after another (device, nx doubles each); B and X may alias. */
+int opf_gx_solve(opf_handle* h, int trans, const double* B, double* X, int nrhs);
+
+/* ---- A4-A8: condensation (Sec. 3.3, Eq. algo:reduction) ---------------------- */
+/* Refactor G_x (unless opf_gx_factor ran since the last evaluation), assemble
+ * K = W + diag(sig_u, sig_x) + A^T diag(sig_s) A, and form Kred (nu x nu,
+ * symmetric, written to device Kred when non-NULL and kept in the handle).
+ * sig_u[nu], sig_x[nx], sig_s[m] are device vectors.  Errors: SINGULAR. */
+int opf_condense(opf_handle* h, const double* sig_u, const double* sig_x,
+                 const double* sig_s, double* Kred);
+
+/* ---- A9: control-step factorisation (Algorithm 1; Theorem 3; Sec. 4.3) ------- */
+/* Cholesky Kred + delta_w I = L L^T of the Kred of the last opf_condense (kept
+ * unmodified, so the call can be repeated with a larger delta_w).  Errors:
+ * NOT_PD with *fail_col (may be NULL) set to the first failing column. */
+int opf_kkt_factor(opf_handle* h, double delta_w, int* fail_col);
+/* Copy the Cholesky factor (lower triangle, row-major nu x nu; upper part
+ * zero) to device dst. */
+int opf_get_factor(opf_handle* h, double* dst);
+
+/* ---- A8/A10: step recovery (Theorem 1 and 2 recoveries; Algorithm 1) --------- */
+/* Solve K_aug p = -r for nrhs right-hand sides (device, n_kkt doubles each, see
+ * the block order above) with the current factors; step receives
+ * [p_u | p_x | p_s | p_lambda | p_y] per right-hand side.  rhs and step must not
+ * overlap.  K_aug carries Sigma and delta_w of the last condense/factor. */
+int opf_kkt_solve(opf_handle* h, const double* rhs, double* step, int nrhs);
+/* Solve K_aug^T z = -r (K_aug is symmetric; this path applies the transposed
+ * recovery, G_x^{-T} first), same layout.  Used by the dispatch derivative. */
+int opf_kkt_solve_adjoint(opf_handle* h, const double* rhs, double* sol, int nrhs);
+
+/* ---- A11: reduce-then-linearize helpers (Algorithm 2, Sec. 4.4) -------------- */
+/* Newton-Raphson on g(x, u) = 0 for x at fixed u (device u[nu]; device x[nx]
+ * in: start, out: solution) to ||g||_inf <= tol.  Errors: PF_FAILED. */
+int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter,
+                  int* iters);
+
+/* ---- instrumentation ---------------------------------------------------------- */
+/* Kernel launches this library has enqueued since it was loaded (all handles). */
+unsigned long long opf_launch_count(void);
+
+/* Phase timing.  While enabled, CUDA events on the handle's stream bracket every
+ * launch of each phase of opf_condense / opf_kkt_factor; opf_phase_times
+ * synchronises the stream and returns, per phase, the accumulated milliseconds
+ * (ms[OPF_PHASE_COUNT]) and the number of bracketed launches.  Enabling resets
+ * the accumulators. */
+#define OPF_PHASE_REFACTOR 0   /* G_x scatter, numeric LU, factor gathers       */
+#define OPF_PHASE_ASSEMBLE 1   /* K = W + Sigma + A^T Sigma_s A                 */
+#define OPF_PHASE_TRSM     2   /* each multi-RHS triangular solve launch         */
+#define OPF_PHASE_SPMM     3   /* H = K Z                                        */
+#define OPF_PHASE_KRED     4   /* H_u - G_u^T Psi (or S_x^T H_x), symmetrise     */
+#define OPF_PHASE_CHOL     5   /* Cholesky of Kred + delta_w I                   */
+#define OPF_PHASE_COUNT    6
+int opf_profile(opf_handle* h, int enable);
+int opf_phase_times(opf_handle* h, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONDIPM_H */

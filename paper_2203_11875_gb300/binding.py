@@ -1,0 +1,243 @@
+"""Thin ctypes binding of the C ABI in include/condipm.h.
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+libcondipm.so.  Device vectors are passed as torch CUDA tensors (float64,
+contiguous); PyTorch only supplies device memory and streams.  The binding
+raises if the library is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcondipm.so")
+
+OPF_OK = 0
+OPF_ERR_NOT_PD = -3
+OPF_ERR_SINGULAR = -4
+OPF_ERR_PF_FAILED = -5
+OPF_ERR_TIMEOUT = -6
+OPF_ROUTE_ADJOINT = 0
+OPF_ROUTE_EXPLICIT = 1
+OPF_VEC_F, OPF_VEC_G, OPF_VEC_H, OPF_VEC_GRADF = 0, 1, 2, 3
+OPF_MAT_G, OPF_MAT_A, OPF_MAT_W, OPF_MAT_K = 0, 1, 2, 3
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class opf_network(C.Structure):
+    _fields_ = [("nb", C.c_int), ("nl", C.c_int), ("ng", C.c_int), ("slack", C.c_int),
+                ("Pd", _dp), ("Qd", _dp), ("Vmin", _dp), ("Vmax", _dp),
+                ("lf", _ip), ("lt", _ip), ("r", _dp), ("x", _dp), ("b", _dp), ("rate", _dp),
+                ("gbus", _ip), ("Pmin", _dp), ("Pmax", _dp), ("Qmin", _dp), ("Qmax", _dp),
+                ("c2", _dp), ("c1", _dp)]
+
+
+class opf_options(C.Structure):
+    _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "opf_create": (C.c_int, [C.POINTER(opf_network), C.POINTER(opf_options), C.POINTER(C.c_void_p)]),
+    "opf_destroy": (None, [C.c_void_p]),
+    "opf_strerror": (C.c_char_p, [C.c_int]),
+    "opf_sizes": (C.c_int, [C.c_void_p, _ip, _ip, _ip]),
+    "opf_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), _ip, _ip, C.POINTER(C.c_longlong),
+                            C.POINTER(C.c_longlong)]),
+    "opf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_eval_functions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_get_vector": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "opf_get_csr_pattern": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, C.POINTER(C.c_longlong), C.c_void_p,
+                                      C.c_void_p]),
+    "opf_get_csr_values": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "opf_gx_factor": (C.c_int, [C.c_void_p]),
+    "opf_gx_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "opf_condense": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_kkt_factor": (C.c_int, [C.c_void_p, C.c_double, _ip]),
+    "opf_get_factor": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "opf_kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "opf_kkt_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
+    "opf_launch_count": (C.c_ulonglong, []),
+    "opf_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "opf_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+}
+
+PHASES = ("refactor", "assemble", "trsm", "spmm", "kred", "chol")
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libcondipm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2203_11875_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def launch_count() -> int:
+    """Kernel launches libcondipm.so has enqueued since it was loaded."""
+    return int(load_library().opf_launch_count())
+
+
+class OPFError(RuntimeError):
+    def __init__(self, code: int, where: str, info: int = -1):
+        self.code = code
+        self.info = info
+        msg = load_library().opf_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+def _check(code: int, where: str):
+    if code != OPF_OK:
+        raise OPFError(code, where)
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """One network on one GPU: wraps opf_create / opf_destroy and every call."""
+
+    def __init__(self, net, route: int = OPF_ROUTE_ADJOINT, rhs_block: int = 0, spin_limit: int = 0):
+        lib = load_library()
+        self._keep = []
+
+        def d(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        def i(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            self._keep.append(a)
+            return a.ctypes.data_as(_ip)
+        n = opf_network(net.nb, net.nl, net.ng, net.slack, d(net.Pd), d(net.Qd), d(net.Vmin), d(net.Vmax),
+                        i(net.lf), i(net.lt), d(net.r), d(net.x), d(net.b), d(net.rate), i(net.gbus),
+                        d(net.Pmin), d(net.Pmax), d(net.Qmin), d(net.Qmax), d(net.c2), d(net.c1))
+        o = opf_options(route, rhs_block, spin_limit)
+        h = C.c_void_p()
+        _check(lib.opf_create(C.byref(n), C.byref(o), C.byref(h)), "opf_create")
+        self._keep = []
+        self._h = h
+        self._lib = lib
+        nx, nu, m = C.c_int(), C.c_int(), C.c_int()
+        _check(lib.opf_sizes(h, C.byref(nx), C.byref(nu), C.byref(m)), "opf_sizes")
+        self.nx, self.nu, self.m = nx.value, nu.value, m.value
+        self.nw = self.nx + self.nu
+        self.n_kkt = self.nw + 2 * self.m + self.nx
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.opf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- ABI calls (same names as the C entry points, without the opf_ prefix)
+    def stats(self):
+        a, b, c, d_, e = C.c_longlong(), C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong()
+        _check(self._lib.opf_stats(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d_), C.byref(e)),
+               "opf_stats")
+        return dict(nnz_lu=a.value, levels_fwd=b.value, levels_bwd=c.value, nnz_k=d_.value,
+                    lu_flops=e.value)
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream (or None for the legacy default stream)."""
+        ptr = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _check(self._lib.opf_set_stream(self._h, ptr), "opf_set_stream")
+
+    def eval_derivatives(self, x, u, lam=None, y=None):
+        _check(self._lib.opf_eval_derivatives(self._h, _ptr(x), _ptr(u), _ptr(lam), _ptr(y)),
+               "opf_eval_derivatives")
+
+    def eval_functions(self, x, u):
+        _check(self._lib.opf_eval_functions(self._h, _ptr(x), _ptr(u)), "opf_eval_functions")
+
+    def get_vector(self, which, dst):
+        _check(self._lib.opf_get_vector(self._h, which, _ptr(dst)), "opf_get_vector")
+
+    def get_csr_pattern(self, which):
+        nr, nc, nnz = C.c_int(), C.c_int(), C.c_longlong()
+        _check(self._lib.opf_get_csr_pattern(self._h, which, C.byref(nr), C.byref(nc), C.byref(nnz), None,
+                                             None), "opf_get_csr_pattern")
+        rp = np.zeros(nr.value + 1, np.int32)
+        ci = np.zeros(max(1, nnz.value), np.int32)
+        _check(self._lib.opf_get_csr_pattern(self._h, which, None, None, None, rp.ctypes.data_as(C.c_void_p),
+                                             ci.ctypes.data_as(C.c_void_p)), "opf_get_csr_pattern")
+        return nr.value, nc.value, rp, ci[:nnz.value]
+
+    def get_csr_values(self, which, dst):
+        _check(self._lib.opf_get_csr_values(self._h, which, _ptr(dst)), "opf_get_csr_values")
+
+    def gx_factor(self):
+        _check(self._lib.opf_gx_factor(self._h), "opf_gx_factor")
+
+    def gx_solve(self, trans, B, X, nrhs=1):
+        _check(self._lib.opf_gx_solve(self._h, int(trans), _ptr(B), _ptr(X), int(nrhs)), "opf_gx_solve")
+
+    def condense(self, sig_u, sig_x, sig_s, Kred=None):
+        _check(self._lib.opf_condense(self._h, _ptr(sig_u), _ptr(sig_x), _ptr(sig_s), _ptr(Kred)),
+               "opf_condense")
+
+    def kkt_factor(self, delta_w=0.0):
+        """Returns -1 on success, else the failing column (status NOT_PD)."""
+        col = C.c_int(-1)
+        rc = self._lib.opf_kkt_factor(self._h, float(delta_w), C.byref(col))
+        if rc == OPF_ERR_NOT_PD:
+            return col.value
+        _check(rc, "opf_kkt_factor")
+        return -1
+
+    def get_factor(self, dst):
+        _check(self._lib.opf_get_factor(self._h, _ptr(dst)), "opf_get_factor")
+
+    def kkt_solve(self, rhs, step, nrhs=1):
+        _check(self._lib.opf_kkt_solve(self._h, _ptr(rhs), _ptr(step), int(nrhs)), "opf_kkt_solve")
+
+    def kkt_solve_adjoint(self, rhs, sol, nrhs=1):
+        _check(self._lib.opf_kkt_solve_adjoint(self._h, _ptr(rhs), _ptr(sol), int(nrhs)),
+               "opf_kkt_solve_adjoint")
+
+    def profile(self, enable=True):
+        _check(self._lib.opf_profile(self._h, int(bool(enable))), "opf_profile")
+
+    def phase_times(self):
+        ms = (C.c_double * len(PHASES))()
+        n = (C.c_longlong * len(PHASES))()
+        _check(self._lib.opf_phase_times(self._h, ms, n), "opf_phase_times")
+        return {p: (ms[i], n[i]) for i, p in enumerate(PHASES)}
+
+    def powerflow(self, u, x, tol=1e-10, max_iter=30):
+        it = C.c_int(0)
+        _check(self._lib.opf_powerflow(self._h, _ptr(u), _ptr(x), float(tol), int(max_iter), C.byref(it)),
+               "opf_powerflow")
+        return it.value

@@ -1,0 +1,733 @@
+// C ABI of the condensed interior-point hot path (include/condipm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/condipm.h"
+#include "common.cuh"
+#include "opf_handle.h"
+#include "plan.h"
+
+using namespace condipm;
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return OPF_ERR_CUDA;    \
+  } while (0)
+
+namespace condipm {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace condipm
+
+namespace {
+
+cudaEvent_t take_event(opf_handle* h) {
+  if (!h->evpool.empty()) {
+    cudaEvent_t e = h->evpool.back();
+    h->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// bracket the launches between ph_begin and ph_end with events (when profiling)
+void ph_begin(opf_handle* h, int phase) {
+  if (!h->profiling) return;
+  h->open_phase = phase;
+  h->open_ev = take_event(h);
+  cudaEventRecord(h->open_ev, h->s);
+}
+
+void ph_end(opf_handle* h) {
+  if (!h->profiling || h->open_phase < 0) return;
+  cudaEvent_t b = take_event(h);
+  cudaEventRecord(b, h->s);
+  h->recs.push_back({h->open_phase, h->open_ev, b});
+  h->open_phase = -1;
+}
+
+template <class T>
+int upload(opf_handle* h, T** dst, const std::vector<T>& v) {
+  size_t n = std::max<size_t>(v.size(), 1);
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? OPF_ERR_OOM : OPF_ERR_CUDA;
+  h->allocs.push_back(*dst);
+  if (!v.empty()) {
+    e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return OPF_ERR_CUDA;
+  }
+  return OPF_OK;
+}
+
+template <class T>
+int alloc(opf_handle* h, T** dst, size_t n) {
+  n = std::max<size_t>(n, 1);
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? OPF_ERR_OOM : OPF_ERR_CUDA;
+  h->allocs.push_back(*dst);
+  e = cudaMemset(*dst, 0, n * sizeof(T));
+  return e == cudaSuccess ? OPF_OK : OPF_ERR_CUDA;
+}
+
+#define TRY(x)              \
+  do {                      \
+    int r_ = (x);           \
+    if (r_ != OPF_OK) return r_; \
+  } while (0)
+
+int pick_cb(int ncols) {
+  const int cands[4] = {8, 4, 2, 1};
+  for (int c : cands)
+    if ((ncols + c - 1) / c >= 300) return c;
+  return 1;
+}
+
+int upload_all(opf_handle* h) {
+  const Plan& P = h->P;
+  TRY(upload(h, &h->end_i, P.end_i));
+  TRY(upload(h, &h->end_k, P.end_k));
+  TRY(upload(h, &h->end_h, P.end_h));
+  TRY(upload(h, &h->gs, P.gs));
+  TRY(upload(h, &h->bs, P.bs));
+  TRY(upload(h, &h->gm, P.gm));
+  TRY(upload(h, &h->bm, P.bm));
+  TRY(upload(h, &h->bus_end_ptr, P.bus_end_ptr));
+  TRY(upload(h, &h->bus_end, P.bus_end));
+  TRY(upload(h, &h->g_row_P, P.g_row_P));
+  TRY(upload(h, &h->g_row_Q, P.g_row_Q));
+  TRY(upload(h, &h->gen_of_bus, P.gen_of_bus));
+  TRY(upload(h, &h->th_w, P.th_w));
+  TRY(upload(h, &h->vm_w, P.vm_w));
+  TRY(upload(h, &h->Pd, P.Pd));
+  TRY(upload(h, &h->Qd, P.Qd));
+  TRY(upload(h, &h->c2, P.c2));
+  TRY(upload(h, &h->c1, P.c1));
+  std::vector<int> pg_of_w(P.nw, -1), slackpos(P.nw, -1);
+  for (int k = 1; k < P.ng; ++k) pg_of_w[P.pg_w[k]] = k;
+  for (int q = P.A.rp[0]; q < P.A.rp[1]; ++q) slackpos[P.A.ci[q]] = q;
+  TRY(upload(h, &h->pg_of_w, pg_of_w));
+  TRY(upload(h, &h->slackpos, slackpos));
+  // evaluation buffers
+  TRY(alloc(h, &h->Vm, P.nb));
+  TRY(alloc(h, &h->Va, P.nb));
+  TRY(alloc(h, &h->pq, 2 * (size_t)P.ne));
+  TRY(alloc(h, &h->dsrc, 12 * (size_t)P.ne));
+  TRY(alloc(h, &h->hpq, 20 * (size_t)P.ne));
+  TRY(alloc(h, &h->hw, 10 * (size_t)P.ne));
+  TRY(alloc(h, &h->wP, P.nb));
+  TRY(alloc(h, &h->wQ, P.nb));
+  TRY(alloc(h, &h->g, P.nx));
+  TRY(alloc(h, &h->hv, P.m));
+  TRY(alloc(h, &h->f, 1));
+  TRY(alloc(h, &h->gradf, P.nw));
+  TRY(alloc(h, &h->Pg, P.ng));
+  // G, A
+  TRY(upload(h, &h->Ggat_ptr, P.Ggat.ptr));
+  TRY(upload(h, &h->Ggat_idx, P.Ggat.idx));
+  TRY(upload(h, &h->Ggat_cst, P.Ggat.cst));
+  TRY(alloc(h, &h->Gval, P.G.nnz()));
+  TRY(upload(h, &h->Agat_ptr, P.Agat.ptr));
+  TRY(upload(h, &h->Agat_idx, P.Agat.idx));
+  TRY(upload(h, &h->Agat_cst, P.Agat.cst));
+  TRY(alloc(h, &h->Aval, P.A.nnz()));
+  TRY(upload(h, &h->A_rp, P.A.rp));
+  TRY(upload(h, &h->A_ci_c, P.A_ci_c));
+  // K / W
+  TRY(upload(h, &h->K_rp, P.K.rp));
+  TRY(upload(h, &h->K_ci, P.K.ci));
+  TRY(upload(h, &h->Wgat_ptr, P.Wgat.ptr));
+  TRY(upload(h, &h->Wgat_idx, P.Wgat.idx));
+  TRY(upload(h, &h->Wgat_cst, P.Wgat.cst));
+  TRY(upload(h, &h->Wsl_pos, P.Wslack_pos));
+  TRY(upload(h, &h->Wsl_a, P.Wslack_a));
+  TRY(upload(h, &h->Wsl_b, P.Wslack_b));
+  TRY(upload(h, &h->K_diag, P.K_diag));
+  TRY(upload(h, &h->KAA_ptr, P.KAA.ptr));
+  TRY(upload(h, &h->KAA_r, P.KAA.r));
+  TRY(upload(h, &h->KAA_a, P.KAA.a));
+  TRY(upload(h, &h->KAA_b, P.KAA.b));
+  TRY(upload(h, &h->Knat_map, P.Knat_map));
+  TRY(upload(h, &h->perm, P.perm));
+  TRY(upload(h, &h->c2w, P.c2w));
+  TRY(alloc(h, &h->Wval, P.K.nnz()));
+  TRY(alloc(h, &h->Kval, P.K.nnz()));
+  TRY(alloc(h, &h->sig_c, P.nw));
+  TRY(alloc(h, &h->sig_s, P.m));
+  // transposes
+  TRY(upload(h, &h->AT_rp, P.AT.rp));
+  TRY(upload(h, &h->AT_ci, P.AT.ci));
+  TRY(upload(h, &h->AT_map, P.AT_map));
+  TRY(upload(h, &h->PGu_rp, P.PGu.rp));
+  TRY(upload(h, &h->PGu_ci, P.PGu.ci));
+  TRY(upload(h, &h->PGu_map, P.PGu_map));
+  TRY(upload(h, &h->GuT_rp, P.GuT.rp));
+  TRY(upload(h, &h->GuT_ci, P.GuT.ci));
+  TRY(upload(h, &h->GuT_map, P.GuT_map));
+  // LU
+  TRY(upload(h, &h->LU_rp, P.LU.rp));
+  TRY(upload(h, &h->LU_ci, P.LU.ci));
+  TRY(upload(h, &h->LU_diag, P.LU_diag));
+  TRY(upload(h, &h->Gx_to_LU, P.Gx_to_LU));
+  TRY(upload(h, &h->upd_ptr, P.upd_ptr));
+  TRY(upload(h, &h->upd_pos, P.upd_pos));
+  TRY(alloc(h, &h->LUval, P.LU.nnz()));
+  TRY(alloc(h, &h->inv_diag, P.nx));
+  TRY(alloc(h, &h->rmax, P.nx));
+  TRY(alloc(h, &h->flags, P.nx));
+  TRY(upload(h, &h->Lo_rp, P.Lo.rp));
+  TRY(upload(h, &h->Lo_ci, P.Lo.ci));
+  TRY(upload(h, &h->Lo_map, P.Lo_map));
+  TRY(upload(h, &h->Ut_map, P.Ut_map));
+  TRY(upload(h, &h->Up_rp, P.Up.rp));
+  TRY(upload(h, &h->Up_ci, P.Up.ci));
+  TRY(upload(h, &h->Up_map, P.Up_map));
+  TRY(upload(h, &h->Lt_map, P.Lt_map));
+  TRY(alloc(h, &h->Lo_val, P.Lo.nnz()));
+  TRY(alloc(h, &h->Ut_val, P.Lo.nnz()));
+  TRY(alloc(h, &h->Up_val, P.Up.nnz()));
+  TRY(alloc(h, &h->Lt_val, P.Up.nnz()));
+  TRY(upload(h, &h->fwd_ptr, P.fwd.ptr));
+  TRY(upload(h, &h->fwd_rows, P.fwd.rows));
+  TRY(upload(h, &h->bwd_ptr, P.bwd.ptr));
+  TRY(upload(h, &h->bwd_rows, P.bwd.rows));
+  // dense
+  TRY(alloc(h, &h->Zt, (size_t)P.nw * P.nu));
+  TRY(alloc(h, &h->H, (size_t)P.nw * P.nu));
+  TRY(alloc(h, &h->Kred, (size_t)P.nu * P.nu));
+  TRY(alloc(h, &h->F, (size_t)P.nu * P.nu));
+  TRY(alloc(h, &h->st, ST_WORDS));
+  TRY(alloc(h, &h->bar, 4));
+  CK(launch_set_identity(0, P.nu, h->Zt, P.nu));
+  // launch shapes
+  int maxlen = 1;
+  for (int i = 0; i < P.nx; ++i) maxlen = std::max(maxlen, P.LU.rp[i + 1] - P.LU.rp[i]);
+  h->lu_maxlen = maxlen;
+  h->lu_threads = 256;
+  int mb = lu_refactor_max_blocks(h->lu_threads, (size_t)(h->lu_threads / 32) * maxlen * sizeof(double));
+  int need = (P.nx + 7) / 8;
+  h->lu_blocks = std::max(1, std::min(mb, need));
+  h->chol_blocks = std::max(1, std::min(chol_max_blocks(), 2 * 152));
+  CK(cudaDeviceSynchronize());
+  return OPF_OK;
+}
+
+// device status -> OPF code (synchronises the stream); clears the word
+int read_status(opf_handle* h, int* info = nullptr) {
+  int st[ST_WORDS];
+  CK(cudaMemcpyAsync(st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (st[ST_CODE] == 0 && st[ST_TIMEOUT] == 0) return OPF_OK;
+  CK(cudaMemsetAsync(h->st, 0, sizeof(int) * ST_WORDS, h->s));
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
+  if (info) *info = st[ST_INFO];
+  if (st[ST_TIMEOUT]) return OPF_ERR_TIMEOUT;
+  if (st[ST_CODE] == DEV_NOT_PD) return OPF_ERR_NOT_PD;
+  if (st[ST_CODE] == DEV_SINGULAR) return OPF_ERR_SINGULAR;
+  return OPF_ERR_CUDA;
+}
+
+double* workspace(opf_handle* h, size_t n) {
+  if (n > h->ws_cap) {
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_cap = 0;
+    if (cudaMalloc(&h->ws, n * sizeof(double)) != cudaSuccess) return nullptr;
+    h->ws_cap = n;
+  }
+  return h->ws;
+}
+
+}  // namespace
+
+// ============================================================================ internals
+namespace condipm {
+
+int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam, const double* y,
+              bool derivs) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  CK(launch_bus_state(s, P.nb, P.nu, x, u, h->th_w, h->vm_w, h->Vm, h->Va));
+  CK(launch_end_eval(s, P.ne, h->end_i, h->end_k, h->end_h, h->gs, h->bs, h->gm, h->bm, h->Vm, h->Va,
+                     h->pq, h->dsrc, h->hpq, h->hv, derivs ? 1 : 0));
+  CK(launch_bus_sum(s, P.nb, P.ng, P.nu, P.slack, h->bus_end_ptr, h->bus_end, h->pq, h->g_row_P,
+                    h->g_row_Q, h->gen_of_bus, h->Pd, h->Qd, u, h->c2, h->c1, derivs ? lam : nullptr, y,
+                    h->g, h->hv, h->Pg, h->wP, h->wQ));
+  CK(launch_objective(s, P.ng, h->Pg, h->c2, h->c1, h->f));
+  if (!derivs) return OPF_OK;
+  CK(launch_gather(s, int(P.G.nnz()), h->Ggat_ptr, h->Ggat_idx, h->Ggat_cst, h->dsrc, h->Gval));
+  CK(launch_gather(s, int(P.A.nnz()), h->Agat_ptr, h->Agat_idx, h->Agat_cst, h->dsrc, h->Aval));
+  CK(launch_gradf(s, P.nw, P.ng, h->pg_of_w, h->slackpos, h->Pg, h->c2, h->c1, h->Aval, h->gradf));
+  if (lam && y) {
+    CK(launch_end_hess(s, P.ne, h->end_i, h->end_h, h->pq, h->dsrc, h->hpq, h->wP, h->wQ, y, h->hw));
+    CK(launch_gather(s, int(P.K.nnz()), h->Wgat_ptr, h->Wgat_idx, h->Wgat_cst, h->hw, h->Wval));
+    CK(launch_bilin_fixed(s, int(P.Wslack_pos.size()), h->Wsl_pos, h->Wsl_a, h->Wsl_b, 2.0 * P.c2[0],
+                          h->Aval, h->Wval));
+  }
+  h->have_eval = true;
+  h->have_W = lam && y;
+  h->have_lu = false;
+  h->have_condense = false;
+  h->have_factor = false;
+  return OPF_OK;
+}
+
+// numeric refactorisation, asynchronous (status read by the caller)
+int factor_async(opf_handle* h) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  ph_begin(h, OPF_PHASE_REFACTOR);
+  CK(cudaMemsetAsync(h->LUval, 0, sizeof(double) * std::max<long long>(1, P.LU.nnz()), s));
+  CK(launch_lu_scatter(s, P.G.nnz(), h->Gx_to_LU, h->Gval, h->LUval));
+  CK(launch_row_absmax(s, P.nx, h->LU_rp, h->LUval, h->rmax));
+  h->epoch += 1;
+  CK(launch_lu_refactor(s, P.nx, h->fwd_rows, h->LU_rp, h->LU_ci, h->LU_diag, h->upd_ptr, h->upd_pos,
+                        h->LUval, h->inv_diag, h->rmax, h->flags, h->epoch, h->st, h->spin_limit,
+                        h->lu_blocks, h->lu_threads, h->lu_maxlen));
+  CK(launch_gather_map(s, P.Lo.nnz(), h->Lo_map, h->LUval, h->Lo_val));
+  CK(launch_gather_map(s, P.Lo.nnz(), h->Ut_map, h->LUval, h->Ut_val));
+  CK(launch_gather_map(s, P.Up.nnz(), h->Up_map, h->LUval, h->Up_val));
+  CK(launch_gather_map(s, P.Up.nnz(), h->Lt_map, h->LUval, h->Lt_val));
+  ph_end(h);
+  h->have_lu = true;
+  return OPF_OK;
+}
+
+// X (perm space, row-major n x ncols) <- (LU)^{-1} X   or (LU)^{-T} X
+int lu_solve_perm(opf_handle* h, int trans, double* X, int ncols, int cb, bool timed = false) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const double* lov = trans ? h->Ut_val : h->Lo_val;
+  const double* upv = trans ? h->Lt_val : h->Up_val;
+  if (timed) ph_begin(h, OPF_PHASE_TRSM);
+  CK(launch_trsm(s, cb, P.fwd.nlev, h->fwd_ptr, h->fwd_rows, h->Lo_rp, h->Lo_ci, lov,
+                 trans ? h->inv_diag : nullptr, X, ncols, ncols));
+  if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
+  CK(launch_trsm(s, cb, P.bwd.nlev, h->bwd_ptr, h->bwd_rows, h->Up_rp, h->Up_ci, upv,
+                 trans ? nullptr : h->inv_diag, X, ncols, ncols));
+  if (timed) ph_end(h);
+  return OPF_OK;
+}
+
+int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nx = P.nx, nw = P.nw;
+  if (!h->have_lu) TRY(factor_async(h));
+  CK(cudaMemcpyAsync(h->sig_s, sig_s, sizeof(double) * std::max(1, P.m), cudaMemcpyDeviceToDevice, s));
+  // A4: K = W + A^T Sigma_s A + diag(Sigma)
+  ph_begin(h, OPF_PHASE_ASSEMBLE);
+  CK(launch_assemble_K(s, P.K.nnz(), h->Wval, h->KAA_ptr, h->KAA_r, h->KAA_a, h->KAA_b, h->sig_s, h->Aval,
+                       h->Kval));
+  CK(launch_add_diag(s, nw, nu, h->K_diag, h->perm, sig_u, sig_x, h->Kval, h->sig_c));
+  ph_end(h);
+  // A6: Z = [I; S_x],  S_x = -(P G_x P^T)^{-1} P G_u   (perm rows)
+  double* Sx = h->Zt + (size_t)nu * nu;
+  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * nu, s));
+  CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, nu));
+  TRY(lu_solve_perm(h, 0, Sx, nu, h->cb, true));
+  // A7: H = K Z
+  ph_begin(h, OPF_PHASE_SPMM);
+  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, nu, h->H, nu, nu, 1.0, 0.0));
+  ph_end(h);
+  double* Hx = h->H + (size_t)nu * nu;
+  if (h->opt.route == OPF_ROUTE_EXPLICIT) {
+    ph_begin(h, OPF_PHASE_KRED);
+    CK(launch_dense_tn(s, nu, nx, Sx, Hx, h->H, h->F));
+    CK(launch_symmetrize(s, nu, h->F, h->Kred));
+    ph_end(h);
+  } else {
+    // Psi = G_x^{-T} H_x ; Kred = H_u - G_u^T Psi
+    TRY(lu_solve_perm(h, 1, Hx, nu, h->cb, true));
+    ph_begin(h, OPF_PHASE_KRED);
+    CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Hx, nu, h->H, nu, nu, -1.0, 1.0));
+    CK(launch_symmetrize(s, nu, h->H, h->Kred));
+    ph_end(h);
+  }
+  h->have_condense = true;
+  h->have_factor = false;
+  return OPF_OK;
+}
+
+int factor_kred_async(opf_handle* h, double delta_w) {
+  const Plan& P = h->P;
+  ph_begin(h, OPF_PHASE_CHOL);
+  CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
+  CK(launch_chol(h->s, P.nu, h->F, h->st, h->bar, h->spin_limit, h->chol_blocks));
+  ph_end(h);
+  h->delta_w = delta_w;
+  return OPF_OK;
+}
+
+// K_aug p = -r for k right-hand sides (col-major n_kkt x k in, col-major out)
+int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
+  const int N = nw + 2 * m + nx;
+  double* ws = workspace(h, (size_t)k * (6 * (size_t)nw + 8 * (size_t)m + 3 * (size_t)nx + 8));
+  if (!ws) return OPF_ERR_OOM;
+  double* R12 = ws;                      // nw x k (c-order)
+  double* R3 = R12 + (size_t)nw * k;     // m x k
+  double* R5 = R3 + (size_t)m * k;       // m x k
+  double* R4 = R5 + (size_t)m * k;       // nx x k (perm)
+  double* T = R4 + (size_t)nx * k;       // m x k
+  double* C = T + (size_t)m * k;         // nw x k
+  double* D0 = C + (size_t)nw * k;       // nw x k
+  double* Bv = D0 + (size_t)nw * k;      // nw x k
+  double* Pc = Bv + (size_t)nw * k;      // nw x k
+  double* Tm = Pc + (size_t)nw * k;      // m x k
+  double* Vb = Tm + (size_t)m * k;       // nw x k (rows nu.. used)
+  double* Ps = Vb + (size_t)nw * k;      // m x k
+  double* Py = Ps + (size_t)m * k;       // m x k
+  const int cbk = pick_cb(k);
+  // gather the right-hand side blocks
+  CK(launch_permute_rows(s, nw, k, h->c2w, rhs, N, 1, R12, k, 0, 1.0, 0));
+  CK(launch_permute_rows(s, m, k, nullptr, rhs + nw, N, 1, R3, k, 0, 1.0, 0));
+  CK(launch_permute_rows(s, nx, k, h->perm, rhs + nw + m, N, 1, R4, k, 0, 1.0, 0));
+  CK(launch_permute_rows(s, m, k, nullptr, rhs + nw + m + nx, N, 1, R5, k, 0, 1.0, 0));
+  // T = Sigma_s r5 - r3 ; C = A^T T
+  CK(launch_scale_rows(s, m, k, h->sig_s, R5, T, -1.0, R3));
+  CK(launch_spmm(s, nw, h->AT_rp, h->AT_ci, h->Aval, h->AT_map, T, k, C, k, k, 1.0, 0.0));
+  // D0 = [0; q],  q = -G_x^{-1} r4
+  CK(cudaMemsetAsync(D0, 0, sizeof(double) * (size_t)nu * k, s));
+  CK(launch_axpby(s, (long long)nx * k, -1.0, R4, 0.0, nullptr, D0 + (size_t)nu * k));
+  TRY(lu_solve_perm(h, 0, D0 + (size_t)nu * k, k, cbk));
+  // b = [r1; r2] + K D0 + C
+  CK(launch_axpby(s, (long long)nw * k, 1.0, R12, 1.0, C, Bv));
+  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, D0, k, Bv, k, k, 1.0, 1.0));
+  // rhs_u = -(b_u - G_u^T G_x^{-T} b_x)
+  TRY(lu_solve_perm(h, 1, Bv + (size_t)nu * k, k, cbk));
+  CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Bv + (size_t)nu * k, k, Bv, k, k, -1.0,
+                 1.0));
+  CK(launch_axpby(s, (long long)nu * k, -1.0, Bv, 0.0, nullptr, Pc));
+  // p_u = (L L^T)^{-1} rhs_u
+  CK(launch_chol_solve(s, nu, h->F, Pc, k));
+  // p_x = -G_x^{-1} (r4 + G_u p_u)
+  double* Px = Pc + (size_t)nu * k;
+  CK(cudaMemcpyAsync(Px, R4, sizeof(double) * (size_t)nx * k, cudaMemcpyDeviceToDevice, s));
+  CK(launch_spmm(s, nx, h->PGu_rp, h->PGu_ci, h->Gval, h->PGu_map, Pc, k, Px, k, k, 1.0, 1.0));
+  TRY(lu_solve_perm(h, 0, Px, k, cbk));
+  CK(launch_axpby(s, (long long)nx * k, -1.0, Px, 0.0, nullptr, Px));
+  // t = A p + r5 ; p_s = -t ; p_y = Sigma_s t - r3
+  CK(cudaMemcpyAsync(Tm, R5, sizeof(double) * (size_t)m * k, cudaMemcpyDeviceToDevice, s));
+  CK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, Pc, k, Tm, k, k, 1.0, 1.0));
+  CK(launch_axpby(s, (long long)m * k, -1.0, Tm, 0.0, nullptr, Ps));
+  CK(launch_scale_rows(s, m, k, h->sig_s, Tm, Py, -1.0, R3));
+  // p_lambda = -G_x^{-T} (r2 + [K p]_x + C_x)
+  double* Vx = Vb + (size_t)nu * k;
+  CK(launch_axpby(s, (long long)nx * k, 1.0, R12 + (size_t)nu * k, 1.0, C + (size_t)nu * k, Vx));
+  CK(launch_spmm(s, nx, h->K_rp + nu, h->K_ci, h->Kval, nullptr, Pc, k, Vx, k, k, 1.0, 1.0));
+  TRY(lu_solve_perm(h, 1, Vx, k, cbk));
+  // scatter the step back: [p_u | p_x] (c-order), p_s, p_lambda (perm), p_y
+  CK(launch_permute_rows(s, nw, k, h->c2w, Pc, k, 0, step, N, 1, 1.0, 1));
+  CK(launch_permute_rows(s, m, k, nullptr, Ps, k, 0, step + nw, N, 1, 1.0, 0));
+  CK(launch_permute_rows(s, nx, k, h->perm, Vx, k, 0, step + nw + m, N, 1, -1.0, 1));
+  CK(launch_permute_rows(s, m, k, nullptr, Py, k, 0, step + nw + m + nx, N, 1, 1.0, 0));
+  return OPF_OK;
+}
+
+}  // namespace condipm
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* opf_strerror(int code) {
+  switch (code) {
+    case OPF_OK: return "ok";
+    case OPF_ERR_INVALID_ARG: return "invalid argument or call order";
+    case OPF_ERR_CUDA: return "CUDA runtime error";
+    case OPF_ERR_NOT_PD: return "condensed matrix not positive definite";
+    case OPF_ERR_SINGULAR: return "G_x refactorisation met a tiny pivot";
+    case OPF_ERR_PF_FAILED: return "power flow did not converge";
+    case OPF_ERR_TIMEOUT: return "a bounded device wait expired";
+    case OPF_ERR_OOM: return "device allocation failed";
+    case OPF_ERR_NO_CONVERGENCE: return "interior-point iteration cap reached";
+    default: return "unknown status";
+  }
+}
+
+int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out) {
+  if (!net || !out) return OPF_ERR_INVALID_ARG;
+  *out = nullptr;
+  opf_handle* h = new (std::nothrow) opf_handle();
+  if (!h) return OPF_ERR_OOM;
+  if (opt) h->opt = *opt;
+  if (h->opt.route != OPF_ROUTE_ADJOINT && h->opt.route != OPF_ROUTE_EXPLICIT) {
+    delete h;
+    return OPF_ERR_INVALID_ARG;
+  }
+  h->spin_limit = h->opt.spin_limit > 0 ? h->opt.spin_limit : (1LL << 26);
+  std::string err = build_plan(h->P, net->nb, net->nl, net->ng, net->slack, net->Pd, net->Qd, net->Vmin,
+                               net->Vmax, net->lf, net->lt, net->r, net->x, net->b, net->rate, net->gbus,
+                               net->Pmin, net->Pmax, net->Qmin, net->Qmax, net->c2, net->c1);
+  if (!err.empty()) {
+    delete h;
+    return OPF_ERR_INVALID_ARG;
+  }
+  int cb = h->opt.rhs_block;
+  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 8 && cb != 16 && cb != 32) {
+    delete h;
+    return OPF_ERR_INVALID_ARG;
+  }
+  h->cb = cb ? cb : pick_cb(h->P.nu);
+  int rc = upload_all(h);
+  if (rc != OPF_OK) {
+    opf_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return OPF_OK;
+}
+
+void opf_destroy(opf_handle* h) {
+  if (!h) return;
+  for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : h->evpool) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+int opf_sizes(const opf_handle* h, int* nx, int* nu, int* m) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (nx) *nx = h->P.nx;
+  if (nu) *nu = h->P.nu;
+  if (m) *m = h->P.m;
+  return OPF_OK;
+}
+
+int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* levels_bwd, long long* nnz_k,
+              long long* lu_flops) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (nnz_lu) *nnz_lu = h->P.LU.nnz();
+  if (levels_fwd) *levels_fwd = h->P.fwd.nlev;
+  if (levels_bwd) *levels_bwd = h->P.bwd.nlev;
+  if (nnz_k) *nnz_k = h->P.K.nnz();
+  if (lu_flops) *lu_flops = h->P.lu_flops;
+  return OPF_OK;
+}
+
+int opf_set_stream(opf_handle* h, void* stream) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  h->s = (cudaStream_t)stream;
+  return OPF_OK;
+}
+
+int opf_eval_derivatives(opf_handle* h, const double* x, const double* u, const double* lam, const double* y) {
+  if (!h || !x || !u || ((lam == nullptr) != (y == nullptr))) return OPF_ERR_INVALID_ARG;
+  TRY(eval_impl(h, x, u, lam, y, true));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_eval_functions(opf_handle* h, const double* x, const double* u) {
+  if (!h || !x || !u) return OPF_ERR_INVALID_ARG;
+  TRY(eval_impl(h, x, u, nullptr, nullptr, false));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_get_vector(opf_handle* h, int which, double* dst) {
+  if (!h || !dst) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  const double* src = nullptr;
+  size_t n = 0;
+  switch (which) {
+    case OPF_VEC_F: src = h->f; n = 1; break;
+    case OPF_VEC_G: src = h->g; n = P.nx; break;
+    case OPF_VEC_H: src = h->hv; n = P.m; break;
+    case OPF_VEC_GRADF: src = h->gradf; n = P.nw; break;
+    default: return OPF_ERR_INVALID_ARG;
+  }
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_get_csr_pattern(const opf_handle* h, int which, int* nrows, int* ncols, long long* nnz, int* rowptr,
+                        int* colind) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  const std::vector<int>* rp = nullptr;
+  const std::vector<int>* ci = nullptr;
+  int nr = 0;
+  switch (which) {
+    case OPF_MAT_G: rp = &P.G.rp; ci = &P.G.ci; nr = P.nx; break;
+    case OPF_MAT_A: rp = &P.A.rp; ci = &P.A.ci; nr = P.m; break;
+    case OPF_MAT_W:
+    case OPF_MAT_K: rp = &P.Knat_rp; ci = &P.Knat_ci; nr = P.nw; break;
+    default: return OPF_ERR_INVALID_ARG;
+  }
+  if (nrows) *nrows = nr;
+  if (ncols) *ncols = P.nw;
+  if (nnz) *nnz = rp->back();
+  if (rowptr) std::memcpy(rowptr, rp->data(), rp->size() * sizeof(int));
+  if (colind) std::memcpy(colind, ci->data(), ci->size() * sizeof(int));
+  return OPF_OK;
+}
+
+int opf_get_csr_values(opf_handle* h, int which, double* dst) {
+  if (!h || !dst) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  switch (which) {
+    case OPF_MAT_G:
+      if (!h->have_eval) return OPF_ERR_INVALID_ARG;
+      CK(cudaMemcpyAsync(dst, h->Gval, P.G.nnz() * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      break;
+    case OPF_MAT_A:
+      if (!h->have_eval) return OPF_ERR_INVALID_ARG;
+      CK(cudaMemcpyAsync(dst, h->Aval, P.A.nnz() * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      break;
+    case OPF_MAT_W:
+      if (!h->have_W) return OPF_ERR_INVALID_ARG;
+      CK(launch_gather_map(h->s, P.K.nnz(), h->Knat_map, h->Wval, dst));
+      break;
+    case OPF_MAT_K:
+      if (!h->have_condense) return OPF_ERR_INVALID_ARG;
+      CK(launch_gather_map(h->s, P.K.nnz(), h->Knat_map, h->Kval, dst));
+      break;
+    default: return OPF_ERR_INVALID_ARG;
+  }
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_gx_factor(opf_handle* h) {
+  if (!h || !h->have_eval) return OPF_ERR_INVALID_ARG;
+  TRY(factor_async(h));
+  int rc = read_status(h);
+  if (rc != OPF_OK) h->have_lu = false;
+  return rc;
+}
+
+int opf_gx_solve(opf_handle* h, int trans, const double* B, double* X, int nrhs) {
+  if (!h || !B || !X || nrhs < 1 || !h->have_lu) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  double* ws = workspace(h, (size_t)P.nx * nrhs);
+  if (!ws) return OPF_ERR_OOM;
+  CK(launch_permute_rows(h->s, P.nx, nrhs, h->perm, B, P.nx, 1, ws, nrhs, 0, 1.0, 0));
+  TRY(lu_solve_perm(h, trans ? 1 : 0, ws, nrhs, pick_cb(nrhs)));
+  CK(launch_permute_rows(h->s, P.nx, nrhs, h->perm, ws, nrhs, 0, X, P.nx, 1, 1.0, 1));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_condense(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s, double* Kred) {
+  if (!h || !sig_u || !sig_x || !sig_s || !h->have_W) return OPF_ERR_INVALID_ARG;
+  TRY(condense_async(h, sig_u, sig_x, sig_s));
+  if (Kred)
+    CK(cudaMemcpyAsync(Kred, h->Kred, sizeof(double) * (size_t)h->P.nu * h->P.nu, cudaMemcpyDeviceToDevice,
+                       h->s));
+  int rc = read_status(h);
+  if (rc != OPF_OK) {
+    h->have_condense = false;
+    h->have_lu = false;
+  }
+  return rc;
+}
+
+int opf_kkt_factor(opf_handle* h, double delta_w, int* fail_col) {
+  if (!h || !h->have_condense || !(delta_w >= 0.0)) return OPF_ERR_INVALID_ARG;
+  TRY(factor_kred_async(h, delta_w));
+  int info = -1;
+  int rc = read_status(h, &info);
+  if (fail_col) *fail_col = rc == OPF_ERR_NOT_PD ? info : -1;
+  h->have_factor = rc == OPF_OK;
+  return rc;
+}
+
+int opf_get_factor(opf_handle* h, double* dst) {
+  if (!h || !dst || !h->have_factor) return OPF_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(dst, h->F, sizeof(double) * (size_t)h->P.nu * h->P.nu, cudaMemcpyDeviceToDevice, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_kkt_solve(opf_handle* h, const double* rhs, double* step, int nrhs) {
+  if (!h || !rhs || !step || nrhs < 1 || !h->have_factor) return OPF_ERR_INVALID_ARG;
+  TRY(kkt_solve_impl(h, rhs, step, nrhs));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+int opf_kkt_solve_adjoint(opf_handle* h, const double* rhs, double* sol, int nrhs) {
+  // K_aug is symmetric (Eq. kktmatrix:normal), so the transposed system is solved
+  // by the same reduction and recovery.
+  return opf_kkt_solve(h, rhs, sol, nrhs);
+}
+
+unsigned long long opf_launch_count(void) { return launch_count(); }
+
+int opf_profile(opf_handle* h, int enable) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->s));
+  for (auto& r : h->recs) { h->evpool.push_back(r.a); h->evpool.push_back(r.b); }
+  h->recs.clear();
+  for (int p = 0; p < OPF_PHASE_COUNT; ++p) { h->ph_ms[p] = 0.0; h->ph_n[p] = 0; }
+  h->profiling = enable != 0;
+  return OPF_OK;
+}
+
+int opf_phase_times(opf_handle* h, double* ms, long long* launches) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->s));
+  for (auto& r : h->recs) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    h->ph_ms[r.phase] += t;
+    h->ph_n[r.phase] += 1;
+    h->evpool.push_back(r.a);
+    h->evpool.push_back(r.b);
+  }
+  h->recs.clear();
+  for (int p = 0; p < OPF_PHASE_COUNT; ++p) {
+    if (ms) ms[p] = h->ph_ms[p];
+    if (launches) launches[p] = h->ph_n[p];
+  }
+  return OPF_OK;
+}
+
+int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters) {
+  if (!h || !u || !x || !(tol > 0.0) || max_iter < 0) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  double* ws = nullptr;
+  if (cudaMalloc(&ws, sizeof(double) * (P.nx + 1)) != cudaSuccess) return OPF_ERR_OOM;
+  int rc = OPF_ERR_PF_FAILED;
+  int k = 0;
+  for (; k <= max_iter; ++k) {
+    int r = eval_impl(h, x, u, nullptr, nullptr, false);
+    if (r != OPF_OK) { rc = r; break; }
+    double nrm = 0.0;
+    if (launch_absmax(h->s, P.nx, h->g, ws + P.nx) != cudaSuccess ||
+        cudaMemcpyAsync(&nrm, ws + P.nx, sizeof(double), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess) { rc = OPF_ERR_CUDA; break; }
+    if (nrm <= tol) { rc = OPF_OK; break; }
+    if (!(nrm < 1e10) || k == max_iter) break;
+    r = eval_impl(h, x, u, nullptr, nullptr, true);
+    if (r == OPF_OK) r = opf_gx_factor(h);
+    if (r == OPF_OK) r = opf_gx_solve(h, 0, h->g, ws, 1);
+    if (r != OPF_OK) { rc = r == OPF_ERR_SINGULAR ? OPF_ERR_PF_FAILED : r; break; }
+    if (launch_axpby(h->s, P.nx, -1.0, ws, 1.0, x, x) != cudaSuccess) { rc = OPF_ERR_CUDA; break; }
+  }
+  cudaStreamSynchronize(h->s);
+  cudaFree(ws);
+  if (iters) *iters = k;
+  h->have_W = false;
+  h->have_condense = false;
+  h->have_factor = false;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Shared device helpers and kernel declarations of the condensed-IPM library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace condipm {
+
+// device status word: [0] first error code, [1] its detail (row / column),
+// [2] a bounded wait expired
+enum { ST_CODE = 0, ST_INFO = 1, ST_TIMEOUT = 2, ST_WORDS = 4 };
+enum { DEV_OK = 0, DEV_NOT_PD = 1, DEV_SINGULAR = 2, DEV_TIMEOUT = 3 };
+
+__device__ __forceinline__ void set_status(int* st, int code, int info) {
+  if (atomicCAS(&st[ST_CODE], 0, code) == 0) atomicExch(&st[ST_INFO], info);
+}
+
+// Sense-reversing grid barrier with a bounded spin.  bar[0] counts arrivals,
+// bar[1] is the generation.  Returns false (and flags st[ST_TIMEOUT]) when the
+// wait exceeds spin_limit polls; callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long spin_limit,
+                                             int* st) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&bar[0], 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == g) {
+        if (++it > spin_limit) {
+          atomicExch(&st[ST_TIMEOUT], 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Kernel launches enqueued by this library (all handles, all threads).
+void note_launch();
+unsigned long long launch_count();
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `s` and return the launch error.
+
+// model (A1-A3)
+cudaError_t launch_bus_state(cudaStream_t s, int nb, int nu, const double* x, const double* u,
+                             const int* th_w, const int* vm_w, double* Vm, double* Va);
+cudaError_t launch_end_eval(cudaStream_t s, int ne, const int* end_i, const int* end_k,
+                            const int* end_h, const double* gs, const double* bs, const double* gm,
+                            const double* bm, const double* Vm, const double* Va, double* pq,
+                            double* dsrc, double* hpq, double* h, int want_derivs);
+cudaError_t launch_bus_sum(cudaStream_t s, int nb, int ng, int nu, int slack, const int* bus_end_ptr,
+                           const int* bus_end, const double* pq, const int* g_row_P,
+                           const int* g_row_Q, const int* gen_of_bus, const double* Pd,
+                           const double* Qd, const double* u, const double* c2, const double* c1,
+                           const double* lam, const double* y, double* g, double* h, double* Pg,
+                           double* wP, double* wQ);
+cudaError_t launch_objective(cudaStream_t s, int ng, const double* Pg, const double* c2,
+                             const double* c1, double* f);
+cudaError_t launch_gather(cudaStream_t s, int n, const int* ptr, const int* idx, const double* cst,
+                          const double* src, double* out);
+cudaError_t launch_gradf(cudaStream_t s, int nw, int ng, const int* pg_of_w, const int* slackpos,
+                         const double* Pg, const double* c2, const double* c1, const double* Aval,
+                         double* gradf);
+cudaError_t launch_end_hess(cudaStream_t s, int ne, const int* end_i, const int* end_h,
+                            const double* pq, const double* dsrc, const double* hpq, const double* wP,
+                            const double* wQ, const double* y, double* hw);
+cudaError_t launch_bilin_fixed(cudaStream_t s, int n, const int* pos, const int* a, const int* b,
+                               double coef, const double* A, double* out);
+
+// condensation (A4, A7, A8)
+cudaError_t launch_assemble_K(cudaStream_t s, long long nnz, const double* W, const int* ptr,
+                              const int* r, const int* a, const int* b, const double* sig_s,
+                              const double* Aval, double* K);
+cudaError_t launch_add_diag(cudaStream_t s, int nw, int nu, const int* K_diag, const int* perm,
+                            const double* sig_u, const double* sig_x, double* K, double* sig_c);
+cudaError_t launch_scatter_rows(cudaStream_t s, int nrows, const int* rp, const int* ci,
+                                const int* map, const double* src, double alpha, double* X, int ld);
+cudaError_t launch_spmm(cudaStream_t s, int nrows, const int* rp, const int* ci, const double* val,
+                        const int* valmap, const double* X, int ldx, double* Y, int ldy, int ncols,
+                        double alpha, double beta);
+cudaError_t launch_trsm(cudaStream_t s, int cb, int nlev, const int* lptr, const int* lrows,
+                        const int* rp, const int* ci, const double* val, const double* inv_diag,
+                        double* X, int ld, int ncols);
+cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, double* S);
+cudaError_t launch_dense_tn(cudaStream_t s, int nu, int nx, const double* Sx, const double* Hx,
+                            const double* Hu, double* Kred);
+
+// LU (A5)
+cudaError_t launch_lu_scatter(cudaStream_t s, long long nnzG, const int* Gx_to_LU, const double* Gval,
+                              double* LU);
+cudaError_t launch_row_absmax(cudaStream_t s, int n, const int* rp, const double* val, double* rmax);
+cudaError_t launch_lu_refactor(cudaStream_t s, int n, const int* rows, const int* rp, const int* ci,
+                               const int* diag, const long long* upd_ptr, const int* upd_pos,
+                               double* LU, double* inv_diag, const double* rmax, unsigned* flags,
+                               unsigned epoch, int* st, long long spin_limit, int nblocks, int nthreads,
+                               int maxlen);
+int lu_refactor_max_blocks(int nthreads, size_t smem);
+cudaError_t launch_gather_map(cudaStream_t s, long long n, const int* map, const double* src,
+                              double* dst);
+
+// dense Cholesky (A9)
+cudaError_t launch_chol_prepare(cudaStream_t s, int n, const double* A, double delta, double* F);
+cudaError_t launch_chol(cudaStream_t s, int n, double* F, int* st, unsigned* bar, long long spin_limit,
+                        int nblocks);
+int chol_max_blocks();
+cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, double* X, int nrhs);
+
+// vectors
+cudaError_t launch_permute_rows(cudaStream_t s, int n, int ncols, const int* idx, const double* src,
+                                int ld_src, int src_colmajor, double* dst, int ld_dst, int dst_colmajor,
+                                double alpha, int inverse);
+cudaError_t launch_axpby(cudaStream_t s, long long n, double a, const double* x, double b,
+                         const double* y, double* z);
+cudaError_t launch_scale_rows(cudaStream_t s, int n, int ncols, const double* d, const double* x,
+                              double* z, double b, const double* y);
+cudaError_t launch_absmax(cudaStream_t s, long long n, const double* x, double* out);
+cudaError_t launch_fill(cudaStream_t s, long long n, double v, double* x);
+cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld);
+
+}  // namespace condipm

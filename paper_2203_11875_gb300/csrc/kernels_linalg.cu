@@ -1,0 +1,665 @@
+// A4-A10: sparse LU refactorisation of G_x, multi-right-hand-side triangular
+// solves, K assembly and products, the condensed matrix, dense Cholesky and its
+// solves.  FP64 throughout.  On GB300 the FP64 pipe (two DFMA per clock per SM,
+// about 1.2 TFLOP/s per GPU; the f64 mma.sync path is slower still) bounds
+// every kernel here, so the kernels keep every DFMA lane busy with useful work
+// and leave data movement to the load/store pipes.
+#include "common.cuh"
+
+#include <cmath>
+
+namespace condipm {
+namespace {
+
+inline int nblk(long long n, int t) { return int((n + t - 1) / t); }
+
+// ----------------------------------------------------------------- K assembly
+// K[p] = W[p] + sum_q sig_s[r_q] A[a_q] A[b_q]   (A^T Sigma_s A in K's pattern)
+__global__ void k_assemble_K(long long nnz, const double* __restrict__ W, const int* __restrict__ ptr,
+                             const int* __restrict__ r, const int* __restrict__ a,
+                             const int* __restrict__ b, const double* __restrict__ sig_s,
+                             const double* __restrict__ Aval, double* __restrict__ K) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  double acc = W[p];
+  for (int q = ptr[p]; q < ptr[p + 1]; ++q) acc = fma(sig_s[r[q]] * Aval[a[q]], Aval[b[q]], acc);
+  K[p] = acc;
+}
+
+// K[(c,c)] += sigma_c, sigma in c-order ([u; x permuted])
+__global__ void k_add_diag(int nw, int nu, const int* __restrict__ K_diag, const int* __restrict__ perm,
+                           const double* __restrict__ sig_u, const double* __restrict__ sig_x,
+                           double* __restrict__ K, double* __restrict__ sig_c) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nw) return;
+  double s = c < nu ? sig_u[c] : sig_x[perm[c - nu]];
+  K[K_diag[c]] += s;
+  sig_c[c] = s;
+}
+
+// X[i][col] = alpha * src[map[q]] for the entries q of row i (dense X zeroed before)
+__global__ void k_scatter_rows(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const int* __restrict__ map, const double* __restrict__ src, double alpha,
+                               double* __restrict__ X, int ld) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  for (int q = rp[i]; q < rp[i + 1]; ++q) X[(size_t)i * ld + ci[q]] = alpha * src[map ? map[q] : q];
+}
+
+// Y = alpha * M X + beta * Y, M CSR, X and Y row-major.  Thread (row, col) with the
+// column fastest, so neighbouring threads read neighbouring X entries.
+__global__ void k_spmm(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                       const double* __restrict__ val, const int* __restrict__ valmap,
+                       const double* __restrict__ X, int ldx, double* __restrict__ Y, int ldy, int ncols,
+                       double alpha, double beta) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long total = (long long)nrows * ncols;
+  if (t >= total) return;
+  int r = int(t / ncols), c = int(t % ncols);
+  double acc = 0.0;
+  const int e = rp[r + 1];
+  if (valmap) {
+    for (int q = rp[r]; q < e; ++q) acc = fma(val[valmap[q]], X[(size_t)ci[q] * ldx + c], acc);
+  } else {
+    for (int q = rp[r]; q < e; ++q) acc = fma(val[q], X[(size_t)ci[q] * ldx + c], acc);
+  }
+  double* y = Y + (size_t)r * ldy + c;
+  *y = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *y);
+}
+
+// Multi-right-hand-side sparse triangular solve, level-scheduled inside one CTA.
+// CTA b owns columns [b*CB, b*CB + CB); its threads form slots of CB lanes, one
+// lane per column, and a slot walks the rows of the current level.  Levels are
+// separated by __syncthreads only: the columns are independent, so no CTA ever
+// waits for another.  Row i: X_i <- (X_i - sum_q val_q X_{ci_q}) * inv_diag_i
+// (inv_diag NULL = unit diagonal).
+template <int CB>
+__global__ void __launch_bounds__(256) k_trsm(int nlev, const int* __restrict__ lptr,
+                                              const int* __restrict__ lrows, const int* __restrict__ rp,
+                                              const int* __restrict__ ci, const double* __restrict__ val,
+                                              const double* __restrict__ inv_diag, double* X, int ld,
+                                              int ncols) {
+  const int c = blockIdx.x * CB + (threadIdx.x % CB);
+  const int slot = threadIdx.x / CB;
+  const int nslots = blockDim.x / CB;
+  const bool active = c < ncols;
+  double* Xc = X + c;
+  for (int lev = 0; lev < nlev; ++lev) {
+    const int beg = lptr[lev], end = lptr[lev + 1];
+    if (active) {
+      for (int t = beg + slot; t < end; t += nslots) {
+        const int i = lrows[t];
+        double acc = Xc[(size_t)i * ld];
+        const int qe = rp[i + 1];
+        for (int q = rp[i]; q < qe; ++q) acc = fma(-val[q], Xc[(size_t)ci[q] * ld], acc);
+        if (inv_diag) acc *= inv_diag[i];
+        Xc[(size_t)i * ld] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_symmetrize(int n, const double* __restrict__ A, double* __restrict__ S) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int i = int(t / n), j = int(t % n);
+  S[t] = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+}
+
+// Kred = Hu + Sx^T Hx (explicit route): C[a][c] = Hu[a][c] + sum_j Sx[j][a] Hx[j][c],
+// 64x64 output tiles, 16-deep k slices staged in shared memory, 4x4 per thread.
+__global__ void __launch_bounds__(256) k_dense_tn(int nu, int nx, const double* __restrict__ Sx,
+                                                  const double* __restrict__ Hx,
+                                                  const double* __restrict__ Hu, double* __restrict__ C) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int a0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < nx; k0 += 16) {
+    for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+      int kk = t / 64, j = t % 64;
+      int k = k0 + kk;
+      As[kk][j] = (k < nx && a0 + j < nu) ? Sx[(size_t)k * nu + a0 + j] : 0.0;
+      Bs[kk][j] = (k < nx && c0 + j < nu) ? Hx[(size_t)k * nu + c0 + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { av[u] = As[kk][ty * 4 + u]; bv[u] = Bs[kk][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int a = a0 + ty * 4 + u, c = c0 + tx * 4 + v;
+      if (a < nu && c < nu) C[(size_t)a * nu + c] = Hu[(size_t)a * nu + c] + acc[u][v];
+    }
+}
+
+// ----------------------------------------------------------------- LU refactor
+__global__ void k_lu_scatter(long long nnzG, const int* __restrict__ map, const double* __restrict__ G,
+                             double* __restrict__ LU) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= nnzG) return;
+  int p = map[q];
+  if (p >= 0) LU[p] = G[q];
+}
+
+__global__ void k_row_absmax(int n, const int* __restrict__ rp, const double* __restrict__ v,
+                             double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double m = 0.0;
+  for (int q = rp[i]; q < rp[i + 1]; ++q) m = fmax(m, fabs(v[q]));
+  out[i] = m;
+}
+
+// Numeric up-looking LU of P G_x P^T in its fixed pattern (static pivots).
+// One warp per row, rows taken in level order; a row waits (bounded) on the
+// completion flag of each row k it references, so rows of different levels
+// overlap instead of meeting at grid-wide barriers.  The row being factored is
+// staged in shared memory; rows of other warps are read through L2 (ld.cg).
+// Row i: for k in L(i) ascending: l_ik = w_k / u_kk; w_j -= l_ik u_kj (j in U(k)).
+__global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __restrict__ rp,
+                              const int* __restrict__ ci, const int* __restrict__ diag,
+                              const long long* __restrict__ upd_ptr, const int* __restrict__ upd_pos,
+                              double* LU, double* inv_diag, const double* __restrict__ rmax,
+                              unsigned* flags, unsigned epoch, int* st, long long spin_limit,
+                              int maxlen) {
+  extern __shared__ double wsh[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  double* w = wsh + (size_t)wib * maxlen;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  volatile int* vst = st;
+  for (int t = warp; t < n; t += nwarps) {
+    const int i = rows[t];
+    const int r0 = rp[i], r1 = rp[i + 1], dpos = diag[i];
+    for (int j = r0 + lane; j < r1; j += 32) w[j - r0] = __ldcg(&LU[j]);
+    __syncwarp();
+    for (int q = r0; q < dpos; ++q) {
+      const int k = ci[q];
+      if (lane == 0) {
+        volatile unsigned* vf = flags + k;
+        long long it = 0;
+        while (*vf != epoch) {
+          if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); break; }
+          __nanosleep(32);
+        }
+      }
+      __syncwarp();
+      __threadfence();
+      if (vst[ST_TIMEOUT]) return;
+      const double lik = w[q - r0] * __ldcg(&inv_diag[k]);
+      __syncwarp();
+      const int ub = diag[k] + 1, ue = rp[k + 1];
+      const long long base = upd_ptr[q];
+      for (int j = ub + lane; j < ue; j += 32) {
+        const int pos = upd_pos[base + (j - ub)] - r0;
+        w[pos] = fma(-lik, __ldcg(&LU[j]), w[pos]);
+      }
+      if (lane == 0) w[q - r0] = lik;
+      __syncwarp();
+    }
+    for (int j = r0 + lane; j < r1; j += 32) LU[j] = w[j - r0];
+    __syncwarp();
+    if (lane == 0) {
+      const double u = w[dpos - r0];
+      double inv = 0.0;
+      if (!(fabs(u) > 1e-14 * rmax[i]) || !isfinite(u)) set_status(st, DEV_SINGULAR, i);
+      else inv = 1.0 / u;
+      inv_diag[i] = inv;
+      __threadfence();
+      atomicExch(&flags[i], epoch);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_gather_map(long long n, const int* __restrict__ map, const double* __restrict__ src,
+                             double* __restrict__ dst) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q < n) dst[q] = src[map[q]];
+}
+
+// ----------------------------------------------------------------- Cholesky
+constexpr int CNB = 32;
+
+__global__ void k_chol_prepare(int n, const double* __restrict__ A, double delta, double* __restrict__ F) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int i = int(t / n), j = int(t % n);
+  F[t] = j > i ? 0.0 : (i == j ? A[t] + delta : A[t]);
+}
+
+// Right-looking blocked Cholesky of the lower triangle of F (row-major n x n),
+// 32x32 tiles, one persistent cooperative grid; phases (diagonal tile, panel,
+// trailing update) are separated by a bounded grid barrier.  A non-positive or
+// non-finite pivot records DEV_NOT_PD with its column and ends the kernel.
+__global__ void __launch_bounds__(256) k_chol(double* F, int n, int* st, unsigned* bar,
+                                              long long spin_limit) {
+  __shared__ double Ta[CNB][CNB + 1];
+  __shared__ double Tb[CNB][CNB + 1];
+  __shared__ double dinv[CNB];
+  __shared__ int okflag;
+  const int tid = threadIdx.x;
+  const int nt = (n + CNB - 1) / CNB;
+  const unsigned nbk = gridDim.x;
+  volatile int* vst = st;
+  for (int k = 0; k < nt; ++k) {
+    const int k0 = k * CNB, kb = min(CNB, n - k0);
+    // ---- phase 1: factor the diagonal tile
+    if (blockIdx.x == 0) {
+      for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+        int i = t / CNB, j = t % CNB;
+        Ta[i][j] = (i < kb && j <= i) ? F[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
+      }
+      __syncthreads();
+      for (int j = 0; j < kb; ++j) {
+        if (tid == 0) {
+          double d = Ta[j][j];
+          okflag = (d > 0.0 && isfinite(d));
+          if (okflag) { d = sqrt(d); Ta[j][j] = d; dinv[j] = 1.0 / d; }
+          else set_status(st, DEV_NOT_PD, k0 + j);
+        }
+        __syncthreads();
+        if (!okflag) break;
+        for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ta[i][j] *= dinv[j];
+        __syncthreads();
+        const int rem = kb - j - 1;
+        for (int t = tid; t < rem * rem; t += blockDim.x) {
+          int i = j + 1 + t / rem, l = j + 1 + t % rem;
+          if (l <= i) Ta[i][l] = fma(-Ta[i][j], Ta[l][j], Ta[i][l]);
+        }
+        __syncthreads();
+      }
+      for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+        int i = t / CNB, j = t % CNB;
+        if (i < kb && j <= i) F[(size_t)(k0 + i) * n + k0 + j] = Ta[i][j];
+      }
+    }
+    if (!grid_barrier(bar, nbk, spin_limit, st)) return;
+    if (vst[ST_CODE] != 0) return;
+    // ---- phase 2: panel  L_ik = A_ik L_kk^{-T}
+    if (k + 1 < nt) {
+      bool loaded = false;
+      for (int ti = k + 1 + blockIdx.x; ti < nt; ti += nbk) {
+        if (!loaded) {
+          for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+            int i = t / CNB, j = t % CNB;
+            Ta[i][j] = (i < kb && j <= i) ? F[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
+          }
+          __syncthreads();
+          if (tid < CNB) dinv[tid] = 1.0 / Ta[tid][tid];
+          loaded = true;
+        }
+        const int i0 = ti * CNB, ib = min(CNB, n - i0);
+        for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+          int i = t / CNB, j = t % CNB;
+          Tb[i][j] = (i < ib && j < kb) ? F[(size_t)(i0 + i) * n + k0 + j] : 0.0;
+        }
+        __syncthreads();
+        // each warp solves 4 rows; lane l holds column l of its row
+        const int warp = tid >> 5, lane = tid & 31;
+        double a[4];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) a[rr] = Tb[warp * 4 + rr][lane];
+        for (int j = 0; j < kb; ++j) {
+          const double ljl = Ta[lane][j];
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            double xj = __shfl_sync(0xffffffffu, a[rr], j) * dinv[j];
+            if (lane == j) a[rr] = xj;
+            else if (lane > j) a[rr] = fma(-xj, ljl, a[rr]);
+          }
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          int i = warp * 4 + rr;
+          if (i < ib && lane < kb) F[(size_t)(i0 + i) * n + k0 + lane] = a[rr];
+        }
+        __syncthreads();
+      }
+    }
+    if (!grid_barrier(bar, nbk, spin_limit, st)) return;
+    // ---- phase 3: trailing update  A_ij -= L_ik L_jk^T,  k < j <= i
+    const int m = nt - k - 1;
+    const long long ntile = (long long)m * (m + 1) / 2;
+    for (long long tt = blockIdx.x; tt < ntile; tt += nbk) {
+      int ii = int((sqrt(8.0 * (double)tt + 1.0) - 1.0) * 0.5);
+      while ((long long)(ii + 1) * (ii + 2) / 2 <= tt) ++ii;
+      while ((long long)ii * (ii + 1) / 2 > tt) --ii;
+      const int jj = int(tt - (long long)ii * (ii + 1) / 2);
+      const int ti = k + 1 + ii, tj = k + 1 + jj;
+      const int i0 = ti * CNB, j0 = tj * CNB;
+      const int ib = min(CNB, n - i0), jb = min(CNB, n - j0);
+      for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+        int i = t / CNB, j = t % CNB;
+        Ta[i][j] = (i < ib && j < kb) ? F[(size_t)(i0 + i) * n + k0 + j] : 0.0;
+        Tb[i][j] = (i < jb && j < kb) ? F[(size_t)(j0 + i) * n + k0 + j] : 0.0;
+      }
+      __syncthreads();
+      const int r0 = (tid >> 4) * 2, c0 = (tid & 15) * 2;
+      double acc[2][2] = {};
+#pragma unroll 8
+      for (int l = 0; l < CNB; ++l) {
+        double a0 = Ta[r0][l], a1 = Ta[r0 + 1][l], b0 = Tb[c0][l], b1 = Tb[c0 + 1][l];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          int gi = i0 + r0 + u, gj = j0 + c0 + v;
+          if (r0 + u < ib && c0 + v < jb && gj <= gi) F[(size_t)gi * n + gj] -= acc[u][v];
+        }
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, nbk, spin_limit, st)) return;
+  }
+}
+
+// Solve L L^T X = B for the columns of X (row-major n x nrhs); one CTA per column.
+// Forward: 32-row tiles, x_I = L_II^{-1}(b_I - L_I,<I x_<I), the GEMV part with warps
+// over rows and lanes over columns of L; backward mirrors it with L^T.
+__global__ void __launch_bounds__(256) k_chol_solve(int n, const double* __restrict__ F, double* X,
+                                                    int nrhs) {
+  extern __shared__ double xs[];   // n entries: the column being solved
+  __shared__ double part[8][CNB];
+  const int col = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < n; i += blockDim.x) xs[i] = X[(size_t)i * nrhs + col];
+  __syncthreads();
+  const int nt = (n + CNB - 1) / CNB;
+  // forward
+  for (int I = 0; I < nt; ++I) {
+    const int i0 = I * CNB, ib = min(CNB, n - i0);
+    // b_I -= L[I rows][0:i0] x[0:i0]: warp w takes rows i0+w, i0+w+8, ...
+    for (int rr = warp; rr < ib; rr += 8) {
+      const double* Lr = F + (size_t)(i0 + rr) * n;
+      double acc = 0.0;
+      for (int j = lane; j < i0; j += 32) acc = fma(Lr[j], xs[j], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) xs[i0 + rr] -= acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double xv = lane < ib ? xs[i0 + lane] : 0.0;
+      for (int j = 0; j < ib; ++j) {
+        double xj = __shfl_sync(0xffffffffu, xv, j) / F[(size_t)(i0 + j) * n + i0 + j];
+        if (lane == j) xv = xj;
+        else if (lane > j && lane < ib) xv = fma(-xj, F[(size_t)(i0 + lane) * n + i0 + j], xv);
+      }
+      if (lane < ib) xs[i0 + lane] = xv;
+    }
+    __syncthreads();
+  }
+  // backward: L^T x = y
+  for (int I = nt - 1; I >= 0; --I) {
+    const int i0 = I * CNB, ib = min(CNB, n - i0);
+    // y_I -= sum_{r >= i0+ib} L[r][i0 + c] x_r : warps over rows r, lanes over c
+    double acc = 0.0;
+    for (int r = i0 + ib + warp; r < n; r += 8)
+      if (lane < ib) acc = fma(F[(size_t)r * n + i0 + lane], xs[r], acc);
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      double s = 0.0;
+      for (int w2 = 0; w2 < 8; ++w2) s += part[w2][lane];
+      double xv = lane < ib ? xs[i0 + lane] - s : 0.0;
+      for (int j = ib - 1; j >= 0; --j) {
+        double xj = __shfl_sync(0xffffffffu, xv, j) / F[(size_t)(i0 + j) * n + i0 + j];
+        if (lane == j) xv = xj;
+        else if (lane < j) xv = fma(-xj, F[(size_t)(i0 + j) * n + i0 + lane], xv);
+      }
+      if (lane < ib) xs[i0 + lane] = xv;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += blockDim.x) X[(size_t)i * nrhs + col] = xs[i];
+}
+
+// ----------------------------------------------------------------- vectors
+// Row permutation and layout change of an n x ncols block:
+//   inverse = 0: dst(r, c) = alpha * src(idx[r], c);  inverse = 1: dst(idx[r], c) = alpha * src(r, c)
+// (idx NULL = identity).  *_colmajor selects element (row, c) at [c*ld + row]
+// instead of [row*ld + c].
+__global__ void k_permute_rows(int n, int ncols, const int* __restrict__ idx, const double* __restrict__ src,
+                               int lds, int scm, double* __restrict__ dst, int ldd, int dcm, double alpha,
+                               int inverse) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * ncols) return;
+  int r = int(t / ncols), c = int(t % ncols);
+  int rs = r, rd = r;
+  if (idx) { if (inverse) rd = idx[r]; else rs = idx[r]; }
+  double v = scm ? src[(size_t)c * lds + rs] : src[(size_t)rs * lds + c];
+  if (dcm) dst[(size_t)c * ldd + rd] = alpha * v;
+  else dst[(size_t)rd * ldd + c] = alpha * v;
+}
+
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ z) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  z[t] = y ? fma(a, x[t], b * y[t]) : a * x[t];
+}
+
+// z(r, c) = d[r] * x(r, c) + b * y(r, c)   (row-major, y may be NULL)
+__global__ void k_scale_rows(int n, int ncols, const double* __restrict__ d, const double* __restrict__ x,
+                             double* __restrict__ z, double b, const double* __restrict__ y) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * ncols) return;
+  int r = int(t / ncols);
+  z[t] = y ? fma(d[r], x[t], b * y[t]) : d[r] * x[t];
+}
+
+__global__ void k_absmax(long long n, const double* __restrict__ x, double* __restrict__ out) {
+  __shared__ double sh[1024];
+  double m = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) m = fmax(m, fabs(x[t]));
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+__global__ void k_fill(long long n, double v, double* __restrict__ x) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) x[t] = v;
+}
+
+__global__ void k_set_identity(int n, double* __restrict__ X, int ld) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int i = int(t / n), j = int(t % n);
+  X[(size_t)i * ld + j] = i == j ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers
+cudaError_t launch_assemble_K(cudaStream_t s, long long nnz, const double* W, const int* ptr, const int* r,
+                              const int* a, const int* b, const double* sig_s, const double* Aval,
+                              double* K) {
+  k_assemble_K<<<nblk(nnz, 256), 256, 0, s>>>(nnz, W, ptr, r, a, b, sig_s, Aval, K);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_add_diag(cudaStream_t s, int nw, int nu, const int* K_diag, const int* perm,
+                            const double* sig_u, const double* sig_x, double* K, double* sig_c) {
+  k_add_diag<<<nblk(nw, 256), 256, 0, s>>>(nw, nu, K_diag, perm, sig_u, sig_x, K, sig_c);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter_rows(cudaStream_t s, int nrows, const int* rp, const int* ci, const int* map,
+                                const double* src, double alpha, double* X, int ld) {
+  if (nrows <= 0) return cudaSuccess;
+  k_scatter_rows<<<nblk(nrows, 256), 256, 0, s>>>(nrows, rp, ci, map, src, alpha, X, ld);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_spmm(cudaStream_t s, int nrows, const int* rp, const int* ci, const double* val,
+                        const int* valmap, const double* X, int ldx, double* Y, int ldy, int ncols,
+                        double alpha, double beta) {
+  long long total = (long long)nrows * ncols;
+  if (total <= 0) return cudaSuccess;
+  k_spmm<<<nblk(total, 256), 256, 0, s>>>(nrows, rp, ci, val, valmap, X, ldx, Y, ldy, ncols, alpha, beta);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_trsm(cudaStream_t s, int cb, int nlev, const int* lptr, const int* lrows, const int* rp,
+                        const int* ci, const double* val, const double* inv_diag, double* X, int ld,
+                        int ncols) {
+  if (ncols <= 0 || nlev <= 0) return cudaSuccess;
+  const int T = 256;
+#define TRSM_CASE(CBV)                                                                           \
+  case CBV:                                                                                      \
+    k_trsm<CBV><<<nblk(ncols, CBV), T, 0, s>>>(nlev, lptr, lrows, rp, ci, val, inv_diag, X, ld, ncols); \
+    break;
+  switch (cb) {
+    TRSM_CASE(1) TRSM_CASE(2) TRSM_CASE(4) TRSM_CASE(8) TRSM_CASE(16) TRSM_CASE(32)
+    default: return cudaErrorInvalidValue;
+  }
+#undef TRSM_CASE
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, double* S) {
+  k_symmetrize<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, A, S);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_dense_tn(cudaStream_t s, int nu, int nx, const double* Sx, const double* Hx,
+                            const double* Hu, double* Kred) {
+  dim3 grid(nblk(nu, 64), nblk(nu, 64));
+  k_dense_tn<<<grid, 256, 0, s>>>(nu, nx, Sx, Hx, Hu, Kred);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_lu_scatter(cudaStream_t s, long long nnzG, const int* Gx_to_LU, const double* Gval,
+                              double* LU) {
+  k_lu_scatter<<<nblk(nnzG, 256), 256, 0, s>>>(nnzG, Gx_to_LU, Gval, LU);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_row_absmax(cudaStream_t s, int n, const int* rp, const double* val, double* rmax) {
+  k_row_absmax<<<nblk(n, 256), 256, 0, s>>>(n, rp, val, rmax);
+  note_launch();
+  return cudaGetLastError();
+}
+int lu_refactor_max_blocks(int nthreads, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_lu_refactor, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lu_refactor, nthreads, smem);
+  return sms * per;
+}
+// Cooperative launch: every warp of the grid is resident, which the flag waits
+// of the sync-free schedule rely on.
+cudaError_t launch_lu_refactor(cudaStream_t s, int n, const int* rows, const int* rp, const int* ci,
+                               const int* diag, const long long* upd_ptr, const int* upd_pos, double* LU,
+                               double* inv_diag, const double* rmax, unsigned* flags, unsigned epoch,
+                               int* st, long long spin_limit, int nblocks, int nthreads, int maxlen) {
+  size_t smem = (size_t)(nthreads / 32) * maxlen * sizeof(double);
+  void* args[] = {&n, &rows, &rp, &ci, &diag, &upd_ptr, &upd_pos, &LU, &inv_diag, &rmax, &flags, &epoch,
+                  &st, &spin_limit, &maxlen};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_lu_refactor, dim3(nblocks), dim3(nthreads), args, smem, s);
+}
+cudaError_t launch_gather_map(cudaStream_t s, long long n, const int* map, const double* src, double* dst) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_map<<<nblk(n, 256), 256, 0, s>>>(n, map, src, dst);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_chol_prepare(cudaStream_t s, int n, const double* A, double delta, double* F) {
+  k_chol_prepare<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, A, delta, F);
+  note_launch();
+  return cudaGetLastError();
+}
+int chol_max_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol, 256, 0);
+  return sms * (per > 0 ? per : 1);
+}
+cudaError_t launch_chol(cudaStream_t s, int n, double* F, int* st, unsigned* bar, long long spin_limit,
+                        int nblocks) {
+  void* args[] = {&F, &n, &st, &bar, &spin_limit};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_chol, dim3(nblocks), dim3(256), args, 0, s);
+}
+cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, double* X, int nrhs) {
+  if (nrhs <= 0) return cudaSuccess;
+  size_t sm = (size_t)n * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+  }
+  k_chol_solve<<<nrhs, 256, sm, s>>>(n, F, X, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_permute_rows(cudaStream_t s, int n, int ncols, const int* idx, const double* src,
+                                int ld_src, int src_colmajor, double* dst, int ld_dst, int dst_colmajor,
+                                double alpha, int inverse) {
+  long long total = (long long)n * ncols;
+  if (total <= 0) return cudaSuccess;
+  k_permute_rows<<<nblk(total, 256), 256, 0, s>>>(n, ncols, idx, src, ld_src, src_colmajor, dst, ld_dst,
+                                                 dst_colmajor, alpha, inverse);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_axpby(cudaStream_t s, long long n, double a, const double* x, double b, const double* y,
+                         double* z) {
+  if (n <= 0) return cudaSuccess;
+  k_axpby<<<nblk(n, 256), 256, 0, s>>>(n, a, x, b, y, z);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_rows(cudaStream_t s, int n, int ncols, const double* d, const double* x, double* z,
+                              double b, const double* y) {
+  long long total = (long long)n * ncols;
+  if (total <= 0) return cudaSuccess;
+  k_scale_rows<<<nblk(total, 256), 256, 0, s>>>(n, ncols, d, x, z, b, y);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_absmax(cudaStream_t s, long long n, const double* x, double* out) {
+  k_absmax<<<1, 1024, 0, s>>>(n, x, out);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_fill(cudaStream_t s, long long n, double v, double* x) {
+  if (n <= 0) return cudaSuccess;
+  k_fill<<<nblk(n, 256), 256, 0, s>>>(n, v, x);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld) {
+  k_set_identity<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, X, ld);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace condipm

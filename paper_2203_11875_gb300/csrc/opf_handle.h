@@ -1,0 +1,74 @@
+// Internal state behind the opaque opf_handle of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/condipm.h"
+#include "plan.h"
+
+struct opf_handle {
+  condipm::Plan P;
+  opf_options opt{};
+  cudaStream_t s = nullptr;
+  long long spin_limit = 1LL << 26;
+  std::vector<void*> allocs;
+  // topology / network (device)
+  int *end_i = nullptr, *end_k = nullptr, *end_h = nullptr, *bus_end_ptr = nullptr, *bus_end = nullptr;
+  int *g_row_P = nullptr, *g_row_Q = nullptr, *gen_of_bus = nullptr, *th_w = nullptr, *vm_w = nullptr;
+  int *pg_of_w = nullptr, *slackpos = nullptr;
+  double *gs = nullptr, *bs = nullptr, *gm = nullptr, *bm = nullptr, *Pd = nullptr, *Qd = nullptr;
+  double *c2 = nullptr, *c1 = nullptr;
+  // model evaluation
+  double *Vm = nullptr, *Va = nullptr, *pq = nullptr, *dsrc = nullptr, *hpq = nullptr, *hw = nullptr;
+  double *wP = nullptr, *wQ = nullptr, *g = nullptr, *hv = nullptr, *f = nullptr, *gradf = nullptr;
+  double *Pg = nullptr;
+  // G, A
+  int *Ggat_ptr = nullptr, *Ggat_idx = nullptr;
+  double *Ggat_cst = nullptr, *Gval = nullptr;
+  int *Agat_ptr = nullptr, *Agat_idx = nullptr, *A_rp = nullptr, *A_ci_c = nullptr;
+  double *Agat_cst = nullptr, *Aval = nullptr;
+  // K and W (c-order pattern)
+  int *K_rp = nullptr, *K_ci = nullptr, *Wgat_ptr = nullptr, *Wgat_idx = nullptr;
+  int *Wsl_pos = nullptr, *Wsl_a = nullptr, *Wsl_b = nullptr, *K_diag = nullptr;
+  int *KAA_ptr = nullptr, *KAA_r = nullptr, *KAA_a = nullptr, *KAA_b = nullptr, *Knat_map = nullptr;
+  int *perm = nullptr, *c2w = nullptr;
+  double *Wgat_cst = nullptr, *Wval = nullptr, *Kval = nullptr, *sig_c = nullptr, *sig_s = nullptr;
+  // transposes
+  int *AT_rp = nullptr, *AT_ci = nullptr, *AT_map = nullptr;
+  int *PGu_rp = nullptr, *PGu_ci = nullptr, *PGu_map = nullptr;
+  int *GuT_rp = nullptr, *GuT_ci = nullptr, *GuT_map = nullptr;
+  // LU
+  int *LU_rp = nullptr, *LU_ci = nullptr, *LU_diag = nullptr, *Gx_to_LU = nullptr, *upd_pos = nullptr;
+  long long* upd_ptr = nullptr;
+  double *LUval = nullptr, *inv_diag = nullptr, *rmax = nullptr;
+  unsigned* flags = nullptr;
+  unsigned epoch = 0;
+  int *Lo_rp = nullptr, *Lo_ci = nullptr, *Lo_map = nullptr, *Ut_map = nullptr;
+  int *Up_rp = nullptr, *Up_ci = nullptr, *Up_map = nullptr, *Lt_map = nullptr;
+  double *Lo_val = nullptr, *Ut_val = nullptr, *Up_val = nullptr, *Lt_val = nullptr;
+  int *fwd_ptr = nullptr, *fwd_rows = nullptr, *bwd_ptr = nullptr, *bwd_rows = nullptr;
+  // dense condensed buffers: Zt = [I; S_x] and H = K Zt (nw x nu, row-major, x rows permuted),
+  // Kred (nu x nu, symmetric) and its Cholesky factor F
+  double *Zt = nullptr, *H = nullptr, *Kred = nullptr, *F = nullptr;
+  // device status word and grid-barrier state
+  int* st = nullptr;
+  unsigned* bar = nullptr;
+  // growable workspace for solves
+  double* ws = nullptr;
+  size_t ws_cap = 0;
+  // launch shapes
+  int lu_blocks = 1, lu_threads = 256, lu_maxlen = 1, chol_blocks = 1, cb = 1;
+  // call-order state
+  bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
+  double delta_w = 0.0;
+  // phase timing (opf_profile)
+  bool profiling = false;
+  struct PhaseRec { int phase; cudaEvent_t a, b; };
+  std::vector<PhaseRec> recs;
+  std::vector<cudaEvent_t> evpool;
+  int open_phase = -1;
+  cudaEvent_t open_ev = nullptr;
+  double ph_ms[OPF_PHASE_COUNT] = {};
+  long long ph_n[OPF_PHASE_COUNT] = {};
+};
