@@ -196,6 +196,7 @@ def main():
             delta = max(1e-4, 8 * delta)
         h.kkt_solve(D["r"], step)
     torch.cuda.synchronize()
+    trsm_kernel, trsm_tune = h.trsm_choice()
     n_launch0 = binding.launch_count()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -262,7 +263,10 @@ def main():
            "warmup": args.warmup, "ms_per_step": t_full, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "l2": "256 MB flush written between timed steps",
-                      "route": "adjoint", "rhs_block": None, "delta_w": delta},
+                      "route": "adjoint", "delta_w": delta,
+                      "trsm_kernel": {32: "column-parallel", 1: "staged x1", 2: "staged x2", 4: "staged x4"}.get(
+                          trsm_kernel, str(trsm_kernel)),
+                      "autotune_ms": trsm_tune},
            "clocks": clocks, "gpu_launches": int(n_launch),
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                    "includes": "H2D of x,u,lambda,y,Sigma,r + derivatives + condense + Cholesky + step + D2H of the step"},
@@ -301,7 +305,8 @@ def main():
             b.synchronize()
             t10.append(a.elapsed_time(b))
         ph10 = h10.phase_times()
-        out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)),
+        k10, tune10 = h10.trsm_choice()
+        out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)), "trsm_kernel": k10, "autotune_ms": tune10,
                           "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
                           "symbolic": h10.stats()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

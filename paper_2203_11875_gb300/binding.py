@@ -50,6 +50,7 @@ _SIGS = {
     "opf_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), _ip, _ip, C.POINTER(C.c_longlong),
                             C.POINTER(C.c_longlong)]),
     "opf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_eval_functions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_get_vector": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -169,6 +170,12 @@ class Handle:
                "opf_stats")
         return dict(nnz_lu=a.value, levels_fwd=b.value, levels_bwd=c.value, nnz_k=d_.value,
                     lu_flops=e.value)
+
+    def trsm_choice(self):
+        k = C.c_int()
+        ms = (C.c_float * 4)()
+        _check(self._lib.opf_trsm_choice(self._h, C.byref(k), ms), "opf_trsm_choice")
+        return k.value, {"cols": ms[0], "staged1": ms[1], "staged2": ms[2], "staged4": ms[3]}
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""

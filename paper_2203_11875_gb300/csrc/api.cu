@@ -201,14 +201,49 @@ int upload_all(opf_handle* h) {
   TRY(upload(h, &h->fwd_rows, P.fwd.rows));
   TRY(upload(h, &h->bwd_ptr, P.bwd.ptr));
   TRY(upload(h, &h->bwd_rows, P.bwd.rows));
+  h->st_cap = std::max(P.stL.max_chunk, P.stU.max_chunk);
+  h->st_cap = (h->st_cap + 15) & ~15;
+  for (int k = 0; k < 2; ++k) {
+    const SnStream& S = k ? P.stU : P.stL;
+    opf_handle::StBuf& D = k ? h->stUp : h->stLo;
+    D.nchunks = int(S.chunk_off.size());
+    D.nslots = (long long)S.slot.size();
+    TRY(upload(h, &D.chunk_off, S.chunk_off));
+    TRY(upload(h, &D.chunk_bytes, S.chunk_bytes));
+    TRY(upload(h, &D.chunk_big_f, S.chunk_big_f));
+    TRY(upload(h, &D.chunk_big_w, S.chunk_big_w));
+    TRY(upload(h, &D.int_beg, (k ? P.snU : P.snL).int_beg));
+    TRY(upload(h, &D.slot, S.slot));
+    TRY(upload(h, &D.src, S.src));
+    TRY(upload(h, &D.bytes_a, S.bytes));
+    TRY(upload(h, &D.bytes_b, S.bytes));
+  }
+  for (int k = 0; k < 2; ++k) {
+    const ColSched& C = k ? P.csU : P.csL;
+    int *a, *b, *c, *d, *e, *f, *g0, *g, *hh, *i, *j, *l;
+    TRY(upload(h, &a, C.lvl_ptr)); TRY(upload(h, &b, C.sn_first)); TRY(upload(h, &c, C.sn_w));
+    TRY(upload(h, &d, C.lvl_seg_ptr)); TRY(upload(h, &e, C.seg_q0)); TRY(upload(h, &f, C.seg_q1));
+    TRY(upload(h, &g0, C.seg_row));
+    TRY(upload(h, &g, C.row_seg)); TRY(upload(h, &hh, C.row_nseg)); TRY(upload(h, &i, C.ext_beg));
+    TRY(upload(h, &j, C.ext_end)); TRY(upload(h, &l, C.int_beg));
+    (k ? h->csU : h->csL) = ColDev{C.nlev, C.maxseg, a, b, c, d, e, f, g0, g, hh, i, j, l};
+  }
+  h->ldp = (P.nu + 31) / 32 * 32;
+  h->cs_ncb_max = std::max((P.nu + 31) / 32, 8);
+  {
+    const int maxseg = std::max(1, std::max(P.csL.maxseg, P.csU.maxseg));
+    TRY(alloc(h, &h->cs_scratch, (size_t)h->cs_ncb_max * maxseg * 32));
+    TRY(alloc(h, &h->cs_bar, (size_t)h->cs_ncb_max));
+  }
   // dense
-  TRY(alloc(h, &h->Zt, (size_t)P.nw * P.nu));
-  TRY(alloc(h, &h->H, (size_t)P.nw * P.nu));
+  TRY(alloc(h, &h->Zt, (size_t)P.nw * h->ldp));
+  TRY(alloc(h, &h->H, (size_t)P.nw * h->ldp));
   TRY(alloc(h, &h->Kred, (size_t)P.nu * P.nu));
   TRY(alloc(h, &h->F, (size_t)P.nu * P.nu));
+  TRY(alloc(h, &h->Fdinv, (size_t)P.nu));
   TRY(alloc(h, &h->st, ST_WORDS));
   TRY(alloc(h, &h->bar, 4));
-  CK(launch_set_identity(0, P.nu, h->Zt, P.nu));
+  CK(launch_set_identity(0, P.nu, h->Zt, h->ldp));
   // launch shapes
   int maxlen = 1;
   for (int i = 0; i < P.nx; ++i) maxlen = std::max(maxlen, P.LU.rp[i + 1] - P.LU.rp[i]);
@@ -217,7 +252,15 @@ int upload_all(opf_handle* h) {
   int mb = lu_refactor_max_blocks(h->lu_threads, (size_t)(h->lu_threads / 32) * maxlen * sizeof(double));
   int need = (P.nx + 7) / 8;
   h->lu_blocks = std::max(1, std::min(mb, need));
-  h->chol_blocks = std::max(1, std::min(chol_max_blocks(), 2 * 152));
+  {
+    const int ntl = (P.nu + 31) / 32;
+    const int need = std::max(1, std::max((ntl - 1) * ntl / 2 * 4, (ntl + 7) / 8));
+    h->chol_blocks = std::max(1, std::min(chol_max_blocks(), std::min(need, 2 * 152)));
+  }
+  h->cs_ksplit_max = std::max(1, trsm_cols_max_blocks());
+  {
+    h->sn_cb = trsm_st_max_cb(P.nx, h->st_cap);
+  }
   CK(cudaDeviceSynchronize());
   return OPF_OK;
 }
@@ -298,24 +341,90 @@ int factor_async(opf_handle* h) {
   CK(launch_gather_map(s, P.Lo.nnz(), h->Ut_map, h->LUval, h->Ut_val));
   CK(launch_gather_map(s, P.Up.nnz(), h->Up_map, h->LUval, h->Up_val));
   CK(launch_gather_map(s, P.Up.nnz(), h->Lt_map, h->LUval, h->Lt_val));
+  CK(launch_fill_stream(s, h->stLo.nslots, h->stLo.slot, h->stLo.src, h->Lo_val, h->inv_diag, 1, h->stLo.bytes_a));
+  CK(launch_fill_stream(s, h->stLo.nslots, h->stLo.slot, h->stLo.src, h->Ut_val, h->inv_diag, 0, h->stLo.bytes_b));
+  CK(launch_fill_stream(s, h->stUp.nslots, h->stUp.slot, h->stUp.src, h->Up_val, h->inv_diag, 0, h->stUp.bytes_a));
+  CK(launch_fill_stream(s, h->stUp.nslots, h->stUp.slot, h->stUp.src, h->Lt_val, h->inv_diag, 1, h->stUp.bytes_b));
   ph_end(h);
   h->have_lu = true;
   return OPF_OK;
 }
 
-// X (perm space, row-major n x ncols) <- (LU)^{-1} X   or (LU)^{-T} X
-int lu_solve_perm(opf_handle* h, int trans, double* X, int ncols, int cb, bool timed = false) {
+// X (perm space, n x ncols, element (i, c) at X[i*xr + c*xc]) <- (LU)^{-1} X or (LU)^{-T} X
+int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols,
+                  bool timed = false) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const double* lov = trans ? h->Ut_val : h->Lo_val;
   const double* upv = trans ? h->Lt_val : h->Up_val;
+  const double* dlo = trans ? h->inv_diag : nullptr;
+  const double* dup = trans ? nullptr : h->inv_diag;
+  const bool cols_ok = ncols >= 32 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max;
+  int mode = (ncols >= 32 && xc == 1) ? h->trsm_mode : 1;
+  if (mode < 0) mode = 32;
+  if (mode == 32 && cols_ok) {
+    const int ncb = (ncols + 31) / 32;
+    const int ksplit = std::max(1, std::min(32, h->cs_ksplit_max / ncb));
+    if (timed) ph_begin(h, OPF_PHASE_TRSM);
+    CK(launch_trsm_cols(s, false, h->csL, h->Lo_ci, lov, dlo, X, xr, ncols, ksplit, h->cs_scratch, h->cs_bar,
+                        h->st, h->spin_limit));
+    if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
+    CK(launch_trsm_cols(s, true, h->csU, h->Up_ci, upv, dup, X, xr, ncols, ksplit, h->cs_scratch, h->cs_bar,
+                        h->st, h->spin_limit));
+    if (timed) ph_end(h);
+    return OPF_OK;
+  }
+  int cb = (mode == 32) ? 1 : std::min(mode, h->sn_cb);
+  if (h->sn_cb == 0) cb = 0;
+  const opf_handle::StBuf& Lb = h->stLo;
+  const opf_handle::StBuf& Ub = h->stUp;
+  const StDev lo{Lb.nchunks, h->st_cap, Lb.chunk_off, Lb.chunk_bytes, Lb.chunk_big_f, Lb.chunk_big_w,
+                 trans ? Lb.bytes_b : Lb.bytes_a, Lb.int_beg, lov, dlo};
+  const StDev up{Ub.nchunks, h->st_cap, Ub.chunk_off, Ub.chunk_bytes, Ub.chunk_big_f, Ub.chunk_big_w,
+                 trans ? Ub.bytes_b : Ub.bytes_a, Ub.int_beg, upv, dup};
   if (timed) ph_begin(h, OPF_PHASE_TRSM);
-  CK(launch_trsm(s, cb, P.fwd.nlev, h->fwd_ptr, h->fwd_rows, h->Lo_rp, h->Lo_ci, lov,
-                 trans ? h->inv_diag : nullptr, X, ncols, ncols));
+  if (cb > 0) CK(launch_trsm_st(s, cb, false, lo, P.nx, X, xr, xc, ncols, h->st, h->spin_limit));
+  else CK(launch_trsm(s, 1, P.fwd.nlev, h->fwd_ptr, h->fwd_rows, h->Lo_rp, h->Lo_ci, lov, dlo, X, xr, xc, ncols));
   if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
-  CK(launch_trsm(s, cb, P.bwd.nlev, h->bwd_ptr, h->bwd_rows, h->Up_rp, h->Up_ci, upv,
-                 trans ? nullptr : h->inv_diag, X, ncols, ncols));
+  if (cb > 0) CK(launch_trsm_st(s, cb, true, up, P.nx, X, xr, xc, ncols, h->st, h->spin_limit));
+  else CK(launch_trsm(s, 1, P.bwd.nlev, h->bwd_ptr, h->bwd_rows, h->Up_rp, h->Up_ci, upv, dup, X, xr, xc, ncols));
   if (timed) ph_end(h);
+  return OPF_OK;
+}
+
+// Pick the fastest multi-RHS solve kernel for this network on the device at hand:
+// each candidate solves the real right-hand side (in the H buffer, which the
+// condensation overwrites afterwards) twice, the second run timed with events.
+int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
+  const Plan& P = h->P;
+  const int nu = P.nu, nx = P.nx;
+  double* trial = h->H + (size_t)nu * ld;
+  const int cands[4] = {32, 1, 2, 4};
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  int pick = 1;
+  for (int k = 0; k < 4; ++k) {
+    const int m = cands[k];
+    if (m != 32 && (h->sn_cb == 0 || m > h->sn_cb)) continue;
+    if (m == 32 && (nu < 32 || (nu + 31) / 32 > h->cs_ncb_max)) continue;
+    h->trsm_mode = m;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaMemcpyAsync(trial, Sx, sizeof(double) * (size_t)nx * ld, cudaMemcpyDeviceToDevice, h->s));
+      CK(cudaEventRecord(a, h->s));
+      TRY(lu_solve_perm(h, 0, trial, ld, 1, nu));
+      CK(cudaEventRecord(b, h->s));
+      CK(cudaEventSynchronize(b));
+      CK(cudaEventElapsedTime(&ms, a, b));
+    }
+    h->tune_ms[0][k] = ms;
+    if (ms < best) { best = ms; pick = m; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->trsm_mode = pick;
   return OPF_OK;
 }
 
@@ -331,27 +440,31 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
                        h->Kval));
   CK(launch_add_diag(s, nw, nu, h->K_diag, h->perm, sig_u, sig_x, h->Kval, h->sig_c));
   ph_end(h);
-  // A6: Z = [I; S_x],  S_x = -(P G_x P^T)^{-1} P G_u   (perm rows)
-  double* Sx = h->Zt + (size_t)nu * nu;
-  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * nu, s));
-  CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, nu));
-  TRY(lu_solve_perm(h, 0, Sx, nu, h->cb, true));
+  // A6: Z = [I; S_x],  S_x = -(P G_x P^T)^{-1} P G_u   (perm rows); Z and H are
+  // row-major with leading dimension ldp (nu rounded up to 32): lanes of a warp
+  // hold consecutive right-hand-side columns
+  const long long ld = h->ldp;
+  double* Sx = h->Zt + (size_t)nu * ld;
+  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s));
+  CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
+  if (h->trsm_mode < 0) TRY(autotune_trsm(h, Sx, ld));
+  TRY(lu_solve_perm(h, 0, Sx, ld, 1, nu, true));
   // A7: H = K Z
   ph_begin(h, OPF_PHASE_SPMM);
-  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, nu, h->H, nu, nu, 1.0, 0.0));
+  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, ld, 1, h->H, ld, 1, nu, 1.0, 0.0));
   ph_end(h);
-  double* Hx = h->H + (size_t)nu * nu;
+  double* Hx = h->H + (size_t)nu * ld;
   if (h->opt.route == OPF_ROUTE_EXPLICIT) {
     ph_begin(h, OPF_PHASE_KRED);
-    CK(launch_dense_tn(s, nu, nx, Sx, Hx, h->H, h->F));
-    CK(launch_symmetrize(s, nu, h->F, h->Kred));
+    CK(launch_dense_tn(s, nu, nx, Sx, Hx, h->H, ld, h->F));
+    CK(launch_symmetrize(s, nu, h->F, nu, 1, h->Kred));
     ph_end(h);
   } else {
     // Psi = G_x^{-T} H_x ; Kred = H_u - G_u^T Psi
-    TRY(lu_solve_perm(h, 1, Hx, nu, h->cb, true));
+    TRY(lu_solve_perm(h, 1, Hx, ld, 1, nu, true));
     ph_begin(h, OPF_PHASE_KRED);
-    CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Hx, nu, h->H, nu, nu, -1.0, 1.0));
-    CK(launch_symmetrize(s, nu, h->H, h->Kred));
+    CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Hx, ld, 1, h->H, ld, 1, nu, -1.0, 1.0));
+    CK(launch_symmetrize(s, nu, h->H, ld, 1, h->Kred));
     ph_end(h);
   }
   h->have_condense = true;
@@ -364,7 +477,7 @@ int factor_kred_async(opf_handle* h, double delta_w) {
   ph_begin(h, OPF_PHASE_CHOL);
   CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
   CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
-  CK(launch_chol(h->s, P.nu, h->F, h->st, h->bar, h->spin_limit, h->chol_blocks));
+  CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, h->chol_blocks));
   ph_end(h);
   h->delta_w = delta_w;
   return OPF_OK;
@@ -391,7 +504,6 @@ int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k) {
   double* Vb = Tm + (size_t)m * k;       // nw x k (rows nu.. used)
   double* Ps = Vb + (size_t)nw * k;      // m x k
   double* Py = Ps + (size_t)m * k;       // m x k
-  const int cbk = pick_cb(k);
   // gather the right-hand side blocks
   CK(launch_permute_rows(s, nw, k, h->c2w, rhs, N, 1, R12, k, 0, 1.0, 0));
   CK(launch_permute_rows(s, m, k, nullptr, rhs + nw, N, 1, R3, k, 0, 1.0, 0));
@@ -399,37 +511,37 @@ int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k) {
   CK(launch_permute_rows(s, m, k, nullptr, rhs + nw + m + nx, N, 1, R5, k, 0, 1.0, 0));
   // T = Sigma_s r5 - r3 ; C = A^T T
   CK(launch_scale_rows(s, m, k, h->sig_s, R5, T, -1.0, R3));
-  CK(launch_spmm(s, nw, h->AT_rp, h->AT_ci, h->Aval, h->AT_map, T, k, C, k, k, 1.0, 0.0));
+  CK(launch_spmm(s, nw, h->AT_rp, h->AT_ci, h->Aval, h->AT_map, T, k, 1, C, k, 1, k, 1.0, 0.0));
   // D0 = [0; q],  q = -G_x^{-1} r4
   CK(cudaMemsetAsync(D0, 0, sizeof(double) * (size_t)nu * k, s));
   CK(launch_axpby(s, (long long)nx * k, -1.0, R4, 0.0, nullptr, D0 + (size_t)nu * k));
-  TRY(lu_solve_perm(h, 0, D0 + (size_t)nu * k, k, cbk));
+  TRY(lu_solve_perm(h, 0, D0 + (size_t)nu * k, k, 1, k));
   // b = [r1; r2] + K D0 + C
   CK(launch_axpby(s, (long long)nw * k, 1.0, R12, 1.0, C, Bv));
-  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, D0, k, Bv, k, k, 1.0, 1.0));
+  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, D0, k, 1, Bv, k, 1, k, 1.0, 1.0));
   // rhs_u = -(b_u - G_u^T G_x^{-T} b_x)
-  TRY(lu_solve_perm(h, 1, Bv + (size_t)nu * k, k, cbk));
-  CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Bv + (size_t)nu * k, k, Bv, k, k, -1.0,
-                 1.0));
+  TRY(lu_solve_perm(h, 1, Bv + (size_t)nu * k, k, 1, k));
+  CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Bv + (size_t)nu * k, k, 1, Bv, k, 1, k,
+                 -1.0, 1.0));
   CK(launch_axpby(s, (long long)nu * k, -1.0, Bv, 0.0, nullptr, Pc));
   // p_u = (L L^T)^{-1} rhs_u
-  CK(launch_chol_solve(s, nu, h->F, Pc, k));
+  CK(launch_chol_solve(s, nu, h->F, h->Fdinv, Pc, k));
   // p_x = -G_x^{-1} (r4 + G_u p_u)
   double* Px = Pc + (size_t)nu * k;
   CK(cudaMemcpyAsync(Px, R4, sizeof(double) * (size_t)nx * k, cudaMemcpyDeviceToDevice, s));
-  CK(launch_spmm(s, nx, h->PGu_rp, h->PGu_ci, h->Gval, h->PGu_map, Pc, k, Px, k, k, 1.0, 1.0));
-  TRY(lu_solve_perm(h, 0, Px, k, cbk));
+  CK(launch_spmm(s, nx, h->PGu_rp, h->PGu_ci, h->Gval, h->PGu_map, Pc, k, 1, Px, k, 1, k, 1.0, 1.0));
+  TRY(lu_solve_perm(h, 0, Px, k, 1, k));
   CK(launch_axpby(s, (long long)nx * k, -1.0, Px, 0.0, nullptr, Px));
   // t = A p + r5 ; p_s = -t ; p_y = Sigma_s t - r3
   CK(cudaMemcpyAsync(Tm, R5, sizeof(double) * (size_t)m * k, cudaMemcpyDeviceToDevice, s));
-  CK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, Pc, k, Tm, k, k, 1.0, 1.0));
+  CK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, Pc, k, 1, Tm, k, 1, k, 1.0, 1.0));
   CK(launch_axpby(s, (long long)m * k, -1.0, Tm, 0.0, nullptr, Ps));
   CK(launch_scale_rows(s, m, k, h->sig_s, Tm, Py, -1.0, R3));
   // p_lambda = -G_x^{-T} (r2 + [K p]_x + C_x)
   double* Vx = Vb + (size_t)nu * k;
   CK(launch_axpby(s, (long long)nx * k, 1.0, R12 + (size_t)nu * k, 1.0, C + (size_t)nu * k, Vx));
-  CK(launch_spmm(s, nx, h->K_rp + nu, h->K_ci, h->Kval, nullptr, Pc, k, Vx, k, k, 1.0, 1.0));
-  TRY(lu_solve_perm(h, 1, Vx, k, cbk));
+  CK(launch_spmm(s, nx, h->K_rp + nu, h->K_ci, h->Kval, nullptr, Pc, k, 1, Vx, k, 1, k, 1.0, 1.0));
+  TRY(lu_solve_perm(h, 1, Vx, k, 1, k));
   // scatter the step back: [p_u | p_x] (c-order), p_s, p_lambda (perm), p_y
   CK(launch_permute_rows(s, nw, k, h->c2w, Pc, k, 0, step, N, 1, 1.0, 1));
   CK(launch_permute_rows(s, m, k, nullptr, Ps, k, 0, step + nw, N, 1, 1.0, 0));
@@ -477,11 +589,12 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return OPF_ERR_INVALID_ARG;
   }
   int cb = h->opt.rhs_block;
-  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 8 && cb != 16 && cb != 32) {
+  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
-  h->cb = cb ? cb : pick_cb(h->P.nu);
+  h->trsm_mode = cb ? cb : -1;
+  h->cb = pick_cb(h->P.nu);
   int rc = upload_all(h);
   if (rc != OPF_OK) {
     opf_destroy(h);
@@ -516,6 +629,14 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
   if (levels_bwd) *levels_bwd = h->P.bwd.nlev;
   if (nnz_k) *nnz_k = h->P.K.nnz();
   if (lu_flops) *lu_flops = h->P.lu_flops;
+  return OPF_OK;
+}
+
+int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (kernel) *kernel = h->trsm_mode;
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = h->tune_ms[0][k];
   return OPF_OK;
 }
 
@@ -618,7 +739,7 @@ int opf_gx_solve(opf_handle* h, int trans, const double* B, double* X, int nrhs)
   double* ws = workspace(h, (size_t)P.nx * nrhs);
   if (!ws) return OPF_ERR_OOM;
   CK(launch_permute_rows(h->s, P.nx, nrhs, h->perm, B, P.nx, 1, ws, nrhs, 0, 1.0, 0));
-  TRY(lu_solve_perm(h, trans ? 1 : 0, ws, nrhs, pick_cb(nrhs)));
+  TRY(lu_solve_perm(h, trans ? 1 : 0, ws, nrhs, 1, nrhs));
   CK(launch_permute_rows(h->s, P.nx, nrhs, h->perm, ws, nrhs, 0, X, P.nx, 1, 1.0, 1));
   CK(cudaStreamSynchronize(h->s));
   return OPF_OK;

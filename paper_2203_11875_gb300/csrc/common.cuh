@@ -89,16 +89,51 @@ cudaError_t launch_assemble_K(cudaStream_t s, long long nnz, const double* W, co
 cudaError_t launch_add_diag(cudaStream_t s, int nw, int nu, const int* K_diag, const int* perm,
                             const double* sig_u, const double* sig_x, double* K, double* sig_c);
 cudaError_t launch_scatter_rows(cudaStream_t s, int nrows, const int* rp, const int* ci,
-                                const int* map, const double* src, double alpha, double* X, int ld);
+                                const int* map, const double* src, double alpha, double* X, long long xr,
+                                long long xc);
 cudaError_t launch_spmm(cudaStream_t s, int nrows, const int* rp, const int* ci, const double* val,
-                        const int* valmap, const double* X, int ldx, double* Y, int ldy, int ncols,
-                        double alpha, double beta);
+                        const int* valmap, const double* X, long long xr, long long xc, double* Y,
+                        long long yr, long long yc, int ncols, double alpha, double beta);
 cudaError_t launch_trsm(cudaStream_t s, int cb, int nlev, const int* lptr, const int* lrows,
                         const int* rp, const int* ci, const double* val, const double* inv_diag,
-                        double* X, int ld, int ncols);
-cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, double* S);
+                        double* X, long long xr, long long xc, int ncols);
+cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, long long ar, long long ac,
+                              double* S);
 cudaError_t launch_dense_tn(cudaStream_t s, int nu, int nx, const double* Sx, const double* Hx,
-                            const double* Hu, double* Kred);
+                            const double* Hu, long long ld, double* Kred);
+
+// Staged supernodal multi-RHS triangular solve (device view of an SnStream with
+// its values filled for one factor).  big supernodes read int_beg / val /
+// inv_diag (NULL = unit diagonal) of the strict pattern in place.
+struct StDev {
+  int nchunks, cap;
+  const long long* chunk_off;
+  const int *chunk_bytes, *chunk_big_f, *chunk_big_w;
+  const unsigned char* bytes;
+  const int* int_beg;
+  const double* val;
+  const double* inv_diag;
+};
+// Solve in place on an n x ncols block, element (i, c) at X[i*xr + c*xc]; upper
+// selects the backward sweep; cb columns per CTA in shared memory.
+cudaError_t launch_trsm_st(cudaStream_t s, int cb, bool upper, const StDev& T, int n, double* X, long long xr,
+                           long long xc, int ncols, int* st, long long spin_limit);
+int trsm_st_max_cb(int n, int cap);
+// Column-parallel multi-RHS triangular solve (device view of a ColSched).
+struct ColDev {
+  int nlev, maxseg;
+  const int *lvl_ptr, *sn_first, *sn_w, *lvl_seg_ptr, *seg_q0, *seg_q1, *seg_row, *row_seg, *row_nseg;
+  const int *ext_beg, *ext_end, *int_beg;
+};
+// X row-major (element (i, c) at X[i*ld + c]); ksplit CTAs per 32 columns, all
+// resident (cooperative launch); scratch holds ncb * maxseg * 32 doubles and bar
+// ncb counters.
+cudaError_t launch_trsm_cols(cudaStream_t s, bool upper, const ColDev& S, const int* ci, const double* val,
+                             const double* inv_diag, double* X, long long ld, int ncols, int ksplit,
+                             double* scratch, unsigned* bar, int* st, long long spin_limit);
+int trsm_cols_max_blocks();
+cudaError_t launch_fill_stream(cudaStream_t s, long long nslots, const long long* slot, const int* src,
+                               const double* vals, const double* inv_diag, int unit, unsigned char* stream);
 
 // LU (A5)
 cudaError_t launch_lu_scatter(cudaStream_t s, long long nnzG, const int* Gx_to_LU, const double* Gval,
@@ -115,10 +150,10 @@ cudaError_t launch_gather_map(cudaStream_t s, long long n, const int* map, const
 
 // dense Cholesky (A9)
 cudaError_t launch_chol_prepare(cudaStream_t s, int n, const double* A, double delta, double* F);
-cudaError_t launch_chol(cudaStream_t s, int n, double* F, int* st, unsigned* bar, long long spin_limit,
-                        int nblocks);
+cudaError_t launch_chol(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* bar,
+                        long long spin_limit, int nblocks);
 int chol_max_blocks();
-cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, double* X, int nrhs);
+cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, const double* dinv, double* X, int nrhs);
 
 // vectors
 cudaError_t launch_permute_rows(cudaStream_t s, int n, int ncols, const int* idx, const double* src,

@@ -37,33 +37,39 @@ __global__ void k_add_diag(int nw, int nu, const int* __restrict__ K_diag, const
   sig_c[c] = s;
 }
 
-// X[i][col] = alpha * src[map[q]] for the entries q of row i (dense X zeroed before)
+// X(i, ci[q]) = alpha * src[map[q]] for the entries q of row i (X zeroed before),
+// element (i, c) at X[i*xr + c*xc]
 __global__ void k_scatter_rows(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                const int* __restrict__ map, const double* __restrict__ src, double alpha,
-                               double* __restrict__ X, int ld) {
+                               double* __restrict__ X, long long xr, long long xc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nrows) return;
-  for (int q = rp[i]; q < rp[i + 1]; ++q) X[(size_t)i * ld + ci[q]] = alpha * src[map ? map[q] : q];
+  for (int q = rp[i]; q < rp[i + 1]; ++q) X[i * xr + ci[q] * xc] = alpha * src[map ? map[q] : q];
 }
 
-// Y = alpha * M X + beta * Y, M CSR, X and Y row-major.  Thread (row, col) with the
-// column fastest, so neighbouring threads read neighbouring X entries.
+// Y = alpha * M X + beta * Y, M CSR; element (i, c) of X at X[i*xr + c*xc] and of
+// Y at Y[i*yr + c*yc].  rows_fast selects the thread order (row index fastest for
+// column-major operands, column index fastest for row-major ones), so
+// neighbouring threads touch neighbouring addresses of Y.
 __global__ void k_spmm(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                        const double* __restrict__ val, const int* __restrict__ valmap,
-                       const double* __restrict__ X, int ldx, double* __restrict__ Y, int ldy, int ncols,
-                       double alpha, double beta) {
+                       const double* __restrict__ X, long long xr, long long xc, double* __restrict__ Y,
+                       long long yr, long long yc, int ncols, double alpha, double beta, int rows_fast) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long total = (long long)nrows * ncols;
   if (t >= total) return;
-  int r = int(t / ncols), c = int(t % ncols);
+  int r, c;
+  if (rows_fast) { r = int(t % nrows); c = int(t / nrows); }
+  else { r = int(t / ncols); c = int(t % ncols); }
+  const double* Xc = X + c * xc;
   double acc = 0.0;
   const int e = rp[r + 1];
   if (valmap) {
-    for (int q = rp[r]; q < e; ++q) acc = fma(val[valmap[q]], X[(size_t)ci[q] * ldx + c], acc);
+    for (int q = rp[r]; q < e; ++q) acc = fma(val[valmap[q]], Xc[ci[q] * xr], acc);
   } else {
-    for (int q = rp[r]; q < e; ++q) acc = fma(val[q], X[(size_t)ci[q] * ldx + c], acc);
+    for (int q = rp[r]; q < e; ++q) acc = fma(val[q], Xc[ci[q] * xr], acc);
   }
-  double* y = Y + (size_t)r * ldy + c;
+  double* y = Y + r * yr + c * yc;
   *y = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *y);
 }
 
@@ -77,41 +83,45 @@ template <int CB>
 __global__ void __launch_bounds__(256) k_trsm(int nlev, const int* __restrict__ lptr,
                                               const int* __restrict__ lrows, const int* __restrict__ rp,
                                               const int* __restrict__ ci, const double* __restrict__ val,
-                                              const double* __restrict__ inv_diag, double* X, int ld,
-                                              int ncols) {
+                                              const double* __restrict__ inv_diag, double* X,
+                                              long long xr, long long xc, int ncols) {
   const int c = blockIdx.x * CB + (threadIdx.x % CB);
   const int slot = threadIdx.x / CB;
   const int nslots = blockDim.x / CB;
   const bool active = c < ncols;
-  double* Xc = X + c;
+  double* Xc = X + c * xc;
   for (int lev = 0; lev < nlev; ++lev) {
     const int beg = lptr[lev], end = lptr[lev + 1];
     if (active) {
       for (int t = beg + slot; t < end; t += nslots) {
         const int i = lrows[t];
-        double acc = Xc[(size_t)i * ld];
+        double acc = Xc[i * xr];
         const int qe = rp[i + 1];
-        for (int q = rp[i]; q < qe; ++q) acc = fma(-val[q], Xc[(size_t)ci[q] * ld], acc);
+        for (int q = rp[i]; q < qe; ++q) acc = fma(-val[q], Xc[ci[q] * xr], acc);
         if (inv_diag) acc *= inv_diag[i];
-        Xc[(size_t)i * ld] = acc;
+        Xc[i * xr] = acc;
       }
     }
     __syncthreads();
   }
 }
 
-__global__ void k_symmetrize(int n, const double* __restrict__ A, double* __restrict__ S) {
+// S (n x n, symmetric) = (A + A^T) / 2, element (i, j) of A at A[i*ar + j*ac]
+__global__ void k_symmetrize(int n, const double* __restrict__ A, long long ar, long long ac,
+                             double* __restrict__ S) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)n * n) return;
   int i = int(t / n), j = int(t % n);
-  S[t] = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+  S[t] = 0.5 * (A[i * ar + j * ac] + A[j * ar + i * ac]);
 }
 
-// Kred = Hu + Sx^T Hx (explicit route): C[a][c] = Hu[a][c] + sum_j Sx[j][a] Hx[j][c],
-// 64x64 output tiles, 16-deep k slices staged in shared memory, 4x4 per thread.
+// Kred = Hu + Sx^T Hx (explicit route): C[a][c] = Hu(a, c) + sum_j Sx(j, a) Hx(j, c),
+// operands row-major with leading dimension ld; 64x64 output tiles, 16-deep
+// k slices staged in shared memory, 4x4 outputs per thread.
 __global__ void __launch_bounds__(256) k_dense_tn(int nu, int nx, const double* __restrict__ Sx,
                                                   const double* __restrict__ Hx,
-                                                  const double* __restrict__ Hu, double* __restrict__ C) {
+                                                  const double* __restrict__ Hu, long long ld,
+                                                  double* __restrict__ C) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
   const int a0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
@@ -121,8 +131,8 @@ __global__ void __launch_bounds__(256) k_dense_tn(int nu, int nx, const double* 
     for (int t = threadIdx.x; t < 16 * 64; t += 256) {
       int kk = t / 64, j = t % 64;
       int k = k0 + kk;
-      As[kk][j] = (k < nx && a0 + j < nu) ? Sx[(size_t)k * nu + a0 + j] : 0.0;
-      Bs[kk][j] = (k < nx && c0 + j < nu) ? Hx[(size_t)k * nu + c0 + j] : 0.0;
+      As[kk][j] = (k < nx && a0 + j < nu) ? Sx[k * ld + a0 + j] : 0.0;
+      Bs[kk][j] = (k < nx && c0 + j < nu) ? Hx[k * ld + c0 + j] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -142,7 +152,7 @@ __global__ void __launch_bounds__(256) k_dense_tn(int nu, int nx, const double* 
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int a = a0 + ty * 4 + u, c = c0 + tx * 4 + v;
-      if (a < nu && c < nu) C[(size_t)a * nu + c] = Hu[(size_t)a * nu + c] + acc[u][v];
+      if (a < nu && c < nu) C[(size_t)a * nu + c] = Hu[a * ld + c] + acc[u][v];
     }
 }
 
@@ -243,130 +253,153 @@ __global__ void k_chol_prepare(int n, const double* __restrict__ A, double delta
   F[t] = j > i ? 0.0 : (i == j ? A[t] + delta : A[t]);
 }
 
+// 1/sqrt(d) by Newton-Raphson on f(x) = x^-2 - d (x <- x (3 - d x^2) / 2), seeded
+// with the single-precision hardware estimate; two steps take the ~23-bit seed
+// to double precision.  Pivots outside the single-precision exponent range use
+// the library square root.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double x = (double)rsqrtf((float)d);
+  x = x * fma(-0.5 * d, x * x, 1.5);
+  x = x * fma(-0.5 * d, x * x, 1.5);
+  return x;
+}
+
+// Block-wide right-looking Cholesky of the 32x32 tile T (kb valid rows); writes
+// 1/L(j,j) to dv[j].  Returns the first failing local column or -1.  The FP64
+// work of each rank-1 update is spread over all warps (all four SM sub-partition
+// FP64 units).
+__device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, int* failsh) {
+  const int tid = threadIdx.x;
+  if (tid == 0) *failsh = -1;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      const double d = T[j][j];
+      if (!(d > 0.0 && isfinite(d))) *failsh = j;
+      else {
+        const double x = rsqrt_nr(d);
+        T[j][j] = d * x;
+        dv[j] = x;
+      }
+    }
+    __syncthreads();
+    if (*failsh >= 0) return *failsh;
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) T[i][j] *= dv[j];
+    __syncthreads();
+    const int rem = kb - j - 1;
+    for (int t = tid; t < rem * (rem + 1) / 2; t += blockDim.x) {
+      int i = int((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int l = t - i * (i + 1) / 2;
+      T[j + 1 + i][j + 1 + l] = fma(-T[j + 1 + i][j], T[j + 1 + l][j], T[j + 1 + i][j + 1 + l]);
+    }
+    __syncthreads();
+  }
+  return -1;
+}
+
 // Right-looking blocked Cholesky of the lower triangle of F (row-major n x n),
-// 32x32 tiles, one persistent cooperative grid; phases (diagonal tile, panel,
-// trailing update) are separated by a bounded grid barrier.  A non-positive or
-// non-finite pivot records DEV_NOT_PD with its column and ends the kernel.
-__global__ void __launch_bounds__(256) k_chol(double* F, int n, int* st, unsigned* bar,
+// 32x32 tiles, one persistent cooperative grid, two phases per block column
+// separated by a bounded grid barrier:
+//   P. each block that owns panel tiles factors the diagonal tile itself
+//      (block-wide, in shared memory; the owner of the diagonal writes it back),
+//      then solves its tiles X L_kk^T = A_ik (four rows per warp, one column per
+//      lane) -- no barrier between the diagonal and the panel;
+//   U. the trailing update A_ij -= L_ik L_jk^T in 16x16 sub-tiles.
+// A non-positive or non-finite pivot records DEV_NOT_PD with its column.  The
+// inverse diagonal of L is written to dinv (used by the solves).
+__global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out, int* st, unsigned* bar,
                                               long long spin_limit) {
   __shared__ double Ta[CNB][CNB + 1];
   __shared__ double Tb[CNB][CNB + 1];
-  __shared__ double dinv[CNB];
-  __shared__ int okflag;
-  const int tid = threadIdx.x;
+  __shared__ double dv[CNB];
+  __shared__ int failsh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = (n + CNB - 1) / CNB;
   const unsigned nbk = gridDim.x;
   volatile int* vst = st;
   for (int k = 0; k < nt; ++k) {
     const int k0 = k * CNB, kb = min(CNB, n - k0);
-    // ---- phase 1: factor the diagonal tile
-    if (blockIdx.x == 0) {
+    const int npan = nt - k;   // tile rows k..nt-1; row k is the diagonal
+    // ---- phase P
+    if ((int)blockIdx.x < npan) {
       for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-        int i = t / CNB, j = t % CNB;
+        const int i = t / CNB, j = t % CNB;
         Ta[i][j] = (i < kb && j <= i) ? F[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
       }
       __syncthreads();
-      for (int j = 0; j < kb; ++j) {
-        if (tid == 0) {
-          double d = Ta[j][j];
-          okflag = (d > 0.0 && isfinite(d));
-          if (okflag) { d = sqrt(d); Ta[j][j] = d; dinv[j] = 1.0 / d; }
-          else set_status(st, DEV_NOT_PD, k0 + j);
+      const int fail = block_chol_tile(Ta, dv, kb, &failsh);
+      if (fail >= 0) {
+        if (tid == 0) set_status(st, DEV_NOT_PD, k0 + fail);
+      } else {
+        if (blockIdx.x == 0) {
+          for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+            const int i = t / CNB, j = t % CNB;
+            if (i < kb && j <= i) F[(size_t)(k0 + i) * n + k0 + j] = Ta[i][j];
+          }
+          if (tid < kb) dinv_out[k0 + tid] = dv[tid];
         }
-        __syncthreads();
-        if (!okflag) break;
-        for (int i = j + 1 + tid; i < kb; i += blockDim.x) Ta[i][j] *= dinv[j];
-        __syncthreads();
-        const int rem = kb - j - 1;
-        for (int t = tid; t < rem * rem; t += blockDim.x) {
-          int i = j + 1 + t / rem, l = j + 1 + t % rem;
-          if (l <= i) Ta[i][l] = fma(-Ta[i][j], Ta[l][j], Ta[i][l]);
+        for (int pt = 1 + blockIdx.x; pt < npan; pt += nbk) {
+          const int i0 = (k + pt) * CNB, ib = min(CNB, n - i0);
+          for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+            const int i = t / CNB, j = t % CNB;
+            Tb[i][j] = (i < ib && j < kb) ? F[(size_t)(i0 + i) * n + k0 + j] : 0.0;
+          }
+          __syncthreads();
+          double a[4];
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) a[rr] = Tb[warp * 4 + rr][lane];
+          for (int j = 0; j < kb; ++j) {
+            const double ljl = Ta[lane][j];
+            const double inv = dv[j];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+              const double xj = __shfl_sync(0xffffffffu, a[rr], j) * inv;
+              if (lane == j) a[rr] = xj;
+              else if (lane > j) a[rr] = fma(-xj, ljl, a[rr]);
+            }
+          }
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const int i = warp * 4 + rr;
+            if (i < ib && lane < kb) F[(size_t)(i0 + i) * n + k0 + lane] = a[rr];
+          }
+          __syncthreads();
         }
-        __syncthreads();
-      }
-      for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-        int i = t / CNB, j = t % CNB;
-        if (i < kb && j <= i) F[(size_t)(k0 + i) * n + k0 + j] = Ta[i][j];
       }
     }
     if (!grid_barrier(bar, nbk, spin_limit, st)) return;
     if (vst[ST_CODE] != 0) return;
-    // ---- phase 2: panel  L_ik = A_ik L_kk^{-T}
-    if (k + 1 < nt) {
-      bool loaded = false;
-      for (int ti = k + 1 + blockIdx.x; ti < nt; ti += nbk) {
-        if (!loaded) {
-          for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-            int i = t / CNB, j = t % CNB;
-            Ta[i][j] = (i < kb && j <= i) ? F[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
-          }
-          __syncthreads();
-          if (tid < CNB) dinv[tid] = 1.0 / Ta[tid][tid];
-          loaded = true;
-        }
-        const int i0 = ti * CNB, ib = min(CNB, n - i0);
-        for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-          int i = t / CNB, j = t % CNB;
-          Tb[i][j] = (i < ib && j < kb) ? F[(size_t)(i0 + i) * n + k0 + j] : 0.0;
-        }
-        __syncthreads();
-        // each warp solves 4 rows; lane l holds column l of its row
-        const int warp = tid >> 5, lane = tid & 31;
-        double a[4];
-#pragma unroll
-        for (int rr = 0; rr < 4; ++rr) a[rr] = Tb[warp * 4 + rr][lane];
-        for (int j = 0; j < kb; ++j) {
-          const double ljl = Ta[lane][j];
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr) {
-            double xj = __shfl_sync(0xffffffffu, a[rr], j) * dinv[j];
-            if (lane == j) a[rr] = xj;
-            else if (lane > j) a[rr] = fma(-xj, ljl, a[rr]);
-          }
-        }
-#pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          int i = warp * 4 + rr;
-          if (i < ib && lane < kb) F[(size_t)(i0 + i) * n + k0 + lane] = a[rr];
-        }
-        __syncthreads();
-      }
-    }
-    if (!grid_barrier(bar, nbk, spin_limit, st)) return;
-    // ---- phase 3: trailing update  A_ij -= L_ik L_jk^T,  k < j <= i
+    // ---- phase U: 16x16 sub-tiles of the lower trailing tiles
     const int m = nt - k - 1;
-    const long long ntile = (long long)m * (m + 1) / 2;
-    for (long long tt = blockIdx.x; tt < ntile; tt += nbk) {
-      int ii = int((sqrt(8.0 * (double)tt + 1.0) - 1.0) * 0.5);
-      while ((long long)(ii + 1) * (ii + 2) / 2 <= tt) ++ii;
-      while ((long long)ii * (ii + 1) / 2 > tt) --ii;
-      const int jj = int(tt - (long long)ii * (ii + 1) / 2);
-      const int ti = k + 1 + ii, tj = k + 1 + jj;
-      const int i0 = ti * CNB, j0 = tj * CNB;
-      const int ib = min(CNB, n - i0), jb = min(CNB, n - j0);
-      for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-        int i = t / CNB, j = t % CNB;
-        Ta[i][j] = (i < ib && j < kb) ? F[(size_t)(i0 + i) * n + k0 + j] : 0.0;
-        Tb[i][j] = (i < jb && j < kb) ? F[(size_t)(j0 + i) * n + k0 + j] : 0.0;
+    const long long nsub = (long long)m * (m + 1) / 2 * 4;
+    for (long long tt = blockIdx.x; tt < nsub; tt += nbk) {
+      const long long tile = tt >> 2;
+      const int sub = int(tt & 3);
+      int ii = int((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+      while ((long long)(ii + 1) * (ii + 2) / 2 <= tile) ++ii;
+      while ((long long)ii * (ii + 1) / 2 > tile) --ii;
+      const int jj = int(tile - (long long)ii * (ii + 1) / 2);
+      if (ii == jj && sub == 1) continue;   // strictly upper quarter of a diagonal tile
+      const int i0 = (k + 1 + ii) * CNB + (sub >> 1) * 16;
+      const int j0 = (k + 1 + jj) * CNB + (sub & 1) * 16;
+      for (int t = tid; t < 16 * CNB; t += blockDim.x) {
+        const int rr = t / CNB, l = t % CNB;
+        Ta[rr][l] = (i0 + rr < n && l < kb) ? F[(size_t)(i0 + rr) * n + k0 + l] : 0.0;
+        Tb[rr][l] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : 0.0;
       }
       __syncthreads();
-      const int r0 = (tid >> 4) * 2, c0 = (tid & 15) * 2;
-      double acc[2][2] = {};
-#pragma unroll 8
-      for (int l = 0; l < CNB; ++l) {
-        double a0 = Ta[r0][l], a1 = Ta[r0 + 1][l], b0 = Tb[c0][l], b1 = Tb[c0 + 1][l];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
+      const int rr = tid >> 4, cc = tid & 15;
+      double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+      for (int l = 0; l < CNB; l += 2) {
+        acc0 = fma(Ta[rr][l], Tb[cc][l], acc0);
+        acc1 = fma(Ta[rr][l + 1], Tb[cc][l + 1], acc1);
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          int gi = i0 + r0 + u, gj = j0 + c0 + v;
-          if (r0 + u < ib && c0 + v < jb && gj <= gi) F[(size_t)gi * n + gj] -= acc[u][v];
-        }
+      const int gi = i0 + rr, gj = j0 + cc;
+      if (gi < n && gj < n && gj <= gi) F[(size_t)gi * n + gj] -= acc0 + acc1;
       __syncthreads();
     }
     if (!grid_barrier(bar, nbk, spin_limit, st)) return;
@@ -376,8 +409,8 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, int* st, unsigne
 // Solve L L^T X = B for the columns of X (row-major n x nrhs); one CTA per column.
 // Forward: 32-row tiles, x_I = L_II^{-1}(b_I - L_I,<I x_<I), the GEMV part with warps
 // over rows and lanes over columns of L; backward mirrors it with L^T.
-__global__ void __launch_bounds__(256) k_chol_solve(int n, const double* __restrict__ F, double* X,
-                                                    int nrhs) {
+__global__ void __launch_bounds__(256) k_chol_solve(int n, const double* __restrict__ F,
+                                                    const double* __restrict__ dinv, double* X, int nrhs) {
   extern __shared__ double xs[];   // n entries: the column being solved
   __shared__ double part[8][CNB];
   const int col = blockIdx.x;
@@ -400,7 +433,7 @@ __global__ void __launch_bounds__(256) k_chol_solve(int n, const double* __restr
     if (warp == 0) {
       double xv = lane < ib ? xs[i0 + lane] : 0.0;
       for (int j = 0; j < ib; ++j) {
-        double xj = __shfl_sync(0xffffffffu, xv, j) / F[(size_t)(i0 + j) * n + i0 + j];
+        double xj = __shfl_sync(0xffffffffu, xv, j) * dinv[i0 + j];
         if (lane == j) xv = xj;
         else if (lane > j && lane < ib) xv = fma(-xj, F[(size_t)(i0 + lane) * n + i0 + j], xv);
       }
@@ -422,7 +455,7 @@ __global__ void __launch_bounds__(256) k_chol_solve(int n, const double* __restr
       for (int w2 = 0; w2 < 8; ++w2) s += part[w2][lane];
       double xv = lane < ib ? xs[i0 + lane] - s : 0.0;
       for (int j = ib - 1; j >= 0; --j) {
-        double xj = __shfl_sync(0xffffffffu, xv, j) / F[(size_t)(i0 + j) * n + i0 + j];
+        double xj = __shfl_sync(0xffffffffu, xv, j) * dinv[i0 + j];
         if (lane == j) xv = xj;
         else if (lane < j) xv = fma(-xj, F[(size_t)(i0 + j) * n + i0 + lane], xv);
       }
@@ -485,11 +518,12 @@ __global__ void k_fill(long long n, double v, double* __restrict__ x) {
   if (t < n) x[t] = v;
 }
 
+// identity in the leading n x n block of a column-major X with leading dimension ld
 __global__ void k_set_identity(int n, double* __restrict__ X, int ld) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)n * n) return;
-  int i = int(t / n), j = int(t % n);
-  X[(size_t)i * ld + j] = i == j ? 1.0 : 0.0;
+  int i = int(t % n), j = int(t / n);
+  X[(size_t)j * ld + i] = i == j ? 1.0 : 0.0;
 }
 
 }  // namespace
@@ -509,29 +543,31 @@ cudaError_t launch_add_diag(cudaStream_t s, int nw, int nu, const int* K_diag, c
   return cudaGetLastError();
 }
 cudaError_t launch_scatter_rows(cudaStream_t s, int nrows, const int* rp, const int* ci, const int* map,
-                                const double* src, double alpha, double* X, int ld) {
+                                const double* src, double alpha, double* X, long long xr, long long xc) {
   if (nrows <= 0) return cudaSuccess;
-  k_scatter_rows<<<nblk(nrows, 256), 256, 0, s>>>(nrows, rp, ci, map, src, alpha, X, ld);
+  k_scatter_rows<<<nblk(nrows, 256), 256, 0, s>>>(nrows, rp, ci, map, src, alpha, X, xr, xc);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_spmm(cudaStream_t s, int nrows, const int* rp, const int* ci, const double* val,
-                        const int* valmap, const double* X, int ldx, double* Y, int ldy, int ncols,
-                        double alpha, double beta) {
+                        const int* valmap, const double* X, long long xr, long long xc, double* Y,
+                        long long yr, long long yc, int ncols, double alpha, double beta) {
   long long total = (long long)nrows * ncols;
   if (total <= 0) return cudaSuccess;
-  k_spmm<<<nblk(total, 256), 256, 0, s>>>(nrows, rp, ci, val, valmap, X, ldx, Y, ldy, ncols, alpha, beta);
+  const int rows_fast = yr == 1 ? 1 : 0;
+  k_spmm<<<nblk(total, 256), 256, 0, s>>>(nrows, rp, ci, val, valmap, X, xr, xc, Y, yr, yc, ncols, alpha,
+                                          beta, rows_fast);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_trsm(cudaStream_t s, int cb, int nlev, const int* lptr, const int* lrows, const int* rp,
-                        const int* ci, const double* val, const double* inv_diag, double* X, int ld,
-                        int ncols) {
+                        const int* ci, const double* val, const double* inv_diag, double* X, long long xr,
+                        long long xc, int ncols) {
   if (ncols <= 0 || nlev <= 0) return cudaSuccess;
   const int T = 256;
 #define TRSM_CASE(CBV)                                                                           \
   case CBV:                                                                                      \
-    k_trsm<CBV><<<nblk(ncols, CBV), T, 0, s>>>(nlev, lptr, lrows, rp, ci, val, inv_diag, X, ld, ncols); \
+    k_trsm<CBV><<<nblk(ncols, CBV), T, 0, s>>>(nlev, lptr, lrows, rp, ci, val, inv_diag, X, xr, xc, ncols); \
     break;
   switch (cb) {
     TRSM_CASE(1) TRSM_CASE(2) TRSM_CASE(4) TRSM_CASE(8) TRSM_CASE(16) TRSM_CASE(32)
@@ -541,15 +577,16 @@ cudaError_t launch_trsm(cudaStream_t s, int cb, int nlev, const int* lptr, const
   note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, double* S) {
-  k_symmetrize<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, A, S);
+cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, long long ar, long long ac,
+                              double* S) {
+  k_symmetrize<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, A, ar, ac, S);
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_dense_tn(cudaStream_t s, int nu, int nx, const double* Sx, const double* Hx,
-                            const double* Hu, double* Kred) {
+                            const double* Hu, long long ld, double* Kred) {
   dim3 grid(nblk(nu, 64), nblk(nu, 64));
-  k_dense_tn<<<grid, 256, 0, s>>>(nu, nx, Sx, Hx, Hu, Kred);
+  k_dense_tn<<<grid, 256, 0, s>>>(nu, nx, Sx, Hx, Hu, ld, Kred);
   note_launch();
   return cudaGetLastError();
 }
@@ -603,20 +640,20 @@ int chol_max_blocks() {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol, 256, 0);
   return sms * (per > 0 ? per : 1);
 }
-cudaError_t launch_chol(cudaStream_t s, int n, double* F, int* st, unsigned* bar, long long spin_limit,
-                        int nblocks) {
-  void* args[] = {&F, &n, &st, &bar, &spin_limit};
+cudaError_t launch_chol(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* bar,
+                        long long spin_limit, int nblocks) {
+  void* args[] = {&F, &n, &dinv, &st, &bar, &spin_limit};
   note_launch();
   return cudaLaunchCooperativeKernel((void*)k_chol, dim3(nblocks), dim3(256), args, 0, s);
 }
-cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, double* X, int nrhs) {
+cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, const double* dinv, double* X, int nrhs) {
   if (nrhs <= 0) return cudaSuccess;
   size_t sm = (size_t)n * sizeof(double);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
   }
-  k_chol_solve<<<nrhs, 256, sm, s>>>(n, F, X, nrhs);
+  k_chol_solve<<<nrhs, 256, sm, s>>>(n, F, dinv, X, nrhs);
   note_launch();
   return cudaGetLastError();
 }

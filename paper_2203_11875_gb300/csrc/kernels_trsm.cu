@@ -1,0 +1,550 @@
+// A6: supernodal multi-right-hand-side triangular solves with the factors of
+// P G_x P^T = L U (Sec. 3.3: G_x^{-1} b = Q U^{-1} L^{-1} P b, applied to all nu
+// columns of G_u, and the transposed solves of the adjoint route).
+//
+// Each CTA owns cb right-hand-side columns and keeps them in shared memory for
+// the whole solve, so no CTA ever waits for another.  Rows are grouped into
+// fundamental supernodes (runs of rows with a dense diagonal block -- the
+// (theta, Vm) pair of a bus, and the separator chains of the ordering); the
+// supernodes are level-scheduled and packed, in level order, into a byte stream
+// of chunks (plan.h, SnStream).  The CTA streams that data through two
+// shared-memory buffers with cp.async.bulk (the TMA bulk-copy engine), issuing
+// chunk c+1 while it works on chunk c, so that after the first chunk every
+// operand comes from shared memory.  Per chunk:
+//   A. every row subtracts its external entries (columns of earlier levels):
+//      ga lanes per row, shuffle reduction;
+//   B. every supernode sweeps its packed dense diagonal triangle with one lane
+//      per row and one shuffle broadcast per column, warp-synchronous.
+// Supernodes wider than 32 rows sweep 32-column panels with the whole CTA,
+// reading their diagonal block from the factor in place.
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace condipm {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int TRSM_THREADS = 512;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
+}
+
+// thread 0: stage chunk bytes [src, src+bytes) into dst, completion on bar
+__device__ __forceinline__ void stage_chunk(void* dst, const void* src, int bytes, uint64_t* bar) {
+  const uint32_t b = smem_addr(bar);
+  if (bytes > 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(b)
+        : "memory");
+  } else {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+  }
+}
+
+// bounded wait for the given phase parity; false when the limit expires
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  const uint32_t b = smem_addr(bar);
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int CB>
+__device__ __forceinline__ void chunk_phase_a(const unsigned char* B, double* Xs) {
+  const int* hdr = reinterpret_cast<const int*>(B);
+  const int nA = hdr[0], ga = hdr[4];
+  const int* Aptr = reinterpret_cast<const int*>(B + hdr[8]);
+  const int* Arow = reinterpret_cast<const int*>(B + hdr[9]);
+  const int* Eci = reinterpret_cast<const int*>(B + hdr[10]);
+  const double* Eval = reinterpret_cast<const double*>(B + hdr[11]);
+  const int tid = threadIdx.x;
+  const int grp = tid / ga, lig = tid % ga, ngrp = blockDim.x / ga;
+  for (int base = 0; base < nA; base += ngrp) {
+    const int t = base + grp;
+    double part[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) part[c] = 0.0;
+    int r = -1;
+    if (t < nA) {
+      r = Arow[t];
+      const int qe = Aptr[t + 1];
+      for (int q = Aptr[t] + lig; q < qe; q += ga) {
+        const double v = Eval[q];
+        const int j = Eci[q];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) part[c] = fma(v, Xs[j * CB + c], part[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      for (int o = ga >> 1; o > 0; o >>= 1) part[c] += __shfl_xor_sync(FULL, part[c], o, ga);
+    if (lig == 0 && r >= 0) {
+#pragma unroll
+      for (int c = 0; c < CB; ++c) Xs[r * CB + c] -= part[c];
+    }
+  }
+}
+
+// narrow supernodes (width <= 4): one lane sweeps a whole supernode, so every
+// FP64 instruction of the sweep has all its lanes busy
+template <int CB, bool UPPER>
+__device__ __forceinline__ void chunk_phase_b_narrow(const unsigned char* B, double* Xs) {
+  const int* hdr = reinterpret_cast<const int*>(B);
+  const int nB = hdr[1];
+  const int* Bf = reinterpret_cast<const int*>(B + hdr[12]);
+  const int* Bw = reinterpret_cast<const int*>(B + hdr[13]);
+  const int* Biptr = reinterpret_cast<const int*>(B + hdr[14]);
+  const int* Bdptr = reinterpret_cast<const int*>(B + hdr[15]);
+  const double* Ival = reinterpret_cast<const double*>(B + hdr[16]);
+  const double* Bd = reinterpret_cast<const double*>(B + hdr[17]);
+  for (int s = threadIdx.x; s < nB; s += blockDim.x) {
+    const int f = Bf[s], w = Bw[s];
+    const double* tri = Ival + Biptr[s];
+    const double* dg = Bd + Bdptr[s];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      double a[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = i < w ? Xs[(f + i) * CB + c] : 0.0;
+      if (!UPPER) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (t < w) {
+            a[t] *= dg[t];
+#pragma unroll
+            for (int i = t + 1; i < 4; ++i)
+              if (i < w) a[i] = fma(-tri[i * (i - 1) / 2 + t], a[t], a[i]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int tt = 0; tt < 4; ++tt) {
+          const int t = 3 - tt;
+          if (t < w) {
+            a[t] *= dg[t];
+#pragma unroll
+            for (int i = 0; i < t; ++i) a[i] = fma(-tri[i * (w - 1) - i * (i - 1) / 2 + (t - i - 1)], a[t], a[i]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < w) Xs[(f + i) * CB + c] = a[i];
+    }
+  }
+}
+
+template <int CB, bool UPPER, int LV>
+__device__ __forceinline__ void chunk_phase_b(const unsigned char* B, double* Xs) {
+  const int* hdr = reinterpret_cast<const int*>(B);
+  const int nB = hdr[1], gs = hdr[5], wmax = hdr[6];
+  const int* Bf = reinterpret_cast<const int*>(B + hdr[12]);
+  const int* Bw = reinterpret_cast<const int*>(B + hdr[13]);
+  const int* Biptr = reinterpret_cast<const int*>(B + hdr[14]);
+  const int* Bdptr = reinterpret_cast<const int*>(B + hdr[15]);
+  const double* Ival = reinterpret_cast<const double*>(B + hdr[16]);
+  const double* Bd = reinterpret_cast<const double*>(B + hdr[17]);
+  const int tid = threadIdx.x;
+  const int grp = tid / gs, lig = tid % gs, ngrp = blockDim.x / gs;
+  for (int base = 0; base < nB; base += ngrp) {
+    const int s = base + grp;
+    const bool act = s < nB;
+    const int f = act ? Bf[s] : 0;
+    const int w = act ? Bw[s] : 0;
+    const bool own = lig < w;
+    const int r = f + lig;
+    const double* tri = Ival + (act ? Biptr[s] : 0) +
+                        (UPPER ? (lig * (w - 1) - lig * (lig - 1) / 2) : (lig * (lig - 1) / 2));
+    double lv[LV];
+#pragma unroll
+    for (int t = 0; t < LV; ++t) {
+      if (!UPPER) lv[t] = (own && t < lig) ? tri[t] : 0.0;
+      else lv[t] = (own && t > lig && t < w) ? tri[t - lig - 1] : 0.0;
+    }
+    double acc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) acc[c] = own ? Xs[r * CB + c] : 0.0;
+    const double dinv = own ? Bd[Bdptr[s] + lig] : 1.0;
+#pragma unroll
+    for (int tt = 0; tt < LV; ++tt) {
+      const int t = UPPER ? LV - 1 - tt : tt;
+      if (t < wmax) {
+        if (own && lig == t) {
+#pragma unroll
+          for (int c = 0; c < CB; ++c) { acc[c] *= dinv; Xs[r * CB + c] = acc[c]; }
+        }
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          const double xt = __shfl_sync(FULL, acc[c], t, gs);
+          if (own && (UPPER ? lig < t : lig > t)) acc[c] = fma(-lv[t], xt, acc[c]);
+        }
+      }
+    }
+  }
+}
+
+// supernode wider than 32 rows: 32-column panels with the whole CTA, diagonal
+// block read from the factor (int_beg / val / inv_diag of the solve)
+template <int CB, bool UPPER>
+__device__ __forceinline__ void big_supernode(const StDev& T, int f, int w, double* Xs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int npan = (w + 31) / 32;
+  for (int pi = 0; pi < npan; ++pi) {
+    const int p0 = UPPER ? max(0, w - 32 * (pi + 1)) : 32 * pi;
+    const int pe = UPPER ? w - 32 * pi : min(w, 32 * (pi + 1));
+    const int pw = pe - p0;
+    if (warp == 0) {
+      const bool own = lane < pw;
+      const int r = f + p0 + lane;
+      double lv[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        if (!UPPER) lv[t] = (own && t < lane) ? T.val[T.int_beg[r] + p0 + t] : 0.0;
+        else lv[t] = (own && t > lane && t < pw) ? T.val[T.int_beg[r] + (t - lane - 1)] : 0.0;
+      }
+      double acc[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) acc[c] = own ? Xs[r * CB + c] : 0.0;
+      const double dinv = (own && T.inv_diag) ? T.inv_diag[r] : 1.0;
+#pragma unroll
+      for (int tt = 0; tt < 32; ++tt) {
+        const int t = UPPER ? 31 - tt : tt;
+        if (t < pw) {
+          if (own && lane == t) {
+#pragma unroll
+            for (int c = 0; c < CB; ++c) { acc[c] *= dinv; Xs[r * CB + c] = acc[c]; }
+          }
+#pragma unroll
+          for (int c = 0; c < CB; ++c) {
+            const double xt = __shfl_sync(FULL, acc[c], t);
+            if (own && (UPPER ? lane < t : lane > t)) acc[c] = fma(-lv[t], xt, acc[c]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int rb = UPPER ? 0 : pe, re = UPPER ? p0 : w;
+    for (int ri = rb + warp; ri < re; ri += nwarps) {
+      const int r = f + ri;
+      const bool on = lane < pw;
+      const double v = on ? (UPPER ? T.val[T.int_beg[r] + (p0 + lane - ri - 1)] : T.val[T.int_beg[r] + p0 + lane])
+                          : 0.0;
+      double part[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        part[c] = on ? v * Xs[(f + p0 + lane) * CB + c] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_xor_sync(FULL, part[c], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c) Xs[r * CB + c] -= part[c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int CB, bool UPPER>
+__global__ void __launch_bounds__(TRSM_THREADS) k_trsm_st(StDev T, int n, double* X, long long xr, long long xc,
+                                                          int ncols, int* st, long long spin_limit) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* Xs = reinterpret_cast<double*>(smem);
+  const size_t xs_bytes = ((size_t)n * CB * sizeof(double) + 15) & ~size_t(15);
+  unsigned char* buf0 = smem + xs_bytes;
+  unsigned char* buf1 = buf0 + T.cap;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(buf1 + T.cap);
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int c0 = blockIdx.x * CB;
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(&bars[0]);
+    mbar_init(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0 && T.nchunks > 0)
+    stage_chunk(buf0, T.bytes + T.chunk_off[0], T.chunk_bytes[0], &bars[0]);
+  for (int t = tid; t < n * CB; t += nthr) {
+    const int i = t / CB, c = t % CB;
+    Xs[t] = (c0 + c < ncols) ? X[i * xr + (c0 + c) * xc] : 0.0;
+  }
+  __syncthreads();
+  for (int ch = 0; ch < T.nchunks; ++ch) {
+    unsigned char* B = (ch & 1) ? buf1 : buf0;
+    if (tid == 0 && ch + 1 < T.nchunks) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      stage_chunk((ch & 1) ? buf0 : buf1, T.bytes + T.chunk_off[ch + 1], T.chunk_bytes[ch + 1],
+                  &bars[(ch + 1) & 1]);
+    }
+    if (!mbar_wait(&bars[ch & 1], (ch >> 1) & 1, spin_limit)) {
+      atomicExch(&abort_flag, 1);
+      atomicExch(&st[ST_TIMEOUT], 1);
+    }
+    __syncthreads();
+    if (abort_flag) {
+      // let the copy in flight land before the CTA leaves
+      if (tid == 0 && ch + 1 < T.nchunks) mbar_wait(&bars[(ch + 1) & 1], ((ch + 1) >> 1) & 1, spin_limit);
+      return;
+    }
+    const int bigw = T.chunk_big_w[ch];
+    if (bigw > 0) {
+      big_supernode<CB, UPPER>(T, T.chunk_big_f[ch], bigw, Xs);
+      continue;
+    }
+    const int* hdr = reinterpret_cast<const int*>(B);
+    if (hdr[0] > 0 && hdr[2] > 0) {
+      chunk_phase_a<CB>(B, Xs);
+      __syncthreads();
+    }
+    if (hdr[1] > 0) {
+      const int wmax = hdr[6];
+      if (wmax <= 4) chunk_phase_b_narrow<CB, UPPER>(B, Xs);
+      else if (wmax <= 8) chunk_phase_b<CB, UPPER, 8>(B, Xs);
+      else if (wmax <= 16) chunk_phase_b<CB, UPPER, 16>(B, Xs);
+      else chunk_phase_b<CB, UPPER, 32>(B, Xs);
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n * CB; t += nthr) {
+    const int i = t / CB, c = t % CB;
+    if (c0 + c < ncols) X[i * xr + (c0 + c) * xc] = Xs[t];
+  }
+}
+
+size_t st_smem(int n, int cb, int cap) {
+  return (((size_t)n * cb * sizeof(double) + 15) & ~size_t(15)) + 2 * (size_t)cap + 16;
+}
+
+template <int CB, bool UPPER>
+cudaError_t launch_one(cudaStream_t s, const StDev& T, int n, double* X, long long xr, long long xc, int ncols,
+                       int* st, long long spin_limit) {
+  const size_t smem = st_smem(n, CB, T.cap);
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_st<CB, UPPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int grid = (ncols + CB - 1) / CB;
+  k_trsm_st<CB, UPPER><<<grid, TRSM_THREADS, smem, s>>>(T, n, X, xr, xc, ncols, st, spin_limit);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_stream(long long nslots, const long long* __restrict__ slot, const int* __restrict__ src,
+                              const double* __restrict__ vals, const double* __restrict__ inv_diag, int unit,
+                              double* __restrict__ stream) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= nslots) return;
+  const int sidx = src[k];
+  double v;
+  if (sidx >= 0) v = vals[sidx];
+  else if (sidx == -1 || unit) v = 1.0;
+  else v = inv_diag[-2 - sidx];
+  stream[slot[k]] = v;
+}
+
+}  // namespace
+
+int trsm_st_max_cb(int n, int cap) {
+  int dev = 0, lim = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  for (int cb : {4, 2, 1})
+    if (st_smem(n, cb, cap) + 1024 <= (size_t)lim) return cb;
+  return 0;
+}
+
+cudaError_t launch_trsm_st(cudaStream_t s, int cb, bool upper, const StDev& T, int n, double* X, long long xr,
+                           long long xc, int ncols, int* st, long long spin_limit) {
+  if (ncols <= 0 || T.nchunks <= 0) return cudaSuccess;
+  switch (cb * 2 + (upper ? 1 : 0)) {
+    case 2: return launch_one<1, false>(s, T, n, X, xr, xc, ncols, st, spin_limit);
+    case 3: return launch_one<1, true>(s, T, n, X, xr, xc, ncols, st, spin_limit);
+    case 4: return launch_one<2, false>(s, T, n, X, xr, xc, ncols, st, spin_limit);
+    case 5: return launch_one<2, true>(s, T, n, X, xr, xc, ncols, st, spin_limit);
+    case 8: return launch_one<4, false>(s, T, n, X, xr, xc, ncols, st, spin_limit);
+    case 9: return launch_one<4, true>(s, T, n, X, xr, xc, ncols, st, spin_limit);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fill_stream(cudaStream_t s, long long nslots, const long long* slot, const int* src,
+                               const double* vals, const double* inv_diag, int unit, unsigned char* stream) {
+  if (nslots <= 0) return cudaSuccess;
+  k_fill_stream<<<int((nslots + 255) / 256), 256, 0, s>>>(nslots, slot, src, vals, inv_diag, unit,
+                                                           reinterpret_cast<double*>(stream));
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace condipm
+
+// ============================================================================
+// Column-parallel variant: one warp lane per right-hand-side column, so every
+// FP64 instruction carries 32 useful multiply-adds (on GB300 a warp-wide DFMA
+// occupies the SM's FP64 pipe for the same time whatever its active mask).  A
+// warp solves one supernode (<= 32 rows, one accumulator register per row) for
+// its 32 columns; long rows first have their external part cut into segments
+// summed by other warps.  The ksplit CTAs that share a 32-column block split
+// each level between them and meet at a bounded counter barrier, so the launch
+// is cooperative (every CTA resident).  X is row-major: element (i, c) at
+// X[i*ld + c], ld a multiple of 32.
+namespace condipm {
+namespace {
+
+constexpr int COLS_THREADS = 256;
+
+__device__ __forceinline__ bool block_group_barrier(unsigned* ctr, unsigned target, long long limit, int* st) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    long long it = 0;
+    while (atomicAdd(ctr, 0u) < target) {
+      if (++it > limit) { atomicExch(&st[ST_TIMEOUT], 1); ok = 0; break; }
+      __nanosleep(20);
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <bool UPPER, int WC>
+__device__ __forceinline__ void sweep_supernode(const ColDev& S, int f, int w, const double* __restrict__ val,
+                                                const double* __restrict__ inv_diag, double* X, long long ld,
+                                                int c, bool on, const double* part) {
+  double acc[WC];
+#pragma unroll
+  for (int si = 0; si < WC; ++si) {
+    if (si < w) {
+      const int r = f + si;
+      double a = on ? X[r * ld + c] : 0.0;
+      const int ns = S.row_nseg[r];
+      if (ns > 0) {
+        const int s0 = S.row_seg[r];
+        for (int k = 0; k < ns; ++k) a -= part[(long long)(s0 + k) * 32];
+      }
+      acc[si] = a;
+    }
+  }
+#pragma unroll
+  for (int tt = 0; tt < WC; ++tt) {
+    const int t = UPPER ? WC - 1 - tt : tt;
+    if (t < w) {
+      const int rt = f + t;
+      if (inv_diag) acc[t] *= inv_diag[rt];
+      if (on) X[rt * ld + c] = acc[t];
+#pragma unroll
+      for (int s2 = 0; s2 < WC; ++s2) {
+        if (UPPER ? (s2 < t) : (s2 > t && s2 < w)) {
+          const double l = UPPER ? val[S.int_beg[f + s2] + (t - s2 - 1)] : val[S.int_beg[f + s2] + t];
+          acc[s2] = fma(-l, acc[t], acc[s2]);
+        }
+      }
+    }
+  }
+}
+
+template <bool UPPER>
+__global__ void __launch_bounds__(COLS_THREADS) k_trsm_cols(ColDev S, const int* __restrict__ ci,
+                                                            const double* __restrict__ val,
+                                                            const double* __restrict__ inv_diag, double* X,
+                                                            long long ld, int ncols, int ksplit, double* scratch,
+                                                            unsigned* bar, int* st, long long spin_limit) {
+  const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int c = cb * 32 + lane;
+  const bool on = c < ncols;
+  const int gw = p * nwarps + warp, W = ksplit * nwarps;
+  double* part = scratch + (long long)cb * S.maxseg * 32 + lane;
+  unsigned* ctr = bar + cb;
+  unsigned nbar = 0;
+  for (int lev = 0; lev < S.nlev; ++lev) {
+    const int g0 = S.lvl_seg_ptr[lev], g1 = S.lvl_seg_ptr[lev + 1];
+    if (g1 > g0) {
+      // external entries: one segment (<= 32 entries) per warp; the segment's
+      // indices and values are fetched once, one per lane, and broadcast
+      for (int g = g0 + gw; g < g1; g += W) {
+        const int q0 = S.seg_q0[g], len = S.seg_q1[g] - q0;
+        const int myj = lane < len ? ci[q0 + lane] : 0;
+        const double myv = lane < len ? val[q0 + lane] : 0.0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < 32; k += 4) {
+          if (k < len) {
+            const int j0 = __shfl_sync(FULL, myj, k), j1 = __shfl_sync(FULL, myj, k + 1);
+            const int j2 = __shfl_sync(FULL, myj, k + 2), j3 = __shfl_sync(FULL, myj, k + 3);
+            const double v0 = __shfl_sync(FULL, myv, k), v1 = __shfl_sync(FULL, myv, k + 1);
+            const double v2 = __shfl_sync(FULL, myv, k + 2), v3 = __shfl_sync(FULL, myv, k + 3);
+            a0 = fma(v0, on ? X[j0 * ld + c] : 0.0, a0);
+            if (k + 1 < len) a1 = fma(v1, on ? X[j1 * ld + c] : 0.0, a1);
+            if (k + 2 < len) a2 = fma(v2, on ? X[j2 * ld + c] : 0.0, a2);
+            if (k + 3 < len) a3 = fma(v3, on ? X[j3 * ld + c] : 0.0, a3);
+          }
+        }
+        const double dot = (a0 + a1) + (a2 + a3);
+        const int tr = S.seg_row[g];
+        if (tr >= 0) {
+          if (on) X[tr * ld + c] -= dot;
+        } else {
+          part[(long long)(-1 - tr) * 32] = dot;
+        }
+      }
+      if (!block_group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
+    }
+    for (int s = S.lvl_ptr[lev] + gw; s < S.lvl_ptr[lev + 1]; s += W) {
+      const int f = S.sn_first[s], w = S.sn_w[s];
+      if (w <= 4) sweep_supernode<UPPER, 4>(S, f, w, val, inv_diag, X, ld, c, on, part);
+      else if (w <= 8) sweep_supernode<UPPER, 8>(S, f, w, val, inv_diag, X, ld, c, on, part);
+      else if (w <= 16) sweep_supernode<UPPER, 16>(S, f, w, val, inv_diag, X, ld, c, on, part);
+      else sweep_supernode<UPPER, 32>(S, f, w, val, inv_diag, X, ld, c, on, part);
+    }
+    if (!block_group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
+  }
+}
+
+}  // namespace
+
+int trsm_cols_max_blocks() {
+  int dev = 0, sms = 0, a = 0, b = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsm_cols<false>, COLS_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trsm_cols<true>, COLS_THREADS, 0);
+  return sms * std::min(a, b);
+}
+
+cudaError_t launch_trsm_cols(cudaStream_t s, bool upper, const ColDev& S, const int* ci, const double* val,
+                             const double* inv_diag, double* X, long long ld, int ncols, int ksplit,
+                             double* scratch, unsigned* bar, int* st, long long spin_limit) {
+  if (ncols <= 0 || S.nlev <= 0) return cudaSuccess;
+  const int ncb = (ncols + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned) * ncb, s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&inv_diag, (void*)&X, (void*)&ld, (void*)&ncols,
+                  (void*)&ksplit, (void*)&scratch, (void*)&bar, (void*)&st, (void*)&spin_limit};
+  void* fn = upper ? (void*)k_trsm_cols<true> : (void*)k_trsm_cols<false>;
+  note_launch();
+  return cudaLaunchCooperativeKernel(fn, dim3(ncb * ksplit), dim3(COLS_THREADS), args, 0, s);
+}
+
+}  // namespace condipm

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "../../include/condipm.h"
+#include "common.cuh"
 #include "plan.h"
 
 struct opf_handle {
@@ -48,9 +49,30 @@ struct opf_handle {
   int *Up_rp = nullptr, *Up_ci = nullptr, *Up_map = nullptr, *Lt_map = nullptr;
   double *Lo_val = nullptr, *Ut_val = nullptr, *Up_val = nullptr, *Lt_val = nullptr;
   int *fwd_ptr = nullptr, *fwd_rows = nullptr, *bwd_ptr = nullptr, *bwd_rows = nullptr;
+  // staged supernodal solves: structure per pattern (lower / upper), values per
+  // factor (L and U^T on the lower structure, U and L^T on the upper one)
+  struct StBuf {
+    int nchunks = 0;
+    long long* chunk_off = nullptr;
+    int *chunk_bytes = nullptr, *chunk_big_f = nullptr, *chunk_big_w = nullptr, *int_beg = nullptr;
+    long long* slot = nullptr;
+    int* src = nullptr;
+    long long nslots = 0;
+    unsigned char *bytes_a = nullptr, *bytes_b = nullptr;
+  } stLo, stUp;
+  int st_cap = 0;
+  condipm::ColDev csL{}, csU{};  // column-parallel schedules
+  double* cs_scratch = nullptr;  // segment partial sums, ncb_max * maxseg * 32
+  unsigned* cs_bar = nullptr;    // per column-block barrier counters
+  int cs_ncb_max = 0, cs_ksplit_max = 1;
+  int ldp = 32;                  // leading dimension of Zt / H (nu rounded up to 32)
+  int sn_cb = 0;                 // columns per CTA of the staged solves (0 = level fallback)
+  int trsm_mode = -1;            // multi-RHS solve kernel: -1 autotune, 32 column-parallel,
+                                 // 1/2/4 staged with that many columns per CTA
+  float tune_ms[3][4] = {};      // autotuner timings: {cols, staged 1, 2, 4} per role
   // dense condensed buffers: Zt = [I; S_x] and H = K Zt (nw x nu, row-major, x rows permuted),
   // Kred (nu x nu, symmetric) and its Cholesky factor F
-  double *Zt = nullptr, *H = nullptr, *Kred = nullptr, *F = nullptr;
+  double *Zt = nullptr, *H = nullptr, *Kred = nullptr, *F = nullptr, *Fdinv = nullptr;
   // device status word and grid-barrier state
   int* st = nullptr;
   unsigned* bar = nullptr;

@@ -5,6 +5,7 @@
 #include <array>
 #include <iterator>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <numeric>
 #include <queue>
@@ -131,7 +132,338 @@ Levels make_levels(const CSR& M, bool lower) {
   return L;
 }
 
+// Supernodal schedule for the strict-lower (upper = false) or strict-upper
+// pattern M, supernodes given by start offsets.
+std::string make_sn_sched(const CSR& M, const std::vector<int>& start, bool upper, SnSched& S) {
+  const int n = M.nrows;
+  const int ns = int(start.size()) - 1;
+  std::vector<int> sn_of(n);
+  for (int s = 0; s < ns; ++s)
+    for (int i = start[s]; i < start[s + 1]; ++i) sn_of[i] = s;
+  S.ext_beg.resize(n); S.ext_end.resize(n); S.int_beg.resize(n);
+  std::vector<int> lev(ns, 0);
+  std::vector<double> ext_len(ns, 0.0);
+  int nlev = 0;
+  auto visit = [&](int s) {
+    const int f = start[s], w = start[s + 1] - start[s];
+    int l = 0;
+    for (int r = f; r < f + w; ++r) {
+      const int nint = upper ? (f + w - 1 - r) : (r - f);
+      const int len = M.rp[r + 1] - M.rp[r];
+      if (len < nint) return std::string("supernode diagonal block is not dense");
+      if (upper) {
+        S.int_beg[r] = M.rp[r];
+        S.ext_beg[r] = M.rp[r] + nint;
+        S.ext_end[r] = M.rp[r + 1];
+        for (int t = 0; t < nint; ++t)
+          if (M.ci[M.rp[r] + t] != r + 1 + t) return std::string("supernode diagonal block is not dense");
+      } else {
+        S.int_beg[r] = M.rp[r + 1] - nint;
+        S.ext_beg[r] = M.rp[r];
+        S.ext_end[r] = M.rp[r + 1] - nint;
+        for (int t = 0; t < nint; ++t)
+          if (M.ci[M.rp[r + 1] - nint + t] != f + t) return std::string("supernode diagonal block is not dense");
+      }
+      for (int q = S.ext_beg[r]; q < S.ext_end[r]; ++q) l = std::max(l, lev[sn_of[M.ci[q]]] + 1);
+      ext_len[s] += S.ext_end[r] - S.ext_beg[r];
+    }
+    lev[s] = l;
+    nlev = std::max(nlev, l + 1);
+    return std::string();
+  };
+  if (upper) {
+    for (int s = ns - 1; s >= 0; --s) { std::string e = visit(s); if (!e.empty()) return e; }
+  } else {
+    for (int s = 0; s < ns; ++s) { std::string e = visit(s); if (!e.empty()) return e; }
+  }
+  S.nlev = ns ? nlev : 0;
+  S.lvl_ptr.assign(S.nlev + 1, 0);
+  S.lvl_bptr.assign(S.nlev + 1, 0);
+  S.lvl_gs.assign(S.nlev, 1);
+  S.lvl_wmax.assign(S.nlev, 1);
+  S.lvl_ga.assign(S.nlev, 0);
+  S.lvl_rptr.assign(S.nlev + 1, 0);
+  std::vector<std::vector<int>> small(S.nlev), big(S.nlev);
+  for (int s = 0; s < ns; ++s) (start[s + 1] - start[s] > 32 ? big : small)[lev[s]].push_back(s);
+  for (int l = 0; l < S.nlev; ++l) {
+    int wmax = 1;
+    double ext = 0.0;
+    long long rows = 0;
+    for (int s : small[l]) {
+      wmax = std::max(wmax, start[s + 1] - start[s]);
+      ext += ext_len[s];
+      rows += start[s + 1] - start[s];
+    }
+    int want = std::max(wmax, rows ? int(std::ceil(ext / rows / 4.0)) : 1);
+    int gs = 1;
+    while (gs < want && gs < 32) gs <<= 1;
+    S.lvl_gs[l] = gs;
+    S.lvl_wmax[l] = wmax;
+    // rows of the level and lanes per row for their external entries
+    long long next = 0, nrows = 0;
+    for (auto* grp : {&small[l], &big[l]})
+      for (int s2 : *grp)
+        for (int r = start[s2]; r < start[s2 + 1]; ++r) {
+          S.rows.push_back(r);
+          next += S.ext_end[r] - S.ext_beg[r];
+          ++nrows;
+        }
+    S.lvl_rptr[l + 1] = int(S.rows.size());
+    if (next > 0) {
+      int wantA = int(std::ceil(double(next) / double(nrows) / 8.0));
+      int ga = 1;
+      while (ga < wantA && ga < 32) ga <<= 1;
+      S.lvl_ga[l] = ga;
+    }
+    for (int s : small[l]) { S.sn_first.push_back(start[s]); S.sn_w.push_back(start[s + 1] - start[s]); }
+    for (int s : big[l]) { S.big_first.push_back(start[s]); S.big_w.push_back(start[s + 1] - start[s]); }
+    S.lvl_ptr[l + 1] = int(S.sn_first.size());
+    S.lvl_bptr[l + 1] = int(S.big_first.size());
+  }
+  return "";
+}
+
 }  // namespace
+
+void build_sn_stream(const CSR& M, const SnSched& S, const std::vector<int>& start, bool upper, bool unit,
+                     int budget, SnStream& out) {
+  out = SnStream();
+  auto al16 = [](long long b) { return (b + 15) & ~15LL; };
+  struct Sup { int f, w; };
+  // bytes a set of supernodes needs in one chunk
+  auto chunk_size = [&](const std::vector<Sup>& sn, long long& nE, long long& nI, int& nA) {
+    nE = 0; nI = 0; nA = 0;
+    long long nd = 0;
+    for (auto& x : sn) {
+      for (int r = x.f; r < x.f + x.w; ++r) { nE += S.ext_end[r] - S.ext_beg[r]; ++nA; }
+      nI += (long long)x.w * (x.w - 1) / 2;
+      nd += x.w;
+    }
+    const long long nB = sn.size();
+    long long b = 80;
+    b = al16(b + 4 * (nA + 1)); b = al16(b + 4 * nA); b = al16(b + 4 * nE); b = al16(b + 8 * nE);
+    b = al16(b + 4 * nB); b = al16(b + 4 * nB); b = al16(b + 4 * (nB + 1)); b = al16(b + 4 * (nB + 1));
+    b = al16(b + 8 * nI); b = al16(b + 8 * nd);
+    return b;
+  };
+  auto emit = [&](const std::vector<Sup>& sn, bool with_b, int ga, int gs, int wmax) {
+    long long nE, nI;
+    int nA;
+    chunk_size(sn, nE, nI, nA);
+    if (!with_b) nI = 0;
+    const int nB = with_b ? int(sn.size()) : 0;
+    long long nd = 0;
+    if (with_b) for (auto& x : sn) nd += x.w;
+    long long o = 80;
+    const long long oAptr = o; o = al16(o + 4LL * (nA + 1));
+    const long long oArow = o; o = al16(o + 4LL * nA);
+    const long long oEci = o; o = al16(o + 4 * nE);
+    const long long oEval = o; o = al16(o + 8 * nE);
+    const long long oBf = o; o = al16(o + 4LL * nB);
+    const long long oBw = o; o = al16(o + 4LL * nB);
+    const long long oBiptr = o; o = al16(o + 4LL * (nB + 1));
+    const long long oBdptr = o; o = al16(o + 4LL * (nB + 1));
+    const long long oIval = o; o = al16(o + 8 * nI);
+    const long long oBd = o; o = al16(o + 8 * nd);
+    const long long base = out.bytes.size();
+    out.bytes.resize(base + o, 0);
+    out.chunk_off.push_back(base);
+    out.chunk_bytes.push_back(int(o));
+    out.chunk_big_f.push_back(-1);
+    out.chunk_big_w.push_back(0);
+    out.max_chunk = std::max(out.max_chunk, int(o));
+    unsigned char* B = out.bytes.data() + base;
+    int hdr[20] = {nA, nB, int(nE), int(nI), ga, gs, wmax, 0, int(oAptr), int(oArow), int(oEci), int(oEval),
+                   int(oBf), int(oBw), int(oBiptr), int(oBdptr), int(oIval), int(oBd), 0, 0};
+    std::memcpy(B, hdr, sizeof(hdr));
+    int* Aptr = reinterpret_cast<int*>(B + oAptr);
+    int* Arow = reinterpret_cast<int*>(B + oArow);
+    int* Eci = reinterpret_cast<int*>(B + oEci);
+    int a = 0, e = 0;
+    Aptr[0] = 0;
+    std::vector<int> order;
+    for (auto& x : sn)
+      for (int r = x.f; r < x.f + x.w; ++r) order.push_back(r);
+    std::stable_sort(order.begin(), order.end(), [&](int p1, int p2) {
+      return S.ext_end[p1] - S.ext_beg[p1] > S.ext_end[p2] - S.ext_beg[p2];
+    });
+    for (int r : order) {
+      Arow[a] = r;
+      for (int q = S.ext_beg[r]; q < S.ext_end[r]; ++q, ++e) {
+        Eci[e] = M.ci[q];
+        out.slot.push_back((base + oEval) / 8 + e);
+        out.src.push_back(q);
+      }
+      Aptr[++a] = e;
+    }
+    if (!with_b) return;
+    int* Bf = reinterpret_cast<int*>(B + oBf);
+    int* Bw = reinterpret_cast<int*>(B + oBw);
+    int* Biptr = reinterpret_cast<int*>(B + oBiptr);
+    int* Bdptr = reinterpret_cast<int*>(B + oBdptr);
+    long long ip = 0, dp = 0;
+    for (int k = 0; k < nB; ++k) {
+      const int f = sn[k].f, w = sn[k].w;
+      Bf[k] = f; Bw[k] = w; Biptr[k] = int(ip); Bdptr[k] = int(dp);
+      for (int si = 0; si < w; ++si) {
+        const int r = f + si;
+        const int cnt = upper ? (w - 1 - si) : si;
+        const long long off = upper ? ((long long)si * (w - 1) - (long long)si * (si - 1) / 2) : (long long)si * (si - 1) / 2;
+        for (int t = 0; t < cnt; ++t) {
+          out.slot.push_back((base + oIval) / 8 + ip + off + t);
+          out.src.push_back(S.int_beg[r] + t);
+        }
+        out.slot.push_back((base + oBd) / 8 + dp + si);
+        out.src.push_back(unit ? -1 : -2 - r);
+      }
+      ip += (long long)w * (w - 1) / 2;
+      dp += w;
+    }
+    Biptr[nB] = int(ip);
+    Bdptr[nB] = int(dp);
+  };
+  for (int l = 0; l < S.nlev; ++l) {
+    const int ga = std::max(1, S.lvl_ga[l]), gs = S.lvl_gs[l], wmax = S.lvl_wmax[l];
+    std::vector<Sup> cur;
+    for (int k = S.lvl_ptr[l]; k < S.lvl_ptr[l + 1]; ++k) {
+      Sup x{S.sn_first[k], S.sn_w[k]};
+      std::vector<Sup> trial = cur;
+      trial.push_back(x);
+      long long nE, nI;
+      int nA;
+      if (chunk_size(trial, nE, nI, nA) <= budget) { cur.swap(trial); continue; }
+      if (!cur.empty()) { emit(cur, true, ga, gs, wmax); cur.clear(); }
+      std::vector<Sup> one{x};
+      if (chunk_size(one, nE, nI, nA) <= budget) { cur = one; continue; }
+      // a supernode whose rows alone overflow a chunk: its external entries go in
+      // row chunks first, its diagonal block in a chunk of its own
+      std::vector<Sup> rows;
+      for (int r = x.f; r < x.f + x.w; ++r) {
+        std::vector<Sup> t2 = rows;
+        t2.push_back({r, 1});
+        if (!rows.empty() && chunk_size(t2, nE, nI, nA) > budget) { emit(rows, false, 32, 1, 1); rows.clear(); t2 = {{r, 1}}; }
+        rows.swap(t2);
+      }
+      if (!rows.empty()) emit(rows, false, 32, 1, 1);
+      // its diagonal block in a chunk without rows (external entries already applied)
+      {
+        // build the chunk by hand with nA = nE = 0
+        const long long nI2 = (long long)x.w * (x.w - 1) / 2;
+        long long o = 80;
+        const long long oAptr = o; o = al16(o + 4);
+        const long long oArow = o;
+        const long long oEci = o;
+        const long long oEval = o;
+        const long long oBf = o; o = al16(o + 4);
+        const long long oBw = o; o = al16(o + 4);
+        const long long oBiptr = o; o = al16(o + 8);
+        const long long oBdptr = o; o = al16(o + 8);
+        const long long oIval = o; o = al16(o + 8 * nI2);
+        const long long oBd = o; o = al16(o + 8LL * x.w);
+        const long long base = out.bytes.size();
+        out.bytes.resize(base + o, 0);
+        out.chunk_off.push_back(base);
+        out.chunk_bytes.push_back(int(o));
+        out.chunk_big_f.push_back(-1);
+        out.chunk_big_w.push_back(0);
+        out.max_chunk = std::max(out.max_chunk, int(o));
+        unsigned char* B = out.bytes.data() + base;
+        int hdr[20] = {0, 1, 0, int(nI2), 1, gs, wmax, 0, int(oAptr), int(oArow), int(oEci), int(oEval),
+                       int(oBf), int(oBw), int(oBiptr), int(oBdptr), int(oIval), int(oBd), 0, 0};
+        std::memcpy(B, hdr, sizeof(hdr));
+        reinterpret_cast<int*>(B + oAptr)[0] = 0;
+        reinterpret_cast<int*>(B + oBf)[0] = x.f;
+        reinterpret_cast<int*>(B + oBw)[0] = x.w;
+        reinterpret_cast<int*>(B + oBiptr)[0] = 0;
+        reinterpret_cast<int*>(B + oBiptr)[1] = int(nI2);
+        reinterpret_cast<int*>(B + oBdptr)[0] = 0;
+        reinterpret_cast<int*>(B + oBdptr)[1] = x.w;
+        for (int si = 0; si < x.w; ++si) {
+          const int r = x.f + si;
+          const int cnt = upper ? (x.w - 1 - si) : si;
+          const long long off = upper ? ((long long)si * (x.w - 1) - (long long)si * (si - 1) / 2)
+                                      : (long long)si * (si - 1) / 2;
+          for (int t = 0; t < cnt; ++t) {
+            out.slot.push_back((base + oIval) / 8 + off + t);
+            out.src.push_back(S.int_beg[r] + t);
+          }
+          out.slot.push_back((base + oBd) / 8 + si);
+          out.src.push_back(unit ? -1 : -2 - r);
+        }
+      }
+    }
+    if (!cur.empty()) emit(cur, true, ga, gs, wmax);
+    // big supernodes: external entries in row chunks, then a big marker chunk
+    for (int k = S.lvl_bptr[l]; k < S.lvl_bptr[l + 1]; ++k) {
+      const int f = S.big_first[k], w = S.big_w[k];
+      std::vector<Sup> rows;
+      long long nE, nI;
+      int nA;
+      for (int r = f; r < f + w; ++r) {
+        std::vector<Sup> t2 = rows;
+        t2.push_back({r, 1});
+        if (!rows.empty() && chunk_size(t2, nE, nI, nA) > budget) { emit(rows, false, 32, 1, 1); rows.clear(); t2 = {{r, 1}}; }
+        rows.swap(t2);
+      }
+      if (!rows.empty()) emit(rows, false, 32, 1, 1);
+      out.chunk_off.push_back(out.bytes.size());
+      out.chunk_bytes.push_back(0);
+      out.chunk_big_f.push_back(f);
+      out.chunk_big_w.push_back(w);
+    }
+  }
+}
+
+// column-parallel schedule: supernodes cut to <= 32 rows, long rows in segments
+std::string build_col_sched(const CSR& M, const std::vector<int>& sn_start, bool upper, ColSched& C) {
+  std::vector<int> start{0};
+  for (size_t s = 0; s + 1 < sn_start.size(); ++s)
+    for (int f = sn_start[s] + 32; f < sn_start[s + 1]; f += 32) start.push_back(f);
+  {
+    std::vector<int> all(sn_start.begin() + 1, sn_start.end());
+    all.insert(all.end(), start.begin() + 1, start.end());
+    std::sort(all.begin(), all.end());
+    start.assign(1, 0);
+    for (int v : all) if (v != start.back()) start.push_back(v);
+  }
+  SnSched S;
+  std::string e = make_sn_sched(M, start, upper, S);
+  if (!e.empty()) return e;
+  if (!S.big_first.empty()) return "column schedule has a supernode wider than 32";
+  const int SEG = 32;
+  C = ColSched();
+  C.nlev = S.nlev;
+  C.lvl_ptr = S.lvl_ptr;
+  C.sn_first = S.sn_first;
+  C.sn_w = S.sn_w;
+  C.ext_beg = S.ext_beg;
+  C.ext_end = S.ext_end;
+  C.int_beg = S.int_beg;
+  const int n = M.nrows;
+  C.row_seg.assign(n, -1);
+  C.row_nseg.assign(n, 0);
+  C.lvl_seg_ptr.assign(C.nlev + 1, 0);
+  for (int l = 0; l < C.nlev; ++l) {
+    int slot = 0;
+    for (int k = C.lvl_ptr[l]; k < C.lvl_ptr[l + 1]; ++k)
+      for (int r = C.sn_first[k]; r < C.sn_first[k] + C.sn_w[k]; ++r) {
+        const int len = C.ext_end[r] - C.ext_beg[r];
+        if (len == 0) continue;
+        const int ns = (len + SEG - 1) / SEG;
+        C.row_seg[r] = ns > 1 ? slot : -1;
+        C.row_nseg[r] = ns > 1 ? ns : -1;      // -1: one segment, applied to X directly
+        for (int q = C.ext_beg[r]; q < C.ext_end[r]; q += SEG) {
+          C.seg_q0.push_back(q);
+          C.seg_q1.push_back(std::min(q + SEG, C.ext_end[r]));
+          C.seg_row.push_back(ns > 1 ? -1 - slot : r);   // >= 0: row to update; < 0: scratch slot
+          if (ns > 1) ++slot;
+        }
+      }
+    C.lvl_seg_ptr[l + 1] = int(C.seg_q0.size());
+    C.maxseg = std::max(C.maxseg, slot);
+  }
+  return "";
+}
 
 std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double* Pd,
                        const double* Qd, const double* Vmin, const double* Vmax,
@@ -412,6 +744,26 @@ std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double*
     }
     P.fwd = make_levels(P.Lo, true);
     P.bwd = make_levels(P.Up, false);
+    // fundamental supernodes: column j joins j-1 when parent(j-1) = j and
+    // struct(L(:, j-1)) = {j} + struct(L(:, j)); the diagonal block is then dense
+    P.sn_start.assign(1, 0);
+    for (int j = 1; j < n; ++j) {
+      const int lp = P.Up.rp[j] - P.Up.rp[j - 1];
+      const int lj = P.Up.rp[j + 1] - P.Up.rp[j];
+      const bool merge = lp > 0 && P.Up.ci[P.Up.rp[j - 1]] == j && lp == lj + 1;
+      if (!merge) P.sn_start.push_back(j);
+    }
+    P.sn_start.push_back(n);
+    std::string e1 = make_sn_sched(P.Lo, P.sn_start, false, P.snL);
+    if (!e1.empty()) return e1;
+    std::string e2 = make_sn_sched(P.Up, P.sn_start, true, P.snU);
+    if (!e2.empty()) return e2;
+    build_sn_stream(P.Lo, P.snL, P.sn_start, false, false, 32 * 1024, P.stL);
+    build_sn_stream(P.Up, P.snU, P.sn_start, true, false, 32 * 1024, P.stU);
+    std::string e3 = build_col_sched(P.Lo, P.sn_start, false, P.csL);
+    if (!e3.empty()) return e3;
+    std::string e4 = build_col_sched(P.Up, P.sn_start, true, P.csU);
+    if (!e4.empty()) return e4;
     // G_x entries -> LU positions
     P.Gx_to_LU.assign(P.G.nnz(), -1);
     for (int rr = 0; rr < nx; ++rr)

@@ -32,6 +32,71 @@ struct Levels {
   std::vector<int> ptr, rows;  // rows grouped by level, ascending within a level
 };
 
+// Supernodal schedule of one triangular solve (lower = forward, upper = backward).
+// Supernodes are runs of consecutive rows whose diagonal block is dense; a row's
+// entries split into "internal" ones (inside its supernode's diagonal block) and
+// "external" ones (in supernodes solved at earlier levels).  Level 0 runs first.
+struct SnSched {
+  int nlev = 0;
+  std::vector<int> lvl_ptr;   // [nlev+1] range of small supernodes (width <= 32)
+  std::vector<int> lvl_gs;    // [nlev] lanes per small supernode (power of two <= 32)
+  std::vector<int> lvl_wmax;  // [nlev] widest small supernode of the level
+  std::vector<int> lvl_ga;    // [nlev] lanes per row for the external entries (0 = none)
+  std::vector<int> lvl_rptr;  // [nlev+1] range of rows (small and big supernodes) in rows
+  std::vector<int> rows;      // rows of each level, in level order
+  std::vector<int> lvl_bptr;  // [nlev+1] range of big supernodes (width > 32)
+  std::vector<int> sn_first, sn_w;    // small supernodes in level order
+  std::vector<int> big_first, big_w;  // big supernodes in level order
+  std::vector<int> ext_beg, ext_end, int_beg;  // [n] per row
+};
+
+// Byte stream of one supernodal triangular solve, cut into chunks that a CTA
+// stages into shared memory one ahead of use.  A chunk holds complete
+// supernodes of one level: their rows' external entries (phase A) and their
+// packed dense diagonal triangles and diagonal inverses (phase B).  Chunk layout
+// (byte offsets from the chunk start, every array 16-byte aligned):
+//   int hdr[20] = {nA, nB, nE, nI, ga, gs, wmax, 0,
+//                  oAptr, oArow, oEci, oEval, oBf, oBw, oBiptr, oBdptr, oIval, oBd, 0, 0}
+//   int   Aptr[nA+1]  entry range of each row (chunk-relative)
+//   int   Arow[nA]    row index
+//   int   Eci[nE]     column of each external entry
+//   double Eval[nE]   its value
+//   int   Bf[nB], Bw[nB]        first row and width of each supernode
+//   int   Biptr[nB+1], Bdptr[nB+1]   offsets into Ival and Bd
+//   double Ival[nI]   dense triangles: lower row s holds columns 0..s-1 at s(s-1)/2;
+//                     upper row s holds columns s+1..w-1 at s(w-1) - s(s-1)/2
+//   double Bd[]       inverse diagonal of each row (1 for a unit diagonal)
+// A "big" chunk (width > 32) carries no data: its rows' external entries sit in
+// earlier chunks and its diagonal block is read from the factor in place.
+struct SnStream {
+  std::vector<unsigned char> bytes;   // structure with value slots left zero
+  std::vector<long long> chunk_off;   // [nchunks] byte offsets (16-byte aligned)
+  std::vector<int> chunk_bytes;       // [nchunks] sizes (multiples of 16)
+  std::vector<int> chunk_big_f, chunk_big_w;  // -1 / 0 unless a big chunk
+  // value slots: double index into bytes, and the factor position it takes
+  // (>= 0: entry of the factor's strict part; -1: 1.0; -2 - i: inverse diagonal of row i)
+  std::vector<long long> slot;
+  std::vector<int> src;
+  int max_chunk = 0;
+};
+
+// Schedule of the column-parallel triangular solve (one warp lane per right-hand
+// side column): supernodes split to at most 32 rows, level-scheduled; rows whose
+// external part is long are cut into segments whose partial dot products run
+// on separate warps before the supernode sweep.
+struct ColSched {
+  int nlev = 0;
+  int maxseg = 0;                      // most segments in one level
+  std::vector<int> lvl_ptr;            // [nlev+1] supernodes of each level
+  std::vector<int> sn_first, sn_w;     // level order, width <= 32
+  std::vector<int> lvl_seg_ptr;        // [nlev+1] segments of each level
+  std::vector<int> seg_q0, seg_q1;     // entry range of a segment
+  std::vector<int> seg_row;            // >= 0: row the segment updates in place; < 0: -1 - scratch slot
+  std::vector<int> row_seg;            // [n] first segment slot (level-relative) or -1
+  std::vector<int> row_nseg;           // [n] segments in scratch (0: none, -1: applied in place)
+  std::vector<int> ext_beg, ext_end, int_beg;  // [n]
+};
+
 struct Plan {
   // ---- sizes
   int nb = 0, nl = 0, ng = 0, slack = 0, nx = 0, nu = 0, nw = 0, m = 0, nlim = 0, ne = 0;
@@ -87,8 +152,18 @@ struct Plan {
   std::vector<int> Up_map;     // U values
   std::vector<int> Lt_map;     // L^T values (strict upper pattern)
   Levels fwd, bwd;             // level schedules of the lower / upper solves
+  std::vector<int> sn_start;   // [nsn+1] fundamental supernodes (perm space)
+  SnSched snL, snU;            // supernodal schedules of the lower / upper solves
+  SnStream stL, stU;           // staged streams of the lower / upper solves (positions
+                               // in the strict pattern: Lo for lower, Up for upper)
+  ColSched csL, csU;           // column-parallel schedules of the lower / upper solves
   long long lu_flops = 0;      // multiply-adds of one numeric refactorisation
 };
+
+// Chunked stream of a supernodal schedule over strict pattern M (lower or
+// upper), unit or non-unit diagonal, chunks of at most budget bytes.
+void build_sn_stream(const CSR& M, const SnSched& S, const std::vector<int>& start, bool upper,
+                     bool unit, int budget, SnStream& out);
 
 // Builds the plan; returns an empty string on success, else the reason.
 std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double* Pd,
