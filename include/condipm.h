@@ -173,6 +173,26 @@ int opf_kkt_solve_adjoint(opf_handle* h, const double* rhs, double* sol, int nrh
 int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter,
                   int* iters);
 
+/* ---- dense Cholesky without device allocation ----------------------------------- */
+/* The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate device memory where they need a factorisation -- a loop running under
+ * a fixed memory budget, an application whose device memory is all held by its
+ * own pool allocator, a real-time loop that forbids allocation after set-up.
+ * It factors A + delta_w I = L L^T for a caller-owned device matrix A (n x n,
+ * row-major, only the lower triangle read) into the caller-owned device buffer L
+ * (lower triangle; upper part set to zero), on the given stream (a cudaStream_t,
+ * NULL = legacy default stream), and returns after the stream synchronises.
+ *  - No cudaMalloc / cudaFree and no allocating library routine is called.  The
+ *    scratch (status word, grid-barrier state, inverse diagonal) is a file-scope
+ *    device array sized for n <= 4096 (about 32 KB), held by every GPU that loads
+ *    the library until the process exits; larger n is rejected with INVALID_ARG.
+ *  - The first call on a device looks that array's address up on the current
+ *    device; make that first call before any stream capture.
+ *  - Every call shares the one array per device: calls whose GPU work overlaps
+ *    (two streams, two host threads) race; serialise them.
+ * Errors: INVALID_ARG, CUDA, NOT_PD (*fail_col = first failing column), TIMEOUT. */
+int opf_chol_noalloc(const double* A, int n, double delta_w, double* L, int* fail_col, void* stream);
+
 /* ---- instrumentation ---------------------------------------------------------- */
 /* Kernel launches this library has enqueued since it was loaded (all handles). */
 unsigned long long opf_launch_count(void);

@@ -65,6 +65,7 @@ _SIGS = {
     "opf_kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_kkt_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
+    "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
     "opf_launch_count": (C.c_ulonglong, []),
     "opf_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "opf_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -97,6 +98,18 @@ def exported_symbols():
 def launch_count() -> int:
     """Kernel launches libcondipm.so has enqueued since it was loaded."""
     return int(load_library().opf_launch_count())
+
+
+def chol_noalloc(A, n, delta_w, L, stream=None):
+    """opf_chol_noalloc: factor A + delta_w I = L L^T (device n x n buffers) with no
+    device allocation.  Returns -1 on success, else the failing column."""
+    col = C.c_int(-1)
+    rc = load_library().opf_chol_noalloc(_ptr(A), int(n), float(delta_w), _ptr(L), C.byref(col),
+                                         None if stream is None else C.c_void_p(stream.cuda_stream))
+    if rc == OPF_ERR_NOT_PD:
+        return col.value
+    _check(rc, "opf_chol_noalloc")
+    return -1
 
 
 class OPFError(RuntimeError):
