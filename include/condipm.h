@@ -173,6 +173,38 @@ int opf_kkt_solve_adjoint(opf_handle* h, const double* rhs, double* sol, int nrh
 int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter,
                   int* iters);
 
+/* ---- the interior-point loop (Algorithms 1 and 2; Sec. 4.3, 4.4) --------------- */
+#define OPF_LINRED 0   /* linearize-then-reduce (Algorithm 1) */
+#define OPF_REDLIN 1   /* reduce-then-linearize (Algorithm 2) */
+
+typedef struct opf_ipm_options {
+    int variant;       /* OPF_LINRED or OPF_REDLIN                                  */
+    double tol;        /* scaled optimality error to stop at (paper: 1e-8)          */
+    int max_iter;      /* iteration cap                                             */
+    double mu0;        /* initial barrier parameter                                 */
+    double pf_tol;     /* Newton-Raphson tolerance of the RedLin projection (1e-10) */
+    int verbose;       /* print one line per iteration to stdout                    */
+} opf_ipm_options;
+
+typedef struct opf_ipm_result {
+    int status;        /* OPF_OK, OPF_ERR_NO_CONVERGENCE, or the failing call's code */
+    int iters;
+    double obj, err, mu;
+    int n_factor;      /* Cholesky attempts (inertia correction included)          */
+    double ms_total, ms_eval, ms_condense, ms_factor, ms_solve, ms_linesearch, ms_pf;  /* host wall */
+} opf_ipm_result;
+
+/* Solve the OPF of the handle's network from the flat start (theta = 0, Vm = 1 at
+ * load buses and 1.05 at generator buses, Pg at mid-range, y0 = 0).  The loop's
+ * scalar and vector bookkeeping runs on the host; every model evaluation,
+ * refactorisation, condensation, Cholesky factorisation, step recovery and power
+ * flow runs on the device (opt may be NULL: LinRed, tol 1e-8, 300 iterations,
+ * mu0 0.1, pf_tol 1e-10).  Returns res->status. */
+int opf_solve(opf_handle* h, const opf_ipm_options* opt, opf_ipm_result* res);
+/* The last solve's point (host outputs, any may be NULL): w[nu+nx] = [u; x],
+ * lam[nx], y[m], Pg[ng] (every generator, slack included). */
+int opf_get_solution(const opf_handle* h, double* w, double* lam, double* y, double* Pg);
+
 /* ---- dense Cholesky without device allocation ----------------------------------- */
 /* The paper has no counterpart to this call.  It serves callers that cannot
  * allocate device memory where they need a factorisation -- a loop running under

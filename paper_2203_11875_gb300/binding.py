@@ -41,6 +41,20 @@ class opf_options(C.Structure):
     _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong)]
 
 
+class opf_ipm_options(C.Structure):
+    _fields_ = [("variant", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("mu0", C.c_double),
+                ("pf_tol", C.c_double), ("verbose", C.c_int)]
+
+
+class opf_ipm_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("obj", C.c_double), ("err", C.c_double),
+                ("mu", C.c_double), ("n_factor", C.c_int), ("ms_total", C.c_double), ("ms_eval", C.c_double),
+                ("ms_condense", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
+                ("ms_linesearch", C.c_double), ("ms_pf", C.c_double)]
+
+
+OPF_LINRED, OPF_REDLIN = 0, 1
+
 # name -> (restype, argtypes)
 _SIGS = {
     "opf_create": (C.c_int, [C.POINTER(opf_network), C.POINTER(opf_options), C.POINTER(C.c_void_p)]),
@@ -65,6 +79,8 @@ _SIGS = {
     "opf_kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_kkt_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
+    "opf_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result)]),
+    "opf_get_solution": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
     "opf_launch_count": (C.c_ulonglong, []),
     "opf_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -246,6 +262,28 @@ class Handle:
     def kkt_solve_adjoint(self, rhs, sol, nrhs=1):
         _check(self._lib.opf_kkt_solve_adjoint(self._h, _ptr(rhs), _ptr(sol), int(nrhs)),
                "opf_kkt_solve_adjoint")
+
+    def solve(self, variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False):
+        """opf_solve: the interior-point loop; returns the result fields as a dict."""
+        o = opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
+                            int(bool(verbose)))
+        r = opf_ipm_result()
+        rc = self._lib.opf_solve(self._h, C.byref(o), C.byref(r))
+        out = {f: getattr(r, f) for f, _ in opf_ipm_result._fields_}
+        if rc not in (OPF_OK, -8):
+            raise OPFError(rc, "opf_solve")
+        return out
+
+    def solution(self):
+        """(w = [u; x], lam, y, Pg) of the last solve, host numpy arrays."""
+        w = np.zeros(self.nw)
+        lam = np.zeros(self.nx)
+        y = np.zeros(self.m)
+        pg = np.zeros((self.nu + 1) // 2)
+        _check(self._lib.opf_get_solution(self._h, w.ctypes.data_as(C.c_void_p), lam.ctypes.data_as(C.c_void_p),
+                                          y.ctypes.data_as(C.c_void_p), pg.ctypes.data_as(C.c_void_p)),
+               "opf_get_solution")
+        return w, lam, y, pg
 
     def profile(self, enable=True):
         _check(self._lib.opf_profile(self._h, int(bool(enable))), "opf_profile")

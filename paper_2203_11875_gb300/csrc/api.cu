@@ -11,6 +11,7 @@
 
 #include "../../include/condipm.h"
 #include "common.cuh"
+#include "internal.h"
 #include "opf_handle.h"
 #include "plan.h"
 
@@ -174,6 +175,12 @@ int upload_all(opf_handle* h) {
   TRY(upload(h, &h->GuT_rp, P.GuT.rp));
   TRY(upload(h, &h->GuT_ci, P.GuT.ci));
   TRY(upload(h, &h->GuT_map, P.GuT_map));
+  TRY(upload(h, &h->GTn_rp, P.GTn.rp));
+  TRY(upload(h, &h->GTn_ci, P.GTn.ci));
+  TRY(upload(h, &h->GTn_map, P.GTn_map));
+  TRY(upload(h, &h->ATn_rp, P.ATn.rp));
+  TRY(upload(h, &h->ATn_ci, P.ATn.ci));
+  TRY(upload(h, &h->ATn_map, P.ATn_map));
   // LU
   TRY(upload(h, &h->LU_rp, P.LU.rp));
   TRY(upload(h, &h->LU_ci, P.LU.ci));
@@ -242,6 +249,7 @@ int upload_all(opf_handle* h) {
   TRY(alloc(h, &h->F, (size_t)P.nu * P.nu));
   TRY(alloc(h, &h->Fdinv, (size_t)P.nu));
   TRY(alloc(h, &h->st, ST_WORDS));
+  TRY(alloc(h, &h->pf_ws, (size_t)P.nx + 1));
   TRY(alloc(h, &h->bar, 4));
   CK(launch_set_identity(0, P.nu, h->Zt, h->ldp));
   // launch shapes
@@ -265,8 +273,11 @@ int upload_all(opf_handle* h) {
   return OPF_OK;
 }
 
+}  // namespace
+
+namespace condipm {
 // device status -> OPF code (synchronises the stream); clears the word
-int read_status(opf_handle* h, int* info = nullptr) {
+int read_status(opf_handle* h, int* info) {
   int st[ST_WORDS];
   CK(cudaMemcpyAsync(st, h->st, sizeof(st), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -291,7 +302,47 @@ double* workspace(opf_handle* h, size_t n) {
   return h->ws;
 }
 
-}  // namespace
+// Newton-Raphson on g(x, u) = 0 for x at fixed u (Sec. 4.4): residual, its
+// max-norm on the host, refactorisation of G_x and one solve per iteration.
+int powerflow_impl(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters) {
+  const Plan& P = h->P;
+  double* ws = h->pf_ws;
+  int rc = OPF_ERR_PF_FAILED;
+  int k = 0;
+  for (; k <= max_iter; ++k) {
+    int r = eval_impl(h, x, u, nullptr, nullptr, false);
+    if (r != OPF_OK) { rc = r; break; }
+    double nrm = 0.0;
+    if (launch_absmax(h->s, P.nx, h->g, ws + P.nx) != cudaSuccess ||
+        cudaMemcpyAsync(&nrm, ws + P.nx, sizeof(double), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess) { rc = OPF_ERR_CUDA; break; }
+    if (nrm <= tol) { rc = OPF_OK; break; }
+    if (!(nrm < 1e10) || k == max_iter) break;
+    r = eval_impl(h, x, u, nullptr, nullptr, true);
+    if (r == OPF_OK) r = factor_async(h);
+    if (r == OPF_OK) r = read_status(h, nullptr);
+    if (r == OPF_OK) r = opf_gx_solve(h, 0, h->g, ws, 1);
+    if (r != OPF_OK) { rc = r == OPF_ERR_SINGULAR ? OPF_ERR_PF_FAILED : r; break; }
+    if (launch_axpby(h->s, P.nx, -1.0, ws, 1.0, x, x) != cudaSuccess) { rc = OPF_ERR_CUDA; break; }
+  }
+  cudaStreamSynchronize(h->s);
+  if (iters) *iters = k;
+  h->have_W = false;
+  h->have_condense = false;
+  h->have_factor = false;
+  return rc;
+}
+
+// grad_w L = grad f + G^T lam + A^T y at the last derivative evaluation (device, natural order)
+int lagrangian_gradient(opf_handle* h, const double* lam, const double* y, double* out) {
+  const Plan& P = h->P;
+  CK(cudaMemcpyAsync(out, h->gradf, sizeof(double) * P.nw, cudaMemcpyDeviceToDevice, h->s));
+  if (lam) CK(launch_spmm(h->s, P.nw, h->GTn_rp, h->GTn_ci, h->Gval, h->GTn_map, lam, 1, 1, out, 1, 1, 1, 1.0, 1.0));
+  if (y) CK(launch_spmm(h->s, P.nw, h->ATn_rp, h->ATn_ci, h->Aval, h->ATn_map, y, 1, 1, out, 1, 1, 1, 1.0, 1.0));
+  return OPF_OK;
+}
+}  // namespace condipm
+
 
 // ============================================================================ internals
 namespace condipm {
@@ -763,7 +814,7 @@ int opf_kkt_factor(opf_handle* h, double delta_w, int* fail_col) {
   if (!h || !h->have_condense || !(delta_w >= 0.0)) return OPF_ERR_INVALID_ARG;
   TRY(factor_kred_async(h, delta_w));
   int info = -1;
-  int rc = read_status(h, &info);
+  int rc = condipm::read_status(h, &info);
   if (fail_col) *fail_col = rc == OPF_ERR_NOT_PD ? info : -1;
   h->have_factor = rc == OPF_OK;
   return rc;
@@ -822,33 +873,7 @@ int opf_phase_times(opf_handle* h, double* ms, long long* launches) {
 
 int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters) {
   if (!h || !u || !x || !(tol > 0.0) || max_iter < 0) return OPF_ERR_INVALID_ARG;
-  const Plan& P = h->P;
-  double* ws = nullptr;
-  if (cudaMalloc(&ws, sizeof(double) * (P.nx + 1)) != cudaSuccess) return OPF_ERR_OOM;
-  int rc = OPF_ERR_PF_FAILED;
-  int k = 0;
-  for (; k <= max_iter; ++k) {
-    int r = eval_impl(h, x, u, nullptr, nullptr, false);
-    if (r != OPF_OK) { rc = r; break; }
-    double nrm = 0.0;
-    if (launch_absmax(h->s, P.nx, h->g, ws + P.nx) != cudaSuccess ||
-        cudaMemcpyAsync(&nrm, ws + P.nx, sizeof(double), cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
-        cudaStreamSynchronize(h->s) != cudaSuccess) { rc = OPF_ERR_CUDA; break; }
-    if (nrm <= tol) { rc = OPF_OK; break; }
-    if (!(nrm < 1e10) || k == max_iter) break;
-    r = eval_impl(h, x, u, nullptr, nullptr, true);
-    if (r == OPF_OK) r = opf_gx_factor(h);
-    if (r == OPF_OK) r = opf_gx_solve(h, 0, h->g, ws, 1);
-    if (r != OPF_OK) { rc = r == OPF_ERR_SINGULAR ? OPF_ERR_PF_FAILED : r; break; }
-    if (launch_axpby(h->s, P.nx, -1.0, ws, 1.0, x, x) != cudaSuccess) { rc = OPF_ERR_CUDA; break; }
-  }
-  cudaStreamSynchronize(h->s);
-  cudaFree(ws);
-  if (iters) *iters = k;
-  h->have_W = false;
-  h->have_condense = false;
-  h->have_factor = false;
-  return rc;
+  return condipm::powerflow_impl(h, u, x, tol, max_iter, iters);
 }
 
 }  // extern "C"

@@ -1,0 +1,686 @@
+// Interior-point driver around the device hot path, and the derivative of the
+// optimal dispatch with respect to the bus loads.
+//
+// The outer loop is the primal-dual barrier method of Wachter and Biegler (2006)
+// that the paper defers to (Sec. 4.3): monotone barrier update, fraction to the
+// boundary, bound multipliers eliminated into Sigma, scaled optimality error,
+// y0 = 0, inertia correction by a primal regularisation of the control block
+// until the condensed matrix is positive definite (Theorem 3).  Steps are
+// accepted by backtracking on the l1 exact-penalty merit function (Nocedal and
+// Wright, Sec. 19.4).  As in the paper (Sec. 3, "only the interior-point routines
+// run on the host"), the scalar and vector bookkeeping of the loop is host code;
+// every model evaluation, G_x factorisation, condensation, Cholesky factorisation,
+// step recovery and power-flow projection runs in the library's kernels.
+//   LinRed (Algorithm 1): condensed step of the full-space barrier system.
+//   RedLin (Algorithm 2): Newton-Raphson projection onto g(x, u) = 0 at every
+//     control (Sec. 4.4), adjoint solve for lambda, state bounds as rows -x of
+//     h_r (Eq. reduced:problem); its condensed matrix is the LinRed one with the
+//     bound rows' Sigma in place of Sigma_x.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/condipm.h"
+#include "internal.h"
+
+namespace condipm {
+namespace {
+
+constexpr double TAU_MIN = 0.99, KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5, ETA = 1e-4;
+constexpr double KAPPA_SIGMA = 1e10, SMAX = 100.0;
+
+using Vec = std::vector<double>;
+
+#define CKD(call)                                                                       \
+  do {                                                                                  \
+    if ((call) != cudaSuccess) return OPF_ERR_CUDA;                                      \
+  } while (0)
+#define TRYD(x)                    \
+  do {                             \
+    int r_ = (x);                  \
+    if (r_ != OPF_OK) return r_;   \
+  } while (0)
+
+inline bool finite_bound(double b) { return std::fabs(b) < 1e299; }
+
+// finite-bound bookkeeping of a vector v with lo <= v <= hi
+struct Bounds {
+  Vec lo, hi;
+  std::vector<char> fl, fu;
+  Bounds() = default;
+  Bounds(const Vec& l, const Vec& u) : lo(l), hi(u), fl(l.size()), fu(u.size()) {
+    for (size_t i = 0; i < l.size(); ++i) { fl[i] = finite_bound(l[i]); fu[i] = finite_bound(u[i]); }
+  }
+  size_t n() const { return lo.size(); }
+  double dl(const Vec& v, size_t i) const { return v[i] - lo[i]; }
+  double du(const Vec& v, size_t i) const { return hi[i] - v[i]; }
+  void push(Vec& v) const {   // Ipopt's initial bound push (kappa_1 = kappa_2 = 1e-2)
+    for (size_t i = 0; i < n(); ++i) {
+      double pl = fl[i] ? 1e-2 * std::max(1.0, std::fabs(lo[i])) : 0.0;
+      double pu = fu[i] ? 1e-2 * std::max(1.0, std::fabs(hi[i])) : 0.0;
+      if (fl[i] && fu[i]) { pl = std::min(pl, 1e-2 * (hi[i] - lo[i])); pu = std::min(pu, 1e-2 * (hi[i] - lo[i])); }
+      if (fl[i]) v[i] = std::max(v[i], lo[i] + pl);
+      if (fu[i]) v[i] = std::min(v[i], hi[i] - pu);
+    }
+  }
+  void sigma(const Vec& v, const Vec& zl, const Vec& zu, Vec& out) const {
+    out.assign(n(), 0.0);
+    for (size_t i = 0; i < n(); ++i) {
+      if (fl[i]) out[i] += zl[i] / dl(v, i);
+      if (fu[i]) out[i] += zu[i] / du(v, i);
+    }
+  }
+  double bgrad(const Vec& v, size_t i, double mu) const {
+    double g = 0.0;
+    if (fl[i]) g -= mu / dl(v, i);
+    if (fu[i]) g += mu / du(v, i);
+    return g;
+  }
+  double barrier(const Vec& v, double mu) const {
+    double b = 0.0;
+    for (size_t i = 0; i < n(); ++i) {
+      if (fl[i]) b -= mu * std::log(dl(v, i));
+      if (fu[i]) b -= mu * std::log(du(v, i));
+    }
+    return b;
+  }
+  double max_step(const Vec& v, const Vec& dv, double tau) const {
+    double a = 1.0;
+    for (size_t i = 0; i < n(); ++i) {
+      if (fl[i] && dv[i] < 0) a = std::min(a, -tau * dl(v, i) / dv[i]);
+      if (fu[i] && dv[i] > 0) a = std::min(a, tau * du(v, i) / dv[i]);
+    }
+    return a;
+  }
+  void dz(const Vec& v, const Vec& zl, const Vec& zu, const Vec& dv, double mu, Vec& dzl, Vec& dzu) const {
+    dzl.assign(n(), 0.0);
+    dzu.assign(n(), 0.0);
+    for (size_t i = 0; i < n(); ++i) {
+      if (fl[i]) dzl[i] = mu / dl(v, i) - zl[i] - zl[i] / dl(v, i) * dv[i];
+      if (fu[i]) dzu[i] = mu / du(v, i) - zu[i] + zu[i] / du(v, i) * dv[i];
+    }
+  }
+  void safeguard(const Vec& v, Vec& zl, Vec& zu, double mu) const {
+    for (size_t i = 0; i < n(); ++i) {
+      if (fl[i]) zl[i] = std::min(std::max(zl[i], mu / (KAPPA_SIGMA * dl(v, i))), KAPPA_SIGMA * mu / dl(v, i));
+      else zl[i] = 0.0;
+      if (fu[i]) zu[i] = std::min(std::max(zu[i], mu / (KAPPA_SIGMA * du(v, i))), KAPPA_SIGMA * mu / du(v, i));
+      else zu[i] = 0.0;
+    }
+  }
+  // complementarity max-norm and the multiplier l1 sum / count
+  double compl_inf(const Vec& v, const Vec& zl, const Vec& zu, double mu, double& zsum, long long& zcnt) const {
+    double e = 0.0;
+    for (size_t i = 0; i < n(); ++i) {
+      if (fl[i]) { e = std::max(e, std::fabs(dl(v, i) * zl[i] - mu)); zsum += std::fabs(zl[i]); ++zcnt; }
+      if (fu[i]) { e = std::max(e, std::fabs(du(v, i) * zu[i] - mu)); zsum += std::fabs(zu[i]); ++zcnt; }
+    }
+    return e;
+  }
+};
+
+double max_step_z(const Vec& z, const Vec& dz, const std::vector<char>& mask, double tau) {
+  double a = 1.0;
+  for (size_t i = 0; i < z.size(); ++i)
+    if (mask[i] && dz[i] < 0) a = std::min(a, -tau * z[i] / dz[i]);
+  return a;
+}
+
+double inf_norm(const Vec& v) {
+  double m = 0.0;
+  for (double x : v) m = std::max(m, std::fabs(x));
+  return m;
+}
+double l1_norm(const Vec& v) {
+  double m = 0.0;
+  for (double x : v) m += std::fabs(x);
+  return m;
+}
+
+// Ipopt-style scaled optimality error
+double opt_error(double dual_inf, double primal_inf, double compl_inf, double mult_sum, long long mult_cnt) {
+  const double sd = std::max(SMAX, mult_sum / std::max(1LL, mult_cnt)) / SMAX;
+  return std::max(std::max(dual_inf / sd, primal_inf), compl_inf / sd);
+}
+
+// device scratch for one solve
+struct Dev {
+  double *x = nullptr, *u = nullptr, *lam = nullptr, *y = nullptr, *sig_u = nullptr, *sig_x = nullptr,
+         *sig_s = nullptr, *rhs = nullptr, *step = nullptr, *grad = nullptr, *tmp = nullptr;
+  ~Dev() {
+    for (double* p : {x, u, lam, y, sig_u, sig_x, sig_s, rhs, step, grad, tmp})
+      if (p) cudaFree(p);
+  }
+};
+
+int alloc_dev(Dev& d, const Plan& P) {
+  const int nkkt = P.nw + 2 * P.m + P.nx;
+  auto A = [](double** p, size_t n) { return cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(double)) == cudaSuccess; };
+  if (!A(&d.x, P.nx) || !A(&d.u, P.nu) || !A(&d.lam, P.nx) || !A(&d.y, P.m) || !A(&d.sig_u, P.nu) ||
+      !A(&d.sig_x, P.nx) || !A(&d.sig_s, P.m) || !A(&d.rhs, nkkt) || !A(&d.step, nkkt) || !A(&d.grad, P.nw) ||
+      !A(&d.tmp, std::max(P.nw, P.nx)))
+    return OPF_ERR_OOM;
+  return OPF_OK;
+}
+
+int h2d(cudaStream_t s, double* dst, const double* src, size_t n) {
+  if (n == 0) return OPF_OK;
+  return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, s) == cudaSuccess ? OPF_OK : OPF_ERR_CUDA;
+}
+int d2h(cudaStream_t s, double* dst, const double* src, size_t n) {
+  if (n == 0) return OPF_OK;
+  return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s) == cudaSuccess ? OPF_OK : OPF_ERR_CUDA;
+}
+
+using clk = std::chrono::steady_clock;
+double ms_since(clk::time_point t0) { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); }
+
+// f, g, h at (x, u) (device copies made here)
+int eval_fgh(opf_handle* h, Dev& d, const Vec& w, double& f, Vec& g, Vec& hv) {
+  const Plan& P = h->P;
+  TRYD(h2d(h->s, d.u, w.data(), P.nu));
+  TRYD(h2d(h->s, d.x, w.data() + P.nu, P.nx));
+  TRYD(eval_impl(h, d.x, d.u, nullptr, nullptr, false));
+  g.resize(P.nx);
+  hv.resize(P.m);
+  TRYD(d2h(h->s, &f, h->f, 1));
+  TRYD(d2h(h->s, g.data(), h->g, P.nx));
+  TRYD(d2h(h->s, hv.data(), h->hv, P.m));
+  CKD(cudaStreamSynchronize(h->s));
+  return OPF_OK;
+}
+
+// Cholesky of Kred + delta I with the inertia-correction schedule; delta in/out
+int factor_with_correction(opf_handle* h, double& delta, double delta_last, int& attempts) {
+  attempts = 0;
+  double d = 0.0;
+  for (;;) {
+    TRYD(factor_kred_async(h, d));
+    ++attempts;
+    int rc = read_status(h, nullptr);
+    if (rc == OPF_OK) {
+      h->have_factor = true;
+      delta = d;
+      return OPF_OK;
+    }
+    if (rc != OPF_ERR_NOT_PD) return rc;
+    if (d == 0.0) d = delta_last > 0.0 ? std::max(1e-20, delta_last / 3.0) : 1e-4;
+    else d *= 8.0;
+    if (d > 1e40) return OPF_ERR_NOT_PD;
+  }
+}
+
+// the initial primal point: theta = 0, Vm = 1 at load buses, 1.05 at generator
+// buses (clipped to bounds), non-slack Pg at the middle of its range
+Vec flat_start(const Plan& P) {
+  Vec w(P.nw, 0.0);
+  for (int i = 0; i < P.nb; ++i) w[P.vm_w[i]] = 1.0;
+  for (int k = 0; k < P.ng; ++k) {
+    const int i = P.gbus[k];
+    w[P.vm_w[i]] = std::min(std::max(1.05, P.Vmin[i]), P.Vmax[i]);
+  }
+  for (int k = 1; k < P.ng; ++k) w[P.pg_w[k]] = 0.5 * (P.Pmin[k] + P.Pmax[k]);
+  return w;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ LinRed
+int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
+  const Plan& P = h->P;
+  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
+  const int nkkt = nw + 2 * m + nx;
+  Dev d;
+  TRYD(alloc_dev(d, P));
+  Vec slo(m), shi(m);
+  for (int i = 0; i < m; ++i) { slo[i] = -P.hu[i]; shi[i] = -P.hl[i]; }
+  Bounds bw(P.wl, P.wu), bs(slo, shi);
+  Vec w = flat_start(P);
+  bw.push(w);
+  double f;
+  Vec g, hv;
+  TRYD(eval_fgh(h, d, w, f, g, hv));
+  Vec s(m);
+  for (int i = 0; i < m; ++i) s[i] = -hv[i];
+  bs.push(s);
+  Vec lam(nx, 0.0), y(m, 0.0);
+  Vec zwl(nw), zwu(nw), zsl(m), zsu(m);
+  for (int i = 0; i < nw; ++i) { zwl[i] = bw.fl[i] ? 1.0 : 0.0; zwu[i] = bw.fu[i] ? 1.0 : 0.0; }
+  for (int i = 0; i < m; ++i) { zsl[i] = bs.fl[i] ? 1.0 : 0.0; zsu[i] = bs.fu[i] ? 1.0 : 0.0; }
+  double mu = o.mu0, nu_pen = 1.0, delta = 0.0, err0 = 1e300;
+  Vec grad(nw), gradf(nw), sw, ss, r(nkkt), step(nkkt), dzwl, dzwu, dzsl, dzsu;
+  const auto t_start = clk::now();
+  int it = 0;
+  R.status = OPF_ERR_NO_CONVERGENCE;
+  for (; it <= o.max_iter; ++it) {
+    auto t0 = clk::now();
+    TRYD(h2d(h->s, d.u, w.data(), nu));
+    TRYD(h2d(h->s, d.x, w.data() + nu, nx));
+    TRYD(h2d(h->s, d.lam, lam.data(), nx));
+    TRYD(h2d(h->s, d.y, y.data(), m));
+    TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+    TRYD(lagrangian_gradient(h, d.lam, d.y, d.grad));
+    TRYD(d2h(h->s, &f, h->f, 1));
+    g.resize(nx);
+    hv.resize(m);
+    TRYD(d2h(h->s, g.data(), h->g, nx));
+    TRYD(d2h(h->s, hv.data(), h->hv, m));
+    TRYD(d2h(h->s, grad.data(), d.grad, nw));
+    TRYD(d2h(h->s, gradf.data(), h->gradf, nw));
+    CKD(cudaStreamSynchronize(h->s));
+    R.ms_eval += ms_since(t0);
+    // optimality error (mu = 0) and barrier update
+    double dual = 0.0, primal = 0.0, zsum = 0.0;
+    long long zcnt = 0;
+    for (int i = 0; i < nw; ++i) dual = std::max(dual, std::fabs(grad[i] - zwl[i] + zwu[i]));
+    for (int i = 0; i < m; ++i) dual = std::max(dual, std::fabs(y[i] - zsl[i] + zsu[i]));
+    double pl1 = 0.0;
+    for (int i = 0; i < nx; ++i) { primal = std::max(primal, std::fabs(g[i])); pl1 += std::fabs(g[i]); }
+    for (int i = 0; i < m; ++i) { primal = std::max(primal, std::fabs(hv[i] + s[i])); pl1 += std::fabs(hv[i] + s[i]); }
+    for (double v : lam) zsum += std::fabs(v);
+    for (double v : y) zsum += std::fabs(v);
+    zcnt += nx + m;
+    double zs2 = zsum;
+    long long zc2 = zcnt;
+    double c0 = std::max(bw.compl_inf(w, zwl, zwu, 0.0, zs2, zc2), bs.compl_inf(s, zsl, zsu, 0.0, zs2, zc2));
+    err0 = opt_error(dual, primal, c0, zs2, zc2);
+    if (o.verbose) std::printf("linred it %3d obj %.10f err %.2e mu %.1e inf_pr %.2e delta %.1e\n", it, f, err0, mu, primal, delta);
+    if (err0 <= o.tol) { R.status = OPF_OK; break; }
+    if (it == o.max_iter) break;
+    for (;;) {
+      double zs3 = zsum;
+      long long zc3 = zcnt;
+      double cm = std::max(bw.compl_inf(w, zwl, zwu, mu, zs3, zc3), bs.compl_inf(s, zsl, zsu, mu, zs3, zc3));
+      double errmu = opt_error(dual, primal, cm, zs3, zc3);
+      if (errmu > KAPPA_EPS * mu || mu <= o.tol / 10) break;
+      mu = std::max(o.tol / 10, std::min(KAPPA_MU * mu, std::pow(mu, THETA_MU)));
+    }
+    const double tau = std::max(TAU_MIN, 1.0 - mu);
+    bw.sigma(w, zwl, zwu, sw);
+    bs.sigma(s, zsl, zsu, ss);
+    // condense + factor with inertia correction
+    t0 = clk::now();
+    TRYD(h2d(h->s, d.sig_u, sw.data(), nu));
+    TRYD(h2d(h->s, d.sig_x, sw.data() + nu, nx));
+    TRYD(h2d(h->s, d.sig_s, ss.data(), m));
+    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+    TRYD(read_status(h, nullptr));
+    R.ms_condense += ms_since(t0);
+    t0 = clk::now();
+    int att = 0;
+    TRYD(factor_with_correction(h, delta, delta, att));
+    R.n_factor += att;
+    R.ms_factor += ms_since(t0);
+    // right-hand side and step
+    for (int i = 0; i < nw; ++i) r[i] = grad[i] + bw.bgrad(w, i, mu);
+    for (int i = 0; i < m; ++i) r[nw + i] = y[i] + bs.bgrad(s, i, mu);
+    for (int i = 0; i < nx; ++i) r[nw + m + i] = g[i];
+    for (int i = 0; i < m; ++i) r[nw + m + nx + i] = hv[i] + s[i];
+    Vec pw(nw), ps(m), plam(nx), py(m);
+    double amax = 1.0, az = 1.0, a = 1.0;
+    bool accepted = false;
+    for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
+      t0 = clk::now();
+      TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
+      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1));
+      TRYD(d2h(h->s, step.data(), d.step, nkkt));
+      CKD(cudaStreamSynchronize(h->s));
+      R.ms_solve += ms_since(t0);
+      std::copy(step.begin(), step.begin() + nw, pw.begin());
+      std::copy(step.begin() + nw, step.begin() + nw + m, ps.begin());
+      std::copy(step.begin() + nw + m, step.begin() + nw + m + nx, plam.begin());
+      std::copy(step.begin() + nw + m + nx, step.end(), py.begin());
+      bw.dz(w, zwl, zwu, pw, mu, dzwl, dzwu);
+      bs.dz(s, zsl, zsu, ps, mu, dzsl, dzsu);
+      amax = std::min(bw.max_step(w, pw, tau), bs.max_step(s, ps, tau));
+      az = std::min(std::min(max_step_z(zwl, dzwl, bw.fl, tau), max_step_z(zwu, dzwu, bw.fu, tau)),
+                    std::min(max_step_z(zsl, dzsl, bs.fl, tau), max_step_z(zsu, dzsu, bs.fu, tau)));
+      double mmax = 0.0;
+      for (int i = 0; i < nx; ++i) mmax = std::max(mmax, std::fabs(lam[i] + plam[i]));
+      for (int i = 0; i < m; ++i) mmax = std::max(mmax, std::fabs(y[i] + py[i]));
+      nu_pen = std::max(nu_pen, 1.1 * mmax);
+      const double phi0 = f + bw.barrier(w, mu) + bs.barrier(s, mu) + nu_pen * pl1;
+      double dphi = -nu_pen * pl1;
+      for (int i = 0; i < nw; ++i) dphi += (gradf[i] + bw.bgrad(w, i, mu)) * pw[i];
+      for (int i = 0; i < m; ++i) dphi += bs.bgrad(s, i, mu) * ps[i];
+      t0 = clk::now();
+      a = amax;
+      Vec wt(nw), st2(m);
+      while (a > 1e-4 * amax) {
+        for (int i = 0; i < nw; ++i) wt[i] = w[i] + a * pw[i];
+        for (int i = 0; i < m; ++i) st2[i] = s[i] + a * ps[i];
+        double ft;
+        Vec gt, ht;
+        TRYD(eval_fgh(h, d, wt, ft, gt, ht));
+        double c1 = 0.0;
+        for (double v : gt) c1 += std::fabs(v);
+        for (int i = 0; i < m; ++i) c1 += std::fabs(ht[i] + st2[i]);
+        const double phit = ft + bw.barrier(wt, mu) + bs.barrier(st2, mu) + nu_pen * c1;
+        if (std::isfinite(phit) && phit <= phi0 + ETA * a * std::min(dphi, 0.0)) { accepted = true; break; }
+        a *= 0.5;
+      }
+      R.ms_linesearch += ms_since(t0);
+      if (!accepted) {
+        // backtracking failed: shorten the step by a larger primal regularisation
+        delta = std::max(1e-8, 10.0 * delta);
+        TRYD(factor_kred_async(h, delta));
+        ++R.n_factor;
+        int rc = read_status(h, nullptr);
+        if (rc == OPF_ERR_NOT_PD) { att = 0; TRYD(factor_with_correction(h, delta, delta, att)); R.n_factor += att; }
+        else if (rc != OPF_OK) return rc;
+      }
+    }
+    for (int i = 0; i < nw; ++i) w[i] += a * pw[i];
+    for (int i = 0; i < m; ++i) s[i] += a * ps[i];
+    for (int i = 0; i < nx; ++i) lam[i] += a * plam[i];
+    for (int i = 0; i < m; ++i) y[i] += a * py[i];
+    for (int i = 0; i < nw; ++i) { zwl[i] += az * dzwl[i]; zwu[i] += az * dzwu[i]; }
+    for (int i = 0; i < m; ++i) { zsl[i] += az * dzsl[i]; zsu[i] += az * dzsu[i]; }
+    bw.safeguard(w, zwl, zwu, mu);
+    bs.safeguard(s, zsl, zsu, mu);
+  }
+  R.iters = it;
+  R.obj = f;
+  R.err = err0;
+  R.mu = mu;
+  R.ms_total = ms_since(t_start);
+  // the converged state, kept for the dispatch derivative
+  h->sol_w = w;
+  h->sol_lam = lam;
+  h->sol_y = y;
+  h->sol_s = s;
+  bw.sigma(w, zwl, zwu, h->sol_sig_w);
+  bs.sigma(s, zsl, zsu, h->sol_sig_s);
+  h->sol_mu = mu;
+  h->sol_pg0 = hv.empty() ? 0.0 : hv[0];
+  h->have_solution = true;
+  return OPF_OK;
+}
+
+// ------------------------------------------------------------------ RedLin
+int powerflow_impl(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters);
+
+int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
+  const Plan& P = h->P;
+  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
+  const int nkkt = nw + 2 * m + nx;
+  Dev d;
+  TRYD(alloc_dev(d, P));
+  std::vector<int> xb;   // bounded states (Vm at load buses)
+  for (int j = 0; j < nx; ++j)
+    if (finite_bound(P.wl[nu + j]) || finite_bound(P.wu[nu + j])) xb.push_back(j);
+  const int nbnd = int(xb.size());
+  const int mr = m + nbnd;
+  Vec ulo(P.wl.begin(), P.wl.begin() + nu), uhi(P.wu.begin(), P.wu.begin() + nu);
+  Vec slo(mr), shi(mr);
+  for (int i = 0; i < m; ++i) { slo[i] = -P.hu[i]; shi[i] = -P.hl[i]; }
+  for (int k = 0; k < nbnd; ++k) { slo[m + k] = P.wl[nu + xb[k]]; shi[m + k] = P.wu[nu + xb[k]]; }
+  Bounds bu(ulo, uhi), bs(slo, shi);
+  Vec w = flat_start(P);
+  {
+    Bounds bw(P.wl, P.wu);
+    bw.push(w);
+  }
+  auto project = [&](Vec& wt) -> int {   // x <- NR solution at u (device), from wt's x
+    TRYD(h2d(h->s, d.u, wt.data(), nu));
+    TRYD(h2d(h->s, d.x, wt.data() + nu, nx));
+    int its = 0;
+    auto t0 = clk::now();
+    int rc = powerflow_impl(h, d.u, d.x, o.pf_tol, 30, &its);
+    R.ms_pf += ms_since(t0);
+    if (rc != OPF_OK) return rc;
+    TRYD(d2h(h->s, wt.data() + nu, d.x, nx));
+    CKD(cudaStreamSynchronize(h->s));
+    return OPF_OK;
+  };
+  {
+    int rc = project(w);
+    if (rc != OPF_OK) return rc == OPF_ERR_PF_FAILED ? OPF_ERR_PF_FAILED : rc;
+  }
+  double f;
+  Vec g, hv;
+  TRYD(eval_fgh(h, d, w, f, g, hv));
+  auto hr_of = [&](const Vec& wt, const Vec& hh, Vec& out) {
+    out.resize(mr);
+    for (int i = 0; i < m; ++i) out[i] = hh[i];
+    for (int k = 0; k < nbnd; ++k) out[m + k] = -wt[nu + xb[k]];
+  };
+  Vec hr;
+  hr_of(w, hv, hr);
+  Vec s(mr);
+  for (int i = 0; i < mr; ++i) s[i] = -hr[i];
+  bs.push(s);
+  Vec y(mr, 0.0), lam(nx, 0.0);
+  Vec zul(nu), zuu(nu), zsl(mr), zsu(mr);
+  for (int i = 0; i < nu; ++i) { zul[i] = bu.fl[i] ? 1.0 : 0.0; zuu[i] = bu.fu[i] ? 1.0 : 0.0; }
+  for (int i = 0; i < mr; ++i) { zsl[i] = bs.fl[i] ? 1.0 : 0.0; zsu[i] = bs.fu[i] ? 1.0 : 0.0; }
+  double mu = o.mu0, nu_pen = 1.0, delta = 0.0, err0 = 1e300;
+  Vec grad0(nw), grad(nw), gradf(nw), su, ss, r(nkkt), step(nkkt), t(nx), dzul, dzuu, dzsl, dzsu;
+  const auto t_start = clk::now();
+  int it = 0;
+  R.status = OPF_ERR_NO_CONVERGENCE;
+  for (; it <= o.max_iter; ++it) {
+    auto t0 = clk::now();
+    Vec yh(y.begin(), y.begin() + m);
+    TRYD(h2d(h->s, d.u, w.data(), nu));
+    TRYD(h2d(h->s, d.x, w.data() + nu, nx));
+    TRYD(h2d(h->s, d.y, yh.data(), m));
+    TRYD(eval_impl(h, d.x, d.u, nullptr, nullptr, true));
+    TRYD(lagrangian_gradient(h, nullptr, d.y, d.grad));
+    TRYD(d2h(h->s, grad0.data(), d.grad, nw));
+    TRYD(d2h(h->s, gradf.data(), h->gradf, nw));
+    TRYD(d2h(h->s, &f, h->f, 1));
+    hv.resize(m);
+    TRYD(d2h(h->s, hv.data(), h->hv, m));
+    CKD(cudaStreamSynchronize(h->s));
+    // adjoint step: lambda = -G_x^{-T} (grad_x f + A_x^T y_h - E_b^T y_b)
+    for (int j = 0; j < nx; ++j) t[j] = grad0[nu + j];
+    for (int k = 0; k < nbnd; ++k) t[xb[k]] -= y[m + k];
+    TRYD(factor_async(h));
+    TRYD(read_status(h, nullptr));
+    TRYD(h2d(h->s, d.tmp, t.data(), nx));
+    TRYD(opf_gx_solve(h, 1, d.tmp, d.lam, 1));
+    TRYD(d2h(h->s, lam.data(), d.lam, nx));
+    CKD(cudaStreamSynchronize(h->s));
+    for (double& v : lam) v = -v;
+    TRYD(h2d(h->s, d.lam, lam.data(), nx));
+    // Hessian of the Lagrangian at (lambda, y_h); G_x (and its factors) unchanged
+    TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+    h->have_lu = true;
+    TRYD(lagrangian_gradient(h, d.lam, d.y, d.grad));
+    TRYD(d2h(h->s, grad.data(), d.grad, nw));
+    CKD(cudaStreamSynchronize(h->s));
+    R.ms_eval += ms_since(t0);
+    hr_of(w, hv, hr);
+    double dual = 0.0, primal = 0.0, zsum = 0.0, pl1 = 0.0;
+    long long zcnt = 0;
+    for (int i = 0; i < nu; ++i) dual = std::max(dual, std::fabs(grad[i] - zul[i] + zuu[i]));
+    for (int i = 0; i < mr; ++i) dual = std::max(dual, std::fabs(y[i] - zsl[i] + zsu[i]));
+    for (int i = 0; i < mr; ++i) { primal = std::max(primal, std::fabs(hr[i] + s[i])); pl1 += std::fabs(hr[i] + s[i]); }
+    for (double v : y) zsum += std::fabs(v);
+    zcnt += mr;
+    double zs2 = zsum;
+    long long zc2 = zcnt;
+    Vec uu(w.begin(), w.begin() + nu);
+    double c0 = std::max(bu.compl_inf(uu, zul, zuu, 0.0, zs2, zc2), bs.compl_inf(s, zsl, zsu, 0.0, zs2, zc2));
+    err0 = opt_error(dual, primal, c0, zs2, zc2);
+    if (o.verbose) std::printf("redlin it %3d obj %.10f err %.2e mu %.1e delta %.1e\n", it, f, err0, mu, delta);
+    if (err0 <= o.tol) { R.status = OPF_OK; break; }
+    if (it == o.max_iter) break;
+    for (;;) {
+      double zs3 = zsum;
+      long long zc3 = zcnt;
+      double cm = std::max(bu.compl_inf(uu, zul, zuu, mu, zs3, zc3), bs.compl_inf(s, zsl, zsu, mu, zs3, zc3));
+      double errmu = opt_error(dual, primal, cm, zs3, zc3);
+      if (errmu > KAPPA_EPS * mu || mu <= o.tol / 10) break;
+      mu = std::max(o.tol / 10, std::min(KAPPA_MU * mu, std::pow(mu, THETA_MU)));
+    }
+    const double tau = std::max(TAU_MIN, 1.0 - mu);
+    bu.sigma(uu, zul, zuu, su);
+    bs.sigma(s, zsl, zsu, ss);
+    Vec sigx(nx, 0.0);
+    for (int k = 0; k < nbnd; ++k) sigx[xb[k]] = ss[m + k];
+    t0 = clk::now();
+    TRYD(h2d(h->s, d.sig_u, su.data(), nu));
+    TRYD(h2d(h->s, d.sig_x, sigx.data(), nx));
+    TRYD(h2d(h->s, d.sig_s, ss.data(), m));
+    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+    TRYD(read_status(h, nullptr));
+    R.ms_condense += ms_since(t0);
+    t0 = clk::now();
+    int att = 0;
+    TRYD(factor_with_correction(h, delta, delta, att));
+    R.n_factor += att;
+    R.ms_factor += ms_since(t0);
+    // reduced right-hand sides in the full-space layout (r4 = 0)
+    Vec r2b(nbnd), r3b(nbnd);
+    for (int k = 0; k < nbnd; ++k) {
+      r2b[k] = y[m + k] + bs.bgrad(s, m + k, mu);
+      r3b[k] = hr[m + k] + s[m + k];
+    }
+    std::fill(r.begin(), r.end(), 0.0);
+    for (int i = 0; i < nu; ++i) r[i] = grad[i] + bu.bgrad(uu, i, mu);
+    for (int k = 0; k < nbnd; ++k) r[nu + xb[k]] = -(ss[m + k] * r3b[k] - r2b[k]);
+    for (int i = 0; i < m; ++i) r[nw + i] = y[i] + bs.bgrad(s, i, mu);
+    for (int i = 0; i < m; ++i) r[nw + m + nx + i] = hv[i] + s[i];
+    Vec pu(nu), px(nx), ps(mr), py(mr);
+    double amax = 1.0, az = 1.0, a = 1.0;
+    bool accepted = false;
+    Vec wn;
+    for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
+      t0 = clk::now();
+      TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
+      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1));
+      TRYD(d2h(h->s, step.data(), d.step, nkkt));
+      CKD(cudaStreamSynchronize(h->s));
+      R.ms_solve += ms_since(t0);
+      std::copy(step.begin(), step.begin() + nu, pu.begin());
+      std::copy(step.begin() + nu, step.begin() + nw, px.begin());
+      for (int i = 0; i < m; ++i) { ps[i] = step[nw + i]; py[i] = step[nw + m + nx + i]; }
+      for (int k = 0; k < nbnd; ++k) {
+        ps[m + k] = px[xb[k]] - r3b[k];
+        py[m + k] = ss[m + k] * (-px[xb[k]] + r3b[k]) - r2b[k];
+      }
+      bu.dz(uu, zul, zuu, pu, mu, dzul, dzuu);
+      bs.dz(s, zsl, zsu, ps, mu, dzsl, dzsu);
+      amax = std::min(bu.max_step(uu, pu, tau), bs.max_step(s, ps, tau));
+      az = std::min(std::min(max_step_z(zul, dzul, bu.fl, tau), max_step_z(zuu, dzuu, bu.fu, tau)),
+                    std::min(max_step_z(zsl, dzsl, bs.fl, tau), max_step_z(zsu, dzsu, bs.fu, tau)));
+      double mmax = 0.0;
+      for (int i = 0; i < mr; ++i) mmax = std::max(mmax, std::fabs(y[i] + py[i]));
+      nu_pen = std::max(nu_pen, 1.1 * mmax);
+      const double phi0 = f + bu.barrier(uu, mu) + bs.barrier(s, mu) + nu_pen * pl1;
+      double dphi = -nu_pen * pl1;
+      for (int i = 0; i < nu; ++i) dphi += (gradf[i] + bu.bgrad(uu, i, mu)) * pu[i];
+      for (int j = 0; j < nx; ++j) dphi += gradf[nu + j] * px[j];
+      for (int i = 0; i < mr; ++i) dphi += bs.bgrad(s, i, mu) * ps[i];
+      t0 = clk::now();
+      a = amax;
+      Vec st2(mr), hrt;
+      while (a > 1e-4 * amax) {
+        Vec wt = w;
+        for (int i = 0; i < nu; ++i) wt[i] = w[i] + a * pu[i];
+        for (int j = 0; j < nx; ++j) wt[nu + j] = w[nu + j] + a * px[j];
+        for (int i = 0; i < mr; ++i) st2[i] = s[i] + a * ps[i];
+        int rc = project(wt);
+        if (rc == OPF_OK) {
+          double ft;
+          Vec gt, ht;
+          TRYD(eval_fgh(h, d, wt, ft, gt, ht));
+          hr_of(wt, ht, hrt);
+          double c1 = 0.0;
+          for (int i = 0; i < mr; ++i) c1 += std::fabs(hrt[i] + st2[i]);
+          Vec ut(wt.begin(), wt.begin() + nu);
+          const double phit = ft + bu.barrier(ut, mu) + bs.barrier(st2, mu) + nu_pen * c1;
+          if (std::isfinite(phit) && phit <= phi0 + ETA * a * std::min(dphi, 0.0)) {
+            accepted = true;
+            wn = wt;
+            break;
+          }
+        } else if (rc != OPF_ERR_PF_FAILED && rc != OPF_ERR_SINGULAR) {
+          return rc;
+        }
+        a *= 0.5;
+      }
+      R.ms_linesearch += ms_since(t0);
+      if (!accepted) {
+        delta = std::max(1e-8, 10.0 * delta);
+        TRYD(factor_kred_async(h, delta));
+        ++R.n_factor;
+        int rc = read_status(h, nullptr);
+        if (rc == OPF_ERR_NOT_PD) { att = 0; TRYD(factor_with_correction(h, delta, delta, att)); R.n_factor += att; }
+        else if (rc != OPF_OK) return rc;
+      }
+    }
+    if (!accepted) { R.status = OPF_ERR_NO_CONVERGENCE; break; }
+    w = wn;
+    for (int i = 0; i < mr; ++i) { s[i] += a * ps[i]; y[i] += a * py[i]; }
+    for (int i = 0; i < nu; ++i) { zul[i] += az * dzul[i]; zuu[i] += az * dzuu[i]; }
+    for (int i = 0; i < mr; ++i) { zsl[i] += az * dzsl[i]; zsu[i] += az * dzsu[i]; }
+    Vec un(w.begin(), w.begin() + nu);
+    bu.safeguard(un, zul, zuu, mu);
+    bs.safeguard(s, zsl, zsu, mu);
+  }
+  R.iters = it;
+  R.obj = f;
+  R.err = err0;
+  R.mu = mu;
+  R.ms_total = ms_since(t_start);
+  // the converged state in the full-space form: state-bound rows become Sigma_x
+  h->sol_w = w;
+  h->sol_lam = lam;
+  h->sol_y.assign(y.begin(), y.begin() + m);
+  h->sol_s.assign(s.begin(), s.begin() + m);
+  Vec uu(w.begin(), w.begin() + nu);
+  bu.sigma(uu, zul, zuu, su);
+  bs.sigma(s, zsl, zsu, ss);
+  h->sol_sig_w.assign(nw, 0.0);
+  for (int i = 0; i < nu; ++i) h->sol_sig_w[i] = su[i];
+  for (int k = 0; k < nbnd; ++k) h->sol_sig_w[nu + xb[k]] = ss[m + k];
+  h->sol_sig_s.assign(ss.begin(), ss.begin() + m);
+  h->sol_mu = mu;
+  h->sol_pg0 = hv.empty() ? 0.0 : hv[0];
+  h->have_solution = true;
+  return OPF_OK;
+}
+
+}  // namespace condipm
+
+using namespace condipm;
+
+extern "C" int opf_solve(opf_handle* h, const opf_ipm_options* opt, opf_ipm_result* res) {
+  if (!h || !res) return OPF_ERR_INVALID_ARG;
+  opf_ipm_options o{};
+  o.variant = OPF_LINRED;
+  o.tol = 1e-8;
+  o.max_iter = 300;
+  o.mu0 = 0.1;
+  o.pf_tol = 1e-10;
+  if (opt) o = *opt;
+  if (!(o.tol > 0) || o.max_iter < 0 || !(o.mu0 > 0) || !(o.pf_tol > 0) ||
+      (o.variant != OPF_LINRED && o.variant != OPF_REDLIN))
+    return OPF_ERR_INVALID_ARG;
+  *res = opf_ipm_result{};
+  h->have_solution = false;
+  const int rc = o.variant == OPF_LINRED ? ipm_linred(h, o, *res) : ipm_redlin(h, o, *res);
+  if (rc != OPF_OK) { res->status = rc; return rc; }
+  return res->status;
+}
+
+extern "C" int opf_get_solution(const opf_handle* h, double* w, double* lam, double* y, double* Pg) {
+  if (!h || !h->have_solution) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  if (w) std::copy(h->sol_w.begin(), h->sol_w.end(), w);
+  if (lam) std::copy(h->sol_lam.begin(), h->sol_lam.end(), lam);
+  if (y) std::copy(h->sol_y.begin(), h->sol_y.end(), y);
+  if (Pg) {
+    // Pg of the slack generator from the slack row of h at the solution
+    for (int k = 1; k < P.ng; ++k) Pg[k] = h->sol_w[P.pg_w[k]];
+    Pg[0] = h->sol_pg0;
+  }
+  return OPF_OK;
+}

@@ -39,6 +39,8 @@ struct opf_handle {
   int *AT_rp = nullptr, *AT_ci = nullptr, *AT_map = nullptr;
   int *PGu_rp = nullptr, *PGu_ci = nullptr, *PGu_map = nullptr;
   int *GuT_rp = nullptr, *GuT_ci = nullptr, *GuT_map = nullptr;
+  int *GTn_rp = nullptr, *GTn_ci = nullptr, *GTn_map = nullptr;
+  int *ATn_rp = nullptr, *ATn_ci = nullptr, *ATn_map = nullptr;
   // LU
   int *LU_rp = nullptr, *LU_ci = nullptr, *LU_diag = nullptr, *Gx_to_LU = nullptr, *upd_pos = nullptr;
   long long* upd_ptr = nullptr;
@@ -84,6 +86,12 @@ struct opf_handle {
   // call-order state
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   double delta_w = 0.0;
+  double* pf_ws = nullptr;       // power-flow step and norm (nx + 1)
+  // converged state of the last opf_solve (host), full-space form
+  bool have_solution = false;
+  std::vector<double> sol_w, sol_lam, sol_y, sol_s, sol_sig_w, sol_sig_s;
+  double sol_mu = 0.0, sol_pg0 = 0.0;
+  bool sens_ready = false;       // K_aug at the solution factored for opf_dispatch_vjp
   // phase timing (opf_profile)
   bool profiling = false;
   struct PhaseRec { int phase; cudaEvent_t a, b; };

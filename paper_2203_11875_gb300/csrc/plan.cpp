@@ -858,6 +858,25 @@ std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double*
       P.Knat_rp[wv + 1] = int(P.Knat_ci.size());
     }
   }
+  // ---------------------------------------------------------------- G^T, A^T (natural order)
+  {
+    auto transpose = [&](const CSR& M, CSR& T, std::vector<int>& map) {
+      std::vector<std::vector<std::pair<int, int>>> rw(nw);
+      for (int rr = 0; rr < M.nrows; ++rr)
+        for (int q = M.rp[rr]; q < M.rp[rr + 1]; ++q) rw[M.ci[q]].push_back({rr, q});
+      T.nrows = nw;
+      T.ncols = M.nrows;
+      T.rp.assign(nw + 1, 0);
+      T.ci.clear();
+      map.clear();
+      for (int c = 0; c < nw; ++c) {
+        T.rp[c + 1] = T.rp[c] + int(rw[c].size());
+        for (auto& p2 : rw[c]) { T.ci.push_back(p2.first); map.push_back(p2.second); }
+      }
+    };
+    transpose(P.G, P.GTn, P.GTn_map);
+    transpose(P.A, P.ATn, P.ATn_map);
+  }
   // ---------------------------------------------------------------- A in c-order, A^T
   {
     P.A_ci_c.resize(P.A.nnz());

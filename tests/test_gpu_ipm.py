@@ -1,0 +1,48 @@
+"""End-to-end interior-point solves through the C ABI (opf_solve) against the
+CPU oracle's IPM: final objective to 1e-6 relative, power balance at the
+converged point (LinRed) and along the path (RedLin), both variants."""
+import numpy as np
+import pytest
+
+import gridgen
+from oracle import ipm, model
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL_OBJ = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2203_11875_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000"])
+@pytest.mark.parametrize("variant", ["linred", "redlin"])
+def test_solve_matches_oracle(pkg, name, variant):
+    net = gridgen.WORKLOADS[name]()
+    lay = model.Layout(net)
+    ref = getattr(ipm, variant)(net)
+    assert ref.status == "converged"
+    h = pkg.Handle(net)
+    res = h.solve(variant)
+    assert res["status"] == 0, res
+    assert abs(res["obj"] - ref.obj) <= TOL_OBJ * abs(ref.obj)
+    w, lam, y, pg = h.solution()
+    g = model.cons_g(lay, w)
+    assert np.abs(g).max() <= (1e-10 if variant == "redlin" else 1e-8)
+    pg_ref, _ = model.dispatch(lay, w)
+    np.testing.assert_allclose(pg, pg_ref, rtol=0, atol=1e-8)
+    assert abs(model.objective(lay, w) - res["obj"]) <= 1e-9 * abs(res["obj"])
+
+
+def test_variants_agree_on_grid2000(pkg):
+    net = gridgen.grid2000()
+    a = pkg.Handle(net).solve("linred")
+    b = pkg.Handle(net).solve("redlin")
+    assert a["status"] == b["status"] == 0
+    assert abs(a["obj"] - b["obj"]) <= TOL_OBJ * abs(a["obj"])
