@@ -205,6 +205,58 @@ int opf_solve(opf_handle* h, const opf_ipm_options* opt, opf_ipm_result* res);
  * lam[nx], y[m], Pg[ng] (every generator, slack included). */
 int opf_get_solution(const opf_handle* h, double* w, double* lam, double* y, double* Pg);
 
+/* ---- A13: derivative of the optimal dispatch with respect to the bus loads ------ */
+/* The paper stops at the Newton step; this extension reuses its recoveries
+ * (Theorems 1 and 2, Sec. 3.3) for the implicit-function derivative of the
+ * barrier solution F(xi; d) = 0 at fixed mu (bound multipliers eliminated into
+ * Sigma), d = (Pd, Qd):
+ *   dPg/dd = dPg/dd|direct - J_out K_aug^{-1} dF/dd,   J_out = dPg/dxi,
+ * with K_aug of Eq. kktmatrix:normal at the point, delta_w = delta_c = 0. */
+
+/* Replace the bus loads Pd[nb], Qd[nb] (host, p.u.) used by every later
+ * evaluation and solve; the library copies them.  Drops the factors and the
+ * stored solution.  Errors: INVALID_ARG (NULL or non-finite entry). */
+int opf_set_loads(opf_handle* h, const double* Pd, const double* Qd);
+
+/* Build K_aug at a barrier KKT point and factor it for opf_dispatch_vjp:
+ * evaluates the derivatives at (w, lam, y), refactors G_x, condenses with
+ * (sig_w, sig_s) and factors Kred with delta_w = 0.  Host arrays, natural
+ * order: w[nw] = [u; x], lam[nx], y[m], sig_w[nw] = [Sigma_u; Sigma_x], sig_s[m].
+ * All five NULL: the last successful opf_solve's solution, first moved onto the
+ * barrier solution at its final mu by Newton's method at that fixed mu (the IPM
+ * stops at its tolerance, short of that point; full steps cut by the
+ * fraction-to-the-boundary rule, refined K_aug solves, residual <= 1e-12 or
+ * until it stops falling; on failure the IPM's point is kept).  A RedLin
+ * solution is used in its full-space form: the state-bound rows' slacks and
+ * multipliers become the bounds of x.  Any later evaluate / condense / factor
+ * call drops the preparation.
+ * Errors: INVALID_ARG (no stored solution, or some but not all pointers NULL),
+ * NOT_PD (Kred not positive definite at the point: K_aug has the wrong inertia,
+ * Theorem 3, and the derivative of the barrier solution is not defined there),
+ * SINGULAR, CUDA, TIMEOUT. */
+int opf_vjp_prepare(opf_handle* h, const double* w, const double* lam, const double* y,
+                    const double* sig_w, const double* sig_s);
+
+/* Vector-Jacobian products of the optimal dispatch Pg[ng] (every generator,
+ * slack included; generator 0 is the slack) for k cotangents:
+ *   grad_Pd[j][i] = sum_g vbar[j][g] dPg_g/dPd_i,  grad_Qd likewise.
+ * Device arrays, row-major: vbar[k][ng] in, grad_Pd[k][nb] and grad_Qd[k][nb]
+ * out (caller-owned; may not overlap vbar).  zeta = K_aug^{-1} J_out^T vbar comes
+ * from the condensed solve (one Cholesky solve with Kred and three multi-RHS
+ * solves with G_x, all k at once), then iterative refinement against the full
+ * sparse K_aug (each correction: one Cholesky and four G_x solves) until the
+ * residual reaches rounding level or stops falling, at most 4 corrections: at
+ * a converged point Sigma spans many orders of magnitude and Kred's condition
+ * number grows like 1/mu.  Synchronises the handle's stream.
+ * Errors: INVALID_ARG (not prepared, k < 0, NULL with k > 0), CUDA, OOM, TIMEOUT. */
+int opf_dispatch_vjp(opf_handle* h, const double* vbar, int k, double* grad_Pd, double* grad_Qd);
+/* Refinement corrections taken by the last opf_dispatch_vjp and its final
+ * residual max|b - K_aug zeta| / max|b|; Newton iterations of the last polish of
+ * the stored solution (-1: it failed) and its final barrier KKT residual.
+ * Outputs may be NULL. */
+int opf_vjp_info(const opf_handle* h, int* refine_steps, double* rel_residual, int* polish_iters,
+                 double* kkt_residual);
+
 /* ---- dense Cholesky without device allocation ----------------------------------- */
 /* The paper has no counterpart to this call.  It serves callers that cannot
  * allocate device memory where they need a factorisation -- a loop running under

@@ -81,6 +81,10 @@ _SIGS = {
     "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
     "opf_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result)]),
     "opf_get_solution": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_set_loads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_vjp_prepare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_dispatch_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "opf_vjp_info": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_double), _ip, C.POINTER(C.c_double)]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
     "opf_launch_count": (C.c_ulonglong, []),
     "opf_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -179,6 +183,7 @@ class Handle:
         _check(lib.opf_sizes(h, C.byref(nx), C.byref(nu), C.byref(m)), "opf_sizes")
         self.nx, self.nu, self.m = nx.value, nu.value, m.value
         self.nw = self.nx + self.nu
+        self.nb, self.ng = int(net.nb), int(net.ng)
         self.n_kkt = self.nw + 2 * self.m + self.nx
 
     def close(self):
@@ -270,6 +275,7 @@ class Handle:
         r = opf_ipm_result()
         rc = self._lib.opf_solve(self._h, C.byref(o), C.byref(r))
         out = {f: getattr(r, f) for f, _ in opf_ipm_result._fields_}
+        self.last_result = out
         if rc not in (OPF_OK, -8):
             raise OPFError(rc, "opf_solve")
         return out
@@ -284,6 +290,36 @@ class Handle:
                                           y.ctypes.data_as(C.c_void_p), pg.ctypes.data_as(C.c_void_p)),
                "opf_get_solution")
         return w, lam, y, pg
+
+    def set_loads(self, Pd, Qd):
+        """opf_set_loads: host arrays of nb loads (the library copies them)."""
+        Pd = np.ascontiguousarray(Pd, dtype=np.float64)
+        Qd = np.ascontiguousarray(Qd, dtype=np.float64)
+        if Pd.shape != (self.nb,) or Qd.shape != (self.nb,):
+            raise ValueError(f"expected Pd, Qd of shape ({self.nb},)")
+        _check(self._lib.opf_set_loads(self._h, Pd.ctypes.data_as(C.c_void_p), Qd.ctypes.data_as(C.c_void_p)),
+               "opf_set_loads")
+
+    def vjp_prepare(self, w=None, lam=None, y=None, sig_w=None, sig_s=None):
+        """opf_vjp_prepare: factor K_aug at the given point (host arrays) or, with
+        no arguments, at the last solve's solution."""
+        args = [w, lam, y, sig_w, sig_s]
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in args]
+        ptrs = [None if a is None else a.ctypes.data_as(C.c_void_p) for a in keep]
+        _check(self._lib.opf_vjp_prepare(self._h, *ptrs), "opf_vjp_prepare")
+
+    def dispatch_vjp(self, vbar, grad_Pd, grad_Qd):
+        """opf_dispatch_vjp: vbar (k, ng) -> grad_Pd, grad_Qd (k, nb), device tensors."""
+        k = 0 if vbar.numel() == 0 else vbar.shape[0]
+        _check(self._lib.opf_dispatch_vjp(self._h, _ptr(vbar), int(k), _ptr(grad_Pd), _ptr(grad_Qd)),
+               "opf_dispatch_vjp")
+
+    def vjp_info(self):
+        """dict: refinement corrections and relative residual of the last
+        dispatch_vjp; Newton iterations and KKT residual of the last polish."""
+        n, r, pi, pr = C.c_int(), C.c_double(), C.c_int(), C.c_double()
+        _check(self._lib.opf_vjp_info(self._h, C.byref(n), C.byref(r), C.byref(pi), C.byref(pr)), "opf_vjp_info")
+        return dict(refine_steps=n.value, rel_residual=r.value, polish_iters=pi.value, kkt_residual=pr.value)
 
     def profile(self, enable=True):
         _check(self._lib.opf_profile(self._h, int(bool(enable))), "opf_profile")

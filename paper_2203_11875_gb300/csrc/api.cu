@@ -175,6 +175,12 @@ int upload_all(opf_handle* h) {
   TRY(upload(h, &h->GuT_rp, P.GuT.rp));
   TRY(upload(h, &h->GuT_ci, P.GuT.ci));
   TRY(upload(h, &h->GuT_map, P.GuT_map));
+  TRY(upload(h, &h->Gc_rp, P.Gc.rp));
+  TRY(upload(h, &h->Gc_ci, P.Gc.ci));
+  TRY(upload(h, &h->Gc_map, P.Gc_map));
+  TRY(upload(h, &h->GcT_rp, P.GcT.rp));
+  TRY(upload(h, &h->GcT_ci, P.GcT.ci));
+  TRY(upload(h, &h->GcT_map, P.GcT_map));
   TRY(upload(h, &h->GTn_rp, P.GTn.rp));
   TRY(upload(h, &h->GTn_ci, P.GTn.ci));
   TRY(upload(h, &h->GTn_map, P.GTn_map));
@@ -370,6 +376,7 @@ int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam
   }
   h->have_eval = true;
   h->have_W = lam && y;
+  h->sens_ready = false;
   h->have_lu = false;
   h->have_condense = false;
   h->have_factor = false;
@@ -402,8 +409,7 @@ int factor_async(opf_handle* h) {
 }
 
 // X (perm space, n x ncols, element (i, c) at X[i*xr + c*xc]) <- (LU)^{-1} X or (LU)^{-T} X
-int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols,
-                  bool timed = false) {
+int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols, bool timed) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const double* lov = trans ? h->Ut_val : h->Lo_val;
@@ -520,6 +526,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   }
   h->have_condense = true;
   h->have_factor = false;
+  h->sens_ready = false;
   return OPF_OK;
 }
 
@@ -531,73 +538,7 @@ int factor_kred_async(opf_handle* h, double delta_w) {
   CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, h->chol_blocks));
   ph_end(h);
   h->delta_w = delta_w;
-  return OPF_OK;
-}
-
-// K_aug p = -r for k right-hand sides (col-major n_kkt x k in, col-major out)
-int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k) {
-  const Plan& P = h->P;
-  cudaStream_t s = h->s;
-  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
-  const int N = nw + 2 * m + nx;
-  double* ws = workspace(h, (size_t)k * (6 * (size_t)nw + 8 * (size_t)m + 3 * (size_t)nx + 8));
-  if (!ws) return OPF_ERR_OOM;
-  double* R12 = ws;                      // nw x k (c-order)
-  double* R3 = R12 + (size_t)nw * k;     // m x k
-  double* R5 = R3 + (size_t)m * k;       // m x k
-  double* R4 = R5 + (size_t)m * k;       // nx x k (perm)
-  double* T = R4 + (size_t)nx * k;       // m x k
-  double* C = T + (size_t)m * k;         // nw x k
-  double* D0 = C + (size_t)nw * k;       // nw x k
-  double* Bv = D0 + (size_t)nw * k;      // nw x k
-  double* Pc = Bv + (size_t)nw * k;      // nw x k
-  double* Tm = Pc + (size_t)nw * k;      // m x k
-  double* Vb = Tm + (size_t)m * k;       // nw x k (rows nu.. used)
-  double* Ps = Vb + (size_t)nw * k;      // m x k
-  double* Py = Ps + (size_t)m * k;       // m x k
-  // gather the right-hand side blocks
-  CK(launch_permute_rows(s, nw, k, h->c2w, rhs, N, 1, R12, k, 0, 1.0, 0));
-  CK(launch_permute_rows(s, m, k, nullptr, rhs + nw, N, 1, R3, k, 0, 1.0, 0));
-  CK(launch_permute_rows(s, nx, k, h->perm, rhs + nw + m, N, 1, R4, k, 0, 1.0, 0));
-  CK(launch_permute_rows(s, m, k, nullptr, rhs + nw + m + nx, N, 1, R5, k, 0, 1.0, 0));
-  // T = Sigma_s r5 - r3 ; C = A^T T
-  CK(launch_scale_rows(s, m, k, h->sig_s, R5, T, -1.0, R3));
-  CK(launch_spmm(s, nw, h->AT_rp, h->AT_ci, h->Aval, h->AT_map, T, k, 1, C, k, 1, k, 1.0, 0.0));
-  // D0 = [0; q],  q = -G_x^{-1} r4
-  CK(cudaMemsetAsync(D0, 0, sizeof(double) * (size_t)nu * k, s));
-  CK(launch_axpby(s, (long long)nx * k, -1.0, R4, 0.0, nullptr, D0 + (size_t)nu * k));
-  TRY(lu_solve_perm(h, 0, D0 + (size_t)nu * k, k, 1, k));
-  // b = [r1; r2] + K D0 + C
-  CK(launch_axpby(s, (long long)nw * k, 1.0, R12, 1.0, C, Bv));
-  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, D0, k, 1, Bv, k, 1, k, 1.0, 1.0));
-  // rhs_u = -(b_u - G_u^T G_x^{-T} b_x)
-  TRY(lu_solve_perm(h, 1, Bv + (size_t)nu * k, k, 1, k));
-  CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Bv + (size_t)nu * k, k, 1, Bv, k, 1, k,
-                 -1.0, 1.0));
-  CK(launch_axpby(s, (long long)nu * k, -1.0, Bv, 0.0, nullptr, Pc));
-  // p_u = (L L^T)^{-1} rhs_u
-  CK(launch_chol_solve(s, nu, h->F, h->Fdinv, Pc, k));
-  // p_x = -G_x^{-1} (r4 + G_u p_u)
-  double* Px = Pc + (size_t)nu * k;
-  CK(cudaMemcpyAsync(Px, R4, sizeof(double) * (size_t)nx * k, cudaMemcpyDeviceToDevice, s));
-  CK(launch_spmm(s, nx, h->PGu_rp, h->PGu_ci, h->Gval, h->PGu_map, Pc, k, 1, Px, k, 1, k, 1.0, 1.0));
-  TRY(lu_solve_perm(h, 0, Px, k, 1, k));
-  CK(launch_axpby(s, (long long)nx * k, -1.0, Px, 0.0, nullptr, Px));
-  // t = A p + r5 ; p_s = -t ; p_y = Sigma_s t - r3
-  CK(cudaMemcpyAsync(Tm, R5, sizeof(double) * (size_t)m * k, cudaMemcpyDeviceToDevice, s));
-  CK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, Pc, k, 1, Tm, k, 1, k, 1.0, 1.0));
-  CK(launch_axpby(s, (long long)m * k, -1.0, Tm, 0.0, nullptr, Ps));
-  CK(launch_scale_rows(s, m, k, h->sig_s, Tm, Py, -1.0, R3));
-  // p_lambda = -G_x^{-T} (r2 + [K p]_x + C_x)
-  double* Vx = Vb + (size_t)nu * k;
-  CK(launch_axpby(s, (long long)nx * k, 1.0, R12 + (size_t)nu * k, 1.0, C + (size_t)nu * k, Vx));
-  CK(launch_spmm(s, nx, h->K_rp + nu, h->K_ci, h->Kval, nullptr, Pc, k, 1, Vx, k, 1, k, 1.0, 1.0));
-  TRY(lu_solve_perm(h, 1, Vx, k, 1, k));
-  // scatter the step back: [p_u | p_x] (c-order), p_s, p_lambda (perm), p_y
-  CK(launch_permute_rows(s, nw, k, h->c2w, Pc, k, 0, step, N, 1, 1.0, 1));
-  CK(launch_permute_rows(s, m, k, nullptr, Ps, k, 0, step + nw, N, 1, 1.0, 0));
-  CK(launch_permute_rows(s, nx, k, h->perm, Vx, k, 0, step + nw + m, N, 1, -1.0, 1));
-  CK(launch_permute_rows(s, m, k, nullptr, Py, k, 0, step + nw + m + nx, N, 1, 1.0, 0));
+  h->sens_ready = false;
   return OPF_OK;
 }
 
@@ -829,7 +770,7 @@ int opf_get_factor(opf_handle* h, double* dst) {
 
 int opf_kkt_solve(opf_handle* h, const double* rhs, double* step, int nrhs) {
   if (!h || !rhs || !step || nrhs < 1 || !h->have_factor) return OPF_ERR_INVALID_ARG;
-  TRY(kkt_solve_impl(h, rhs, step, nrhs));
+  TRY(kkt_solve_impl(h, rhs, step, nrhs, 0));
   CK(cudaStreamSynchronize(h->s));
   return OPF_OK;
 }

@@ -8,10 +8,36 @@ int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam
 int factor_async(opf_handle* h);
 int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s);
 int factor_kred_async(opf_handle* h, double delta_w);
-int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k);
+// K_aug p = -r (external layout), with up to `refine` refinement corrections
+int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int refine);
+int polish_solution(opf_handle* h, double tol, int max_iter);
+
+// k right-hand sides of K_aug in the internal layout (row-major, k lanes): the w
+// block in c-order, s and y natural, lambda in elimination order; contiguous
+// blocks [w | s | l | y] when made by kb_at.
+struct KB {
+  double *w = nullptr, *s = nullptr, *l = nullptr, *y = nullptr;
+};
+size_t kkt_rows(const Plan& P);
+size_t kkt_core_scratch(const Plan& P);
+size_t kkt_refine_scratch(const Plan& P, int k);
+KB kb_at(const Plan& P, double* base, int k);
+// p = K_aug^{-1} b through the condensed system (b_l = 0 may be declared)
+int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, double* scratch);
+// R = b - K_aug z with the full sparse K_aug
+int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R);
+// z <- refined solution of K_aug z = b (solve_first: start from the condensed
+// solve, else from z); at most max_steps corrections; relative max-norm residual
+// and the corrections taken are returned
+int kkt_refine(opf_handle* h, int k, const KB& b, const KB& z, bool solve_first, bool bl_zero, int max_steps,
+               double* scratch, double* final_res, int* steps);
 int read_status(opf_handle* h, int* info = nullptr);
 double* workspace(opf_handle* h, size_t n);
 int lagrangian_gradient(opf_handle* h, const double* lam, const double* y, double* out);
+int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols,
+                  bool timed = false);
+int sens_prepare(opf_handle* h, const double* w, const double* lam, const double* y, const double* sig_w,
+                 const double* sig_s);
 int powerflow_impl(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters);
 
 }  // namespace condipm

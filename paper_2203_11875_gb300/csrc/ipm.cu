@@ -326,7 +326,7 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
     for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
       t0 = clk::now();
       TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
-      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1));
+      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
       TRYD(d2h(h->s, step.data(), d.step, nkkt));
       CKD(cudaStreamSynchronize(h->s));
       R.ms_solve += ms_since(t0);
@@ -395,9 +395,14 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   h->sol_s = s;
   bw.sigma(w, zwl, zwu, h->sol_sig_w);
   bs.sigma(s, zsl, zsu, h->sol_sig_s);
+  h->sol_zwl = zwl;
+  h->sol_zwu = zwu;
+  h->sol_zsl = zsl;
+  h->sol_zsu = zsu;
   h->sol_mu = mu;
   h->sol_pg0 = hv.empty() ? 0.0 : hv[0];
   h->have_solution = true;
+  h->polished = false;
   return OPF_OK;
 }
 
@@ -554,7 +559,7 @@ int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
     for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
       t0 = clk::now();
       TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
-      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1));
+      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
       TRYD(d2h(h->s, step.data(), d.step, nkkt));
       CKD(cudaStreamSynchronize(h->s));
       R.ms_solve += ms_since(t0);
@@ -642,9 +647,110 @@ int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   for (int i = 0; i < nu; ++i) h->sol_sig_w[i] = su[i];
   for (int k = 0; k < nbnd; ++k) h->sol_sig_w[nu + xb[k]] = ss[m + k];
   h->sol_sig_s.assign(ss.begin(), ss.begin() + m);
+  // bound multipliers: the state-bound rows' slack multipliers are those of x's bounds
+  h->sol_zwl.assign(nw, 0.0);
+  h->sol_zwu.assign(nw, 0.0);
+  for (int i = 0; i < nu; ++i) { h->sol_zwl[i] = zul[i]; h->sol_zwu[i] = zuu[i]; }
+  for (int k = 0; k < nbnd; ++k) { h->sol_zwl[nu + xb[k]] = zsl[m + k]; h->sol_zwu[nu + xb[k]] = zsu[m + k]; }
+  h->sol_zsl.assign(zsl.begin(), zsl.begin() + m);
+  h->sol_zsu.assign(zsu.begin(), zsu.begin() + m);
+  h->polished = false;
   h->sol_mu = mu;
   h->sol_pg0 = hv.empty() ? 0.0 : hv[0];
   h->have_solution = true;
+  return OPF_OK;
+}
+
+// ------------------------------------------------------------------ polish
+// Newton's method on the full-space barrier KKT system at the fixed mu of the
+// stored solution, from that solution: the point whose derivative the dispatch
+// VJP takes.  Full primal-dual steps cut only by the fraction-to-the-boundary
+// rule (tau = 0.995); each K_aug solve is refined against the full matrix.
+// Stops when the residual (stationarity, feasibility, perturbed
+// complementarity; max-norm) is <= tol or stops falling below 1e-9.
+int polish_solution(opf_handle* h, double tol, int max_iter) {
+  const Plan& P = h->P;
+  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
+  const int nkkt = nw + 2 * m + nx;
+  const double mu = h->sol_mu;
+  Dev d;
+  TRYD(alloc_dev(d, P));
+  Vec slo(m), shi(m);
+  for (int i = 0; i < m; ++i) { slo[i] = -P.hu[i]; shi[i] = -P.hl[i]; }
+  Bounds bw(P.wl, P.wu), bs(slo, shi);
+  Vec w = h->sol_w, s = h->sol_s, lam = h->sol_lam, y = h->sol_y;
+  Vec zwl = h->sol_zwl, zwu = h->sol_zwu, zsl = h->sol_zsl, zsu = h->sol_zsu;
+  Vec g(nx), hv(m), grad(nw), sw, ss, r(nkkt), step(nkkt), dzwl, dzwu, dzsl, dzsu;
+  double prev = 1e300, res = 1e300;
+  int it = 0;
+  for (;; ++it) {
+    TRYD(h2d(h->s, d.u, w.data(), nu));
+    TRYD(h2d(h->s, d.x, w.data() + nu, nx));
+    TRYD(h2d(h->s, d.lam, lam.data(), nx));
+    TRYD(h2d(h->s, d.y, y.data(), m));
+    TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+    TRYD(lagrangian_gradient(h, d.lam, d.y, d.grad));
+    TRYD(d2h(h->s, g.data(), h->g, nx));
+    TRYD(d2h(h->s, hv.data(), h->hv, m));
+    TRYD(d2h(h->s, grad.data(), d.grad, nw));
+    CKD(cudaStreamSynchronize(h->s));
+    res = 0.0;
+    for (int i = 0; i < nw; ++i) res = std::max(res, std::fabs(grad[i] - zwl[i] + zwu[i]));
+    for (int i = 0; i < m; ++i) res = std::max(res, std::fabs(y[i] - zsl[i] + zsu[i]));
+    for (int i = 0; i < nx; ++i) res = std::max(res, std::fabs(g[i]));
+    for (int i = 0; i < m; ++i) res = std::max(res, std::fabs(hv[i] + s[i]));
+    double zs = 0.0;
+    long long zc = 0;
+    res = std::max(res, std::max(bw.compl_inf(w, zwl, zwu, mu, zs, zc), bs.compl_inf(s, zsl, zsu, mu, zs, zc)));
+    if (!std::isfinite(res)) return OPF_ERR_NO_CONVERGENCE;
+    if (res <= tol || (res < 1e-9 && res > 0.5 * prev) || it == max_iter) break;
+    prev = res;
+    bw.sigma(w, zwl, zwu, sw);
+    bs.sigma(s, zsl, zsu, ss);
+    TRYD(h2d(h->s, d.sig_u, sw.data(), nu));
+    TRYD(h2d(h->s, d.sig_x, sw.data() + nu, nx));
+    TRYD(h2d(h->s, d.sig_s, ss.data(), m));
+    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+    TRYD(read_status(h, nullptr));
+    TRYD(factor_kred_async(h, 0.0));
+    TRYD(read_status(h, nullptr));
+    h->have_factor = true;
+    for (int i = 0; i < nw; ++i) r[i] = grad[i] + bw.bgrad(w, i, mu);
+    for (int i = 0; i < m; ++i) r[nw + i] = y[i] + bs.bgrad(s, i, mu);
+    for (int i = 0; i < nx; ++i) r[nw + m + i] = g[i];
+    for (int i = 0; i < m; ++i) r[nw + m + nx + i] = hv[i] + s[i];
+    TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
+    TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 4));
+    TRYD(d2h(h->s, step.data(), d.step, nkkt));
+    CKD(cudaStreamSynchronize(h->s));
+    Vec pw(step.begin(), step.begin() + nw), ps(step.begin() + nw, step.begin() + nw + m);
+    bw.dz(w, zwl, zwu, pw, mu, dzwl, dzwu);
+    bs.dz(s, zsl, zsu, ps, mu, dzsl, dzsu);
+    double a = std::min(bw.max_step(w, pw, 0.995), bs.max_step(s, ps, 0.995));
+    a = std::min(a, std::min(std::min(max_step_z(zwl, dzwl, bw.fl, 0.995), max_step_z(zwu, dzwu, bw.fu, 0.995)),
+                             std::min(max_step_z(zsl, dzsl, bs.fl, 0.995), max_step_z(zsu, dzsu, bs.fu, 0.995))));
+    for (int i = 0; i < nw; ++i) { w[i] += a * pw[i]; zwl[i] += a * dzwl[i]; zwu[i] += a * dzwu[i]; }
+    for (int i = 0; i < m; ++i) {
+      s[i] += a * ps[i];
+      y[i] += a * step[nw + m + nx + i];
+      zsl[i] += a * dzsl[i];
+      zsu[i] += a * dzsu[i];
+    }
+    for (int i = 0; i < nx; ++i) lam[i] += a * step[nw + m + i];
+  }
+  h->sol_w = w;
+  h->sol_s = s;
+  h->sol_lam = lam;
+  h->sol_y = y;
+  h->sol_zwl = zwl;
+  h->sol_zwu = zwu;
+  h->sol_zsl = zsl;
+  h->sol_zsu = zsu;
+  bw.sigma(w, zwl, zwu, h->sol_sig_w);
+  bs.sigma(s, zsl, zsu, h->sol_sig_s);
+  h->sol_pg0 = hv.empty() ? 0.0 : hv[0];
+  h->polish_iters = it;
+  h->polish_res = res;
   return OPF_OK;
 }
 

@@ -39,6 +39,8 @@ struct opf_handle {
   int *AT_rp = nullptr, *AT_ci = nullptr, *AT_map = nullptr;
   int *PGu_rp = nullptr, *PGu_ci = nullptr, *PGu_map = nullptr;
   int *GuT_rp = nullptr, *GuT_ci = nullptr, *GuT_map = nullptr;
+  int *Gc_rp = nullptr, *Gc_ci = nullptr, *Gc_map = nullptr;
+  int *GcT_rp = nullptr, *GcT_ci = nullptr, *GcT_map = nullptr;
   int *GTn_rp = nullptr, *GTn_ci = nullptr, *GTn_map = nullptr;
   int *ATn_rp = nullptr, *ATn_ci = nullptr, *ATn_map = nullptr;
   // LU
@@ -90,8 +92,17 @@ struct opf_handle {
   // converged state of the last opf_solve (host), full-space form
   bool have_solution = false;
   std::vector<double> sol_w, sol_lam, sol_y, sol_s, sol_sig_w, sol_sig_s;
+  std::vector<double> sol_zwl, sol_zwu, sol_zsl, sol_zsu;   // bound multipliers (full-space form)
   double sol_mu = 0.0, sol_pg0 = 0.0;
+  bool polished = false;         // stored solution already moved onto the barrier solution
+  int polish_iters = 0;          // fixed-mu Newton iterations of the last polish (-1: failed)
+  double polish_res = 0.0;       // its final barrier KKT residual (max-norm)
   bool sens_ready = false;       // K_aug at the solution factored for opf_dispatch_vjp
+  double* sens_buf = nullptr;    // dispatch derivative: point, Sigma and a_0 (in allocs)
+  int vjp_steps = 0;             // refinement steps and relative residual of the last VJP
+  double vjp_res = 0.0;
+  int vjp_max_refine = 4;
+  int* sens_pq = nullptr;        // [2 nb] elimination position of P_i / Q_i rows, -1 if none (in allocs)
   // phase timing (opf_profile)
   bool profiling = false;
   struct PhaseRec { int phase; cudaEvent_t a, b; };

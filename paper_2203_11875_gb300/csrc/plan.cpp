@@ -797,6 +797,17 @@ std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double*
     };
     build(P.PGu, P.PGu_map, nu, rows);
     build(P.GuT, P.GuT_map, nx, trows);
+    // all of G with rows in elimination order and columns in c-order, and its
+    // transpose: the G and G^T products of the full K_aug residual
+    std::vector<std::vector<std::pair<int, int>>> grows(nx), gtrows(nw);
+    for (int rr = 0; rr < nx; ++rr)
+      for (int q = P.G.rp[rr]; q < P.G.rp[rr + 1]; ++q) {
+        const int cc = P.w2c[P.G.ci[q]];
+        grows[P.iperm[rr]].push_back({cc, q});
+        gtrows[cc].push_back({P.iperm[rr], q});
+      }
+    build(P.Gc, P.Gc_map, nw, grows);
+    build(P.GcT, P.GcT_map, nx, gtrows);
   }
   // ---------------------------------------------------------------- K pattern (c-order)
   {

@@ -139,6 +139,8 @@ struct Plan {
   std::vector<int> PGu_map;    // value map into G
   CSR GuT;                     // nu x nx (perm cols) : (P G_u)^T
   std::vector<int> GuT_map;
+  CSR Gc, GcT;                 // P G (nx perm rows x nw c-order cols) and its transpose
+  std::vector<int> Gc_map, GcT_map;
   CSR GTn, ATn;                // G^T (nw x nx) and A^T (nw x m), natural order
   std::vector<int> GTn_map, ATn_map;
   // ---- LU of P G_x P^T (perm space)
