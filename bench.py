@@ -121,6 +121,32 @@ def cpu_oracle_condense(net, it, budget_s=15.0):
     return float(np.median(times)), reps
 
 
+def run_batch(binding, nthreads):
+    """OPF solves/s of the 96 uneven instances (32 each at 500 / 1,500 / 3,000
+    buses, loads scaled per bus): one at a time versus opf_batch_solve, on the
+    same handles after the batch autotuner picked their solve kernels.  Every
+    batched objective is compared with its single-instance objective."""
+    nets = gridgen.batch96()
+    hs = [binding.Handle(n) for n in nets]
+    b = binding.Batch(hs, nthreads=nthreads)
+    b.autotune()
+    hs[0].solve()                    # warm-up: first-call costs out of the timing
+    t0 = time.perf_counter()
+    single = [h.solve() for h in hs]
+    t_single = time.perf_counter() - t0
+    batched, wall_ms = b.solve()
+    t_batch = wall_ms * 1e-3
+    rel = max(abs(a["obj"] - c["obj"]) / abs(a["obj"]) for a, c in zip(single, batched))
+    ok = all(a["status"] == 0 and c["status"] == 0 for a, c in zip(single, batched))
+    out = {"instances": len(nets), "sizes": "32 x 500 + 32 x 1,500 + 32 x 3,000 buses",
+           "solves_per_s_single": len(nets) / t_single, "solves_per_s_batched": len(nets) / t_batch,
+           "speedup": t_single / t_batch, "wall_s_single": t_single, "wall_s_batched": t_batch,
+           "host_threads": b.nthreads, "all_converged": ok, "max_rel_obj_diff_batched_vs_single": rel,
+           "iters_total": int(sum(c["iters"] for c in batched))}
+    b.close()
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: same metric, workload and unit."""
     rank = int(os.environ.get("RANK", "0"))
@@ -158,6 +184,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the 10,000-bus measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched solves")
+    ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,6 +337,8 @@ def main():
         out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)), "trsm_kernel": k10, "autotune_ms": tune10,
                           "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
                           "symbolic": h10.stats()}
+    if not args.no_batch:
+        out["batch96"] = run_batch(binding, args.batch_threads)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms, reps = cpu_oracle_condense(net, it)
         out["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

@@ -257,6 +257,33 @@ int opf_dispatch_vjp(opf_handle* h, const double* vbar, int k, double* grad_Pd, 
 int opf_vjp_info(const opf_handle* h, int* refine_steps, double* rel_residual, int* polish_iters,
                  double* kkt_residual);
 
+/* ---- A12: many instances at once ------------------------------------------------ */
+/* A batch runs the interior-point loops of n independent handles concurrently
+ * on the current device: each handle gets its own non-blocking stream (its
+ * previous stream comes back at opf_batch_destroy), and nthreads host threads
+ * (0 = one per hardware thread, at most 32; never more than n) take instances
+ * from a queue, largest first, each thread driving one loop at a time.  Kernels
+ * of different instances overlap on the SMs and one instance's host work hides
+ * behind the others' device work.  Every handle's loop scratch is allocated at
+ * creation, so nothing is allocated or freed while the batch solves.  The
+ * handles stay owned by the caller, must be distinct, and must not be used
+ * outside the batch while it lives.  Errors: INVALID_ARG, CUDA, OOM. */
+typedef struct opf_batch opf_batch;
+int opf_batch_create(opf_handle* const* handles, int n, int nthreads, opf_batch** out);
+void opf_batch_destroy(opf_batch* b);
+/* Number of instances and host threads (outputs may be NULL). */
+int opf_batch_size(const opf_batch* b, int* n, int* nthreads);
+/* Pick every instance's multi-RHS solve kernel now, one instance at a time with
+ * the GPU to itself (at the flat start; see opf_options.rhs_block); handles
+ * whose kernel is already chosen are skipped. */
+int opf_batch_autotune(opf_batch* b);
+/* opf_solve of every instance with the same options (opt may be NULL),
+ * concurrently; results[n] receives each instance's result and *wall_ms (may be
+ * NULL) the host wall time of the whole batch.  Returns OPF_OK when every
+ * instance converged, else the first failing instance's code (errors before
+ * OPF_ERR_NO_CONVERGENCE). */
+int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm_result* results, double* wall_ms);
+
 /* ---- dense Cholesky without device allocation ----------------------------------- */
 /* The paper has no counterpart to this call.  It serves callers that cannot
  * allocate device memory where they need a factorisation -- a loop running under
@@ -278,6 +305,10 @@ int opf_vjp_info(const opf_handle* h, int* refine_steps, double* rel_residual, i
 int opf_chol_noalloc(const double* A, int n, double delta_w, double* L, int* fail_col, void* stream);
 
 /* ---- instrumentation ---------------------------------------------------------- */
+/* The CUDA error of the last runtime call that made any call of this library
+ * return OPF_ERR_CUDA (any thread; 0 if none), and its name into name[len]
+ * (may be NULL). */
+int opf_last_cuda_error(char* name, int len);
 /* Kernel launches this library has enqueued since it was loaded (all handles). */
 unsigned long long opf_launch_count(void);
 

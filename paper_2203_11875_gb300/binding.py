@@ -85,8 +85,15 @@ _SIGS = {
     "opf_vjp_prepare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_dispatch_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "opf_vjp_info": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_double), _ip, C.POINTER(C.c_double)]),
+    "opf_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "opf_batch_destroy": (None, [C.c_void_p]),
+    "opf_batch_size": (C.c_int, [C.c_void_p, _ip, _ip]),
+    "opf_batch_autotune": (C.c_int, [C.c_void_p]),
+    "opf_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result),
+                                  C.POINTER(C.c_double)]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
     "opf_launch_count": (C.c_ulonglong, []),
+    "opf_last_cuda_error": (C.c_int, [C.c_char_p, C.c_int]),
     "opf_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "opf_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
 }
@@ -136,7 +143,12 @@ class OPFError(RuntimeError):
     def __init__(self, code: int, where: str, info: int = -1):
         self.code = code
         self.info = info
-        msg = load_library().opf_strerror(code).decode()
+        lib = load_library()
+        msg = lib.opf_strerror(code).decode()
+        if code == -2:
+            buf = C.create_string_buffer(64)
+            e = lib.opf_last_cuda_error(buf, 64)
+            msg += f" [{buf.value.decode()} ({e})]"
         super().__init__(f"{where}: {msg} (status {code})")
 
 
@@ -335,3 +347,48 @@ class Handle:
         _check(self._lib.opf_powerflow(self._h, _ptr(u), _ptr(x), float(tol), int(max_iter), C.byref(it)),
                "opf_powerflow")
         return it.value
+
+
+def _ipm_options(variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False):
+    return opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
+                           int(bool(verbose)))
+
+
+class Batch:
+    """Concurrent interior-point solves of several handles (opf_batch_*)."""
+
+    def __init__(self, handles, nthreads: int = 0):
+        lib = load_library()
+        self._handles = list(handles)      # keeps the handles alive while the batch lives
+        arr = (C.c_void_p * len(self._handles))(*[h._h.value for h in self._handles])
+        b = C.c_void_p()
+        _check(lib.opf_batch_create(arr, len(self._handles), int(nthreads), C.byref(b)), "opf_batch_create")
+        self._b, self._lib = b, lib
+        n, t = C.c_int(), C.c_int()
+        _check(lib.opf_batch_size(b, C.byref(n), C.byref(t)), "opf_batch_size")
+        self.n, self.nthreads = n.value, t.value
+
+    def autotune(self):
+        _check(self._lib.opf_batch_autotune(self._b), "opf_batch_autotune")
+
+    def solve(self, **options):
+        """opf_batch_solve; returns (per-instance result dicts, host wall ms)."""
+        o = _ipm_options(**options)
+        res = (opf_ipm_result * self.n)()
+        ms = C.c_double()
+        rc = self._lib.opf_batch_solve(self._b, C.byref(o), res, C.byref(ms))
+        out = [{f: getattr(r, f) for f, _ in opf_ipm_result._fields_} for r in res]
+        if rc not in (OPF_OK, -8):
+            raise OPFError(rc, "opf_batch_solve")
+        return out, ms.value
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._lib.opf_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

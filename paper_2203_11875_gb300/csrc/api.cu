@@ -5,6 +5,8 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <new>
 #include <string>
 #include <vector>
@@ -17,16 +19,43 @@
 
 using namespace condipm;
 
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return OPF_ERR_CUDA;    \
+#define CK(call)                                                  \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      condipm::note_cuda_error(e_);                               \
+      return OPF_ERR_CUDA;                                        \
+    }                                                             \
   } while (0)
 
 namespace condipm {
 static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<int> g_last_cuda_error{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void note_cuda_error(cudaError_t e) { g_last_cuda_error.store(int(e), std::memory_order_relaxed); }
+int last_cuda_error() { return g_last_cuda_error.load(std::memory_order_relaxed); }
+
+cudaError_t allow_max_smem(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return cudaSuccess;
+  int mx = 0;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  // the opt-in limit covers static and dynamic shared memory together
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - int(fa.sharedSizeBytes));
+  if (e != cudaSuccess) return e;
+  done.insert({dev, fn});
+  return cudaSuccess;
+}
 }  // namespace condipm
 
 namespace {
@@ -603,6 +632,14 @@ void opf_destroy(opf_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->ws) cudaFree(h->ws);
   delete h;
+}
+
+int opf_last_cuda_error(char* name, int len) {
+  const int e = condipm::last_cuda_error();
+  if (name && len > 0) {
+    std::snprintf(name, size_t(len), "%s", cudaGetErrorName(cudaError_t(e)));
+  }
+  return e;
 }
 
 int opf_sizes(const opf_handle* h, int* nx, int* nu, int* m) {

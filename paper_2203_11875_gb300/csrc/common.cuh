@@ -52,6 +52,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, lo
 // Kernel launches enqueued by this library (all handles, all threads).
 void note_launch();
 unsigned long long launch_count();
+// The last failed CUDA runtime call's error (any thread), for diagnostics.
+void note_cuda_error(cudaError_t e);
+int last_cuda_error();
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per kernel and device.  The limit is process-wide per kernel, so it is
+// never set per launch: a launch of another handle on another host thread,
+// needing more, could otherwise run between the setting and this launch.
+cudaError_t allow_max_smem(const void* fn);
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch error.

@@ -11,6 +11,8 @@ int factor_kred_async(opf_handle* h, double delta_w);
 // K_aug p = -r (external layout), with up to `refine` refinement corrections
 int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int refine);
 int polish_solution(opf_handle* h, double tol, int max_iter);
+int ipm_reserve(opf_handle* h);
+int autotune_at_flat_start(opf_handle* h);
 
 // k right-hand sides of K_aug in the internal layout (row-major, k lanes): the w
 // block in c-order, s and y natural, lambda in elimination order; contiguous

@@ -35,9 +35,13 @@ constexpr double KAPPA_SIGMA = 1e10, SMAX = 100.0;
 
 using Vec = std::vector<double>;
 
-#define CKD(call)                                                                       \
-  do {                                                                                  \
-    if ((call) != cudaSuccess) return OPF_ERR_CUDA;                                      \
+#define CKD(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      note_cuda_error(e_);                \
+      return OPF_ERR_CUDA;                \
+    }                                     \
   } while (0)
 #define TRYD(x)                    \
   do {                             \
@@ -147,23 +151,30 @@ double opt_error(double dual_inf, double primal_inf, double compl_inf, double mu
   return std::max(std::max(dual_inf / sd, primal_inf), compl_inf / sd);
 }
 
-// device scratch for one solve
+// device scratch of the interior-point loop: one allocation per handle, kept
+// for the handle's lifetime (freeing device memory would synchronise the whole
+// device and serialise concurrent solves on other streams)
 struct Dev {
   double *x = nullptr, *u = nullptr, *lam = nullptr, *y = nullptr, *sig_u = nullptr, *sig_x = nullptr,
          *sig_s = nullptr, *rhs = nullptr, *step = nullptr, *grad = nullptr, *tmp = nullptr;
-  ~Dev() {
-    for (double* p : {x, u, lam, y, sig_u, sig_x, sig_s, rhs, step, grad, tmp})
-      if (p) cudaFree(p);
-  }
 };
 
-int alloc_dev(Dev& d, const Plan& P) {
-  const int nkkt = P.nw + 2 * P.m + P.nx;
-  auto A = [](double** p, size_t n) { return cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(double)) == cudaSuccess; };
-  if (!A(&d.x, P.nx) || !A(&d.u, P.nu) || !A(&d.lam, P.nx) || !A(&d.y, P.m) || !A(&d.sig_u, P.nu) ||
-      !A(&d.sig_x, P.nx) || !A(&d.sig_s, P.m) || !A(&d.rhs, nkkt) || !A(&d.step, nkkt) || !A(&d.grad, P.nw) ||
-      !A(&d.tmp, std::max(P.nw, P.nx)))
-    return OPF_ERR_OOM;
+int alloc_dev(Dev& d, opf_handle* h) {
+  const Plan& P = h->P;
+  const size_t nkkt = (size_t)P.nw + 2 * (size_t)P.m + P.nx;
+  const size_t sizes[11] = {(size_t)P.nx, (size_t)P.nu, (size_t)P.nx, (size_t)P.m, (size_t)P.nu, (size_t)P.nx,
+                            (size_t)P.m, nkkt, nkkt, (size_t)P.nw, (size_t)std::max(P.nw, P.nx)};
+  size_t total = 0;
+  for (size_t n : sizes) total += std::max<size_t>(n, 1);
+  if (!h->ipm_buf) {
+    if (cudaMalloc(&h->ipm_buf, total * sizeof(double)) != cudaSuccess) { h->ipm_buf = nullptr; return OPF_ERR_OOM; }
+    h->allocs.push_back(h->ipm_buf);
+  }
+  double** slots[11] = {&d.x, &d.u, &d.lam, &d.y, &d.sig_u, &d.sig_x, &d.sig_s, &d.rhs, &d.step, &d.grad, &d.tmp};
+  double* p = h->ipm_buf;
+  for (int i = 0; i < 11; ++i) { *slots[i] = p; p += std::max<size_t>(sizes[i], 1); }
+  // the single-right-hand-side K_aug solves of the loop use this much workspace
+  if (!workspace(h, 2 * nkkt + kkt_refine_scratch(P, 1) + 8)) return OPF_ERR_OOM;
   return OPF_OK;
 }
 
@@ -235,7 +246,7 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
   const int nkkt = nw + 2 * m + nx;
   Dev d;
-  TRYD(alloc_dev(d, P));
+  TRYD(alloc_dev(d, h));
   Vec slo(m), shi(m);
   for (int i = 0; i < m; ++i) { slo[i] = -P.hu[i]; shi[i] = -P.hl[i]; }
   Bounds bw(P.wl, P.wu), bs(slo, shi);
@@ -414,7 +425,7 @@ int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
   const int nkkt = nw + 2 * m + nx;
   Dev d;
-  TRYD(alloc_dev(d, P));
+  TRYD(alloc_dev(d, h));
   std::vector<int> xb;   // bounded states (Vm at load buses)
   for (int j = 0; j < nx; ++j)
     if (finite_bound(P.wl[nu + j]) || finite_bound(P.wu[nu + j])) xb.push_back(j);
@@ -661,6 +672,35 @@ int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   return OPF_OK;
 }
 
+// Device scratch and workspace of the interior-point loop, allocated ahead of
+// the solves (opf_batch_create calls it before concurrent solves start).
+int ipm_reserve(opf_handle* h) {
+  Dev d;
+  return alloc_dev(d, h);
+}
+
+// Run the multi-RHS solve autotuner at the flat start with zero multipliers and
+// unit Sigma: which kernel is fastest depends on the network's sparsity and
+// the number of right-hand sides, not on the values.
+int autotune_at_flat_start(opf_handle* h) {
+  const Plan& P = h->P;
+  Dev d;
+  TRYD(alloc_dev(d, h));
+  Vec w = flat_start(P);
+  Bounds(P.wl, P.wu).push(w);
+  Vec ones(std::max(P.nw, P.m), 1.0);
+  TRYD(h2d(h->s, d.u, w.data(), P.nu));
+  TRYD(h2d(h->s, d.x, w.data() + P.nu, P.nx));
+  CKD(cudaMemsetAsync(d.lam, 0, sizeof(double) * std::max(1, P.nx), h->s));
+  CKD(cudaMemsetAsync(d.y, 0, sizeof(double) * std::max(1, P.m), h->s));
+  TRYD(h2d(h->s, d.sig_u, ones.data(), P.nu));
+  TRYD(h2d(h->s, d.sig_x, ones.data(), P.nx));
+  TRYD(h2d(h->s, d.sig_s, ones.data(), P.m));
+  TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+  TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+  return read_status(h, nullptr);
+}
+
 // ------------------------------------------------------------------ polish
 // Newton's method on the full-space barrier KKT system at the fixed mu of the
 // stored solution, from that solution: the point whose derivative the dispatch
@@ -674,7 +714,7 @@ int polish_solution(opf_handle* h, double tol, int max_iter) {
   const int nkkt = nw + 2 * m + nx;
   const double mu = h->sol_mu;
   Dev d;
-  TRYD(alloc_dev(d, P));
+  TRYD(alloc_dev(d, h));
   Vec slo(m), shi(m);
   for (int i = 0; i < m; ++i) { slo[i] = -P.hu[i]; shi[i] = -P.hl[i]; }
   Bounds bw(P.wl, P.wu), bs(slo, shi);

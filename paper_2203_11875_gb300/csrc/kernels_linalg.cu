@@ -605,8 +605,7 @@ int lu_refactor_max_blocks(int nthreads, size_t smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_lu_refactor, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (smem > 48 * 1024 && allow_max_smem((const void*)k_lu_refactor) != cudaSuccess) return 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lu_refactor, nthreads, smem);
   return sms * per;
 }
@@ -650,7 +649,7 @@ cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, const doub
   if (nrhs <= 0) return cudaSuccess;
   size_t sm = (size_t)n * sizeof(double);
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    cudaError_t e = allow_max_smem((const void*)k_chol_solve);
     if (e != cudaSuccess) return e;
   }
   k_chol_solve<<<nrhs, 256, sm, s>>>(n, F, dinv, X, nrhs);

@@ -337,7 +337,7 @@ template <int CB, bool UPPER>
 cudaError_t launch_one(cudaStream_t s, const StDev& T, int n, double* X, long long xr, long long xc, int ncols,
                        int* st, long long spin_limit) {
   const size_t smem = st_smem(n, CB, T.cap);
-  cudaError_t e = cudaFuncSetAttribute(k_trsm_st<CB, UPPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_max_smem((const void*)k_trsm_st<CB, UPPER>);
   if (e != cudaSuccess) return e;
   const int grid = (ncols + CB - 1) / CB;
   k_trsm_st<CB, UPPER><<<grid, TRSM_THREADS, smem, s>>>(T, n, X, xr, xc, ncols, st, spin_limit);

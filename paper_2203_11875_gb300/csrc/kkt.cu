@@ -33,9 +33,13 @@
 namespace condipm {
 namespace {
 
-#define CKK(call)                                   \
-  do {                                              \
-    if ((call) != cudaSuccess) return OPF_ERR_CUDA; \
+#define CKK(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      note_cuda_error(e_);                \
+      return OPF_ERR_CUDA;                \
+    }                                     \
   } while (0)
 #define TRYK(x)                  \
   do {                           \

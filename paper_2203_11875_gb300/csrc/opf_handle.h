@@ -89,6 +89,7 @@ struct opf_handle {
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   double delta_w = 0.0;
   double* pf_ws = nullptr;       // power-flow step and norm (nx + 1)
+  double* ipm_buf = nullptr;     // interior-point loop scratch (in allocs)
   // converged state of the last opf_solve (host), full-space form
   bool have_solution = false;
   std::vector<double> sol_w, sol_lam, sol_y, sol_s, sol_sig_w, sol_sig_s;

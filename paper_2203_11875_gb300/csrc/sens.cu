@@ -32,9 +32,13 @@
 namespace condipm {
 namespace {
 
-#define CKS(call)                                   \
-  do {                                              \
-    if ((call) != cudaSuccess) return OPF_ERR_CUDA; \
+#define CKS(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      note_cuda_error(e_);                \
+      return OPF_ERR_CUDA;                \
+    }                                     \
   } while (0)
 #define TRYS(x)                  \
   do {                           \

@@ -1,0 +1,74 @@
+"""Batched solves (opf_batch_*) of the 96 uneven instances: 32 networks each at
+500, 1,500 and 3,000 buses with per-bus load scaling.  Every instance solved in
+the batch must reach its own single-instance objective to 1e-6 relative, and
+one instance per size class must match the CPU oracle's objective to 1e-6."""
+import numpy as np
+import pytest
+
+import gridgen
+from oracle import ipm
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL_OBJ = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2203_11875_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def runs(pkg):
+    nets = gridgen.batch96()
+    hs = [pkg.Handle(n) for n in nets]
+    b = pkg.Batch(hs)
+    b.autotune()
+    single = [h.solve() for h in hs]
+    batched, wall_ms = b.solve()
+    b.close()
+    return nets, single, batched, wall_ms
+
+
+def test_every_batched_instance_matches_its_single_solve(runs):
+    nets, single, batched, _ = runs
+    assert len(batched) == 96
+    for net, a, b in zip(nets, single, batched):
+        assert a["status"] == 0 and b["status"] == 0, (net.name, a["status"], b["status"])
+        assert abs(a["obj"] - b["obj"]) <= TOL_OBJ * abs(a["obj"]), net.name
+
+
+@pytest.mark.parametrize("j", [0, 32, 64])
+def test_one_instance_per_size_class_matches_the_oracle(runs, j):
+    nets, _, batched, _ = runs
+    ref = ipm.linred(nets[j])
+    assert ref.status == "converged"
+    assert abs(batched[j]["obj"] - ref.obj) <= TOL_OBJ * abs(ref.obj)
+
+
+def test_batch_rejects_a_repeated_handle(pkg):
+    net = gridgen.tiny3()
+    h = pkg.Handle(net)
+    with pytest.raises(pkg.OPFError):
+        pkg.Batch([h, h])
+
+
+def test_small_batch_of_mixed_networks(pkg):
+    nets = [gridgen.tiny3(), gridgen.ring30(), gridgen.tiny3()]
+    hs = [pkg.Handle(n) for n in nets]
+    ref = [pkg.Handle(n).solve() for n in nets]
+    b = pkg.Batch(hs, nthreads=2)
+    assert b.n == 3 and b.nthreads == 2
+    out, ms = b.solve()
+    assert ms > 0
+    for r, o in zip(ref, out):
+        assert o["status"] == 0
+        assert abs(r["obj"] - o["obj"]) <= 1e-12 * abs(r["obj"])
+    # the handles get their own streams back and still work alone
+    b.close()
+    assert hs[1].solve()["status"] == 0
+    assert np.isfinite(hs[1].solution()[3]).all()
