@@ -56,6 +56,29 @@ def synthetic_iterate(net, nx, nu, m, seed=2203):
     return dict(x=x, u=u, lam=lam, y=y, sig_u=sig_u, sig_x=sig_x, sig_s=sig_s, r=r)
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` on this workload from the committed ncu
+    summary (profiles/traffic.json), or None when the summary is missing, is for
+    another kernel, or was taken from different kernel sources."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for f in ent.get("sources", []):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != ent.get("sha256"):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -179,7 +202,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -263,6 +286,8 @@ def main():
     trsm_ms, trsm_n = phases["trsm"]
     per_launch_ms = trsm_ms / max(1, trsm_n)
     achieved = (flops_trsm / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
+    trsm_name = "k_trsm_cols (column-parallel)" if trsm_kernel == 32 else f"k_trsm_st<{trsm_kernel}> (staged)"
+    traffic = measured_traffic("k_trsm_cols" if trsm_kernel == 32 else f"k_trsm_st<{trsm_kernel}>")
     # end-to-end through the public API with pinned host buffers
     host = {k: torch.as_tensor(v, dtype=torch.float64).pin_memory() for k, v in it.items()}
     step_h = torch.zeros(h.n_kkt, dtype=torch.float64).pin_memory()
@@ -299,9 +324,9 @@ def main():
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                    "includes": "H2D of x,u,lambda,y,Sigma,r + derivatives + condense + Cholesky + step + D2H of the step"},
            "phases_ms_per_step": {p: v[0] / args.steps for p, v in phases.items()},
-           "roofline": {"bound": "alu", "kernel": "k_trsm (multi-RHS triangular solve)",
+           "roofline": {"bound": "alu", "kernel": trsm_name,
                         "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                        "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None, "traffic": None,
+                        "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None, "traffic": traffic,
                         "flops_per_launch": flops_trsm / 4, "ms_per_launch": per_launch_ms,
                         "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
            "symbolic": st}

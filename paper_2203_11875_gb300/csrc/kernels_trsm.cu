@@ -300,8 +300,15 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_st(StDev T, int n, double
     }
     __syncthreads();
     if (abort_flag) {
-      // let the copy in flight land before the CTA leaves
-      if (tid == 0 && ch + 1 < T.nchunks) mbar_wait(&bars[(ch + 1) & 1], ((ch + 1) >> 1) & 1, spin_limit);
+      // let the copies in flight (this chunk's and the next one's) land in shared
+      // memory before the CTA leaves; a bulk copy takes microseconds, so these
+      // waits get at least 2^22 polls whatever the caller's limit
+      if (tid == 0) {
+        const long long lim = spin_limit > (1LL << 22) ? spin_limit : (1LL << 22);
+        mbar_wait(&bars[ch & 1], (ch >> 1) & 1, lim);
+        if (ch + 1 < T.nchunks) mbar_wait(&bars[(ch + 1) & 1], ((ch + 1) >> 1) & 1, lim);
+      }
+      __syncthreads();
       return;
     }
     const int bigw = T.chunk_big_w[ch];
