@@ -34,6 +34,7 @@ import gridgen  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flop/DFMA x GHz (max SM clock)
 METRIC = "condense+Cholesky ms/IPM iter"
+KERNEL_NAMES = {32: "column-parallel", 64: "level-blocked", 1: "staged x1", 2: "staged x2", 4: "staged x4"}
 UNIT = "ms/iter"
 WORKLOAD = "grid2000: 2,000-bus lattice, 200 generators, nu=399, nx=3,799, FP64, LinRed iterate"
 
@@ -247,7 +248,7 @@ def main():
             delta = max(1e-4, 8 * delta)
         h.kkt_solve(D["r"], step)
     torch.cuda.synchronize()
-    trsm_kernel, trsm_tune = h.trsm_choice()
+    trsm_kernel, trsm_tune, trsm_kernel1 = h.trsm_choice()
     n_launch0 = binding.launch_count()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -286,8 +287,9 @@ def main():
     trsm_ms, trsm_n = phases["trsm"]
     per_launch_ms = trsm_ms / max(1, trsm_n)
     achieved = (flops_trsm / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
-    trsm_name = "k_trsm_cols (column-parallel)" if trsm_kernel == 32 else f"k_trsm_st<{trsm_kernel}> (staged)"
-    traffic = measured_traffic("k_trsm_cols" if trsm_kernel == 32 else f"k_trsm_st<{trsm_kernel}>")
+    trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk"}.get(trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
+    trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)"}.get(trsm_kernel, " (staged)")
+    traffic = measured_traffic(trsm_base)
     # end-to-end through the public API with pinned host buffers
     host = {k: torch.as_tensor(v, dtype=torch.float64).pin_memory() for k, v in it.items()}
     step_h = torch.zeros(h.n_kkt, dtype=torch.float64).pin_memory()
@@ -317,8 +319,8 @@ def main():
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "l2": "256 MB flush written between timed steps",
                       "route": "adjoint", "delta_w": delta,
-                      "trsm_kernel": {32: "column-parallel", 1: "staged x1", 2: "staged x2", 4: "staged x4"}.get(
-                          trsm_kernel, str(trsm_kernel)),
+                      "trsm_kernel": KERNEL_NAMES.get(trsm_kernel, str(trsm_kernel)),
+                      "trsm_kernel_1rhs": KERNEL_NAMES.get(trsm_kernel1, str(trsm_kernel1)),
                       "autotune_ms": trsm_tune},
            "clocks": clocks, "gpu_launches": int(n_launch),
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -358,7 +360,7 @@ def main():
             b.synchronize()
             t10.append(a.elapsed_time(b))
         ph10 = h10.phase_times()
-        k10, tune10 = h10.trsm_choice()
+        k10, tune10, _ = h10.trsm_choice()
         out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)), "trsm_kernel": k10, "autotune_ms": tune10,
                           "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
                           "symbolic": h10.stats()}

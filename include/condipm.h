@@ -72,9 +72,11 @@ typedef struct opf_options {
     int route;            /* OPF_ROUTE_*                                               */
     int rhs_block;        /* multi-right-hand-side solve kernel: 1, 2 or 4 = staged
                              supernodal kernel with that many columns per CTA; 32 =
-                             column-parallel kernel (one lane per column); 0 =
-                             autotune on the first opf_condense (times each kernel
-                             on the actual right-hand side and keeps the fastest)    */
+                             column-parallel kernel (one lane per column); 64 =
+                             level-blocked kernel (explicit inverses of the diagonal
+                             blocks, one lane per column); 0 = autotune on the first
+                             opf_condense (times each kernel on the actual right-hand
+                             side and keeps the fastest)                              */
     long long spin_limit; /* iteration cap of every device-side wait; 0 = 1<<26        */
 } opf_options;
 
@@ -97,9 +99,11 @@ int opf_sizes(const opf_handle* h, int* nx, int* nu, int* m);
 int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* levels_bwd,
               long long* nnz_k, long long* lu_flops);
 /* Multi-RHS solve kernel in use (host outputs, may be NULL): *kernel as in
- * opf_options.rhs_block (-1 before the autotuner ran), ms[4] the autotuner's
- * timings of {column-parallel, staged 1, 2, 4} (0 = not tried). */
-int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms);
+ * opf_options.rhs_block (-1 before the autotuner ran), ms[5] the autotuner's
+ * timings of {column-parallel, staged 1, 2, 4, level-blocked} (0 = not tried),
+ * *kernel1 the kernel of solves with fewer than 32 right-hand sides (1 staged,
+ * 64 level-blocked, -1 not chosen yet). */
+int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);
 /* Stream for all device work (a cudaStream_t, NULL = legacy default stream). */
 int opf_set_stream(opf_handle* h, void* stream);
 

@@ -64,7 +64,7 @@ _SIGS = {
     "opf_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), _ip, _ip, C.POINTER(C.c_longlong),
                             C.POINTER(C.c_longlong)]),
     "opf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
-    "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
+    "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float), _ip]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_eval_functions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_get_vector": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -218,10 +218,11 @@ class Handle:
                     lu_flops=e.value)
 
     def trsm_choice(self):
-        k = C.c_int()
-        ms = (C.c_float * 4)()
-        _check(self._lib.opf_trsm_choice(self._h, C.byref(k), ms), "opf_trsm_choice")
-        return k.value, {"cols": ms[0], "staged1": ms[1], "staged2": ms[2], "staged4": ms[3]}
+        """(multi-RHS kernel, autotuner ms per candidate, single-RHS kernel)."""
+        k, k1 = C.c_int(), C.c_int()
+        ms = (C.c_float * 5)()
+        _check(self._lib.opf_trsm_choice(self._h, C.byref(k), ms, C.byref(k1)), "opf_trsm_choice")
+        return k.value, {"cols": ms[0], "staged1": ms[1], "staged2": ms[2], "staged4": ms[3], "blocked": ms[4]}, k1.value
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""

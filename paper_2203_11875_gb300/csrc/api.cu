@@ -270,8 +270,27 @@ int upload_all(opf_handle* h) {
     TRY(upload(h, &j, C.ext_end)); TRY(upload(h, &l, C.int_beg));
     (k ? h->csU : h->csL) = ColDev{C.nlev, C.maxseg, a, b, c, d, e, f, g0, g, hh, i, j, l};
   }
+  // level-blocked schedules: each level's rows with their supernode, and the
+  // offsets of the supernodes' dense inverses
+  for (int k = 0; k < 2; ++k) {
+    const ColSched& C = k ? P.csU : P.csL;
+    std::vector<int> rptr(C.nlev + 1, 0), rows, rsn, doff(C.sn_first.size() + 1, 0);
+    for (size_t q = 0; q < C.sn_first.size(); ++q) doff[q + 1] = doff[q] + C.sn_w[q] * C.sn_w[q];
+    for (int l = 0; l < C.nlev; ++l) {
+      for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
+        for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) { rows.push_back(r); rsn.push_back(q); }
+      rptr[l + 1] = int(rows.size());
+    }
+    const ColDev& cd = k ? h->csU : h->csL;
+    int *a, *b, *c, *d;
+    TRY(upload(h, &a, rptr)); TRY(upload(h, &b, rows)); TRY(upload(h, &c, rsn)); TRY(upload(h, &d, doff));
+    (k ? h->bkU : h->bkL) = BlkDev{C.nlev, a, b, c, cd.sn_first, cd.sn_w, d, cd.ext_beg, cd.ext_end};
+    const size_t nd = std::max<size_t>(1, size_t(doff.back()));
+    if (k == 0) { TRY(alloc(h, &h->D_L, nd)); TRY(alloc(h, &h->D_Ut, nd)); }
+    else { TRY(alloc(h, &h->D_U, nd)); TRY(alloc(h, &h->D_Lt, nd)); }
+  }
   h->ldp = (P.nu + 31) / 32 * 32;
-  h->cs_ncb_max = std::max((P.nu + 31) / 32, 8);
+  h->cs_ncb_max = std::max((P.nu + 31) / 32, 64);
   {
     const int maxseg = std::max(1, std::max(P.csL.maxseg, P.csU.maxseg));
     TRY(alloc(h, &h->cs_scratch, (size_t)h->cs_ncb_max * maxseg * 32));
@@ -301,6 +320,8 @@ int upload_all(opf_handle* h) {
     h->chol_blocks = std::max(1, std::min(chol_max_blocks(), std::min(need, 2 * 152)));
   }
   h->cs_ksplit_max = std::max(1, trsm_cols_max_blocks());
+  h->blk_max = std::max(1, trsm_blk_max_blocks());
+  if (!ybuf_reserve(h, (size_t)P.nx * h->ldp)) return OPF_ERR_OOM;
   {
     h->sn_cb = trsm_st_max_cb(P.nx, h->st_cap);
   }
@@ -324,6 +345,17 @@ int read_status(opf_handle* h, int* info) {
   if (st[ST_CODE] == DEV_NOT_PD) return OPF_ERR_NOT_PD;
   if (st[ST_CODE] == DEV_SINGULAR) return OPF_ERR_SINGULAR;
   return OPF_ERR_CUDA;
+}
+
+double* ybuf_reserve(opf_handle* h, size_t n) {
+  if (n > h->ybuf_cap) {
+    if (h->ybuf) cudaFree(h->ybuf);
+    h->ybuf = nullptr;
+    h->ybuf_cap = 0;
+    if (cudaMalloc(&h->ybuf, n * sizeof(double)) != cudaSuccess) return nullptr;
+    h->ybuf_cap = n;
+  }
+  return h->ybuf;
 }
 
 double* workspace(opf_handle* h, size_t n) {
@@ -432,6 +464,15 @@ int factor_async(opf_handle* h) {
   CK(launch_fill_stream(s, h->stLo.nslots, h->stLo.slot, h->stLo.src, h->Ut_val, h->inv_diag, 0, h->stLo.bytes_b));
   CK(launch_fill_stream(s, h->stUp.nslots, h->stUp.slot, h->stUp.src, h->Up_val, h->inv_diag, 0, h->stUp.bytes_a));
   CK(launch_fill_stream(s, h->stUp.nslots, h->stUp.slot, h->stUp.src, h->Lt_val, h->inv_diag, 1, h->stUp.bytes_b));
+  {
+    const int nl = int(P.csL.sn_first.size()), nu_ = int(P.csU.sn_first.size());
+    const ColDev& L = h->csL;
+    const ColDev& U = h->csU;
+    CK(launch_diag_inv(s, false, nl, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Lo_val, nullptr, h->D_L));
+    CK(launch_diag_inv(s, false, nl, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Ut_val, h->inv_diag, h->D_Ut));
+    CK(launch_diag_inv(s, true, nu_, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Up_val, h->inv_diag, h->D_U));
+    CK(launch_diag_inv(s, true, nu_, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Lt_val, nullptr, h->D_Lt));
+  }
   ph_end(h);
   h->have_lu = true;
   return OPF_OK;
@@ -446,8 +487,23 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
   const double* dlo = trans ? h->inv_diag : nullptr;
   const double* dup = trans ? nullptr : h->inv_diag;
   const bool cols_ok = ncols >= 32 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max;
-  int mode = (ncols >= 32 && xc == 1) ? h->trsm_mode : 1;
+  int mode = (ncols >= 32 && xc == 1) ? h->trsm_mode : (xc == 1 && h->trsm_mode1 == 64 ? 64 : 1);
   if (mode < 0) mode = 32;
+  if (mode == 64 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max) {
+    double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
+    if (!Y) return OPF_ERR_OOM;
+    const int ncb = (ncols + 31) / 32;
+    const int ksplit = std::max(1, std::min(16, h->blk_max / ncb));
+    if (timed) ph_begin(h, OPF_PHASE_TRSM);
+    CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
+                       h->st, h->spin_limit));
+    if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
+    CK(launch_trsm_blk(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->cs_bar,
+                       h->st, h->spin_limit));
+    if (timed) ph_end(h);
+    return OPF_OK;
+  }
+  if (mode == 64) mode = ncols >= 32 ? 32 : 1;
   if (mode == 32 && cols_ok) {
     const int ncb = (ncols + 31) / 32;
     const int ksplit = std::max(1, std::min(32, h->cs_ksplit_max / ncb));
@@ -485,16 +541,16 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
   const Plan& P = h->P;
   const int nu = P.nu, nx = P.nx;
   double* trial = h->H + (size_t)nu * ld;
-  const int cands[4] = {32, 1, 2, 4};
+  const int cands[5] = {32, 1, 2, 4, 64};
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   float best = 1e30f;
   int pick = 1;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     const int m = cands[k];
-    if (m != 32 && (h->sn_cb == 0 || m > h->sn_cb)) continue;
-    if (m == 32 && (nu < 32 || (nu + 31) / 32 > h->cs_ncb_max)) continue;
+    if (m != 32 && m != 64 && (h->sn_cb == 0 || m > h->sn_cb)) continue;
+    if ((m == 32 || m == 64) && (nu < 32 || (nu + 31) / 32 > h->cs_ncb_max)) continue;
     h->trsm_mode = m;
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {
@@ -507,6 +563,27 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
     }
     h->tune_ms[0][k] = ms;
     if (ms < best) { best = ms; pick = m; }
+  }
+  // one right-hand side (the step recovery): staged (one CTA) or level-blocked
+  {
+    float b1 = 1e30f;
+    int p1 = 1;
+    const int c1[2] = {1, 64};
+    for (int k = 0; k < 2; ++k) {
+      h->trsm_mode1 = c1[k];
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaMemcpyAsync(trial, Sx, sizeof(double) * (size_t)nx * ld, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaEventRecord(a, h->s));
+        TRY(lu_solve_perm(h, 0, trial, ld, 1, 1));
+        CK(cudaEventRecord(b, h->s));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(&ms, a, b));
+      }
+      h->tune_ms[1][k] = ms;
+      if (ms < b1) { b1 = ms; p1 = c1[k]; }
+    }
+    h->trsm_mode1 = p1;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -610,7 +687,7 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return OPF_ERR_INVALID_ARG;
   }
   int cb = h->opt.rhs_block;
-  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32) {
+  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32 && cb != 64) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
@@ -631,6 +708,7 @@ void opf_destroy(opf_handle* h) {
   for (auto e : h->evpool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->ws) cudaFree(h->ws);
+  if (h->ybuf) cudaFree(h->ybuf);
   delete h;
 }
 
@@ -661,11 +739,12 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
   return OPF_OK;
 }
 
-int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms) {
+int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1) {
   if (!h) return OPF_ERR_INVALID_ARG;
   if (kernel) *kernel = h->trsm_mode;
   if (ms)
-    for (int k = 0; k < 4; ++k) ms[k] = h->tune_ms[0][k];
+    for (int k = 0; k < 5; ++k) ms[k] = h->tune_ms[0][k];
+  if (kernel1) *kernel1 = h->trsm_mode1;
   return OPF_OK;
 }
 

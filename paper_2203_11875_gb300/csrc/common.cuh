@@ -141,6 +141,23 @@ cudaError_t launch_trsm_cols(cudaStream_t s, bool upper, const ColDev& S, const 
                              const double* inv_diag, double* X, long long ld, int ncols, int ksplit,
                              double* scratch, unsigned* bar, int* st, long long spin_limit);
 int trsm_cols_max_blocks();
+
+// Level-blocked solve with explicit inverses of the diagonal blocks.  rows /
+// row_sn list each level's rows and their (split) supernode; D holds every
+// supernode's dense inverse, row-major w x w at d_off[s].
+struct BlkDev {
+  int nlev;
+  const int *lvl_rptr, *rows, *row_sn, *sn_first, *sn_w, *d_off, *ext_beg, *ext_end;
+};
+cudaError_t launch_diag_inv(cudaStream_t s, bool upper, int nsn, const int* sn_first, const int* sn_w,
+                            const int* d_off, const int* int_beg, const double* val, const double* inv_diag,
+                            double* D);
+// X, Y row-major with leading dimension ld (Y: scratch of the same shape);
+// ksplit CTAs per 32 columns, cooperative launch; bar holds ncb counters.
+cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
+                            double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
+                            long long spin_limit);
+int trsm_blk_max_blocks();
 cudaError_t launch_fill_stream(cudaStream_t s, long long nslots, const long long* slot, const int* src,
                                const double* vals, const double* inv_diag, int unit, unsigned char* stream);
 

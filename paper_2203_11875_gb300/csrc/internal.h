@@ -35,6 +35,7 @@ int kkt_refine(opf_handle* h, int k, const KB& b, const KB& z, bool solve_first,
                double* scratch, double* final_res, int* steps);
 int read_status(opf_handle* h, int* info = nullptr);
 double* workspace(opf_handle* h, size_t n);
+double* ybuf_reserve(opf_handle* h, size_t n);
 int lagrangian_gradient(opf_handle* h, const double* lam, const double* y, double* out);
 int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols,
                   bool timed = false);

@@ -265,48 +265,74 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
   return x;
 }
 
-// Block-wide right-looking Cholesky of the 32x32 tile T (kb valid rows); writes
-// 1/L(j,j) to dv[j].  Returns the first failing local column or -1.  The FP64
-// work of each rank-1 update is spread over all warps (all four SM sub-partition
-// FP64 units).
-__device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, int* failsh) {
+// Pairs (i, l), 0 <= l <= i < 32, of a 32x32 lower triangle, ordered by l
+// descending: the trailing triangle of column j (l > j) is the prefix of
+// length (31 - j)(32 - j) / 2, and the pair (j+1, j+1) is its last but (31 - j)
+// entries.  Packed as i << 8 | l.  Filled by each CTA at kernel start.
+__device__ __forceinline__ void fill_pairs(unsigned short* pairs) {
+  for (int t = threadIdx.x; t < CNB * (CNB + 1) / 2; t += blockDim.x) {
+    // q = 31 - l is the largest q with q (q + 1) / 2 <= t
+    int q = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
+    while ((q + 1) * (q + 2) / 2 <= t) ++q;
+    while (q * (q + 1) / 2 > t) --q;
+    const int l = CNB - 1 - q, i = l + (t - q * (q + 1) / 2);
+    pairs[t] = (unsigned short)((i << 8) | l);
+  }
+}
+
+// Cholesky of the 32x32 tile T in shared memory (kb valid rows, the rest an
+// identity block).  Column j: every thread takes pairs of the trailing
+// triangle from the table, so each rank-1 update is spread evenly over all
+// warps (all four FP64 pipes of the SM); the update uses the unscaled column,
+// T_il -= T_ij T_lj / d_j, and the column itself is scaled one step later, when
+// nothing reads it any more.  The thread that updates T_{j+1,j+1} computes the
+// next pivot's reciprocal square root at once, so a column costs one barrier.
+// Writes 1 / L_jj to dv[j]; returns the first failing local column or -1.
+__device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const unsigned short* pairs) {
   const int tid = threadIdx.x;
-  if (tid == 0) *failsh = -1;
+  // dv[j] = 1 / sqrt(pivot j), or 0 for a non-positive / non-finite pivot; every
+  // thread reads it after a barrier, so all leave together on a failure
+  if (tid == 0) {
+    const double d = T[0][0];
+    dv[0] = (d > 0.0 && isfinite(d)) ? rsqrt_nr(d) : 0.0;
+  }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    if (tid == 0) {
-      const double d = T[j][j];
-      if (!(d > 0.0 && isfinite(d))) *failsh = j;
-      else {
-        const double x = rsqrt_nr(d);
-        T[j][j] = d * x;
-        dv[j] = x;
-      }
+    const double xj = dv[j];
+    if (!(xj > 0.0)) return j;
+    const double inv_d = xj * xj;
+    if (j > 0) {
+      // scale column j - 1 (not read in this step)
+      const double xp = dv[j - 1];
+      for (int i = j + tid; i < CNB; i += blockDim.x) T[i][j - 1] *= xp;
+      if (tid == 0) T[j - 1][j - 1] *= xp;
     }
-    __syncthreads();
-    if (*failsh >= 0) return *failsh;
-    for (int i = j + 1 + tid; i < kb; i += blockDim.x) T[i][j] *= dv[j];
-    __syncthreads();
-    const int rem = kb - j - 1;
-    for (int t = tid; t < rem * (rem + 1) / 2; t += blockDim.x) {
-      int i = int((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-      while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      while (i * (i + 1) / 2 > t) --i;
-      const int l = t - i * (i + 1) / 2;
-      T[j + 1 + i][j + 1 + l] = fma(-T[j + 1 + i][j], T[j + 1 + l][j], T[j + 1 + i][j + 1 + l]);
+    const int cnt = (CNB - 1 - j) * (CNB - j) / 2;
+    const int diag_next = (CNB - 2 - j) * (CNB - 1 - j) / 2;   // position of (j+1, j+1)
+    for (int t = tid; t < cnt; t += blockDim.x) {
+      const int pr = pairs[t], i = pr >> 8, l = pr & 255;
+      const double v = fma(-T[i][j] * inv_d, T[l][j], T[i][l]);
+      T[i][l] = v;
+      if (t == diag_next && j + 1 < kb) dv[j + 1] = (v > 0.0 && isfinite(v)) ? rsqrt_nr(v) : 0.0;
     }
     __syncthreads();
   }
+  if (kb > 0) {
+    const double xp = dv[kb - 1];
+    for (int i = kb + tid; i < CNB; i += blockDim.x) T[i][kb - 1] *= xp;
+    if (tid == 0) T[kb - 1][kb - 1] *= xp;
+  }
+  __syncthreads();
   return -1;
 }
 
 // Right-looking blocked Cholesky of the lower triangle of F (row-major n x n),
 // 32x32 tiles, one persistent cooperative grid, two phases per block column
 // separated by a bounded grid barrier:
-//   P. each block that owns panel tiles factors the diagonal tile itself
-//      (block-wide, in shared memory; the owner of the diagonal writes it back),
-//      then solves its tiles X L_kk^T = A_ik (four rows per warp, one column per
-//      lane) -- no barrier between the diagonal and the panel;
+//   P. the rows below the diagonal tile are shared out eight per CTA, one per
+//      warp; a CTA with rows (and CTA 0, which writes the tile back) factors the
+//      diagonal tile itself in shared memory, then each warp solves its row
+//      x L_kk^T = a (one column per lane) -- no barrier between the two;
 //   U. the trailing update A_ij -= L_ik L_jk^T in 16x16 sub-tiles.
 // A non-positive or non-finite pivot records DEV_NOT_PD with its column.  The
 // inverse diagonal of L is written to dinv (used by the solves).
@@ -315,22 +341,25 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
   __shared__ double Ta[CNB][CNB + 1];
   __shared__ double Tb[CNB][CNB + 1];
   __shared__ double dv[CNB];
-  __shared__ int failsh;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ unsigned short pairs[CNB * (CNB + 1) / 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int nt = (n + CNB - 1) / CNB;
   const unsigned nbk = gridDim.x;
   volatile int* vst = st;
+  fill_pairs(pairs);
+  __syncthreads();
   for (int k = 0; k < nt; ++k) {
     const int k0 = k * CNB, kb = min(CNB, n - k0);
-    const int npan = nt - k;   // tile rows k..nt-1; row k is the diagonal
+    const int r0 = k0 + kb, nrows = n - r0;              // panel rows r0 .. n-1
+    const int row_blocks = (nrows + nwarps - 1) / nwarps;
     // ---- phase P
-    if ((int)blockIdx.x < npan) {
+    if ((int)blockIdx.x == 0 || (int)blockIdx.x < row_blocks) {
       for (int t = tid; t < CNB * CNB; t += blockDim.x) {
         const int i = t / CNB, j = t % CNB;
         Ta[i][j] = (i < kb && j <= i) ? F[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
       }
       __syncthreads();
-      const int fail = block_chol_tile(Ta, dv, kb, &failsh);
+      const int fail = block_chol_tile(Ta, dv, kb, pairs);
       if (fail >= 0) {
         if (tid == 0) set_status(st, DEV_NOT_PD, k0 + fail);
       } else {
@@ -341,32 +370,17 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
           }
           if (tid < kb) dinv_out[k0 + tid] = dv[tid];
         }
-        for (int pt = 1 + blockIdx.x; pt < npan; pt += nbk) {
-          const int i0 = (k + pt) * CNB, ib = min(CNB, n - i0);
-          for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-            const int i = t / CNB, j = t % CNB;
-            Tb[i][j] = (i < ib && j < kb) ? F[(size_t)(i0 + i) * n + k0 + j] : 0.0;
-          }
-          __syncthreads();
-          double a[4];
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr) a[rr] = Tb[warp * 4 + rr][lane];
-          for (int j = 0; j < kb; ++j) {
-            const double ljl = Ta[lane][j];
-            const double inv = dv[j];
-#pragma unroll
-            for (int rr = 0; rr < 4; ++rr) {
-              const double xj = __shfl_sync(0xffffffffu, a[rr], j) * inv;
-              if (lane == j) a[rr] = xj;
-              else if (lane > j) a[rr] = fma(-xj, ljl, a[rr]);
+        for (int rb = blockIdx.x; rb < row_blocks; rb += nbk) {
+          const int r = r0 + rb * nwarps + warp;
+          if (r < n) {
+            double a = lane < kb ? F[(size_t)r * n + k0 + lane] : 0.0;
+            for (int j = 0; j < kb; ++j) {
+              const double xj = __shfl_sync(0xffffffffu, a, j) * dv[j];
+              if (lane == j) a = xj;
+              else if (lane > j) a = fma(-xj, Ta[lane][j], a);
             }
+            if (lane < kb) F[(size_t)r * n + k0 + lane] = a;
           }
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr) {
-            const int i = warp * 4 + rr;
-            if (i < ib && lane < kb) F[(size_t)(i0 + i) * n + k0 + lane] = a[rr];
-          }
-          __syncthreads();
         }
       }
     }
@@ -378,7 +392,7 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
     for (long long tt = blockIdx.x; tt < nsub; tt += nbk) {
       const long long tile = tt >> 2;
       const int sub = int(tt & 3);
-      int ii = int((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+      int ii = int((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
       while ((long long)(ii + 1) * (ii + 2) / 2 <= tile) ++ii;
       while ((long long)ii * (ii + 1) / 2 > tile) --ii;
       const int jj = int(tile - (long long)ii * (ii + 1) / 2);

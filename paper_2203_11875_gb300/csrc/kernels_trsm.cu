@@ -555,3 +555,182 @@ cudaError_t launch_trsm_cols(cudaStream_t s, bool upper, const ColDev& S, const 
 }
 
 }  // namespace condipm
+
+// ============================================================================
+// Level-blocked variant with explicit inverses of the diagonal blocks.  The
+// supernodes (split to at most 32 rows) of the column schedule keep their
+// levels; after every refactorisation each block's dense inverse D_s is formed
+// (k_diag_inv, one warp per supernode, one column of D per lane).  A level is
+// then two fully parallel phases, with every row of the level given to some
+// warp of the ksplit CTAs that share a 32-column block (one lane per column):
+//   A. Y_r = X_r - sum_{external k} T_rk X_k      (dot product along the row)
+//   B. X_r = sum_{j in s} D_s(r, j) Y_j            (the block's inverse)
+// separated by a bounded counter barrier of the group.  Unlike a sweep of the
+// dense triangle, no chain of dependent steps runs inside a supernode, and the
+// rows of the widest blocks spread over many warps and SMs.
+namespace condipm {
+namespace {
+
+constexpr int BLK_THREADS = 256;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// group barrier of the CTAs of one column block: arrive with a release, poll
+// with acquire loads (bounded), as in block_group_barrier
+__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, long long limit, int* st) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    long long it = 0;
+    while (ld_acquire_u32(ctr) < target) {
+      if (++it > limit) { atomicExch(&st[ST_TIMEOUT], 1); ok = 0; break; }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <bool UPPER>
+__global__ void k_diag_inv(int nsn, const int* __restrict__ sn_first, const int* __restrict__ sn_w,
+                           const int* __restrict__ d_off, const int* __restrict__ int_beg,
+                           const double* __restrict__ val, const double* __restrict__ inv_diag,
+                           double* __restrict__ D) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int c = threadIdx.x & 31;
+  if (s >= nsn) return;
+  const int f = sn_first[s], w = sn_w[s];
+  double d[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) d[r] = 0.0;
+  if (!UPPER) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      if (r < w) {
+        double acc = (r == c) ? 1.0 : 0.0;
+        const double* Tr = val + int_beg[f + r];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < r) acc = fma(-Tr[j], d[j], acc);
+        d[r] = inv_diag ? acc * inv_diag[f + r] : acc;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) {
+      const int r = 31 - rr;
+      if (r < w) {
+        double acc = (r == c) ? 1.0 : 0.0;
+        const double* Tr = val + int_beg[f + r];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j > r && j < w) acc = fma(-Tr[j - r - 1], d[j], acc);
+        d[r] = inv_diag ? acc * inv_diag[f + r] : acc;
+      }
+    }
+  }
+  if (c < w) {
+    double* Ds = D + d_off[s];
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+      if (r < w) Ds[r * w + c] = d[r];
+  }
+}
+
+__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ D, double* X, double* Y,
+                                                          long long ld, int ncols, int ksplit, unsigned* bar,
+                                                          int* st, long long spin_limit) {
+  const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int c = cb * 32 + lane;
+  const bool on = c < ncols;
+  const int gw = p * nwarps + warp, W = ksplit * nwarps;
+  unsigned* ctr = bar + cb;
+  unsigned nbar = 0;
+  for (int lev = 0; lev < S.nlev; ++lev) {
+    const int q0 = S.lvl_rptr[lev], q1 = S.lvl_rptr[lev + 1];
+    // A: Y_r = X_r - external part of row r
+    for (int q = q0 + gw; q < q1; q += W) {
+      const int r = S.rows[q];
+      const int e0 = S.ext_beg[r], e1 = S.ext_end[r];
+      double a0 = on ? X[(long long)r * ld + c] : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int e = e0;
+      for (; e + 3 < e1; e += 4) {
+        const int j0 = ci[e], j1 = ci[e + 1], j2 = ci[e + 2], j3 = ci[e + 3];
+        const double v0 = val[e], v1 = val[e + 1], v2 = val[e + 2], v3 = val[e + 3];
+        if (on) {
+          a0 = fma(-v0, X[(long long)j0 * ld + c], a0);
+          a1 = fma(-v1, X[(long long)j1 * ld + c], a1);
+          a2 = fma(-v2, X[(long long)j2 * ld + c], a2);
+          a3 = fma(-v3, X[(long long)j3 * ld + c], a3);
+        }
+      }
+      for (; e < e1; ++e)
+        if (on) a0 = fma(-val[e], X[(long long)ci[e] * ld + c], a0);
+      if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
+    }
+    if (!group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
+    // B: X_r = D_s(r, :) Y_s
+    for (int q = q0 + gw; q < q1; q += W) {
+      const int r = S.rows[q], s = S.row_sn[q];
+      const int f = S.sn_first[s], w = S.sn_w[s];
+      const double* Dr = D + S.d_off[s] + (r - f) * w;
+      double a0 = 0.0, a1 = 0.0;
+      int j = 0;
+      if (on) {
+        for (; j + 1 < w; j += 2) {
+          a0 = fma(Dr[j], Y[(long long)(f + j) * ld + c], a0);
+          a1 = fma(Dr[j + 1], Y[(long long)(f + j + 1) * ld + c], a1);
+        }
+        if (j < w) a0 = fma(Dr[j], Y[(long long)(f + j) * ld + c], a0);
+        X[(long long)r * ld + c] = a0 + a1;
+      }
+    }
+    if (!group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_diag_inv(cudaStream_t s, bool upper, int nsn, const int* sn_first, const int* sn_w,
+                            const int* d_off, const int* int_beg, const double* val, const double* inv_diag,
+                            double* D) {
+  if (nsn <= 0) return cudaSuccess;
+  const int threads = 128, blocks = (nsn * 32 + threads - 1) / threads;
+  if (upper) k_diag_inv<true><<<blocks, threads, 0, s>>>(nsn, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
+  else k_diag_inv<false><<<blocks, threads, 0, s>>>(nsn, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
+  note_launch();
+  return cudaGetLastError();
+}
+
+int trsm_blk_max_blocks() {
+  int dev = 0, sms = 0, a = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsm_blk, BLK_THREADS, 0);
+  return sms * std::max(a, 1);
+}
+
+cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
+                            double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
+                            long long spin_limit) {
+  if (ncols <= 0 || S.nlev <= 0) return cudaSuccess;
+  const int ncb = (ncols + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned) * ncb, s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&D, (void*)&X, (void*)&Y, (void*)&ld,
+                  (void*)&ncols, (void*)&ksplit, (void*)&bar, (void*)&st, (void*)&spin_limit};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_trsm_blk, dim3(ncb * ksplit), dim3(BLK_THREADS), args, 0, s);
+}
+
+}  // namespace condipm

@@ -73,7 +73,14 @@ struct opf_handle {
   int sn_cb = 0;                 // columns per CTA of the staged solves (0 = level fallback)
   int trsm_mode = -1;            // multi-RHS solve kernel: -1 autotune, 32 column-parallel,
                                  // 1/2/4 staged with that many columns per CTA
-  float tune_ms[3][4] = {};      // autotuner timings: {cols, staged 1, 2, 4} per role
+  float tune_ms[3][5] = {};      // autotuner timings: {cols, staged 1, 2, 4, blocked} per role
+  int trsm_mode1 = -1;           // kernel of the solves with fewer than 32 right-hand sides
+                                 // (-1 autotune, 1 staged, 64 level-blocked)
+  condipm::BlkDev bkL{}, bkU{};  // level-blocked schedules of the lower / upper solves
+  double *D_L = nullptr, *D_Ut = nullptr, *D_U = nullptr, *D_Lt = nullptr;  // diagonal-block inverses
+  double* ybuf = nullptr;        // level-blocked solve scratch (rows x leading dimension)
+  size_t ybuf_cap = 0;
+  int blk_max = 1;               // resident CTAs of the level-blocked kernel
   // dense condensed buffers: Zt = [I; S_x] and H = K Zt (nw x nu, row-major, x rows permuted),
   // Kred (nu x nu, symmetric) and its Cholesky factor F
   double *Zt = nullptr, *H = nullptr, *Kred = nullptr, *F = nullptr, *Fdinv = nullptr;
