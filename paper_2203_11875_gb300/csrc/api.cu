@@ -489,6 +489,18 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
   const bool cols_ok = ncols >= 32 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max;
   int mode = (ncols >= 32 && xc == 1) ? h->trsm_mode : (xc == 1 && h->trsm_mode1 == 64 ? 64 : 1);
   if (mode < 0) mode = 32;
+  if (mode == 64 && ncols == 1) {
+    double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
+    if (!Y) return OPF_ERR_OOM;
+    const int nblk = std::max(1, std::min(h->blk_max, 64));
+    if (timed) ph_begin(h, OPF_PHASE_TRSM);
+    CK(launch_trsm_blk1(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, nblk, h->cs_bar, h->st,
+                        h->spin_limit));
+    CK(launch_trsm_blk1(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, nblk, h->cs_bar, h->st,
+                        h->spin_limit));
+    if (timed) ph_end(h);
+    return OPF_OK;
+  }
   if (mode == 64 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max) {
     double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
     if (!Y) return OPF_ERR_OOM;

@@ -158,6 +158,11 @@ cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, cons
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
                             long long spin_limit);
 int trsm_blk_max_blocks();
+// One right-hand side X[i * xs] (Y: scratch of the same stride); nblocks CTAs,
+// cooperative launch; bar holds one counter.
+cudaError_t launch_trsm_blk1(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
+                             double* X, double* Y, long long xs, int nblocks, unsigned* bar, int* st,
+                             long long spin_limit);
 cudaError_t launch_fill_stream(cudaStream_t s, long long nslots, const long long* slot, const int* src,
                                const double* vals, const double* inv_diag, int unit, unsigned char* stream);
 

@@ -200,17 +200,21 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
     __syncwarp();
     for (int q = r0; q < dpos; ++q) {
       const int k = ci[q];
+      int expired = 0;
       if (lane == 0) {
-        volatile unsigned* vf = flags + k;
+        // acquire load: row k's values and inverse pivot are visible once the
+        // flag is (its writer fences before publishing the flag)
         long long it = 0;
-        while (*vf != epoch) {
-          if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); break; }
-          __nanosleep(32);
+        unsigned f;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
+        while (f != epoch) {
+          if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); expired = 1; break; }
+          // another warp's expired wait ends this one too (its row never comes)
+          if ((it & 1023) == 0 && vst[ST_TIMEOUT]) { expired = 1; break; }
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
         }
       }
-      __syncwarp();
-      __threadfence();
-      if (vst[ST_TIMEOUT]) return;
+      if (__shfl_sync(0xffffffffu, expired, 0)) return;
       const double lik = w[q - r0] * __ldcg(&inv_diag[k]);
       __syncwarp();
       const int ub = diag[k] + 1, ue = rp[k + 1];

@@ -663,19 +663,31 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
       const int r = S.rows[q];
       const int e0 = S.ext_beg[r], e1 = S.ext_end[r];
       double a0 = on ? X[(long long)r * ld + c] : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int e = e0;
-      for (; e + 3 < e1; e += 4) {
-        const int j0 = ci[e], j1 = ci[e + 1], j2 = ci[e + 2], j3 = ci[e + 3];
-        const double v0 = val[e], v1 = val[e + 1], v2 = val[e + 2], v3 = val[e + 3];
-        if (on) {
-          a0 = fma(-v0, X[(long long)j0 * ld + c], a0);
-          a1 = fma(-v1, X[(long long)j1 * ld + c], a1);
-          a2 = fma(-v2, X[(long long)j2 * ld + c], a2);
-          a3 = fma(-v3, X[(long long)j3 * ld + c], a3);
+      // 32 entries at a time: one coalesced load of their columns and values,
+      // broadcast by shuffles, so the X loads do not wait on index loads
+      for (int eb = e0; eb < e1; eb += 32) {
+        const int len = min(32, e1 - eb);
+        const int myj = lane < len ? ci[eb + lane] : 0;
+        const double myv = lane < len ? val[eb + lane] : 0.0;
+        int k = 0;
+        for (; k + 3 < len; k += 4) {
+          const int j0 = __shfl_sync(FULL, myj, k), j1 = __shfl_sync(FULL, myj, k + 1);
+          const int j2 = __shfl_sync(FULL, myj, k + 2), j3 = __shfl_sync(FULL, myj, k + 3);
+          const double v0 = __shfl_sync(FULL, myv, k), v1 = __shfl_sync(FULL, myv, k + 1);
+          const double v2 = __shfl_sync(FULL, myv, k + 2), v3 = __shfl_sync(FULL, myv, k + 3);
+          if (on) {
+            a0 = fma(-v0, X[(long long)j0 * ld + c], a0);
+            a1 = fma(-v1, X[(long long)j1 * ld + c], a1);
+            a2 = fma(-v2, X[(long long)j2 * ld + c], a2);
+            a3 = fma(-v3, X[(long long)j3 * ld + c], a3);
+          }
+        }
+        for (; k < len; ++k) {
+          const int j = __shfl_sync(FULL, myj, k);
+          const double v = __shfl_sync(FULL, myv, k);
+          if (on) a0 = fma(-v, X[(long long)j * ld + c], a0);
         }
       }
-      for (; e < e1; ++e)
-        if (on) a0 = fma(-val[e], X[(long long)ci[e] * ld + c], a0);
       if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
     }
     if (!group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
@@ -699,7 +711,69 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
   }
 }
 
+// One right-hand side (the Newton-step recovery): the same two phases, with a
+// row's entries spread over G lanes (32 / G rows per warp) and a shuffle
+// reduction, so the FP64 instructions stay packed without 32 columns.
+template <int G>
+__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk1(BlkDev S, const int* __restrict__ ci,
+                                                           const double* __restrict__ val,
+                                                           const double* __restrict__ D, double* X, double* Y,
+                                                           long long xs, unsigned* bar, int* st,
+                                                           long long spin_limit) {
+  constexpr int RPW = 32 / G;   // rows per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int sub = lane / G, gl = lane % G;
+  const int gw = blockIdx.x * nwarps + warp, W = gridDim.x * nwarps;
+  unsigned nbar = 0;
+  for (int lev = 0; lev < S.nlev; ++lev) {
+    const int q0 = S.lvl_rptr[lev], q1 = S.lvl_rptr[lev + 1];
+    // A: Y_r = X_r - external part of row r
+    for (int qb = q0 + gw * RPW; qb < q1; qb += W * RPW) {
+      const int q = qb + sub;
+      double a = 0.0;
+      int r = 0;
+      if (q < q1) {
+        r = S.rows[q];
+        const int e1 = S.ext_end[r];
+        for (int e = S.ext_beg[r] + gl; e < e1; e += G) a = fma(val[e], X[(long long)ci[e] * xs], a);
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+      if (q < q1 && gl == 0) Y[(long long)r * xs] = X[(long long)r * xs] - a;
+    }
+    if (!group_barrier(bar, gridDim.x * (++nbar), spin_limit, st)) return;
+    // B: X_r = D_s(r, :) Y_s
+    for (int qb = q0 + gw * RPW; qb < q1; qb += W * RPW) {
+      const int q = qb + sub;
+      double a = 0.0;
+      int r = 0;
+      if (q < q1) {
+        r = S.rows[q];
+        const int s = S.row_sn[q], f = S.sn_first[s], w = S.sn_w[s];
+        const double* Dr = D + S.d_off[s] + (r - f) * w;
+        for (int j = gl; j < w; j += G) a = fma(Dr[j], Y[(long long)(f + j) * xs], a);
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+      if (q < q1 && gl == 0) X[(long long)r * xs] = a;
+    }
+    if (!group_barrier(bar, gridDim.x * (++nbar), spin_limit, st)) return;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_trsm_blk1(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
+                             double* X, double* Y, long long xs, int nblocks, unsigned* bar, int* st,
+                             long long spin_limit) {
+  if (S.nlev <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&D, (void*)&X, (void*)&Y, (void*)&xs,
+                  (void*)&bar, (void*)&st, (void*)&spin_limit};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_trsm_blk1<8>, dim3(nblocks), dim3(BLK_THREADS), args, 0, s);
+}
 
 cudaError_t launch_diag_inv(cudaStream_t s, bool upper, int nsn, const int* sn_first, const int* sn_w,
                             const int* d_off, const int* int_beg, const double* val, const double* inv_diag,
