@@ -492,7 +492,7 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
   if (mode == 64 && ncols == 1) {
     double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
     if (!Y) return OPF_ERR_OOM;
-    const int nblk = std::max(1, std::min(h->blk_max, 64));
+    const int nblk = std::max(1, std::min(h->blk_max, h->blk1_blocks));
     if (timed) ph_begin(h, OPF_PHASE_TRSM);
     CK(launch_trsm_blk1(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, nblk, h->cs_bar, h->st,
                         h->spin_limit));
@@ -505,7 +505,8 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
     if (!Y) return OPF_ERR_OOM;
     const int ncb = (ncols + 31) / 32;
-    const int ksplit = std::max(1, std::min(16, h->blk_max / ncb));
+    const int kmax = std::max(1, h->blk_max / ncb);
+    const int ksplit = std::max(1, std::min(kmax, h->blk_ksplit > 0 ? h->blk_ksplit : 16));
     if (timed) ph_begin(h, OPF_PHASE_TRSM);
     CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
                        h->st, h->spin_limit));
@@ -559,43 +560,61 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
   CK(cudaEventCreate(&b));
   float best = 1e30f;
   int pick = 1;
+  auto time_solve = [&](int ncols, float* out) -> int {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaMemcpyAsync(trial, Sx, sizeof(double) * (size_t)nx * ld, cudaMemcpyDeviceToDevice, h->s));
+      CK(cudaEventRecord(a, h->s));
+      TRY(lu_solve_perm(h, 0, trial, ld, 1, ncols));
+      CK(cudaEventRecord(b, h->s));
+      CK(cudaEventSynchronize(b));
+      CK(cudaEventElapsedTime(&ms, a, b));
+    }
+    *out = ms;
+    return OPF_OK;
+  };
+  int best_ks = 0;
   for (int k = 0; k < 5; ++k) {
     const int m = cands[k];
     if (m != 32 && m != 64 && (h->sn_cb == 0 || m > h->sn_cb)) continue;
     if ((m == 32 || m == 64) && (nu < 32 || (nu + 31) / 32 > h->cs_ncb_max)) continue;
     h->trsm_mode = m;
-    float ms = 0.f;
-    for (int rep = 0; rep < 2; ++rep) {
-      CK(cudaMemcpyAsync(trial, Sx, sizeof(double) * (size_t)nx * ld, cudaMemcpyDeviceToDevice, h->s));
-      CK(cudaEventRecord(a, h->s));
-      TRY(lu_solve_perm(h, 0, trial, ld, 1, nu));
-      CK(cudaEventRecord(b, h->s));
-      CK(cudaEventSynchronize(b));
-      CK(cudaEventElapsedTime(&ms, a, b));
+    if (m == 64) {
+      // the level-blocked kernel also picks its CTAs per column block
+      const int kss[5] = {4, 8, 12, 16, 24};
+      float bk = 1e30f;
+      for (int ks : kss) {
+        h->blk_ksplit = ks;
+        float ms = 0.f;
+        TRY(time_solve(nu, &ms));
+        if (ms < bk) { bk = ms; best_ks = ks; }
+      }
+      h->blk_ksplit = best_ks;
+      h->tune_ms[0][k] = bk;
+      if (bk < best) { best = bk; pick = m; }
+      continue;
     }
+    float ms = 0.f;
+    TRY(time_solve(nu, &ms));
     h->tune_ms[0][k] = ms;
     if (ms < best) { best = ms; pick = m; }
   }
   // one right-hand side (the step recovery): staged (one CTA) or level-blocked
   {
     float b1 = 1e30f;
-    int p1 = 1;
-    const int c1[2] = {1, 64};
-    for (int k = 0; k < 2; ++k) {
+    int p1 = 1, pb = h->blk1_blocks;
+    const int c1[5] = {1, 64, 64, 64, 64};
+    const int nb1[5] = {0, 8, 16, 32, 64};
+    for (int k = 0; k < 5; ++k) {
       h->trsm_mode1 = c1[k];
+      if (nb1[k]) h->blk1_blocks = nb1[k];
       float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        CK(cudaMemcpyAsync(trial, Sx, sizeof(double) * (size_t)nx * ld, cudaMemcpyDeviceToDevice, h->s));
-        CK(cudaEventRecord(a, h->s));
-        TRY(lu_solve_perm(h, 0, trial, ld, 1, 1));
-        CK(cudaEventRecord(b, h->s));
-        CK(cudaEventSynchronize(b));
-        CK(cudaEventElapsedTime(&ms, a, b));
-      }
+      TRY(time_solve(1, &ms));
       h->tune_ms[1][k] = ms;
-      if (ms < b1) { b1 = ms; p1 = c1[k]; }
+      if (ms < b1) { b1 = ms; p1 = c1[k]; pb = nb1[k] ? nb1[k] : pb; }
     }
     h->trsm_mode1 = p1;
+    h->blk1_blocks = pb;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -81,6 +81,8 @@ struct opf_handle {
   double* ybuf = nullptr;        // level-blocked solve scratch (rows x leading dimension)
   size_t ybuf_cap = 0;
   int blk_max = 1;               // resident CTAs of the level-blocked kernel
+  int blk_ksplit = 0;            // its CTAs per 32-column block (0: as many as fit, at most 16)
+  int blk1_blocks = 32;          // CTAs of the single-right-hand-side level-blocked solve
   // dense condensed buffers: Zt = [I; S_x] and H = K Zt (nw x nu, row-major, x rows permuted),
   // Kred (nu x nu, symmetric) and its Cholesky factor F
   double *Zt = nullptr, *H = nullptr, *Kred = nullptr, *F = nullptr, *Fdinv = nullptr;
