@@ -34,7 +34,8 @@ import gridgen  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flop/DFMA x GHz (max SM clock)
 METRIC = "condense+Cholesky ms/IPM iter"
-KERNEL_NAMES = {32: "column-parallel", 64: "level-blocked", 1: "staged x1", 2: "staged x2", 4: "staged x4"}
+KERNEL_NAMES = {32: "column-parallel", 64: "level-blocked", 96: "dataflow", 1: "staged x1", 2: "staged x2",
+                4: "staged x4"}
 UNIT = "ms/iter"
 WORKLOAD = "grid2000: 2,000-bus lattice, 200 generators, nu=399, nx=3,799, FP64, LinRed iterate"
 
@@ -287,8 +288,9 @@ def main():
     trsm_ms, trsm_n = phases["trsm"]
     per_launch_ms = trsm_ms / max(1, trsm_n)
     achieved = (flops_trsm / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
-    trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk"}.get(trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
-    trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)"}.get(trsm_kernel, " (staged)")
+    trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk", 96: "k_trsm_df"}.get(trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
+    trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)", 96: " (dataflow)"}.get(
+        trsm_kernel, " (staged)")
     traffic = measured_traffic(trsm_base)
     # end-to-end through the public API with pinned host buffers
     host = {k: torch.as_tensor(v, dtype=torch.float64).pin_memory() for k, v in it.items()}

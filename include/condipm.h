@@ -74,7 +74,8 @@ typedef struct opf_options {
                              supernodal kernel with that many columns per CTA; 32 =
                              column-parallel kernel (one lane per column); 64 =
                              level-blocked kernel (explicit inverses of the diagonal
-                             blocks, one lane per column); 0 = autotune on the first
+                             blocks, one lane per column); 96 = its barrier-free
+                             dataflow form; 0 = autotune on the first
                              opf_condense (times each kernel on the actual right-hand
                              side and keeps the fastest)                              */
     long long spin_limit; /* iteration cap of every device-side wait; 0 = 1<<26        */
@@ -99,8 +100,9 @@ int opf_sizes(const opf_handle* h, int* nx, int* nu, int* m);
 int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* levels_bwd,
               long long* nnz_k, long long* lu_flops);
 /* Multi-RHS solve kernel in use (host outputs, may be NULL): *kernel as in
- * opf_options.rhs_block (-1 before the autotuner ran), ms[5] the autotuner's
- * timings of {column-parallel, staged 1, 2, 4, level-blocked} (0 = not tried),
+ * opf_options.rhs_block (-1 before the autotuner ran), ms[6] the autotuner's
+ * timings of {column-parallel, staged 1, 2, 4, level-blocked, dataflow}
+ * (0 = not tried),
  * *kernel1 the kernel of solves with fewer than 32 right-hand sides (1 staged,
  * 64 level-blocked, -1 not chosen yet). */
 int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);

@@ -220,9 +220,10 @@ class Handle:
     def trsm_choice(self):
         """(multi-RHS kernel, autotuner ms per candidate, single-RHS kernel)."""
         k, k1 = C.c_int(), C.c_int()
-        ms = (C.c_float * 5)()
+        ms = (C.c_float * 6)()
         _check(self._lib.opf_trsm_choice(self._h, C.byref(k), ms, C.byref(k1)), "opf_trsm_choice")
-        return k.value, {"cols": ms[0], "staged1": ms[1], "staged2": ms[2], "staged4": ms[3], "blocked": ms[4]}, k1.value
+        names = ("cols", "staged1", "staged2", "staged4", "blocked", "dataflow")
+        return k.value, dict(zip(names, ms)), k1.value
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""

@@ -291,6 +291,39 @@ int upload_all(opf_handle* h) {
   }
   h->ldp = (P.nu + 31) / 32 * 32;
   h->cs_ncb_max = std::max((P.nu + 31) / 32, 64);
+  // dataflow task lists: phase A then phase B of each level's rows, each row's
+  // supernode, and the supernodes its external entries lie in
+  size_t nsn_max = 1;
+  for (int k = 0; k < 2; ++k) {
+    const ColSched& C = k ? P.csU : P.csL;
+    const CSR& M = k ? P.Up : P.Lo;
+    const int nsn = int(C.sn_first.size());
+    nsn_max = std::max(nsn_max, size_t(nsn));
+    std::vector<int> sn_of(P.nx, -1), task, dptr(P.nx + 1, 0), dsn;
+    for (int q = 0; q < nsn; ++q)
+      for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) sn_of[r] = q;
+    for (int l = 0; l < C.nlev; ++l) {
+      for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
+        for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(r);
+      for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
+        for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(-1 - r);
+    }
+    std::vector<int> seen(nsn, -1);
+    for (int r = 0; r < P.nx; ++r) {
+      for (int e = C.ext_beg[r]; e < C.ext_end[r]; ++e) {
+        const int q = sn_of[M.ci[e]];
+        if (seen[q] != r) { seen[q] = r; dsn.push_back(q); }
+      }
+      dptr[r + 1] = int(dsn.size());
+    }
+    const ColDev& cd = k ? h->csU : h->csL;
+    const BlkDev& bd = k ? h->bkU : h->bkL;
+    int *a, *b, *c, *d;
+    TRY(upload(h, &a, task)); TRY(upload(h, &b, sn_of)); TRY(upload(h, &c, dptr)); TRY(upload(h, &d, dsn));
+    (k ? h->dfU : h->dfL) = DfDev{int(task.size()), nsn, a, b, cd.sn_first, cd.sn_w, bd.d_off, cd.ext_beg,
+                                  cd.ext_end, c, d};
+  }
+  TRY(alloc(h, &h->df_cnt, 2 * (size_t)h->cs_ncb_max * nsn_max));
   {
     const int maxseg = std::max(1, std::max(P.csL.maxseg, P.csU.maxseg));
     TRY(alloc(h, &h->cs_scratch, (size_t)h->cs_ncb_max * maxseg * 32));
@@ -321,6 +354,7 @@ int upload_all(opf_handle* h) {
   }
   h->cs_ksplit_max = std::max(1, trsm_cols_max_blocks());
   h->blk_max = std::max(1, trsm_blk_max_blocks());
+  h->df_max = std::max(1, trsm_df_max_blocks());
   if (!ybuf_reserve(h, (size_t)P.nx * h->ldp)) return OPF_ERR_OOM;
   {
     h->sn_cb = trsm_st_max_cb(P.nx, h->st_cap);
@@ -501,6 +535,22 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     if (timed) ph_end(h);
     return OPF_OK;
   }
+  if (mode == 96 && ncols >= 32 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max) {
+    double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
+    if (!Y) return OPF_ERR_OOM;
+    const int ncb = (ncols + 31) / 32;
+    const int kmax = std::max(1, h->df_max / ncb);
+    const int ksplit = std::max(1, std::min(kmax, h->df_ksplit > 0 ? h->df_ksplit : 16));
+    if (timed) ph_begin(h, OPF_PHASE_TRSM);
+    CK(launch_trsm_df(s, h->dfL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->df_cnt,
+                      h->st, h->spin_limit));
+    if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
+    CK(launch_trsm_df(s, h->dfU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->df_cnt,
+                      h->st, h->spin_limit));
+    if (timed) ph_end(h);
+    return OPF_OK;
+  }
+  if (mode == 96) mode = 64;
   if (mode == 64 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max) {
     double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
     if (!Y) return OPF_ERR_OOM;
@@ -554,7 +604,7 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
   const Plan& P = h->P;
   const int nu = P.nu, nx = P.nx;
   double* trial = h->H + (size_t)nu * ld;
-  const int cands[5] = {32, 1, 2, 4, 64};
+  const int cands[6] = {32, 1, 2, 4, 64, 96};
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
@@ -574,14 +624,32 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
     return OPF_OK;
   };
   int best_ks = 0;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     const int m = cands[k];
-    if (m != 32 && m != 64 && (h->sn_cb == 0 || m > h->sn_cb)) continue;
-    if ((m == 32 || m == 64) && (nu < 32 || (nu + 31) / 32 > h->cs_ncb_max)) continue;
+    const bool lanes = m == 32 || m == 64 || m == 96;
+    if (!lanes && (h->sn_cb == 0 || m > h->sn_cb)) continue;
+    if (lanes && (nu < 32 || (nu + 31) / 32 > h->cs_ncb_max)) continue;
     h->trsm_mode = m;
+    if (m == 96) {
+      // the dataflow kernel picks its CTAs per column block
+      const int kss[5] = {8, 16, 24, 32, 48};
+      float bk = 1e30f;
+      int bks = 16;
+      for (int ks : kss) {
+        if (ks > 1 && ks > h->df_max / ((nu + 31) / 32)) continue;
+        h->df_ksplit = ks;
+        float ms = 0.f;
+        TRY(time_solve(nu, &ms));
+        if (ms < bk) { bk = ms; bks = ks; }
+      }
+      h->df_ksplit = bks;
+      h->tune_ms[0][5] = bk;
+      if (bk < best) { best = bk; pick = m; }
+      continue;
+    }
     if (m == 64) {
       // the level-blocked kernel also picks its CTAs per column block
-      const int kss[5] = {4, 8, 12, 16, 24};
+      const int kss[6] = {4, 8, 12, 16, 24, 32};
       float bk = 1e30f;
       for (int ks : kss) {
         h->blk_ksplit = ks;
@@ -718,7 +786,7 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return OPF_ERR_INVALID_ARG;
   }
   int cb = h->opt.rhs_block;
-  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32 && cb != 64) {
+  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32 && cb != 64 && cb != 96) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
@@ -774,7 +842,7 @@ int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1) {
   if (!h) return OPF_ERR_INVALID_ARG;
   if (kernel) *kernel = h->trsm_mode;
   if (ms)
-    for (int k = 0; k < 5; ++k) ms[k] = h->tune_ms[0][k];
+    for (int k = 0; k < 6; ++k) ms[k] = h->tune_ms[0][k];
   if (kernel1) *kernel1 = h->trsm_mode1;
   return OPF_OK;
 }

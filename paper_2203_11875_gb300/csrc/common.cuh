@@ -158,6 +158,18 @@ cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, cons
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
                             long long spin_limit);
 int trsm_blk_max_blocks();
+// Dataflow (barrier-free) form of the level-blocked solve: task list of
+// phase-A (row >= 0) and phase-B (-1 - row) warp tasks in level order, each
+// row's supernode, and the supernodes each row's external entries lie in.
+struct DfDev {
+  int ntask, nsn;
+  const int *task, *sn_of, *sn_first, *sn_w, *d_off, *ext_beg, *ext_end, *dep_ptr, *dep_sn;
+};
+// cnt: 2 * ncb * nsn counters (zeroed here); cooperative launch of ncb * ksplit CTAs.
+cudaError_t launch_trsm_df(cudaStream_t s, const DfDev& S, const int* ci, const double* val, const double* D,
+                           double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* cnt, int* st,
+                           long long spin_limit);
+int trsm_df_max_blocks();
 // One right-hand side X[i * xs] (Y: scratch of the same stride); nblocks CTAs,
 // cooperative launch; bar holds one counter.
 cudaError_t launch_trsm_blk1(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,

@@ -215,6 +215,7 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
         }
       }
       if (__shfl_sync(0xffffffffu, expired, 0)) return;
+      __syncwarp();   // orders lane 0's acquire before every lane's loads of row k
       const double lik = w[q - r0] * __ldcg(&inv_diag[k]);
       __syncwarp();
       const int ub = diag[k] + 1, ue = rp[k + 1];

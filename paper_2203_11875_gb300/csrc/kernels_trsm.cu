@@ -808,3 +808,143 @@ cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, cons
 }
 
 }  // namespace condipm
+
+// ============================================================================
+// Dataflow variant of the level-blocked solve: no barrier at all.  Every row
+// of the solve is two warp tasks, in level order:
+//   A(r): wait until every supernode that r's external entries lie in is
+//         complete, then Y_r = X_r - external part, and count r into its
+//         supernode's A counter;
+//   B(r): wait until all rows of r's supernode have passed A, then
+//         X_r = D_s(r, :) Y_s and count r into the supernode's B counter
+//         (the supernode is complete when it reaches its width).
+// Tasks go round-robin to the warps of the ksplit CTAs that share a 32-column
+// block (one lane per column); each warp runs its tasks in list order, every
+// wait of a task is on tasks earlier in the list, and all warps are resident
+// (cooperative launch), so the waits always end.  Compared with the level
+// barriers, a row waits only for the supernodes it reads, not for the slowest
+// row of the level, and separate branches of the elimination tree proceed
+// independently.
+namespace condipm {
+namespace {
+
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned need, long long limit, int* st) {
+  volatile int* vst = st;
+  long long it = 0;
+  while (ld_acquire_u32(p) < need) {
+    if (++it > limit) { atomicExch(&st[ST_TIMEOUT], 1); return false; }
+    if ((it & 1023) == 0 && vst[ST_TIMEOUT]) return false;   // another wait expired
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __restrict__ ci,
+                                                         const double* __restrict__ val,
+                                                         const double* __restrict__ D, double* X, double* Y,
+                                                         long long ld, int ncols, int ksplit, unsigned* cntA,
+                                                         unsigned* cntB, int* st, long long spin_limit) {
+  const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int c = cb * 32 + lane;
+  const bool on = c < ncols;
+  const int gw = p * nwarps + warp, W = ksplit * nwarps;
+  unsigned* cA = cntA + (size_t)cb * S.nsn;
+  unsigned* cB = cntB + (size_t)cb * S.nsn;
+  for (int q = gw; q < S.ntask; q += W) {
+    const int code = S.task[q];
+    if (code >= 0) {
+      const int r = code;
+      const int d0 = S.dep_ptr[r], d1 = S.dep_ptr[r + 1];
+      for (int db = d0; db < d1; db += 32) {
+        bool ok = true;
+        if (db + lane < d1) {
+          const int sd = S.dep_sn[db + lane];
+          ok = wait_count(cB + sd, (unsigned)S.sn_w[sd], spin_limit, st);
+        }
+        if (!__all_sync(FULL, ok)) return;
+      }
+      __syncwarp();
+      const int e0 = S.ext_beg[r], e1 = S.ext_end[r];
+      double a0 = on ? __ldcg(&X[(long long)r * ld + c]) : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      for (int eb = e0; eb < e1; eb += 32) {
+        const int len = min(32, e1 - eb);
+        const int myj = lane < len ? ci[eb + lane] : 0;
+        const double myv = lane < len ? val[eb + lane] : 0.0;
+        int k = 0;
+        for (; k + 3 < len; k += 4) {
+          const int j0 = __shfl_sync(FULL, myj, k), j1 = __shfl_sync(FULL, myj, k + 1);
+          const int j2 = __shfl_sync(FULL, myj, k + 2), j3 = __shfl_sync(FULL, myj, k + 3);
+          const double v0 = __shfl_sync(FULL, myv, k), v1 = __shfl_sync(FULL, myv, k + 1);
+          const double v2 = __shfl_sync(FULL, myv, k + 2), v3 = __shfl_sync(FULL, myv, k + 3);
+          if (on) {
+            a0 = fma(-v0, __ldcg(&X[(long long)j0 * ld + c]), a0);
+            a1 = fma(-v1, __ldcg(&X[(long long)j1 * ld + c]), a1);
+            a2 = fma(-v2, __ldcg(&X[(long long)j2 * ld + c]), a2);
+            a3 = fma(-v3, __ldcg(&X[(long long)j3 * ld + c]), a3);
+          }
+        }
+        for (; k < len; ++k) {
+          const int j = __shfl_sync(FULL, myj, k);
+          const double v = __shfl_sync(FULL, myv, k);
+          if (on) a0 = fma(-v, __ldcg(&X[(long long)j * ld + c]), a0);
+        }
+      }
+      if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(cA + S.sn_of[r], 1u);
+      }
+    } else {
+      const int r = -1 - code, s = S.sn_of[r];
+      const int f = S.sn_first[s], w = S.sn_w[s];
+      bool ok = true;
+      if (lane == 0) ok = wait_count(cA + s, (unsigned)w, spin_limit, st);
+      if (!__shfl_sync(FULL, (int)ok, 0)) return;
+      __syncwarp();
+      const double* Dr = D + S.d_off[s] + (r - f) * w;
+      double a0 = 0.0, a1 = 0.0;
+      if (on) {
+        int j = 0;
+        for (; j + 1 < w; j += 2) {
+          a0 = fma(Dr[j], __ldcg(&Y[(long long)(f + j) * ld + c]), a0);
+          a1 = fma(Dr[j + 1], __ldcg(&Y[(long long)(f + j + 1) * ld + c]), a1);
+        }
+        if (j < w) a0 = fma(Dr[j], __ldcg(&Y[(long long)(f + j) * ld + c]), a0);
+        X[(long long)r * ld + c] = a0 + a1;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(cB + s, 1u);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_trsm_df(cudaStream_t s, const DfDev& S, const int* ci, const double* val, const double* D,
+                           double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* cnt, int* st,
+                           long long spin_limit) {
+  if (ncols <= 0 || S.ntask <= 0) return cudaSuccess;
+  const int ncb = (ncols + 31) / 32;
+  unsigned* cntA = cnt;
+  unsigned* cntB = cnt + (size_t)ncb * S.nsn;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 2 * (size_t)ncb * S.nsn, s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&D, (void*)&X, (void*)&Y, (void*)&ld,
+                  (void*)&ncols, (void*)&ksplit, (void*)&cntA, (void*)&cntB, (void*)&st, (void*)&spin_limit};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_trsm_df, dim3(ncb * ksplit), dim3(BLK_THREADS), args, 0, s);
+}
+
+int trsm_df_max_blocks() {
+  int dev = 0, sms = 0, a = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsm_df, BLK_THREADS, 0);
+  return sms * std::max(a, 1);
+}
+
+}  // namespace condipm

@@ -73,7 +73,7 @@ struct opf_handle {
   int sn_cb = 0;                 // columns per CTA of the staged solves (0 = level fallback)
   int trsm_mode = -1;            // multi-RHS solve kernel: -1 autotune, 32 column-parallel,
                                  // 1/2/4 staged with that many columns per CTA
-  float tune_ms[3][5] = {};      // autotuner timings: {cols, staged 1, 2, 4, blocked} per role
+  float tune_ms[3][6] = {};      // autotuner timings: {cols, staged 1, 2, 4, blocked, dataflow} per role
   int trsm_mode1 = -1;           // kernel of the solves with fewer than 32 right-hand sides
                                  // (-1 autotune, 1 staged, 64 level-blocked)
   condipm::BlkDev bkL{}, bkU{};  // level-blocked schedules of the lower / upper solves
@@ -83,6 +83,9 @@ struct opf_handle {
   int blk_max = 1;               // resident CTAs of the level-blocked kernel
   int blk_ksplit = 0;            // its CTAs per 32-column block (0: as many as fit, at most 16)
   int blk1_blocks = 32;          // CTAs of the single-right-hand-side level-blocked solve
+  condipm::DfDev dfL{}, dfU{};   // dataflow task lists of the lower / upper solves
+  unsigned* df_cnt = nullptr;    // their supernode counters (2 x column blocks x supernodes)
+  int df_max = 1, df_ksplit = 0; // resident CTAs of the dataflow kernel; CTAs per column block
   // dense condensed buffers: Zt = [I; S_x] and H = K Zt (nw x nu, row-major, x rows permuted),
   // Kred (nu x nu, symmetric) and its Cholesky factor F
   double *Zt = nullptr, *H = nullptr, *Kred = nullptr, *F = nullptr, *Fdinv = nullptr;
