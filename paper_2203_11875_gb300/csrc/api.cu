@@ -632,11 +632,11 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
     h->trsm_mode = m;
     if (m == 96) {
       // the dataflow kernel picks its CTAs per column block
-      const int kss[5] = {8, 16, 24, 32, 48};
+      const int kss[6] = {16, 24, 32, 48, 64, 96};
       float bk = 1e30f;
       int bks = 16;
       for (int ks : kss) {
-        if (ks > 1 && ks > h->df_max / ((nu + 31) / 32)) continue;
+        if (ks > 16 && ks > h->df_max / ((nu + 31) / 32)) continue;
         h->df_ksplit = ks;
         float ms = 0.f;
         TRY(time_solve(nu, &ms));

@@ -235,8 +235,9 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
       if (!(fabs(u) > 1e-14 * rmax[i]) || !isfinite(u)) set_status(st, DEV_SINGULAR, i);
       else inv = 1.0 / u;
       inv_diag[i] = inv;
-      __threadfence();
-      atomicExch(&flags[i], epoch);
+      // release: the row's values (ordered before lane 0 by __syncwarp) and its
+      // inverse pivot are visible to whoever acquires the flag
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + i), "r"(epoch) : "memory");
     }
     __syncwarp();
   }

@@ -828,6 +828,12 @@ cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, cons
 namespace condipm {
 namespace {
 
+// add with release semantics at GPU scope: the warp's earlier writes (ordered
+// before lane 0 by __syncwarp) are visible to whoever acquires the count
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool wait_count(const unsigned* p, unsigned need, long long limit, int* st) {
   volatile int* vst = st;
   long long it = 0;
@@ -891,10 +897,7 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
       }
       if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
       __syncwarp();
-      if (lane == 0) {
-        __threadfence();
-        atomicAdd(cA + S.sn_of[r], 1u);
-      }
+      if (lane == 0) red_release_add(cA + S.sn_of[r], 1u);
     } else {
       const int r = -1 - code, s = S.sn_of[r];
       const int f = S.sn_first[s], w = S.sn_w[s];
@@ -914,10 +917,7 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
         X[(long long)r * ld + c] = a0 + a1;
       }
       __syncwarp();
-      if (lane == 0) {
-        __threadfence();
-        atomicAdd(cB + s, 1u);
-      }
+      if (lane == 0) red_release_add(cB + s, 1u);
     }
   }
 }
