@@ -207,10 +207,13 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
         long long it = 0;
         unsigned f;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
+        unsigned ns = 32;
         while (f != epoch) {
           if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); expired = 1; break; }
           // another warp's expired wait ends this one too (its row never comes)
           if ((it & 1023) == 0 && vst[ST_TIMEOUT]) { expired = 1; break; }
+          __nanosleep(ns);   // back off, leaving issue slots to working warps
+          ns = ns < 128 ? 2 * ns : 128;
           asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
         }
       }

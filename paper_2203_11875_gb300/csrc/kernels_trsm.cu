@@ -837,9 +837,14 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 __device__ __forceinline__ bool wait_count(const unsigned* p, unsigned need, long long limit, int* st) {
   volatile int* vst = st;
   long long it = 0;
+  unsigned ns = 32;
   while (ld_acquire_u32(p) < need) {
     if (++it > limit) { atomicExch(&st[ST_TIMEOUT], 1); return false; }
     if ((it & 1023) == 0 && vst[ST_TIMEOUT]) return false;   // another wait expired
+    // back off: waiting warps would otherwise take the issue slots of the
+    // working warps on the same SM sub-partition
+    __nanosleep(ns);
+    ns = ns < 256 ? 2 * ns : 256;
   }
   return true;
 }
