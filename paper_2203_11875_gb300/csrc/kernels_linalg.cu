@@ -200,6 +200,12 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
     __syncwarp();
     for (int q = r0; q < dpos; ++q) {
       const int k = ci[q];
+      // the structure of row k's update needs no wait: fetch it first, so that
+      // after the flag only the values cost a round trip
+      const int ub = diag[k] + 1, ue = rp[k + 1];
+      const long long base = upd_ptr[q];
+      const int j0 = ub + lane;
+      const int pos0 = j0 < ue ? upd_pos[base + lane] - r0 : 0;
       int expired = 0;
       if (lane == 0) {
         // acquire load: row k's values and inverse pivot are visible once the
@@ -219,11 +225,12 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
       }
       if (__shfl_sync(0xffffffffu, expired, 0)) return;
       __syncwarp();   // orders lane 0's acquire before every lane's loads of row k
-      const double lik = w[q - r0] * __ldcg(&inv_diag[k]);
+      const double dk = __ldcg(&inv_diag[k]);
+      const double u0 = j0 < ue ? __ldcg(&LU[j0]) : 0.0;
+      const double lik = w[q - r0] * dk;
       __syncwarp();
-      const int ub = diag[k] + 1, ue = rp[k + 1];
-      const long long base = upd_ptr[q];
-      for (int j = ub + lane; j < ue; j += 32) {
+      if (j0 < ue) w[pos0] = fma(-lik, u0, w[pos0]);
+      for (int j = j0 + 32; j < ue; j += 32) {
         const int pos = upd_pos[base + (j - ub)] - r0;
         w[pos] = fma(-lik, __ldcg(&LU[j]), w[pos]);
       }
