@@ -502,10 +502,12 @@ int factor_async(opf_handle* h) {
     const int nl = int(P.csL.sn_first.size()), nu_ = int(P.csU.sn_first.size());
     const ColDev& L = h->csL;
     const ColDev& U = h->csU;
-    CK(launch_diag_inv(s, false, nl, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Lo_val, nullptr, h->D_L));
-    CK(launch_diag_inv(s, false, nl, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Ut_val, h->inv_diag, h->D_Ut));
-    CK(launch_diag_inv(s, true, nu_, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Up_val, h->inv_diag, h->D_U));
-    CK(launch_diag_inv(s, true, nu_, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Lt_val, nullptr, h->D_Lt));
+    const DiagInvJob jobs[4] = {
+        {nl, 0, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Lo_val, nullptr, h->D_L},
+        {nl, 0, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Ut_val, h->inv_diag, h->D_Ut},
+        {nu_, 1, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Up_val, h->inv_diag, h->D_U},
+        {nu_, 1, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Lt_val, nullptr, h->D_Lt}};
+    CK(launch_diag_inv4(s, jobs));
   }
   ph_end(h);
   h->have_lu = true;

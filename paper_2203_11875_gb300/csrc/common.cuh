@@ -149,9 +149,14 @@ struct BlkDev {
   int nlev;
   const int *lvl_rptr, *rows, *row_sn, *sn_first, *sn_w, *d_off, *ext_beg, *ext_end;
 };
-cudaError_t launch_diag_inv(cudaStream_t s, bool upper, int nsn, const int* sn_first, const int* sn_w,
-                            const int* d_off, const int* int_beg, const double* val, const double* inv_diag,
-                            double* D);
+// inverse of every (split) supernode's diagonal block of one factor
+struct DiagInvJob {
+  int nsn, upper;
+  const int *sn_first, *sn_w, *d_off, *int_beg;
+  const double *val, *inv_diag;   // inv_diag NULL: unit diagonal
+  double* D;
+};
+cudaError_t launch_diag_inv4(cudaStream_t s, const DiagInvJob* jobs);
 // X, Y row-major with leading dimension ld (Y: scratch of the same shape);
 // ksplit CTAs per 32 columns, cooperative launch; bar holds ncb counters.
 cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,

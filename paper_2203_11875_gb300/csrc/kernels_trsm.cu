@@ -599,13 +599,10 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, lo
 }
 
 template <bool UPPER>
-__global__ void k_diag_inv(int nsn, const int* __restrict__ sn_first, const int* __restrict__ sn_w,
-                           const int* __restrict__ d_off, const int* __restrict__ int_beg,
-                           const double* __restrict__ val, const double* __restrict__ inv_diag,
-                           double* __restrict__ D) {
-  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int c = threadIdx.x & 31;
-  if (s >= nsn) return;
+__device__ __forceinline__ void diag_inv_one(int s, int c, const int* __restrict__ sn_first,
+                                             const int* __restrict__ sn_w, const int* __restrict__ d_off,
+                                             const int* __restrict__ int_beg, const double* __restrict__ val,
+                                             const double* __restrict__ inv_diag, double* __restrict__ D) {
   const int f = sn_first[s], w = sn_w[s];
   double d[32];
 #pragma unroll
@@ -642,6 +639,17 @@ __global__ void k_diag_inv(int nsn, const int* __restrict__ sn_first, const int*
     for (int r = 0; r < 32; ++r)
       if (r < w) Ds[r * w + c] = d[r];
   }
+}
+
+// the four factors' diagonal-block inverses in one launch (blockIdx.y picks
+// the factor), so that their widest blocks are inverted side by side
+__global__ void k_diag_inv4(DiagInvJob j0, DiagInvJob j1, DiagInvJob j2, DiagInvJob j3) {
+  const DiagInvJob J = blockIdx.y == 0 ? j0 : blockIdx.y == 1 ? j1 : blockIdx.y == 2 ? j2 : j3;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int c = threadIdx.x & 31;
+  if (s >= J.nsn) return;
+  if (J.upper) diag_inv_one<true>(s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
+  else diag_inv_one<false>(s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
 }
 
 __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
@@ -775,13 +783,13 @@ cudaError_t launch_trsm_blk1(cudaStream_t s, const BlkDev& S, const int* ci, con
   return cudaLaunchCooperativeKernel((void*)k_trsm_blk1<8>, dim3(nblocks), dim3(BLK_THREADS), args, 0, s);
 }
 
-cudaError_t launch_diag_inv(cudaStream_t s, bool upper, int nsn, const int* sn_first, const int* sn_w,
-                            const int* d_off, const int* int_beg, const double* val, const double* inv_diag,
-                            double* D) {
-  if (nsn <= 0) return cudaSuccess;
-  const int threads = 128, blocks = (nsn * 32 + threads - 1) / threads;
-  if (upper) k_diag_inv<true><<<blocks, threads, 0, s>>>(nsn, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
-  else k_diag_inv<false><<<blocks, threads, 0, s>>>(nsn, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
+cudaError_t launch_diag_inv4(cudaStream_t s, const DiagInvJob* jobs) {
+  int nmax = 0;
+  for (int k = 0; k < 4; ++k) nmax = std::max(nmax, jobs[k].nsn);
+  if (nmax <= 0) return cudaSuccess;
+  const int threads = 128;
+  const dim3 grid((nmax * 32 + threads - 1) / threads, 4);
+  k_diag_inv4<<<grid, threads, 0, s>>>(jobs[0], jobs[1], jobs[2], jobs[3]);
   note_launch();
   return cudaGetLastError();
 }
