@@ -472,6 +472,7 @@ int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam
   h->have_eval = true;
   h->have_W = lam && y;
   h->sens_ready = false;
+  h->psi_valid = false;
   h->have_lu = false;
   h->have_condense = false;
   h->have_factor = false;
@@ -696,6 +697,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const int nu = P.nu, nx = P.nx, nw = P.nw;
+  h->psi_valid = false;
   if (!h->have_lu) TRY(factor_async(h));
   CK(cudaMemcpyAsync(h->sig_s, sig_s, sizeof(double) * std::max(1, P.m), cudaMemcpyDeviceToDevice, s));
   // A4: K = W + A^T Sigma_s A + diag(Sigma)
@@ -734,6 +736,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   h->have_condense = true;
   h->have_factor = false;
   h->sens_ready = false;
+  h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
   return OPF_OK;
 }
 

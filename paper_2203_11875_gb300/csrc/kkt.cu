@@ -80,6 +80,32 @@ __global__ void k_absmax_partial(long long n, const double* __restrict__ x, doub
   if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
+// out(i, j) = base(i, j) + alpha * sum_c M(i, c) V(c, j)   (i < n, j < k <= 4;
+// M row-major with leading dimension ld, V and out row-major with k lanes);
+// one warp per row, lanes over c
+__global__ void k_dense_rows(int n, int ncol, int k, const double* __restrict__ M, long long ld,
+                             const double* __restrict__ V, const double* __restrict__ base, double alpha,
+                             double* __restrict__ out) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const double* Mi = M + (long long)i * ld;
+  for (int cc = lane; cc < ncol; cc += 32) {
+    const double m = Mi[cc];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < k) acc[j] = fma(m, V[(long long)cc * k + j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j < k) {
+      double a = acc[j];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) out[(long long)i * k + j] = (base ? base[(long long)i * k + j] : 0.0) + alpha * a;
+    }
+  }
+}
+
 int launched() {
   note_launch();
   return cudaGetLastError() == cudaSuccess ? OPF_OK : OPF_ERR_CUDA;
@@ -130,8 +156,25 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   CKK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, E + (size_t)nu * k, k, 1, p.w, k, 1, k, -1.0,
                   1.0));
   CKK(launch_chol_solve(s, nu, h->F, h->Fdinv, p.w, k));
-  // p_x = G_x^{-1} (b_l - G_u p_u)
   double* px = p.w + (size_t)nu * k;
+  if (h->psi_valid && k <= 4) {
+    // the condensation left S_x = -G_x^{-1} G_u (in Z) and Psi = G_x^{-T} H_x (in
+    // H's x rows, H = K Z); with phi = G_x^{-T} e_x (already in E):
+    //   p_x = q + S_x p_u,   p_l = phi - Psi p_u       (two products, no solves)
+    const long long ld = h->ldp;
+    const int nb = (nx * 32 + 127) / 128;
+    k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->Zt + (size_t)nu * ld, ld, p.w,
+                                    bl_zero ? nullptr : D0 + (size_t)nu * k, 1.0, px);
+    TRYK(launched());
+    CKK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, p.w, k, 1, p.s, k, 1, k, -1.0, 0.0));
+    CKK(launch_axpby(s, (long long)m * k, 1.0, b.y, 1.0, p.s, p.s));
+    k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->sig_s, p.s, b.s, p.y);
+    TRYK(launched());
+    k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->H + (size_t)nu * ld, ld, p.w, E + (size_t)nu * k, -1.0, p.l);
+    TRYK(launched());
+    return OPF_OK;
+  }
+  // p_x = G_x^{-1} (b_l - G_u p_u)
   if (bl_zero) CKK(launch_spmm(s, nx, h->PGu_rp, h->PGu_ci, h->Gval, h->PGu_map, p.w, k, 1, px, k, 1, k, -1.0, 0.0));
   else {
     CKK(cudaMemcpyAsync(px, b.l, sizeof(double) * (size_t)nx * k, cudaMemcpyDeviceToDevice, s));

@@ -99,6 +99,7 @@ struct opf_handle {
   int lu_blocks = 1, lu_threads = 256, lu_maxlen = 1, chol_blocks = 1, cb = 1;
   // call-order state
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
+  bool psi_valid = false;         // Zt holds S_x and H's x rows G_x^{-T} H_x of the last condensation
   double delta_w = 0.0;
   double* pf_ws = nullptr;       // power-flow step and norm (nx + 1)
   double* ipm_buf = nullptr;     // interior-point loop scratch (in allocs)
