@@ -740,8 +740,42 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   return OPF_OK;
 }
 
+// Time the Cholesky with a few grid sizes (fewer CTAs: cheaper grid barriers;
+// more: more of the trailing update in flight) and keep the fastest.  The
+// factor does not depend on the grid size.
+int tune_chol_blocks(opf_handle* h, double delta_w) {
+  const Plan& P = h->P;
+  const int cap = h->chol_blocks;
+  const int cands[4] = {38, 76, 152, 304};
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  int pick = cap;
+  for (int nb : cands) {
+    if (nb > cap) continue;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(a, h->s));
+      CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
+      CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
+      CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, nb));
+      CK(cudaEventRecord(b, h->s));
+      CK(cudaEventSynchronize(b));
+      CK(cudaEventElapsedTime(&ms, a, b));
+    }
+    if (ms < best) { best = ms; pick = nb; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->chol_blocks = pick;
+  h->chol_tuned = true;
+  return OPF_OK;
+}
+
 int factor_kred_async(opf_handle* h, double delta_w) {
   const Plan& P = h->P;
+  if (!h->chol_tuned) TRY(tune_chol_blocks(h, delta_w));
   ph_begin(h, OPF_PHASE_CHOL);
   CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
   CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));

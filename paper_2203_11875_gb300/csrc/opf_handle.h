@@ -97,6 +97,7 @@ struct opf_handle {
   size_t ws_cap = 0;
   // launch shapes
   int lu_blocks = 1, lu_threads = 256, lu_maxlen = 1, chol_blocks = 1, cb = 1;
+  bool chol_tuned = false;       // Cholesky grid size picked by timing (first factorisation)
   // call-order state
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   bool psi_valid = false;         // Zt holds S_x and H's x rows G_x^{-T} H_x of the last condensation
