@@ -306,7 +306,8 @@ int upload_all(opf_handle* h) {
       for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
         for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(r);
       for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
-        for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(-1 - r);
+        if (C.sn_w[q] > DF_INLINE_B)   // narrower supernodes: the last phase-A task does phase B
+          for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(-1 - r);
     }
     std::vector<int> seen(nsn, -1);
     for (int r = 0; r < P.nx; ++r) {

@@ -166,6 +166,9 @@ int trsm_blk_max_blocks();
 // Dataflow (barrier-free) form of the level-blocked solve: task list of
 // phase-A (row >= 0) and phase-B (-1 - row) warp tasks in level order, each
 // row's supernode, and the supernodes each row's external entries lie in.
+// supernodes up to this width get no phase-B tasks: the warp whose phase-A
+// task completes the supernode multiplies by D_s itself
+constexpr int DF_INLINE_B = 4;
 struct DfDev {
   int ntask, nsn;
   const int *task, *sn_of, *sn_first, *sn_w, *d_off, *ext_beg, *ext_end, *dep_ptr, *dep_sn;

@@ -910,7 +910,37 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
       }
       if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
       __syncwarp();
-      if (lane == 0) red_release_add(cA + S.sn_of[r], 1u);
+      const int s = S.sn_of[r], w = S.sn_w[s];
+      if (w > DF_INLINE_B) {
+        if (lane == 0) red_release_add(cA + s, 1u);
+      } else {
+        // narrow supernode: the warp that completes phase A also does phase B
+        unsigned old = 0;
+        if (lane == 0)
+          asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cA + s) : "memory");
+        old = __shfl_sync(FULL, old, 0);
+        if (old + 1 == (unsigned)w) {
+          __syncwarp();
+          const int f = S.sn_first[s];
+          const double* Ds = D + S.d_off[s];
+          double yv[DF_INLINE_B];
+#pragma unroll
+          for (int j = 0; j < DF_INLINE_B; ++j)
+            yv[j] = (on && j < w) ? __ldcg(&Y[(long long)(f + j) * ld + c]) : 0.0;
+#pragma unroll
+          for (int i = 0; i < DF_INLINE_B; ++i) {
+            if (i < w) {
+              double a = 0.0;
+#pragma unroll
+              for (int j = 0; j < DF_INLINE_B; ++j)
+                if (j < w) a = fma(Ds[i * w + j], yv[j], a);
+              if (on) X[(long long)(f + i) * ld + c] = a;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) red_release_add(cB + s, (unsigned)w);
+        }
+      }
     } else {
       const int r = -1 - code, s = S.sn_of[r];
       const int f = S.sn_first[s], w = S.sn_w[s];
