@@ -58,6 +58,24 @@ def synthetic_iterate(net, nx, nu, m, seed=2203):
     return dict(x=x, u=u, lam=lam, y=y, sig_u=sig_u, sig_x=sig_x, sig_s=sig_s, r=r)
 
 
+def shard(n_units, rank, world):
+    """The units (instances) one rank of `world` processes: every world-th one,
+    so that each size class is spread over the ranks."""
+    return list(range(rank, n_units, world))
+
+
+def aggregate(t_local, units_local, dist=None, device=None):
+    """(max of the ranks' times, sum of the ranks' units); plain values alone."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(t_local), int(units_local)
+    import torch
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([int(units_local)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def measured_traffic(kernel):
     """DRAM bytes per launch of `kernel` on this workload from the committed ncu
     summary (profiles/traffic.json), or None when the summary is missing, is for
@@ -146,12 +164,15 @@ def cpu_oracle_condense(net, it, budget_s=15.0):
     return float(np.median(times)), reps
 
 
-def run_batch(binding, nthreads):
+def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
     """OPF solves/s of the 96 uneven instances (32 each at 500 / 1,500 / 3,000
     buses, loads scaled per bus): one at a time versus opf_batch_solve, on the
     same handles after the batch autotuner picked their solve kernels.  Every
-    batched objective is compared with its single-instance objective."""
-    nets = gridgen.batch96()
+    batched objective is compared with its single-instance objective.  With
+    several ranks each solves its shard of the instances (no collective on
+    the data path); the rates are the instances of all ranks over the slowest
+    rank's time."""
+    nets = [gridgen.batch96()[i] for i in shard(96, rank, world)]
     hs = [binding.Handle(n) for n in nets]
     b = binding.Batch(hs, nthreads=nthreads)
     b.autotune()
@@ -163,8 +184,10 @@ def run_batch(binding, nthreads):
     t_batch = wall_ms * 1e-3
     rel = max(abs(a["obj"] - c["obj"]) / abs(a["obj"]) for a, c in zip(single, batched))
     ok = all(a["status"] == 0 and c["status"] == 0 for a, c in zip(single, batched))
-    out = {"instances": len(nets), "sizes": "32 x 500 + 32 x 1,500 + 32 x 3,000 buses",
-           "solves_per_s_single": len(nets) / t_single, "solves_per_s_batched": len(nets) / t_batch,
+    t_single, n_all = aggregate(t_single, len(nets), dist, device)
+    t_batch, _ = aggregate(t_batch, len(nets), dist, device)
+    out = {"instances": n_all, "sizes": "32 x 500 + 32 x 1,500 + 32 x 3,000 buses",
+           "solves_per_s_single": n_all / t_single, "solves_per_s_batched": n_all / t_batch,
            "speedup": t_single / t_batch, "wall_s_single": t_single, "wall_s_batched": t_batch,
            "host_threads": b.nthreads, "all_converged": ok, "max_rel_obj_diff_batched_vs_single": rel,
            "iters_total": int(sum(c["iters"] for c in batched))}
@@ -367,7 +390,7 @@ def main():
                           "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
                           "symbolic": h10.stats()}
     if not args.no_batch:
-        out["batch96"] = run_batch(binding, args.batch_threads)
+        out["batch96"] = run_batch(binding, args.batch_threads, rank, world, dist, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms, reps = cpu_oracle_condense(net, it)
         out["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
