@@ -172,10 +172,14 @@ def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
     several ranks each solves its shard of the instances (no collective on
     the data path); the rates are the instances of all ranks over the slowest
     rank's time."""
-    nets = [gridgen.batch96()[i] for i in shard(96, rank, world)]
+    t00 = time.perf_counter()
+    every = gridgen.batch96()
+    nets = [every[i] for i in shard(len(every), rank, world)]
     hs = [binding.Handle(n) for n in nets]
+    t01 = time.perf_counter()
     b = binding.Batch(hs, nthreads=nthreads)
     b.autotune()
+    t02 = time.perf_counter()
     hs[0].solve()                    # warm-up: first-call costs out of the timing
     t0 = time.perf_counter()
     single = [h.solve() for h in hs]
@@ -190,8 +194,12 @@ def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
            "solves_per_s_single": n_all / t_single, "solves_per_s_batched": n_all / t_batch,
            "speedup": t_single / t_batch, "wall_s_single": t_single, "wall_s_batched": t_batch,
            "host_threads": b.nthreads, "all_converged": ok, "max_rel_obj_diff_batched_vs_single": rel,
-           "iters_total": int(sum(c["iters"] for c in batched))}
+           "iters_total": int(sum(c["iters"] for c in batched)),
+           "graph_iters_total": int(sum(c.get("graph_iters", 0) for c in batched))}
+    t03 = time.perf_counter()
     b.close()
+    del hs
+    out["setup_s"] = {"create": t01 - t00, "batch_and_autotune": t02 - t01, "teardown": time.perf_counter() - t03}
     return out
 
 

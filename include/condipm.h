@@ -198,6 +198,8 @@ typedef struct opf_ipm_result {
     double obj, err, mu;
     int n_factor;      /* Cholesky attempts (inertia correction included)          */
     double ms_total, ms_eval, ms_condense, ms_factor, ms_solve, ms_linesearch, ms_pf;  /* host wall */
+    int graph_iters;   /* iterations whose condensation + first Cholesky attempt ran as
+                          a replayed CUDA graph (needs a non-default stream)           */
 } opf_ipm_result;
 
 /* Solve the OPF of the handle's network from the flat start (theta = 0, Vm = 1 at

@@ -50,7 +50,7 @@ class opf_ipm_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("obj", C.c_double), ("err", C.c_double),
                 ("mu", C.c_double), ("n_factor", C.c_int), ("ms_total", C.c_double), ("ms_eval", C.c_double),
                 ("ms_condense", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
-                ("ms_linesearch", C.c_double), ("ms_pf", C.c_double)]
+                ("ms_linesearch", C.c_double), ("ms_pf", C.c_double), ("graph_iters", C.c_int)]
 
 
 OPF_LINRED, OPF_REDLIN = 0, 1

@@ -488,7 +488,10 @@ int factor_async(opf_handle* h) {
   CK(cudaMemsetAsync(h->LUval, 0, sizeof(double) * std::max<long long>(1, P.LU.nnz()), s));
   CK(launch_lu_scatter(s, P.G.nnz(), h->Gx_to_LU, h->Gval, h->LUval));
   CK(launch_row_absmax(s, P.nx, h->LU_rp, h->LUval, h->rmax));
-  h->epoch += 1;
+  // the row flags restart from zero every refactorisation (one epoch value), so
+  // that a captured graph of this sequence can be replayed
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned) * std::max(1, P.nx), s));
+  h->epoch = 1;
   CK(launch_lu_refactor(s, P.nx, h->fwd_rows, h->LU_rp, h->LU_ci, h->LU_diag, h->upd_ptr, h->upd_pos,
                         h->LUval, h->inv_diag, h->rmax, h->flags, h->epoch, h->st, h->spin_limit,
                         h->lu_blocks, h->lu_threads, h->lu_maxlen));
@@ -845,6 +848,7 @@ void opf_destroy(opf_handle* h) {
   if (!h) return;
   for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : h->evpool) cudaEventDestroy(e);
+  if (h->cf_exec) cudaGraphExecDestroy(h->cf_exec);
   for (void* p : h->allocs) cudaFree(p);
   if (h->ws) cudaFree(h->ws);
   if (h->ybuf) cudaFree(h->ybuf);

@@ -205,10 +205,12 @@ int eval_fgh(opf_handle* h, Dev& d, const Vec& w, double& f, Vec& g, Vec& hv) {
   return OPF_OK;
 }
 
-// Cholesky of Kred + delta I with the inertia-correction schedule; delta in/out
-int factor_with_correction(opf_handle* h, double& delta, double delta_last, int& attempts) {
+// Cholesky of Kred + delta I with the inertia-correction schedule; delta in/out.
+// skip_zero: the attempt with delta = 0 already failed (NOT_PD)
+int factor_with_correction(opf_handle* h, double& delta, double delta_last, int& attempts, bool skip_zero = false) {
   attempts = 0;
   double d = 0.0;
+  if (skip_zero) d = delta_last > 0.0 ? std::max(1e-20, delta_last / 3.0) : 1e-4;
   for (;;) {
     TRYD(factor_kred_async(h, d));
     ++attempts;
@@ -223,6 +225,52 @@ int factor_with_correction(opf_handle* h, double& delta, double delta_last, int&
     else d *= 8.0;
     if (d > 1e40) return OPF_ERR_NOT_PD;
   }
+}
+
+// Condensation and the Cholesky attempt with delta_w = 0, enqueued as one CUDA
+// graph: captured once the solve kernels are autotuned, replayed at every
+// later iteration (the inputs live in the loop's fixed device buffers; the
+// sequence resets its own counters and flags).  Where capture or instantiation
+// is refused, or while phases are being profiled, the launches are enqueued
+// one by one.  Returns the device status (one synchronisation).
+int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
+  const bool graph_ok = h->use_graphs && !h->cf_failed && !h->profiling && h->trsm_mode >= 0 && h->chol_tuned;
+  if (graph_ok && !h->cf_exec) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int rc = condense_async(h, d.sig_u, d.sig_x, d.sig_s);
+      if (rc == OPF_OK) rc = factor_kred_async(h, 0.0);
+      const cudaError_t e = cudaStreamEndCapture(h->s, &g);
+      if (rc == OPF_OK && e == cudaSuccess && g &&
+          cudaGraphInstantiate(&h->cf_exec, g, 0) == cudaSuccess) {
+        // captured
+      } else {
+        h->cf_exec = nullptr;
+        h->cf_failed = true;
+      }
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    } else {
+      h->cf_failed = true;
+      cudaGetLastError();
+    }
+  }
+  if (graph_ok && h->cf_exec) {
+    if (cudaGraphLaunch(h->cf_exec, h->s) != cudaSuccess) return OPF_ERR_CUDA;
+    ++*graph_iters;
+    // the host-side state the enqueued sequence stands for
+    h->have_lu = true;
+    h->have_condense = true;
+    h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
+    h->sens_ready = false;
+    h->delta_w = 0.0;
+  } else {
+    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+    TRYD(factor_kred_async(h, 0.0));
+  }
+  const int rc = read_status(h, nullptr);
+  h->have_factor = rc == OPF_OK;
+  return rc;
 }
 
 // the initial primal point: theta = 0, Vm = 1 at load buses, 1.05 at generator
@@ -318,12 +366,17 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
     TRYD(h2d(h->s, d.sig_u, sw.data(), nu));
     TRYD(h2d(h->s, d.sig_x, sw.data() + nu, nx));
     TRYD(h2d(h->s, d.sig_s, ss.data(), m));
-    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
-    TRYD(read_status(h, nullptr));
-    R.ms_condense += ms_since(t0);
-    t0 = clk::now();
-    int att = 0;
-    TRYD(factor_with_correction(h, delta, delta, att));
+    // condensation + first Cholesky attempt (one graph); inertia correction
+    // only when Kred is not positive definite
+    int att = 1;
+    {
+      const int rc0 = condense_factor0(h, d, &R.graph_iters);
+      R.ms_condense += ms_since(t0);
+      t0 = clk::now();
+      if (rc0 == OPF_OK) delta = 0.0;
+      else if (rc0 == OPF_ERR_NOT_PD) { TRYD(factor_with_correction(h, delta, delta, att, true)); ++att; }
+      else return rc0;
+    }
     R.n_factor += att;
     R.ms_factor += ms_since(t0);
     // right-hand side and step
@@ -544,12 +597,17 @@ int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
     TRYD(h2d(h->s, d.sig_u, su.data(), nu));
     TRYD(h2d(h->s, d.sig_x, sigx.data(), nx));
     TRYD(h2d(h->s, d.sig_s, ss.data(), m));
-    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
-    TRYD(read_status(h, nullptr));
-    R.ms_condense += ms_since(t0);
-    t0 = clk::now();
-    int att = 0;
-    TRYD(factor_with_correction(h, delta, delta, att));
+    // condensation + first Cholesky attempt (one graph); inertia correction
+    // only when Kred is not positive definite
+    int att = 1;
+    {
+      const int rc0 = condense_factor0(h, d, &R.graph_iters);
+      R.ms_condense += ms_since(t0);
+      t0 = clk::now();
+      if (rc0 == OPF_OK) delta = 0.0;
+      else if (rc0 == OPF_ERR_NOT_PD) { TRYD(factor_with_correction(h, delta, delta, att, true)); ++att; }
+      else return rc0;
+    }
     R.n_factor += att;
     R.ms_factor += ms_since(t0);
     // reduced right-hand sides in the full-space layout (r4 = 0)

@@ -98,6 +98,11 @@ struct opf_handle {
   // launch shapes
   int lu_blocks = 1, lu_threads = 256, lu_maxlen = 1, chol_blocks = 1, cb = 1;
   bool chol_tuned = false;       // Cholesky grid size picked by timing (first factorisation)
+  // condensation + first Cholesky attempt of the interior-point loop as a CUDA
+  // graph (inputs in the loop's fixed device buffers)
+  cudaGraphExec_t cf_exec = nullptr;
+  bool cf_failed = false;        // capture or instantiation was refused: plain launches
+  bool use_graphs = true;
   // call-order state
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   bool psi_valid = false;         // Zt holds S_x and H's x rows G_x^{-T} H_x of the last condensation

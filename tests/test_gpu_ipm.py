@@ -46,3 +46,18 @@ def test_variants_agree_on_grid2000(pkg):
     b = pkg.Handle(net).solve("redlin")
     assert a["status"] == b["status"] == 0
     assert abs(a["obj"] - b["obj"]) <= TOL_OBJ * abs(a["obj"])
+
+
+def test_solve_on_a_stream_replays_the_condensation_graph(pkg):
+    """On a non-default stream the loop enqueues condensation + Cholesky as one
+    captured graph from the second iteration on; the solve must not change."""
+    net = gridgen.grid2000()
+    a = pkg.Handle(net).solve("linred")
+    h = pkg.Handle(net)
+    st = torch.cuda.Stream()
+    h.set_stream(st)
+    b = h.solve("linred")
+    assert a["status"] == b["status"] == 0
+    assert a["graph_iters"] == 0 and b["graph_iters"] == b["iters"] - 1
+    assert a["iters"] == b["iters"]
+    assert abs(a["obj"] - b["obj"]) <= 1e-12 * abs(a["obj"])
