@@ -241,6 +241,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the 10,000-bus measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched solves")
+    ap.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -399,11 +400,38 @@ def main():
                           "symbolic": h10.stats()}
     if not args.no_batch:
         out["batch96"] = run_batch(binding, args.batch_threads, rank, world, dist, dev)
+    # one whole interior-point solve of the same network (LinRed), GPU path
+    if not args.no_solve:
+        hs = binding.Handle(net)
+        hs.set_stream(stream)
+        t0 = time.perf_counter()
+        rs = hs.solve("linred")
+        out["solve"] = {"workload": "grid2000 LinRed from the flat start", "wall_s": time.perf_counter() - t0,
+                        "iters": rs["iters"], "obj": rs["obj"], "status": rs["status"],
+                        "graph_iters": rs["graph_iters"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms, reps = cpu_oracle_condense(net, it)
         out["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"{reps} oracle condense+Cholesky evaluations of the same grid2000 "
                                          "iterate (SciPy splu + BLAS, all host threads)"}
+        # the same on one host thread, in a child process whose BLAS is limited to one thread
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        try:
+            r1 = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                                 "--steps", "5", "--warmup", "1"], env=env, capture_output=True, text=True,
+                                timeout=300)
+            one = json.loads(r1.stdout.strip().splitlines()[-1])
+            out["cpu_baseline_1thread"] = {"value": one["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                           "sample": "5 oracle condense+Cholesky evaluations, BLAS on one thread"}
+        except (subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+            out["cpu_baseline_1thread"] = {"unavailable": str(e)[:200]}
+        if not args.no_solve:
+            from oracle import ipm as oracle_ipm
+            t0 = time.perf_counter()
+            ro = oracle_ipm.linred(net)
+            out["solve"]["cpu_oracle_wall_s"] = time.perf_counter() - t0
+            out["solve"]["cpu_oracle_iters"] = ro.iters
+            out["solve"]["rel_obj_diff_vs_oracle"] = abs(ro.obj - out["solve"]["obj"]) / abs(ro.obj)
     if rank == 0:
         print(json.dumps(out))
     if dist:

@@ -402,35 +402,94 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
     }
     if (!grid_barrier(bar, nbk, spin_limit, st)) return;
     if (vst[ST_CODE] != 0) return;
-    // ---- phase U: 16x16 sub-tiles of the lower trailing tiles
     const int m = nt - k - 1;
-    const long long nsub = (long long)m * (m + 1) / 2 * 4;
-    for (long long tt = blockIdx.x; tt < nsub; tt += nbk) {
-      const long long tile = tt >> 2;
-      const int sub = int(tt & 3);
-      int ii = int((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
-      while ((long long)(ii + 1) * (ii + 2) / 2 <= tile) ++ii;
-      while ((long long)ii * (ii + 1) / 2 > tile) --ii;
-      const int jj = int(tile - (long long)ii * (ii + 1) / 2);
-      if (ii == jj && sub == 1) continue;   // strictly upper quarter of a diagonal tile
-      const int i0 = (k + 1 + ii) * CNB + (sub >> 1) * 16;
-      const int j0 = (k + 1 + jj) * CNB + (sub & 1) * 16;
-      for (int t = tid; t < 16 * CNB; t += blockDim.x) {
-        const int rr = t / CNB, l = t % CNB;
-        Ta[rr][l] = (i0 + rr < n && l < kb) ? F[(size_t)(i0 + rr) * n + k0 + l] : 0.0;
-        Tb[rr][l] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : 0.0;
-      }
-      __syncthreads();
-      const int rr = tid >> 4, cc = tid & 15;
-      double acc0 = 0.0, acc1 = 0.0;
+    const long long ntile = (long long)m * (m + 1) / 2;
+    if (ntile < (long long)nbk) {
+      // ---- phase U, few tiles left: 16x16 sub-tiles (four per tile) for more
+      // work items than CTAs
+      const long long nsub = ntile * 4;
+      for (long long tt = blockIdx.x; tt < nsub; tt += nbk) {
+        const long long tile = tt >> 2;
+        const int sub = int(tt & 3);
+        int ii = int((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+        while ((long long)(ii + 1) * (ii + 2) / 2 <= tile) ++ii;
+        while ((long long)ii * (ii + 1) / 2 > tile) --ii;
+        const int jj = int(tile - (long long)ii * (ii + 1) / 2);
+        if (ii == jj && sub == 1) continue;   // strictly upper quarter of a diagonal tile
+        const int i0 = (k + 1 + ii) * CNB + (sub >> 1) * 16;
+        const int j0 = (k + 1 + jj) * CNB + (sub & 1) * 16;
+        for (int t = tid; t < 16 * CNB; t += blockDim.x) {
+          const int rr = t / CNB, l = t % CNB;
+          Ta[rr][l] = (i0 + rr < n && l < kb) ? F[(size_t)(i0 + rr) * n + k0 + l] : 0.0;
+          Tb[rr][l] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : 0.0;
+        }
+        __syncthreads();
+        const int rr = tid >> 4, cc = tid & 15;
+        double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
-      for (int l = 0; l < CNB; l += 2) {
-        acc0 = fma(Ta[rr][l], Tb[cc][l], acc0);
-        acc1 = fma(Ta[rr][l + 1], Tb[cc][l + 1], acc1);
+        for (int l = 0; l < CNB; l += 2) {
+          acc0 = fma(Ta[rr][l], Tb[cc][l], acc0);
+          acc1 = fma(Ta[rr][l + 1], Tb[cc][l + 1], acc1);
+        }
+        const int gi = i0 + rr, gj = j0 + cc;
+        if (gi < n && gj < n && gj <= gi) F[(size_t)gi * n + gj] -= acc0 + acc1;
+        __syncthreads();
       }
-      const int gi = i0 + rr, gj = j0 + cc;
-      if (gi < n && gj < n && gj <= gi) F[(size_t)gi * n + gj] -= acc0 + acc1;
-      __syncthreads();
+    } else {
+      // ---- phase U: whole 32x32 tiles of the lower trailing triangle; thread
+      // (ty, tx) owns rows {ty, ty + 16} x columns {tx, tx + 16}; the panel tiles
+      // of the next tile are fetched into registers while this one is computed
+      const int ty = tid >> 4, tx = tid & 15;
+      auto tile_ij = [&](long long tile, int& i0, int& j0) {
+        int ii = int((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+        while ((long long)(ii + 1) * (ii + 2) / 2 <= tile) ++ii;
+        while ((long long)ii * (ii + 1) / 2 > tile) --ii;
+        const int jj = int(tile - (long long)ii * (ii + 1) / 2);
+        i0 = (k + 1 + ii) * CNB;
+        j0 = (k + 1 + jj) * CNB;
+      };
+      // each thread moves 4 elements of each panel tile: rows (t / 32) + 8 q, column t % 32
+      double pa[4], pb[4];
+      auto fetch = [&](long long tile) {
+        int i0, j0;
+        tile_ij(tile, i0, j0);
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = (tid >> 5) + 8 * q, l = tid & 31;
+          pa[q] = (i0 + rr < n && l < kb) ? F[(size_t)(i0 + rr) * n + k0 + l] : 0.0;
+          pb[q] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : 0.0;
+        }
+      };
+      long long tt = blockIdx.x;
+      if (tt < ntile) fetch(tt);
+      for (; tt < ntile; tt += nbk) {
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = (tid >> 5) + 8 * q, l = tid & 31;
+          Ta[rr][l] = pa[q];
+          Tb[rr][l] = pb[q];
+        }
+        __syncthreads();
+        if (tt + nbk < ntile) fetch(tt + nbk);
+        int i0, j0;
+        tile_ij(tt, i0, j0);
+        double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+  #pragma unroll 8
+        for (int l = 0; l < CNB; ++l) {
+          const double a0 = Ta[ty][l], a1 = Ta[ty + 16][l];
+          const double b0 = Tb[tx][l], b1 = Tb[tx + 16][l];
+          c00 = fma(a0, b0, c00);
+          c01 = fma(a0, b1, c01);
+          c10 = fma(a1, b0, c10);
+          c11 = fma(a1, b1, c11);
+        }
+        const int r0g = i0 + ty, r1g = i0 + ty + 16, c0g = j0 + tx, c1g = j0 + tx + 16;
+        if (r0g < n && c0g <= r0g) F[(size_t)r0g * n + c0g] -= c00;
+        if (r0g < n && c1g < n && c1g <= r0g) F[(size_t)r0g * n + c1g] -= c01;
+        if (r1g < n && c0g <= r1g) F[(size_t)r1g * n + c0g] -= c10;
+        if (r1g < n && c1g < n && c1g <= r1g) F[(size_t)r1g * n + c1g] -= c11;
+        __syncthreads();
+      }
     }
     if (!grid_barrier(bar, nbk, spin_limit, st)) return;
   }
