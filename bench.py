@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--no-scale", action="store_true", help="skip the 10,000-bus measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched solves")
     ap.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing")
+    ap.add_argument("--no-vjp", action="store_true", help="skip the 10,000-bus dispatch-derivative timing")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -398,6 +399,27 @@ def main():
         out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)), "trsm_kernel": k10, "autotune_ms": tune10,
                           "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
                           "symbolic": h10.stats()}
+        if not args.no_vjp:
+            # the dispatch derivative of the converged 10,000-bus solve for 256 unit cotangents
+            h10.profile(False)
+            r10 = h10.solve("linred")
+            V = torch.as_tensor(gridgen.cotangents(n10.ng), dtype=torch.float64, device=dev)
+            gP = torch.empty((V.shape[0], n10.nb), dtype=torch.float64, device=dev)
+            gQ = torch.empty_like(gP)
+            t0 = time.perf_counter()
+            h10.vjp_prepare()
+            t_prep = time.perf_counter() - t0
+            h10.dispatch_vjp(V, gP, gQ)                    # warm-up (workspace growth)
+            reps = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                h10.dispatch_vjp(V, gP, gQ)
+                reps.append(time.perf_counter() - t0)
+            info = h10.vjp_info()
+            out["vjp_grid10k"] = {"cotangents": int(V.shape[0]), "solve_s": r10["ms_total"] * 1e-3,
+                                  "solve_iters": r10["iters"], "prepare_ms": t_prep * 1e3,
+                                  "vjp_ms": float(np.median(reps)) * 1e3, "refine_steps": info["refine_steps"],
+                                  "rel_residual": info["rel_residual"], "polish_iters": info["polish_iters"]}
     if not args.no_batch:
         out["batch96"] = run_batch(binding, args.batch_threads, rank, world, dist, dev)
     # one whole interior-point solve of the same network (LinRed), GPU path
