@@ -283,6 +283,7 @@ def main():
         h.kkt_solve(D["r"], step)
     torch.cuda.synchronize()
     trsm_kernel, trsm_tune, trsm_kernel1 = h.trsm_choice()
+    chol_form, chol_grid, chol_tune = h.chol_choice()
     n_launch0 = binding.launch_count()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -356,7 +357,9 @@ def main():
                       "route": "adjoint", "delta_w": delta,
                       "trsm_kernel": KERNEL_NAMES.get(trsm_kernel, str(trsm_kernel)),
                       "trsm_kernel_1rhs": KERNEL_NAMES.get(trsm_kernel1, str(trsm_kernel1)),
-                      "autotune_ms": trsm_tune},
+                      "autotune_ms": trsm_tune,
+                      "cholesky": {"form": {1: "barrier", 2: "dataflow"}.get(chol_form, str(chol_form)),
+                                   "ctas": chol_grid, "autotune_ms": chol_tune}},
            "clocks": clocks, "gpu_launches": int(n_launch),
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                    "includes": "H2D of x,u,lambda,y,Sigma,r + derivatives + condense + Cholesky + step + D2H of the step"},
@@ -396,7 +399,9 @@ def main():
             t10.append(a.elapsed_time(b))
         ph10 = h10.phase_times()
         k10, tune10, _ = h10.trsm_choice()
+        cf10, cg10, ct10 = h10.chol_choice()
         out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)), "trsm_kernel": k10, "autotune_ms": tune10,
+                          "cholesky": {"form": cf10, "ctas": cg10, "autotune_ms": ct10},
                           "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
                           "symbolic": h10.stats()}
         if not args.no_vjp:

@@ -79,6 +79,12 @@ typedef struct opf_options {
                              opf_condense (times each kernel on the actual right-hand
                              side and keeps the fastest)                              */
     long long spin_limit; /* iteration cap of every device-side wait; 0 = 1<<26        */
+    int chol_form;        /* dense Cholesky of Kred (Sec. 3.4): 1 = blocked right-looking
+                             kernel with grid barriers between steps; 2 = its dataflow
+                             form (panel and trailing-update CTA groups synchronised
+                             by per-column counters, so the next panel overlaps the
+                             rest of the update); 0 = autotune on the first
+                             factorisation (times both forms at a few grid sizes)   */
 } opf_options;
 
 typedef struct opf_handle opf_handle;
@@ -106,6 +112,13 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
  * *kernel1 the kernel of solves with fewer than 32 right-hand sides (1 staged,
  * 64 level-blocked, -1 not chosen yet). */
 int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);
+/* Dense Cholesky kernel in use (host outputs, may be NULL): *form as in
+ * opf_options.chol_form (0 before the first factorisation), *nblocks its grid,
+ * ms[OPF_CHOL_CANDIDATES] the autotuner's timings of {barrier form at 38, 76,
+ * 152, 304 CTAs; dataflow form at 76, 152, 304 CTAs with a small panel group;
+ * dataflow form at 152, 304 CTAs with a large panel group} (0 = not tried). */
+#define OPF_CHOL_CANDIDATES 9
+int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms);
 /* Stream for all device work (a cudaStream_t, NULL = legacy default stream). */
 int opf_set_stream(opf_handle* h, void* stream);
 

@@ -38,7 +38,8 @@ class opf_network(C.Structure):
 
 
 class opf_options(C.Structure):
-    _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong)]
+    _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong),
+                ("chol_form", C.c_int)]
 
 
 class opf_ipm_options(C.Structure):
@@ -65,6 +66,7 @@ _SIGS = {
                             C.POINTER(C.c_longlong)]),
     "opf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float), _ip]),
+    "opf_chol_choice": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_float)]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_eval_functions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_get_vector": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -169,7 +171,8 @@ def _ptr(t):
 class Handle:
     """One network on one GPU: wraps opf_create / opf_destroy and every call."""
 
-    def __init__(self, net, route: int = OPF_ROUTE_ADJOINT, rhs_block: int = 0, spin_limit: int = 0):
+    def __init__(self, net, route: int = OPF_ROUTE_ADJOINT, rhs_block: int = 0, spin_limit: int = 0,
+                 chol_form: int = 0):
         lib = load_library()
         self._keep = []
 
@@ -185,7 +188,7 @@ class Handle:
         n = opf_network(net.nb, net.nl, net.ng, net.slack, d(net.Pd), d(net.Qd), d(net.Vmin), d(net.Vmax),
                         i(net.lf), i(net.lt), d(net.r), d(net.x), d(net.b), d(net.rate), i(net.gbus),
                         d(net.Pmin), d(net.Pmax), d(net.Qmin), d(net.Qmax), d(net.c2), d(net.c1))
-        o = opf_options(route, rhs_block, spin_limit)
+        o = opf_options(route, rhs_block, spin_limit, chol_form)
         h = C.c_void_p()
         _check(lib.opf_create(C.byref(n), C.byref(o), C.byref(h)), "opf_create")
         self._keep = []
@@ -224,6 +227,16 @@ class Handle:
         _check(self._lib.opf_trsm_choice(self._h, C.byref(k), ms, C.byref(k1)), "opf_trsm_choice")
         names = ("cols", "staged1", "staged2", "staged4", "blocked", "dataflow")
         return k.value, dict(zip(names, ms)), k1.value
+
+    def chol_choice(self):
+        """(Cholesky form: 1 barrier, 2 dataflow, 0 not tuned yet; its grid;
+        autotuner ms per candidate)."""
+        f, nb = C.c_int(), C.c_int()
+        ms = (C.c_float * 9)()
+        _check(self._lib.opf_chol_choice(self._h, C.byref(f), C.byref(nb), ms), "opf_chol_choice")
+        names = ("barrier38", "barrier76", "barrier152", "barrier304", "dataflow76", "dataflow152", "dataflow304",
+                 "dataflow152_wide_panel", "dataflow304_wide_panel")
+        return f.value, nb.value, dict(zip(names, ms))
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""

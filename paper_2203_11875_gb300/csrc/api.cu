@@ -339,6 +339,7 @@ int upload_all(opf_handle* h) {
   TRY(alloc(h, &h->st, ST_WORDS));
   TRY(alloc(h, &h->pf_ws, (size_t)P.nx + 1));
   TRY(alloc(h, &h->bar, 4));
+  TRY(alloc(h, &h->chol_cnt, 2 * (size_t)((P.nu + 31) / 32 + 1)));
   CK(launch_set_identity(0, P.nu, h->Zt, h->ldp));
   // launch shapes
   int maxlen = 1;
@@ -750,29 +751,61 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
 int tune_chol_blocks(opf_handle* h, double delta_w) {
   const Plan& P = h->P;
   const int cap = h->chol_blocks;
-  const int cands[4] = {38, 76, 152, 304};
+  // candidates {form, grid, panel CTAs}: the barrier form with four grid sizes;
+  // the dataflow form with three grid sizes and a small panel group (a quarter
+  // of the first step's row groups), and with two grid sizes and a panel group
+  // of one row group per CTA
+  const int rows0 = (std::max(0, P.nu - 32) + 7) / 8;   // panel row groups of the first step
+  const int df_cap = chol_df_max_blocks();
+  const int want = h->opt.chol_form;   // 0 both, 1 barrier form only, 2 dataflow form only
+  struct Cand { int form, nb, np; };
+  const Cand cand[OPF_CHOL_CANDIDATES] = {
+      {0, 38, 0}, {0, 76, 0}, {0, 152, 0}, {0, 304, 0},
+      {1, 76, std::max(1, std::min(76 / 3, std::max(8, rows0 / 4)))},
+      {1, 152, std::max(1, std::min(152 / 3, std::max(8, rows0 / 4)))},
+      {1, 304, std::max(1, std::min(304 / 3, std::max(8, rows0 / 4)))},
+      {1, 152, std::max(1, std::min(152 / 2, std::max(8, rows0)))},
+      {1, 304, std::max(1, std::min(304 / 2, std::max(8, rows0)))}};
+  // time only from a clean status word: a run that stops early on an error
+  // (the dataflow form leaves as soon as one is flagged) would look fast
+  int st0[ST_WORDS];
+  CK(cudaMemcpyAsync(st0, h->st, sizeof(st0), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (st0[ST_CODE] != 0 || st0[ST_TIMEOUT] != 0) return OPF_OK;   // untuned; tried again next time
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   float best = 1e30f;
-  int pick = cap;
-  for (int nb : cands) {
-    if (nb > cap) continue;
+  int pick = cap, pick_df = 0, pick_np = 0;
+  for (int c = 0; c < OPF_CHOL_CANDIDATES; ++c) {
+    const int form = cand[c].form, nb = cand[c].nb, np = cand[c].np;
+    if (want != 0 && want != form + 1) continue;
+    if (form == 0 && nb > cap) continue;
+    if (form == 1 && (nb > df_cap || nb - np < 1)) continue;
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaMemsetAsync(h->st, 0, sizeof(int) * ST_WORDS, h->s));
       CK(cudaEventRecord(a, h->s));
       CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
-      CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
-      CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, nb));
+      if (form == 0) {
+        CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
+        CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, nb));
+      } else {
+        CK(launch_chol_df(h->s, P.nu, h->F, h->Fdinv, h->st, h->chol_cnt, h->spin_limit, nb, np));
+      }
       CK(cudaEventRecord(b, h->s));
       CK(cudaEventSynchronize(b));
       CK(cudaEventElapsedTime(&ms, a, b));
     }
-    if (ms < best) { best = ms; pick = nb; }
+    h->chol_ms[c] = ms;
+    if (ms < best) { best = ms; pick = nb; pick_df = form; pick_np = np; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  CK(cudaMemsetAsync(h->st, 0, sizeof(int) * ST_WORDS, h->s));
   h->chol_blocks = pick;
+  h->chol_df = pick_df;
+  h->chol_np = pick_np;
   h->chol_tuned = true;
   return OPF_OK;
 }
@@ -783,7 +816,11 @@ int factor_kred_async(opf_handle* h, double delta_w) {
   ph_begin(h, OPF_PHASE_CHOL);
   CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
   CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
-  CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, h->chol_blocks));
+  if (h->chol_df) {
+    CK(launch_chol_df(h->s, P.nu, h->F, h->Fdinv, h->st, h->chol_cnt, h->spin_limit, h->chol_blocks, h->chol_np));
+  } else {
+    CK(launch_chol(h->s, P.nu, h->F, h->Fdinv, h->st, h->bar, h->spin_limit, h->chol_blocks));
+  }
   ph_end(h);
   h->delta_w = delta_w;
   h->sens_ready = false;
@@ -828,6 +865,10 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
+  if (h->opt.chol_form < 0 || h->opt.chol_form > 2) {
+    delete h;
+    return OPF_ERR_INVALID_ARG;
+  }
   int cb = h->opt.rhs_block;
   if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32 && cb != 64 && cb != 96) {
     delete h;
@@ -841,6 +882,14 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return rc;
   }
   *out = h;
+  return OPF_OK;
+}
+
+int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (form) *form = h->chol_tuned ? 1 + h->chol_df : 0;
+  if (nblocks) *nblocks = h->chol_blocks;
+  if (ms) for (int c = 0; c < OPF_CHOL_CANDIDATES; ++c) ms[c] = h->chol_ms[c];
   return OPF_OK;
 }
 

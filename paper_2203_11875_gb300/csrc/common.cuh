@@ -204,6 +204,11 @@ cudaError_t launch_chol_prepare(cudaStream_t s, int n, const double* A, double d
 cudaError_t launch_chol(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* bar,
                         long long spin_limit, int nblocks);
 int chol_max_blocks();
+// Dataflow (barrier-free, look-ahead) Cholesky: np panel CTAs, nblocks - np
+// update CTAs (at least one); cnt holds 2 * ceil(n / 32) counters (zeroed here).
+int chol_df_max_blocks();
+cudaError_t launch_chol_df(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* cnt,
+                           long long spin_limit, int nblocks, int np);
 cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, const double* dinv, double* X, int nrhs);
 
 // vectors

@@ -296,48 +296,97 @@ __device__ __forceinline__ void fill_pairs(unsigned short* pairs) {
   }
 }
 
-// Cholesky of the 32x32 tile T in shared memory (kb valid rows, the rest an
-// identity block).  Column j: every thread takes pairs of the trailing
-// triangle from the table, so each rank-1 update is spread evenly over all
-// warps (all four FP64 pipes of the SM); the update uses the unscaled column,
-// T_il -= T_ij T_lj / d_j, and the column itself is scaled one step later, when
-// nothing reads it any more.  The thread that updates T_{j+1,j+1} computes the
-// next pivot's reciprocal square root at once, so a column costs one barrier.
-// Writes 1 / L_jj to dv[j]; returns the first failing local column or -1.
-__device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const unsigned short* pairs) {
-  const int tid = threadIdx.x;
-  // dv[j] = 1 / sqrt(pivot j), or 0 for a non-positive / non-finite pivot; every
-  // thread reads it after a barrier, so all leave together on a failure
-  if (tid == 0) {
-    const double d = T[0][0];
-    dv[0] = (d > 0.0 && isfinite(d)) ? rsqrt_nr(d) : 0.0;
+// Store the lower triangle of a factored diagonal tile (tile column k) into F.
+__device__ __forceinline__ void write_tile_back(double* F, int n, const double (*T)[CNB + 1], int k) {
+  const int k0 = k * CNB, kb = min(CNB, n - k0);
+  for (int t = threadIdx.x; t < CNB * CNB; t += blockDim.x) {
+    const int i = t / CNB, j = t % CNB;
+    if (i < kb && j <= i) F[(size_t)(k0 + i) * n + k0 + j] = T[i][j];
   }
+}
+
+// Reciprocal of a pivot, or 0 when the pivot is not a positive finite number.
+// Inside [2^-1000, 2^1000] (tested on the bit pattern, integer compares only:
+// on this GPU every FP64 instruction, compares included, goes through the FP64
+// pipe at about 64 cycles) it takes the hardware estimate rcp.approx.ftz.f64
+// and one third-order Householder step: with e = 1 - d r, 1/d = r / (1 - e) =
+// r (1 + e + e^2 + ...), so r (1 + e + e^2) leaves a relative error of e^3 --
+// three dependent FP64 operations where the IEEE division takes a longer
+// sequence, and the reciprocal of each pivot sits on the factorisation's
+// critical path.  Other positive finite pivots use the division.
+__device__ __forceinline__ double pivot_rcp(double d) {
+  const long long b = __double_as_longlong(d);
+  if (b >= (23LL << 52) && b < (2023LL << 52)) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+  }
+  return (b > 0 && b < 0x7FF0000000000000LL) ? 1.0 / d : 0.0;
+}
+
+// Cholesky of the 32x32 tile T in shared memory (kb valid rows, the rest an
+// identity block), computed as T = U D U^T with the columns of U left unscaled
+// (the root-free form) and converted to L = U D^{-1/2} at the end.  Column j:
+// every thread takes pairs of the trailing triangle from the table, so each
+// rank-1 update T_il -= T_ij T_lj / d_j is spread evenly over all warps (all
+// four FP64 pipes of the SM); the thread that updates T_{j+1,j+1} computes the
+// next pivot's reciprocal at once, so a column costs one barrier and its
+// critical path is a multiply, an FMA and a reciprocal.  The square roots of
+// the pivots are taken once, all together, at the end.  Writes 1 / L_jj to
+// dv[j]; returns the first failing local column (non-positive or non-finite
+// pivot) or -1.
+// R (optional, nr = 8 rows) holds panel rows below the tile: they are
+// eliminated along with it, as further rows of the column block, and leave as
+// rows of L (R L_kk^T = the rows given), so the panel solve costs no separate
+// sequence of dependent steps.
+__device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const unsigned short* pairs,
+                               double (*R)[CNB + 1] = nullptr, int nr = 0) {
+  const int tid = threadIdx.x;
+  // during the loop dv[j] = 1 / d_j, or 0 for a failed pivot; every thread reads
+  // it after a barrier, so all leave together on a failure
+  if (tid == 0) dv[0] = pivot_rcp(T[0][0]);
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    const double xj = dv[j];
-    if (!(xj > 0.0)) return j;
-    const double inv_d = xj * xj;
-    if (j > 0) {
-      // scale column j - 1 (not read in this step)
-      const double xp = dv[j - 1];
-      for (int i = j + tid; i < CNB; i += blockDim.x) T[i][j - 1] *= xp;
-      if (tid == 0) T[j - 1][j - 1] *= xp;
-    }
+    const double rj = dv[j];
+    if (__double_as_longlong(rj) <= 0) return j;   // 0 marks a failed pivot
     const int cnt = (CNB - 1 - j) * (CNB - j) / 2;
     const int diag_next = (CNB - 2 - j) * (CNB - 1 - j) / 2;   // position of (j+1, j+1)
-    for (int t = tid; t < cnt; t += blockDim.x) {
+    // thread 0 takes the next pivot's pair first, so its reciprocal overlaps
+    // the rest of the update
+    for (int q = tid; q < cnt; q += blockDim.x) {
+      int t = diag_next + q;
+      if (t >= cnt) t -= cnt;
       const int pr = pairs[t], i = pr >> 8, l = pr & 255;
-      const double v = fma(-T[i][j] * inv_d, T[l][j], T[i][l]);
+      const double v = fma(-T[i][j] * rj, T[l][j], T[i][l]);
       T[i][l] = v;
-      if (t == diag_next && j + 1 < kb) dv[j + 1] = (v > 0.0 && isfinite(v)) ? rsqrt_nr(v) : 0.0;
+      if (q == 0 && j + 1 < kb) dv[j + 1] = pivot_rcp(v);
+    }
+    if (nr > 0) {
+      // panel rows: R_rl -= R_rj T_lj / d_j for l > j (eight rows, row index fastest)
+      for (int q = tid; q < 8 * (CNB - 1 - j); q += blockDim.x) {
+        const int rr = q & 7, l = j + 1 + (q >> 3);
+        R[rr][l] = fma(-R[rr][j] * rj, T[l][j], R[rr][l]);
+      }
     }
     __syncthreads();
   }
-  if (kb > 0) {
-    const double xp = dv[kb - 1];
-    for (int i = kb + tid; i < CNB; i += blockDim.x) T[i][kb - 1] *= xp;
-    if (tid == 0) T[kb - 1][kb - 1] *= xp;
+  // L_jj = sqrt(d_j) = d_j / sqrt(d_j), L_ij = U_ij / sqrt(d_j)
+  if (tid < kb) {
+    const double d = T[tid][tid], s = rsqrt_nr(d);
+    dv[tid] = s;
+    T[tid][tid] = d * s;
   }
+  __syncthreads();
+  for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+    const int i = t / CNB, j = t % CNB;
+    if (j < kb && i > j) T[i][j] *= dv[j];
+  }
+  if (nr > 0)
+    for (int t = tid; t < 8 * CNB; t += blockDim.x) {
+      const int rr = t / CNB, j = t % CNB;
+      if (j < kb) R[rr][j] *= dv[j];
+    }
   __syncthreads();
   return -1;
 }
@@ -346,9 +395,10 @@ __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const u
 // 32x32 tiles, one persistent cooperative grid, two phases per block column
 // separated by a bounded grid barrier:
 //   P. the rows below the diagonal tile are shared out eight per CTA, one per
-//      warp; a CTA with rows (and CTA 0, which writes the tile back) factors the
-//      diagonal tile itself in shared memory, then each warp solves its row
-//      x L_kk^T = a (one column per lane) -- no barrier between the two;
+//      warp; a CTA with rows (and CTA 0, which writes the tile back once the
+//      barrier shows every CTA done reading it) factors the diagonal tile
+//      itself in shared memory, then each warp solves its row x L_kk^T = a
+//      (one column per lane) -- no barrier between the two;
 //   U. the trailing update A_ij -= L_ik L_jk^T in 16x16 sub-tiles.
 // A non-positive or non-finite pivot records DEV_NOT_PD with its column.  The
 // inverse diagonal of L is written to dinv (used by the solves).
@@ -380,10 +430,9 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
         if (tid == 0) set_status(st, DEV_NOT_PD, k0 + fail);
       } else {
         if (blockIdx.x == 0) {
-          for (int t = tid; t < CNB * CNB; t += blockDim.x) {
-            const int i = t / CNB, j = t % CNB;
-            if (i < kb && j <= i) F[(size_t)(k0 + i) * n + k0 + j] = Ta[i][j];
-          }
+          // the factored tile goes back to F after the barrier: the other panel
+          // CTAs may still be reading the unfactored one now
+          for (int t = tid; t < CNB * CNB; t += blockDim.x) Tb[t / CNB][t % CNB] = Ta[t / CNB][t % CNB];
           if (tid < kb) dinv_out[k0 + tid] = dv[tid];
         }
         for (int rb = blockIdx.x; rb < row_blocks; rb += nbk) {
@@ -402,6 +451,10 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
     }
     if (!grid_barrier(bar, nbk, spin_limit, st)) return;
     if (vst[ST_CODE] != 0) return;
+    if (blockIdx.x == 0) {
+      write_tile_back(F, n, Tb, k);
+      __syncthreads();   // Tb is reused by the update below
+    }
     const int m = nt - k - 1;
     const long long ntile = (long long)m * (m + 1) / 2;
     if (ntile < (long long)nbk) {
@@ -785,6 +838,224 @@ cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld) {
   k_set_identity<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, X, ld);
   note_launch();
   return cudaGetLastError();
+}
+
+}  // namespace condipm
+
+// ============================================================================
+// Dataflow form of the blocked Cholesky (look-ahead without grid barriers).
+// The CTAs split into a panel group (np CTAs) and an update group.  Step k:
+//   panel group: wait until tile column k has received the step k-1 update
+//     (counter cdone[k-1]), factor the diagonal tile (every panel CTA, in
+//     shared memory; CTA 0 writes it back), solve the panel rows below it (one
+//     row per warp), count the finished row groups into pdone[k];
+//   update group: wait until pdone[k] is complete, then apply the step-k update
+//     to the tiles (or 16x16 sub-tiles) it owns -- each tile has one owner CTA
+//     for all steps, so a tile's updates stay in order -- doing the tiles of
+//     column k+1 first and counting them into cdone[k].
+// The next diagonal factorisation therefore starts as soon as its column is
+// updated, while the rest of the trailing update proceeds.  Every wait is
+// bounded and also ends when the status word reports an error; the panel
+// values are read through L2 (ld.cg), since an SM's L1 may hold them from the
+// previous step's update.
+namespace condipm {
+namespace {
+
+__device__ __forceinline__ bool chol_wait(const unsigned* p, unsigned need, long long limit, int* st) {
+  volatile int* vst = st;
+  long long it = 0;
+  unsigned v, ns = 32;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  while (v < need) {
+    if (++it > limit) { atomicExch(&st[ST_TIMEOUT], 1); return false; }
+    if ((it & 255) == 0 && (vst[ST_TIMEOUT] || vst[ST_CODE])) return false;
+    __nanosleep(ns);
+    ns = ns < 256 ? 2 * ns : 256;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  }
+  return true;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_out, int* st, unsigned* cnt,
+                                                 int np, int sub_mode, long long spin_limit) {
+  __shared__ double Ta[CNB][CNB + 1];
+  __shared__ double Tb[CNB][CNB + 1];
+  __shared__ double Tr[8][CNB + 1];   // the panel rows eliminated with the diagonal tile
+  __shared__ double dv[CNB];
+  __shared__ unsigned short pairs[CNB * (CNB + 1) / 2];
+  __shared__ int ok_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int nt = (n + CNB - 1) / CNB;
+  unsigned* pdone = cnt;          // [nt]
+  unsigned* cdone = cnt + nt;     // [nt]
+  fill_pairs(pairs);
+  __syncthreads();
+  const bool panel = (int)blockIdx.x < np;
+  const int nU = gridDim.x - np, ub = blockIdx.x - np;
+  for (int k = 0; k < nt; ++k) {
+    const int k0 = k * CNB, kb = min(CNB, n - k0);
+    const int r0 = k0 + kb, nrows = n - r0;
+    const int row_blocks = (nrows + nwarps - 1) / nwarps;
+    const int m = nt - k - 1;
+    if (panel) {
+      if (tid == 0) {
+        int ok = 1;
+        if (k > 0) {
+          // (sub-)tiles of column k below its diagonal, counted at step k-1
+          const int gmax = sub_mode ? (n + 15) / 16 : nt;
+          const unsigned need = sub_mode ? (unsigned)((gmax - 2 * k) + (gmax - 2 * k - 1)) : (unsigned)(nt - k);
+          ok = chol_wait(cdone + (k - 1), need, spin_limit, st);
+        }
+        ok_s = ok;
+      }
+      __syncthreads();
+      if (!ok_s) return;
+      // every panel CTA has finished with diagonal tile k-1 once column k is updated
+      if (blockIdx.x == 0 && k > 0) write_tile_back(F, n, Tb, k - 1);
+      if ((int)blockIdx.x == 0 || (int)blockIdx.x < row_blocks) {
+        for (int t = tid; t < CNB * CNB; t += blockDim.x) {
+          const int i = t / CNB, j = t % CNB;
+          Ta[i][j] = (i < kb && j <= i) ? __ldcg(&F[(size_t)(k0 + i) * n + k0 + j]) : (i == j ? 1.0 : 0.0);
+        }
+        // the first row group of this CTA (rows r0 + 8 blockIdx.x ..) rides along
+        const bool fused = (int)blockIdx.x < row_blocks;
+        const int rf0 = r0 + (int)blockIdx.x * nwarps;
+        if (fused)
+          for (int t = tid; t < 8 * CNB; t += blockDim.x) {
+            const int rr = t / CNB, j = t % CNB;
+            Tr[rr][j] = (rf0 + rr < n && j < kb) ? __ldcg(&F[(size_t)(rf0 + rr) * n + k0 + j]) : 0.0;
+          }
+        __syncthreads();
+        const int fail = block_chol_tile(Ta, dv, kb, pairs, Tr, fused ? 8 : 0);
+        if (fail >= 0) {
+          if (tid == 0) set_status(st, DEV_NOT_PD, k0 + fail);
+          return;
+        }
+        if (blockIdx.x == 0) {
+          // the factored tile goes back to F only at the next step: the other
+          // panel CTAs may still be reading the unfactored one now
+          for (int t = tid; t < CNB * CNB; t += blockDim.x) Tb[t / CNB][t % CNB] = Ta[t / CNB][t % CNB];
+          if (tid < kb) dinv_out[k0 + tid] = dv[tid];
+        }
+        int mine = 0;
+        if (fused) {
+          ++mine;
+          for (int t = tid; t < 8 * CNB; t += blockDim.x) {
+            const int rr = t / CNB, j = t % CNB;
+            if (rf0 + rr < n && j < kb) F[(size_t)(rf0 + rr) * n + k0 + j] = Tr[rr][j];
+          }
+        }
+        // further row groups: one row per warp, forward substitution with L_kk
+        for (int rb = blockIdx.x + np; rb < row_blocks; rb += np) {
+          ++mine;
+          const int r = r0 + rb * nwarps + warp;
+          if (r < n) {
+            double a = lane < kb ? __ldcg(&F[(size_t)r * n + k0 + lane]) : 0.0;
+            for (int j = 0; j < kb; ++j) {
+              const double xj = __shfl_sync(0xffffffffu, a, j) * dv[j];
+              if (lane == j) a = xj;
+              else if (lane > j) a = fma(-xj, Ta[lane][j], a);
+            }
+            if (lane < kb) F[(size_t)r * n + k0 + lane] = a;
+          }
+        }
+        __syncthreads();
+        if (tid == 0 && mine > 0) red_add_release(pdone + k, (unsigned)mine);
+      }
+      continue;
+    }
+    // ---- update group
+    if (m == 0) continue;
+    if (tid == 0) ok_s = chol_wait(pdone + k, (unsigned)row_blocks, spin_limit, st);
+    __syncthreads();
+    if (!ok_s) return;
+    // ownership: the (sub-)tiles of the lower triangle are numbered column by
+    // column, (sub-)column gj holding (sub-)rows gj .. gmax-1, and tile number t
+    // belongs to update CTA t mod nU for every step.  The trailing triangle of a
+    // step is a suffix of that numbering, so every CTA gets an equal share of
+    // it.  Columns in order, column k+1 first.
+    const int g = sub_mode ? 2 : 1;                   // (sub-)tiles per tile side
+    const int gmax = sub_mode ? (n + 15) / 16 : nt;   // (sub-)rows in the matrix
+    for (int gj = g * (k + 1); gj < gmax; ++gj) {
+      const bool col0 = gj < g * (k + 2);
+      const int base = gj * gmax - gj * (gj - 1) / 2;   // number of tile (gj, gj)
+      int gi = gj + (((ub - base) % nU) + nU) % nU;
+      for (; gi < gmax; gi += nU) {
+        const int hh = sub_mode ? 16 : CNB;
+        const int i0 = gi * hh, j0 = gj * hh;
+        if (sub_mode) {
+          for (int t = tid; t < 16 * CNB; t += blockDim.x) {
+            const int rr = t / CNB, l = t % CNB;
+            Ta[rr][l] = (i0 + rr < n && l < kb) ? __ldcg(&F[(size_t)(i0 + rr) * n + k0 + l]) : 0.0;
+            Tb[rr][l] = (j0 + rr < n && l < kb) ? __ldcg(&F[(size_t)(j0 + rr) * n + k0 + l]) : 0.0;
+          }
+          __syncthreads();
+          const int rr = tid >> 4, cc = tid & 15;
+          double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+          for (int l = 0; l < CNB; l += 2) {
+            acc0 = fma(Ta[rr][l], Tb[cc][l], acc0);
+            acc1 = fma(Ta[rr][l + 1], Tb[cc][l + 1], acc1);
+          }
+          const int gr = i0 + rr, gc = j0 + cc;
+          if (gr < n && gc < n && gc <= gr) F[(size_t)gr * n + gc] -= acc0 + acc1;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int rr = (tid >> 5) + 8 * q, l = tid & 31;
+            Ta[rr][l] = (i0 + rr < n && l < kb) ? __ldcg(&F[(size_t)(i0 + rr) * n + k0 + l]) : 0.0;
+            Tb[rr][l] = (j0 + rr < n && l < kb) ? __ldcg(&F[(size_t)(j0 + rr) * n + k0 + l]) : 0.0;
+          }
+          __syncthreads();
+          const int ty = tid >> 4, tx = tid & 15;
+          double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+#pragma unroll 8
+          for (int l = 0; l < CNB; ++l) {
+            const double a0 = Ta[ty][l], a1 = Ta[ty + 16][l];
+            const double b0 = Tb[tx][l], b1 = Tb[tx + 16][l];
+            c00 = fma(a0, b0, c00);
+            c01 = fma(a0, b1, c01);
+            c10 = fma(a1, b0, c10);
+            c11 = fma(a1, b1, c11);
+          }
+          const int r0g = i0 + ty, r1g = i0 + ty + 16, c0g = j0 + tx, c1g = j0 + tx + 16;
+          if (r0g < n && c0g <= r0g) F[(size_t)r0g * n + c0g] -= c00;
+          if (r0g < n && c1g < n && c1g <= r0g) F[(size_t)r0g * n + c1g] -= c01;
+          if (r1g < n && c0g <= r1g) F[(size_t)r1g * n + c0g] -= c10;
+          if (r1g < n && c1g < n && c1g <= r1g) F[(size_t)r1g * n + c1g] -= c11;
+        }
+        __syncthreads();
+        if (tid == 0 && col0) red_add_release(cdone + k, 1u);
+      }
+    }
+  }
+  if (blockIdx.x == 0 && nt > 0) write_tile_back(F, n, Tb, nt - 1);
+}
+
+}  // namespace
+
+int chol_df_max_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_df, 256, 0);
+  return sms * (per > 0 ? per : 1);
+}
+
+cudaError_t launch_chol_df(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* cnt,
+                           long long spin_limit, int nblocks, int np) {
+  const int nt = (n + CNB - 1) / CNB;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 2 * (size_t)nt, s);
+  if (e != cudaSuccess) return e;
+  const int nU = std::max(1, nblocks - np);
+  const int sub_mode = (nt * (nt - 1) / 2 < 2 * nU) ? 1 : 0;
+  void* args[] = {&F, &n, &dinv, &st, &cnt, &np, (void*)&sub_mode, &spin_limit};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_chol_df, dim3(nblocks), dim3(256), args, 0, s);
 }
 
 }  // namespace condipm

@@ -97,7 +97,10 @@ struct opf_handle {
   size_t ws_cap = 0;
   // launch shapes
   int lu_blocks = 1, lu_threads = 256, lu_maxlen = 1, chol_blocks = 1, cb = 1;
-  bool chol_tuned = false;       // Cholesky grid size picked by timing (first factorisation)
+  bool chol_tuned = false;       // Cholesky form and grid size picked by timing (first factorisation)
+  int chol_df = 0, chol_np = 0;  // dataflow form (1) and its panel CTAs
+  float chol_ms[OPF_CHOL_CANDIDATES] = {};   // tuner timings
+  unsigned* chol_cnt = nullptr;  // its step counters (2 x tile columns)
   // condensation + first Cholesky attempt of the interior-point loop as a CUDA
   // graph (inputs in the loop's fixed device buffers)
   cudaGraphExec_t cf_exec = nullptr;

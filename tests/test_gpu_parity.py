@@ -157,16 +157,18 @@ def _first_failing_column(M):
     return -1
 
 
+@pytest.mark.parametrize("chol_form", [1, 2])
 @pytest.mark.parametrize("name", ["ring30", "grid2000"])
-def test_kkt_factor_and_solve_match_full_space_step(pkg, name):
+def test_kkt_factor_and_solve_match_full_space_step(pkg, name, chol_form):
     net, rec = oracle_iterate(name)
     lay = model.Layout(net)
-    h = pkg.Handle(net)
+    h = pkg.Handle(net, chol_form=chol_form)
     w, lam, y = rec["w"], rec["lam"], rec["y"]
     gpu_eval(pkg, h, lay, w, lam, y)
     sw, ss, delta = rec["sig_w"], rec["sig_s"], rec["delta"]
     h.condense(T(sw[:lay.nu]), T(sw[lay.nu:]), T(ss))
     assert h.kkt_factor(delta) == -1
+    assert h.chol_choice()[0] == chol_form
     F = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
     h.get_factor(F)
     F = N(F).reshape(lay.nu, lay.nu)
@@ -189,20 +191,35 @@ def test_kkt_factor_and_solve_match_full_space_step(pkg, name):
     assert rel_err(N(adj).reshape(3, -1), step) <= 1e-12
 
 
-def test_kkt_factor_reports_not_pd(pkg):
+# (network, seed, multiplier scale): scaling lam and y makes W, hence Kred,
+# indefinite; the grid2000 cases fail in tile columns 5 and 1 of the blocked
+# factorisation (columns 169 and 47, pivots far from zero), the ring30 case in
+# its first tile
+@pytest.mark.parametrize("name,seed,scale", [("ring30", 11, 1.0), ("grid2000", 11, 3.0), ("grid2000", 11, 10.0)])
+@pytest.mark.parametrize("chol_form", [1, 2])
+def test_kkt_factor_reports_not_pd(pkg, name, seed, scale, chol_form):
     """An indefinite condensed matrix is reported with its failing column; a large
     enough delta_w then succeeds (the inertia-correction loop of Sec. 4.3)."""
-    net, lay, w, lam, y, sw, ss = random_point("ring30", seed=11)
-    h = pkg.Handle(net)
+    net, lay, w, lam, y, sw, ss = random_point(name, seed=seed)
+    lam, y = scale * lam, scale * y
+    h = pkg.Handle(net, chol_form=chol_form)
     gpu_eval(pkg, h, lay, w, lam, y)
     h.condense(T(sw[:lay.nu]), T(sw[lay.nu:]), T(ss))
     _, G, A = model.jacobians(lay, w)
     W = model.lagrangian_hessian(lay, w, lam, y)
     Ko = kkt.kred_definition(G, A, W, sw, ss, lay.nu)
-    want = _first_failing_column(0.5 * (Ko + Ko.T))
+    S = 0.5 * (Ko + Ko.T)
+    want = _first_failing_column(S)
     assert want >= 0
     assert h.kkt_factor(0.0) == want
-    assert h.kkt_factor(1e4) == -1
+    assert h.chol_choice()[0] == chol_form
+    big = 2.0 * abs(np.linalg.eigvalsh(S)[0]) + 1.0
+    assert h.kkt_factor(big) == -1
+    # and the factor of the shifted matrix is right after the aborted one
+    F = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
+    h.get_factor(F)
+    F = N(F).reshape(lay.nu, lay.nu)
+    assert rel_err(F @ F.T, S + big * np.eye(lay.nu)) <= TOL_KRED
 
 
 @pytest.mark.parametrize("name", ["ring30", "grid2000"])
