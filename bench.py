@@ -244,6 +244,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing")
     ap.add_argument("--no-vjp", action="store_true", help="skip the 10,000-bus dispatch-derivative timing")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
+    ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
+                    help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -261,7 +263,7 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     net = gridgen.grid2000()
-    h = binding.Handle(net)
+    h = binding.Handle(net, chol_form=args.chol_form)
     stream = torch.cuda.Stream(device=dev)
     h.set_stream(stream)
     it = synthetic_iterate(net, h.nx, h.nu, h.m)
@@ -310,6 +312,9 @@ def main():
     h.profile(False)
     cf = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     full = [ev[k][0].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    split = {"eval": float(np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])),
+             "condense_cholesky": float(np.mean(cf)),
+             "step_recovery": float(np.mean([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)]))}
     t_cf, t_full = float(np.mean(cf)), float(np.mean(full))
     if dist:
         t = torch.tensor([t_cf, t_full], dtype=torch.float64, device=dev)
@@ -363,6 +368,7 @@ def main():
            "clocks": clocks, "gpu_launches": int(n_launch),
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                    "includes": "H2D of x,u,lambda,y,Sigma,r + derivatives + condense + Cholesky + step + D2H of the step"},
+           "split_ms_per_step": split,
            "phases_ms_per_step": {p: v[0] / args.steps for p, v in phases.items()},
            "roofline": {"bound": "alu", "kernel": trsm_name,
                         "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -374,7 +380,7 @@ def main():
         out["value"] = t_cf / world
     if not args.no_scale:
         n10 = gridgen.grid10k()
-        h10 = binding.Handle(n10)
+        h10 = binding.Handle(n10, chol_form=args.chol_form)
         h10.set_stream(stream)
         i10 = synthetic_iterate(n10, h10.nx, h10.nu, h10.m)
         D10 = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in i10.items()}

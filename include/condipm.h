@@ -85,6 +85,15 @@ typedef struct opf_options {
                              by per-column counters, so the next panel overlaps the
                              rest of the update); 0 = autotune on the first
                              factorisation (times both forms at a few grid sizes)   */
+    int rhs1_kernel;      /* solve kernel for one right-hand side (the Newton-step
+                             recovery): 1 = staged supernodal kernel in one CTA; 64 =
+                             level-blocked kernel over several CTAs with grid
+                             barriers; 65 = level-blocked kernel in one CTA with the
+                             vector in shared memory; 66 = level-blocked kernel on a
+                             thread-block cluster, a copy of the vector in each
+                             CTA's shared memory (65 and 66 fall back to 64 when
+                             they do not fit); 0 = autotune together with rhs_block
+                             (until then: 1)                                       */
 } opf_options;
 
 typedef struct opf_handle opf_handle;
@@ -110,7 +119,9 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
  * timings of {column-parallel, staged 1, 2, 4, level-blocked, dataflow}
  * (0 = not tried),
  * *kernel1 the kernel of solves with fewer than 32 right-hand sides (1 staged,
- * 64 level-blocked, -1 not chosen yet). */
+ * 64 level-blocked, 65 level-blocked in one CTA with the vector in shared
+ * memory, 66 level-blocked on a thread-block cluster -- 65 and 66 for one
+ * right-hand side only, others then use 64 --, -1 not chosen yet). */
 int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);
 /* Dense Cholesky kernel in use (host outputs, may be NULL): *form as in
  * opf_options.chol_form (0 before the first factorisation), *nblocks its grid,

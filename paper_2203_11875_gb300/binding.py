@@ -39,7 +39,7 @@ class opf_network(C.Structure):
 
 class opf_options(C.Structure):
     _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong),
-                ("chol_form", C.c_int)]
+                ("chol_form", C.c_int), ("rhs1_kernel", C.c_int)]
 
 
 class opf_ipm_options(C.Structure):
@@ -172,7 +172,7 @@ class Handle:
     """One network on one GPU: wraps opf_create / opf_destroy and every call."""
 
     def __init__(self, net, route: int = OPF_ROUTE_ADJOINT, rhs_block: int = 0, spin_limit: int = 0,
-                 chol_form: int = 0):
+                 chol_form: int = 0, rhs1_kernel: int = 0):
         lib = load_library()
         self._keep = []
 
@@ -188,7 +188,7 @@ class Handle:
         n = opf_network(net.nb, net.nl, net.ng, net.slack, d(net.Pd), d(net.Qd), d(net.Vmin), d(net.Vmax),
                         i(net.lf), i(net.lt), d(net.r), d(net.x), d(net.b), d(net.rate), i(net.gbus),
                         d(net.Pmin), d(net.Pmax), d(net.Qmin), d(net.Qmax), d(net.c2), d(net.c1))
-        o = opf_options(route, rhs_block, spin_limit, chol_form)
+        o = opf_options(route, rhs_block, spin_limit, chol_form, rhs1_kernel)
         h = C.c_void_p()
         _check(lib.opf_create(C.byref(n), C.byref(o), C.byref(h)), "opf_create")
         self._keep = []

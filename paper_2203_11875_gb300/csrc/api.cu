@@ -285,9 +285,39 @@ int upload_all(opf_handle* h) {
     int *a, *b, *c, *d;
     TRY(upload(h, &a, rptr)); TRY(upload(h, &b, rows)); TRY(upload(h, &c, rsn)); TRY(upload(h, &d, doff));
     (k ? h->bkU : h->bkL) = BlkDev{C.nlev, a, b, c, cd.sn_first, cd.sn_w, d, cd.ext_beg, cd.ext_end};
+    for (int l = 0; l < C.nlev; ++l) h->lu1s_ymax = std::max(h->lu1s_ymax, rptr[l + 1] - rptr[l]);
+    // the one-CTA form's row descriptions
+    std::vector<int> ma(4 * rows.size()), mb(4 * rows.size());
+    for (size_t q = 0; q < rows.size(); ++q) {
+      const int r = rows[q], sn = rsn[q], f = C.sn_first[sn], w = C.sn_w[sn];
+      ma[4 * q] = r; ma[4 * q + 1] = C.ext_beg[r]; ma[4 * q + 2] = C.ext_end[r]; ma[4 * q + 3] = 0;
+      mb[4 * q] = r; mb[4 * q + 1] = r - f; mb[4 * q + 2] = w; mb[4 * q + 3] = doff[sn] + (r - f) * w;
+    }
+    int *pa, *pb;
+    TRY(upload(h, &pa, ma)); TRY(upload(h, &pb, mb));
+    (k ? h->l1U : h->l1L) = Lu1sDev{C.nlev, a, reinterpret_cast<const int4*>(pa), reinterpret_cast<const int4*>(pb)};
     const size_t nd = std::max<size_t>(1, size_t(doff.back()));
     if (k == 0) { TRY(alloc(h, &h->D_L, nd)); TRY(alloc(h, &h->D_Ut, nd)); }
     else { TRY(alloc(h, &h->D_U, nd)); TRY(alloc(h, &h->D_Lt, nd)); }
+  }
+  h->lu1s_ok = sizeof(double) * ((size_t)P.nx + (size_t)h->lu1s_ymax) <= trsm_lu1s_max_smem();
+  // the cluster form of the one-right-hand-side solve, for 4, 8 and 16 CTAs
+  for (int c = 0; c < 3; ++c) {
+    const int CL = 4 << c;
+    Cl1Dev dv[2];
+    int ymax = 0, nlev = 0;
+    for (int k = 0; k < 2; ++k) {
+      ClSched S;
+      if (!build_cl_sched(k ? P.csU : P.csL, CL, S).empty()) return OPF_ERR_INVALID_ARG;
+      int *tp, *ta, *tb;
+      TRY(upload(h, &tp, S.t_ptr)); TRY(upload(h, &ta, S.ta)); TRY(upload(h, &tb, S.tb));
+      dv[k] = Cl1Dev{S.nlev, CL, S.ymax, tp, reinterpret_cast<const int4*>(ta), reinterpret_cast<const int4*>(tb)};
+      ymax = std::max(ymax, S.ymax);
+      nlev = std::max(nlev, S.nlev);
+    }
+    h->cl1L[c] = dv[0];
+    h->cl1U[c] = dv[1];
+    h->cl1_ok[c] = trsm_lu1c_max_clusters(CL, P.nx, ymax, nlev) >= 1;
   }
   h->ldp = (P.nu + 31) / 32 * 32;
   h->cs_ncb_max = std::max((P.nu + 31) / 32, 64);
@@ -529,8 +559,25 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
   const double* dlo = trans ? h->inv_diag : nullptr;
   const double* dup = trans ? nullptr : h->inv_diag;
   const bool cols_ok = ncols >= 32 && xc == 1 && (ncols + 31) / 32 <= h->cs_ncb_max;
-  int mode = (ncols >= 32 && xc == 1) ? h->trsm_mode : (xc == 1 && h->trsm_mode1 == 64 ? 64 : 1);
+  int mode = (ncols >= 32 && xc == 1) ? h->trsm_mode
+                                      : (xc == 1 && h->trsm_mode1 >= 64 ? h->trsm_mode1 : 1);
   if (mode < 0) mode = 32;
+  if (mode == 65 && ncols == 1 && h->lu1s_ok) {
+    if (timed) ph_begin(h, OPF_PHASE_TRSM);
+    CK(launch_trsm_lu1s(s, h->lu1s_g, h->l1L, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, h->l1U, h->Up_ci, upv,
+                        trans ? h->D_Lt : h->D_U, X, xr, P.nx, h->lu1s_ymax));
+    if (timed) ph_end(h);
+    return OPF_OK;
+  }
+  if (mode == 66 && ncols == 1 && h->cl1_ok[h->cl1_pick]) {
+    if (timed) ph_begin(h, OPF_PHASE_TRSM);
+    const int c = h->cl1_pick;
+    CK(launch_trsm_lu1c(s, h->cl1L[c], h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, h->cl1U[c], h->Up_ci, upv,
+                        trans ? h->D_Lt : h->D_U, X, xr, P.nx));
+    if (timed) ph_end(h);
+    return OPF_OK;
+  }
+  if (mode == 65 || mode == 66) mode = 64;
   if (mode == 64 && ncols == 1) {
     double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
     if (!Y) return OPF_ERR_OOM;
@@ -675,22 +722,38 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
     h->tune_ms[0][k] = ms;
     if (ms < best) { best = ms; pick = m; }
   }
-  // one right-hand side (the step recovery): staged (one CTA) or level-blocked
-  {
+  // one right-hand side (the step recovery): staged (one CTA), level-blocked
+  // over 8 .. 64 CTAs, or level-blocked in one CTA with the vector in shared
+  // memory (4 or 8 lanes per row)
+  if (h->opt.rhs1_kernel == 0) {
     float b1 = 1e30f;
-    int p1 = 1, pb = h->blk1_blocks;
-    const int c1[5] = {1, 64, 64, 64, 64};
-    const int nb1[5] = {0, 8, 16, 32, 64};
-    for (int k = 0; k < 5; ++k) {
+    int p1 = 1, pb = h->blk1_blocks, pg = h->lu1s_g, pc = h->cl1_pick;
+    const int c1[10] = {1, 64, 64, 64, 64, 65, 65, 66, 66, 66};
+    const int nb1[10] = {0, 8, 16, 32, 64, 0, 0, 0, 0, 0};
+    const int g1[10] = {0, 0, 0, 0, 0, 8, 4, 0, 0, 0};
+    const int cl1[10] = {-1, -1, -1, -1, -1, -1, -1, 0, 1, 2};
+    for (int k = 0; k < 10; ++k) {
+      if (c1[k] == 65 && !h->lu1s_ok) continue;
+      if (c1[k] == 66 && !h->cl1_ok[cl1[k]]) continue;
       h->trsm_mode1 = c1[k];
       if (nb1[k]) h->blk1_blocks = nb1[k];
+      if (g1[k]) h->lu1s_g = g1[k];
+      if (cl1[k] >= 0) h->cl1_pick = cl1[k];
       float ms = 0.f;
       TRY(time_solve(1, &ms));
       h->tune_ms[1][k] = ms;
-      if (ms < b1) { b1 = ms; p1 = c1[k]; pb = nb1[k] ? nb1[k] : pb; }
+      if (ms < b1) {
+        b1 = ms;
+        p1 = c1[k];
+        pb = nb1[k] ? nb1[k] : pb;
+        pg = g1[k] ? g1[k] : pg;
+        pc = cl1[k] >= 0 ? cl1[k] : pc;
+      }
     }
     h->trsm_mode1 = p1;
     h->blk1_blocks = pb;
+    h->lu1s_g = pg;
+    h->cl1_pick = pc;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -875,6 +938,12 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return OPF_ERR_INVALID_ARG;
   }
   h->trsm_mode = cb ? cb : -1;
+  const int k1 = h->opt.rhs1_kernel;
+  if (k1 != 0 && k1 != 1 && k1 != 64 && k1 != 65 && k1 != 66) {
+    delete h;
+    return OPF_ERR_INVALID_ARG;
+  }
+  if (k1) h->trsm_mode1 = k1;
   h->cb = pick_cb(h->P.nu);
   int rc = upload_all(h);
   if (rc != OPF_OK) {

@@ -183,6 +183,38 @@ int trsm_df_max_blocks();
 cudaError_t launch_trsm_blk1(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                              double* X, double* Y, long long xs, int nblocks, unsigned* bar, int* st,
                              long long spin_limit);
+// One-CTA level-blocked schedule of one factor: the levels of the level list
+// (as in BlkDev) and, per position q in it, the row's descriptions for the
+// two phases: ma[q] = {row, first and end external entry, 0}, mb[q] = {row,
+// offset of the row in its supernode, supernode width, offset of the row's
+// entries in D}.
+struct Lu1sDev {
+  int nlev;
+  const int* lvl_rptr;
+  const int4 *ma, *mb;
+};
+// One right-hand side X[i * xs] through both triangles (L then U) in one CTA
+// with the vector and a level's worth of Y (ymax entries) in shared memory;
+// g = lanes per row (4 or 8).  The shared memory it needs, (n + ymax) doubles,
+// must not exceed trsm_lu1s_max_smem().
+cudaError_t launch_trsm_lu1s(cudaStream_t s, int g, const Lu1sDev& L, const int* ciL, const double* valL,
+                             const double* DL, const Lu1sDev& U, const int* ciU, const double* valU,
+                             const double* DU, double* X, long long xs, int n, int ymax);
+size_t trsm_lu1s_max_smem();
+// One right-hand side on one thread-block cluster of CL CTAs (CL <= 16), each
+// with a full copy of the vector; the schedule of each triangle (layout as the
+// host ClSched) shares every level's supernodes out over the CTAs.
+struct Cl1Dev {
+  int nlev, CL, ymax;
+  const int* t_ptr;
+  const int4 *ta, *tb;
+};
+cudaError_t launch_trsm_lu1c(cudaStream_t s, const Cl1Dev& L, const int* ciL, const double* valL,
+                             const double* DL, const Cl1Dev& U, const int* ciU, const double* valU,
+                             const double* DU, double* X, long long xs, int n);
+// clusters of CL CTAs that can be resident at once with the shared memory the
+// solve needs, (n + ymax) doubles and nlev + 1 ints (0: it does not fit)
+int trsm_lu1c_max_clusters(int CL, int n, int ymax, int nlev);
 cudaError_t launch_fill_stream(cudaStream_t s, long long nslots, const long long* slot, const int* src,
                                const double* vals, const double* inv_diag, int unit, unsigned char* stream);
 

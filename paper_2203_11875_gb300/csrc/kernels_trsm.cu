@@ -22,7 +22,10 @@
 
 #include "common.cuh"
 
+#include <cooperative_groups.h>
+
 namespace condipm {
+namespace cg = cooperative_groups;
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -769,7 +772,328 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk1(BlkDev S, const int* 
   }
 }
 
+// One right-hand side in one CTA: the whole vector lives in shared memory (xv)
+// together with the current level's Y (yv, indexed by the row's position in
+// the level, where a supernode's rows are consecutive), so every gather of X
+// and Y is a shared-memory access and the levels are separated by
+// __syncthreads alone, with no grid-wide barrier.  Same two phases per level as
+// the multi-CTA form (external part with G lanes per row, then the dense
+// inverse of the supernode's diagonal block).  Each row's description is one
+// int4 per phase (MA: row, external entries; MB: row, offset in its supernode,
+// width, offset of its row of D), and a thread's descriptions for the next
+// level, and its D entries for this level, are loaded ahead of the barriers, so
+// a level waits on global memory about once instead of three times per phase.
+template <int G>
+__device__ __forceinline__ void lu1s_tri(int nlev, const int* __restrict__ lvl_rptr, const int4* __restrict__ MA,
+                                         const int4* __restrict__ MB, const int* __restrict__ ci,
+                                         const double* __restrict__ val, const double* __restrict__ D, double* xv,
+                                         double* yv) {
+  constexpr int RPW = 32 / G;   // rows per warp
+  constexpr int ND = 32 / G;    // D entries per lane (supernodes are at most 32 wide)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int sub = lane / G, gl = lane % G;
+  const int slot = warp * RPW + sub, nslot = nwarps * RPW;
+  const int4 z4 = make_int4(0, 0, 0, 0);
+  int4 ma = z4, mb = z4;
+  if (nlev > 0 && lvl_rptr[0] + slot < lvl_rptr[1]) { ma = MA[lvl_rptr[0] + slot]; mb = MB[lvl_rptr[0] + slot]; }
+  for (int lev = 0; lev < nlev; ++lev) {
+    const int q0 = lvl_rptr[lev], q1 = lvl_rptr[lev + 1];
+    const bool first_on = q0 + slot < q1;
+    // D row of this thread's first-pass row, for phase B
+    double dreg[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      const int j = gl + k * G;
+      dreg[k] = (first_on && j < mb.z) ? D[mb.w + j] : 0.0;
+    }
+    // the next level's descriptions of this thread's first-pass row
+    int4 na = z4, nb = z4;
+    if (lev + 1 < nlev && q1 + slot < lvl_rptr[lev + 2]) { na = MA[q1 + slot]; nb = MB[q1 + slot]; }
+    // A: Y_r = X_r - external part of row r
+    for (int qb = q0 + warp * RPW, pass = 0; qb < q1; qb += nslot, ++pass) {
+      const int q = qb + sub;
+      double a0 = 0.0, a1 = 0.0;
+      int r = 0;
+      if (q < q1) {
+        const int4 m = pass == 0 ? ma : MA[q];
+        r = m.x;
+        int e = m.y + gl;
+        for (; e + G < m.z; e += 2 * G) {
+          a0 = fma(val[e], xv[ci[e]], a0);
+          a1 = fma(val[e + G], xv[ci[e + G]], a1);
+        }
+        if (e < m.z) a0 = fma(val[e], xv[ci[e]], a0);
+      }
+      double a = a0 + a1;
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+      if (q < q1 && gl == 0) yv[q - q0] = xv[r] - a;
+    }
+    __syncthreads();
+    // B: X_r = D_s(r, :) Y_s
+    for (int qb = q0 + warp * RPW, pass = 0; qb < q1; qb += nslot, ++pass) {
+      const int q = qb + sub;
+      double a = 0.0;
+      int r = 0;
+      if (q < q1) {
+        if (pass == 0) {
+          r = mb.x;
+          const double* Ys = yv + (q - q0 - mb.y);   // Y of the supernode's first row
+#pragma unroll
+          for (int k = 0; k < ND; ++k) {
+            const int j = gl + k * G;
+            if (j < mb.z) a = fma(dreg[k], Ys[j], a);
+          }
+        } else {
+          const int4 m = MB[q];
+          r = m.x;
+          const double* Ys = yv + (q - q0 - m.y);
+          for (int j = gl; j < m.z; j += G) a = fma(D[m.w + j], Ys[j], a);
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+      if (q < q1 && gl == 0) xv[r] = a;
+    }
+    __syncthreads();
+    ma = na;
+    mb = nb;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(1024) k_trsm_lu1s(Lu1sDev L, const int* __restrict__ ciL,
+                                                    const double* __restrict__ valL, const double* __restrict__ DL,
+                                                    Lu1sDev U, const int* __restrict__ ciU,
+                                                    const double* __restrict__ valU, const double* __restrict__ DU,
+                                                    double* X, long long xs, int n) {
+  extern __shared__ double sm1[];
+  double* xv = sm1;       // n
+  double* yv = sm1 + n;   // the largest level
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xv[i] = X[(long long)i * xs];
+  __syncthreads();
+  lu1s_tri<G>(L.nlev, L.lvl_rptr, L.ma, L.mb, ciL, valL, DL, xv, yv);
+  lu1s_tri<G>(U.nlev, U.lvl_rptr, U.ma, U.mb, ciU, valU, DU, xv, yv);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)i * xs] = xv[i];
+}
+
+// One right-hand side on a thread-block cluster of CL CTAs: every CTA keeps a
+// full copy of the vector in its shared memory, so every gather is a local
+// shared-memory access.  The supernodes of each level are shared out over the
+// CTAs; a CTA computes Y for the rows of its supernodes (phase A, external
+// parts), then X_r = D_s(r, :) Y_s (phase B), writing X_r into every CTA's copy
+// (distributed shared memory stores) before the cluster barrier that ends the
+// level.  A level's FP64 work spreads over CL SMs and costs one CTA barrier and
+// one hardware cluster barrier; a thread's first row of the next level is
+// described, its first two external entries and its D row fetched, ahead of
+// the barriers.
+template <int G>
+__device__ __forceinline__ void lu1c_tri(const Cl1Dev& S, int p, int CL, const int* __restrict__ ci,
+                                         const double* __restrict__ val, const double* __restrict__ D,
+                                         double* xv, double* yv, double* const* rx, int* lv) {
+  constexpr int RPW = 32 / G;
+  constexpr int ND = 32 / G;   // D entries per lane (supernodes are at most 32 wide)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int sub = lane / G, gl = lane % G;
+  const int slot = warp * RPW + sub, nslot = nwarps * RPW;
+  const int L1 = S.nlev + 1;
+  // this CTA's level boundaries, staged in shared memory (lv: nlev + 1 ints)
+  int* tp = lv;
+  for (int i = threadIdx.x; i < L1; i += blockDim.x) tp[i] = S.t_ptr[p * L1 + i];
+  __syncthreads();
+  const int4 z4 = make_int4(0, 0, 0, 0);
+  cg::cluster_group cl = cg::this_cluster();
+  int4 ma = z4, mb = z4;
+  int pc0 = 0, pc1 = 0;   // ... and its first two external entries
+  double pv0 = 0.0, pv1 = 0.0;
+  if (S.nlev > 0 && tp[0] + slot < tp[1]) {
+    ma = S.ta[tp[0] + slot];
+    mb = S.tb[tp[0] + slot];
+    const int e0 = ma.y + gl, e1 = e0 + G;
+    if (e0 < ma.z) { pc0 = ci[e0]; pv0 = val[e0]; }
+    if (e1 < ma.z) { pc1 = ci[e1]; pv1 = val[e1]; }
+  }
+  for (int lev = 0; lev < S.nlev; ++lev) {
+    const int t0 = tp[lev], t1 = tp[lev + 1];
+    double dreg[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      const int j = gl + k * G;
+      dreg[k] = (t0 + slot < t1 && j < mb.z) ? D[mb.w + j] : 0.0;
+    }
+    int4 na = z4, nb = z4;
+    if (lev + 1 < S.nlev && t1 + slot < tp[lev + 2]) {
+      na = S.ta[t1 + slot];
+      nb = S.tb[t1 + slot];
+    }
+    // A: Y_r = X_r - external part of row r, G lanes per row
+    for (int tb = t0 + warp * RPW, pass = 0; tb < t1; tb += nslot, ++pass) {
+      const int t = tb + sub;
+      double s0 = 0.0, s1 = 0.0;
+      int4 m = z4;
+      if (t < t1) {
+        m = pass == 0 ? ma : S.ta[t];
+        int e = m.y + gl;
+        if (pass == 0) {
+          if (e < m.z) s0 = pv0 * xv[pc0];
+          if (e + G < m.z) s1 = pv1 * xv[pc1];
+          e += 2 * G;
+        }
+        for (; e + G < m.z; e += 2 * G) {
+          s0 = fma(val[e], xv[ci[e]], s0);
+          s1 = fma(val[e + G], xv[ci[e + G]], s1);
+        }
+        if (e < m.z) s0 = fma(val[e], xv[ci[e]], s0);
+      }
+      double a = s0 + s1;
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+      if (t < t1 && gl == 0) yv[m.w] = xv[m.x] - a;
+    }
+    __syncthreads();
+    // the next level's first two external entries of this thread's first row
+    pc0 = pc1 = 0;
+    pv0 = pv1 = 0.0;
+    {
+      const int e0 = na.y + gl, e1 = e0 + G;
+      if (e0 < na.z) { pc0 = ci[e0]; pv0 = val[e0]; }
+      if (e1 < na.z) { pc1 = ci[e1]; pv1 = val[e1]; }
+    }
+    // B: X_r = D_s(r, :) Y_s, written into every CTA's copy
+    for (int tb = t0 + warp * RPW, pass = 0; tb < t1; tb += nslot, ++pass) {
+      const int t = tb + sub;
+      double a = 0.0;
+      int r = 0;
+      if (t < t1) {
+        if (pass == 0) {
+          r = mb.x;
+#pragma unroll
+          for (int k = 0; k < ND; ++k) {
+            const int j = gl + k * G;
+            if (j < mb.z) a = fma(dreg[k], yv[mb.y + j], a);
+          }
+        } else {
+          const int4 m = S.tb[t];
+          r = m.x;
+          const double* Dr = D + m.w;
+          for (int j = gl; j < m.z; j += G) a = fma(Dr[j], yv[m.y + j], a);
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+      if (t < t1)
+        for (int q = gl; q < CL; q += G) rx[q][r] = a;
+    }
+    cl.sync();   // every X of the level is in every copy
+    ma = na;
+    mb = nb;
+  }
+}
+
+constexpr int LU1C_THREADS = 1024;
+
+template <int G>
+__global__ void __launch_bounds__(LU1C_THREADS, 1) k_trsm_lu1c(Cl1Dev L, const int* __restrict__ ciL,
+                                                               const double* __restrict__ valL,
+                                                               const double* __restrict__ DL, Cl1Dev U,
+                                                               const int* __restrict__ ciU,
+                                                               const double* __restrict__ valU,
+                                                               const double* __restrict__ DU, double* X,
+                                                               long long xs, int n) {
+  extern __shared__ double smc[];
+  __shared__ double* rx[16];
+  cg::cluster_group cl = cg::this_cluster();
+  const int p = int(cl.block_rank()), CL = int(cl.num_blocks());
+  double* xv = smc;       // n: this CTA's copy of the vector
+  double* yv = smc + n;   // Y of the rows of the supernodes this CTA owns in the current level
+  int* lv = reinterpret_cast<int*>(yv + max(L.ymax, U.ymax));   // level boundaries of one triangle
+  if (threadIdx.x < CL) rx[threadIdx.x] = cl.map_shared_rank(xv, threadIdx.x);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xv[i] = X[(long long)i * xs];
+  cl.sync();   // every copy is loaded before any CTA writes into another's
+  lu1c_tri<G>(L, p, CL, ciL, valL, DL, xv, yv, rx, lv);
+  lu1c_tri<G>(U, p, CL, ciU, valU, DU, xv, yv, rx, lv);
+  if (p == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)i * xs] = xv[i];
+}
+
 }  // namespace
+
+int trsm_lu1c_max_clusters(int CL, int n, int ymax, int nlev) {
+  const size_t smem = sizeof(double) * ((size_t)n + (size_t)ymax) + sizeof(int) * ((size_t)nlev + 1);
+  if (allow_max_smem((const void*)k_trsm_lu1c<8>) != cudaSuccess) return 0;
+  if (CL > 8 && cudaFuncSetAttribute((const void*)k_trsm_lu1c<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                    cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(LU1C_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_trsm_lu1c<8>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return ncl;
+}
+
+cudaError_t launch_trsm_lu1c(cudaStream_t s, const Cl1Dev& L, const int* ciL, const double* valL,
+                             const double* DL, const Cl1Dev& U, const int* ciU, const double* valU,
+                             const double* DU, double* X, long long xs, int n) {
+  const int CL = L.CL;
+  const size_t smem = sizeof(double) * ((size_t)n + (size_t)std::max(L.ymax, U.ymax)) +
+                      sizeof(int) * ((size_t)std::max(L.nlev, U.nlev) + 1);
+  cudaError_t e = allow_max_smem((const void*)k_trsm_lu1c<8>);
+  if (e != cudaSuccess) return e;
+  if (CL > 8) {
+    e = cudaFuncSetAttribute((const void*)k_trsm_lu1c<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(LU1C_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, k_trsm_lu1c<8>, L, ciL, valL, DL, U, ciU, valU, DU, X, xs, n);
+}
+
+size_t trsm_lu1s_max_smem() {
+  int dev = 0, mx = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, (const void*)k_trsm_lu1s<8>);
+  return mx > int(fa.sharedSizeBytes) ? size_t(mx) - fa.sharedSizeBytes : 0;
+}
+
+cudaError_t launch_trsm_lu1s(cudaStream_t s, int g, const Lu1sDev& L, const int* ciL, const double* valL,
+                             const double* DL, const Lu1sDev& U, const int* ciU, const double* valU,
+                             const double* DU, double* X, long long xs, int n, int ymax) {
+  const size_t smem = sizeof(double) * ((size_t)n + (size_t)ymax);
+  const void* fn = g == 4 ? (const void*)k_trsm_lu1s<4> : (const void*)k_trsm_lu1s<8>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_max_smem(fn);
+    if (e != cudaSuccess) return e;
+  }
+  if (g == 4) k_trsm_lu1s<4><<<1, 1024, smem, s>>>(L, ciL, valL, DL, U, ciU, valU, DU, X, xs, n);
+  else k_trsm_lu1s<8><<<1, 1024, smem, s>>>(L, ciL, valL, DL, U, ciU, valU, DU, X, xs, n);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_trsm_blk1(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                              double* X, double* Y, long long xs, int nblocks, unsigned* bar, int* st,

@@ -73,7 +73,8 @@ struct opf_handle {
   int sn_cb = 0;                 // columns per CTA of the staged solves (0 = level fallback)
   int trsm_mode = -1;            // multi-RHS solve kernel: -1 autotune, 32 column-parallel,
                                  // 1/2/4 staged with that many columns per CTA
-  float tune_ms[3][6] = {};      // autotuner timings: {cols, staged 1, 2, 4, blocked, dataflow} per role
+  float tune_ms[3][10] = {};     // autotuner timings per role: multi-RHS {cols, staged 1, 2, 4, blocked,
+                                 // dataflow}; one RHS {staged, blocked x 4 grids, one-CTA x 2, cluster x 3}
   int trsm_mode1 = -1;           // kernel of the solves with fewer than 32 right-hand sides
                                  // (-1 autotune, 1 staged, 64 level-blocked)
   condipm::BlkDev bkL{}, bkU{};  // level-blocked schedules of the lower / upper solves
@@ -83,6 +84,13 @@ struct opf_handle {
   int blk_max = 1;               // resident CTAs of the level-blocked kernel
   int blk_ksplit = 0;            // its CTAs per 32-column block (0: as many as fit, at most 16)
   int blk1_blocks = 32;          // CTAs of the single-right-hand-side level-blocked solve
+  condipm::Lu1sDev l1L{}, l1U{}; // the one-CTA single-right-hand-side solve's schedules
+  int lu1s_ymax = 0;             // rows of the largest level (the one-CTA solve's Y buffer)
+  bool lu1s_ok = false;          // the one-CTA solve's vector and Y fit in shared memory
+  int lu1s_g = 8;                // its lanes per row
+  condipm::Cl1Dev cl1L[3]{}, cl1U[3]{};   // cluster one-RHS schedules for 4, 8, 16 CTAs
+  bool cl1_ok[3] = {false, false, false};  // ... and whether each fits on the device
+  int cl1_pick = 2;              // the cluster size in use (index)
   condipm::DfDev dfL{}, dfU{};   // dataflow task lists of the lower / upper solves
   unsigned* df_cnt = nullptr;    // their supernode counters (2 x column blocks x supernodes)
   int df_max = 1, df_ksplit = 0; // resident CTAs of the dataflow kernel; CTAs per column block

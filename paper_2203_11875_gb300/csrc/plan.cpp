@@ -907,4 +907,56 @@ std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double*
   return "";
 }
 
+
+std::string build_cl_sched(const ColSched& C, int CL, ClSched& S) {
+  S = ClSched();
+  S.CL = CL;
+  S.nlev = C.nlev;
+  const int ns = int(C.sn_first.size());
+  if (CL < 1 || CL > 16) return "bad cluster size";
+  std::vector<int> doff(ns + 1, 0), owner(ns, 0);
+  for (int q = 0; q < ns; ++q) doff[q + 1] = doff[q] + C.sn_w[q] * C.sn_w[q];
+  // owners: per level, largest work first to the least loaded CTA
+  for (int l = 0; l < C.nlev; ++l) {
+    std::vector<std::pair<long long, int>> work;
+    for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q) {
+      long long wk = (long long)C.sn_w[q] * C.sn_w[q];
+      for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) wk += C.ext_end[r] - C.ext_beg[r];
+      work.push_back({wk, q});
+    }
+    std::stable_sort(work.begin(), work.end(), [](const std::pair<long long, int>& a,
+                                                  const std::pair<long long, int>& b) { return a.first > b.first; });
+    std::vector<long long> load(CL, 0);
+    for (const auto& wq : work) {
+      int best = 0;
+      for (int p = 1; p < CL; ++p)
+        if (load[p] < load[best]) best = p;
+      owner[wq.second] = best;
+      load[best] += wq.first;
+    }
+  }
+  const int L1 = C.nlev + 1;
+  S.t_ptr.assign(size_t(CL) * L1, 0);
+  auto push4 = [](std::vector<int>& v, int a, int b, int c, int d) {
+    v.push_back(a); v.push_back(b); v.push_back(c); v.push_back(d);
+  };
+  for (int p = 0; p < CL; ++p) {
+    for (int l = 0; l < C.nlev; ++l) {
+      S.t_ptr[p * L1 + l] = int(S.ta.size() / 4);
+      int ycount = 0;
+      for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q) {
+        if (owner[q] != p) continue;
+        const int f = C.sn_first[q], w = C.sn_w[q];
+        for (int r = f; r < f + w; ++r) {
+          push4(S.ta, r, C.ext_beg[r], C.ext_end[r], ycount + (r - f));
+          push4(S.tb, r, ycount, w, doff[q] + (r - f) * w);
+        }
+        ycount += w;
+      }
+      S.ymax = std::max(S.ymax, ycount);
+    }
+    S.t_ptr[p * L1 + C.nlev] = int(S.ta.size() / 4);
+  }
+  return "";
+}
 }  // namespace condipm

@@ -97,6 +97,21 @@ struct ColSched {
   std::vector<int> ext_beg, ext_end, int_beg;  // [n]
 };
 
+// Cluster form of the one-right-hand-side level-blocked solve on CL CTAs.  In
+// every level the supernodes are shared out over the CTAs by largest work
+// first to the least loaded CTA; a CTA computes both phases of the supernodes
+// it owns.  For CTA p and level l, entries t_ptr[p * (nlev + 1) + l] .. of
+//   ta: {row, first and end external entry, Y slot of the row},
+//   tb: {row, Y slot of the supernode's first row, width, offset of the row of
+//        D_s};
+// a supernode's rows are consecutive, so its Y is consecutive too.
+struct ClSched {
+  int CL = 0, nlev = 0, ymax = 0;
+  std::vector<int> t_ptr;
+  std::vector<int> ta, tb;   // 4 ints per row
+};
+std::string build_cl_sched(const ColSched& C, int CL, ClSched& S);
+
 struct Plan {
   // ---- sizes
   int nb = 0, nl = 0, ng = 0, slack = 0, nx = 0, nu = 0, nw = 0, m = 0, nlim = 0, ne = 0;

@@ -61,3 +61,14 @@ def test_solve_on_a_stream_replays_the_condensation_graph(pkg):
     assert a["graph_iters"] == 0 and b["graph_iters"] == b["iters"] - 1
     assert a["iters"] == b["iters"]
     assert abs(a["obj"] - b["obj"]) <= 1e-12 * abs(a["obj"])
+
+
+@pytest.mark.parametrize("rhs1", [1, 64, 65, 66])
+def test_one_rhs_kernels_give_the_same_solve(pkg, rhs1):
+    """The Newton-step recovery's single-vector solves through each kernel: the
+    loop must take the same path to the same optimum."""
+    net = gridgen.grid2000()
+    ref = pkg.Handle(net, rhs1_kernel=1).solve("linred")
+    res = pkg.Handle(net, rhs1_kernel=rhs1).solve("linred")
+    assert ref["status"] == res["status"] == 0
+    assert abs(res["obj"] - ref["obj"]) <= 1e-9 * abs(ref["obj"])

@@ -83,9 +83,11 @@ def test_model_values_and_derivatives(pkg, name):
 
 
 @pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000"])
-def test_gx_factor_and_solves(pkg, name):
+@pytest.mark.parametrize("rhs1", [0, 1, 64, 65, 66])
+def test_gx_factor_and_solves(pkg, name, rhs1):
+    """rhs1 = the one-right-hand-side kernel (0: staged until an autotune ran)."""
     net, lay, w, lam, y, _, _ = random_point(name, seed=2)
-    h = pkg.Handle(net)
+    h = pkg.Handle(net, rhs1_kernel=rhs1)
     gpu_eval(pkg, h, lay, w)
     h.gx_factor()
     _, G, _ = model.jacobians(lay, w)
