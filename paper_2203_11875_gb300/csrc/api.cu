@@ -370,6 +370,8 @@ int upload_all(opf_handle* h) {
   TRY(alloc(h, &h->pf_ws, (size_t)P.nx + 1));
   TRY(alloc(h, &h->bar, 4));
   TRY(alloc(h, &h->chol_cnt, 2 * (size_t)((P.nu + 31) / 32 + 1)));
+  TRY(alloc(h, &h->Finv, (size_t)std::max(1, (P.nu + 31) / 32) * 32 * 32));
+  h->chol_solve_cl = (P.nu + 31) / 32 > 8 ? 16 : 8;
   CK(launch_set_identity(0, P.nu, h->Zt, h->ldp));
   // launch shapes
   int maxlen = 1;
@@ -766,6 +768,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   cudaStream_t s = h->s;
   const int nu = P.nu, nx = P.nx, nw = P.nw;
   h->psi_valid = false;
+  h->finv_valid = false;   // the explicit route uses the factor's buffer as scratch
   if (!h->have_lu) TRY(factor_async(h));
   CK(cudaMemcpyAsync(h->sig_s, sig_s, sizeof(double) * std::max(1, P.m), cudaMemcpyDeviceToDevice, s));
   // A4: K = W + A^T Sigma_s A + diag(Sigma)
@@ -887,6 +890,24 @@ int factor_kred_async(opf_handle* h, double delta_w) {
   ph_end(h);
   h->delta_w = delta_w;
   h->sens_ready = false;
+  h->finv_valid = false;
+  return OPF_OK;
+}
+
+// X (row-major nu x k) <- (L L^T)^{-1} X with the current factor: for a few
+// columns one cluster per column (tile inverses computed on first use after
+// each factorisation), else one CTA per column
+int chol_solve_async(opf_handle* h, double* X, int k) {
+  const int nu = h->P.nu;
+  if (k >= 1 && k <= 8 && h->chol_solve_cl > 0) {
+    if (!h->finv_valid) {
+      CK(launch_tile_inv(h->s, nu, h->F, h->Fdinv, h->Finv));
+      h->finv_valid = true;
+    }
+    CK(launch_chol_solve_cl(h->s, nu, h->F, h->Finv, X, k, h->chol_solve_cl));
+    return OPF_OK;
+  }
+  CK(launch_chol_solve(h->s, nu, h->F, h->Fdinv, X, k));
   return OPF_OK;
 }
 

@@ -239,6 +239,13 @@ int chol_max_blocks();
 // Dataflow (barrier-free, look-ahead) Cholesky: np panel CTAs, nblocks - np
 // update CTAs (at least one); cnt holds 2 * ceil(n / 32) counters (zeroed here).
 int chol_df_max_blocks();
+// Finv[I] = inverse of the I-th 32 x 32 diagonal tile of the Cholesky factor
+// (zero-padded), for nt = ceil(n / 32) tiles
+cudaError_t launch_tile_inv(cudaStream_t s, int n, const double* F, const double* dinv, double* Finv);
+// X (row-major n x nrhs) <- (L L^T)^{-1} X, one cluster of CL (<= 16) CTAs per
+// column, with the tile inverses of launch_tile_inv
+cudaError_t launch_chol_solve_cl(cudaStream_t s, int n, const double* F, const double* Finv, double* X, int nrhs,
+                                 int CL);
 cudaError_t launch_chol_df(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* cnt,
                            long long spin_limit, int nblocks, int np);
 cudaError_t launch_chol_solve(cudaStream_t s, int n, const double* F, const double* dinv, double* X, int nrhs);

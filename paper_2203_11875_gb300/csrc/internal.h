@@ -8,6 +8,8 @@ int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam
 int factor_async(opf_handle* h);
 int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s);
 int factor_kred_async(opf_handle* h, double delta_w);
+// X (row-major nu x k, device) <- (L L^T)^{-1} X with the current factor
+int chol_solve_async(opf_handle* h, double* X, int k);
 // K_aug p = -r (external layout), with up to `refine` refinement corrections
 int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int refine);
 int polish_solution(opf_handle* h, double tol, int max_iter);

@@ -263,6 +263,7 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
     h->have_condense = true;
     h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
     h->sens_ready = false;
+    h->finv_valid = false;
     h->delta_w = 0.0;
   } else {
     TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));

@@ -1059,3 +1059,156 @@ cudaError_t launch_chol_df(cudaStream_t s, int n, double* F, double* dinv, int* 
 }
 
 }  // namespace condipm
+
+// ============================================================================
+// Solves with the dense Cholesky factor for a few right-hand sides (the Newton
+// step's reduced system, Sec. 3.4).  A column's forward and backward
+// substitutions are chains of nt = ceil(n / 32) tile steps; one CTA per column
+// leaves each step to one SM and walks the diagonal tile row by row.  Here a
+// thread-block cluster takes one column: every CTA keeps a copy of the
+// solution in shared memory, the row tiles are shared out over the CTAs, and a
+// tile step is x_J = Linv_JJ part_J by the tile's owner (explicit inverses of
+// the diagonal tiles, computed once per factorisation), written into every
+// copy, one cluster barrier, then every CTA folds x_J into the partial sums of
+// its later tiles.
+#include <cooperative_groups.h>
+namespace condipm {
+namespace cgl = cooperative_groups;
+namespace {
+
+// Finv[I] = L_II^{-1} (32 x 32, zero outside the tile's kb x kb lower triangle):
+// forward substitution on the identity, one row per step, 32 x 32 threads
+__global__ void __launch_bounds__(1024) k_tile_inv(int n, const double* __restrict__ F,
+                                                   const double* __restrict__ dinv, double* __restrict__ Finv) {
+  __shared__ double Lt[CNB][CNB + 1];
+  __shared__ double Y[CNB][CNB + 1];
+  const int I = blockIdx.x, i0 = I * CNB, kb = min(CNB, n - i0);
+  const int r = threadIdx.x / CNB, c = threadIdx.x % CNB;
+  Lt[r][c] = (r < kb && c <= r) ? F[(size_t)(i0 + r) * n + i0 + c] : 0.0;
+  Y[r][c] = (r == c && r < kb) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int i = 0; i < kb; ++i) {
+    if (r == i) Y[i][c] *= dinv[i0 + i];
+    __syncthreads();
+    if (r > i && r < kb) Y[r][c] = fma(-Lt[r][i], Y[i][c], Y[r][c]);
+    __syncthreads();
+  }
+  Finv[(size_t)I * CNB * CNB + r * CNB + c] = Y[r][c];
+}
+
+// One cluster per right-hand side column (X row-major n x nrhs); CTA p owns
+// the row tiles p, p + CL, ...; 32 warps, warp w handles row (or column) w of
+// a tile with the lanes over the other index and a shuffle reduction.
+__global__ void __launch_bounds__(1024, 1) k_chol_solve_cl(int n, const double* __restrict__ F,
+                                                           const double* __restrict__ Finv, double* X, int nrhs) {
+  extern __shared__ double smd[];
+  __shared__ double* rx[16];
+  cgl::cluster_group cl = cgl::this_cluster();
+  const int p = int(cl.block_rank()), CL = int(cl.num_blocks());
+  const int col = blockIdx.x / CL;
+  const int nt = (n + CNB - 1) / CNB, nown = (nt - p + CL - 1) / CL;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* xv = smd;                      // nt * 32: this CTA's copy of the solution
+  double* part = smd + (size_t)nt * CNB; // nown * 32: partial sums of the owned tiles
+  if (threadIdx.x < CL) rx[threadIdx.x] = cl.map_shared_rank(xv, threadIdx.x);
+  for (int i = threadIdx.x; i < nt * CNB; i += blockDim.x) xv[i] = 0.0;
+  for (int o = 0; o < nown; ++o) {
+    const int g = (p + o * CL) * CNB + lane;
+    if (w == 0) part[o * CNB + lane] = g < n ? X[(size_t)g * nrhs + col] : 0.0;
+  }
+  cl.sync();
+  // forward: L x = b
+  for (int J = 0; J < nt; ++J) {
+    if (J % CL == p) {
+      const double* Li = Finv + (size_t)J * CNB * CNB;
+      double v = Li[w * CNB + lane] * part[(J / CL) * CNB + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < CL) rx[lane][J * CNB + w] = v;
+    }
+    cl.sync();
+    // part_I -= L_IJ x_J for the owned tiles I > J (row w of the tile per warp)
+    const double xj = xv[J * CNB + lane];
+    const int gc = J * CNB + lane;
+    for (int o = 0; o < nown; ++o) {
+      const int I = p + o * CL;
+      if (I <= J) continue;
+      const int gr = I * CNB + w;
+      double v = (gr < n && gc < n) ? F[(size_t)gr * n + gc] * xj : 0.0;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+      if (lane == 0) part[o * CNB + w] -= v;
+    }
+    __syncthreads();
+  }
+  // backward: L^T x = y, starting from the forward solution
+  for (int o = 0; o < nown; ++o)
+    if (w == 0) part[o * CNB + lane] = xv[(p + o * CL) * CNB + lane];
+  cl.sync();   // no copy is overwritten before every CTA has read its y
+  for (int I = nt - 1; I >= 0; --I) {
+    if (I % CL == p) {
+      const double* Li = Finv + (size_t)I * CNB * CNB;
+      double v = Li[lane * CNB + w] * part[(I / CL) * CNB + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < CL) rx[lane][I * CNB + w] = v;
+    }
+    cl.sync();
+    // part_J -= L_IJ^T x_I for the owned tiles J < I (column w of the tile per warp)
+    const int gr = I * CNB + lane;
+    const double xi = xv[gr];
+    for (int o = 0; o < nown; ++o) {
+      const int J = p + o * CL;
+      if (J >= I) continue;
+      const int gc = J * CNB + w;
+      double v = (gr < n && gc < n) ? F[(size_t)gr * n + gc] * xi : 0.0;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+      if (lane == 0) part[o * CNB + w] -= v;
+    }
+    __syncthreads();
+  }
+  if (p == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * nrhs + col] = xv[i];
+}
+
+}  // namespace
+
+cudaError_t launch_tile_inv(cudaStream_t s, int n, const double* F, const double* dinv, double* Finv) {
+  const int nt = (n + CNB - 1) / CNB;
+  if (nt <= 0) return cudaSuccess;
+  k_tile_inv<<<nt, 1024, 0, s>>>(n, F, dinv, Finv);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_solve_cl(cudaStream_t s, int n, const double* F, const double* Finv, double* X, int nrhs,
+                                 int CL) {
+  const int nt = (n + CNB - 1) / CNB;
+  if (nrhs <= 0 || nt <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * ((size_t)nt * CNB + (size_t)((nt + CL - 1) / CL) * CNB);
+  if (CL > 8) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_chol_solve_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e = allow_max_smem((const void*)k_chol_solve_cl);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL * nrhs);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, k_chol_solve_cl, n, F, Finv, X, nrhs);
+}
+
+}  // namespace condipm

@@ -155,7 +155,7 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   CKK(cudaMemcpyAsync(p.w, E, sizeof(double) * (size_t)nu * k, cudaMemcpyDeviceToDevice, s));
   CKK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, E + (size_t)nu * k, k, 1, p.w, k, 1, k, -1.0,
                   1.0));
-  CKK(launch_chol_solve(s, nu, h->F, h->Fdinv, p.w, k));
+  TRYK(chol_solve_async(h, p.w, k));
   double* px = p.w + (size_t)nu * k;
   if (h->psi_valid && k <= 4) {
     // the condensation left S_x = -G_x^{-1} G_u (in Z) and Psi = G_x^{-T} H_x (in

@@ -107,6 +107,9 @@ struct opf_handle {
   int lu_blocks = 1, lu_threads = 256, lu_maxlen = 1, chol_blocks = 1, cb = 1;
   bool chol_tuned = false;       // Cholesky form and grid size picked by timing (first factorisation)
   int chol_df = 0, chol_np = 0;  // dataflow form (1) and its panel CTAs
+  double* Finv = nullptr;        // inverses of the factor's 32 x 32 diagonal tiles (few-RHS solves)
+  bool finv_valid = false;       // Finv belongs to the current factor
+  int chol_solve_cl = 0;         // cluster size of the few-RHS solve (0: one CTA per column)
   float chol_ms[OPF_CHOL_CANDIDATES] = {};   // tuner timings
   unsigned* chol_cnt = nullptr;  // its step counters (2 x tile columns)
   // condensation + first Cholesky attempt of the interior-point loop as a CUDA
