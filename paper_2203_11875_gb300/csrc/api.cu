@@ -323,20 +323,50 @@ int upload_all(opf_handle* h) {
   h->cs_ncb_max = std::max((P.nu + 31) / 32, 64);
   // dataflow task lists: phase A then phase B of each level's rows, each row's
   // supernode, and the supernodes its external entries lie in
-  size_t nsn_max = 1;
+  size_t nsn_max = 1, nck_max = 1, nchunked_max = 1;
   for (int k = 0; k < 2; ++k) {
     const ColSched& C = k ? P.csU : P.csL;
     const CSR& M = k ? P.Up : P.Lo;
     const int nsn = int(C.sn_first.size());
     nsn_max = std::max(nsn_max, size_t(nsn));
-    std::vector<int> sn_of(P.nx, -1), task, dptr(P.nx + 1, 0), dsn;
+    std::vector<int> sn_of(P.nx, -1), task, dptr(P.nx + 1, 0), dsn, leaf;
     for (int q = 0; q < nsn; ++q)
       for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) sn_of[r] = q;
+    // narrow supernodes without external entries need no waiting and no Y: a
+    // separate pass multiplies them by their inverse blocks
+    std::vector<char> is_leaf(nsn, 0);
+    for (int q = 0; q < nsn; ++q) {
+      bool ext = false;
+      for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) ext = ext || C.ext_end[r] > C.ext_beg[r];
+      if (!ext && C.sn_w[q] <= DF_LEAF_W) { is_leaf[q] = 1; leaf.push_back(q); }
+    }
+    // long rows: chunks of at most DF_CHUNK external entries, ids in row order
+    std::vector<int> ck_row, ck_e0, ck_e1, rw_ck0(P.nx + 1, 0), rw_cidx(P.nx, 0);
+    int nchunked = 0;
+    for (int r = 0; r < P.nx; ++r) {
+      const int e0 = C.ext_beg[r], len = C.ext_end[r] - e0;
+      if (len > DF_CHUNK && !is_leaf[sn_of[r]]) {
+        const int m = (len + DF_CHUNK - 1) / DF_CHUNK;
+        for (int k = 0; k < m; ++k) {
+          ck_row.push_back(r);
+          ck_e0.push_back(e0 + int((long long)len * k / m));
+          ck_e1.push_back(e0 + int((long long)len * (k + 1) / m));
+        }
+        rw_cidx[r] = nchunked++;
+      }
+      rw_ck0[r + 1] = int(ck_row.size());
+    }
     for (int l = 0; l < C.nlev; ++l) {
       for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
-        for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(r);
+        if (!is_leaf[q])
+          for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) {
+            if (rw_ck0[r + 1] > rw_ck0[r])
+              for (int k = rw_ck0[r]; k < rw_ck0[r + 1]; ++k) task.push_back(P.nx + k);
+            else
+              task.push_back(r);
+          }
       for (int q = C.lvl_ptr[l]; q < C.lvl_ptr[l + 1]; ++q)
-        if (C.sn_w[q] > DF_INLINE_B)   // narrower supernodes: the last phase-A task does phase B
+        if (!is_leaf[q] && C.sn_w[q] > DF_INLINE_B)   // narrower supernodes: the last phase-A task does phase B
           for (int r = C.sn_first[q]; r < C.sn_first[q] + C.sn_w[q]; ++r) task.push_back(-1 - r);
     }
     std::vector<int> seen(nsn, -1);
@@ -349,12 +379,19 @@ int upload_all(opf_handle* h) {
     }
     const ColDev& cd = k ? h->csU : h->csL;
     const BlkDev& bd = k ? h->bkU : h->bkL;
-    int *a, *b, *c, *d;
+    int *a, *b, *c, *d, *e, *f1, *f2, *f3, *f4, *f5;
     TRY(upload(h, &a, task)); TRY(upload(h, &b, sn_of)); TRY(upload(h, &c, dptr)); TRY(upload(h, &d, dsn));
+    TRY(upload(h, &e, leaf));
+    TRY(upload(h, &f1, ck_row)); TRY(upload(h, &f2, ck_e0)); TRY(upload(h, &f3, ck_e1));
+    TRY(upload(h, &f4, rw_ck0)); TRY(upload(h, &f5, rw_cidx));
     (k ? h->dfU : h->dfL) = DfDev{int(task.size()), nsn, a, b, cd.sn_first, cd.sn_w, bd.d_off, cd.ext_beg,
-                                  cd.ext_end, c, d};
+                                  cd.ext_end, c, d, int(leaf.size()), e, P.nx, int(ck_row.size()), nchunked,
+                                  f1, f2, f3, f4, f5};
+    nck_max = std::max(nck_max, ck_row.size());
+    nchunked_max = std::max(nchunked_max, size_t(nchunked));
   }
-  TRY(alloc(h, &h->df_cnt, 2 * (size_t)h->cs_ncb_max * nsn_max));
+  TRY(alloc(h, &h->df_cnt, (size_t)h->cs_ncb_max * (2 * nsn_max + nchunked_max)));
+  TRY(alloc(h, &h->df_part, nck_max * (size_t)h->cs_ncb_max * 32));
   {
     const int maxseg = std::max(1, std::max(P.csL.maxseg, P.csU.maxseg));
     TRY(alloc(h, &h->cs_scratch, (size_t)h->cs_ncb_max * maxseg * 32));
@@ -599,10 +636,10 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     const int kmax = std::max(1, h->df_max / ncb);
     const int ksplit = std::max(1, std::min(kmax, h->df_ksplit > 0 ? h->df_ksplit : 16));
     if (timed) ph_begin(h, OPF_PHASE_TRSM);
-    CK(launch_trsm_df(s, h->dfL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->df_cnt,
+    CK(launch_trsm_df(s, h->dfL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->df_cnt, h->df_part,
                       h->st, h->spin_limit));
     if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
-    CK(launch_trsm_df(s, h->dfU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->df_cnt,
+    CK(launch_trsm_df(s, h->dfU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->df_cnt, h->df_part,
                       h->st, h->spin_limit));
     if (timed) ph_end(h);
     return OPF_OK;

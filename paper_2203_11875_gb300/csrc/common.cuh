@@ -172,11 +172,24 @@ constexpr int DF_INLINE_B = 4;
 struct DfDev {
   int ntask, nsn;
   const int *task, *sn_of, *sn_first, *sn_w, *d_off, *ext_beg, *ext_end, *dep_ptr, *dep_sn;
+  // leaf supernodes (no external entries, width <= DF_LEAF_W): solved by a
+  // separate pass before the dataflow kernel, their tasks left out of task
+  int nleaf;
+  const int* leaf;
+  // rows with more than DF_CHUNK external entries are split into chunk tasks
+  // (task code n + chunk id): chunk k covers entries ck_e0[k] .. ck_e1[k] of
+  // row ck_row[k]; row r's chunks are rw_ck0[r] .. rw_ck0[r + 1] (none for
+  // short rows) and it counts its finished chunks in slot rw_cidx[r]
+  int n, nchunks, nchunked;
+  const int *ck_row, *ck_e0, *ck_e1, *rw_ck0, *rw_cidx;
 };
-// cnt: 2 * ncb * nsn counters (zeroed here); cooperative launch of ncb * ksplit CTAs.
+constexpr int DF_LEAF_W = 8;
+constexpr int DF_CHUNK = 24;
+// cnt: ncb * (2 nsn + nchunked) counters (zeroed here); Pc: nchunks * 32 ncb
+// partial sums of the chunk tasks; cooperative launch of ncb * ksplit CTAs.
 cudaError_t launch_trsm_df(cudaStream_t s, const DfDev& S, const int* ci, const double* val, const double* D,
-                           double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* cnt, int* st,
-                           long long spin_limit);
+                           double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* cnt,
+                           double* Pc, int* st, long long spin_limit);
 int trsm_df_max_blocks();
 // One right-hand side X[i * xs] (Y: scratch of the same stride); nblocks CTAs,
 // cooperative launch; bar holds one counter.

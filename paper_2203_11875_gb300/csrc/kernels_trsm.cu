@@ -1185,7 +1185,8 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
                                                          const double* __restrict__ val,
                                                          const double* __restrict__ D, double* X, double* Y,
                                                          long long ld, int ncols, int ksplit, unsigned* cntA,
-                                                         unsigned* cntB, int* st, long long spin_limit) {
+                                                         unsigned* cntB, double* Pc, int* st,
+                                                         long long spin_limit) {
   const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int c = cb * 32 + lane;
@@ -1193,10 +1194,15 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
   const int gw = p * nwarps + warp, W = ksplit * nwarps;
   unsigned* cA = cntA + (size_t)cb * S.nsn;
   unsigned* cB = cntB + (size_t)cb * S.nsn;
+  unsigned* cC = cntB + (size_t)gridDim.x / ksplit * S.nsn + (size_t)cb * S.nchunked;
+  const long long pld = (long long)(gridDim.x / ksplit) * 32;   // row stride of the chunk partials
   for (int q = gw; q < S.ntask; q += W) {
     const int code = S.task[q];
     if (code >= 0) {
-      const int r = code;
+      // a row's external part, or one chunk of a long row's
+      const bool chunk = code >= S.n;
+      const int ck = chunk ? code - S.n : 0;
+      const int r = chunk ? S.ck_row[ck] : code;
       const int d0 = S.dep_ptr[r], d1 = S.dep_ptr[r + 1];
       for (int db = d0; db < d1; db += 32) {
         bool ok = true;
@@ -1207,8 +1213,8 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
         if (!__all_sync(FULL, ok)) return;
       }
       __syncwarp();
-      const int e0 = S.ext_beg[r], e1 = S.ext_end[r];
-      double a0 = on ? __ldcg(&X[(long long)r * ld + c]) : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      const int e0 = chunk ? S.ck_e0[ck] : S.ext_beg[r], e1 = chunk ? S.ck_e1[ck] : S.ext_end[r];
+      double a0 = (on && !chunk) ? __ldcg(&X[(long long)r * ld + c]) : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       for (int eb = e0; eb < e1; eb += 32) {
         const int len = min(32, e1 - eb);
         const int myj = lane < len ? ci[eb + lane] : 0;
@@ -1232,7 +1238,26 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
           if (on) a0 = fma(-v, __ldcg(&X[(long long)j * ld + c]), a0);
         }
       }
-      if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
+      if (!chunk) {
+        if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
+      } else {
+        // the chunk's sum (entries subtracted) goes to its slot; the chunk that
+        // completes the row adds the slots up in order and goes on as the row
+        Pc[(long long)ck * pld + c] = (a0 + a1) + (a2 + a3);
+        __syncwarp();
+        const int ck0 = S.rw_ck0[r], nch = S.rw_ck0[r + 1] - ck0;
+        unsigned old = 0;
+        if (lane == 0)
+          asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cC + S.rw_cidx[r]) : "memory");
+        old = __shfl_sync(FULL, old, 0);
+        if (old + 1 != (unsigned)nch) continue;
+        __syncwarp();
+        if (on) {
+          double y = __ldcg(&X[(long long)r * ld + c]);
+          for (int k = 0; k < nch; ++k) y += __ldcg(&Pc[(long long)(ck0 + k) * pld + c]);
+          Y[(long long)r * ld + c] = y;
+        }
+      }
       __syncwarp();
       const int s = S.sn_of[r], w = S.sn_w[s];
       if (w > DF_INLINE_B) {
@@ -1289,19 +1314,59 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
   }
 }
 
+// The leaf supernodes of the dataflow schedule: X_s <- D_s X_s, one warp per
+// (leaf, 32-column block), the supernode's rows held in registers (at most
+// DF_LEAF_W); then its completion count is set for the dataflow kernel that
+// follows on the stream.
+__global__ void __launch_bounds__(256) k_trsm_df_leaf(DfDev S, const double* __restrict__ D, double* X,
+                                                      long long ld, int ncols, unsigned* cntB) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int ncb = (ncols + 31) / 32;
+  if (gw >= S.nleaf * ncb) return;
+  const int l = gw % S.nleaf, cb = gw / S.nleaf;
+  const int sn = S.leaf[l], f = S.sn_first[sn], w = S.sn_w[sn];
+  const int c = cb * 32 + lane;
+  const bool on = c < ncols;
+  const double* Ds = D + S.d_off[sn];
+  double xr[DF_LEAF_W];
+#pragma unroll
+  for (int j = 0; j < DF_LEAF_W; ++j) xr[j] = (on && j < w) ? X[(long long)(f + j) * ld + c] : 0.0;
+#pragma unroll
+  for (int i = 0; i < DF_LEAF_W; ++i) {
+    if (i < w) {
+      double a = 0.0;
+#pragma unroll
+      for (int j = 0; j < DF_LEAF_W; ++j)
+        if (j < w) a = fma(Ds[i * w + j], xr[j], a);
+      if (on) X[(long long)(f + i) * ld + c] = a;
+    }
+  }
+  if (lane == 0) cntB[(size_t)cb * S.nsn + sn] = (unsigned)w;
+}
+
 }  // namespace
 
 cudaError_t launch_trsm_df(cudaStream_t s, const DfDev& S, const int* ci, const double* val, const double* D,
-                           double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* cnt, int* st,
-                           long long spin_limit) {
-  if (ncols <= 0 || S.ntask <= 0) return cudaSuccess;
+                           double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* cnt,
+                           double* Pc, int* st, long long spin_limit) {
+  if (ncols <= 0 || S.ntask + S.nleaf <= 0) return cudaSuccess;
   const int ncb = (ncols + 31) / 32;
   unsigned* cntA = cnt;
   unsigned* cntB = cnt + (size_t)ncb * S.nsn;
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 2 * (size_t)ncb * S.nsn, s);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * ((size_t)2 * ncb * S.nsn + (size_t)ncb * S.nchunked), s);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&D, (void*)&X, (void*)&Y, (void*)&ld,
-                  (void*)&ncols, (void*)&ksplit, (void*)&cntA, (void*)&cntB, (void*)&st, (void*)&spin_limit};
+  if (S.nleaf > 0) {
+    const long long warps = (long long)S.nleaf * ncb;
+    k_trsm_df_leaf<<<int((warps * 32 + 255) / 256), 256, 0, s>>>(S, D, X, ld, ncols, cntB);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (S.ntask <= 0) return cudaSuccess;
+  void* args[] = {(void*)&S,   (void*)&ci,     (void*)&val,  (void*)&D,    (void*)&X,  (void*)&Y,
+                  (void*)&ld,  (void*)&ncols,  (void*)&ksplit, (void*)&cntA, (void*)&cntB, (void*)&Pc,
+                  (void*)&st,  (void*)&spin_limit};
   note_launch();
   return cudaLaunchCooperativeKernel((void*)k_trsm_df, dim3(ncb * ksplit), dim3(BLK_THREADS), args, 0, s);
 }

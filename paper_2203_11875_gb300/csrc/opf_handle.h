@@ -92,6 +92,7 @@ struct opf_handle {
   bool cl1_ok[3] = {false, false, false};  // ... and whether each fits on the device
   int cl1_pick = 2;              // the cluster size in use (index)
   condipm::DfDev dfL{}, dfU{};   // dataflow task lists of the lower / upper solves
+  double* df_part = nullptr;     // partial sums of their chunk tasks (chunks x 32 column blocks)
   unsigned* df_cnt = nullptr;    // their supernode counters (2 x column blocks x supernodes)
   int df_max = 1, df_ksplit = 0; // resident CTAs of the dataflow kernel; CTAs per column block
   // dense condensed buffers: Zt = [I; S_x] and H = K Zt (nw x nu, row-major, x rows permuted),
