@@ -246,6 +246,10 @@ def main():
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
+    ap.add_argument("--rhs-block", type=int, default=0, choices=[0, 1, 2, 4, 32, 64, 96],
+                    help="multi-RHS solve kernel (opf_options.rhs_block; 0 autotune)")
+    ap.add_argument("--rhs1-kernel", type=int, default=0, choices=[0, 1, 64, 65, 66],
+                    help="one-RHS solve kernel (opf_options.rhs1_kernel; 0 autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -263,7 +267,7 @@ def main():
     build.build()
     dev = torch.device("cuda", local)
     net = gridgen.grid2000()
-    h = binding.Handle(net, chol_form=args.chol_form)
+    h = binding.Handle(net, chol_form=args.chol_form, rhs_block=args.rhs_block, rhs1_kernel=args.rhs1_kernel)
     stream = torch.cuda.Stream(device=dev)
     h.set_stream(stream)
     it = synthetic_iterate(net, h.nx, h.nu, h.m)
