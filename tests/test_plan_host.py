@@ -1,0 +1,48 @@
+"""Host-side schedules of the symbolic analysis, checked without a GPU: a small
+C++ driver (tests/plan_check.cpp) is compiled against csrc/plan.cpp and run on
+generated networks."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import gridgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2203_11875_gb300", "csrc")
+
+
+def _write(net, path):
+    with open(path, "wb") as f:
+        np.array([net.nb, net.nl, net.ng, net.slack], np.int32).tofile(f)
+        for a in (net.Pd, net.Qd, net.Vmin, net.Vmax):
+            np.asarray(a, np.float64).tofile(f)
+        np.asarray(net.lf, np.int32).tofile(f)
+        np.asarray(net.lt, np.int32).tofile(f)
+        for a in (net.r, net.x, net.b, net.rate):
+            np.asarray(a, np.float64).tofile(f)
+        np.asarray(net.gbus, np.int32).tofile(f)
+        for a in (net.Pmin, net.Pmax, net.Qmin, net.Qmax, net.c2, net.c1):
+            np.asarray(a, np.float64).tofile(f)
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    out = tmp_path_factory.mktemp("plan") / "plan_check"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, "-o", str(out),
+                    os.path.join(ROOT, "tests", "plan_check.cpp"), os.path.join(CSRC, "plan.cpp")],
+                   check=True, capture_output=True)
+    return out
+
+
+@pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000"])
+def test_cluster_solve_schedules(checker, tmp_path, name):
+    path = tmp_path / f"{name}.bin"
+    _write(gridgen.WORKLOADS[name](), str(path))
+    res = subprocess.run([str(checker), str(path)], capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0 and res.stdout.strip() == "ok", res.stdout + res.stderr
