@@ -343,6 +343,11 @@ __device__ __forceinline__ double pivot_rcp(double d) {
 __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const unsigned short* pairs,
                                double (*R)[CNB + 1] = nullptr, int nr = 0) {
   const int tid = threadIdx.x;
+  // worker index of the threads outside sub-partition 0 (warps 1-3, 5-7, ...)
+  const int warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const bool one_warp = nwarps == 1;   // then every thread is a worker
+  const int wk = one_warp ? tid : ((warp & 3) ? (warp - (warp >> 2) - 1) * 32 + (tid & 31) : -1);
+  const int nwk = one_warp ? 32 : (nwarps - (nwarps + 3) / 4) * 32;
   // during the loop dv[j] = 1 / d_j, or 0 for a failed pivot; every thread reads
   // it after a barrier, so all leave together on a failure
   if (tid == 0) dv[0] = pivot_rcp(T[0][0]);
@@ -352,19 +357,28 @@ __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const u
     if (__double_as_longlong(rj) <= 0) return j;   // 0 marks a failed pivot
     const int cnt = (CNB - 1 - j) * (CNB - j) / 2;
     const int diag_next = (CNB - 2 - j) * (CNB - 1 - j) / 2;   // position of (j+1, j+1)
-    // thread 0 takes the next pivot's pair first, so its reciprocal overlaps
-    // the rest of the update
-    for (int q = tid; q < cnt; q += blockDim.x) {
-      int t = diag_next + q;
-      if (t >= cnt) t -= cnt;
-      const int pr = pairs[t], i = pr >> 8, l = pr & 255;
+    // thread 0 takes the next pivot's pair and its reciprocal alone: warp w
+    // runs on sub-partition w mod 4, and the other warps of thread 0's
+    // sub-partition stay off the FP64 pipe, so that chain is not queued behind
+    // their updates; the warps of the other three sub-partitions share the
+    // rest of the pairs
+    if (tid == 0 && cnt > 0) {
+      const int pr = pairs[diag_next], i = pr >> 8, l = pr & 255;
       const double v = fma(-T[i][j] * rj, T[l][j], T[i][l]);
       T[i][l] = v;
-      if (q == 0 && j + 1 < kb) dv[j + 1] = pivot_rcp(v);
+      if (j + 1 < kb) dv[j + 1] = pivot_rcp(v);
     }
-    if (nr > 0) {
+    if (wk >= 0) {
+      for (int q = 1 + wk; q < cnt; q += nwk) {
+        int t = diag_next + q;
+        if (t >= cnt) t -= cnt;
+        const int pr = pairs[t], i = pr >> 8, l = pr & 255;
+        T[i][l] = fma(-T[i][j] * rj, T[l][j], T[i][l]);
+      }
+    }
+    if (nr > 0 && wk >= 0) {
       // panel rows: R_rl -= R_rj T_lj / d_j for l > j (eight rows, row index fastest)
-      for (int q = tid; q < 8 * (CNB - 1 - j); q += blockDim.x) {
+      for (int q = wk; q < 8 * (CNB - 1 - j); q += nwk) {
         const int rr = q & 7, l = j + 1 + (q >> 3);
         R[rr][l] = fma(-R[rr][j] * rj, T[l][j], R[rr][l]);
       }
