@@ -36,6 +36,20 @@ unsigned long long launch_count() { return g_launches.load(std::memory_order_rel
 void note_cuda_error(cudaError_t e) { g_last_cuda_error.store(int(e), std::memory_order_relaxed); }
 int last_cuda_error() { return g_last_cuda_error.load(std::memory_order_relaxed); }
 
+cudaError_t allow_cluster16(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  done.insert({dev, fn});
+  return cudaSuccess;
+}
+
 cudaError_t allow_max_smem(const void* fn) {
   static std::mutex mu;
   static std::set<std::pair<int, const void*>> done;

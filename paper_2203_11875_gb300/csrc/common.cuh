@@ -61,6 +61,9 @@ int last_cuda_error();
 // never set per launch: a launch of another handle on another host thread,
 // needing more, could otherwise run between the setting and this launch.
 cudaError_t allow_max_smem(const void* fn);
+// Allow clusters of up to 16 CTAs for a kernel, once per kernel and device
+// (the same reasoning: attributes are not set per launch).
+cudaError_t allow_cluster16(const void* fn);
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch error.

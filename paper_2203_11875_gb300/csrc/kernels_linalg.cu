@@ -1202,7 +1202,7 @@ cudaError_t launch_chol_solve_cl(cudaStream_t s, int n, const double* F, const d
   if (nrhs <= 0 || nt <= 0) return cudaSuccess;
   const size_t smem = sizeof(double) * ((size_t)nt * CNB + (size_t)((nt + CL - 1) / CL) * CNB);
   if (CL > 8) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_chol_solve_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = allow_cluster16((const void*)k_chol_solve_cl);
     if (e != cudaSuccess) return e;
   }
   if (smem > 48 * 1024) {

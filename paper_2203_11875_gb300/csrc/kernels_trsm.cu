@@ -1021,9 +1021,7 @@ __global__ void __launch_bounds__(LU1C_THREADS, 1) k_trsm_lu1c(Cl1Dev L, const i
 int trsm_lu1c_max_clusters(int CL, int n, int ymax, int nlev) {
   const size_t smem = sizeof(double) * ((size_t)n + (size_t)ymax) + sizeof(int) * ((size_t)nlev + 1);
   if (allow_max_smem((const void*)k_trsm_lu1c<8>) != cudaSuccess) return 0;
-  if (CL > 8 && cudaFuncSetAttribute((const void*)k_trsm_lu1c<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                    cudaSuccess)
-    return 0;
+  if (CL > 8 && allow_cluster16((const void*)k_trsm_lu1c<8>) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(LU1C_THREADS);
@@ -1052,7 +1050,7 @@ cudaError_t launch_trsm_lu1c(cudaStream_t s, const Cl1Dev& L, const int* ciL, co
   cudaError_t e = allow_max_smem((const void*)k_trsm_lu1c<8>);
   if (e != cudaSuccess) return e;
   if (CL > 8) {
-    e = cudaFuncSetAttribute((const void*)k_trsm_lu1c<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = allow_cluster16((const void*)k_trsm_lu1c<8>);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
