@@ -165,13 +165,25 @@ __global__ void k_lu_scatter(long long nnzG, const int* __restrict__ map, const 
   if (p >= 0) LU[p] = G[q];
 }
 
+// max_q |v_q| over each row, one warp per row.  Magnitudes are compared as
+// integers on the bit patterns with the sign cleared (the order of non-negative
+// doubles), so no FP64 instruction is issued; NaN entries count as 0.
 __global__ void k_row_absmax(int n, const int* __restrict__ rp, const double* __restrict__ v,
                              double* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
-  double m = 0.0;
-  for (int q = rp[i]; q < rp[i + 1]; ++q) m = fmax(m, fabs(v[q]));
-  out[i] = m;
+  unsigned long long m = 0;
+  for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v[q]) & 0x7FFFFFFFFFFFFFFFULL;
+    if (b > 0x7FF0000000000000ULL) b = 0;   // NaN
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+    m = u > m ? u : m;
+  }
+  if (lane == 0) out[i] = __longlong_as_double((long long)m);
 }
 
 // Numeric up-looking LU of P G_x P^T in its fixed pattern (static pivots).
@@ -753,7 +765,7 @@ cudaError_t launch_lu_scatter(cudaStream_t s, long long nnzG, const int* Gx_to_L
   return cudaGetLastError();
 }
 cudaError_t launch_row_absmax(cudaStream_t s, int n, const int* rp, const double* val, double* rmax) {
-  k_row_absmax<<<nblk(n, 256), 256, 0, s>>>(n, rp, val, rmax);
+  k_row_absmax<<<nblk((long long)n * 32, 256), 256, 0, s>>>(n, rp, val, rmax);
   note_launch();
   return cudaGetLastError();
 }

@@ -602,11 +602,28 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, lo
 }
 
 template <bool UPPER>
-__device__ __forceinline__ void diag_inv_one(int s, int c, const int* __restrict__ sn_first,
+__device__ __forceinline__ void diag_inv_one(double (*Ts)[33], int s, int c, const int* __restrict__ sn_first,
                                              const int* __restrict__ sn_w, const int* __restrict__ d_off,
                                              const int* __restrict__ int_beg, const double* __restrict__ val,
                                              const double* __restrict__ inv_diag, double* __restrict__ D) {
   const int f = sn_first[s], w = sn_w[s];
+  // the block's strict triangle goes to shared memory first, all loads in
+  // flight together (lane c loads entry c of every row), so the substitution
+  // below waits on no global load
+  const int ib = c < w ? int_beg[f + c] : 0;   // lane r: where row r's entries start
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int ibr = __shfl_sync(0xffffffffu, ib, r);
+    if (r < w) {
+      if (!UPPER) {
+        if (c < r) Ts[r][c] = val[ibr + c];
+      } else {
+        if (c > r && c < w) Ts[r][c] = val[ibr + c - r - 1];
+      }
+    }
+  }
+  const double idg = (inv_diag && c < w) ? inv_diag[f + c] : 1.0;
+  __syncwarp();
   double d[32];
 #pragma unroll
   for (int r = 0; r < 32; ++r) d[r] = 0.0;
@@ -615,11 +632,10 @@ __device__ __forceinline__ void diag_inv_one(int s, int c, const int* __restrict
     for (int r = 0; r < 32; ++r) {
       if (r < w) {
         double acc = (r == c) ? 1.0 : 0.0;
-        const double* Tr = val + int_beg[f + r];
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (j < r) acc = fma(-Tr[j], d[j], acc);
-        d[r] = inv_diag ? acc * inv_diag[f + r] : acc;
+          if (j < r) acc = fma(-Ts[r][j], d[j], acc);
+        d[r] = inv_diag ? acc * __shfl_sync(0xffffffffu, idg, r) : acc;
       }
     }
   } else {
@@ -628,11 +644,10 @@ __device__ __forceinline__ void diag_inv_one(int s, int c, const int* __restrict
       const int r = 31 - rr;
       if (r < w) {
         double acc = (r == c) ? 1.0 : 0.0;
-        const double* Tr = val + int_beg[f + r];
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (j > r && j < w) acc = fma(-Tr[j - r - 1], d[j], acc);
-        d[r] = inv_diag ? acc * inv_diag[f + r] : acc;
+          if (j > r && j < w) acc = fma(-Ts[r][j], d[j], acc);
+        d[r] = inv_diag ? acc * __shfl_sync(0xffffffffu, idg, r) : acc;
       }
     }
   }
@@ -647,12 +662,14 @@ __device__ __forceinline__ void diag_inv_one(int s, int c, const int* __restrict
 // the four factors' diagonal-block inverses in one launch (blockIdx.y picks
 // the factor), so that their widest blocks are inverted side by side
 __global__ void k_diag_inv4(DiagInvJob j0, DiagInvJob j1, DiagInvJob j2, DiagInvJob j3) {
+  __shared__ double Tsh[4][32][33];   // one block per warp (128 threads)
   const DiagInvJob J = blockIdx.y == 0 ? j0 : blockIdx.y == 1 ? j1 : blockIdx.y == 2 ? j2 : j3;
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int c = threadIdx.x & 31;
   if (s >= J.nsn) return;
-  if (J.upper) diag_inv_one<true>(s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
-  else diag_inv_one<false>(s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
+  double (*Ts)[33] = Tsh[(threadIdx.x >> 5) & 3];
+  if (J.upper) diag_inv_one<true>(Ts, s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
+  else diag_inv_one<false>(Ts, s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
 }
 
 __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
