@@ -51,3 +51,22 @@ def test_aggregate_over_two_gloo_ranks():
 
 def test_aggregate_alone_is_identity():
     assert bench.aggregate(3.5, 7) == (3.5, 7)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference times the CPU oracle on the same workload and
+    metric and prints one JSON line with the reference arm's keys."""
+    import json
+    import subprocess
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["higher_is_better"] is False
+    assert d["metric"] == "condense+Cholesky ms/IPM iter" and d["unit"] == "ms/iter"
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
