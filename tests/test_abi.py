@@ -51,3 +51,16 @@ def test_create_rejects_invalid_network_before_touching_the_gpu(lib):
     with pytest.raises(binding.OPFError) as e:
         binding.Handle(net)
     assert e.value.code == -1
+
+
+def test_queries_reject_a_null_handle(lib):
+    """The inspection calls check their handle before touching anything."""
+    import ctypes as C
+    from paper_2203_11875_gb300 import binding
+    L = binding.load_library()
+    f, nb = C.c_int(), C.c_int()
+    ms = (C.c_float * 9)()
+    assert L.opf_chol_choice(None, C.byref(f), C.byref(nb), ms) == -1
+    k, k1 = C.c_int(), C.c_int()
+    ms6 = (C.c_float * 6)()
+    assert L.opf_trsm_choice(None, C.byref(k), ms6, C.byref(k1)) == -1
