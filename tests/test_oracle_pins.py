@@ -159,6 +159,60 @@ def test_condensed_step_equals_full_space_ldl(make, seed):
     assert np.abs(p - p_ref).max() <= 1e-10 * np.abs(p_ref).max()
 
 
+@pytest.mark.parametrize("make,seed", [(gridgen.tiny3, 1), (gridgen.ring30, 2)])
+@pytest.mark.parametrize("delta_c", [1e-3, 0.7])
+def test_condensed_step_with_dual_regularization_equals_full_space(make, seed, delta_c):
+    """The dual regularisation -delta_c I on the (p_y, p_y) block of K_aug
+    (Sec. 4.3, placed on the inequality rows): the condensed route with
+    Sigma_t = (Sigma_s^{-1} + delta_c)^{-1} reaches the full-space step of that
+    regularised K_aug, solved densely by LU; the step differs from the
+    unregularised one, so a dropped delta_c term fails."""
+    lay, G, A, W, sw, ss, r = _random_point(make, seed)
+    d = 0.0
+    while True:
+        out = kkt.condensed_step(G, A, W, sw, ss, r, lay.nu, delta_w=d, delta_c=delta_c)
+        if out[-1]:
+            break
+        d = 1e-2 if d == 0 else d * 8
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, d), np.zeros(lay.nx)])
+    Kfull = kkt.kaug(G, A, Wd, sw, ss, delta_c=delta_c).toarray()
+    m = lay.m
+    yy = slice(Kfull.shape[0] - m, Kfull.shape[0])
+    assert np.array_equal(np.diag(Kfull[yy, yy]), np.full(m, -delta_c))
+    p_ref = np.linalg.solve(Kfull, -r)
+    p = np.concatenate(out[:4])
+    assert np.abs(p - p_ref).max() <= 1e-10 * np.abs(p_ref).max()
+    p0 = np.concatenate(kkt.full_space_step(G, A, Wd, sw, ss, r))
+    assert np.abs(p - p0).max() > 1e-6 * np.abs(p0).max()
+    # the condensed matrix is Kred by definition with Sigma_t in place of Sigma_s
+    Kt = kkt.kred_definition(G, A, Wd, sw, kkt.regularized_sigma(ss, delta_c), lay.nu)
+    assert np.abs(out[4] - Kt).max() <= 1e-12 * np.abs(Kt).max()
+
+
+@pytest.mark.parametrize("delta_c", [0.05, 2.0])
+@pytest.mark.parametrize("delta", [0.0, 10.0, 1e3])
+def test_inertia_theorem3_with_dual_regularization(delta, delta_c):
+    """Theorem 3 with -delta_c I in the (p_y, p_y) block: K_cond (with Sigma_t)
+    is positive definite exactly when K_aug has inertia (nx+nu+m, nx+m, 0)."""
+    lay, G, A, W, sw, ss, r = _random_point(gridgen.ring30, 11)
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, delta), np.zeros(lay.nx)])
+    Kr = kkt.kred_definition(G, A, Wd, sw, kkt.regularized_sigma(ss, delta_c), lay.nu)
+    pd = np.linalg.eigvalsh(Kr).min() > 0
+    inert = kkt.inertia_dense(kkt.kaug(G, A, Wd, sw, ss, delta_c=delta_c))
+    assert pd == (inert == (lay.nw + lay.m, lay.nx + lay.m, 0))
+
+
+def test_regularized_sigma_closed_form():
+    """Sigma_t = (Sigma_s^{-1} + delta_c)^{-1}, its limits and its monotonicity."""
+    ss = np.array([1e-8, 0.3, 1.0, 7.0, 1e8])
+    for dc in (0.0, 1e-6, 0.5, 3.0):
+        t = kkt.regularized_sigma(ss, dc)
+        np.testing.assert_allclose(t, 1.0 / (1.0 / ss + dc), rtol=1e-15)
+        assert np.all(t <= ss)
+    assert np.array_equal(kkt.regularized_sigma(ss, 0.0), ss)
+    assert abs(kkt.regularized_sigma(np.array([1e12]), 2.0)[0] - 0.5) <= 1e-12
+
+
 @pytest.mark.parametrize("make,seed", [(gridgen.tiny3, 4), (gridgen.ring30, 5)])
 def test_kred_definition_is_symmetric_and_matches_theorem1(make, seed):
     lay, G, A, W, sw, ss, r = _random_point(make, seed)
@@ -285,7 +339,12 @@ def test_reduced_derivatives_through_projection():
         fp = model.objective(lay, reduced(u0 + e)[0])
         fm = model.objective(lay, reduced(u0 - e)[0])
         gfr_fd[j] = (fp - fm) / (2 * h)
-    Gx = G[:, nu:].tocsc()
-    gfr = gf[:nu] - G[:, :nu].T @ spla.splu(Gx).solve(gf[nu:], trans="T")
+    gfr, lam_f = kkt.reduced_gradient(G, gf, nu)
     assert np.abs(gfr - gfr_fd).max() <= 1e-6 * np.abs(gfr).max()
+    # its adjoint is the multiplier that makes the state block of grad f + G^T lam vanish
+    assert np.abs(gf[nu:] + G[:, nu:].T @ lam_f).max() <= 1e-12 * np.abs(gf[nu:]).max()
+    # the same call on grad_w L reproduces the projection's reduced Lagrangian gradient
+    gl, lam_l = kkt.reduced_gradient(G, gf + A.T @ y, nu)
+    assert np.abs(gl - grad0).max() <= 1e-10 * np.abs(gl).max()
+    assert np.abs(lam_l - lam).max() <= 1e-10 * np.abs(lam).max()
     assert np.abs(W_hat - Hfd).max() <= 1e-5 * np.abs(W_hat).max()
