@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the condensed-IPM hot path on GB300.
 
-Metric: condense + Cholesky milliseconds per IPM iteration (FP64), on the
-seeded 2,000-bus lattice workload (nu = 399 controls, nx = 3,799 states).  One
-step is one pass of the per-iteration hot path at a fixed mid-solve-like
-iterate: model derivatives, G_x refactorisation, multi-right-hand-side
-triangular solves over all nu columns, K assembly and H = K Z, the condensed
-matrix, its Cholesky factor, and the Newton-step recovery.  ``value`` is the
-condense + Cholesky part (the metric); ``ms_per_step`` the whole step.
+Metric: condense + Cholesky milliseconds per IPM iteration (FP64) on the seeded
+10,000-bus lattice workload (1,000 generators: nu = 1,999 controls, nx = 18,999
+states), the largest single-instance configuration, at the oracle's own
+linearize-then-reduce iterate 3 (stored in tests/golden/grid10k_iterate.npz).
+One step is one pass of the per-iteration hot path: model derivatives (A1-A3),
+G_x refactorisation, multi-right-hand-side triangular solves over all nu
+columns, K assembly, H = K Z and the condensed matrix (A4-A7), the condensed
+right-hand side (A8), one Cholesky attempt (A9) and the step recovery (A10).
+``value`` is A4-A9 (the metric); ``ms_per_step`` the whole step.
 
-L2 (129 MB) holds the whole working set of this workload, so a 256 MB buffer is
-written on the stream between timed steps.  Device time comes from CUDA events
-on the library's stream.  ``--impl reference`` times the CPU FP64 oracle on the
-host cores for the same metric and workload.
+Z and H (168 MB each) exceed L2 (129 MB); a 256 MB buffer is still written on
+the stream between timed steps, so the factors and K start cold too.  Device
+time comes from CUDA events on the library's stream.  ``e2e`` times the same
+step through opf_newton_step with pinned HOST buffers (copies inside).
+``--impl reference`` times the CPU FP64 oracle on the host cores for the same
+metric and workload.
 """
 from __future__ import annotations
 
@@ -32,19 +36,29 @@ sys.path.insert(0, ROOT)
 
 import gridgen  # noqa: E402
 
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flop/DFMA x GHz (max SM clock)
 METRIC = "condense+Cholesky ms/IPM iter"
 KERNEL_NAMES = {32: "column-parallel", 64: "level-blocked", 96: "dataflow", 1: "staged x1", 2: "staged x2",
                 4: "staged x4"}
 UNIT = "ms/iter"
-WORKLOAD = "grid2000: 2,000-bus lattice, 200 generators, nu=399, nx=3,799, FP64, LinRed iterate"
+WORKLOAD = ("grid10k: 10,000-bus lattice, 1,000 generators, nu=1,999, nx=18,999, FP64, "
+            "LinRed oracle iterate 3")
+ITERATE = os.path.join(ROOT, "tests", "golden", "grid10k_iterate.npz")
+
+
+def stored_iterate(path=ITERATE):
+    """The oracle's LinRed iterate 3 of the 10,000-bus workload: x, u, lambda,
+    y, Sigma, the full-space right-hand side r and the delta_w its inertia
+    correction took."""
+    z = np.load(path)
+    nu = (len(z["w"]) - len(z["lam"]))
+    sw = z["sig_w"]
+    return dict(x=z["w"][nu:], u=z["w"][:nu], lam=z["lam"], y=z["y"], sig_u=sw[:nu], sig_x=sw[nu:],
+                sig_s=z["sig_s"], r=z["r"]), float(z["delta"])
 
 
 def synthetic_iterate(net, nx, nu, m, seed=2203):
     """Flat-start-like primal point with moderate multipliers and barrier terms."""
     rng = np.random.default_rng(seed)
-    is_gen = np.zeros(net.nb, bool)
-    is_gen[net.gbus] = True
     n_ns = net.nb - 1
     x = np.concatenate([0.02 * rng.standard_normal(n_ns), 1.0 + 0.01 * rng.standard_normal(net.nb - net.ng)])
     u = np.concatenate([np.clip(1.05, net.Vmin[net.gbus], net.Vmax[net.gbus]),
@@ -76,10 +90,10 @@ def aggregate(t_local, units_local, dist=None, device=None):
     return float(t.item()), int(u.item())
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` on this workload from the committed ncu
-    summary (profiles/traffic.json), or None when the summary is missing, is for
-    another kernel, or was taken from different kernel sources."""
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/traffic.json, key "kernel@workload"), or None when the
+    summary is missing or was taken from different kernel sources."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -87,7 +101,7 @@ def measured_traffic(kernel):
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    ent = rec.get(kernel)
+    ent = rec.get(f"{kernel}@{workload}")
     if not ent:
         return None
     h = hashlib.sha256()
@@ -142,24 +156,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_condense(net, it, budget_s=15.0):
-    """Oracle condense + Cholesky per iteration at the same iterate (host cores)."""
+def cpu_oracle_condense(net, it, delta, budget_s=15.0, max_reps=200):
+    """Oracle condense + Cholesky per iteration at the same iterate (host
+    cores): Kred = Z^T K Z by its definition (SciPy splu for S_x, BLAS for the
+    dense products) and numpy's Cholesky of Kred + delta I.  Returns the median
+    milliseconds and the number of evaluations."""
     from oracle import kkt, model
     lay = model.Layout(net)
     w = np.concatenate([it["u"], it["x"]])
     sw = np.concatenate([it["sig_u"], it["sig_x"]])
+    _, G, A = model.jacobians(lay, w)
+    W = model.lagrangian_hessian(lay, w, it["lam"], it["y"])
     reps, t0 = 0, time.perf_counter()
     times = []
     while time.perf_counter() - t0 < budget_s or reps < 1:
-        t1 = time.perf_counter()
-        _, G, A = model.jacobians(lay, w)
-        W = model.lagrangian_hessian(lay, w, it["lam"], it["y"])
         t2 = time.perf_counter()
         K = kkt.kred_definition(G, A, W, sw, it["sig_s"], lay.nu)
-        np.linalg.cholesky(K + 1e-8 * np.eye(lay.nu))
+        np.linalg.cholesky(K + delta * np.eye(lay.nu))
         times.append((time.perf_counter() - t2) * 1e3)
         reps += 1
-        if reps >= 200:
+        if reps >= max_reps:
             break
     return float(np.median(times)), reps
 
@@ -204,45 +220,105 @@ def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
 
 
 def run_reference(args):
-    """The oracle as the reference arm: same metric, workload and unit."""
+    """The oracle as the reference arm: same metric, workload and unit; one
+    oracle evaluation of condense + Cholesky at the stored iterate per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    net = gridgen.grid2000()
-    from oracle import model
-    lay = model.Layout(net)
-    it = synthetic_iterate(net, lay.nx, lay.nu, lay.m)
+    net = gridgen.grid10k()
+    it, delta = stored_iterate()
     for _ in range(args.warmup):
-        cpu_oracle_condense(net, it, budget_s=0.0)
+        cpu_oracle_condense(net, it, delta, budget_s=0.0)
     per = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ms, _ = cpu_oracle_condense(net, it, budget_s=0.0)
+        ms, _ = cpu_oracle_condense(net, it, delta, budget_s=0.0)
         per.append(ms)
     wall = time.perf_counter() - t0
     value = float(np.mean(per))
+    threads = os.environ.get("OMP_NUM_THREADS")
+    cores = int(threads) if threads and threads.isdigit() else os.cpu_count()
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"{args.steps} oracle condense+Cholesky evaluations of the same iterate"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} oracle condense+Cholesky evaluations of the stored grid10k "
+                                      "iterate (SciPy splu for S_x, serial; BLAS dense products and Cholesky)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 
 
+def fp64_peaks(binding, torch, dev):
+    """Measured FP64 throughput (GFLOP/s) of this GPU: the library's DFMA and
+    f64 mma.sync probes, and torch's f64 matmul and Cholesky for context."""
+    out = {}
+    for k, name in enumerate(("dfma", "dmma_m8n8k4", "dmma_m16n8k4", "dmma_m16n8k16")):
+        out[name] = binding.fp64_peak(k)
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    spd = a @ a.T + n * torch.eye(n, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, fn, fl in (("torch_matmul_4096", lambda: a @ b, 2.0 * n ** 3),
+                         ("torch_cholesky_4096", lambda: torch.linalg.cholesky(spd), n ** 3 / 3.0)):
+        fn()
+        best = 1e30
+        for _ in range(3):
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = fl / (best * 1e-3) / 1e9
+    del a, b, spd
+    return out
+
+
+def path_flops(h):
+    """Algorithmic FP64 flop of one condense + Cholesky (A4-A9, adjoint route,
+    N = nu columns): four triangular solves over nu columns with the factors'
+    strict parts (2 S nu each) and their diagonal scaling (nx nu per pair), the
+    numeric LU (2 x the symbolic multiply-add count), H = K Z (2 nnz(K) nu),
+    G_u^T Psi (2 nnz(G_u) nu) and the Cholesky (nu^3 / 3)."""
+    st = h.stats()
+    S = (st["nnz_lu"] - h.nx) // 2
+    _, _, _, ci = h.get_csr_pattern(0)        # G = [G_u G_x], columns [u; x]
+    nnz_gu = int((ci < h.nu).sum())
+    trsm = 4 * 2 * S * h.nu + 2 * h.nx * h.nu
+    return {"trsm": trsm, "refactor": 2 * st["lu_flops"], "spmm": 2 * st["nnz_k"] * h.nu,
+            "kred": 2 * nnz_gu * h.nu, "chol": h.nu ** 3 / 3.0, "S": S}
+
+
+def time_condense(h, D, delta, reps, stream, torch):
+    """Mean CUDA-event ms of condense + Cholesky (after one untimed pass)."""
+    ts = []
+    for k in range(reps + 1):
+        h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        h.kkt_factor(delta)
+        b.record(stream)
+        b.synchronize()
+        if k:
+            ts.append(a.elapsed_time(b))
+    return float(np.mean(ts))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-scale", action="store_true", help="skip the 10,000-bus measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 2,000-bus measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-instance batched solves")
     ap.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing")
     ap.add_argument("--no-vjp", action="store_true", help="skip the 10,000-bus dispatch-derivative timing")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP64 peak probes (derived peak instead)")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
@@ -266,23 +342,32 @@ def main():
     from paper_2203_11875_gb300 import binding, build
     build.build()
     dev = torch.device("cuda", local)
-    net = gridgen.grid2000()
+    props = torch.cuda.get_device_properties(dev)
+    peaks = None if args.no_peaks else fp64_peaks(binding, torch, dev)
+    sm_max = 2070.0
+    try:
+        sm_max = float(subprocess.run(["nvidia-smi", f"--id={local}", "--query-gpu=clocks.max.sm",
+                                       "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                      timeout=30).stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        pass
+    derived = props.multi_processor_count * 2 * 2 * sm_max / 1e3   # SMs x DFMA/clk x flop x GHz
+    peak = peaks["dfma"] if peaks else derived
+    net = gridgen.grid10k()
     h = binding.Handle(net, chol_form=args.chol_form, rhs_block=args.rhs_block, rhs1_kernel=args.rhs1_kernel)
     stream = torch.cuda.Stream(device=dev)
     h.set_stream(stream)
-    it = synthetic_iterate(net, h.nx, h.nu, h.m)
+    it, delta = stored_iterate()
     D = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in it.items()}
     step = torch.zeros(h.n_kkt, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def hot_step(delta):
+    def hot_step(dl):
         h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
         h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
-        col = h.kkt_factor(delta)
-        return col
+        return h.kkt_factor(dl)
 
     torch.cuda.synchronize()
-    delta = 0.0
     for _ in range(max(args.warmup, 3)):
         while hot_step(delta) >= 0:
             delta = max(1e-4, 8 * delta)
@@ -290,13 +375,13 @@ def main():
     torch.cuda.synchronize()
     trsm_kernel, trsm_tune, trsm_kernel1 = h.trsm_choice()
     chol_form, chol_grid, chol_tune = h.chol_choice()
-    n_launch0 = binding.launch_count()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     h.profile(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    n_launch0 = binding.launch_count()
     sampler.start()
     for k in range(args.steps):
         with torch.cuda.stream(stream):
@@ -310,33 +395,37 @@ def main():
         h.kkt_solve(D["r"], step)
         ev[k][3].record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
     n_launch = binding.launch_count() - n_launch0
+    clocks = sampler.stop()
     phases = h.phase_times()
     h.profile(False)
     cf = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     full = [ev[k][0].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    ph = {p: v[0] / args.steps for p, v in phases.items()}
     split = {"eval": float(np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])),
              "condense_cholesky": float(np.mean(cf)),
+             "condensed_rhs": ph["rhs"],
              "step_recovery": float(np.mean([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)]))}
-    t_cf, t_full = float(np.mean(cf)), float(np.mean(full))
+    t_cf = float(np.mean(cf)) + ph["rhs"]      # A4-A9: condensation, Cholesky and the condensed RHS
+    t_full = float(np.mean(full))
     if dist:
         t = torch.tensor([t_cf, t_full], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_cf, t_full = t.tolist()
     # roofline of the dominant kernel: the multi-RHS triangular solves
-    st = h.stats()
-    S = (st["nnz_lu"] - h.nx) // 2           # strict lower = strict upper entries
-    flops_trsm = (4 * 2 * S * h.nu + 2 * h.nx * h.nu)  # L, U, U^T, L^T over nu columns; 2 diagonal scalings
+    fl = path_flops(h)
     trsm_ms, trsm_n = phases["trsm"]
     per_launch_ms = trsm_ms / max(1, trsm_n)
-    achieved = (flops_trsm / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
+    achieved = (fl["trsm"] / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
     trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk", 96: "k_trsm_df"}.get(trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
     trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)", 96: " (dataflow)"}.get(
         trsm_kernel, " (staged)")
-    traffic = measured_traffic(trsm_base)
-    # end-to-end through the public API with pinned host buffers
-    host = {k: torch.as_tensor(v, dtype=torch.float64).pin_memory() for k, v in it.items()}
+    traffic = measured_traffic(trsm_base, "grid10k")
+    fl_path = sum(v for k, v in fl.items() if k != "S")
+    cf_ms = float(np.mean(cf))
+    # end to end through the public API with pinned host buffers: opf_newton_step
+    keys = ("x", "u", "lam", "y", "sig_u", "sig_x", "sig_s", "r")
+    host = {k: torch.as_tensor(it[k], dtype=torch.float64).pin_memory() for k in keys}
     step_h = torch.zeros(h.n_kkt, dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * 8 for v in host.values())
     d2h = step_h.numel() * 8
@@ -347,22 +436,22 @@ def main():
         with torch.cuda.stream(stream):
             flush.zero_()
             e0.record(stream)
-            for key in host:
-                D[key].copy_(host[key], non_blocking=True)
-        h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
-        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
-        h.kkt_factor(delta)
-        h.kkt_solve(D["r"], step)
+        assert h.newton_step(*[host[k_] for k_ in keys], step_h, delta_w=delta) == -1
         with torch.cuda.stream(stream):
-            step_h.copy_(step, non_blocking=True)
             e1.record(stream)
         e1.synchronize()
         e2e.append(e0.elapsed_time(e1))
     e2e_ms = float(np.mean(e2e))
-    out = {"metric": METRIC, "value": t_cf / max(1, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    step_dev = step.cpu().numpy()
+    e2e_rel = float(np.abs(step_h.numpy() - step_dev).max() / max(np.abs(step_dev).max(), 1e-300))
+    out = {"metric": METRIC, "value": t_cf, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_full, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "l2": "256 MB flush written between timed steps",
+           "config": {"workload": WORKLOAD, "inputs": "tests/golden/grid10k_iterate.npz (oracle LinRed iterate 3 "
+                      "of the seeded 10,000-bus network)",
+                      "l2": "inputs larger than L2 (Z, H 168 MB each) and a 256 MB flush written between timed steps",
+                      "timed": "A4-A9: G_x refactor, multi-RHS solves, K, H = K Z, Kred, one Cholesky attempt "
+                               "(events) + the condensed right-hand side of the step solve (phase events)",
                       "route": "adjoint", "delta_w": delta,
                       "trsm_kernel": KERNEL_NAMES.get(trsm_kernel, str(trsm_kernel)),
                       "trsm_kernel_1rhs": KERNEL_NAMES.get(trsm_kernel1, str(trsm_kernel1)),
@@ -371,75 +460,77 @@ def main():
                                    "ctas": chol_grid, "autotune_ms": chol_tune}},
            "clocks": clocks, "gpu_launches": int(n_launch),
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                   "includes": "H2D of x,u,lambda,y,Sigma,r + derivatives + condense + Cholesky + step + D2H of the step"},
+                   "includes": "opf_newton_step from pinned host buffers: H2D of x, u, lambda, y, Sigma, r + "
+                               "derivatives + condense + Cholesky + step solve and recovery + D2H of the step",
+                   "max_rel_diff_vs_device_step": e2e_rel},
            "split_ms_per_step": split,
-           "phases_ms_per_step": {p: v[0] / args.steps for p, v in phases.items()},
+           "phases_ms_per_step": ph,
            "roofline": {"bound": "alu", "kernel": trsm_name,
-                        "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                        "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None, "traffic": traffic,
-                        "flops_per_launch": flops_trsm / 4, "ms_per_launch": per_launch_ms,
-                        "peak_note": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
-           "symbolic": st}
+                        "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                        "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                        "flops_per_launch": fl["trsm"] / 4, "ms_per_launch": per_launch_ms,
+                        "peak_note": ("FP64 DFMA measured live in this run (opf_fp64_peak: fma chains on every "
+                                      "FP64 pipe); no FP64 entry in the measured-peak file" if peaks else
+                                      "FP64 derived: SMs x 2 DFMA/clk x 2 flop x max SM clock"),
+                        "peak_derived": derived},
+           "path_roofline": {"flops": fl_path, "ms": cf_ms, "achieved": fl_path / (cf_ms * 1e-3) / 1e9,
+                             "peak": peak, "frac": fl_path / (cf_ms * 1e-3) / 1e9 / peak,
+                             "flops_by_phase": {k: v for k, v in fl.items() if k != "S"},
+                             "note": "algorithmic FP64 flop of condense + Cholesky (adjoint route) over its "
+                                     "CUDA-event time, against the measured DFMA peak"},
+           "fp64_peaks_gflops": peaks,
+           "symbolic": h.stats()}
     if world > 1:
         out["value"] = t_cf / world
-    if not args.no_scale:
-        n10 = gridgen.grid10k()
-        h10 = binding.Handle(n10, chol_form=args.chol_form)
-        h10.set_stream(stream)
-        i10 = synthetic_iterate(n10, h10.nx, h10.nu, h10.m)
-        D10 = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in i10.items()}
-        d10 = 0.0
-        for _ in range(2):
-            h10.eval_derivatives(D10["x"], D10["u"], D10["lam"], D10["y"])
-            h10.condense(D10["sig_u"], D10["sig_x"], D10["sig_s"])
-            while h10.kkt_factor(d10) >= 0:
-                d10 = max(1e-4, 8 * d10)
-        h10.profile(True)
-        t10 = []
+    if not args.no_small:
+        n2 = gridgen.grid2000()
+        h2 = binding.Handle(n2, chol_form=args.chol_form)
+        h2.set_stream(stream)
+        i2 = synthetic_iterate(n2, h2.nx, h2.nu, h2.m)
+        D2 = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in i2.items()}
+        d2 = 0.0
         for _ in range(3):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            h10.eval_derivatives(D10["x"], D10["u"], D10["lam"], D10["y"])
-            with torch.cuda.stream(stream):
-                a.record(stream)
-            h10.condense(D10["sig_u"], D10["sig_x"], D10["sig_s"])
-            h10.kkt_factor(d10)
-            with torch.cuda.stream(stream):
-                b.record(stream)
-            b.synchronize()
-            t10.append(a.elapsed_time(b))
-        ph10 = h10.phase_times()
-        k10, tune10, _ = h10.trsm_choice()
-        cf10, cg10, ct10 = h10.chol_choice()
-        out["grid10k"] = {"condense_cholesky_ms": float(np.mean(t10)), "trsm_kernel": k10, "autotune_ms": tune10,
-                          "cholesky": {"form": cf10, "ctas": cg10, "autotune_ms": ct10},
-                          "phases_ms_per_step": {p: v[0] / 3 for p, v in ph10.items()},
-                          "symbolic": h10.stats()}
-        if not args.no_vjp:
-            # the dispatch derivative of the converged 10,000-bus solve for 256 unit cotangents
-            h10.profile(False)
-            r10 = h10.solve("linred")
-            V = torch.as_tensor(gridgen.cotangents(n10.ng), dtype=torch.float64, device=dev)
-            gP = torch.empty((V.shape[0], n10.nb), dtype=torch.float64, device=dev)
-            gQ = torch.empty_like(gP)
+            h2.eval_derivatives(D2["x"], D2["u"], D2["lam"], D2["y"])
+            h2.condense(D2["sig_u"], D2["sig_x"], D2["sig_s"])
+            while h2.kkt_factor(d2) >= 0:
+                d2 = max(1e-4, 8 * d2)
+        h2.profile(True)
+        t2 = time_condense(h2, D2, d2, 20, stream, torch)
+        ph2 = h2.phase_times()
+        h2.profile(False)
+        k2, tune2, _ = h2.trsm_choice()
+        cf2, cg2, ct2 = h2.chol_choice()
+        out["grid2000"] = {"workload": "grid2000: nu=399, nx=3,799, synthetic flat-start-like iterate",
+                           "condense_cholesky_ms": t2, "trsm_kernel": KERNEL_NAMES.get(k2, str(k2)),
+                           "cholesky": {"form": cf2, "ctas": cg2},
+                           "phases_ms_per_step": {p: v[0] / 21 for p, v in ph2.items()}}
+        del h2
+    if not args.no_vjp:
+        # the dispatch derivative of the converged 10,000-bus solve for 256 unit cotangents
+        r10 = h.solve("linred")
+        V = torch.as_tensor(gridgen.cotangents(net.ng), dtype=torch.float64, device=dev)
+        gP = torch.empty((V.shape[0], net.nb), dtype=torch.float64, device=dev)
+        gQ = torch.empty_like(gP)
+        t0 = time.perf_counter()
+        h.vjp_prepare()
+        t_prep = time.perf_counter() - t0
+        h.dispatch_vjp(V, gP, gQ)                    # warm-up (workspace growth)
+        reps = []
+        for _ in range(3):
             t0 = time.perf_counter()
-            h10.vjp_prepare()
-            t_prep = time.perf_counter() - t0
-            h10.dispatch_vjp(V, gP, gQ)                    # warm-up (workspace growth)
-            reps = []
-            for _ in range(3):
-                t0 = time.perf_counter()
-                h10.dispatch_vjp(V, gP, gQ)
-                reps.append(time.perf_counter() - t0)
-            info = h10.vjp_info()
-            out["vjp_grid10k"] = {"cotangents": int(V.shape[0]), "solve_s": r10["ms_total"] * 1e-3,
-                                  "solve_iters": r10["iters"], "prepare_ms": t_prep * 1e3,
-                                  "vjp_ms": float(np.median(reps)) * 1e3, "refine_steps": info["refine_steps"],
-                                  "rel_residual": info["rel_residual"], "polish_iters": info["polish_iters"]}
+            h.dispatch_vjp(V, gP, gQ)
+            reps.append(time.perf_counter() - t0)
+        info = h.vjp_info()
+        out["vjp_grid10k"] = {"cotangents": int(V.shape[0]), "solve_s": r10["ms_total"] * 1e-3,
+                              "solve_iters": r10["iters"], "solve_obj": r10["obj"], "prepare_ms": t_prep * 1e3,
+                              "vjp_ms": float(np.median(reps)) * 1e3, "refine_steps": info["refine_steps"],
+                              "rel_residual": info["rel_residual"], "polish_iters": info["polish_iters"]}
     if not args.no_batch:
         out["batch96"] = run_batch(binding, args.batch_threads, rank, world, dist, dev)
-    # one whole interior-point solve of the same network (LinRed), GPU path
+    # one whole interior-point solve of the 2,000-bus network (LinRed), GPU path
     if not args.no_solve:
-        hs = binding.Handle(net)
+        n2 = gridgen.grid2000()
+        hs = binding.Handle(n2)
         hs.set_stream(stream)
         t0 = time.perf_counter()
         rs = hs.solve("linred")
@@ -447,25 +538,27 @@ def main():
                         "iters": rs["iters"], "obj": rs["obj"], "status": rs["status"],
                         "graph_iters": rs["graph_iters"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms, reps = cpu_oracle_condense(net, it)
+        ms, reps = cpu_oracle_condense(net, it, delta, budget_s=20.0)
         out["cpu_baseline"] = {"value": ms, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": f"{reps} oracle condense+Cholesky evaluations of the same grid2000 "
-                                         "iterate (SciPy splu + BLAS, all host threads)"}
-        # the same on one host thread, in a child process whose BLAS is limited to one thread
+                               "sample": f"{reps} oracle condense+Cholesky evaluations of the stored grid10k "
+                                         "iterate (SciPy splu for S_x runs on one thread; the BLAS products "
+                                         "and the Cholesky on all host threads)"}
+        # the same with BLAS pinned to one thread, in a child process
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
         try:
             r1 = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                                 "--steps", "5", "--warmup", "1"], env=env, capture_output=True, text=True,
-                                timeout=300)
+                                 "--steps", "2", "--warmup", "0"], env=env, capture_output=True, text=True,
+                                timeout=600)
             one = json.loads(r1.stdout.strip().splitlines()[-1])
             out["cpu_baseline_1thread"] = {"value": one["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                           "sample": "5 oracle condense+Cholesky evaluations, BLAS on one thread"}
+                                           "sample": "2 oracle condense+Cholesky evaluations of the stored "
+                                                     "grid10k iterate, BLAS on one thread"}
         except (subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
             out["cpu_baseline_1thread"] = {"unavailable": str(e)[:200]}
         if not args.no_solve:
             from oracle import ipm as oracle_ipm
             t0 = time.perf_counter()
-            ro = oracle_ipm.linred(net)
+            ro = oracle_ipm.linred(gridgen.grid2000())
             out["solve"]["cpu_oracle_wall_s"] = time.perf_counter() - t0
             out["solve"]["cpu_oracle_iters"] = ro.iters
             out["solve"]["rel_obj_diff_vs_oracle"] = abs(ro.obj - out["solve"]["obj"]) / abs(ro.obj)

@@ -179,10 +179,23 @@ int opf_condense(opf_handle* h, const double* sig_u, const double* sig_x,
                  const double* sig_s, double* Kred);
 
 /* ---- A9: control-step factorisation (Algorithm 1; Theorem 3; Sec. 4.3) ------- */
-/* Cholesky Kred + delta_w I = L L^T of the Kred of the last opf_condense (kept
- * unmodified, so the call can be repeated with a larger delta_w).  Errors:
- * NOT_PD with *fail_col (may be NULL) set to the first failing column. */
-int opf_kkt_factor(opf_handle* h, double delta_w, int* fail_col);
+/* Inertia correction and Cholesky of the control step: Kred + delta_w I = L L^T.
+ * The paper regularises until the condensed matrix is positive definite
+ * (Sec. 4.3); the two terms sit here:
+ *  - delta_w >= 0, the primal term, on the control block (Kred + delta_w I);
+ *  - delta_c >= 0, the dual term, on the inequality rows only: -delta_c I in the
+ *    (p_y, p_y) block of K_aug.  Eliminating p_s and p_y turns Sigma_s into
+ *    Sigma_t = (Sigma_s^{-1} + delta_c)^{-1}, so a delta_c different from the
+ *    one the handle holds re-forms K = W + diag(Sigma_w) + A^T Sigma_t A, H and
+ *    Kred from the last opf_condense (the G_x factor and S_x are kept; on the
+ *    adjoint route this costs one product H = K Z and one multi-RHS G_x^{-T}
+ *    solve).  Every opf_condense starts again from delta_c = 0.
+ * The condensed matrix is kept unmodified by delta_w, so the call can be
+ * repeated with a larger delta_w.  Later opf_kkt_solve calls solve the K_aug
+ * with both terms.  Errors: INVALID_ARG (no condensation, negative or
+ * non-finite delta), NOT_PD with *fail_col (may be NULL; -1 otherwise) set to
+ * the first failing column, SINGULAR, TIMEOUT. */
+int opf_kkt_factor(opf_handle* h, double delta_w, double delta_c, int* fail_col);
 /* Copy the Cholesky factor (lower triangle, row-major nu x nu; upper part
  * zero) to device dst. */
 int opf_get_factor(opf_handle* h, double* dst);
@@ -191,17 +204,45 @@ int opf_get_factor(opf_handle* h, double* dst);
 /* Solve K_aug p = -r for nrhs right-hand sides (device, n_kkt doubles each, see
  * the block order above) with the current factors; step receives
  * [p_u | p_x | p_s | p_lambda | p_y] per right-hand side.  rhs and step must not
- * overlap.  K_aug carries Sigma and delta_w of the last condense/factor. */
+ * overlap.  K_aug carries Sigma of the last condense and delta_w, delta_c of the
+ * last factor (-delta_c I in its (p_y, p_y) block). */
 int opf_kkt_solve(opf_handle* h, const double* rhs, double* step, int nrhs);
 /* Solve K_aug^T z = -r (K_aug is symmetric; this path applies the transposed
  * recovery, G_x^{-T} first), same layout.  Used by the dispatch derivative. */
 int opf_kkt_solve_adjoint(opf_handle* h, const double* rhs, double* sol, int nrhs);
+
+/* One Newton step from HOST buffers (Algorithm 1's linear algebra in one call):
+ * copy x[nx], u[nu], lam[nx], y[m], sig_u[nu], sig_x[nx], sig_s[m] and the
+ * full-space right-hand side rhs[n_kkt] to the device, evaluate the derivatives,
+ * refactor G_x and condense (A1-A7), factor Kred + delta_w I with the dual
+ * regularisation delta_c (A9, as opf_kkt_factor), solve K_aug p = -rhs and
+ * recover the step (A8, A10), and copy step[n_kkt] = [p_u | p_x | p_s | p_lambda |
+ * p_y] back.  All pointers are host memory (pinned memory makes the copies
+ * asynchronous); the handle's stream carries every copy and launch, and the call
+ * returns after the step has landed.  The handle is left as after
+ * opf_kkt_factor (later opf_kkt_solve calls reuse the factors).
+ * Errors: INVALID_ARG, NOT_PD (*fail_col = first failing column; no step is
+ * written), SINGULAR, CUDA, OOM, TIMEOUT. */
+int opf_newton_step(opf_handle* h, const double* x, const double* u, const double* lam, const double* y,
+                    const double* sig_u, const double* sig_x, const double* sig_s, const double* rhs,
+                    double delta_w, double delta_c, double* step, int* fail_col);
 
 /* ---- A11: reduce-then-linearize helpers (Algorithm 2, Sec. 4.4) -------------- */
 /* Newton-Raphson on g(x, u) = 0 for x at fixed u (device u[nu]; device x[nx]
  * in: start, out: solution) to ||g||_inf <= tol.  Errors: PF_FAILED. */
 int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter,
                   int* iters);
+/* Reduced gradient of Eq. reduced:derivatives (Sec. 2.3) and the adjoint step of
+ * Algorithm 2, with the G_x factor of the last refactorisation (opf_gx_factor,
+ * opf_condense or opf_powerflow's last Newton step at the same point):
+ *   lam = -G_x^{-T} grad_x,   grad_r = grad_u + G_u^T lam.
+ * grad[nu+nx] = [grad_u; grad_x] (device) is any gradient over w = [u; x]: grad f
+ * gives grad f_r, grad_w (f + y^T h) the reduced Lagrangian gradient; NULL takes
+ * grad f of the last opf_eval_derivatives.  Outputs (device): grad_r[nu], and
+ * lam[nx] when non-NULL.  One G_x^{-T} solve; synchronises the handle's stream.
+ * Errors: INVALID_ARG (no factor of G_x at the last evaluation, NULL grad_r),
+ * CUDA, OOM. */
+int opf_reduced_gradient(opf_handle* h, const double* grad, double* grad_r, double* lam);
 
 /* ---- the interior-point loop (Algorithms 1 and 2; Sec. 4.3, 4.4) --------------- */
 #define OPF_LINRED 0   /* linearize-then-reduce (Algorithm 1) */
@@ -330,7 +371,8 @@ int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm_result* re
  *    device array sized for n <= 4096 (about 32 KB), held by every GPU that loads
  *    the library until the process exits; larger n is rejected with INVALID_ARG.
  *  - The first call on a device looks that array's address up on the current
- *    device; make that first call before any stream capture.
+ *    device (once per device).  Every call ends by synchronising the stream, so
+ *    the call cannot be used inside a stream capture.
  *  - Every call shares the one array per device: calls whose GPU work overlaps
  *    (two streams, two host threads) race; serialise them.
  * Errors: INVALID_ARG, CUDA, NOT_PD (*fail_col = first failing column), TIMEOUT. */
@@ -343,9 +385,17 @@ int opf_chol_noalloc(const double* A, int n, double delta_w, double* L, int* fai
 int opf_last_cuda_error(char* name, int len);
 /* Kernel launches this library has enqueued since it was loaded (all handles). */
 unsigned long long opf_launch_count(void);
+/* Measured FP64 throughput of the current device in GFLOP/s (host output), the
+ * roofline denominator of this library's FP64 kernels: which = 0 DFMA (fma
+ * chains on every FP64 pipe of a full grid), 1 / 2 / 3 the warp-level f64
+ * tensor-core path mma.sync m8n8k4 / m16n8k4 / m16n8k16 (four accumulators per
+ * warp).  Best of two timed launches on the legacy default stream; allocates
+ * and frees a small output buffer; synchronises the device.  The paper has no
+ * counterpart (it reports no roofline).  Errors: INVALID_ARG, CUDA, OOM. */
+int opf_fp64_peak(int which, double* gflops);
 
 /* Phase timing.  While enabled, CUDA events on the handle's stream bracket every
- * launch of each phase of opf_condense / opf_kkt_factor; opf_phase_times
+ * launch of each phase of opf_condense / opf_kkt_factor / opf_kkt_solve; opf_phase_times
  * synchronises the stream and returns, per phase, the accumulated milliseconds
  * (ms[OPF_PHASE_COUNT]) and the number of bracketed launches.  Enabling resets
  * the accumulators. */
@@ -355,7 +405,9 @@ unsigned long long opf_launch_count(void);
 #define OPF_PHASE_SPMM     3   /* H = K Z                                        */
 #define OPF_PHASE_KRED     4   /* H_u - G_u^T Psi (or S_x^T H_x), symmetrise     */
 #define OPF_PHASE_CHOL     5   /* Cholesky of Kred + delta_w I                   */
-#define OPF_PHASE_COUNT    6
+#define OPF_PHASE_RHS      6   /* condensed right-hand side of opf_kkt_solve     */
+#define OPF_PHASE_RECOVER  7   /* its Cholesky solve and step recovery           */
+#define OPF_PHASE_COUNT    8
 int opf_profile(opf_handle* h, int enable);
 int opf_phase_times(opf_handle* h, double* ms, long long* launches);
 

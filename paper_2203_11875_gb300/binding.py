@@ -76,11 +76,13 @@ _SIGS = {
     "opf_gx_factor": (C.c_int, [C.c_void_p]),
     "opf_gx_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_condense": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "opf_kkt_factor": (C.c_int, [C.c_void_p, C.c_double, _ip]),
+    "opf_kkt_factor": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _ip]),
     "opf_get_factor": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "opf_newton_step": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_void_p, _ip]),
     "opf_kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_kkt_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
+    "opf_reduced_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result)]),
     "opf_get_solution": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_set_loads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -95,12 +97,13 @@ _SIGS = {
                                   C.POINTER(C.c_double)]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
     "opf_launch_count": (C.c_ulonglong, []),
+    "opf_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "opf_last_cuda_error": (C.c_int, [C.c_char_p, C.c_int]),
     "opf_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "opf_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
 }
 
-PHASES = ("refactor", "assemble", "trsm", "spmm", "kred", "chol")
+PHASES = ("refactor", "assemble", "trsm", "spmm", "kred", "chol", "rhs", "recover")
 
 _lib = None
 
@@ -127,6 +130,14 @@ def exported_symbols():
 def launch_count() -> int:
     """Kernel launches libcondipm.so has enqueued since it was loaded."""
     return int(load_library().opf_launch_count())
+
+
+def fp64_peak(which: int = 0) -> float:
+    """opf_fp64_peak: measured FP64 GFLOP/s of the current device (0 DFMA,
+    1/2/3 mma.sync f64 m8n8k4 / m16n8k4 / m16n8k16)."""
+    g = C.c_double(0.0)
+    _check(load_library().opf_fp64_peak(int(which), C.byref(g)), "opf_fp64_peak")
+    return g.value
 
 
 def chol_noalloc(A, n, delta_w, L, stream=None):
@@ -166,6 +177,17 @@ def _ptr(t):
     if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
         raise ValueError("expected a contiguous float64 CUDA tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, writable=False):
+    """Host pointer of a contiguous float64 CPU tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or (writable and not a.flags.writeable):
+            raise ValueError("expected a contiguous float64 numpy array")
+        return C.c_void_p(a.ctypes.data)
+    if getattr(a, "is_cuda", True) or a.dtype.itemsize != 8 or not a.is_contiguous():
+        raise ValueError("expected a contiguous float64 CPU tensor")
+    return C.c_void_p(a.data_ptr())
 
 
 class Handle:
@@ -276,13 +298,26 @@ class Handle:
         _check(self._lib.opf_condense(self._h, _ptr(sig_u), _ptr(sig_x), _ptr(sig_s), _ptr(Kred)),
                "opf_condense")
 
-    def kkt_factor(self, delta_w=0.0):
+    def kkt_factor(self, delta_w=0.0, delta_c=0.0):
         """Returns -1 on success, else the failing column (status NOT_PD)."""
         col = C.c_int(-1)
-        rc = self._lib.opf_kkt_factor(self._h, float(delta_w), C.byref(col))
+        rc = self._lib.opf_kkt_factor(self._h, float(delta_w), float(delta_c), C.byref(col))
         if rc == OPF_ERR_NOT_PD:
             return col.value
         _check(rc, "opf_kkt_factor")
+        return -1
+
+    def newton_step(self, x, u, lam, y, sig_u, sig_x, sig_s, rhs, step, delta_w=0.0, delta_c=0.0):
+        """opf_newton_step with HOST buffers: float64 CPU tensors or numpy arrays
+        (contiguous; pinned tensors make the copies asynchronous).  Returns -1
+        on success, else the failing Cholesky column (no step written)."""
+        args = [_host_ptr(a) for a in (x, u, lam, y, sig_u, sig_x, sig_s, rhs)]
+        col = C.c_int(-1)
+        rc = self._lib.opf_newton_step(self._h, *args, float(delta_w), float(delta_c), _host_ptr(step, True),
+                                       C.byref(col))
+        if rc == OPF_ERR_NOT_PD:
+            return col.value
+        _check(rc, "opf_newton_step")
         return -1
 
     def get_factor(self, dst):
@@ -356,6 +391,12 @@ class Handle:
         n = (C.c_longlong * len(PHASES))()
         _check(self._lib.opf_phase_times(self._h, ms, n), "opf_phase_times")
         return {p: (ms[i], n[i]) for i, p in enumerate(PHASES)}
+
+    def reduced_gradient(self, grad, grad_r, lam=None):
+        """opf_reduced_gradient: grad (nu+nx device vector, or None for grad f) ->
+        grad_r (nu) and, when given, the adjoint lam (nx)."""
+        _check(self._lib.opf_reduced_gradient(self._h, _ptr(grad), _ptr(grad_r), _ptr(lam)),
+               "opf_reduced_gradient")
 
     def powerflow(self, u, x, tol=1e-10, max_iter=30):
         it = C.c_int(0)

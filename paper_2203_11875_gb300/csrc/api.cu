@@ -72,9 +72,9 @@ cudaError_t allow_max_smem(const void* fn) {
 }
 }  // namespace condipm
 
-namespace {
+namespace condipm {
 
-cudaEvent_t take_event(opf_handle* h) {
+static cudaEvent_t take_event(opf_handle* h) {
   if (!h->evpool.empty()) {
     cudaEvent_t e = h->evpool.back();
     h->evpool.pop_back();
@@ -100,6 +100,10 @@ void ph_end(opf_handle* h) {
   h->recs.push_back({h->open_phase, h->open_ev, b});
   h->open_phase = -1;
 }
+
+}  // namespace condipm
+
+namespace {
 
 template <class T>
 int upload(opf_handle* h, T** dst, const std::vector<T>& v) {
@@ -208,6 +212,8 @@ int upload_all(opf_handle* h) {
   TRY(alloc(h, &h->Kval, P.K.nnz()));
   TRY(alloc(h, &h->sig_c, P.nw));
   TRY(alloc(h, &h->sig_s, P.m));
+  TRY(alloc(h, &h->sig_se, P.m));
+  TRY(alloc(h, &h->ps_sc, P.m));
   // transposes
   TRY(upload(h, &h->AT_rp, P.AT.rp));
   TRY(upload(h, &h->AT_ci, P.AT.ci));
@@ -432,10 +438,15 @@ int upload_all(opf_handle* h) {
   int mb = lu_refactor_max_blocks(h->lu_threads, (size_t)(h->lu_threads / 32) * maxlen * sizeof(double));
   int need = (P.nx + 7) / 8;
   h->lu_blocks = std::max(1, std::min(mb, need));
-  {
-    const int ntl = (P.nu + 31) / 32;
-    const int need = std::max(1, std::max((ntl - 1) * ntl / 2 * 4, (ntl + 7) / 8));
-    h->chol_blocks = std::max(1, std::min(chol_max_blocks(), std::min(need, 2 * 152)));
+  h->chol_blocks = chol_grid_cap(P.nu);
+  if (h->opt.chol_form == 2) {
+    // the dataflow form until the first complete factorisation tunes it: one CTA
+    // per SM, a quarter of the first step's panel row groups in the panel group
+    const int nb = std::max(2, std::min(chol_df_max_blocks(), device_sms()));
+    const int rows0 = (std::max(0, P.nu - 32) + 7) / 8;
+    h->chol_df = 1;
+    h->chol_blocks = nb;
+    h->chol_np = std::max(1, std::min(nb / 3, std::max(8, rows0 / 4)));
   }
   h->cs_ksplit_max = std::max(1, trsm_cols_max_blocks());
   h->blk_max = std::max(1, trsm_blk_max_blocks());
@@ -466,8 +477,16 @@ int read_status(opf_handle* h, int* info) {
   return OPF_ERR_CUDA;
 }
 
+// A captured graph of the condensation holds the addresses of these buffers:
+// when one is reallocated the graph is dropped, so that it is captured again.
+static void drop_graph(opf_handle* h) {
+  if (h->cf_exec) cudaGraphExecDestroy(h->cf_exec);
+  h->cf_exec = nullptr;
+}
+
 double* ybuf_reserve(opf_handle* h, size_t n) {
   if (n > h->ybuf_cap) {
+    drop_graph(h);
     if (h->ybuf) cudaFree(h->ybuf);
     h->ybuf = nullptr;
     h->ybuf_cap = 0;
@@ -479,6 +498,7 @@ double* ybuf_reserve(opf_handle* h, size_t n) {
 
 double* workspace(opf_handle* h, size_t n) {
   if (n > h->ws_cap) {
+    drop_graph(h);
     if (h->ws) cudaFree(h->ws);
     h->ws = nullptr;
     h->ws_cap = 0;
@@ -814,30 +834,14 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
   return OPF_OK;
 }
 
-int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s) {
+// A7 on the current K and Z = [I; S_x]: H = K Z, then Kred by the handle's route
+// (the x rows of H end up holding Psi = G_x^{-T} H_x on the adjoint route)
+static int reduce_async(opf_handle* h) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const int nu = P.nu, nx = P.nx, nw = P.nw;
-  h->psi_valid = false;
-  h->finv_valid = false;   // the explicit route uses the factor's buffer as scratch
-  if (!h->have_lu) TRY(factor_async(h));
-  CK(cudaMemcpyAsync(h->sig_s, sig_s, sizeof(double) * std::max(1, P.m), cudaMemcpyDeviceToDevice, s));
-  // A4: K = W + A^T Sigma_s A + diag(Sigma)
-  ph_begin(h, OPF_PHASE_ASSEMBLE);
-  CK(launch_assemble_K(s, P.K.nnz(), h->Wval, h->KAA_ptr, h->KAA_r, h->KAA_a, h->KAA_b, h->sig_s, h->Aval,
-                       h->Kval));
-  CK(launch_add_diag(s, nw, nu, h->K_diag, h->perm, sig_u, sig_x, h->Kval, h->sig_c));
-  ph_end(h);
-  // A6: Z = [I; S_x],  S_x = -(P G_x P^T)^{-1} P G_u   (perm rows); Z and H are
-  // row-major with leading dimension ldp (nu rounded up to 32): lanes of a warp
-  // hold consecutive right-hand-side columns
   const long long ld = h->ldp;
   double* Sx = h->Zt + (size_t)nu * ld;
-  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s));
-  CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
-  if (h->trsm_mode < 0) TRY(autotune_trsm(h, Sx, ld));
-  TRY(lu_solve_perm(h, 0, Sx, ld, 1, nu, true));
-  // A7: H = K Z
   ph_begin(h, OPF_PHASE_SPMM);
   CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, ld, 1, h->H, ld, 1, nu, 1.0, 0.0));
   ph_end(h);
@@ -855,9 +859,62 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
     CK(launch_symmetrize(s, nu, h->H, ld, 1, h->Kred));
     ph_end(h);
   }
+  return OPF_OK;
+}
+
+int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nx = P.nx, nw = P.nw;
+  h->psi_valid = false;
+  h->finv_valid = false;   // the explicit route uses the factor's buffer as scratch
+  h->delta_c = 0.0;
+  if (!h->have_lu) TRY(factor_async(h));
+  CK(cudaMemcpyAsync(h->sig_s, sig_s, sizeof(double) * std::max(1, P.m), cudaMemcpyDeviceToDevice, s));
+  // A4: K = W + A^T Sigma_s A + diag(Sigma)
+  ph_begin(h, OPF_PHASE_ASSEMBLE);
+  CK(launch_assemble_K(s, P.K.nnz(), h->Wval, h->KAA_ptr, h->KAA_r, h->KAA_a, h->KAA_b, h->sig_s, h->Aval,
+                       h->Kval));
+  CK(launch_add_diag(s, nw, nu, h->K_diag, h->perm, sig_u, sig_x, h->Kval, h->sig_c));
+  ph_end(h);
+  // A6: Z = [I; S_x],  S_x = -(P G_x P^T)^{-1} P G_u   (perm rows); Z and H are
+  // row-major with leading dimension ldp (nu rounded up to 32): lanes of a warp
+  // hold consecutive right-hand-side columns
+  const long long ld = h->ldp;
+  double* Sx = h->Zt + (size_t)nu * ld;
+  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s));
+  CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
+  if (h->trsm_mode < 0) TRY(autotune_trsm(h, Sx, ld));
+  TRY(lu_solve_perm(h, 0, Sx, ld, 1, nu, true));
+  TRY(reduce_async(h));
   h->have_condense = true;
   h->have_factor = false;
   h->sens_ready = false;
+  h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
+  return OPF_OK;
+}
+
+// Fold the dual regularisation delta_c of the inequality rows into K and Kred
+// of the last condensation: K = W + diag(Sigma_w) + A^T Sigma_t A with
+// Sigma_t = (Sigma_s^{-1} + delta_c)^{-1}, then H and Kred again.  The
+// refactorisation and S_x do not depend on Sigma and are kept.
+int recondense_dc(opf_handle* h, double delta_c) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  h->psi_valid = false;
+  h->finv_valid = false;
+  h->have_factor = false;
+  const double* sig = h->sig_s;
+  if (delta_c > 0.0) {
+    CK(launch_sigma_dc(s, P.m, delta_c, h->sig_s, h->sig_se, h->ps_sc));
+    sig = h->sig_se;
+  }
+  ph_begin(h, OPF_PHASE_ASSEMBLE);
+  CK(launch_assemble_K(s, P.K.nnz(), h->Wval, h->KAA_ptr, h->KAA_r, h->KAA_a, h->KAA_b, sig, h->Aval, h->Kval));
+  CK(launch_add_diag_c(s, P.nw, h->K_diag, h->sig_c, h->Kval));
+  ph_end(h);
+  TRY(reduce_async(h));
+  h->delta_c = delta_c;
   h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
   return OPF_OK;
 }
@@ -868,23 +925,29 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
 int tune_chol_blocks(opf_handle* h, double delta_w) {
   const Plan& P = h->P;
   const int cap = h->chol_blocks;
-  // candidates {form, grid, panel CTAs}: the barrier form with four grid sizes;
-  // the dataflow form with three grid sizes and a small panel group (a quarter
-  // of the first step's row groups), and with two grid sizes and a panel group
-  // of one row group per CTA
+  // candidates {form, grid, panel CTAs}, grids in units of the device's SM
+  // count: the barrier form at a quarter, a half, one and two CTAs per SM; the
+  // dataflow form at a half, one and two CTAs per SM with a small panel group (a
+  // quarter of the first step's row groups), and at one and two CTAs per SM with
+  // a panel group of one row group per CTA
+  const int sm = device_sms();
   const int rows0 = (std::max(0, P.nu - 32) + 7) / 8;   // panel row groups of the first step
   const int df_cap = chol_df_max_blocks();
   const int want = h->opt.chol_form;   // 0 both, 1 barrier form only, 2 dataflow form only
   struct Cand { int form, nb, np; };
+  const int q = std::max(1, sm / 4), hf = std::max(1, sm / 2), one = sm, two = 2 * sm;
   const Cand cand[OPF_CHOL_CANDIDATES] = {
-      {0, 38, 0}, {0, 76, 0}, {0, 152, 0}, {0, 304, 0},
-      {1, 76, std::max(1, std::min(76 / 3, std::max(8, rows0 / 4)))},
-      {1, 152, std::max(1, std::min(152 / 3, std::max(8, rows0 / 4)))},
-      {1, 304, std::max(1, std::min(304 / 3, std::max(8, rows0 / 4)))},
-      {1, 152, std::max(1, std::min(152 / 2, std::max(8, rows0)))},
-      {1, 304, std::max(1, std::min(304 / 2, std::max(8, rows0)))}};
-  // time only from a clean status word: a run that stops early on an error
-  // (the dataflow form leaves as soon as one is flagged) would look fast
+      {0, q, 0}, {0, hf, 0}, {0, one, 0}, {0, two, 0},
+      {1, hf, std::max(1, std::min(hf / 3, std::max(8, rows0 / 4)))},
+      {1, one, std::max(1, std::min(one / 3, std::max(8, rows0 / 4)))},
+      {1, two, std::max(1, std::min(two / 3, std::max(8, rows0 / 4)))},
+      {1, one, std::max(1, std::min(one / 2, std::max(8, rows0)))},
+      {1, two, std::max(1, std::min(two / 2, std::max(8, rows0)))}};
+  // time only from a clean status word, and keep the timings only if every
+  // candidate factored the whole matrix: a run that stops early on a
+  // non-positive pivot (the dataflow form leaves as soon as one is flagged)
+  // would look fast, so an indefinite matrix leaves the handle untuned and the
+  // next factorisation tries again
   int st0[ST_WORDS];
   CK(cudaMemcpyAsync(st0, h->st, sizeof(st0), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -894,13 +957,15 @@ int tune_chol_blocks(opf_handle* h, double delta_w) {
   CK(cudaEventCreate(&b));
   float best = 1e30f;
   int pick = cap, pick_df = 0, pick_np = 0;
-  for (int c = 0; c < OPF_CHOL_CANDIDATES; ++c) {
+  bool complete = true;
+  float ms_c[OPF_CHOL_CANDIDATES] = {};
+  for (int c = 0; c < OPF_CHOL_CANDIDATES && complete; ++c) {
     const int form = cand[c].form, nb = cand[c].nb, np = cand[c].np;
     if (want != 0 && want != form + 1) continue;
     if (form == 0 && nb > cap) continue;
     if (form == 1 && (nb > df_cap || nb - np < 1)) continue;
     float ms = 0.f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 2 && complete; ++rep) {
       CK(cudaMemsetAsync(h->st, 0, sizeof(int) * ST_WORDS, h->s));
       CK(cudaEventRecord(a, h->s));
       CK(launch_chol_prepare(h->s, P.nu, h->Kred, delta_w, h->F));
@@ -913,13 +978,20 @@ int tune_chol_blocks(opf_handle* h, double delta_w) {
       CK(cudaEventRecord(b, h->s));
       CK(cudaEventSynchronize(b));
       CK(cudaEventElapsedTime(&ms, a, b));
+      int stc[ST_WORDS];
+      CK(cudaMemcpyAsync(stc, h->st, sizeof(stc), cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      if (stc[ST_CODE] != 0 || stc[ST_TIMEOUT] != 0) complete = false;
     }
-    h->chol_ms[c] = ms;
+    ms_c[c] = ms;
     if (ms < best) { best = ms; pick = nb; pick_df = form; pick_np = np; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   CK(cudaMemsetAsync(h->st, 0, sizeof(int) * ST_WORDS, h->s));
+  CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->s));
+  if (!complete) return OPF_OK;   // untuned: defaults for this factorisation
+  for (int c = 0; c < OPF_CHOL_CANDIDATES; ++c) h->chol_ms[c] = ms_c[c];
   h->chol_blocks = pick;
   h->chol_df = pick_df;
   h->chol_np = pick_np;
@@ -1200,8 +1272,18 @@ int opf_condense(opf_handle* h, const double* sig_u, const double* sig_x, const 
   return rc;
 }
 
-int opf_kkt_factor(opf_handle* h, double delta_w, int* fail_col) {
-  if (!h || !h->have_condense || !(delta_w >= 0.0)) return OPF_ERR_INVALID_ARG;
+int opf_kkt_factor(opf_handle* h, double delta_w, double delta_c, int* fail_col) {
+  if (fail_col) *fail_col = -1;
+  if (!h || !h->have_condense || !(delta_w >= 0.0) || !(delta_c >= 0.0) || !(delta_c < 1e300))
+    return OPF_ERR_INVALID_ARG;
+  if (delta_c != h->delta_c) {
+    TRY(recondense_dc(h, delta_c));
+    int rc = condipm::read_status(h);
+    if (rc != OPF_OK) {
+      h->have_condense = false;
+      return rc;
+    }
+  }
   TRY(factor_kred_async(h, delta_w));
   int info = -1;
   int rc = condipm::read_status(h, &info);
@@ -1259,6 +1341,26 @@ int opf_phase_times(opf_handle* h, double* ms, long long* launches) {
     if (launches) launches[p] = h->ph_n[p];
   }
   return OPF_OK;
+}
+
+int opf_reduced_gradient(opf_handle* h, const double* grad, double* grad_r, double* lam) {
+  if (!h || !grad_r || !h->have_eval || !h->have_lu) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const double* g = grad ? grad : h->gradf;
+  double* ws = workspace(h, 2 * (size_t)P.nx);
+  if (!ws) return OPF_ERR_OOM;
+  double* t = ws;                 // elimination order
+  double* ln = ws + P.nx;         // natural order
+  // lam = -G_x^{-T} grad_x
+  CK(launch_permute_rows(s, P.nx, 1, h->perm, g + P.nu, P.nx, 1, t, 1, 0, -1.0, 0));
+  TRY(lu_solve_perm(h, 1, t, 1, 1, 1));
+  CK(launch_permute_rows(s, P.nx, 1, h->perm, t, 1, 0, ln, P.nx, 1, 1.0, 1));
+  // grad_r = grad_u + G_u^T lam  (the first nu rows of G^T in natural order)
+  CK(cudaMemcpyAsync(grad_r, g, sizeof(double) * P.nu, cudaMemcpyDeviceToDevice, s));
+  CK(launch_spmm(s, P.nu, h->GTn_rp, h->GTn_ci, h->Gval, h->GTn_map, ln, 1, 1, grad_r, 1, 1, 1, 1.0, 1.0));
+  if (lam) CK(cudaMemcpyAsync(lam, ln, sizeof(double) * P.nx, cudaMemcpyDeviceToDevice, s));
+  return read_status(h);
 }
 
 int opf_powerflow(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters) {

@@ -100,6 +100,8 @@ cudaError_t launch_assemble_K(cudaStream_t s, long long nnz, const double* W, co
                               const double* Aval, double* K);
 cudaError_t launch_add_diag(cudaStream_t s, int nw, int nu, const int* K_diag, const int* perm,
                             const double* sig_u, const double* sig_x, double* K, double* sig_c);
+cudaError_t launch_add_diag_c(cudaStream_t s, int nw, const int* K_diag, const double* sig_c, double* K);
+cudaError_t launch_sigma_dc(cudaStream_t s, int m, double dc, const double* sig_s, double* sig_t, double* scale);
 cudaError_t launch_scatter_rows(cudaStream_t s, int nrows, const int* rp, const int* ci,
                                 const int* map, const double* src, double alpha, double* X, long long xr,
                                 long long xc);
@@ -252,6 +254,11 @@ cudaError_t launch_chol_prepare(cudaStream_t s, int n, const double* A, double d
 cudaError_t launch_chol(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* bar,
                         long long spin_limit, int nblocks);
 int chol_max_blocks();
+// SMs of the current device
+int device_sms();
+// grid of the barrier-form Cholesky of an n x n matrix before tuning: enough CTAs
+// for the first step's tiles, at most two per SM and never more than are resident
+int chol_grid_cap(int n);
 // Dataflow (barrier-free, look-ahead) Cholesky: np panel CTAs, nblocks - np
 // update CTAs (at least one); cnt holds 2 * ceil(n / 32) counters (zeroed here).
 int chol_df_max_blocks();

@@ -8,6 +8,8 @@ int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam
 int factor_async(opf_handle* h);
 int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s);
 int factor_kred_async(opf_handle* h, double delta_w);
+// fold the dual regularisation delta_c of the inequality rows into K, H and Kred
+int recondense_dc(opf_handle* h, double delta_c);
 // X (row-major nu x k, device) <- (L L^T)^{-1} X with the current factor
 int chol_solve_async(opf_handle* h, double* X, int k);
 // K_aug p = -r (external layout), with up to `refine` refinement corrections
@@ -36,6 +38,9 @@ int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R);
 int kkt_refine(opf_handle* h, int k, const KB& b, const KB& z, bool solve_first, bool bl_zero, int max_steps,
                double* scratch, double* final_res, int* steps);
 int read_status(opf_handle* h, int* info = nullptr);
+// bracket the launches enqueued between the two calls with events (opf_profile)
+void ph_begin(opf_handle* h, int phase);
+void ph_end(opf_handle* h);
 double* workspace(opf_handle* h, size_t n);
 double* ybuf_reserve(opf_handle* h, size_t n);
 int lagrangian_gradient(opf_handle* h, const double* lam, const double* y, double* out);

@@ -265,6 +265,7 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
     h->sens_ready = false;
     h->finv_valid = false;
     h->delta_w = 0.0;
+    h->delta_c = 0.0;
   } else {
     TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
     TRYD(factor_kred_async(h, 0.0));
@@ -887,5 +888,47 @@ extern "C" int opf_get_solution(const opf_handle* h, double* w, double* lam, dou
     for (int k = 1; k < P.ng; ++k) Pg[k] = h->sol_w[P.pg_w[k]];
     Pg[0] = h->sol_pg0;
   }
+  return OPF_OK;
+}
+
+// One Newton step of the barrier KKT system (Algorithm 1, its linear-algebra
+// core) from host buffers: copy in, evaluate (A1-A3), condense (A4-A7), factor
+// (A9, with delta_w and delta_c), solve and recover (A8, A10), copy out.  The
+// copies run on the handle's stream through the loop's own device buffers.
+extern "C" int opf_newton_step(opf_handle* h, const double* x, const double* u, const double* lam,
+                               const double* y, const double* sig_u, const double* sig_x,
+                               const double* sig_s, const double* rhs, double delta_w, double delta_c,
+                               double* step, int* fail_col) {
+  if (fail_col) *fail_col = -1;
+  if (!h || !x || !u || !lam || !y || !sig_u || !sig_x || !sig_s || !rhs || !step || !(delta_w >= 0.0) ||
+      !(delta_c >= 0.0) || !(delta_c < 1e300))
+    return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  const size_t nkkt = (size_t)P.nw + 2 * (size_t)P.m + P.nx;
+  Dev d;
+  TRYD(alloc_dev(d, h));
+  TRYD(h2d(h->s, d.x, x, P.nx));
+  TRYD(h2d(h->s, d.u, u, P.nu));
+  TRYD(h2d(h->s, d.lam, lam, P.nx));
+  TRYD(h2d(h->s, d.y, y, P.m));
+  TRYD(h2d(h->s, d.sig_u, sig_u, P.nu));
+  TRYD(h2d(h->s, d.sig_x, sig_x, P.nx));
+  TRYD(h2d(h->s, d.sig_s, sig_s, P.m));
+  TRYD(h2d(h->s, d.rhs, rhs, nkkt));
+  TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+  TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+  if (delta_c > 0.0) TRYD(recondense_dc(h, delta_c));
+  TRYD(factor_kred_async(h, delta_w));
+  int info = -1;
+  const int rc = read_status(h, &info);
+  if (rc != OPF_OK) {
+    if (rc == OPF_ERR_NOT_PD && fail_col) *fail_col = info;
+    if (rc != OPF_ERR_NOT_PD) h->have_condense = false;
+    return rc;
+  }
+  h->have_factor = true;
+  TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
+  TRYD(d2h(h->s, step, d.step, nkkt));
+  CKD(cudaStreamSynchronize(h->s));
   return OPF_OK;
 }

@@ -6,6 +6,7 @@
 // and leave data movement to the load/store pipes.
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace condipm {
@@ -35,6 +36,27 @@ __global__ void k_add_diag(int nw, int nu, const int* __restrict__ K_diag, const
   double s = c < nu ? sig_u[c] : sig_x[perm[c - nu]];
   K[K_diag[c]] += s;
   sig_c[c] = s;
+}
+
+// K[(c,c)] += sigma_c from the stored c-order sigma (re-assembly of K at a new
+// dual regularisation)
+__global__ void k_add_diag_c(int nw, const int* __restrict__ K_diag, const double* __restrict__ sig_c,
+                             double* __restrict__ K) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nw) return;
+  K[K_diag[c]] += sig_c[c];
+}
+
+// Dual regularisation of the inequality rows (-delta_c I in the (p_y, p_y) block
+// of K_aug): Sigma_t = Sigma_s / (1 + delta_c Sigma_s) = (Sigma_s^{-1} + delta_c)^{-1}
+// and the slack-step scale 1 / (1 + delta_c Sigma_s)
+__global__ void k_sigma_dc(int m, double dc, const double* __restrict__ sig_s, double* __restrict__ sig_t,
+                           double* __restrict__ scale) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double d = 1.0 + dc * sig_s[i];
+  sig_t[i] = sig_s[i] / d;
+  scale[i] = 1.0 / d;
 }
 
 // X(i, ci[q]) = alpha * src[map[q]] for the entries q of row i (X zeroed before),
@@ -710,6 +732,17 @@ cudaError_t launch_add_diag(cudaStream_t s, int nw, int nu, const int* K_diag, c
   note_launch();
   return cudaGetLastError();
 }
+cudaError_t launch_add_diag_c(cudaStream_t s, int nw, const int* K_diag, const double* sig_c, double* K) {
+  k_add_diag_c<<<nblk(nw, 256), 256, 0, s>>>(nw, K_diag, sig_c, K);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_sigma_dc(cudaStream_t s, int m, double dc, const double* sig_s, double* sig_t, double* scale) {
+  if (m <= 0) return cudaSuccess;
+  k_sigma_dc<<<nblk(m, 256), 256, 0, s>>>(m, dc, sig_s, sig_t, scale);
+  note_launch();
+  return cudaGetLastError();
+}
 cudaError_t launch_scatter_rows(cudaStream_t s, int nrows, const int* rp, const int* ci, const int* map,
                                 const double* src, double alpha, double* X, long long xr, long long xc) {
   if (nrows <= 0) return cudaSuccess;
@@ -800,12 +833,21 @@ cudaError_t launch_chol_prepare(cudaStream_t s, int n, const double* A, double d
   note_launch();
   return cudaGetLastError();
 }
-int chol_max_blocks() {
-  int dev = 0, sms = 0, per = 0;
+int device_sms() {
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+int chol_max_blocks() {
+  int per = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol, 256, 0);
-  return sms * (per > 0 ? per : 1);
+  return device_sms() * (per > 0 ? per : 1);
+}
+int chol_grid_cap(int n) {
+  const int ntl = (n + 31) / 32;
+  const int need = std::max(1, std::max((ntl - 1) * ntl / 2 * 4, (ntl + 7) / 8));
+  return std::max(1, std::min(chol_max_blocks(), std::min(need, 2 * device_sms())));
 }
 cudaError_t launch_chol(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* bar,
                         long long spin_limit, int nblocks) {

@@ -13,6 +13,11 @@
 //   Kred p_u = e_u - G_u^T G_x^{-T} e_x,
 //   p_x = G_x^{-1} (b_l - G_u p_u),   p_l = G_x^{-T} (bt_w,x - [K p_w]_x).
 // Four multi-RHS solves with G_x (three when b_l = 0) and one with Kred.
+// With the dual regularisation delta_c of the inequality rows (-delta_c I in the
+// (p_y, p_y) block, folded into K by opf_kkt_factor), the same elimination reads
+//   p_s = (b_y' - A p_w) / (1 + delta_c Sigma_s),   b_y' = b_y + delta_c b_s,
+//   p_y = b_s - Sigma_t (b_y' - A p_w),   Sigma_t = Sigma_s / (1 + delta_c Sigma_s),
+// i.e. Sigma_t in place of Sigma_s, b_y' in place of b_y, and a scaled p_s.
 //
 // Internal layout of k right-hand sides: row-major with k lanes (element (i, j)
 // at X[i*k + j]); the w block in c-order ([u; x in elimination order]), the
@@ -66,6 +71,13 @@ __global__ void k_res_s(int m, int k, const double* __restrict__ sig, const doub
   R[t] = b[t] - fma(sig[t / k], zs[t], zy[t]);
 }
 
+// x <- d .* x (k lanes per row)
+__global__ void k_rows_scale_inplace(int n, int k, const double* __restrict__ d, double* x) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * k) return;
+  x[t] *= d[t / k];
+}
+
 __global__ void k_absmax_partial(long long n, const double* __restrict__ x, double* __restrict__ out) {
   __shared__ double sh[256];
   double v = 0.0;
@@ -114,7 +126,7 @@ int launched() {
 }  // namespace
 
 size_t kkt_rows(const Plan& P) { return (size_t)P.nw + 2 * (size_t)P.m + P.nx; }
-size_t kkt_core_scratch(const Plan& P) { return 3 * (size_t)P.nw + P.m; }
+size_t kkt_core_scratch(const Plan& P) { return 3 * (size_t)P.nw + 2 * (size_t)P.m; }
 size_t kkt_refine_scratch(const Plan& P, int k) {
   return (2 * kkt_rows(P) + kkt_core_scratch(P)) * (size_t)k + 512;
 }
@@ -136,8 +148,17 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   double* E = Bt + (size_t)nw * k;        // e     (nw x k)
   double* D0 = E + (size_t)nw * k;        // [0; q](nw x k)
   double* U = D0 + (size_t)nw * k;        // Sigma_s b_y - b_s (m x k)
+  double* Byr = U + (size_t)m * k;        // b_y' = b_y + delta_c b_s (m x k, delta_c > 0)
+  const bool dc = h->delta_c > 0.0;
+  const double* sig = dc ? h->sig_se : h->sig_s;
+  const double* by = b.y;
+  ph_begin(h, OPF_PHASE_RHS);
+  if (dc) {
+    CKK(launch_axpby(s, (long long)m * k, 1.0, b.y, h->delta_c, b.s, Byr));
+    by = Byr;
+  }
   // bt_w = b_w + A^T (Sigma_s b_y - b_s)
-  k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->sig_s, b.y, nullptr, U);
+  k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, sig, by, nullptr, U);
   TRYK(launched());
   CKK(launch_axpby(s, (long long)m * k, 1.0, U, -1.0, b.s, U));
   CKK(cudaMemcpyAsync(Bt, b.w, sizeof(double) * (size_t)nw * k, cudaMemcpyDeviceToDevice, s));
@@ -155,6 +176,8 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   CKK(cudaMemcpyAsync(p.w, E, sizeof(double) * (size_t)nu * k, cudaMemcpyDeviceToDevice, s));
   CKK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, E + (size_t)nu * k, k, 1, p.w, k, 1, k, -1.0,
                   1.0));
+  ph_end(h);
+  ph_begin(h, OPF_PHASE_RECOVER);
   TRYK(chol_solve_async(h, p.w, k));
   double* px = p.w + (size_t)nu * k;
   if (h->psi_valid && k <= 4) {
@@ -167,11 +190,16 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
                                     bl_zero ? nullptr : D0 + (size_t)nu * k, 1.0, px);
     TRYK(launched());
     CKK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, p.w, k, 1, p.s, k, 1, k, -1.0, 0.0));
-    CKK(launch_axpby(s, (long long)m * k, 1.0, b.y, 1.0, p.s, p.s));
-    k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->sig_s, p.s, b.s, p.y);
+    CKK(launch_axpby(s, (long long)m * k, 1.0, by, 1.0, p.s, p.s));
+    k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, sig, p.s, b.s, p.y);
     TRYK(launched());
+    if (dc) {
+      k_rows_scale_inplace<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->ps_sc, p.s);
+      TRYK(launched());
+    }
     k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->H + (size_t)nu * ld, ld, p.w, E + (size_t)nu * k, -1.0, p.l);
     TRYK(launched());
+    ph_end(h);
     return OPF_OK;
   }
   // p_x = G_x^{-1} (b_l - G_u p_u)
@@ -182,14 +210,19 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   }
   TRYK(lu_solve_perm(h, 0, px, k, 1, k));
   // p_s = b_y - A p_w ; p_y = b_s - Sigma_s p_s
-  CKK(cudaMemcpyAsync(p.s, b.y, sizeof(double) * (size_t)m * k, cudaMemcpyDeviceToDevice, s));
+  CKK(cudaMemcpyAsync(p.s, by, sizeof(double) * (size_t)m * k, cudaMemcpyDeviceToDevice, s));
   CKK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, p.w, k, 1, p.s, k, 1, k, -1.0, 1.0));
-  k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->sig_s, p.s, b.s, p.y);
+  k_rows_scale_sub<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, sig, p.s, b.s, p.y);
   TRYK(launched());
+  if (dc) {
+    k_rows_scale_inplace<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->ps_sc, p.s);
+    TRYK(launched());
+  }
   // p_l = G_x^{-T} (bt_w,x - [K p_w]_x)
   CKK(cudaMemcpyAsync(p.l, Bt + (size_t)nu * k, sizeof(double) * (size_t)nx * k, cudaMemcpyDeviceToDevice, s));
   CKK(launch_spmm(s, nx, h->K_rp + nu, h->K_ci, h->Kval, nullptr, p.w, k, 1, p.l, k, 1, k, -1.0, 1.0));
   TRYK(lu_solve_perm(h, 1, p.l, k, 1, k));
+  ph_end(h);
   return OPF_OK;
 }
 
@@ -209,9 +242,10 @@ int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R) {
   // R_l = b_l - G z_w
   CKK(cudaMemcpyAsync(R.l, b.l, sizeof(double) * (size_t)nx * k, cudaMemcpyDeviceToDevice, s));
   CKK(launch_spmm(s, nx, h->Gc_rp, h->Gc_ci, h->Gval, h->Gc_map, z.w, k, 1, R.l, k, 1, k, -1.0, 1.0));
-  // R_y = b_y - A z_w - z_s
+  // R_y = b_y - A z_w - z_s (+ delta_c z_y)
   CKK(launch_axpby(s, (long long)m * k, 1.0, b.y, -1.0, z.s, R.y));
   CKK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, z.w, k, 1, R.y, k, 1, k, -1.0, 1.0));
+  if (h->delta_c > 0.0) CKK(launch_axpby(s, (long long)m * k, 1.0, R.y, h->delta_c, z.y, R.y));
   return OPF_OK;
 }
 

@@ -64,9 +64,7 @@ extern "C" int opf_chol_noalloc(const double* A, int n, double delta_w, double* 
   // status and barrier state must start at zero; the inverse diagonal is overwritten
   if (cudaMemsetAsync(sc, 0, sizeof(int) * ST_WORDS + sizeof(unsigned) * 4, s) != cudaSuccess) return OPF_ERR_CUDA;
   if (launch_chol_prepare(s, n, A, delta_w, L) != cudaSuccess) return OPF_ERR_CUDA;
-  const int ntl = (n + 31) / 32;
-  const int need = std::max(1, std::max((ntl - 1) * ntl / 2 * 4, (ntl + 7) / 8));
-  const int nblocks = std::max(1, std::min(chol_max_blocks(), std::min(need, 2 * 152)));
+  const int nblocks = chol_grid_cap(n);
   if (launch_chol(s, n, L, sc->dinv, sc->st, sc->bar, 1LL << 26, nblocks) != cudaSuccess) return OPF_ERR_CUDA;
   int st[ST_WORDS] = {0, 0, 0, 0};
   if (cudaMemcpyAsync(st, sc->st, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess) return OPF_ERR_CUDA;

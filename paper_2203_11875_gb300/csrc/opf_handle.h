@@ -122,6 +122,11 @@ struct opf_handle {
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   bool psi_valid = false;         // Zt holds S_x and H's x rows G_x^{-T} H_x of the last condensation
   double delta_w = 0.0;
+  // dual regularisation of the inequality rows folded into K, H and Kred
+  // (-delta_c I in the (p_y, p_y) block of K_aug); 0 after every condensation
+  double delta_c = 0.0;
+  double* sig_se = nullptr;      // Sigma_s / (1 + delta_c Sigma_s) (m)
+  double* ps_sc = nullptr;       // 1 / (1 + delta_c Sigma_s) (m)
   double* pf_ws = nullptr;       // power-flow step and norm (nx + 1)
   double* ipm_buf = nullptr;     // interior-point loop scratch (in allocs)
   // converged state of the last opf_solve (host), full-space form

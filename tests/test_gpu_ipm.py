@@ -72,3 +72,28 @@ def test_one_rhs_kernels_give_the_same_solve(pkg, rhs1):
     res = pkg.Handle(net, rhs1_kernel=rhs1).solve("linred")
     assert ref["status"] == res["status"] == 0
     assert abs(res["obj"] - ref["obj"]) <= 1e-9 * abs(ref["obj"])
+
+
+def test_graph_is_recaptured_after_a_wide_vjp_grows_the_solve_buffers(pkg):
+    """A derivative call with many cotangents (256 > the 32-column leading
+    dimension of the 30-bus case) grows the solve scratch the captured
+    condensation graph points into; the next solve on the same handle must
+    capture again and reach the same optimum."""
+    net = gridgen.ring30()
+    ref = ipm.linred(net)
+    h = pkg.Handle(net)
+    st = torch.cuda.Stream()
+    h.set_stream(st)
+    a = h.solve("linred")
+    assert a["status"] == 0 and a["graph_iters"] > 0
+    h.vjp_prepare()
+    V = torch.eye(net.ng, dtype=torch.float64, device="cuda").repeat(256 // net.ng + 1, 1)[:256].contiguous()
+    gP = torch.empty((256, net.nb), dtype=torch.float64, device="cuda")
+    gQ = torch.empty_like(gP)
+    with torch.cuda.stream(st):
+        h.dispatch_vjp(V, gP, gQ)
+    b = h.solve("linred")
+    assert b["status"] == 0 and b["graph_iters"] > 0
+    assert b["iters"] == a["iters"]
+    assert abs(b["obj"] - a["obj"]) <= 1e-12 * abs(a["obj"])
+    assert abs(b["obj"] - ref.obj) <= TOL_OBJ * abs(ref.obj)

@@ -214,14 +214,96 @@ def test_kkt_factor_reports_not_pd(pkg, name, seed, scale, chol_form):
     want = _first_failing_column(S)
     assert want >= 0
     assert h.kkt_factor(0.0) == want
-    assert h.chol_choice()[0] == chol_form
+    # an aborted factorisation does not tune the grid (its timings would be of a
+    # partial factorisation); the forced form still ran
+    assert h.chol_choice()[0] == 0
     big = 2.0 * abs(np.linalg.eigvalsh(S)[0]) + 1.0
     assert h.kkt_factor(big) == -1
+    assert h.chol_choice()[0] == chol_form
     # and the factor of the shifted matrix is right after the aborted one
     F = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
     h.get_factor(F)
     F = N(F).reshape(lay.nu, lay.nu)
     assert rel_err(F @ F.T, S + big * np.eye(lay.nu)) <= TOL_KRED
+
+
+@pytest.mark.parametrize("route", [0, 1])
+@pytest.mark.parametrize("name", ["ring30", "grid2000"])
+def test_dual_regularization_matches_full_space_step(pkg, name, route):
+    """delta_c on the inequality rows (-delta_c I in the (p_y, p_y) block of
+    K_aug, Sec. 4.3): the factor is that of Kred with (Sigma_s^{-1} +
+    delta_c)^{-1} in place of Sigma_s, the step is the full-space step of the
+    regularised K_aug, and delta_c = 0 afterwards gives back the plain factor."""
+    net, rec = oracle_iterate(name)
+    lay = model.Layout(net)
+    h = pkg.Handle(net, route=route)
+    w, lam, y = rec["w"], rec["lam"], rec["y"]
+    gpu_eval(pkg, h, lay, w, lam, y)
+    sw, ss, delta = rec["sig_w"], rec["sig_s"], rec["delta"]
+    h.condense(T(sw[:lay.nu]), T(sw[lay.nu:]), T(ss))
+    _, G, A = model.jacobians(lay, w)
+    W = model.lagrangian_hessian(lay, w, lam, y)
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, delta), np.zeros(lay.nx)])
+    F = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(21)
+    R = np.stack([rec["r"], rng.standard_normal(len(rec["r"]))])
+    for dc in (0.3, 1e-3, 0.0):
+        assert h.kkt_factor(delta, dc) == -1
+        h.get_factor(F)
+        Fm = N(F).reshape(lay.nu, lay.nu)
+        Kt = kkt.kred_definition(G, A, W, sw, kkt.regularized_sigma(ss, dc), lay.nu) + delta * np.eye(lay.nu)
+        assert rel_err(Fm @ Fm.T, Kt) <= TOL_KRED, dc
+        step = torch.zeros(R.size, dtype=torch.float64, device="cuda")
+        h.kkt_solve(T(R.ravel()), step, 2)
+        step = N(step).reshape(2, -1)
+        for k in range(2):
+            ref = np.concatenate(kkt.full_space_step(G, A, Wd, sw, ss, R[k], delta_c=dc))
+            assert rel_err(step[k], ref) <= TOL_KRED, (dc, k)
+    with pytest.raises(pkg.OPFError):
+        h.kkt_factor(delta, -1.0)
+
+
+@pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000"])
+def test_reduced_gradient_matches_oracle(pkg, name):
+    """Eq. reduced:derivatives: grad f_r and the adjoint lam, from the handle's
+    grad f and from a caller's gradient (here grad_w of f + y^T h)."""
+    net, lay, w, lam, y, _, _ = random_point(name, seed=8)
+    h = pkg.Handle(net)
+    gpu_eval(pkg, h, lay, w)
+    with pytest.raises(pkg.OPFError):
+        h.reduced_gradient(None, torch.zeros(lay.nu, dtype=torch.float64, device="cuda"))
+    h.gx_factor()
+    gf, G, A = model.jacobians(lay, w)
+    gr = torch.zeros(lay.nu, dtype=torch.float64, device="cuda")
+    lm = torch.zeros(lay.nx, dtype=torch.float64, device="cuda")
+    h.reduced_gradient(None, gr, lm)
+    ref, lref = kkt.reduced_gradient(G, gf, lay.nu)
+    assert rel_err(N(gr), ref) <= TOL_SOLVE
+    assert rel_err(N(lm), lref) <= TOL_SOLVE
+    gl = gf + A.T @ y
+    h.reduced_gradient(T(gl), gr)
+    ref, _ = kkt.reduced_gradient(G, gl, lay.nu)
+    assert rel_err(N(gr), ref) <= TOL_SOLVE
+
+
+def test_indefinite_first_factorisation_leaves_the_cholesky_untuned(pkg):
+    """The Cholesky autotuner times complete factorisations only: a first call on
+    an indefinite Kred reports NOT_PD and leaves the handle untuned (form 0, no
+    timings), and the first positive definite factorisation tunes it."""
+    net, lay, w, lam, y, sw, ss = random_point("grid2000", seed=11)
+    lam, y = 3.0 * lam, 3.0 * y
+    h = pkg.Handle(net)
+    gpu_eval(pkg, h, lay, w, lam, y)
+    h.condense(T(sw[:lay.nu]), T(sw[lay.nu:]), T(ss))
+    assert h.kkt_factor(0.0) >= 0
+    form, _, ms = h.chol_choice()
+    assert form == 0 and all(v == 0 for v in ms.values())
+    _, G, A = model.jacobians(lay, w)
+    Ko = kkt.kred_definition(G, A, model.lagrangian_hessian(lay, w, lam, y), sw, ss, lay.nu)
+    big = 2.0 * abs(np.linalg.eigvalsh(0.5 * (Ko + Ko.T))[0]) + 1.0
+    assert h.kkt_factor(big) == -1
+    form, _, ms = h.chol_choice()
+    assert form in (1, 2) and any(v > 0 for v in ms.values())
 
 
 @pytest.mark.parametrize("name", ["ring30", "grid2000"])

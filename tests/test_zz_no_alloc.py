@@ -37,11 +37,16 @@ def test_chol_noalloc_matches_kkt_factor_twice(name):
     F = torch.zeros_like(Kred)
     h.get_factor(F)
     ref = F.cpu().numpy()
-    for _ in range(2):
-        L = torch.full_like(Kred, 7.0)
-        assert binding.chol_noalloc(Kred, lay.nu, delta, L) == -1
-        assert rel_err(L.cpu().numpy(), ref) <= 1e-9
-        got = L.cpu().numpy().reshape(lay.nu, lay.nu)
+    Ls = [torch.full_like(Kred, 7.0) for _ in range(2)]
+    torch.cuda.synchronize()
+    for k in range(2):
+        free0 = torch.cuda.mem_get_info()[0]
+        assert binding.chol_noalloc(Kred, lay.nu, delta, Ls[k]) == -1
+        # no device memory taken by the call (the first one may load the module)
+        if k == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+        assert rel_err(Ls[k].cpu().numpy(), ref) <= 1e-9
+        got = Ls[k].cpu().numpy().reshape(lay.nu, lay.nu)
         assert np.array_equal(got, np.tril(got))
 
 
