@@ -215,8 +215,10 @@ def test_kkt_factor_reports_not_pd(pkg, name, seed, scale, chol_form):
     assert want >= 0
     assert h.kkt_factor(0.0) == want
     # an aborted factorisation does not tune the grid (its timings would be of a
-    # partial factorisation); the forced form still ran
-    assert h.chol_choice()[0] == 0
+    # partial factorisation); the forced form still ran.  With one tile (nu <= 32)
+    # there is no grid to choose and nothing is timed.
+    if lay.nu > 32:
+        assert h.chol_choice()[0] == 0
     big = 2.0 * abs(np.linalg.eigvalsh(S)[0]) + 1.0
     assert h.kkt_factor(big) == -1
     assert h.chol_choice()[0] == chol_form
