@@ -304,7 +304,7 @@ int upload_all(opf_handle* h) {
     const ColDev& cd = k ? h->csU : h->csL;
     int *a, *b, *c, *d;
     TRY(upload(h, &a, rptr)); TRY(upload(h, &b, rows)); TRY(upload(h, &c, rsn)); TRY(upload(h, &d, doff));
-    (k ? h->bkU : h->bkL) = BlkDev{C.nlev, a, b, c, cd.sn_first, cd.sn_w, d, cd.ext_beg, cd.ext_end};
+    (k ? h->bkU : h->bkL) = BlkDev{C.nlev, a, b, c, cd.sn_first, cd.sn_w, d, cd.ext_beg, cd.ext_end, k};
     for (int l = 0; l < C.nlev; ++l) h->lu1s_ymax = std::max(h->lu1s_ymax, rptr[l + 1] - rptr[l]);
     // the one-CTA form's row descriptions
     std::vector<int> ma(4 * rows.size()), mb(4 * rows.size());
@@ -406,7 +406,7 @@ int upload_all(opf_handle* h) {
     TRY(upload(h, &f4, rw_ck0)); TRY(upload(h, &f5, rw_cidx));
     (k ? h->dfU : h->dfL) = DfDev{int(task.size()), nsn, a, b, cd.sn_first, cd.sn_w, bd.d_off, cd.ext_beg,
                                   cd.ext_end, c, d, int(leaf.size()), e, P.nx, int(ck_row.size()), nchunked,
-                                  f1, f2, f3, f4, f5};
+                                  f1, f2, f3, f4, f5, k};
     nck_max = std::max(nck_max, ck_row.size());
     nchunked_max = std::max(nchunked_max, size_t(nchunked));
   }

@@ -153,6 +153,9 @@ int trsm_cols_max_blocks();
 struct BlkDev {
   int nlev;
   const int *lvl_rptr, *rows, *row_sn, *sn_first, *sn_w, *d_off, *ext_beg, *ext_end;
+  // the factor's pattern is upper triangular: the diagonal-block inverses D_s
+  // are upper triangular (else lower), so row r of D_s is zero left (right) of r
+  int upper;
 };
 // inverse of every (split) supernode's diagonal block of one factor
 struct DiagInvJob {
@@ -187,6 +190,7 @@ struct DfDev {
   // short rows) and it counts its finished chunks in slot rw_cidx[r]
   int n, nchunks, nchunked;
   const int *ck_row, *ck_e0, *ck_e1, *rw_ck0, *rw_cidx;
+  int upper;   // as in BlkDev: which half of each D_s is zero
 };
 constexpr int DF_LEAF_W = 8;
 constexpr int DF_CHUNK = 24;

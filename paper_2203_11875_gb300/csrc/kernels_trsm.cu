@@ -719,19 +719,20 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
       if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
     }
     if (!group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
-    // B: X_r = D_s(r, :) Y_s
+    // B: X_r = D_s(r, :) Y_s over the nonzero half of the triangular D_s row
     for (int q = q0 + gw; q < q1; q += W) {
       const int r = S.rows[q], s = S.row_sn[q];
       const int f = S.sn_first[s], w = S.sn_w[s];
       const double* Dr = D + S.d_off[s] + (r - f) * w;
+      const int jb = S.upper ? r - f : 0, je = S.upper ? w : r - f + 1;
       double a0 = 0.0, a1 = 0.0;
-      int j = 0;
+      int j = jb;
       if (on) {
-        for (; j + 1 < w; j += 2) {
+        for (; j + 1 < je; j += 2) {
           a0 = fma(Dr[j], Y[(long long)(f + j) * ld + c], a0);
           a1 = fma(Dr[j + 1], Y[(long long)(f + j + 1) * ld + c], a1);
         }
-        if (j < w) a0 = fma(Dr[j], Y[(long long)(f + j) * ld + c], a0);
+        if (j < je) a0 = fma(Dr[j], Y[(long long)(f + j) * ld + c], a0);
         X[(long long)r * ld + c] = a0 + a1;
       }
     }
@@ -779,7 +780,8 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk1(BlkDev S, const int* 
         r = S.rows[q];
         const int s = S.row_sn[q], f = S.sn_first[s], w = S.sn_w[s];
         const double* Dr = D + S.d_off[s] + (r - f) * w;
-        for (int j = gl; j < w; j += G) a = fma(Dr[j], Y[(long long)(f + j) * xs], a);
+        const int jb = S.upper ? r - f : 0, je = S.upper ? w : r - f + 1;   // nonzero half of the row
+        for (int j = jb + gl; j < je; j += G) a = fma(Dr[j], Y[(long long)(f + j) * xs], a);
       }
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
@@ -1297,7 +1299,7 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
               double a = 0.0;
 #pragma unroll
               for (int j = 0; j < DF_INLINE_B; ++j)
-                if (j < w) a = fma(Ds[i * w + j], yv[j], a);
+                if (j < w && (S.upper ? j >= i : j <= i)) a = fma(Ds[i * w + j], yv[j], a);
               if (on) X[(long long)(f + i) * ld + c] = a;
             }
           }
@@ -1313,14 +1315,15 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_df(DfDev S, const int* __r
       if (!__shfl_sync(FULL, (int)ok, 0)) return;
       __syncwarp();
       const double* Dr = D + S.d_off[s] + (r - f) * w;
+      const int jb = S.upper ? r - f : 0, je = S.upper ? w : r - f + 1;   // nonzero half of the row
       double a0 = 0.0, a1 = 0.0;
       if (on) {
-        int j = 0;
-        for (; j + 1 < w; j += 2) {
+        int j = jb;
+        for (; j + 1 < je; j += 2) {
           a0 = fma(Dr[j], __ldcg(&Y[(long long)(f + j) * ld + c]), a0);
           a1 = fma(Dr[j + 1], __ldcg(&Y[(long long)(f + j + 1) * ld + c]), a1);
         }
-        if (j < w) a0 = fma(Dr[j], __ldcg(&Y[(long long)(f + j) * ld + c]), a0);
+        if (j < je) a0 = fma(Dr[j], __ldcg(&Y[(long long)(f + j) * ld + c]), a0);
         X[(long long)r * ld + c] = a0 + a1;
       }
       __syncwarp();
@@ -1353,7 +1356,7 @@ __global__ void __launch_bounds__(256) k_trsm_df_leaf(DfDev S, const double* __r
       double a = 0.0;
 #pragma unroll
       for (int j = 0; j < DF_LEAF_W; ++j)
-        if (j < w) a = fma(Ds[i * w + j], xr[j], a);
+        if (j < w && (S.upper ? j >= i : j <= i)) a = fma(Ds[i * w + j], xr[j], a);
       if (on) X[(long long)(f + i) * ld + c] = a;
     }
   }
