@@ -357,6 +357,31 @@ int opf_batch_autotune(opf_batch* b);
  * OPF_ERR_NO_CONVERGENCE). */
 int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm_result* results, double* wall_ms);
 
+/* One interior-point iteration's condensation and control-step factorisation
+ * (A5-A9: refactor G_x, S_x, K, H = K Z, Psi, Kred, Cholesky of Kred + delta_w I)
+ * for every instance of the batch at once, one kernel launch per phase over
+ * device work lists: the refactorisations are one cooperative launch over the
+ * merged row list (instance, row) in level order; the multi-RHS solves one
+ * launch of one CTA per (instance, 32-column block); the products one launch
+ * per shape with a block range per instance; the factorisations one launch of
+ * one thread-block cluster (8 CTAs) per instance.  Each instance must have been
+ * evaluated (opf_eval_derivatives with lam and y) at its point, and use the
+ * adjoint route.  sig_u[n], sig_x[n], sig_s[n] are host arrays of device
+ * pointers (each instance's Sigma, as in opf_condense); delta_w[n] a host array
+ * (NULL: 0 for all).  The launches wait for the work already on every
+ * instance's stream and every instance's later work waits for them; the call
+ * returns once the factorisations are done.  Outputs (host): status[n] per
+ * instance (OPF_OK, NOT_PD, SINGULAR, TIMEOUT) and, when fail_col is non-NULL,
+ * fail_col[n] (the first failing column of a NOT_PD instance, else -1).  Each
+ * handle is left as after opf_condense + opf_kkt_factor with its delta_w: its
+ * Kred, factor and opf_kkt_solve are available (after NOT_PD, opf_kkt_factor
+ * with a larger delta_w retries on that handle alone).  The first call builds
+ * the work lists.  Returns OPF_OK, or the first instance's failure code.
+ * Errors: INVALID_ARG (an instance not evaluated, on the explicit route, or a
+ * NULL pointer), CUDA, OOM. */
+int opf_batch_condense_factor(opf_batch* b, const double* const* sig_u, const double* const* sig_x,
+                              const double* const* sig_s, const double* delta_w, int* status, int* fail_col);
+
 /* ---- dense Cholesky without device allocation ----------------------------------- */
 /* The paper has no counterpart to this call.  It serves callers that cannot
  * allocate device memory where they need a factorisation -- a loop running under

@@ -95,6 +95,8 @@ _SIGS = {
     "opf_batch_autotune": (C.c_int, [C.c_void_p]),
     "opf_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result),
                                   C.POINTER(C.c_double)]),
+    "opf_batch_condense_factor": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                            C.POINTER(C.c_void_p), C.POINTER(C.c_double), _ip, _ip]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
     "opf_launch_count": (C.c_ulonglong, []),
     "opf_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
@@ -437,6 +439,22 @@ class Batch:
         if rc not in (OPF_OK, -8):
             raise OPFError(rc, "opf_batch_solve")
         return out, ms.value
+
+    def condense_factor(self, sig_u, sig_x, sig_s, delta_w=None):
+        """opf_batch_condense_factor: per-instance device tensors of Sigma (lists
+        of n tensors) and delta_w (n floats or None).  Returns (status list,
+        failing-column list)."""
+        n = self.n
+        if not (len(sig_u) == len(sig_x) == len(sig_s) == n):
+            raise ValueError(f"expected {n} tensors per Sigma block")
+        arr = [(C.c_void_p * n)(*[_ptr(t).value for t in blk]) for blk in (sig_u, sig_x, sig_s)]
+        dw = None if delta_w is None else (C.c_double * n)(*[float(v) for v in delta_w])
+        st = (C.c_int * n)()
+        fc = (C.c_int * n)()
+        rc = self._lib.opf_batch_condense_factor(self._b, arr[0], arr[1], arr[2], dw, st, fc)
+        if rc not in (OPF_OK, OPF_ERR_NOT_PD, OPF_ERR_SINGULAR, OPF_ERR_TIMEOUT):
+            raise OPFError(rc, "opf_batch_condense_factor")
+        return list(st), list(fc)
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

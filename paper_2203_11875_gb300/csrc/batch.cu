@@ -13,6 +13,14 @@
 // Before the timed solves, opf_batch_autotune picks each instance's multi-RHS
 // solve kernel with the GPU to itself (the choice is timed, and timings taken
 // while other instances run would be meaningless).
+//
+// opf_batch_condense_factor is the batched form of the per-iteration hot path:
+// the G_x refactorisation, both multi-RHS solves, K, H = K Z, Kred and the
+// Cholesky of every instance run as one launch per phase over device work
+// lists -- (instance, row) items in level order for the refactorisation,
+// (instance, 32-column block) items for the solves, one thread-block cluster
+// per instance for the Cholesky, and block ranges per instance for the
+// elementwise phases -- so that the uneven instances fill the GPU together.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +40,28 @@ struct opf_batch {
   std::vector<int> order;              // instances, largest first
   int nthreads = 1;
   int device = 0;
+  // batched condensation (built on its first call)
+  bool bc_ready = false;
+  cudaStream_t bs = nullptr;           // the batched launches' stream
+  std::vector<cudaEvent_t> ev;         // per instance: its stream's work so far
+  cudaEvent_t ev_done = nullptr;
+  condipm::BatchInst* dI = nullptr;    // device descriptors
+  condipm::BatchInst* hI = nullptr;    // pinned host copy
+  int2* lu_items = nullptr;            // (instance, row), level order
+  int n_lu_items = 0, lu_blocks = 1, lu_maxlen = 1;
+  int2* cbs = nullptr;                 // (instance, column block)
+  int ncbs = 0, nsn_max = 1;
+  int* boff[condipm::BOFF_KINDS] = {};
+  int nb[condipm::BOFF_KINDS] = {};
+  int* st_host = nullptr;              // pinned: ST_WORDS per instance
+  std::vector<void*> dev_allocs;
 };
+
+#define TRY_B(x)                   \
+  do {                             \
+    int r_ = (x);                  \
+    if (r_ != OPF_OK) return r_;   \
+  } while (0)
 
 namespace condipm {
 namespace {
@@ -86,11 +115,18 @@ extern "C" int opf_batch_create(opf_handle* const* handles, int n, int nthreads,
 
 extern "C" void opf_batch_destroy(opf_batch* b) {
   if (!b) return;
+  if (b->bs) cudaStreamSynchronize(b->bs);
   for (size_t i = 0; i < b->streams.size(); ++i) {
     cudaStreamSynchronize(b->streams[i]);
     if (i < b->prev.size()) b->hs[i]->s = b->prev[i];
     cudaStreamDestroy(b->streams[i]);
   }
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
+  if (b->bs) cudaStreamDestroy(b->bs);
+  for (void* p : b->dev_allocs) cudaFree(p);
+  if (b->hI) cudaFreeHost(b->hI);
+  if (b->st_host) cudaFreeHost(b->st_host);
   delete b;
 }
 
@@ -139,3 +175,207 @@ extern "C" int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm
     if (rcs[i] != OPF_OK) return rcs[i];
   return OPF_OK;
 }
+
+// ------------------------------------------------------------------ batched condensation
+namespace condipm {
+namespace {
+
+template <class T>
+int dev_upload(opf_batch* b, T** dst, const std::vector<T>& v) {
+  const size_t n = std::max<size_t>(1, v.size());
+  if (cudaMalloc((void**)dst, n * sizeof(T)) != cudaSuccess) return OPF_ERR_OOM;
+  b->dev_allocs.push_back(*dst);
+  if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return OPF_ERR_CUDA;
+  return OPF_OK;
+}
+
+// work lists and per-instance block ranges of the batched launches
+int batch_setup(opf_batch* b) {
+  const int n = int(b->hs.size());
+  for (opf_handle* h : b->hs)
+    if (h->opt.route != OPF_ROUTE_ADJOINT) return OPF_ERR_INVALID_ARG;
+  // refactorisation rows: level by level, instances in order within a level
+  std::vector<int2> items;
+  int maxlev = 0;
+  for (opf_handle* h : b->hs) {
+    maxlev = std::max(maxlev, h->P.fwd.nlev);
+    b->lu_maxlen = std::max(b->lu_maxlen, h->lu_maxlen);
+  }
+  for (int l = 0; l < maxlev; ++l)
+    for (int i = 0; i < n; ++i) {
+      const Levels& L = b->hs[i]->P.fwd;
+      if (l >= L.nlev) continue;
+      for (int q = L.ptr[l]; q < L.ptr[l + 1]; ++q) items.push_back(make_int2(i, L.rows[q]));
+    }
+  b->n_lu_items = int(items.size());
+  TRY_B(dev_upload(b, &b->lu_items, items));
+  const int mb = batch_lu_max_blocks(b->lu_maxlen);
+  if (mb < 1) return OPF_ERR_CUDA;
+  b->lu_blocks = std::max(1, std::min(mb, (b->n_lu_items + 7) / 8));
+  // solve items
+  std::vector<int2> cb;
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < (b->hs[i]->P.nu + 31) / 32; ++c) cb.push_back(make_int2(i, c));
+  b->ncbs = int(cb.size());
+  TRY_B(dev_upload(b, &b->cbs, cb));
+  // block ranges: each instance gets blocks in proportion to its elements of
+  // that launch shape (BATCH_EW_ITEMS per thread)
+  const long long per_block = (long long)BATCH_EW_THREADS * BATCH_EW_ITEMS;
+  for (int k = 0; k < BOFF_KINDS; ++k) {
+    std::vector<int> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      const opf_handle* h = b->hs[i];
+      const Plan& P = h->P;
+      long long work = 1;
+      switch (k) {
+        case BOFF_LU: work = std::max<long long>(32LL * P.nx, P.nw); break;
+        case BOFF_K: work = std::max<long long>(P.K.nnz(), P.G.nnz()); break;
+        case BOFF_X: work = std::max<long long>((long long)P.nx * h->ldp, P.LU.nnz()); break;
+        case BOFF_W: work = (long long)P.nw * P.nu; break;
+        case BOFF_U: work = (long long)P.nu * P.nu; break;
+        default:
+          work = std::max(std::max<long long>(P.Lo.nnz(), P.Up.nnz()),
+                          std::max(h->stLo.nslots, h->stUp.nslots));
+      }
+      const long long nbk = std::max(1LL, std::min(65536LL, (work + per_block - 1) / per_block));
+      off[i + 1] = off[i] + int(nbk);
+    }
+    b->nb[k] = off[n];
+    TRY_B(dev_upload(b, &b->boff[k], off));
+  }
+  for (opf_handle* h : b->hs)
+    b->nsn_max = std::max(b->nsn_max, int(std::max(h->P.csL.sn_first.size(), h->P.csU.sn_first.size())));
+  if (cudaMalloc(&b->dI, sizeof(BatchInst) * n) != cudaSuccess) return OPF_ERR_OOM;
+  b->dev_allocs.push_back(b->dI);
+  if (cudaMallocHost(&b->hI, sizeof(BatchInst) * n) != cudaSuccess) return OPF_ERR_OOM;
+  if (cudaMallocHost(&b->st_host, sizeof(int) * ST_WORDS * n) != cudaSuccess) return OPF_ERR_OOM;
+  if (cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess) return OPF_ERR_CUDA;
+  b->ev.resize(n, nullptr);
+  for (int i = 0; i < n; ++i)
+    if (cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) != cudaSuccess) return OPF_ERR_CUDA;
+  if (cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess) return OPF_ERR_CUDA;
+  b->bc_ready = true;
+  return OPF_OK;
+}
+
+BatchInst describe(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s, double delta_w) {
+  const Plan& P = h->P;
+  BatchInst B{};
+  B.nx = P.nx; B.nu = P.nu; B.nw = P.nw; B.m = P.m; B.ld = h->ldp;
+  B.nnzG = P.G.nnz(); B.nnzLU = P.LU.nnz(); B.nnzK = P.K.nnz(); B.nnzLo = P.Lo.nnz(); B.nnzUp = P.Up.nnz();
+  B.Gx_to_LU = h->Gx_to_LU; B.LU_rp = h->LU_rp; B.LU_ci = h->LU_ci; B.LU_diag = h->LU_diag;
+  B.upd_ptr = h->upd_ptr; B.upd_pos = h->upd_pos; B.Gval = h->Gval;
+  B.LUval = h->LUval; B.inv_diag = h->inv_diag; B.rmax = h->rmax; B.flags = h->flags; B.st = h->st;
+  B.maxlen = h->lu_maxlen;
+  B.Lo_map = h->Lo_map; B.Ut_map = h->Ut_map; B.Up_map = h->Up_map; B.Lt_map = h->Lt_map;
+  B.Lo_val = h->Lo_val; B.Ut_val = h->Ut_val; B.Up_val = h->Up_val; B.Lt_val = h->Lt_val;
+  for (int k = 0; k < 2; ++k) {
+    const opf_handle::StBuf& S = k ? h->stUp : h->stLo;
+    B.st_nslots[k] = S.nslots;
+    B.st_slot[k] = S.slot;
+    B.st_src[k] = S.src;
+    B.st_a[k] = reinterpret_cast<double*>(S.bytes_a);
+    B.st_b[k] = reinterpret_cast<double*>(S.bytes_b);
+  }
+  const int nl = int(P.csL.sn_first.size()), nuu = int(P.csU.sn_first.size());
+  const ColDev& L = h->csL;
+  const ColDev& U = h->csU;
+  B.dj[0] = DiagInvJob{nl, 0, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Lo_val, nullptr, h->D_L};
+  B.dj[1] = DiagInvJob{nl, 0, L.sn_first, L.sn_w, h->bkL.d_off, L.int_beg, h->Ut_val, h->inv_diag, h->D_Ut};
+  B.dj[2] = DiagInvJob{nuu, 1, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Up_val, h->inv_diag, h->D_U};
+  B.dj[3] = DiagInvJob{nuu, 1, U.sn_first, U.sn_w, h->bkU.d_off, U.int_beg, h->Lt_val, nullptr, h->D_Lt};
+  B.Wval = h->Wval; B.Aval = h->Aval;
+  B.KAA_ptr = h->KAA_ptr; B.KAA_r = h->KAA_r; B.KAA_a = h->KAA_a; B.KAA_b = h->KAA_b;
+  B.K_diag = h->K_diag; B.perm = h->perm; B.K_rp = h->K_rp; B.K_ci = h->K_ci;
+  B.sig_u = sig_u; B.sig_x = sig_x; B.sig_s_in = sig_s;
+  B.sig_s = h->sig_s; B.sig_c = h->sig_c; B.Kval = h->Kval;
+  B.Zt = h->Zt; B.H = h->H; B.Y = h->ybuf;
+  B.PGu_rp = h->PGu_rp; B.PGu_ci = h->PGu_ci; B.PGu_map = h->PGu_map;
+  B.GuT_rp = h->GuT_rp; B.GuT_ci = h->GuT_ci; B.GuT_map = h->GuT_map;
+  B.bkL = h->bkL; B.bkU = h->bkU; B.Lo_ci = h->Lo_ci; B.Up_ci = h->Up_ci;
+  B.D_L = h->D_L; B.D_Ut = h->D_Ut; B.D_U = h->D_U; B.D_Lt = h->D_Lt;
+  B.Kred = h->Kred; B.F = h->F; B.Fdinv = h->Fdinv;
+  B.delta_w = delta_w;
+  return B;
+}
+
+}  // namespace
+}  // namespace condipm
+
+extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_u, const double* const* sig_x,
+                                         const double* const* sig_s, const double* delta_w, int* status,
+                                         int* fail_col) {
+  if (!b || !sig_u || !sig_x || !sig_s || !status) return OPF_ERR_INVALID_ARG;
+  const int n = int(b->hs.size());
+  for (int i = 0; i < n; ++i) {
+    const opf_handle* h = b->hs[i];
+    if (!h->have_W || !sig_u[i] || !sig_x[i] || !sig_s[i] || (delta_w && !(delta_w[i] >= 0.0)))
+      return OPF_ERR_INVALID_ARG;
+    if ((size_t)h->P.nx * h->ldp > h->ybuf_cap) return OPF_ERR_INVALID_ARG;
+  }
+  if (!b->bc_ready) {
+    const int rc = batch_setup(b);
+    if (rc != OPF_OK) return rc;
+  }
+  for (int i = 0; i < n; ++i)
+    b->hI[i] = describe(b->hs[i], sig_u[i], sig_x[i], sig_s[i], delta_w ? delta_w[i] : 0.0);
+  // the batched launches follow every instance's work so far (its derivatives)
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventRecord(b->ev[i], b->hs[i]->s) != cudaSuccess) return OPF_ERR_CUDA;
+    if (cudaStreamWaitEvent(b->bs, b->ev[i], 0) != cudaSuccess) return OPF_ERR_CUDA;
+  }
+  cudaStream_t s = b->bs;
+  if (cudaMemcpyAsync(b->dI, b->hI, sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return OPF_ERR_CUDA;
+  const long long spin = b->hs[0]->spin_limit;
+  cudaError_t e = launch_batch_prologue(s, b->dI, n, b->boff, b->nb);
+  if (e == cudaSuccess) e = launch_batch_lu(s, b->dI, b->lu_items, b->n_lu_items, b->lu_blocks, b->lu_maxlen, 1u, spin);
+  if (e == cudaSuccess) e = launch_batch_factor_post(s, b->dI, n, b->boff[BOFF_F], b->nb[BOFF_F], b->nsn_max);
+  if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0);
+  if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_W], b->nb[BOFF_W], 0);
+  if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 1);
+  if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U], 1);
+  if (e == cudaSuccess) e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+  if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, 8);
+  for (int i = 0; i < n && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(b->st_host + ST_WORDS * i, b->hs[i]->st, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    note_cuda_error(e);
+    return OPF_ERR_CUDA;
+  }
+  int first = OPF_OK;
+  for (int i = 0; i < n; ++i) {
+    opf_handle* h = b->hs[i];
+    const int* st = b->st_host + ST_WORDS * i;
+    int rc = OPF_OK;
+    if (st[ST_TIMEOUT]) rc = OPF_ERR_TIMEOUT;
+    else if (st[ST_CODE] == DEV_NOT_PD) rc = OPF_ERR_NOT_PD;
+    else if (st[ST_CODE] == DEV_SINGULAR) rc = OPF_ERR_SINGULAR;
+    else if (st[ST_CODE] != 0) rc = OPF_ERR_CUDA;
+    status[i] = rc;
+    if (fail_col) fail_col[i] = rc == OPF_ERR_NOT_PD ? st[ST_INFO] : -1;
+    // the handle is left as after opf_condense + opf_kkt_factor
+    h->epoch = 1;
+    h->have_lu = rc == OPF_OK || rc == OPF_ERR_NOT_PD;
+    h->have_condense = h->have_lu;
+    h->psi_valid = h->have_lu;
+    h->have_factor = rc == OPF_OK;
+    h->delta_w = delta_w ? delta_w[i] : 0.0;
+    h->delta_c = 0.0;
+    h->finv_valid = false;
+    h->sens_ready = false;
+    if (rc != OPF_OK) {
+      cudaMemsetAsync(h->st, 0, sizeof(int) * ST_WORDS, s);
+      cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, s);
+      if (first == OPF_OK) first = rc;
+    }
+  }
+  // later work on each instance's stream follows the batched launches
+  if (cudaEventRecord(b->ev_done, s) != cudaSuccess) return OPF_ERR_CUDA;
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamWaitEvent(b->hs[i]->s, b->ev_done, 0) != cudaSuccess) return OPF_ERR_CUDA;
+  return first;
+}
+

@@ -289,4 +289,88 @@ cudaError_t launch_absmax(cudaStream_t s, long long n, const double* x, double* 
 cudaError_t launch_fill(cudaStream_t s, long long n, double v, double* x);
 cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld);
 
+// ----------------------------------------------------------------- batches
+// One instance of a batched condensation (opf_batch_condense_factor): the device
+// arrays of its handle that the batched phase kernels read and write.  A device
+// array of these, one per instance, is what every batched launch indexes.
+struct BatchInst {
+  int nx, nu, nw, m, ld;
+  long long nnzG, nnzLU, nnzK, nnzLo, nnzUp;
+  // G_x refactorisation
+  const int *Gx_to_LU, *LU_rp, *LU_ci, *LU_diag;
+  const long long* upd_ptr;
+  const int* upd_pos;
+  const double* Gval;
+  double *LUval, *inv_diag, *rmax;
+  unsigned* flags;
+  int* st;
+  int maxlen;
+  const int *Lo_map, *Ut_map, *Up_map, *Lt_map;
+  double *Lo_val, *Ut_val, *Up_val, *Lt_val;
+  // staged-solve byte streams of the lower (0) and upper (1) patterns
+  long long st_nslots[2];
+  const long long* st_slot[2];
+  const int* st_src[2];
+  double *st_a[2], *st_b[2];
+  DiagInvJob dj[4];
+  // K = W + A^T Sigma_s A + diag(Sigma_w)
+  const double *Wval, *Aval;
+  const int *KAA_ptr, *KAA_r, *KAA_a, *KAA_b, *K_diag, *perm, *K_rp, *K_ci;
+  const double *sig_u, *sig_x, *sig_s_in;
+  double *sig_s, *sig_c, *Kval;
+  // Z = [I; S_x], H = K Z, Psi, Kred
+  double *Zt, *H, *Y;
+  const int *PGu_rp, *PGu_ci, *PGu_map, *GuT_rp, *GuT_ci, *GuT_map;
+  BlkDev bkL, bkU;
+  const int *Lo_ci, *Up_ci;
+  const double *D_L, *D_Ut, *D_U, *D_Lt;
+  // Cholesky of Kred + delta_w I
+  double *Kred, *F, *Fdinv;
+  double delta_w;
+};
+
+// Work of one batched elementwise launch: block b of the launch belongs to the
+// instance i with boff[i] <= b < boff[i + 1] (boff[n] = grid size).
+__device__ __forceinline__ int batch_instance(const int* __restrict__ boff, int n, int b) {
+  int lo = 0, hi = n;   // boff[lo] <= b < boff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (boff[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Batched phase launches (one launch for every instance of the batch; I is the
+// device descriptor array, n instances).  Block offsets boff per launch shape:
+// BOFF_LU (nnz(LU) and nnz(G) elements), BOFF_K (nnz(K)), BOFF_X (nx rows of Z),
+// BOFF_W (nw rows of H), BOFF_U (nu rows of Kred), BOFF_F (factor entries
+// nnz(Lo) + nnz(Up) and staged slots).
+enum { BOFF_LU = 0, BOFF_K = 1, BOFF_X = 2, BOFF_W = 3, BOFF_U = 4, BOFF_F = 5, BOFF_KINDS = 6 };
+constexpr int BATCH_EW_THREADS = 256;
+constexpr int BATCH_EW_ITEMS = 4;   // elements (rows) per thread and launch of an elementwise phase
+// A5 prologue: zero LU, the row flags, the status word and S_x; then scatter
+// G_x into LU, -P G_u into S_x, assemble K and copy Sigma_s; then the row
+// maxima of LU and diag(Sigma_w) into K
+cudaError_t launch_batch_prologue(cudaStream_t s, const BatchInst* I, int n, const int* const* boff,
+                                  const int* nblocks);
+// A5: the numeric LU of every instance, one cooperative launch over the merged
+// row list items (instance, row) in level order
+cudaError_t launch_batch_lu(cudaStream_t s, const BatchInst* I, const int2* items, int nitems, int nblocks,
+                            int maxlen, unsigned epoch, long long spin_limit);
+int batch_lu_max_blocks(int maxlen);
+// A5 epilogue: the four factors' gathers and staged streams, then their
+// diagonal-block inverses
+cudaError_t launch_batch_factor_post(cudaStream_t s, const BatchInst* I, int n, const int* boffF, int nbF,
+                                     int nsn_max);
+// A6: S_x (trans = 0: L then U) or Psi = G_x^{-T} H_x (trans = 1: U^T then L^T)
+// for every instance, one CTA per (instance, 32-column block) item
+cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans);
+// A7: H = K Z (which = 0), then H_u -= G_u^T Psi (which = 1)
+cudaError_t launch_batch_spmm(cudaStream_t s, const BatchInst* I, int n, const int* boff, int nblocks, int which);
+// A7 / A9: Kred = sym(H_u) and F = tril(Kred) + delta_w I
+cudaError_t launch_batch_kred(cudaStream_t s, const BatchInst* I, int n, const int* boffU, int nblocks);
+// A9: Cholesky of every instance's F, one thread-block cluster of cl CTAs per instance
+cudaError_t launch_batch_chol(cudaStream_t s, const BatchInst* I, int n, int cl);
+
 }  // namespace condipm

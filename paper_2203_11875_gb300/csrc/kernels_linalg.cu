@@ -6,11 +6,15 @@
 // and leave data movement to the load/store pipes.
 #include "common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
 namespace condipm {
 namespace {
+
+namespace cg = cooperative_groups;
 
 inline int nblk(long long n, int t) { return int((n + t - 1) / t); }
 
@@ -214,6 +218,73 @@ __global__ void k_row_absmax(int n, const int* __restrict__ rp, const double* __
 // overlap instead of meeting at grid-wide barriers.  The row being factored is
 // staged in shared memory; rows of other warps are read through L2 (ld.cg).
 // Row i: for k in L(i) ascending: l_ik = w_k / u_kk; w_j -= l_ik u_kj (j in U(k)).
+// One row i of the up-looking LU, factored by the calling warp into its
+// shared-memory row buffer w (the body of k_lu_refactor and of the batched
+// refactorisation).  Returns false when a bounded wait expired.
+__device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const int* __restrict__ ci,
+                                       const int* __restrict__ diag, const long long* __restrict__ upd_ptr,
+                                       const int* __restrict__ upd_pos, double* LU, double* inv_diag,
+                                       const double* __restrict__ rmax, unsigned* flags, unsigned epoch, int* st,
+                                       long long spin_limit, double* w, int lane) {
+  volatile int* vst = st;
+  const int r0 = rp[i], r1 = rp[i + 1], dpos = diag[i];
+  for (int j = r0 + lane; j < r1; j += 32) w[j - r0] = __ldcg(&LU[j]);
+  __syncwarp();
+  for (int q = r0; q < dpos; ++q) {
+    const int k = ci[q];
+    // the structure of row k's update needs no wait: fetch it first, so that
+    // after the flag only the values cost a round trip
+    const int ub = diag[k] + 1, ue = rp[k + 1];
+    const long long base = upd_ptr[q];
+    const int j0 = ub + lane;
+    const int pos0 = j0 < ue ? upd_pos[base + lane] - r0 : 0;
+    int expired = 0;
+    if (lane == 0) {
+      // acquire load: row k's values and inverse pivot are visible once the
+      // flag is (its writer fences before publishing the flag)
+      long long it = 0;
+      unsigned f;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
+      unsigned ns = 32;
+      while (f != epoch) {
+        if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); expired = 1; break; }
+        // another warp's expired wait ends this one too (its row never comes)
+        if ((it & 1023) == 0 && vst[ST_TIMEOUT]) { expired = 1; break; }
+        __nanosleep(ns);   // back off, leaving issue slots to working warps
+        ns = ns < 128 ? 2 * ns : 128;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
+      }
+    }
+    if (__shfl_sync(0xffffffffu, expired, 0)) return false;
+    __syncwarp();   // orders lane 0's acquire before every lane's loads of row k
+    const double dk = __ldcg(&inv_diag[k]);
+    const double u0 = j0 < ue ? __ldcg(&LU[j0]) : 0.0;
+    const double lik = w[q - r0] * dk;
+    __syncwarp();
+    if (j0 < ue) w[pos0] = fma(-lik, u0, w[pos0]);
+    for (int j = j0 + 32; j < ue; j += 32) {
+      const int pos = upd_pos[base + (j - ub)] - r0;
+      w[pos] = fma(-lik, __ldcg(&LU[j]), w[pos]);
+    }
+    if (lane == 0) w[q - r0] = lik;
+    __syncwarp();
+  }
+  for (int j = r0 + lane; j < r1; j += 32) LU[j] = w[j - r0];
+  __syncwarp();
+  if (lane == 0) {
+    const double u = w[dpos - r0];
+    double inv = 0.0;
+    if (!(fabs(u) > 1e-14 * rmax[i]) || !isfinite(u)) set_status(st, DEV_SINGULAR, i);
+    else inv = 1.0 / u;
+    inv_diag[i] = inv;
+    // release: the row's values (ordered before lane 0 by __syncwarp) and its
+    // inverse pivot are visible to whoever acquires the flag
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + i), "r"(epoch) : "memory");
+  }
+  __syncwarp();
+  return true;
+}
+
 __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __restrict__ rp,
                               const int* __restrict__ ci, const int* __restrict__ diag,
                               const long long* __restrict__ upd_ptr, const int* __restrict__ upd_pos,
@@ -226,64 +297,30 @@ __global__ void k_lu_refactor(int n, const int* __restrict__ rows, const int* __
   double* w = wsh + (size_t)wib * maxlen;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  volatile int* vst = st;
-  for (int t = warp; t < n; t += nwarps) {
-    const int i = rows[t];
-    const int r0 = rp[i], r1 = rp[i + 1], dpos = diag[i];
-    for (int j = r0 + lane; j < r1; j += 32) w[j - r0] = __ldcg(&LU[j]);
-    __syncwarp();
-    for (int q = r0; q < dpos; ++q) {
-      const int k = ci[q];
-      // the structure of row k's update needs no wait: fetch it first, so that
-      // after the flag only the values cost a round trip
-      const int ub = diag[k] + 1, ue = rp[k + 1];
-      const long long base = upd_ptr[q];
-      const int j0 = ub + lane;
-      const int pos0 = j0 < ue ? upd_pos[base + lane] - r0 : 0;
-      int expired = 0;
-      if (lane == 0) {
-        // acquire load: row k's values and inverse pivot are visible once the
-        // flag is (its writer fences before publishing the flag)
-        long long it = 0;
-        unsigned f;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
-        unsigned ns = 32;
-        while (f != epoch) {
-          if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); expired = 1; break; }
-          // another warp's expired wait ends this one too (its row never comes)
-          if ((it & 1023) == 0 && vst[ST_TIMEOUT]) { expired = 1; break; }
-          __nanosleep(ns);   // back off, leaving issue slots to working warps
-          ns = ns < 128 ? 2 * ns : 128;
-          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
-        }
-      }
-      if (__shfl_sync(0xffffffffu, expired, 0)) return;
-      __syncwarp();   // orders lane 0's acquire before every lane's loads of row k
-      const double dk = __ldcg(&inv_diag[k]);
-      const double u0 = j0 < ue ? __ldcg(&LU[j0]) : 0.0;
-      const double lik = w[q - r0] * dk;
-      __syncwarp();
-      if (j0 < ue) w[pos0] = fma(-lik, u0, w[pos0]);
-      for (int j = j0 + 32; j < ue; j += 32) {
-        const int pos = upd_pos[base + (j - ub)] - r0;
-        w[pos] = fma(-lik, __ldcg(&LU[j]), w[pos]);
-      }
-      if (lane == 0) w[q - r0] = lik;
-      __syncwarp();
-    }
-    for (int j = r0 + lane; j < r1; j += 32) LU[j] = w[j - r0];
-    __syncwarp();
-    if (lane == 0) {
-      const double u = w[dpos - r0];
-      double inv = 0.0;
-      if (!(fabs(u) > 1e-14 * rmax[i]) || !isfinite(u)) set_status(st, DEV_SINGULAR, i);
-      else inv = 1.0 / u;
-      inv_diag[i] = inv;
-      // release: the row's values (ordered before lane 0 by __syncwarp) and its
-      // inverse pivot are visible to whoever acquires the flag
-      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + i), "r"(epoch) : "memory");
-    }
-    __syncwarp();
+  for (int t = warp; t < n; t += nwarps)
+    if (!lu_row(rows[t], rp, ci, diag, upd_ptr, upd_pos, LU, inv_diag, rmax, flags, epoch, st, spin_limit, w, lane))
+      return;
+}
+
+// The refactorisation of every instance of a batch in one cooperative launch:
+// the warps take the merged row list (instance, row), ordered by level and,
+// within a level, by instance; each instance's rows keep their level order, so
+// the oldest unfinished item can always proceed and every bounded wait is on
+// an item earlier in the list.
+__global__ void k_b_lu(const BatchInst* __restrict__ I, const int2* __restrict__ items, int nitems, unsigned epoch,
+                       long long spin_limit, int maxlen) {
+  extern __shared__ double wsh[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  double* w = wsh + (size_t)wib * maxlen;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < nitems; t += nwarps) {
+    const int2 it = items[t];
+    const BatchInst& B = I[it.x];
+    if (!lu_row(it.y, B.LU_rp, B.LU_ci, B.LU_diag, B.upd_ptr, B.upd_pos, B.LUval, B.inv_diag, B.rmax, B.flags,
+                epoch, B.st, spin_limit, w, lane))
+      return;
   }
 }
 
@@ -291,6 +328,120 @@ __global__ void k_gather_map(long long n, const int* __restrict__ map, const dou
                              double* __restrict__ dst) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q < n) dst[q] = src[map[q]];
+}
+
+// ----------------------------------------------------------------- batched phases
+// Elementwise work of one instance inside a batched launch: the blocks
+// boff[i] .. boff[i + 1] of the grid serve instance i; lt is this thread's
+// index within them and ls their thread count.
+struct BatchSlice {
+  const BatchInst* B;
+  long long lt, ls;
+};
+__device__ __forceinline__ BatchSlice batch_slice(const BatchInst* I, const int* __restrict__ boff, int n) {
+  const int i = batch_instance(boff, n, blockIdx.x);
+  BatchSlice sl;
+  sl.B = I + i;
+  sl.lt = (long long)(blockIdx.x - boff[i]) * blockDim.x + threadIdx.x;
+  sl.ls = (long long)(boff[i + 1] - boff[i]) * blockDim.x;
+  return sl;
+}
+
+// zero LU, the row flags, the status word and S_x (the x rows of Z)
+__global__ void k_b_clear(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
+  const BatchSlice sl = batch_slice(I, boff, n);
+  const BatchInst& B = *sl.B;
+  for (long long e = sl.lt; e < B.nnzLU; e += sl.ls) B.LUval[e] = 0.0;
+  for (long long e = sl.lt; e < B.nx; e += sl.ls) B.flags[e] = 0u;
+  if (sl.lt < ST_WORDS) B.st[sl.lt] = 0;
+  double* Sx = B.Zt + (size_t)B.nu * B.ld;
+  const long long nsx = (long long)B.nx * B.ld;
+  for (long long e = sl.lt; e < nsx; e += sl.ls) Sx[e] = 0.0;
+}
+
+// G_x into LU; -P G_u into S_x; K = W + A^T Sigma_s A; the handle's copy of Sigma_s
+__global__ void k_b_scatter(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
+  const BatchSlice sl = batch_slice(I, boff, n);
+  const BatchInst& B = *sl.B;
+  for (long long q = sl.lt; q < B.nnzG; q += sl.ls) {
+    const int p = B.Gx_to_LU[q];
+    if (p >= 0) B.LUval[p] = B.Gval[q];
+  }
+  double* Sx = B.Zt + (size_t)B.nu * B.ld;
+  for (long long r = sl.lt; r < B.nx; r += sl.ls)
+    for (int q = B.PGu_rp[r]; q < B.PGu_rp[r + 1]; ++q)
+      Sx[r * B.ld + B.PGu_ci[q]] = -1.0 * B.Gval[B.PGu_map[q]];
+  for (long long p = sl.lt; p < B.nnzK; p += sl.ls) {
+    double acc = B.Wval[p];
+    for (int q = B.KAA_ptr[p]; q < B.KAA_ptr[p + 1]; ++q)
+      acc = fma(B.sig_s_in[B.KAA_r[q]] * B.Aval[B.KAA_a[q]], B.Aval[B.KAA_b[q]], acc);
+    B.Kval[p] = acc;
+  }
+  for (long long i = sl.lt; i < B.m; i += sl.ls) B.sig_s[i] = B.sig_s_in[i];
+}
+
+// row maxima of LU (one warp per row, on the bit patterns as k_row_absmax) and
+// diag(Sigma_w) into K
+__global__ void k_b_rowmax(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
+  const BatchSlice sl = batch_slice(I, boff, n);
+  const BatchInst& B = *sl.B;
+  const int lane = threadIdx.x & 31;
+  for (long long i = sl.lt >> 5; i < B.nx; i += sl.ls >> 5) {
+    unsigned long long mx = 0;
+    for (int q = B.LU_rp[i] + lane; q < B.LU_rp[i + 1]; q += 32) {
+      unsigned long long b = (unsigned long long)__double_as_longlong(B.LUval[q]) & 0x7FFFFFFFFFFFFFFFULL;
+      if (b > 0x7FF0000000000000ULL) b = 0;   // NaN
+      mx = b > mx ? b : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = u > mx ? u : mx;
+    }
+    if (lane == 0) B.rmax[i] = __longlong_as_double((long long)mx);
+  }
+  for (long long c = sl.lt; c < B.nw; c += sl.ls) {
+    const double sg = c < B.nu ? B.sig_u[c] : B.sig_x[B.perm[c - B.nu]];
+    B.Kval[B.K_diag[c]] += sg;
+    B.sig_c[c] = sg;
+  }
+}
+
+// which = 0: H = K Z (nw rows); which = 1: H_u -= G_u^T Psi, Psi in H's x rows
+__global__ void k_b_spmm(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff, int which) {
+  const BatchSlice sl = batch_slice(I, boff, n);
+  const BatchInst& B = *sl.B;
+  const long long ld = B.ld;
+  const int nu = B.nu;
+  const long long total = (long long)(which == 0 ? B.nw : nu) * nu;
+  for (long long e = sl.lt; e < total; e += sl.ls) {
+    const int r = int(e / nu), c = int(e % nu);
+    double acc = 0.0;
+    if (which == 0) {
+      for (int q = B.K_rp[r]; q < B.K_rp[r + 1]; ++q) acc = fma(B.Kval[q], B.Zt[B.K_ci[q] * ld + c], acc);
+      B.H[r * ld + c] = acc;
+    } else {
+      const double* Hx = B.H + (size_t)nu * ld;
+      for (int q = B.GuT_rp[r]; q < B.GuT_rp[r + 1]; ++q)
+        acc = fma(B.Gval[B.GuT_map[q]], Hx[B.GuT_ci[q] * ld + c], acc);
+      double* y = B.H + r * ld + c;
+      *y = fma(-1.0, acc, *y);
+    }
+  }
+}
+
+// Kred = (H_u + H_u^T) / 2 and F = its lower triangle + delta_w I
+__global__ void k_b_kred(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
+  const BatchSlice sl = batch_slice(I, boff, n);
+  const BatchInst& B = *sl.B;
+  const int nu = B.nu;
+  const long long ld = B.ld;
+  for (long long e = sl.lt; e < (long long)nu * nu; e += sl.ls) {
+    const int i = int(e / nu), j = int(e % nu);
+    const double v = 0.5 * (B.H[i * ld + j] + B.H[j * ld + i]);
+    B.Kred[e] = v;
+    B.F[e] = j > i ? 0.0 : (i == j ? v + B.delta_w : v);
+  }
 }
 
 // ----------------------------------------------------------------- Cholesky
@@ -450,15 +601,18 @@ __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const u
 //   U. the trailing update A_ij -= L_ik L_jk^T in 16x16 sub-tiles.
 // A non-positive or non-finite pivot records DEV_NOT_PD with its column.  The
 // inverse diagonal of L is written to dinv (used by the solves).
-__global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out, int* st, unsigned* bar,
-                                              long long spin_limit) {
+// The barrier form's body, for a group of nbk CTAs (this one is rank) that
+// sync() brings together: the whole grid of k_chol, or one thread-block
+// cluster per instance in the batched factorisation.
+template <class Sync>
+__device__ __forceinline__ void chol_run(double* F, int n, double* dinv_out, int* st, int rank, unsigned nbk,
+                                         Sync&& sync) {
   __shared__ double Ta[CNB][CNB + 1];
   __shared__ double Tb[CNB][CNB + 1];
   __shared__ double dv[CNB];
   __shared__ unsigned short pairs[CNB * (CNB + 1) / 2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int nt = (n + CNB - 1) / CNB;
-  const unsigned nbk = gridDim.x;
   volatile int* vst = st;
   fill_pairs(pairs);
   __syncthreads();
@@ -467,7 +621,7 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
     const int r0 = k0 + kb, nrows = n - r0;              // panel rows r0 .. n-1
     const int row_blocks = (nrows + nwarps - 1) / nwarps;
     // ---- phase P
-    if ((int)blockIdx.x == 0 || (int)blockIdx.x < row_blocks) {
+    if (rank == 0 || rank < row_blocks) {
       for (int t = tid; t < CNB * CNB; t += blockDim.x) {
         const int i = t / CNB, j = t % CNB;
         Ta[i][j] = (i < kb && j <= i) ? F[(size_t)(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
@@ -477,13 +631,13 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
       if (fail >= 0) {
         if (tid == 0) set_status(st, DEV_NOT_PD, k0 + fail);
       } else {
-        if (blockIdx.x == 0) {
+        if (rank == 0) {
           // the factored tile goes back to F after the barrier: the other panel
           // CTAs may still be reading the unfactored one now
           for (int t = tid; t < CNB * CNB; t += blockDim.x) Tb[t / CNB][t % CNB] = Ta[t / CNB][t % CNB];
           if (tid < kb) dinv_out[k0 + tid] = dv[tid];
         }
-        for (int rb = blockIdx.x; rb < row_blocks; rb += nbk) {
+        for (int rb = rank; rb < row_blocks; rb += nbk) {
           const int r = r0 + rb * nwarps + warp;
           if (r < n) {
             double a = lane < kb ? F[(size_t)r * n + k0 + lane] : 0.0;
@@ -497,9 +651,9 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
         }
       }
     }
-    if (!grid_barrier(bar, nbk, spin_limit, st)) return;
+    if (!sync()) return;
     if (vst[ST_CODE] != 0) return;
-    if (blockIdx.x == 0) {
+    if (rank == 0) {
       write_tile_back(F, n, Tb, k);
       __syncthreads();   // Tb is reused by the update below
     }
@@ -509,7 +663,7 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
       // ---- phase U, few tiles left: 16x16 sub-tiles (four per tile) for more
       // work items than CTAs
       const long long nsub = ntile * 4;
-      for (long long tt = blockIdx.x; tt < nsub; tt += nbk) {
+      for (long long tt = rank; tt < nsub; tt += nbk) {
         const long long tile = tt >> 2;
         const int sub = int(tt & 3);
         int ii = int((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
@@ -561,7 +715,7 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
           pb[q] = (j0 + rr < n && l < kb) ? F[(size_t)(j0 + rr) * n + k0 + l] : 0.0;
         }
       };
-      long long tt = blockIdx.x;
+      long long tt = rank;
       if (tt < ntile) fetch(tt);
       for (; tt < ntile; tt += nbk) {
   #pragma unroll
@@ -592,8 +746,27 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
         __syncthreads();
       }
     }
-    if (!grid_barrier(bar, nbk, spin_limit, st)) return;
+    if (!sync()) return;
   }
+}
+
+
+__global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out, int* st, unsigned* bar,
+                                              long long spin_limit) {
+  chol_run(F, n, dinv_out, st, (int)blockIdx.x, gridDim.x,
+           [&]() { return grid_barrier(bar, gridDim.x, spin_limit, st); });
+}
+
+// The Cholesky of every instance of a batch in one launch: one thread-block
+// cluster per instance (its CTAs are co-scheduled by the hardware, so the
+// cluster barrier between the panel and update phases always completes).
+__global__ void __launch_bounds__(256) k_b_chol(const BatchInst* __restrict__ I) {
+  cg::cluster_group cl = cg::this_cluster();
+  const BatchInst& B = I[blockIdx.x / cl.num_blocks()];
+  chol_run(B.F, B.nu, B.Fdinv, B.st, (int)cl.block_rank(), cl.num_blocks(), [&]() {
+    cl.sync();
+    return true;
+  });
 }
 
 // Solve L L^T X = B for the columns of X (row-major n x nrhs); one CTA per column.
@@ -1280,3 +1453,70 @@ cudaError_t launch_chol_solve_cl(cudaStream_t s, int n, const double* F, const d
 }
 
 }  // namespace condipm
+
+namespace condipm {
+
+cudaError_t launch_batch_prologue(cudaStream_t s, const BatchInst* I, int n, const int* const* boff,
+                                  const int* nblocks) {
+  if (n <= 0) return cudaSuccess;
+  k_b_clear<<<nblocks[BOFF_X], BATCH_EW_THREADS, 0, s>>>(I, n, boff[BOFF_X]);
+  note_launch();
+  k_b_scatter<<<nblocks[BOFF_K], BATCH_EW_THREADS, 0, s>>>(I, n, boff[BOFF_K]);
+  note_launch();
+  k_b_rowmax<<<nblocks[BOFF_LU], BATCH_EW_THREADS, 0, s>>>(I, n, boff[BOFF_LU]);
+  note_launch();
+  return cudaGetLastError();
+}
+
+int batch_lu_max_blocks(int maxlen) {
+  const size_t smem = (size_t)(256 / 32) * maxlen * sizeof(double);
+  if (smem > 48 * 1024 && allow_max_smem((const void*)k_b_lu) != cudaSuccess) return 0;
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_lu, 256, smem);
+  return device_sms() * per;
+}
+
+// cooperative: every warp of the grid is resident, which the flag waits rely on
+cudaError_t launch_batch_lu(cudaStream_t s, const BatchInst* I, const int2* items, int nitems, int nblocks,
+                            int maxlen, unsigned epoch, long long spin_limit) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(256 / 32) * maxlen * sizeof(double);
+  void* args[] = {(void*)&I, (void*)&items, (void*)&nitems, (void*)&epoch, (void*)&spin_limit, (void*)&maxlen};
+  note_launch();
+  return cudaLaunchCooperativeKernel((void*)k_b_lu, dim3(nblocks), dim3(256), args, smem, s);
+}
+
+cudaError_t launch_batch_spmm(cudaStream_t s, const BatchInst* I, int n, const int* boff, int nblocks, int which) {
+  if (n <= 0) return cudaSuccess;
+  k_b_spmm<<<nblocks, BATCH_EW_THREADS, 0, s>>>(I, n, boff, which);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_kred(cudaStream_t s, const BatchInst* I, int n, const int* boffU, int nblocks) {
+  if (n <= 0) return cudaSuccess;
+  k_b_kred<<<nblocks, BATCH_EW_THREADS, 0, s>>>(I, n, boffU);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_chol(cudaStream_t s, const BatchInst* I, int n, int cl) {
+  if (n <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(n * cl);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, k_b_chol, I);
+}
+
+}  // namespace condipm
+

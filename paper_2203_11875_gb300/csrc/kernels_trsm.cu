@@ -672,18 +672,71 @@ __global__ void k_diag_inv4(DiagInvJob j0, DiagInvJob j1, DiagInvJob j2, DiagInv
   else diag_inv_one<false>(Ts, s, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
 }
 
-__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
-                                                          const double* __restrict__ val,
-                                                          const double* __restrict__ D, double* X, double* Y,
-                                                          long long ld, int ncols, int ksplit, unsigned* bar,
-                                                          int* st, long long spin_limit) {
-  const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
+// The factor epilogue of every instance of a batch: the gathers of L, U^T, U,
+// L^T out of LU and the staged-solve byte streams (read through the same maps)
+__global__ void k_b_gather(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
+  const int i = batch_instance(boff, n, blockIdx.x);
+  const BatchInst& B = I[i];
+  const long long lt = (long long)(blockIdx.x - boff[i]) * blockDim.x + threadIdx.x;
+  const long long ls = (long long)(boff[i + 1] - boff[i]) * blockDim.x;
+  for (long long q = lt; q < B.nnzLo; q += ls) {
+    B.Lo_val[q] = B.LUval[B.Lo_map[q]];
+    B.Ut_val[q] = B.LUval[B.Ut_map[q]];
+  }
+  for (long long q = lt; q < B.nnzUp; q += ls) {
+    B.Up_val[q] = B.LUval[B.Up_map[q]];
+    B.Lt_val[q] = B.LUval[B.Lt_map[q]];
+  }
+  // streams: lower pattern a = L (unit), b = U^T; upper pattern a = U, b = L^T (unit)
+  for (int k = 0; k < 2; ++k) {
+    const int* ma = k ? B.Up_map : B.Lo_map;
+    const int* mb = k ? B.Lt_map : B.Ut_map;
+    for (long long q = lt; q < B.st_nslots[k]; q += ls) {
+      const int sidx = B.st_src[k][q];
+      double va, vb;
+      if (sidx >= 0) {
+        va = B.LUval[ma[sidx]];
+        vb = B.LUval[mb[sidx]];
+      } else if (sidx == -1) {
+        va = vb = 1.0;
+      } else {
+        const double d = B.inv_diag[-2 - sidx];
+        va = k ? d : 1.0;
+        vb = k ? 1.0 : d;
+      }
+      B.st_a[k][B.st_slot[k][q]] = va;
+      B.st_b[k][B.st_slot[k][q]] = vb;
+    }
+  }
+}
+
+// diagonal-block inverses of the four factors of every instance: grid.y = 4 x
+// instance, one warp per supernode
+__global__ void k_b_diag_inv(const BatchInst* __restrict__ I) {
+  __shared__ double Tsh[4][32][33];
+  const BatchInst& B = I[blockIdx.y >> 2];
+  const DiagInvJob& J = B.dj[blockIdx.y & 3];
+  const int c = threadIdx.x & 31;
+  double (*Ts)[33] = Tsh[(threadIdx.x >> 5) & 3];
+  for (int sn = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sn < J.nsn; sn += (gridDim.x * blockDim.x) >> 5) {
+    if (J.upper) diag_inv_one<true>(Ts, sn, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
+    else diag_inv_one<false>(Ts, sn, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
+    __syncwarp();
+  }
+}
+
+// The level-blocked solve of one 32-column block (columns cb * 32 ..), by the
+// ksplit CTAs of its group (this one is p); sync() separates the phases (a
+// bounded group barrier, or __syncthreads when one CTA has the block).
+// Returns false when a barrier wait expired.
+template <class Sync>
+__device__ __forceinline__ bool blk_solve(const BlkDev& S, const int* __restrict__ ci, const double* __restrict__ val,
+                                          const double* __restrict__ D, double* X, double* Y, long long ld,
+                                          int ncols, int cb, int p, int ksplit, Sync&& sync) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int c = cb * 32 + lane;
   const bool on = c < ncols;
   const int gw = p * nwarps + warp, W = ksplit * nwarps;
-  unsigned* ctr = bar + cb;
-  unsigned nbar = 0;
   for (int lev = 0; lev < S.nlev; ++lev) {
     const int q0 = S.lvl_rptr[lev], q1 = S.lvl_rptr[lev + 1];
     // A: Y_r = X_r - external part of row r
@@ -718,7 +771,7 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
       }
       if (on) Y[(long long)r * ld + c] = (a0 + a1) + (a2 + a3);
     }
-    if (!group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
+    if (!sync()) return false;
     // B: X_r = D_s(r, :) Y_s over the nonzero half of the triangular D_s row
     for (int q = q0 + gw; q < q1; q += W) {
       const int r = S.rows[q], s = S.row_sn[q];
@@ -736,8 +789,39 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
         X[(long long)r * ld + c] = a0 + a1;
       }
     }
-    if (!group_barrier(ctr, ksplit * (++nbar), spin_limit, st)) return;
+    if (!sync()) return false;
   }
+  return true;
+}
+
+__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
+                                                          const double* __restrict__ val,
+                                                          const double* __restrict__ D, double* X, double* Y,
+                                                          long long ld, int ncols, int ksplit, unsigned* bar,
+                                                          int* st, long long spin_limit) {
+  const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
+  unsigned* ctr = bar + cb;
+  unsigned nbar = 0;
+  blk_solve(S, ci, val, D, X, Y, ld, ncols, cb, p, ksplit,
+            [&]() { return group_barrier(ctr, ksplit * (++nbar), spin_limit, st); });
+}
+
+// Both triangles of a multi-RHS solve for every instance of a batch: one CTA
+// per (instance, 32-column block) item, its eight warps taking a level's rows
+// and __syncthreads between the phases (no inter-CTA wait, so any number of
+// items can be launched).  trans = 0: S_x <- U^{-1} L^{-1} S_x; trans = 1: the x
+// rows of H <- L^{-T} U^{-T} H_x.
+__global__ void __launch_bounds__(BLK_THREADS) k_b_trsm(const BatchInst* __restrict__ I, const int2* __restrict__ cbs,
+                                                        int trans) {
+  const int2 it = cbs[blockIdx.x];
+  const BatchInst& B = I[it.x];
+  double* X = (trans ? B.H : B.Zt) + (size_t)B.nu * B.ld;
+  auto bar = []() {
+    __syncthreads();
+    return true;
+  };
+  blk_solve(B.bkL, B.Lo_ci, trans ? B.Ut_val : B.Lo_val, trans ? B.D_Ut : B.D_L, X, B.Y, B.ld, B.nu, it.y, 0, 1, bar);
+  blk_solve(B.bkU, B.Up_ci, trans ? B.Lt_val : B.Up_val, trans ? B.D_Lt : B.D_U, X, B.Y, B.ld, B.nu, it.y, 0, 1, bar);
 }
 
 // One right-hand side (the Newton-step recovery): the same two phases, with a
@@ -1398,3 +1482,26 @@ int trsm_df_max_blocks() {
 }
 
 }  // namespace condipm
+
+namespace condipm {
+
+cudaError_t launch_batch_factor_post(cudaStream_t s, const BatchInst* I, int n, const int* boffF, int nbF,
+                                     int nsn_max) {
+  if (n <= 0) return cudaSuccess;
+  k_b_gather<<<nbF, 256, 0, s>>>(I, n, boffF);
+  note_launch();
+  const int gx = std::max(1, std::min(64, (nsn_max * 32 + 127) / 128));
+  k_b_diag_inv<<<dim3(gx, 4 * n), 128, 0, s>>>(I);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans) {
+  if (ncbs <= 0) return cudaSuccess;
+  k_b_trsm<<<ncbs, BLK_THREADS, 0, s>>>(I, cbs, trans);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace condipm
+
