@@ -182,12 +182,16 @@ def cpu_oracle_condense(net, it, delta, budget_s=15.0, max_reps=200):
 
 def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
     """OPF solves/s of the 96 uneven instances (32 each at 500 / 1,500 / 3,000
-    buses, loads scaled per bus): one at a time versus opf_batch_solve, on the
-    same handles after the batch autotuner picked their solve kernels.  Every
-    batched objective is compared with its single-instance objective.  With
-    several ranks each solves its shard of the instances (no collective on
-    the data path); the rates are the instances of all ranks over the slowest
-    rank's time."""
+    buses, loads scaled per bus): one at a time versus opf_batch_solve in
+    lockstep (one batched condensation per iteration for every instance still
+    iterating) and as concurrent independent loops, on the same handles after
+    the batch autotuner picked their solve kernels.  Every batched objective is
+    compared with its single-instance objective.  Also one condense + Cholesky
+    of all instances at once (opf_batch_condense_factor) against the same work
+    one instance at a time.  With several ranks each solves its shard of the
+    instances (no collective on the data path); the rates are the instances of
+    all ranks over the slowest rank's time."""
+    import torch
     t00 = time.perf_counter()
     every = gridgen.batch96()
     nets = [every[i] for i in shard(len(every), rank, world)]
@@ -200,18 +204,59 @@ def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
     t0 = time.perf_counter()
     single = [h.solve() for h in hs]
     t_single = time.perf_counter() - t0
+    b.set_mode("lockstep")
     batched, wall_ms = b.solve()
     t_batch = wall_ms * 1e-3
+    b.set_mode("concurrent")
+    conc, wall_c = b.solve()
+    t_conc = wall_c * 1e-3
     rel = max(abs(a["obj"] - c["obj"]) / abs(a["obj"]) for a, c in zip(single, batched))
-    ok = all(a["status"] == 0 and c["status"] == 0 for a, c in zip(single, batched))
+    rel_c = max(abs(a["obj"] - c["obj"]) / abs(a["obj"]) for a, c in zip(single, conc))
+    ok = all(a["status"] == 0 and c["status"] == 0 and d["status"] == 0 for a, c, d in zip(single, batched, conc))
+    # one condensation + Cholesky of every instance: batched vs one at a time
+    pts = [synthetic_iterate(n, h.nx, h.nu, h.m, seed=7 + k) for k, (n, h) in enumerate(zip(nets, hs))]
+    Ds = [{k: torch.as_tensor(v, dtype=torch.float64, device=device) for k, v in p.items()} for p in pts]
+    for h, D in zip(hs, Ds):
+        h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+    deltas = []
+    for h, D in zip(hs, Ds):
+        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        dl = 0.0
+        while h.kkt_factor(dl) >= 0:
+            dl = max(1e-4, 8 * dl)
+        deltas.append(dl)
+    sig = [[D["sig_u"] for D in Ds], [D["sig_x"] for D in Ds], [D["sig_s"] for D in Ds]]
+    b.condense_factor(*sig, delta_w=deltas)          # builds the work lists
+    reps = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        st, _ = b.condense_factor(*sig, delta_w=deltas)
+    t_bcf = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for h, D, dl in zip(hs, Ds, deltas):
+            h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+            h.kkt_factor(dl)
+    t_scf = (time.perf_counter() - t0) / reps
     t_single, n_all = aggregate(t_single, len(nets), dist, device)
     t_batch, _ = aggregate(t_batch, len(nets), dist, device)
+    t_conc, _ = aggregate(t_conc, len(nets), dist, device)
     out = {"instances": n_all, "sizes": "32 x 500 + 32 x 1,500 + 32 x 3,000 buses",
            "solves_per_s_single": n_all / t_single, "solves_per_s_batched": n_all / t_batch,
-           "speedup": t_single / t_batch, "wall_s_single": t_single, "wall_s_batched": t_batch,
-           "host_threads": b.nthreads, "all_converged": ok, "max_rel_obj_diff_batched_vs_single": rel,
+           "solves_per_s_concurrent": n_all / t_conc,
+           "speedup": t_single / t_batch, "speedup_concurrent": t_single / t_conc,
+           "wall_s_single": t_single, "wall_s_batched": t_batch, "wall_s_concurrent": t_conc,
+           "batched_mode": "lockstep: one opf_batch_condense_factor per iteration for every instance still "
+                           "iterating (one host thread per instance)",
+           "lockstep_condensations": b.lockstep_calls(),
+           "host_threads_concurrent": b.nthreads, "all_converged": ok,
+           "max_rel_obj_diff_batched_vs_single": rel, "max_rel_obj_diff_concurrent_vs_single": rel_c,
            "iters_total": int(sum(c["iters"] for c in batched)),
-           "graph_iters_total": int(sum(c.get("graph_iters", 0) for c in batched))}
+           "iters_max": int(max(c["iters"] for c in batched)),
+           "condense_factor_all_instances_ms": {"batched": t_bcf * 1e3, "one_at_a_time": t_scf * 1e3,
+                                                "speedup": t_scf / t_bcf,
+                                                "all_pd": all(v == 0 for v in st)}}
     t03 = time.perf_counter()
     b.close()
     del hs

@@ -356,6 +356,24 @@ int opf_batch_autotune(opf_batch* b);
  * instance converged, else the first failing instance's code (errors before
  * OPF_ERR_NO_CONVERGENCE). */
 int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm_result* results, double* wall_ms);
+/* How opf_batch_solve runs the loops.
+ *  OPF_BATCH_LOCKSTEP (the default): one host thread per instance; at every
+ *    iteration the loops meet at the condensation, and one
+ *    opf_batch_condense_factor call (one launch per phase for all of them)
+ *    serves every instance still iterating -- instances that have converged or
+ *    stopped are masked on the device.  The rest of each iteration (derivatives,
+ *    step recovery, line search, inertia correction after NOT_PD) stays on the
+ *    instance's own stream.  Needs the adjoint route on every handle.
+ *  OPF_BATCH_CONCURRENT: nthreads host threads take instances from a queue, each
+ *    loop independent on its own stream (kernels of different instances
+ *    overlap on the SMs).
+ * Errors: INVALID_ARG. */
+#define OPF_BATCH_CONCURRENT 0
+#define OPF_BATCH_LOCKSTEP   1
+int opf_batch_set_mode(opf_batch* b, int mode);
+/* Batched condensations issued by lockstep solves since the batch was created
+ * (host output, may be NULL). */
+int opf_batch_stats(const opf_batch* b, long long* lockstep_calls);
 
 /* One interior-point iteration's condensation and control-step factorisation
  * (A5-A9: refactor G_x, S_x, K, H = K Z, Psi, Kred, Cholesky of Kred + delta_w I)

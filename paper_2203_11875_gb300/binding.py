@@ -95,6 +95,8 @@ _SIGS = {
     "opf_batch_autotune": (C.c_int, [C.c_void_p]),
     "opf_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result),
                                   C.POINTER(C.c_double)]),
+    "opf_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "opf_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "opf_batch_condense_factor": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                             C.POINTER(C.c_void_p), C.POINTER(C.c_double), _ip, _ip]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
@@ -439,6 +441,17 @@ class Batch:
         if rc not in (OPF_OK, -8):
             raise OPFError(rc, "opf_batch_solve")
         return out, ms.value
+
+    def set_mode(self, mode):
+        """opf_batch_set_mode: "lockstep" (batched condensation every iteration)
+        or "concurrent" (independent loops on streams)."""
+        code = {"concurrent": 0, "lockstep": 1}[mode]
+        _check(self._lib.opf_batch_set_mode(self._b, code), "opf_batch_set_mode")
+
+    def lockstep_calls(self):
+        n = C.c_longlong(0)
+        _check(self._lib.opf_batch_stats(self._b, C.byref(n)), "opf_batch_stats")
+        return n.value
 
     def condense_factor(self, sig_u, sig_x, sig_s, delta_w=None):
         """opf_batch_condense_factor: per-instance device tensors of Sigma (lists

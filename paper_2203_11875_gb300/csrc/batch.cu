@@ -26,6 +26,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -55,6 +57,16 @@ struct opf_batch {
   int nb[condipm::BOFF_KINDS] = {};
   int* st_host = nullptr;              // pinned: ST_WORDS per instance
   std::vector<void*> dev_allocs;
+  // lockstep solves: the instances' loops meet at every condensation
+  int mode = OPF_BATCH_LOCKSTEP;
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0, arrived = 0;
+  long long generation = 0;
+  std::vector<char> waiting;
+  std::vector<const double*> rsu, rsx, rss;
+  std::vector<int> rstatus;
+  long long lockstep_calls = 0;        // batched condensations issued by lockstep solves
 };
 
 #define TRY_B(x)                   \
@@ -151,22 +163,56 @@ extern "C" int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm
                                double* wall_ms) {
   if (!b || !results) return OPF_ERR_INVALID_ARG;
   const int n = int(b->hs.size());
-  std::atomic<int> next{0};
   std::vector<int> rcs(n, OPF_OK);
   const auto t0 = std::chrono::steady_clock::now();
-  auto worker = [&]() {
-    if (cudaSetDevice(b->device) != cudaSuccess) return;
-    for (;;) {
-      const int q = next.fetch_add(1);
-      if (q >= n) break;
-      const int i = b->order[q];
-      rcs[i] = opf_solve(b->hs[i], opt, &results[i]);
+  if (b->mode == OPF_BATCH_LOCKSTEP) {
+    // one host thread per instance; the loops meet at every condensation, which
+    // one batched call serves (instances that have finished are masked)
+    for (opf_handle* h : b->hs)
+      if (h->opt.route != OPF_ROUTE_ADJOINT) return OPF_ERR_INVALID_ARG;
+    {
+      std::lock_guard<std::mutex> lk(b->mu);
+      b->active = n;
+      b->arrived = 0;
+      b->waiting.assign(n, 0);
+      b->rsu.assign(n, nullptr);
+      b->rsx.assign(n, nullptr);
+      b->rss.assign(n, nullptr);
+      b->rstatus.assign(n, OPF_OK);
     }
-  };
-  std::vector<std::thread> pool;
-  for (int t = 1; t < b->nthreads; ++t) pool.emplace_back(worker);
-  worker();
-  for (auto& th : pool) th.join();
+    auto run = [&](int i) {
+      opf_handle* h = b->hs[i];
+      if (cudaSetDevice(b->device) == cudaSuccess) {
+        h->batch = b;
+        h->batch_idx = i;
+        rcs[i] = opf_solve(h, opt, &results[i]);
+        h->batch = nullptr;
+        h->batch_idx = -1;
+      } else {
+        rcs[i] = OPF_ERR_CUDA;
+      }
+      batch_leave(b);
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < n; ++i) pool.emplace_back(run, i);
+    run(0);
+    for (auto& th : pool) th.join();
+  } else {
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      if (cudaSetDevice(b->device) != cudaSuccess) return;
+      for (;;) {
+        const int q = next.fetch_add(1);
+        if (q >= n) break;
+        const int i = b->order[q];
+        rcs[i] = opf_solve(b->hs[i], opt, &results[i]);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < b->nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+  }
   if (wall_ms) *wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   // the first instance whose loop failed with an error (not merely the iteration cap)
   for (int i = 0; i < n; ++i)
@@ -303,12 +349,16 @@ BatchInst describe(opf_handle* h, const double* sig_u, const double* sig_x, cons
 }  // namespace
 }  // namespace condipm
 
-extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_u, const double* const* sig_x,
-                                         const double* const* sig_s, const double* delta_w, int* status,
-                                         int* fail_col) {
-  if (!b || !sig_u || !sig_x || !sig_s || !status) return OPF_ERR_INVALID_ARG;
+namespace condipm {
+
+// The batched condensation of the instances with on[i] set (the others are
+// masked: their work-list items are skipped on the device).
+int batch_condense_subset(opf_batch* b, const std::vector<char>& on, const double* const* sig_u,
+                          const double* const* sig_x, const double* const* sig_s, const double* delta_w, int* status,
+                          int* fail_col) {
   const int n = int(b->hs.size());
   for (int i = 0; i < n; ++i) {
+    if (!on[i]) continue;
     const opf_handle* h = b->hs[i];
     if (!h->have_W || !sig_u[i] || !sig_x[i] || !sig_s[i] || (delta_w && !(delta_w[i] >= 0.0)))
       return OPF_ERR_INVALID_ARG;
@@ -318,10 +368,18 @@ extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_
     const int rc = batch_setup(b);
     if (rc != OPF_OK) return rc;
   }
-  for (int i = 0; i < n; ++i)
-    b->hI[i] = describe(b->hs[i], sig_u[i], sig_x[i], sig_s[i], delta_w ? delta_w[i] : 0.0);
+  for (int i = 0; i < n; ++i) {
+    if (on[i]) {
+      b->hI[i] = describe(b->hs[i], sig_u[i], sig_x[i], sig_s[i], delta_w ? delta_w[i] : 0.0);
+      b->hI[i].active = 1;
+    } else {
+      b->hI[i] = BatchInst{};
+      b->hI[i].active = 0;
+    }
+  }
   // the batched launches follow every instance's work so far (its derivatives)
   for (int i = 0; i < n; ++i) {
+    if (!on[i]) continue;
     if (cudaEventRecord(b->ev[i], b->hs[i]->s) != cudaSuccess) return OPF_ERR_CUDA;
     if (cudaStreamWaitEvent(b->bs, b->ev[i], 0) != cudaSuccess) return OPF_ERR_CUDA;
   }
@@ -339,7 +397,8 @@ extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_
   if (e == cudaSuccess) e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
   if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, 8);
   for (int i = 0; i < n && e == cudaSuccess; ++i)
-    e = cudaMemcpyAsync(b->st_host + ST_WORDS * i, b->hs[i]->st, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, s);
+    if (on[i])
+      e = cudaMemcpyAsync(b->st_host + ST_WORDS * i, b->hs[i]->st, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     note_cuda_error(e);
@@ -347,6 +406,7 @@ extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_
   }
   int first = OPF_OK;
   for (int i = 0; i < n; ++i) {
+    if (!on[i]) continue;
     opf_handle* h = b->hs[i];
     const int* st = b->st_host + ST_WORDS * i;
     int rc = OPF_OK;
@@ -375,7 +435,70 @@ extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_
   // later work on each instance's stream follows the batched launches
   if (cudaEventRecord(b->ev_done, s) != cudaSuccess) return OPF_ERR_CUDA;
   for (int i = 0; i < n; ++i)
-    if (cudaStreamWaitEvent(b->hs[i]->s, b->ev_done, 0) != cudaSuccess) return OPF_ERR_CUDA;
+    if (on[i] && cudaStreamWaitEvent(b->hs[i]->s, b->ev_done, 0) != cudaSuccess) return OPF_ERR_CUDA;
   return first;
+}
+
+namespace {
+// issue the batched condensation for the instances waiting now (mu held)
+void rendezvous_fire(opf_batch* b) {
+  const int n = int(b->hs.size());
+  std::vector<int> fc(n, -1);
+  const int rc = batch_condense_subset(b, b->waiting, b->rsu.data(), b->rsx.data(), b->rss.data(), nullptr,
+                                       b->rstatus.data(), fc.data());
+  for (int i = 0; i < n; ++i)
+    if (b->waiting[i] && rc != OPF_OK && rc != OPF_ERR_NOT_PD && rc != OPF_ERR_SINGULAR && rc != OPF_ERR_TIMEOUT)
+      b->rstatus[i] = rc;   // the call itself failed
+  std::fill(b->waiting.begin(), b->waiting.end(), 0);
+  b->arrived = 0;
+  ++b->generation;
+  ++b->lockstep_calls;
+  b->cv.notify_all();
+}
+}  // namespace
+
+// A lockstep solve's condensation and first Cholesky attempt: wait until every
+// instance still iterating has arrived, then one batched call serves them all.
+int batch_join(opf_batch* b, int idx, const double* su, const double* sx, const double* ss) {
+  std::unique_lock<std::mutex> lk(b->mu);
+  b->rsu[idx] = su;
+  b->rsx[idx] = sx;
+  b->rss[idx] = ss;
+  b->waiting[idx] = 1;
+  ++b->arrived;
+  const long long g = b->generation;
+  if (b->arrived >= b->active) rendezvous_fire(b);
+  else b->cv.wait(lk, [&]() { return b->generation != g; });
+  return b->rstatus[idx];
+}
+
+// An instance's loop has ended: the others no longer wait for it.
+void batch_leave(opf_batch* b) {
+  std::unique_lock<std::mutex> lk(b->mu);
+  --b->active;
+  if (b->active > 0 && b->arrived >= b->active) rendezvous_fire(b);
+}
+
+}  // namespace condipm
+
+extern "C" int opf_batch_condense_factor(opf_batch* b, const double* const* sig_u, const double* const* sig_x,
+                                         const double* const* sig_s, const double* delta_w, int* status,
+                                         int* fail_col) {
+  if (!b || !sig_u || !sig_x || !sig_s || !status) return OPF_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(b->mu);
+  std::vector<char> on(b->hs.size(), 1);
+  return batch_condense_subset(b, on, sig_u, sig_x, sig_s, delta_w, status, fail_col);
+}
+
+extern "C" int opf_batch_set_mode(opf_batch* b, int mode) {
+  if (!b || (mode != OPF_BATCH_CONCURRENT && mode != OPF_BATCH_LOCKSTEP)) return OPF_ERR_INVALID_ARG;
+  b->mode = mode;
+  return OPF_OK;
+}
+
+extern "C" int opf_batch_stats(const opf_batch* b, long long* lockstep_calls) {
+  if (!b) return OPF_ERR_INVALID_ARG;
+  if (lockstep_calls) *lockstep_calls = b->lockstep_calls;
+  return OPF_OK;
 }
 

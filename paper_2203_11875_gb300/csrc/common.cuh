@@ -294,6 +294,7 @@ cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld);
 // arrays of its handle that the batched phase kernels read and write.  A device
 // array of these, one per instance, is what every batched launch indexes.
 struct BatchInst {
+  int active;   // 0: this instance takes no part in the call (its items are skipped)
   int nx, nu, nw, m, ld;
   long long nnzG, nnzLU, nnzK, nnzLo, nnzUp;
   // G_x refactorisation

@@ -49,5 +49,9 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
 int sens_prepare(opf_handle* h, const double* w, const double* lam, const double* y, const double* sig_w,
                  const double* sig_s);
 int powerflow_impl(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters);
+// lockstep batches: the condensation rendezvous of instance idx (returns its
+// status), and the end of an instance's loop
+int batch_join(opf_batch* b, int idx, const double* su, const double* sx, const double* ss);
+void batch_leave(opf_batch* b);
 
 }  // namespace condipm

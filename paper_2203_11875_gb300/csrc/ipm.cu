@@ -234,6 +234,12 @@ int factor_with_correction(opf_handle* h, double& delta, double delta_last, int&
 // is refused, or while phases are being profiled, the launches are enqueued
 // one by one.  Returns the device status (one synchronisation).
 int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
+  if (h->batch) {
+    // a lockstep batch: one batched call serves every instance still iterating
+    const int rc = batch_join(h->batch, h->batch_idx, d.sig_u, d.sig_x, d.sig_s);
+    h->have_factor = rc == OPF_OK;
+    return rc;
+  }
   const bool graph_ok = h->use_graphs && !h->cf_failed && !h->profiling && h->trsm_mode >= 0 && h->chol_tuned;
   if (graph_ok && !h->cf_exec) {
     cudaGraph_t g = nullptr;

@@ -318,6 +318,7 @@ __global__ void k_b_lu(const BatchInst* __restrict__ I, const int2* __restrict__
   for (int t = warp; t < nitems; t += nwarps) {
     const int2 it = items[t];
     const BatchInst& B = I[it.x];
+    if (!B.active) continue;
     if (!lu_row(it.y, B.LU_rp, B.LU_ci, B.LU_diag, B.upd_ptr, B.upd_pos, B.LUval, B.inv_diag, B.rmax, B.flags,
                 epoch, B.st, spin_limit, w, lane))
       return;
@@ -351,6 +352,7 @@ __device__ __forceinline__ BatchSlice batch_slice(const BatchInst* I, const int*
 __global__ void k_b_clear(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
   const BatchSlice sl = batch_slice(I, boff, n);
   const BatchInst& B = *sl.B;
+  if (!B.active) return;
   for (long long e = sl.lt; e < B.nnzLU; e += sl.ls) B.LUval[e] = 0.0;
   for (long long e = sl.lt; e < B.nx; e += sl.ls) B.flags[e] = 0u;
   if (sl.lt < ST_WORDS) B.st[sl.lt] = 0;
@@ -363,6 +365,7 @@ __global__ void k_b_clear(const BatchInst* __restrict__ I, int n, const int* __r
 __global__ void k_b_scatter(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
   const BatchSlice sl = batch_slice(I, boff, n);
   const BatchInst& B = *sl.B;
+  if (!B.active) return;
   for (long long q = sl.lt; q < B.nnzG; q += sl.ls) {
     const int p = B.Gx_to_LU[q];
     if (p >= 0) B.LUval[p] = B.Gval[q];
@@ -385,6 +388,7 @@ __global__ void k_b_scatter(const BatchInst* __restrict__ I, int n, const int* _
 __global__ void k_b_rowmax(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
   const BatchSlice sl = batch_slice(I, boff, n);
   const BatchInst& B = *sl.B;
+  if (!B.active) return;
   const int lane = threadIdx.x & 31;
   for (long long i = sl.lt >> 5; i < B.nx; i += sl.ls >> 5) {
     unsigned long long mx = 0;
@@ -411,6 +415,7 @@ __global__ void k_b_rowmax(const BatchInst* __restrict__ I, int n, const int* __
 __global__ void k_b_spmm(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff, int which) {
   const BatchSlice sl = batch_slice(I, boff, n);
   const BatchInst& B = *sl.B;
+  if (!B.active) return;
   const long long ld = B.ld;
   const int nu = B.nu;
   const long long total = (long long)(which == 0 ? B.nw : nu) * nu;
@@ -434,6 +439,7 @@ __global__ void k_b_spmm(const BatchInst* __restrict__ I, int n, const int* __re
 __global__ void k_b_kred(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
   const BatchSlice sl = batch_slice(I, boff, n);
   const BatchInst& B = *sl.B;
+  if (!B.active) return;
   const int nu = B.nu;
   const long long ld = B.ld;
   for (long long e = sl.lt; e < (long long)nu * nu; e += sl.ls) {
@@ -763,6 +769,7 @@ __global__ void __launch_bounds__(256) k_chol(double* F, int n, double* dinv_out
 __global__ void __launch_bounds__(256) k_b_chol(const BatchInst* __restrict__ I) {
   cg::cluster_group cl = cg::this_cluster();
   const BatchInst& B = I[blockIdx.x / cl.num_blocks()];
+  if (!B.active) return;   // the whole cluster leaves together, before any cluster barrier
   chol_run(B.F, B.nu, B.Fdinv, B.st, (int)cl.block_rank(), cl.num_blocks(), [&]() {
     cl.sync();
     return true;

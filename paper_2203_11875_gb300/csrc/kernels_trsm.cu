@@ -677,6 +677,7 @@ __global__ void k_diag_inv4(DiagInvJob j0, DiagInvJob j1, DiagInvJob j2, DiagInv
 __global__ void k_b_gather(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
   const int i = batch_instance(boff, n, blockIdx.x);
   const BatchInst& B = I[i];
+  if (!B.active) return;
   const long long lt = (long long)(blockIdx.x - boff[i]) * blockDim.x + threadIdx.x;
   const long long ls = (long long)(boff[i + 1] - boff[i]) * blockDim.x;
   for (long long q = lt; q < B.nnzLo; q += ls) {
@@ -715,6 +716,7 @@ __global__ void k_b_gather(const BatchInst* __restrict__ I, int n, const int* __
 __global__ void k_b_diag_inv(const BatchInst* __restrict__ I) {
   __shared__ double Tsh[4][32][33];
   const BatchInst& B = I[blockIdx.y >> 2];
+  if (!B.active) return;
   const DiagInvJob& J = B.dj[blockIdx.y & 3];
   const int c = threadIdx.x & 31;
   double (*Ts)[33] = Tsh[(threadIdx.x >> 5) & 3];
@@ -815,6 +817,7 @@ __global__ void __launch_bounds__(BLK_THREADS) k_b_trsm(const BatchInst* __restr
                                                         int trans) {
   const int2 it = cbs[blockIdx.x];
   const BatchInst& B = I[it.x];
+  if (!B.active) return;
   double* X = (trans ? B.H : B.Zt) + (size_t)B.nu * B.ld;
   auto bar = []() {
     __syncthreads();

@@ -8,6 +8,8 @@
 #include "common.cuh"
 #include "plan.h"
 
+struct opf_batch;
+
 struct opf_handle {
   condipm::Plan P;
   opf_options opt{};
@@ -118,6 +120,10 @@ struct opf_handle {
   cudaGraphExec_t cf_exec = nullptr;
   bool cf_failed = false;        // capture or instantiation was refused: plain launches
   bool use_graphs = true;
+  // set while a lockstep batch solve runs this handle's loop: its condensation
+  // and first Cholesky attempt go through the batch's rendezvous
+  opf_batch* batch = nullptr;
+  int batch_idx = -1;
   // call-order state
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   bool psi_valid = false;         // Zt holds S_x and H's x rows G_x^{-T} H_x of the last condensation
