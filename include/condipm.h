@@ -371,9 +371,12 @@ int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm_result* re
 #define OPF_BATCH_CONCURRENT 0
 #define OPF_BATCH_LOCKSTEP   1
 int opf_batch_set_mode(opf_batch* b, int mode);
-/* Batched condensations issued by lockstep solves since the batch was created
- * (host output, may be NULL). */
-int opf_batch_stats(const opf_batch* b, long long* lockstep_calls);
+/* Batched condensations issued by lockstep solves since the batch was created;
+ * the cluster sizes (CTAs) of the batched multi-RHS solves and Cholesky (0 until
+ * the first opf_batch_condense_factor whose instances all factored completely
+ * timed the candidates 2, 4, 8, 16); tune_ms[8] those timings (solve, then
+ * Cholesky; 0 = not tried).  Host outputs, any may be NULL. */
+int opf_batch_stats(const opf_batch* b, long long* lockstep_calls, int* trsm_cl, int* chol_cl, float* tune_ms);
 
 /* One interior-point iteration's condensation and control-step factorisation
  * (A5-A9: refactor G_x, S_x, K, H = K Z, Psi, Kred, Cholesky of Kred + delta_w I)

@@ -57,6 +57,10 @@ struct opf_batch {
   int nb[condipm::BOFF_KINDS] = {};
   int* st_host = nullptr;              // pinned: ST_WORDS per instance
   std::vector<void*> dev_allocs;
+  // cluster sizes of the batched solves and Cholesky: 0 until the first call
+  // times the candidates on the batch's own instances
+  int trsm_cl = 0, chol_cl = 0;
+  float tune_trsm_ms[4] = {}, tune_chol_ms[4] = {};   // candidates 2, 4, 8, 16 CTAs
   // lockstep solves: the instances' loops meet at every condensation
   int mode = OPF_BATCH_LOCKSTEP;
   std::mutex mu;
@@ -226,6 +230,8 @@ extern "C" int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm
 namespace condipm {
 namespace {
 
+constexpr int BATCH_CL_CANDIDATES[4] = {2, 4, 8, 16};
+
 template <class T>
 int dev_upload(opf_batch* b, T** dst, const std::vector<T>& v) {
   const size_t n = std::max<size_t>(1, v.size());
@@ -280,9 +286,12 @@ int batch_setup(opf_batch* b) {
         case BOFF_X: work = std::max<long long>((long long)P.nx * h->ldp, P.LU.nnz()); break;
         case BOFF_W: work = (long long)P.nw * P.nu; break;
         case BOFF_U: work = (long long)P.nu * P.nu; break;
-        default:
+        case BOFF_F:
           work = std::max(std::max<long long>(P.Lo.nnz(), P.Up.nnz()),
                           std::max(h->stLo.nslots, h->stUp.nslots));
+          break;
+        default:   // BOFF_D: one warp per (factor, supernode), four warps per block
+          work = 2LL * (long long)(P.csL.sn_first.size() + P.csU.sn_first.size()) * per_block / 4;
       }
       const long long nbk = std::max(1LL, std::min(65536LL, (work + per_block - 1) / per_block));
       off[i + 1] = off[i] + int(nbk);
@@ -387,15 +396,85 @@ int batch_condense_subset(opf_batch* b, const std::vector<char>& on, const doubl
   if (cudaMemcpyAsync(b->dI, b->hI, sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return OPF_ERR_CUDA;
   const long long spin = b->hs[0]->spin_limit;
-  cudaError_t e = launch_batch_prologue(s, b->dI, n, b->boff, b->nb);
-  if (e == cudaSuccess) e = launch_batch_lu(s, b->dI, b->lu_items, b->n_lu_items, b->lu_blocks, b->lu_maxlen, 1u, spin);
-  if (e == cudaSuccess) e = launch_batch_factor_post(s, b->dI, n, b->boff[BOFF_F], b->nb[BOFF_F], b->nsn_max);
-  if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0);
+  // A5: refactorisation with its prologue and epilogue
+  auto front = [&]() {
+    cudaError_t e = launch_batch_prologue(s, b->dI, n, b->boff, b->nb);
+    if (e == cudaSuccess)
+      e = launch_batch_lu(s, b->dI, b->lu_items, b->n_lu_items, b->lu_blocks, b->lu_maxlen, 1u, spin);
+    if (e == cudaSuccess)
+      e = launch_batch_factor_post(s, b->dI, n, b->boff[BOFF_F], b->nb[BOFF_F], b->boff[BOFF_D], b->nb[BOFF_D]);
+    return e;
+  };
+  // time a launch on the batch's stream (the tuning of the first call)
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  auto timed = [&](auto&& launch, float* ms) {
+    cudaError_t e = cudaEventRecord(ta, s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(tb, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(tb);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ta, tb);
+    return e;
+  };
+  const bool tune = b->trsm_cl == 0 || b->chol_cl == 0;
+  cudaError_t e = cudaSuccess;
+  if (tune) {
+    e = cudaEventCreate(&ta);
+    if (e == cudaSuccess) e = cudaEventCreate(&tb);
+  }
+  // A6 (S_x): with the tuned cluster size, or each candidate after its own
+  // refactorisation (the solve works in place; every cluster size gives the
+  // same result, each row being summed by one warp in one order)
+  int trsm_cl = b->trsm_cl;
+  if (e == cudaSuccess && trsm_cl == 0) {
+    float best = 1e30f;
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+      const int cl = BATCH_CL_CANDIDATES[c];
+      if (batch_trsm_clusters(cl) < 1) continue;
+      e = front();
+      float ms = 0.f;
+      if (e == cudaSuccess) e = timed([&]() { return launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, cl); }, &ms);
+      b->tune_trsm_ms[c] = ms;
+      if (ms < best) { best = ms; trsm_cl = cl; }
+      if (c < 3 && e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    // the last candidate's solve stands only if it is the pick: redo otherwise
+    if (e == cudaSuccess && trsm_cl != BATCH_CL_CANDIDATES[3]) {
+      e = front();
+      if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, trsm_cl);
+    }
+  } else if (e == cudaSuccess) {
+    e = front();
+    if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, trsm_cl);
+  }
+  // A7: H = K Z, Psi = G_x^{-T} H_x, H_u -= G_u^T Psi, Kred and F
   if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_W], b->nb[BOFF_W], 0);
-  if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 1);
+  if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 1, trsm_cl);
   if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U], 1);
-  if (e == cudaSuccess) e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
-  if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, 8);
+  // A9: Cholesky, with the tuned cluster size or each candidate on a fresh F
+  int chol_cl = b->chol_cl;
+  if (e == cudaSuccess && chol_cl == 0) {
+    float best = 1e30f;
+    int last = 0;
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+      const int cl = BATCH_CL_CANDIDATES[c];
+      if (batch_chol_clusters(cl) < 1) continue;
+      e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = timed([&]() { return launch_batch_chol(s, b->dI, n, cl); }, &ms);
+      b->tune_chol_ms[c] = ms;
+      if (ms < best) { best = ms; chol_cl = cl; }
+      last = cl;
+    }
+    if (e == cudaSuccess && chol_cl != last) {
+      e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+      if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, chol_cl);
+    }
+  } else if (e == cudaSuccess) {
+    e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+    if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, chol_cl);
+  }
+  if (ta) cudaEventDestroy(ta);
+  if (tb) cudaEventDestroy(tb);
   for (int i = 0; i < n && e == cudaSuccess; ++i)
     if (on[i])
       e = cudaMemcpyAsync(b->st_host + ST_WORDS * i, b->hs[i]->st, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, s);
@@ -405,6 +484,18 @@ int batch_condense_subset(opf_batch* b, const std::vector<char>& on, const doubl
     return OPF_ERR_CUDA;
   }
   int first = OPF_OK;
+  if (tune) {
+    // keep the picks when every instance factored completely (an early stop on
+    // a non-positive pivot makes a candidate look fast); else tune again later
+    bool complete = true;
+    for (int i = 0; i < n; ++i)
+      if (on[i] && (b->st_host[ST_WORDS * i + ST_CODE] != 0 || b->st_host[ST_WORDS * i + ST_TIMEOUT] != 0))
+        complete = false;
+    if (complete) {
+      b->trsm_cl = trsm_cl;
+      b->chol_cl = chol_cl;
+    }
+  }
   for (int i = 0; i < n; ++i) {
     if (!on[i]) continue;
     opf_handle* h = b->hs[i];
@@ -496,9 +587,17 @@ extern "C" int opf_batch_set_mode(opf_batch* b, int mode) {
   return OPF_OK;
 }
 
-extern "C" int opf_batch_stats(const opf_batch* b, long long* lockstep_calls) {
+extern "C" int opf_batch_stats(const opf_batch* b, long long* lockstep_calls, int* trsm_cl, int* chol_cl,
+                               float* tune_ms) {
   if (!b) return OPF_ERR_INVALID_ARG;
   if (lockstep_calls) *lockstep_calls = b->lockstep_calls;
+  if (trsm_cl) *trsm_cl = b->trsm_cl;
+  if (chol_cl) *chol_cl = b->chol_cl;
+  if (tune_ms)
+    for (int c = 0; c < 4; ++c) {
+      tune_ms[c] = b->tune_trsm_ms[c];
+      tune_ms[4 + c] = b->tune_chol_ms[c];
+    }
   return OPF_OK;
 }
 

@@ -346,8 +346,9 @@ __device__ __forceinline__ int batch_instance(const int* __restrict__ boff, int 
 // device descriptor array, n instances).  Block offsets boff per launch shape:
 // BOFF_LU (nnz(LU) and nnz(G) elements), BOFF_K (nnz(K)), BOFF_X (nx rows of Z),
 // BOFF_W (nw rows of H), BOFF_U (nu rows of Kred), BOFF_F (factor entries
-// nnz(Lo) + nnz(Up) and staged slots).
-enum { BOFF_LU = 0, BOFF_K = 1, BOFF_X = 2, BOFF_W = 3, BOFF_U = 4, BOFF_F = 5, BOFF_KINDS = 6 };
+// nnz(Lo) + nnz(Up) and staged slots), BOFF_D (warps: 2 (supernodes of L +
+// supernodes of U), four per block).
+enum { BOFF_LU = 0, BOFF_K = 1, BOFF_X = 2, BOFF_W = 3, BOFF_U = 4, BOFF_F = 5, BOFF_D = 6, BOFF_KINDS = 7 };
 constexpr int BATCH_EW_THREADS = 256;
 constexpr int BATCH_EW_ITEMS = 4;   // elements (rows) per thread and launch of an elementwise phase
 // A5 prologue: zero LU, the row flags, the status word and S_x; then scatter
@@ -361,17 +362,21 @@ cudaError_t launch_batch_lu(cudaStream_t s, const BatchInst* I, const int2* item
                             int maxlen, unsigned epoch, long long spin_limit);
 int batch_lu_max_blocks(int maxlen);
 // A5 epilogue: the four factors' gathers and staged streams, then their
-// diagonal-block inverses
+// diagonal-block inverses (BOFF_D: one warp per factor and supernode)
 cudaError_t launch_batch_factor_post(cudaStream_t s, const BatchInst* I, int n, const int* boffF, int nbF,
-                                     int nsn_max);
+                                     const int* boffD, int nbD);
 // A6: S_x (trans = 0: L then U) or Psi = G_x^{-T} H_x (trans = 1: U^T then L^T)
-// for every instance, one CTA per (instance, 32-column block) item
-cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans);
+// for every instance, one cluster of cl CTAs per (instance, 32-column block) item
+cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans, int cl);
 // A7: H = K Z (which = 0), then H_u -= G_u^T Psi (which = 1)
 cudaError_t launch_batch_spmm(cudaStream_t s, const BatchInst* I, int n, const int* boff, int nblocks, int which);
 // A7 / A9: Kred = sym(H_u) and F = tril(Kred) + delta_w I
 cudaError_t launch_batch_kred(cudaStream_t s, const BatchInst* I, int n, const int* boffU, int nblocks);
 // A9: Cholesky of every instance's F, one thread-block cluster of cl CTAs per instance
 cudaError_t launch_batch_chol(cudaStream_t s, const BatchInst* I, int n, int cl);
+// clusters of cl CTAs of the batched solve / Cholesky that fit on the device at
+// once (0: that cluster size cannot be launched)
+int batch_trsm_clusters(int cl);
+int batch_chol_clusters(int cl);
 
 }  // namespace condipm

@@ -1509,6 +1509,10 @@ cudaError_t launch_batch_kred(cudaStream_t s, const BatchInst* I, int n, const i
 
 cudaError_t launch_batch_chol(cudaStream_t s, const BatchInst* I, int n, int cl) {
   if (n <= 0) return cudaSuccess;
+  if (cl > 8) {
+    cudaError_t e = allow_cluster16((const void*)k_b_chol);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(n * cl);
   cfg.blockDim = dim3(256);
@@ -1523,6 +1527,26 @@ cudaError_t launch_batch_chol(cudaStream_t s, const BatchInst* I, int n, int cl)
   cfg.numAttrs = 1;
   note_launch();
   return cudaLaunchKernelEx(&cfg, k_b_chol, I);
+}
+
+int batch_chol_clusters(int cl) {
+  if (cl > 8 && allow_cluster16((const void*)k_b_chol) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(256);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k_b_chol, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc;
 }
 
 }  // namespace condipm

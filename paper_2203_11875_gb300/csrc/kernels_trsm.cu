@@ -601,8 +601,8 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, lo
   return ok_s != 0;
 }
 
-template <bool UPPER>
-__device__ __forceinline__ void diag_inv_one(double (*Ts)[33], int s, int c, const int* __restrict__ sn_first,
+template <bool UPPER, int WM>
+__device__ __forceinline__ void diag_inv_w(double (*Ts)[33], int s, int c, const int* __restrict__ sn_first,
                                              const int* __restrict__ sn_w, const int* __restrict__ d_off,
                                              const int* __restrict__ int_beg, const double* __restrict__ val,
                                              const double* __restrict__ inv_diag, double* __restrict__ D) {
@@ -612,7 +612,7 @@ __device__ __forceinline__ void diag_inv_one(double (*Ts)[33], int s, int c, con
   // below waits on no global load
   const int ib = c < w ? int_beg[f + c] : 0;   // lane r: where row r's entries start
 #pragma unroll
-  for (int r = 0; r < 32; ++r) {
+  for (int r = 0; r < WM; ++r) {
     const int ibr = __shfl_sync(0xffffffffu, ib, r);
     if (r < w) {
       if (!UPPER) {
@@ -624,29 +624,34 @@ __device__ __forceinline__ void diag_inv_one(double (*Ts)[33], int s, int c, con
   }
   const double idg = (inv_diag && c < w) ? inv_diag[f + c] : 1.0;
   __syncwarp();
-  double d[32];
+  double d[WM];
 #pragma unroll
-  for (int r = 0; r < 32; ++r) d[r] = 0.0;
+  for (int r = 0; r < WM; ++r) d[r] = 0.0;
+  // row r of the inverse needs the rows before it (after it, for UPPER): a
+  // dependent chain; each row's sum is split over four accumulators (by j mod
+  // 4), so the chain of a 32-wide block is about a quarter as long
   if (!UPPER) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
+    for (int r = 0; r < WM; ++r) {
       if (r < w) {
-        double acc = (r == c) ? 1.0 : 0.0;
+        double a[4] = {(r == c) ? 1.0 : 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < r) acc = fma(-Ts[r][j], d[j], acc);
+        for (int j = 0; j < WM; ++j)
+          if (j < r) a[j & 3] = fma(-Ts[r][j], d[j], a[j & 3]);
+        const double acc = (a[0] + a[1]) + (a[2] + a[3]);
         d[r] = inv_diag ? acc * __shfl_sync(0xffffffffu, idg, r) : acc;
       }
     }
   } else {
 #pragma unroll
-    for (int rr = 0; rr < 32; ++rr) {
-      const int r = 31 - rr;
+    for (int rr = 0; rr < WM; ++rr) {
+      const int r = WM - 1 - rr;
       if (r < w) {
-        double acc = (r == c) ? 1.0 : 0.0;
+        double a[4] = {(r == c) ? 1.0 : 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j > r && j < w) acc = fma(-Ts[r][j], d[j], acc);
+        for (int j = 0; j < WM; ++j)
+          if (j > r && j < w) a[j & 3] = fma(-Ts[r][j], d[j], a[j & 3]);
+        const double acc = (a[0] + a[1]) + (a[2] + a[3]);
         d[r] = inv_diag ? acc * __shfl_sync(0xffffffffu, idg, r) : acc;
       }
     }
@@ -654,9 +659,22 @@ __device__ __forceinline__ void diag_inv_one(double (*Ts)[33], int s, int c, con
   if (c < w) {
     double* Ds = D + d_off[s];
 #pragma unroll
-    for (int r = 0; r < 32; ++r)
+    for (int r = 0; r < WM; ++r)
       if (r < w) Ds[r * w + c] = d[r];
   }
+}
+
+// the inverse of supernode s's diagonal block, its loops unrolled to the
+// smallest of 4, 8, 32 that covers the block's width (most blocks are narrow)
+template <bool UPPER>
+__device__ __forceinline__ void diag_inv_one(double (*Ts)[33], int s, int c, const int* __restrict__ sn_first,
+                                             const int* __restrict__ sn_w, const int* __restrict__ d_off,
+                                             const int* __restrict__ int_beg, const double* __restrict__ val,
+                                             const double* __restrict__ inv_diag, double* __restrict__ D) {
+  const int w = sn_w[s];
+  if (w <= 4) diag_inv_w<UPPER, 4>(Ts, s, c, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
+  else if (w <= 8) diag_inv_w<UPPER, 8>(Ts, s, c, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
+  else diag_inv_w<UPPER, 32>(Ts, s, c, sn_first, sn_w, d_off, int_beg, val, inv_diag, D);
 }
 
 // the four factors' diagonal-block inverses in one launch (blockIdx.y picks
@@ -711,16 +729,21 @@ __global__ void k_b_gather(const BatchInst* __restrict__ I, int n, const int* __
   }
 }
 
-// diagonal-block inverses of the four factors of every instance: grid.y = 4 x
-// instance, one warp per supernode
-__global__ void k_b_diag_inv(const BatchInst* __restrict__ I) {
+// diagonal-block inverses of the four factors of every instance: one warp per
+// (factor, supernode), the blocks boff[i] .. boff[i + 1] serving instance i
+__global__ void __launch_bounds__(128, 4) k_b_diag_inv(const BatchInst* __restrict__ I, int n, const int* __restrict__ boff) {
   __shared__ double Tsh[4][32][33];
-  const BatchInst& B = I[blockIdx.y >> 2];
+  const int i = batch_instance(boff, n, blockIdx.x);
+  const BatchInst& B = I[i];
   if (!B.active) return;
-  const DiagInvJob& J = B.dj[blockIdx.y & 3];
   const int c = threadIdx.x & 31;
   double (*Ts)[33] = Tsh[(threadIdx.x >> 5) & 3];
-  for (int sn = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sn < J.nsn; sn += (gridDim.x * blockDim.x) >> 5) {
+  const int nl = B.dj[0].nsn, nuu = B.dj[2].nsn;
+  const int nw = (boff[i + 1] - boff[i]) * (blockDim.x >> 5);
+  for (int t = ((blockIdx.x - boff[i]) * blockDim.x + threadIdx.x) >> 5; t < 2 * (nl + nuu); t += nw) {
+    const int j = t < nl ? 0 : t < 2 * nl ? 1 : t < 2 * nl + nuu ? 2 : 3;
+    const int sn = j < 2 ? t - j * nl : t - 2 * nl - (j - 2) * nuu;
+    const DiagInvJob& J = B.dj[j];
     if (J.upper) diag_inv_one<true>(Ts, sn, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
     else diag_inv_one<false>(Ts, sn, c, J.sn_first, J.sn_w, J.d_off, J.int_beg, J.val, J.inv_diag, J.D);
     __syncwarp();
@@ -808,23 +831,26 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
             [&]() { return group_barrier(ctr, ksplit * (++nbar), spin_limit, st); });
 }
 
-// Both triangles of a multi-RHS solve for every instance of a batch: one CTA
-// per (instance, 32-column block) item, its eight warps taking a level's rows
-// and __syncthreads between the phases (no inter-CTA wait, so any number of
-// items can be launched).  trans = 0: S_x <- U^{-1} L^{-1} S_x; trans = 1: the x
-// rows of H <- L^{-T} U^{-T} H_x.
+// Both triangles of a multi-RHS solve for every instance of a batch: one
+// thread-block cluster per (instance, 32-column block) item, its CTAs sharing
+// out a level's rows and the cluster barrier between the phases (the hardware
+// co-schedules a cluster's CTAs, so the barrier always completes and any
+// number of items can be launched).  trans = 0: S_x <- U^{-1} L^{-1} S_x;
+// trans = 1: the x rows of H <- L^{-T} U^{-T} H_x.
 __global__ void __launch_bounds__(BLK_THREADS) k_b_trsm(const BatchInst* __restrict__ I, const int2* __restrict__ cbs,
                                                         int trans) {
-  const int2 it = cbs[blockIdx.x];
+  cg::cluster_group cl = cg::this_cluster();
+  const int2 it = cbs[blockIdx.x / cl.num_blocks()];
   const BatchInst& B = I[it.x];
-  if (!B.active) return;
+  if (!B.active) return;   // the whole cluster leaves together, before any barrier
   double* X = (trans ? B.H : B.Zt) + (size_t)B.nu * B.ld;
-  auto bar = []() {
-    __syncthreads();
+  const int p = (int)cl.block_rank(), ks = (int)cl.num_blocks();
+  auto bar = [&]() {
+    cl.sync();
     return true;
   };
-  blk_solve(B.bkL, B.Lo_ci, trans ? B.Ut_val : B.Lo_val, trans ? B.D_Ut : B.D_L, X, B.Y, B.ld, B.nu, it.y, 0, 1, bar);
-  blk_solve(B.bkU, B.Up_ci, trans ? B.Lt_val : B.Up_val, trans ? B.D_Lt : B.D_U, X, B.Y, B.ld, B.nu, it.y, 0, 1, bar);
+  blk_solve(B.bkL, B.Lo_ci, trans ? B.Ut_val : B.Lo_val, trans ? B.D_Ut : B.D_L, X, B.Y, B.ld, B.nu, it.y, p, ks, bar);
+  blk_solve(B.bkU, B.Up_ci, trans ? B.Lt_val : B.Up_val, trans ? B.D_Lt : B.D_U, X, B.Y, B.ld, B.nu, it.y, p, ks, bar);
 }
 
 // One right-hand side (the Newton-step recovery): the same two phases, with a
@@ -1489,21 +1515,52 @@ int trsm_df_max_blocks() {
 namespace condipm {
 
 cudaError_t launch_batch_factor_post(cudaStream_t s, const BatchInst* I, int n, const int* boffF, int nbF,
-                                     int nsn_max) {
+                                     const int* boffD, int nbD) {
   if (n <= 0) return cudaSuccess;
   k_b_gather<<<nbF, 256, 0, s>>>(I, n, boffF);
   note_launch();
-  const int gx = std::max(1, std::min(64, (nsn_max * 32 + 127) / 128));
-  k_b_diag_inv<<<dim3(gx, 4 * n), 128, 0, s>>>(I);
+  k_b_diag_inv<<<nbD, 128, 0, s>>>(I, n, boffD);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans) {
+static cudaLaunchConfig_t trsm_cluster_config(int nclusters, int cl, cudaStream_t s, cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nclusters * cl);
+  cfg.blockDim = dim3(BLK_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans, int cl) {
   if (ncbs <= 0) return cudaSuccess;
-  k_b_trsm<<<ncbs, BLK_THREADS, 0, s>>>(I, cbs, trans);
+  if (cl > 8) {
+    cudaError_t e = allow_cluster16((const void*)k_b_trsm);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = trsm_cluster_config(ncbs, cl, s, at);
   note_launch();
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, k_b_trsm, I, cbs, trans);
+}
+
+int batch_trsm_clusters(int cl) {
+  if (cl > 8 && allow_cluster16((const void*)k_b_trsm) != cudaSuccess) return 0;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = trsm_cluster_config(1, cl, nullptr, at);
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k_b_trsm, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc;
 }
 
 }  // namespace condipm
