@@ -195,7 +195,7 @@ def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
     t00 = time.perf_counter()
     every = gridgen.batch96()
     nets = [every[i] for i in shard(len(every), rank, world)]
-    hs = [binding.Handle(n) for n in nets]
+    hs = [binding.Handle(n, route=binding.OPF_ROUTE_AUTO) for n in nets]
     t01 = time.perf_counter()
     b = binding.Batch(hs, nthreads=nthreads)
     b.autotune()
@@ -257,6 +257,19 @@ def run_batch(binding, nthreads, rank=0, world=1, dist=None, device=None):
            "condense_factor_all_instances_ms": {"batched": t_bcf * 1e3, "one_at_a_time": t_scf * 1e3,
                                                 "speedup": t_scf / t_bcf,
                                                 "all_pd": all(v == 0 for v in st)}}
+    # the condensation route each instance's autotuner picked, per size class
+    routes = {}
+    for n, h in zip(nets, hs):
+        r, ms = h.route_choice()
+        cls = routes.setdefault(str(n.nb), {"adjoint": 0, "explicit": 0, "ms_adjoint": [], "ms_explicit": []})
+        cls["adjoint" if r == 0 else "explicit"] += 1
+        cls["ms_adjoint"].append(ms["adjoint"])
+        cls["ms_explicit"].append(ms["explicit"])
+    for cls in routes.values():
+        cls["ms_adjoint"] = float(np.median(cls["ms_adjoint"]))
+        cls["ms_explicit"] = float(np.median(cls["ms_explicit"]))
+    out["route_autotune"] = routes
+    out["batch_tuning"] = b.stats()
     t03 = time.perf_counter()
     b.close()
     del hs

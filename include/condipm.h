@@ -67,6 +67,7 @@ typedef struct opf_network {
  * Kred = H_u + S_x^T H_x as a dense product (the route Sec. 3.3 calls naive). */
 #define OPF_ROUTE_ADJOINT  0
 #define OPF_ROUTE_EXPLICIT 1
+#define OPF_ROUTE_AUTO     2   /* time both on the first opf_condense, keep the faster */
 
 typedef struct opf_options {
     int route;            /* OPF_ROUTE_*                                               */
@@ -130,6 +131,10 @@ int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);
  * dataflow form at 152, 304 CTAs with a large panel group} (0 = not tried). */
 #define OPF_CHOL_CANDIDATES 9
 int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms);
+/* Condensation route in use (host outputs, may be NULL): *route as in
+ * opf_options.route (-1: OPF_ROUTE_AUTO before its first opf_condense), ms[2]
+ * the AUTO timings of {adjoint, explicit} (0 = not timed). */
+int opf_route_choice(const opf_handle* h, int* route, float* ms);
 /* Stream for all device work (a cudaStream_t, NULL = legacy default stream). */
 int opf_set_stream(opf_handle* h, void* stream);
 

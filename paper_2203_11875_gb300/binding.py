@@ -22,6 +22,7 @@ OPF_ERR_PF_FAILED = -5
 OPF_ERR_TIMEOUT = -6
 OPF_ROUTE_ADJOINT = 0
 OPF_ROUTE_EXPLICIT = 1
+OPF_ROUTE_AUTO = 2
 OPF_VEC_F, OPF_VEC_G, OPF_VEC_H, OPF_VEC_GRADF = 0, 1, 2, 3
 OPF_MAT_G, OPF_MAT_A, OPF_MAT_W, OPF_MAT_K = 0, 1, 2, 3
 
@@ -67,6 +68,7 @@ _SIGS = {
     "opf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float), _ip]),
     "opf_chol_choice": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_float)]),
+    "opf_route_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_eval_functions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_get_vector": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -263,6 +265,14 @@ class Handle:
         names = ("barrier38", "barrier76", "barrier152", "barrier304", "dataflow76", "dataflow152", "dataflow304",
                  "dataflow152_wide_panel", "dataflow304_wide_panel")
         return f.value, nb.value, dict(zip(names, ms))
+
+    def route_choice(self):
+        """(route in use: 0 adjoint, 1 explicit, -1 auto before its first
+        condensation; {"adjoint": ms, "explicit": ms} of the AUTO timing)."""
+        r = C.c_int()
+        ms = (C.c_float * 2)()
+        _check(self._lib.opf_route_choice(self._h, C.byref(r), ms), "opf_route_choice")
+        return r.value, {"adjoint": ms[0], "explicit": ms[1]}
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""

@@ -836,17 +836,14 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
 
 // A7 on the current K and Z = [I; S_x]: H = K Z, then Kred by the handle's route
 // (the x rows of H end up holding Psi = G_x^{-T} H_x on the adjoint route)
-static int reduce_async(opf_handle* h) {
+static int reduce_route(opf_handle* h, int route) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
-  const int nu = P.nu, nx = P.nx, nw = P.nw;
+  const int nu = P.nu, nx = P.nx;
   const long long ld = h->ldp;
   double* Sx = h->Zt + (size_t)nu * ld;
-  ph_begin(h, OPF_PHASE_SPMM);
-  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, ld, 1, h->H, ld, 1, nu, 1.0, 0.0));
-  ph_end(h);
   double* Hx = h->H + (size_t)nu * ld;
-  if (h->opt.route == OPF_ROUTE_EXPLICIT) {
+  if (route == OPF_ROUTE_EXPLICIT) {
     ph_begin(h, OPF_PHASE_KRED);
     CK(launch_dense_tn(s, nu, nx, Sx, Hx, h->H, ld, h->F));
     CK(launch_symmetrize(s, nu, h->F, nu, 1, h->Kred));
@@ -859,6 +856,36 @@ static int reduce_async(opf_handle* h) {
     CK(launch_symmetrize(s, nu, h->H, ld, 1, h->Kred));
     ph_end(h);
   }
+  return OPF_OK;
+}
+
+// A7 on the current K and Z = [I; S_x]: H = K Z, then Kred by the handle's route
+// (the x rows of H end up holding Psi = G_x^{-T} H_x on the adjoint route).  With
+// OPF_ROUTE_AUTO the first call times both routes on this network (the explicit
+// one first: it leaves H intact) and keeps the faster; the adjoint route's
+// result stands for that call.
+static int reduce_async(opf_handle* h) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nw = P.nw;
+  const long long ld = h->ldp;
+  ph_begin(h, OPF_PHASE_SPMM);
+  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, ld, 1, h->H, ld, 1, nu, 1.0, 0.0));
+  ph_end(h);
+  if (h->route >= 0) return reduce_route(h, h->route);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], s));
+  TRY(reduce_route(h, OPF_ROUTE_EXPLICIT));
+  CK(cudaEventRecord(ev[1], s));
+  TRY(reduce_route(h, OPF_ROUTE_ADJOINT));
+  CK(cudaEventRecord(ev[2], s));
+  CK(cudaEventSynchronize(ev[2]));
+  CK(cudaEventElapsedTime(&h->route_ms[OPF_ROUTE_EXPLICIT], ev[0], ev[1]));
+  CK(cudaEventElapsedTime(&h->route_ms[OPF_ROUTE_ADJOINT], ev[1], ev[2]));
+  for (auto& e : ev) cudaEventDestroy(e);
+  h->route = h->route_ms[OPF_ROUTE_EXPLICIT] < h->route_ms[OPF_ROUTE_ADJOINT] ? OPF_ROUTE_EXPLICIT : OPF_ROUTE_ADJOINT;
+  h->psi_last_adjoint = true;
   return OPF_OK;
 }
 
@@ -886,11 +913,12 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
   if (h->trsm_mode < 0) TRY(autotune_trsm(h, Sx, ld));
   TRY(lu_solve_perm(h, 0, Sx, ld, 1, nu, true));
+  h->psi_last_adjoint = false;
   TRY(reduce_async(h));
   h->have_condense = true;
   h->have_factor = false;
   h->sens_ready = false;
-  h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
+  h->psi_valid = h->route != OPF_ROUTE_EXPLICIT || h->psi_last_adjoint;
   return OPF_OK;
 }
 
@@ -913,9 +941,10 @@ int recondense_dc(opf_handle* h, double delta_c) {
   CK(launch_assemble_K(s, P.K.nnz(), h->Wval, h->KAA_ptr, h->KAA_r, h->KAA_a, h->KAA_b, sig, h->Aval, h->Kval));
   CK(launch_add_diag_c(s, P.nw, h->K_diag, h->sig_c, h->Kval));
   ph_end(h);
+  h->psi_last_adjoint = false;
   TRY(reduce_async(h));
   h->delta_c = delta_c;
-  h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
+  h->psi_valid = h->route != OPF_ROUTE_EXPLICIT || h->psi_last_adjoint;
   return OPF_OK;
 }
 
@@ -1060,10 +1089,11 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
   opf_handle* h = new (std::nothrow) opf_handle();
   if (!h) return OPF_ERR_OOM;
   if (opt) h->opt = *opt;
-  if (h->opt.route != OPF_ROUTE_ADJOINT && h->opt.route != OPF_ROUTE_EXPLICIT) {
+  if (h->opt.route != OPF_ROUTE_ADJOINT && h->opt.route != OPF_ROUTE_EXPLICIT && h->opt.route != OPF_ROUTE_AUTO) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
+  h->route = h->opt.route == OPF_ROUTE_AUTO ? -1 : h->opt.route;
   h->spin_limit = h->opt.spin_limit > 0 ? h->opt.spin_limit : (1LL << 26);
   std::string err = build_plan(h->P, net->nb, net->nl, net->ng, net->slack, net->Pd, net->Qd, net->Vmin,
                                net->Vmax, net->lf, net->lt, net->r, net->x, net->b, net->rate, net->gbus,
@@ -1095,6 +1125,13 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return rc;
   }
   *out = h;
+  return OPF_OK;
+}
+
+int opf_route_choice(const opf_handle* h, int* route, float* ms) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (route) *route = h->route;
+  if (ms) { ms[0] = h->route_ms[0]; ms[1] = h->route_ms[1]; }
   return OPF_OK;
 }
 

@@ -173,7 +173,7 @@ extern "C" int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm
     // one host thread per instance; the loops meet at every condensation, which
     // one batched call serves (instances that have finished are masked)
     for (opf_handle* h : b->hs)
-      if (h->opt.route != OPF_ROUTE_ADJOINT) return OPF_ERR_INVALID_ARG;
+      if (h->opt.route == OPF_ROUTE_EXPLICIT) return OPF_ERR_INVALID_ARG;
     {
       std::lock_guard<std::mutex> lk(b->mu);
       b->active = n;
@@ -246,7 +246,7 @@ int dev_upload(opf_batch* b, T** dst, const std::vector<T>& v) {
 int batch_setup(opf_batch* b) {
   const int n = int(b->hs.size());
   for (opf_handle* h : b->hs)
-    if (h->opt.route != OPF_ROUTE_ADJOINT) return OPF_ERR_INVALID_ARG;
+    if (h->opt.route == OPF_ROUTE_EXPLICIT) return OPF_ERR_INVALID_ARG;
   // refactorisation rows: level by level, instances in order within a level
   std::vector<int2> items;
   int maxlev = 0;

@@ -240,7 +240,8 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
     h->have_factor = rc == OPF_OK;
     return rc;
   }
-  const bool graph_ok = h->use_graphs && !h->cf_failed && !h->profiling && h->trsm_mode >= 0 && h->chol_tuned;
+  const bool graph_ok = h->use_graphs && !h->cf_failed && !h->profiling && h->trsm_mode >= 0 && h->chol_tuned &&
+                        h->route >= 0;
   if (graph_ok && !h->cf_exec) {
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -267,7 +268,7 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
     // the host-side state the enqueued sequence stands for
     h->have_lu = true;
     h->have_condense = true;
-    h->psi_valid = h->opt.route != OPF_ROUTE_EXPLICIT;
+    h->psi_valid = h->route != OPF_ROUTE_EXPLICIT;
     h->sens_ready = false;
     h->finv_valid = false;
     h->delta_w = 0.0;

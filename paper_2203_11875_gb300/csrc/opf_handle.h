@@ -120,6 +120,11 @@ struct opf_handle {
   cudaGraphExec_t cf_exec = nullptr;
   bool cf_failed = false;        // capture or instantiation was refused: plain launches
   bool use_graphs = true;
+  // condensation route in use: the option, or with OPF_ROUTE_AUTO the faster one
+  // on the first condensation (-1 until then), and the two timings
+  int route = -1;
+  float route_ms[2] = {0.f, 0.f};
+  bool psi_last_adjoint = false;   // the last condensation ended with the adjoint route's Psi
   // set while a lockstep batch solve runs this handle's loop: its condensation
   // and first Cholesky attempt go through the batch's rendezvous
   opf_batch* batch = nullptr;

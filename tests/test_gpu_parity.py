@@ -123,6 +123,34 @@ def test_condense_at_oracle_iterate(pkg, name, route):
 
 
 @pytest.mark.parametrize("name", ["ring30", "grid2000"])
+def test_route_autotune(pkg, name):
+    """OPF_ROUTE_AUTO times the explicit and the adjoint route on the first
+    condensation and keeps the faster; Kred and the step are right on the
+    tuning call and on the next one with the pick."""
+    net, rec = oracle_iterate(name)
+    lay = model.Layout(net)
+    h = pkg.Handle(net, route=pkg.OPF_ROUTE_AUTO)
+    assert h.route_choice()[0] == -1
+    _, G, A = model.jacobians(lay, rec["w"])
+    W = model.lagrangian_hessian(lay, rec["w"], rec["lam"], rec["y"])
+    sw, ss, delta = rec["sig_w"], rec["sig_s"], rec["delta"]
+    Ko = kkt.kred_definition(G, A, W, sw, ss, lay.nu)
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, delta), np.zeros(lay.nx)])
+    ref = np.concatenate(kkt.full_space_step(G, A, Wd, sw, ss, rec["r"]))
+    for call in range(2):
+        gpu_eval(pkg, h, lay, rec["w"], rec["lam"], rec["y"])
+        K = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
+        h.condense(T(sw[:lay.nu]), T(sw[lay.nu:]), T(ss), K)
+        route, ms = h.route_choice()
+        assert route in (0, 1) and ms["adjoint"] > 0 and ms["explicit"] > 0
+        assert rel_err(N(K).reshape(lay.nu, lay.nu), Ko) <= TOL_KRED
+        assert h.kkt_factor(delta) == -1
+        step = torch.zeros(len(rec["r"]), dtype=torch.float64, device="cuda")
+        h.kkt_solve(T(rec["r"]), step)
+        assert rel_err(N(step), ref) <= TOL_KRED, call
+
+
+@pytest.mark.parametrize("name", ["ring30", "grid2000"])
 def test_rhs_block_and_route_invariance(pkg, name):
     """Kred does not depend on the multi-RHS solve kernel (staged with 1, 2, 4
     columns per CTA, column-parallel, level-blocked and its dataflow form; ragged
