@@ -31,6 +31,17 @@ THETA_MU = 1.5
 ETA = 1e-4
 KAPPA_SIGMA = 1e10
 
+# filter line search (Wachter and Biegler 2006, their recommended constants)
+GAMMA_THETA = 1e-5
+GAMMA_PHI = 1e-8
+SWITCH_DELTA = 1.0
+S_THETA = 1.1
+S_PHI = 2.3
+ETA_PHI = 1e-4
+GAMMA_ALPHA = 0.05
+KAPPA_SOC = 0.99
+SOC_MAX = 4
+
 
 @dataclasses.dataclass
 class Result:
@@ -48,6 +59,7 @@ class Result:
     sig_s: np.ndarray = None
     err: float = np.inf
     history: list = dataclasses.field(default_factory=list)
+    soc_steps: int = 0          # accepted second-order corrections (filter line search)
 
 
 def _push(v, lo, hi, k1=1e-2, k2=1e-2):
@@ -126,6 +138,47 @@ def _opt_error(dual, primal, compl, mults, smax=100.0):
     return e
 
 
+class Filter:
+    """The filter: pairs (theta_l, phi_l); a point (theta, phi) is acceptable when
+    no pair dominates it, i.e. theta < theta_l or phi < phi_l for every pair.
+    It starts as the half-plane theta >= theta_max (the pair (theta_max, -inf))."""
+
+    def __init__(self, theta_max):
+        self.pairs = [(theta_max, -np.inf)]
+
+    def acceptable(self, theta, phi):
+        return all(theta < tl or phi < pl for tl, pl in self.pairs)
+
+    def add(self, theta, phi):
+        self.pairs.append((theta, phi))
+
+
+def filter_accepts(filt, theta0, phi0, dphi, alpha, theta_t, phi_t, theta_min):
+    """Acceptance of a trial point (theta_t, phi_t) reached with step length
+    alpha from (theta0, phi0), dphi the directional derivative of the barrier
+    objective.  Returns (accepted, phi_type): with the switching condition
+    alpha (-dphi)^s_phi > delta theta0^s_theta (dphi < 0) and theta0 <=
+    theta_min the step must satisfy the Armijo condition on phi (a phi-type
+    step, the filter is not augmented); otherwise sufficient decrease in theta
+    or phi against the current point."""
+    if not filt.acceptable(theta_t, phi_t):
+        return False, False
+    switching = dphi < 0 and alpha * (-dphi) ** S_PHI > SWITCH_DELTA * theta0 ** S_THETA
+    if switching and theta0 <= theta_min:
+        return phi_t <= phi0 + ETA_PHI * alpha * dphi, True
+    return (theta_t <= (1.0 - GAMMA_THETA) * theta0 or phi_t <= phi0 - GAMMA_PHI * theta0), False
+
+
+def filter_alpha_min(theta0, dphi, theta_min):
+    """Smallest step length the filter line search tries before it gives up."""
+    if dphi < 0:
+        a = min(GAMMA_THETA, GAMMA_PHI * theta0 / -dphi)
+        if theta0 <= theta_min:
+            a = min(a, SWITCH_DELTA * theta0 ** S_THETA / (-dphi) ** S_PHI)
+        return GAMMA_ALPHA * a
+    return GAMMA_ALPHA * GAMMA_THETA
+
+
 def _regularized(step_fn, delta_last):
     """Inertia correction: delta_w = 0, then 1e-4 (or delta_last/3) x 8 until PD."""
     out = step_fn(0.0)
@@ -140,10 +193,83 @@ def _regularized(step_fn, delta_last):
     raise RuntimeError("inertia correction failed")
 
 
+def _filter_search(lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, zwu, zsl, zsu, mu, tau,
+                   pw, ps, plam, py, delta, theta_min, stats):
+    """Filter line search with second-order corrections along the condensed
+    step (Wachter and Biegler 2006, Algorithm A, steps A-5 to A-8).  theta is the
+    l1 norm of c = [g; h + s], phi the barrier objective.  When the step length
+    falls below alpha_min the step is shortened by a larger primal
+    regularization and the search starts again (in place of the restoration
+    phase).  Returns the primal-dual step, its primal and bound-multiplier
+    lengths, the bound-multiplier steps and the delta_w in use."""
+    nw, m = lay.nw, lay.m
+
+    def cons(wt, st):
+        return np.concatenate([model.cons_g(lay, wt), model.cons_h(lay, wt) + st])
+
+    def phi(wt, st):
+        return model.objective(lay, wt) + bw.barrier(wt, mu) + bs.barrier(st, mu)
+
+    gf = model.jacobians(lay, w)[0]
+    c0 = cons(w, s)
+    theta0, phi0 = np.abs(c0).sum(), phi(w, s)
+    for attempt in range(40):
+        dphi = (gf + bw.barrier_grad(w, mu)) @ pw + bs.barrier_grad(s, mu) @ ps
+        amax = min(bw.max_step(w, pw, tau), bs.max_step(s, ps, tau))
+        amin = filter_alpha_min(theta0, dphi, theta_min)
+        a, accepted, phi_type, pw_acc, ps_acc = amax, False, False, pw, ps
+        while a >= amin and not accepted:
+            wt, st = w + a * pw, s + a * ps
+            ct = cons(wt, st)
+            theta_t, phi_t = np.abs(ct).sum(), phi(wt, st)
+            accepted, phi_type = filter_accepts(filt, theta0, phi0, dphi, a, theta_t, phi_t, theta_min)
+            if not accepted and a == amax and theta_t >= theta0:
+                # second-order corrections: the constraint part of the right-hand
+                # side becomes c_soc = a c(x) + c(x + a d), accumulated
+                c_soc, theta_prev = a * c0 + ct, theta0
+                for _ in range(SOC_MAX):
+                    r_soc = r.copy()
+                    r_soc[nw + m:] = c_soc
+                    qw, qs, _, _, _, ok = kkt.condensed_step(G, A, W, sig_w, sig_s, r_soc, nu, delta_w=delta)
+                    if not ok:
+                        break
+                    a_soc = min(bw.max_step(w, qw, tau), bs.max_step(s, qs, tau))
+                    w_soc, s_soc = w + a_soc * qw, s + a_soc * qs
+                    c_new = cons(w_soc, s_soc)
+                    theta_soc, phi_soc = np.abs(c_new).sum(), phi(w_soc, s_soc)
+                    accepted, phi_type = filter_accepts(filt, theta0, phi0, dphi, a, theta_soc, phi_soc, theta_min)
+                    if accepted:
+                        pw_acc, ps_acc = a_soc * qw / a, a_soc * qs / a   # so that w + a pw_acc = w_soc
+                        stats["soc"] += 1
+                        break
+                    if theta_soc > KAPPA_SOC * theta_prev:
+                        break
+                    theta_prev, c_soc = theta_soc, a_soc * c_soc + c_new
+            if not accepted:
+                a *= 0.5
+        if accepted:
+            if not phi_type:
+                filt.add((1.0 - GAMMA_THETA) * theta0, phi0 - GAMMA_PHI * theta0)
+            dzwl, dzwu = bw.dz(w, zwl, zwu, pw, mu)
+            dzsl, dzsu = bs.dz(s, zsl, zsu, ps, mu)
+            az = min(_max_step_z(zwl, dzwl, bw.fl, tau), _max_step_z(zwu, dzwu, bw.fu, tau),
+                     _max_step_z(zsl, dzsl, bs.fl, tau), _max_step_z(zsu, dzsu, bs.fu, tau))
+            return pw_acc, ps_acc, plam, py, a, az, dzwl, dzwu, dzsl, dzsu, delta
+        # out of step length: shorten the step by a larger primal regularization
+        delta = max(1e-8, 10.0 * delta)
+        pw, ps, plam, py, Kc, ok = kkt.condensed_step(G, A, W, sig_w, sig_s, r, nu, delta_w=delta)
+        if not ok:
+            (pw, ps, plam, py, Kc, ok), delta = _regularized(
+                lambda d: kkt.condensed_step(G, A, W, sig_w, sig_s, r, nu, delta_w=d), delta)
+    raise RuntimeError("filter line search failed")
+
+
 # ------------------------------------------------------------------ LinRed
-def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False):
+def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, line_search="merit"):
     """Algorithm 1.  record_at: iteration index whose iterate (and the step
-    inputs) is stored in Result.history as a dict."""
+    inputs) is stored in Result.history as a dict.  line_search: "merit"
+    (l1 exact-penalty backtracking) or "filter" (filter line search with
+    second-order corrections)."""
     lay = model.Layout(net)
     nu, nx, m, nw = lay.nu, lay.nx, lay.m, lay.nw
     bw = _Bounds(lay.wl, lay.wu)
@@ -158,6 +284,11 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False):
     nu_pen = 1.0
     delta = 0.0
     hist = []
+    theta_init = np.abs(model.cons_g(lay, w)).sum() + np.abs(model.cons_h(lay, w) + s).sum()
+    theta_max = 1e4 * max(1.0, theta_init)
+    theta_min = 1e-4 * max(1.0, theta_init)
+    filt, filt_mu = None, None
+    stats = {"soc": 0}
     for it in range(max_iter + 1):
         gf, G, A = model.jacobians(lay, w)
         g = model.cons_g(lay, w)
@@ -174,7 +305,7 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False):
                   f"inf_pr {np.abs(primal).max():.2e} delta {delta:.1e}")
         if err0 <= tol:
             return Result("converged", it, float(model.objective(lay, w)), w, s, lam, y,
-                          (zwl, zsl), (zwu, zsu), mu, err=err0, history=hist)
+                          (zwl, zsl), (zwu, zsu), mu, err=err0, history=hist, soc_steps=stats["soc"])
         if it == max_iter:
             break
         while True:
@@ -195,7 +326,13 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False):
                              sig_w=sig_w.copy(), sig_s=sig_s.copy(), r=r.copy(), mu=mu,
                              delta=delta, pw=pw, ps=ps, plam=plam, py=py, Kc=Kc))
         phi0 = None
-        for attempt in range(40):
+        if line_search == "filter":
+            if filt is None or filt_mu != mu:      # a new barrier problem: a new filter
+                filt, filt_mu = Filter(theta_max), mu
+            pw, ps, plam, py, a, az, dzwl, dzwu, dzsl, dzsu, delta = _filter_search(
+                lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, zwu, zsl, zsu, mu, tau,
+                pw, ps, plam, py, delta, theta_min, stats)
+        for attempt in range(40 if line_search == "merit" else 0):
             dzwl, dzwu = bw.dz(w, zwl, zwu, pw, mu)
             dzsl, dzsu = bs.dz(s, zsl, zsu, ps, mu)
             amax = min(bw.max_step(w, pw, tau), bs.max_step(s, ps, tau))

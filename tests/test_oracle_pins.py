@@ -348,3 +348,56 @@ def test_reduced_derivatives_through_projection():
     assert np.abs(gl - grad0).max() <= 1e-10 * np.abs(gl).max()
     assert np.abs(lam_l - lam).max() <= 1e-10 * np.abs(lam).max()
     assert np.abs(W_hat - Hfd).max() <= 1e-5 * np.abs(W_hat).max()
+
+
+# ------------------------------------------------------------- the filter
+def test_filter_rules():
+    """The filter's dominance test and the acceptance rules of the filter line
+    search (Wachter and Biegler 2006, Sec. 2.3), on hand-made values."""
+    F = ipm.Filter(10.0)
+    assert not F.acceptable(10.0, -1e30) and F.acceptable(9.9, 1e30)   # the initial half-plane
+    F.add(5.0, 3.0)
+    assert not F.acceptable(6.0, 4.0) and not F.acceptable(5.0, 3.0)   # dominated, boundary included
+    assert F.acceptable(6.0, 2.9) and F.acceptable(4.9, 100.0)
+    G = ipm.Filter(1e4)
+    # no switching (dphi >= 0): sufficient decrease in theta or in phi
+    assert ipm.filter_accepts(G, 1.0, 0.0, 0.5, 1.0, 1.0 - 2e-5, 1.0, 1e-4) == (True, False)
+    assert ipm.filter_accepts(G, 1.0, 0.0, 0.5, 1.0, 1.0, -2e-8, 1e-4) == (True, False)
+    assert ipm.filter_accepts(G, 1.0, 0.0, 0.5, 1.0, 1.0, 0.0, 1e-4) == (False, False)
+    # switching (alpha (-dphi)^2.3 > theta^1.1) with theta <= theta_min: Armijo on phi only
+    th = 1e-6
+    assert ipm.filter_accepts(G, th, 0.0, -1.0, 1.0, th, -1e-4 * 0.99, 1e-4) == (False, True)
+    assert ipm.filter_accepts(G, th, 0.0, -1.0, 1.0, th, -1e-4 * 1.01, 1e-4) == (True, True)
+    # alpha_min: gamma_alpha gamma_theta without a descent direction
+    assert abs(ipm.filter_alpha_min(1.0, 0.5, 1e-4) - 0.05 * 1e-5) <= 1e-20
+
+
+def _counted_loads(net, scale):
+    n = net.copy()
+    n.Pd, n.Qd = scale * net.Pd, scale * net.Qd
+    return n
+
+
+@pytest.mark.parametrize("case", ["tiny3", "ring30", "lossless", "tiny3_loaded"])
+def test_filter_line_search_reaches_the_pinned_optima(case):
+    """The filter variant of the loop reaches the optimum the merit variant is
+    pinned to: the same objective on tiny3 and ring30 (KKT tolerance 1e-8),
+    the economic-dispatch closed form on the lossless network, and on tiny3
+    with loads scaled by 1.3 -- a case whose first trial step raises the
+    constraint violation -- through an accepted second-order correction."""
+    if case == "lossless":
+        net = gridgen.lossless(gridgen.ring30())
+        res = ipm.linred(net, line_search="filter", max_iter=80)
+        assert res.err <= 1e-6
+        ed = _economic_dispatch(net)
+        assert abs(res.obj - ed) <= 1e-8 * abs(ed)
+        return
+    net = _counted_loads(gridgen.tiny3(), 1.3) if case == "tiny3_loaded" else getattr(gridgen, case)()
+    res = ipm.linred(net, line_search="filter")
+    ref = ipm.linred(net)
+    assert res.status == ref.status == "converged"
+    assert abs(res.obj - ref.obj) <= 1e-8 * abs(ref.obj)
+    lay = model.Layout(net)
+    assert np.abs(model.cons_g(lay, res.w)).max() <= 1e-8
+    if case == "tiny3_loaded":
+        assert res.soc_steps >= 1
