@@ -260,7 +260,16 @@ typedef struct opf_ipm_options {
     double mu0;        /* initial barrier parameter                                 */
     double pf_tol;     /* Newton-Raphson tolerance of the RedLin projection (1e-10) */
     int verbose;       /* print one line per iteration to stdout                    */
+    int line_search;   /* OPF_LINESEARCH_MERIT: backtracking on the l1 exact-penalty
+                          merit function; OPF_LINESEARCH_FILTER (LinRed only): the
+                          filter line search with second-order corrections of
+                          Wachter and Biegler (2006), the Ipopt algorithm Sec. 4.3
+                          defers to (no restoration phase: when the step length
+                          runs out, a larger primal regularisation shortens the
+                          step)                                                   */
 } opf_ipm_options;
+#define OPF_LINESEARCH_MERIT  0
+#define OPF_LINESEARCH_FILTER 1
 
 typedef struct opf_ipm_result {
     int status;        /* OPF_OK, OPF_ERR_NO_CONVERGENCE, or the failing call's code */
@@ -270,6 +279,7 @@ typedef struct opf_ipm_result {
     double ms_total, ms_eval, ms_condense, ms_factor, ms_solve, ms_linesearch, ms_pf;  /* host wall */
     int graph_iters;   /* iterations whose condensation + first Cholesky attempt ran as
                           a replayed CUDA graph (needs a non-default stream)           */
+    int soc_steps;     /* accepted second-order corrections (filter line search)      */
 } opf_ipm_result;
 
 /* Solve the OPF of the handle's network from the flat start (theta = 0, Vm = 1 at

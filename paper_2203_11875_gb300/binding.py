@@ -45,14 +45,15 @@ class opf_options(C.Structure):
 
 class opf_ipm_options(C.Structure):
     _fields_ = [("variant", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("mu0", C.c_double),
-                ("pf_tol", C.c_double), ("verbose", C.c_int)]
+                ("pf_tol", C.c_double), ("verbose", C.c_int), ("line_search", C.c_int)]
 
 
 class opf_ipm_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("obj", C.c_double), ("err", C.c_double),
                 ("mu", C.c_double), ("n_factor", C.c_int), ("ms_total", C.c_double), ("ms_eval", C.c_double),
                 ("ms_condense", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
-                ("ms_linesearch", C.c_double), ("ms_pf", C.c_double), ("graph_iters", C.c_int)]
+                ("ms_linesearch", C.c_double), ("ms_pf", C.c_double), ("graph_iters", C.c_int),
+                ("soc_steps", C.c_int)]
 
 
 OPF_LINRED, OPF_REDLIN = 0, 1
@@ -344,10 +345,12 @@ class Handle:
         _check(self._lib.opf_kkt_solve_adjoint(self._h, _ptr(rhs), _ptr(sol), int(nrhs)),
                "opf_kkt_solve_adjoint")
 
-    def solve(self, variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False):
-        """opf_solve: the interior-point loop; returns the result fields as a dict."""
+    def solve(self, variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
+              line_search="merit"):
+        """opf_solve: the interior-point loop; returns the result fields as a dict.
+        line_search: "merit" or "filter" (LinRed)."""
         o = opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
-                            int(bool(verbose)))
+                            int(bool(verbose)), 1 if line_search == "filter" else 0)
         r = opf_ipm_result()
         rc = self._lib.opf_solve(self._h, C.byref(o), C.byref(r))
         out = {f: getattr(r, f) for f, _ in opf_ipm_result._fields_}
@@ -419,9 +422,10 @@ class Handle:
         return it.value
 
 
-def _ipm_options(variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False):
+def _ipm_options(variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
+                 line_search="merit"):
     return opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
-                           int(bool(verbose)))
+                           int(bool(verbose)), 1 if line_search == "filter" else 0)
 
 
 class Batch:

@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <utility>
 #include <vector>
 
 #include "../../include/condipm.h"
@@ -32,6 +33,45 @@ namespace {
 
 constexpr double TAU_MIN = 0.99, KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5, ETA = 1e-4;
 constexpr double KAPPA_SIGMA = 1e10, SMAX = 100.0;
+// filter line search (Wachter and Biegler 2006, their recommended constants)
+constexpr double GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-8, SWITCH_DELTA = 1.0, S_THETA = 1.1, S_PHI = 2.3;
+constexpr double ETA_PHI = 1e-4, GAMMA_ALPHA = 0.05, KAPPA_SOC = 0.99;
+constexpr int SOC_MAX = 4;
+
+// The filter: a trial (theta, phi) is acceptable when no pair (theta_l, phi_l)
+// has theta >= theta_l and phi >= phi_l.  It starts as theta >= theta_max.
+struct Filter {
+  std::vector<std::pair<double, double>> pairs;
+  void reset(double theta_max) { pairs.assign(1, {theta_max, -INFINITY}); }
+  bool acceptable(double theta, double phi) const {
+    for (const auto& p : pairs)
+      if (theta >= p.first && phi >= p.second) return false;
+    return true;
+  }
+};
+
+// acceptance of a trial point reached with step length a (Sec. 2.3 of the
+// filter method): returns accepted, sets phi_type for Armijo (phi-type) steps
+bool filter_accepts(const Filter& F, double theta0, double phi0, double dphi, double a, double theta_t,
+                    double phi_t, double theta_min, bool& phi_type) {
+  phi_type = false;
+  if (!std::isfinite(phi_t) || !F.acceptable(theta_t, phi_t)) return false;
+  const bool switching = dphi < 0 && a * std::pow(-dphi, S_PHI) > SWITCH_DELTA * std::pow(theta0, S_THETA);
+  if (switching && theta0 <= theta_min) {
+    phi_type = true;
+    return phi_t <= phi0 + ETA_PHI * a * dphi;
+  }
+  return theta_t <= (1.0 - GAMMA_THETA) * theta0 || phi_t <= phi0 - GAMMA_PHI * theta0;
+}
+
+double filter_alpha_min(double theta0, double dphi, double theta_min) {
+  if (dphi < 0) {
+    double a = std::min(GAMMA_THETA, GAMMA_PHI * theta0 / -dphi);
+    if (theta0 <= theta_min) a = std::min(a, SWITCH_DELTA * std::pow(theta0, S_THETA) / std::pow(-dphi, S_PHI));
+    return GAMMA_ALPHA * a;
+  }
+  return GAMMA_ALPHA * GAMMA_THETA;
+}
 
 using Vec = std::vector<double>;
 
@@ -321,6 +361,13 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   for (int i = 0; i < m; ++i) { zsl[i] = bs.fl[i] ? 1.0 : 0.0; zsu[i] = bs.fu[i] ? 1.0 : 0.0; }
   double mu = o.mu0, nu_pen = 1.0, delta = 0.0, err0 = 1e300;
   Vec grad(nw), gradf(nw), sw, ss, r(nkkt), step(nkkt), dzwl, dzwu, dzsl, dzsu;
+  // filter line search: theta_max / theta_min from the starting point's violation
+  double theta_init = 0.0;
+  for (double v : g) theta_init += std::fabs(v);
+  for (int i = 0; i < m; ++i) theta_init += std::fabs(hv[i] + s[i]);
+  const double theta_max = 1e4 * std::max(1.0, theta_init), theta_min = 1e-4 * std::max(1.0, theta_init);
+  Filter filt;
+  double filt_mu = -1.0;
   const auto t_start = clk::now();
   int it = 0;
   R.status = OPF_ERR_NO_CONVERGENCE;
@@ -423,18 +470,82 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
       t0 = clk::now();
       a = amax;
       Vec wt(nw), st2(m);
-      while (a > 1e-4 * amax) {
-        for (int i = 0; i < nw; ++i) wt[i] = w[i] + a * pw[i];
-        for (int i = 0; i < m; ++i) st2[i] = s[i] + a * ps[i];
-        double ft;
-        Vec gt, ht;
-        TRYD(eval_fgh(h, d, wt, ft, gt, ht));
-        double c1 = 0.0;
-        for (double v : gt) c1 += std::fabs(v);
-        for (int i = 0; i < m; ++i) c1 += std::fabs(ht[i] + st2[i]);
-        const double phit = ft + bw.barrier(wt, mu) + bs.barrier(st2, mu) + nu_pen * c1;
-        if (std::isfinite(phit) && phit <= phi0 + ETA * a * std::min(dphi, 0.0)) { accepted = true; break; }
-        a *= 0.5;
+      if (o.line_search == OPF_LINESEARCH_FILTER) {
+        // filter line search with second-order corrections (the l1 merit values
+        // above are not used); theta0 = |c|_1 at the current point
+        if (filt_mu != mu) { filt.reset(theta_max); filt_mu = mu; }
+        const double theta0 = pl1, ph0 = f + bw.barrier(w, mu) + bs.barrier(s, mu);
+        double dph = 0.0;
+        for (int i = 0; i < nw; ++i) dph += (gradf[i] + bw.bgrad(w, i, mu)) * pw[i];
+        for (int i = 0; i < m; ++i) dph += bs.bgrad(s, i, mu) * ps[i];
+        const double amin = filter_alpha_min(theta0, dph, theta_min);
+        bool phi_type = false;
+        auto trial = [&](const Vec& wv, const Vec& sv, double& theta, double& phi, Vec& c) -> int {
+          double ft;
+          Vec gt, ht;
+          TRYD(eval_fgh(h, d, wv, ft, gt, ht));
+          c.resize(nx + m);
+          theta = 0.0;
+          for (int i = 0; i < nx; ++i) { c[i] = gt[i]; theta += std::fabs(gt[i]); }
+          for (int i = 0; i < m; ++i) { c[nx + i] = ht[i] + sv[i]; theta += std::fabs(c[nx + i]); }
+          phi = ft + bw.barrier(wv, mu) + bs.barrier(sv, mu);
+          return OPF_OK;
+        };
+        while (a >= amin && !accepted) {
+          for (int i = 0; i < nw; ++i) wt[i] = w[i] + a * pw[i];
+          for (int i = 0; i < m; ++i) st2[i] = s[i] + a * ps[i];
+          double tht, pht;
+          Vec ct;
+          TRYD(trial(wt, st2, tht, pht, ct));
+          accepted = filter_accepts(filt, theta0, ph0, dph, a, tht, pht, theta_min, phi_type);
+          if (!accepted && a == amax && tht >= theta0) {
+            // second-order corrections: the constraint part of the right-hand side
+            // becomes c_soc = a c(x) + c(x + a d), accumulated; the factors are reused
+            Vec csoc(nx + m);
+            for (int i = 0; i < nx + m; ++i) csoc[i] = a * r[nw + m + i] + ct[i];
+            double th_prev = theta0;
+            Vec rs = r, q(nkkt), ws(nw), ssoc(m), cn;
+            for (int k = 0; k < SOC_MAX && !accepted; ++k) {
+              std::copy(csoc.begin(), csoc.end(), rs.begin() + nw + m);
+              TRYD(h2d(h->s, d.rhs, rs.data(), nkkt));
+              TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
+              TRYD(d2h(h->s, q.data(), d.step, nkkt));
+              CKD(cudaStreamSynchronize(h->s));
+              Vec qw(q.begin(), q.begin() + nw), qs(q.begin() + nw, q.begin() + nw + m);
+              const double asoc = std::min(bw.max_step(w, qw, tau), bs.max_step(s, qs, tau));
+              for (int i = 0; i < nw; ++i) ws[i] = w[i] + asoc * qw[i];
+              for (int i = 0; i < m; ++i) ssoc[i] = s[i] + asoc * qs[i];
+              double ths, phs;
+              TRYD(trial(ws, ssoc, ths, phs, cn));
+              accepted = filter_accepts(filt, theta0, ph0, dph, a, ths, phs, theta_min, phi_type);
+              if (accepted) {
+                for (int i = 0; i < nw; ++i) pw[i] = asoc * qw[i] / a;   // so that w + a pw = the corrected point
+                for (int i = 0; i < m; ++i) ps[i] = asoc * qs[i] / a;
+                ++R.soc_steps;
+                break;
+              }
+              if (ths > KAPPA_SOC * th_prev) break;
+              th_prev = ths;
+              for (int i = 0; i < nx + m; ++i) csoc[i] = asoc * csoc[i] + cn[i];
+            }
+          }
+          if (!accepted) a *= 0.5;
+        }
+        if (accepted && !phi_type) filt.pairs.push_back({(1.0 - GAMMA_THETA) * theta0, ph0 - GAMMA_PHI * theta0});
+      } else {
+        while (a > 1e-4 * amax) {
+          for (int i = 0; i < nw; ++i) wt[i] = w[i] + a * pw[i];
+          for (int i = 0; i < m; ++i) st2[i] = s[i] + a * ps[i];
+          double ft;
+          Vec gt, ht;
+          TRYD(eval_fgh(h, d, wt, ft, gt, ht));
+          double c1 = 0.0;
+          for (double v : gt) c1 += std::fabs(v);
+          for (int i = 0; i < m; ++i) c1 += std::fabs(ht[i] + st2[i]);
+          const double phit = ft + bw.barrier(wt, mu) + bs.barrier(st2, mu) + nu_pen * c1;
+          if (std::isfinite(phit) && phit <= phi0 + ETA * a * std::min(dphi, 0.0)) { accepted = true; break; }
+          a *= 0.5;
+        }
       }
       R.ms_linesearch += ms_since(t0);
       if (!accepted) {
@@ -873,9 +984,12 @@ extern "C" int opf_solve(opf_handle* h, const opf_ipm_options* opt, opf_ipm_resu
   o.max_iter = 300;
   o.mu0 = 0.1;
   o.pf_tol = 1e-10;
+  o.line_search = OPF_LINESEARCH_MERIT;
   if (opt) o = *opt;
   if (!(o.tol > 0) || o.max_iter < 0 || !(o.mu0 > 0) || !(o.pf_tol > 0) ||
-      (o.variant != OPF_LINRED && o.variant != OPF_REDLIN))
+      (o.variant != OPF_LINRED && o.variant != OPF_REDLIN) ||
+      (o.line_search != OPF_LINESEARCH_MERIT && o.line_search != OPF_LINESEARCH_FILTER) ||
+      (o.line_search == OPF_LINESEARCH_FILTER && o.variant != OPF_LINRED))
     return OPF_ERR_INVALID_ARG;
   *res = opf_ipm_result{};
   h->have_solution = false;

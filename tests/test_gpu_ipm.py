@@ -97,3 +97,25 @@ def test_graph_is_recaptured_after_a_wide_vjp_grows_the_solve_buffers(pkg):
     assert b["iters"] == a["iters"]
     assert abs(b["obj"] - a["obj"]) <= 1e-12 * abs(a["obj"])
     assert abs(b["obj"] - ref.obj) <= TOL_OBJ * abs(ref.obj)
+
+
+@pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000", "tiny3_loaded"])
+def test_filter_line_search_matches_oracle(pkg, name):
+    """The filter line search with second-order corrections (LinRed) reaches
+    the oracle's filter-variant optimum; on tiny3 with loads x1.3 the first
+    trial step raises the constraint violation and a correction is taken, as
+    in the oracle."""
+    if name == "tiny3_loaded":
+        net = gridgen.tiny3()
+        net.Pd, net.Qd = 1.3 * net.Pd, 1.3 * net.Qd
+    else:
+        net = gridgen.WORKLOADS[name]()
+    ref = ipm.linred(net, line_search="filter")
+    assert ref.status == "converged"
+    res = pkg.Handle(net).solve("linred", line_search="filter")
+    assert res["status"] == 0, res
+    assert abs(res["obj"] - ref.obj) <= TOL_OBJ * abs(ref.obj)
+    if name == "tiny3_loaded":
+        assert ref.soc_steps >= 1 and res["soc_steps"] >= 1
+    with pytest.raises(pkg.OPFError):
+        pkg.Handle(net).solve("redlin", line_search="filter")
