@@ -380,7 +380,7 @@ def main():
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
-    ap.add_argument("--rhs-block", type=int, default=0, choices=[0, 1, 2, 4, 32, 64, 96],
+    ap.add_argument("--rhs-block", type=int, default=0, choices=[0, 1, 2, 4, 32, 64, 96, 128],
                     help="multi-RHS solve kernel (opf_options.rhs_block; 0 autotune)")
     ap.add_argument("--rhs1-kernel", type=int, default=0, choices=[0, 1, 64, 65, 66],
                     help="one-RHS solve kernel (opf_options.rhs1_kernel; 0 autotune)")

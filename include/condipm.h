@@ -76,7 +76,10 @@ typedef struct opf_options {
                              column-parallel kernel (one lane per column); 64 =
                              level-blocked kernel (explicit inverses of the diagonal
                              blocks, one lane per column); 96 = its barrier-free
-                             dataflow form; 0 = autotune on the first
+                             dataflow form; 128 = the level-blocked kernel with one
+                             thread-block cluster of 8 CTAs per 32-column block
+                             (hardware cluster barrier between the phases; the
+                             autotuner also tries 2, 4, 16); 0 = autotune on the first
                              opf_condense (times each kernel on the actual right-hand
                              side and keeps the fastest)                              */
     long long spin_limit; /* iteration cap of every device-side wait; 0 = 1<<26        */

@@ -686,11 +686,19 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     const int kmax = std::max(1, h->blk_max / ncb);
     const int ksplit = std::max(1, std::min(kmax, h->blk_ksplit > 0 ? h->blk_ksplit : 16));
     if (timed) ph_begin(h, OPF_PHASE_TRSM);
-    CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
-                       h->st, h->spin_limit));
+    if (h->blk_cl > 0) {
+      CK(launch_trsm_blkc(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, h->blk_cl));
+    } else {
+      CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
+                         h->st, h->spin_limit));
+    }
     if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
-    CK(launch_trsm_blk(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->cs_bar,
-                       h->st, h->spin_limit));
+    if (h->blk_cl > 0) {
+      CK(launch_trsm_blkc(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, h->blk_cl));
+    } else {
+      CK(launch_trsm_blk(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->cs_bar,
+                         h->st, h->spin_limit));
+    }
     if (timed) ph_end(h);
     return OPF_OK;
   }
@@ -776,16 +784,28 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
       continue;
     }
     if (m == 64) {
-      // the level-blocked kernel also picks its CTAs per column block
+      // the level-blocked kernel also picks its CTAs per column block: a group
+      // meeting at a barrier through global memory, or a thread-block cluster
       const int kss[6] = {4, 8, 12, 16, 24, 32};
+      const int cls[4] = {2, 4, 8, 16};
       float bk = 1e30f;
+      int best_cl = 0;
+      h->blk_cl = 0;
       for (int ks : kss) {
         h->blk_ksplit = ks;
         float ms = 0.f;
         TRY(time_solve(nu, &ms));
-        if (ms < bk) { bk = ms; best_ks = ks; }
+        if (ms < bk) { bk = ms; best_ks = ks; best_cl = 0; }
+      }
+      for (int cl : cls) {
+        if (trsm_blkc_clusters(cl) < 1) continue;
+        h->blk_cl = cl;
+        float ms = 0.f;
+        TRY(time_solve(nu, &ms));
+        if (ms < bk) { bk = ms; best_cl = cl; }
       }
       h->blk_ksplit = best_ks;
+      h->blk_cl = best_cl;
       h->tune_ms[0][k] = bk;
       if (bk < best) { best = bk; pick = m; }
       continue;
@@ -844,8 +864,14 @@ static int reduce_route(opf_handle* h, int route) {
   double* Sx = h->Zt + (size_t)nu * ld;
   double* Hx = h->H + (size_t)nu * ld;
   if (route == OPF_ROUTE_EXPLICIT) {
+    const int z = dense_tn_slices(nu, nx);
+    double* scratch = nullptr;
+    if (z > 1) {
+      scratch = workspace(h, (size_t)z * nu * nu);
+      if (!scratch) return OPF_ERR_OOM;
+    }
     ph_begin(h, OPF_PHASE_KRED);
-    CK(launch_dense_tn(s, nu, nx, Sx, Hx, h->H, ld, h->F));
+    CK(launch_dense_tn(s, nu, nx, Sx, Hx, h->H, ld, h->F, scratch, z));
     CK(launch_symmetrize(s, nu, h->F, nu, 1, h->Kred));
     ph_end(h);
   } else {
@@ -1107,11 +1133,12 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return OPF_ERR_INVALID_ARG;
   }
   int cb = h->opt.rhs_block;
-  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32 && cb != 64 && cb != 96) {
+  if (cb != 0 && cb != 1 && cb != 2 && cb != 4 && cb != 32 && cb != 64 && cb != 96 && cb != 128) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
-  h->trsm_mode = cb ? cb : -1;
+  h->trsm_mode = cb == 128 ? 64 : (cb ? cb : -1);
+  if (cb == 128) h->blk_cl = 8;
   const int k1 = h->opt.rhs1_kernel;
   if (k1 != 0 && k1 != 1 && k1 != 64 && k1 != 65 && k1 != 66) {
     delete h;

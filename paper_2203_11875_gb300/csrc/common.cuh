@@ -114,7 +114,10 @@ cudaError_t launch_trsm(cudaStream_t s, int cb, int nlev, const int* lptr, const
 cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, long long ar, long long ac,
                               double* S);
 cudaError_t launch_dense_tn(cudaStream_t s, int nu, int nx, const double* Sx, const double* Hx,
-                            const double* Hu, long long ld, double* Kred);
+                            const double* Hu, long long ld, double* Kred, double* scratch, int nslices);
+// slices of the explicit route's sum over nx (enough CTAs for the device; the
+// scratch of nslices nu x nu partial sums at most 256 MB; 1 = no scratch)
+int dense_tn_slices(int nu, int nx);
 
 // Staged supernodal multi-RHS triangular solve (device view of an SnStream with
 // its values filled for one factor).  big supernodes read int_beg / val /
@@ -171,6 +174,11 @@ cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, cons
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
                             long long spin_limit);
 int trsm_blk_max_blocks();
+// the level-blocked solve with one thread-block cluster of cl CTAs per 32-column
+// block (cluster barrier between phases); clusters of cl that fit at once (0: none)
+cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
+                             double* X, double* Y, long long ld, int ncols, int cl);
+int trsm_blkc_clusters(int cl);
 // Dataflow (barrier-free) form of the level-blocked solve: task list of
 // phase-A (row >= 0) and phase-B (-1 - row) warp tasks in level order, each
 // row's supernode, and the supernodes each row's external entries lie in.

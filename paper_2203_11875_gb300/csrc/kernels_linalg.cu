@@ -143,22 +143,26 @@ __global__ void k_symmetrize(int n, const double* __restrict__ A, long long ar, 
 
 // Kred = Hu + Sx^T Hx (explicit route): C[a][c] = Hu(a, c) + sum_j Sx(j, a) Hx(j, c),
 // operands row-major with leading dimension ld; 64x64 output tiles, 16-deep
-// k slices staged in shared memory, 4x4 outputs per thread.
+// k slices staged in shared memory, 4x4 outputs per thread.  The sum over j
+// (nx terms, with nu x nu outputs only) is split over gridDim.z slices of the
+// j range: slice z writes its partial sums to P + z nu^2 (P = C and Hu added
+// when there is one slice); k_dense_tn_sum adds the slices in order.
 __global__ void __launch_bounds__(256) k_dense_tn(int nu, int nx, const double* __restrict__ Sx,
                                                   const double* __restrict__ Hx,
                                                   const double* __restrict__ Hu, long long ld,
-                                                  double* __restrict__ C) {
+                                                  double* __restrict__ P, int kchunk) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
   const int a0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int kb = blockIdx.z * kchunk, ke = min(nx, kb + kchunk);
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < nx; k0 += 16) {
+  for (int k0 = kb; k0 < ke; k0 += 16) {
     for (int t = threadIdx.x; t < 16 * 64; t += 256) {
       int kk = t / 64, j = t % 64;
       int k = k0 + kk;
-      As[kk][j] = (k < nx && a0 + j < nu) ? Sx[k * ld + a0 + j] : 0.0;
-      Bs[kk][j] = (k < nx && c0 + j < nu) ? Hx[k * ld + c0 + j] : 0.0;
+      As[kk][j] = (k < ke && a0 + j < nu) ? Sx[k * ld + a0 + j] : 0.0;
+      Bs[kk][j] = (k < ke && c0 + j < nu) ? Hx[k * ld + c0 + j] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -173,13 +177,25 @@ __global__ void __launch_bounds__(256) k_dense_tn(int nu, int nx, const double* 
     }
     __syncthreads();
   }
+  double* Pz = P + (size_t)blockIdx.z * nu * nu;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int a = a0 + ty * 4 + u, c = c0 + tx * 4 + v;
-      if (a < nu && c < nu) C[(size_t)a * nu + c] = Hu[a * ld + c] + acc[u][v];
+      if (a < nu && c < nu) Pz[(size_t)a * nu + c] = gridDim.z == 1 ? Hu[a * ld + c] + acc[u][v] : acc[u][v];
     }
+}
+
+// C = Hu + the sum of the slices of P, in slice order (deterministic)
+__global__ void k_dense_tn_sum(int nu, int nslices, const double* __restrict__ P, const double* __restrict__ Hu,
+                               long long ld, double* __restrict__ C) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nu * nu) return;
+  const int a = int(t / nu), c = int(t % nu);
+  double v = 0.0;
+  for (int z = 0; z < nslices; ++z) v += P[(size_t)z * nu * nu + t];
+  C[t] = Hu[a * ld + c] + v;
 }
 
 // ----------------------------------------------------------------- LU refactor
@@ -964,11 +980,24 @@ cudaError_t launch_symmetrize(cudaStream_t s, int n, const double* A, long long 
   note_launch();
   return cudaGetLastError();
 }
+int dense_tn_slices(int nu, int nx) {
+  const int tiles = nblk(nu, 64) * nblk(nu, 64);
+  int z = std::max(1, std::min(64, (2 * device_sms() + tiles - 1) / tiles));
+  z = std::min(z, std::max(1, nx / 256));   // at least 256 terms per slice
+  while (z > 1 && (size_t)z * nu * nu * sizeof(double) > ((size_t)256 << 20)) --z;
+  return z;
+}
 cudaError_t launch_dense_tn(cudaStream_t s, int nu, int nx, const double* Sx, const double* Hx,
-                            const double* Hu, long long ld, double* Kred) {
-  dim3 grid(nblk(nu, 64), nblk(nu, 64));
-  k_dense_tn<<<grid, 256, 0, s>>>(nu, nx, Sx, Hx, Hu, ld, Kred);
+                            const double* Hu, long long ld, double* Kred, double* scratch, int nslices) {
+  const int z = std::max(1, nslices);
+  const int kchunk = (nblk(nx, z) + 15) / 16 * 16;
+  dim3 grid(nblk(nu, 64), nblk(nu, 64), z);
+  k_dense_tn<<<grid, 256, 0, s>>>(nu, nx, Sx, Hx, Hu, ld, z == 1 ? Kred : scratch, kchunk);
   note_launch();
+  if (z > 1) {
+    k_dense_tn_sum<<<nblk((long long)nu * nu, 256), 256, 0, s>>>(nu, z, scratch, Hu, ld, Kred);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_lu_scatter(cudaStream_t s, long long nnzG, const int* Gx_to_LU, const double* Gval,

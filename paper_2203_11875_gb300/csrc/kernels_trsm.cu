@@ -831,6 +831,23 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* _
             [&]() { return group_barrier(ctr, ksplit * (++nbar), spin_limit, st); });
 }
 
+// The level-blocked solve with one thread-block cluster per 32-column block:
+// the cluster's CTAs share out a level's rows and meet at the hardware cluster
+// barrier between the phases (in place of k_trsm_blk's bounded group barrier
+// through global memory); the hardware co-schedules a cluster, so no wait can
+// be left without its partner.
+__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blkc(BlkDev S, const int* __restrict__ ci,
+                                                           const double* __restrict__ val,
+                                                           const double* __restrict__ D, double* X, double* Y,
+                                                           long long ld, int ncols) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int cb = blockIdx.x / cl.num_blocks();
+  blk_solve(S, ci, val, D, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), [&]() {
+    cl.sync();
+    return true;
+  });
+}
+
 // Both triangles of a multi-RHS solve for every instance of a batch: one
 // thread-block cluster per (instance, 32-column block) item, its CTAs sharing
 // out a level's rows and the cluster barrier between the phases (the hardware
@@ -1256,6 +1273,47 @@ int trsm_blk_max_blocks() {
   return sms * std::max(a, 1);
 }
 
+static cudaLaunchConfig_t trsm_cluster_config(int nclusters, int cl, cudaStream_t s, cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(nclusters * cl);
+  cfg.blockDim = dim3(BLK_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
+                             double* X, double* Y, long long ld, int ncols, int cl) {
+  if (ncols <= 0 || S.nlev <= 0) return cudaSuccess;
+  if (cl > 8) {
+    cudaError_t e = allow_cluster16((const void*)k_trsm_blkc);
+    if (e != cudaSuccess) return e;
+  }
+  const int ncb = (ncols + 31) / 32;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = trsm_cluster_config(ncb, cl, s, at);
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, k_trsm_blkc, S, ci, val, D, X, Y, ld, ncols);
+}
+
+int trsm_blkc_clusters(int cl) {
+  if (cl > 8 && allow_cluster16((const void*)k_trsm_blkc) != cudaSuccess) return 0;
+  cudaLaunchAttribute at[1];
+  const cudaLaunchConfig_t cfg = trsm_cluster_config(1, cl, nullptr, at);
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, (const void*)k_trsm_blkc, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc;
+}
+
 cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
                             long long spin_limit) {
@@ -1524,20 +1582,6 @@ cudaError_t launch_batch_factor_post(cudaStream_t s, const BatchInst* I, int n, 
   return cudaGetLastError();
 }
 
-static cudaLaunchConfig_t trsm_cluster_config(int nclusters, int cl, cudaStream_t s, cudaLaunchAttribute* at) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(nclusters * cl);
-  cfg.blockDim = dim3(BLK_THREADS);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cl;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cfg;
-}
 
 cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cbs, int ncbs, int trans, int cl) {
   if (ncbs <= 0) return cudaSuccess;

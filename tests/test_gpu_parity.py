@@ -153,7 +153,8 @@ def test_route_autotune(pkg, name):
 @pytest.mark.parametrize("name", ["ring30", "grid2000"])
 def test_rhs_block_and_route_invariance(pkg, name):
     """Kred does not depend on the multi-RHS solve kernel (staged with 1, 2, 4
-    columns per CTA, column-parallel, level-blocked and its dataflow form; ragged
+    columns per CTA, column-parallel, level-blocked with a group barrier or on
+    thread-block clusters, and its dataflow form; ragged
     column tails included: nu = 11, 399) nor on the route (explicit S^T H vs
     adjoint-adjoint).  The substitution kernels agree to 1e-12; the level-blocked
     kernels multiply by explicit inverses of the diagonal blocks, a different
@@ -162,7 +163,7 @@ def test_rhs_block_and_route_invariance(pkg, name):
     lay = model.Layout(net)
     outs = []
     for route in (0, 1):
-        for cb in (1, 2, 4, 32, 64, 96):
+        for cb in (1, 2, 4, 32, 64, 96, 128):
             h = pkg.Handle(net, route=route, rhs_block=cb)
             gpu_eval(pkg, h, lay, rec["w"], rec["lam"], rec["y"])
             K = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
@@ -170,7 +171,7 @@ def test_rhs_block_and_route_invariance(pkg, name):
             outs.append((cb, N(K)))
     ref = outs[0][1]
     for cb, o in outs[1:]:
-        assert rel_err(o, ref) <= (1e-10 if cb in (64, 96) else 1e-12), cb
+        assert rel_err(o, ref) <= (1e-10 if cb in (64, 96, 128) else 1e-12), cb
 
 
 def _first_failing_column(M):
