@@ -38,7 +38,7 @@ import gridgen  # noqa: E402
 
 METRIC = "condense+Cholesky ms/IPM iter"
 KERNEL_NAMES = {32: "column-parallel", 64: "level-blocked", 96: "dataflow", 1: "staged x1", 2: "staged x2",
-                4: "staged x4"}
+                4: "staged x4", 128: "level-blocked on clusters"}
 UNIT = "ms/iter"
 WORKLOAD = ("grid10k: 10,000-bus lattice, 1,000 generators, nu=1,999, nx=18,999, FP64, "
             "LinRed oracle iterate 3")
@@ -477,9 +477,10 @@ def main():
     trsm_ms, trsm_n = phases["trsm"]
     per_launch_ms = trsm_ms / max(1, trsm_n)
     achieved = (fl["trsm"] / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
-    trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk", 96: "k_trsm_df"}.get(trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
-    trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)", 96: " (dataflow)"}.get(
-        trsm_kernel, " (staged)")
+    trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk", 96: "k_trsm_df", 128: "k_trsm_blkc"}.get(
+        trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
+    trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)", 96: " (dataflow)",
+                             128: " (level-blocked, clusters)"}.get(trsm_kernel, " (staged)")
     traffic = measured_traffic(trsm_base, "grid10k")
     fl_path = sum(v for k, v in fl.items() if k != "S")
     cf_ms = float(np.mean(cf))

@@ -119,7 +119,8 @@ int opf_sizes(const opf_handle* h, int* nx, int* nu, int* m);
 int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* levels_bwd,
               long long* nnz_k, long long* lu_flops);
 /* Multi-RHS solve kernel in use (host outputs, may be NULL): *kernel as in
- * opf_options.rhs_block (-1 before the autotuner ran), ms[6] the autotuner's
+ * opf_options.rhs_block (-1 before the autotuner ran; 128 the level-blocked
+ * kernel on thread-block clusters, of any size), ms[6] the autotuner's
  * timings of {column-parallel, staged 1, 2, 4, level-blocked, dataflow}
  * (0 = not tried),
  * *kernel1 the kernel of solves with fewer than 32 right-hand sides (1 staged,

@@ -1210,7 +1210,7 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
 
 int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1) {
   if (!h) return OPF_ERR_INVALID_ARG;
-  if (kernel) *kernel = h->trsm_mode;
+  if (kernel) *kernel = (h->trsm_mode == 64 && h->blk_cl > 0) ? 128 : h->trsm_mode;
   if (ms)
     for (int k = 0; k < 6; ++k) ms[k] = h->tune_ms[0][k];
   if (kernel1) *kernel1 = h->trsm_mode1;
