@@ -130,10 +130,12 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
 int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);
 /* Dense Cholesky kernel in use (host outputs, may be NULL): *form as in
  * opf_options.chol_form (0 before the first factorisation), *nblocks its grid,
- * ms[OPF_CHOL_CANDIDATES] the autotuner's timings of {barrier form at 38, 76,
- * 152, 304 CTAs; dataflow form at 76, 152, 304 CTAs with a small panel group;
- * dataflow form at 152, 304 CTAs with a large panel group} (0 = not tried). */
-#define OPF_CHOL_CANDIDATES 9
+ * ms[OPF_CHOL_CANDIDATES] the autotuner's timings of {barrier form at 1/4, 1/2,
+ * 1 and 2 CTAs per SM; dataflow form at 1/2, 1, 2 CTAs per SM with a small panel
+ * group; dataflow form at 1, 2 CTAs per SM with a large panel group; dataflow
+ * form at 4 CTAs per SM with a small, then a large panel group} (0 = not tried;
+ * a candidate with more CTAs than fit at once is not tried). */
+#define OPF_CHOL_CANDIDATES 11
 int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms);
 /* Condensation route in use (host outputs, may be NULL): *route as in
  * opf_options.route (-1: OPF_ROUTE_AUTO before its first opf_condense), ms[2]

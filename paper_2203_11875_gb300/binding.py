@@ -261,10 +261,11 @@ class Handle:
         """(Cholesky form: 1 barrier, 2 dataflow, 0 not tuned yet; its grid;
         autotuner ms per candidate)."""
         f, nb = C.c_int(), C.c_int()
-        ms = (C.c_float * 9)()
+        ms = (C.c_float * 11)()
         _check(self._lib.opf_chol_choice(self._h, C.byref(f), C.byref(nb), ms), "opf_chol_choice")
-        names = ("barrier38", "barrier76", "barrier152", "barrier304", "dataflow76", "dataflow152", "dataflow304",
-                 "dataflow152_wide_panel", "dataflow304_wide_panel")
+        names = ("barrier_quarter_sm", "barrier_half_sm", "barrier_1_per_sm", "barrier_2_per_sm",
+                 "dataflow_half_sm", "dataflow_1_per_sm", "dataflow_2_per_sm", "dataflow_1_per_sm_wide_panel",
+                 "dataflow_2_per_sm_wide_panel", "dataflow_4_per_sm", "dataflow_4_per_sm_wide_panel")
         return f.value, nb.value, dict(zip(names, ms))
 
     def route_choice(self):

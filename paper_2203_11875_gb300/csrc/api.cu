@@ -450,6 +450,7 @@ int upload_all(opf_handle* h) {
   }
   h->cs_ksplit_max = std::max(1, trsm_cols_max_blocks());
   h->blk_max = std::max(1, trsm_blk_max_blocks());
+  for (int i = 0; i < 3; ++i) h->blk_max_minb[i] = std::max(1, trsm_blk_max_blocks(BLK_MINB[i]));
   h->df_max = std::max(1, trsm_df_max_blocks());
   if (!ybuf_reserve(h, (size_t)P.nx * h->ldp)) return OPF_ERR_OOM;
   {
@@ -683,21 +684,22 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     double* Y = ybuf_reserve(h, (size_t)P.nx * (size_t)xr);
     if (!Y) return OPF_ERR_OOM;
     const int ncb = (ncols + 31) / 32;
-    const int kmax = std::max(1, h->blk_max / ncb);
+    const int kmax = std::max(1, h->blk_max_minb[h->blk_minb_i] / ncb);
     const int ksplit = std::max(1, std::min(kmax, h->blk_ksplit > 0 ? h->blk_ksplit : 16));
+    const int minb = BLK_MINB[h->blk_minb_i];
     if (timed) ph_begin(h, OPF_PHASE_TRSM);
     if (h->blk_cl > 0) {
       CK(launch_trsm_blkc(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, h->blk_cl));
     } else {
       CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
-                         h->st, h->spin_limit));
+                         h->st, h->spin_limit, minb));
     }
     if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
     if (h->blk_cl > 0) {
       CK(launch_trsm_blkc(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, h->blk_cl));
     } else {
       CK(launch_trsm_blk(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->cs_bar,
-                         h->st, h->spin_limit));
+                         h->st, h->spin_limit, minb));
     }
     if (timed) ph_end(h);
     return OPF_OK;
@@ -791,12 +793,18 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
       float bk = 1e30f;
       int best_cl = 0;
       h->blk_cl = 0;
-      for (int ks : kss) {
-        h->blk_ksplit = ks;
-        float ms = 0.f;
-        TRY(time_solve(nu, &ms));
-        if (ms < bk) { bk = ms; best_ks = ks; best_cl = 0; }
+      int best_mb = 0;
+      for (int mb = 0; mb < 3; ++mb) {
+        h->blk_minb_i = mb;
+        for (int ks : kss) {
+          if (ks > 16 && ks > h->blk_max_minb[mb] / ((nu + 31) / 32)) continue;
+          h->blk_ksplit = ks;
+          float ms = 0.f;
+          TRY(time_solve(nu, &ms));
+          if (ms < bk) { bk = ms; best_ks = ks; best_cl = 0; best_mb = mb; }
+        }
       }
+      h->blk_minb_i = best_mb;
       for (int cl : cls) {
         if (trsm_blkc_clusters(cl) < 1) continue;
         h->blk_cl = cl;
@@ -990,14 +998,16 @@ int tune_chol_blocks(opf_handle* h, double delta_w) {
   const int df_cap = chol_df_max_blocks();
   const int want = h->opt.chol_form;   // 0 both, 1 barrier form only, 2 dataflow form only
   struct Cand { int form, nb, np; };
-  const int q = std::max(1, sm / 4), hf = std::max(1, sm / 2), one = sm, two = 2 * sm;
+  const int q = std::max(1, sm / 4), hf = std::max(1, sm / 2), one = sm, two = 2 * sm, four = 4 * sm;
   const Cand cand[OPF_CHOL_CANDIDATES] = {
       {0, q, 0}, {0, hf, 0}, {0, one, 0}, {0, two, 0},
       {1, hf, std::max(1, std::min(hf / 3, std::max(8, rows0 / 4)))},
       {1, one, std::max(1, std::min(one / 3, std::max(8, rows0 / 4)))},
       {1, two, std::max(1, std::min(two / 3, std::max(8, rows0 / 4)))},
       {1, one, std::max(1, std::min(one / 2, std::max(8, rows0)))},
-      {1, two, std::max(1, std::min(two / 2, std::max(8, rows0)))}};
+      {1, two, std::max(1, std::min(two / 2, std::max(8, rows0)))},
+      {1, four, std::max(1, std::min(four / 3, std::max(8, rows0 / 4)))},
+      {1, four, std::max(1, std::min(four / 2, std::max(8, rows0)))}};
   // time only from a clean status word, and keep the timings only if every
   // candidate factored the whole matrix: a run that stops early on a
   // non-positive pivot (the dataflow form leaves as soon as one is flagged)

@@ -1257,6 +1257,66 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
     // it.  Columns in order, column k+1 first.
     const int g = sub_mode ? 2 : 1;                   // (sub-)tiles per tile side
     const int gmax = sub_mode ? (n + 15) / 16 : nt;   // (sub-)rows in the matrix
+    if (!sub_mode) {
+      // whole 32 x 32 tiles: the owned tiles of this step in order (columns
+      // k+1 .., rows of the CTA's residue class), the next tile's panels fetched
+      // into registers while this one is computed (each thread moves rows
+      // t / 32 + 8 q, column t % 32 of both panels)
+      auto first_row = [&](int gj) { return gj + (((ub - (gj * gmax - gj * (gj - 1) / 2)) % nU) + nU) % nU; };
+      auto advance = [&](int& gi, int& gj) {
+        gi += nU;
+        while (gi >= gmax) {
+          if (++gj >= gmax) return;
+          gi = first_row(gj);
+        }
+      };
+      int gj = k + 1, gi = first_row(gj);
+      if (gi >= gmax) { gi -= nU; advance(gi, gj); }
+      double pa[4], pb[4];
+      auto fetch = [&](int ti, int tj) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = (tid >> 5) + 8 * q, l = tid & 31;
+          pa[q] = (ti * CNB + rr < n && l < kb) ? __ldcg(&F[(size_t)(ti * CNB + rr) * n + k0 + l]) : 0.0;
+          pb[q] = (tj * CNB + rr < n && l < kb) ? __ldcg(&F[(size_t)(tj * CNB + rr) * n + k0 + l]) : 0.0;
+        }
+      };
+      if (gj < gmax) fetch(gi, gj);
+      while (gj < gmax) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = (tid >> 5) + 8 * q, l = tid & 31;
+          Ta[rr][l] = pa[q];
+          Tb[rr][l] = pb[q];
+        }
+        __syncthreads();
+        int ni = gi, nj = gj;
+        advance(ni, nj);
+        if (nj < gmax) fetch(ni, nj);
+        const int i0 = gi * CNB, j0 = gj * CNB;
+        const int ty = tid >> 4, tx = tid & 15;
+        double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+#pragma unroll 8
+        for (int l = 0; l < CNB; ++l) {
+          const double a0 = Ta[ty][l], a1 = Ta[ty + 16][l];
+          const double b0 = Tb[tx][l], b1 = Tb[tx + 16][l];
+          c00 = fma(a0, b0, c00);
+          c01 = fma(a0, b1, c01);
+          c10 = fma(a1, b0, c10);
+          c11 = fma(a1, b1, c11);
+        }
+        const int r0g = i0 + ty, r1g = i0 + ty + 16, c0g = j0 + tx, c1g = j0 + tx + 16;
+        if (r0g < n && c0g <= r0g) F[(size_t)r0g * n + c0g] -= c00;
+        if (r0g < n && c1g < n && c1g <= r0g) F[(size_t)r0g * n + c1g] -= c01;
+        if (r1g < n && c0g <= r1g) F[(size_t)r1g * n + c0g] -= c10;
+        if (r1g < n && c1g < n && c1g <= r1g) F[(size_t)r1g * n + c1g] -= c11;
+        __syncthreads();
+        if (tid == 0 && gj == k + 1) red_add_release(cdone + k, 1u);
+        gi = ni;
+        gj = nj;
+      }
+      continue;
+    }
     for (int gj = g * (k + 1); gj < gmax; ++gj) {
       const bool col0 = gj < g * (k + 2);
       const int base = gj * gmax - gj * (gj - 1) / 2;   // number of tile (gj, gj)

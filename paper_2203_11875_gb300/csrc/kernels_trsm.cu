@@ -819,11 +819,15 @@ __device__ __forceinline__ bool blk_solve(const BlkDev& S, const int* __restrict
   return true;
 }
 
-__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
-                                                          const double* __restrict__ val,
-                                                          const double* __restrict__ D, double* X, double* Y,
-                                                          long long ld, int ncols, int ksplit, unsigned* bar,
-                                                          int* st, long long spin_limit) {
+// MINB: CTAs per SM the register allocation must allow (1: the compiler's
+// choice, 48 registers, 5 CTAs; 6 and 8 trade a few spilled registers for more
+// resident warps); the autotuner times each
+template <int MINB>
+__global__ void __launch_bounds__(BLK_THREADS, MINB) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
+                                                                const double* __restrict__ val,
+                                                                const double* __restrict__ D, double* X, double* Y,
+                                                                long long ld, int ncols, int ksplit, unsigned* bar,
+                                                                int* st, long long spin_limit) {
   const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
   unsigned* ctr = bar + cb;
   unsigned nbar = 0;
@@ -1265,12 +1269,13 @@ cudaError_t launch_diag_inv4(cudaStream_t s, const DiagInvJob* jobs) {
   return cudaGetLastError();
 }
 
-int trsm_blk_max_blocks() {
-  int dev = 0, sms = 0, a = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trsm_blk, BLK_THREADS, 0);
-  return sms * std::max(a, 1);
+static const void* trsm_blk_fn(int minb) {
+  return minb >= 8 ? (const void*)k_trsm_blk<8> : minb >= 6 ? (const void*)k_trsm_blk<6> : (const void*)k_trsm_blk<1>;
+}
+int trsm_blk_max_blocks(int minb) {
+  int a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, trsm_blk_fn(minb), BLK_THREADS, 0);
+  return device_sms() * std::max(a, 1);
 }
 
 static cudaLaunchConfig_t trsm_cluster_config(int nclusters, int cl, cudaStream_t s, cudaLaunchAttribute* at) {
@@ -1316,7 +1321,7 @@ int trsm_blkc_clusters(int cl) {
 
 cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
-                            long long spin_limit) {
+                            long long spin_limit, int minb) {
   if (ncols <= 0 || S.nlev <= 0) return cudaSuccess;
   const int ncb = (ncols + 31) / 32;
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned) * ncb, s);
@@ -1324,7 +1329,7 @@ cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, cons
   void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&D, (void*)&X, (void*)&Y, (void*)&ld,
                   (void*)&ncols, (void*)&ksplit, (void*)&bar, (void*)&st, (void*)&spin_limit};
   note_launch();
-  return cudaLaunchCooperativeKernel((void*)k_trsm_blk, dim3(ncb * ksplit), dim3(BLK_THREADS), args, 0, s);
+  return cudaLaunchCooperativeKernel(trsm_blk_fn(minb), dim3(ncb * ksplit), dim3(BLK_THREADS), args, 0, s);
 }
 
 }  // namespace condipm

@@ -86,6 +86,8 @@ struct opf_handle {
   int blk_max = 1;               // resident CTAs of the level-blocked kernel
   int blk_ksplit = 0;            // its CTAs per 32-column block (0: as many as fit, at most 16)
   int blk_cl = 0;                // > 0: instead, one thread-block cluster of that many CTAs per block
+  int blk_minb_i = 0;            // register-bound variant of the level-blocked kernel (index into BLK_MINB)
+  int blk_max_minb[3] = {1, 1, 1};  // resident CTAs of each variant
   int blk1_blocks = 32;          // CTAs of the single-right-hand-side level-blocked solve
   condipm::Lu1sDev l1L{}, l1U{}; // the one-CTA single-right-hand-side solve's schedules
   int lu1s_ymax = 0;             // rows of the largest level (the one-CTA solve's Y buffer)

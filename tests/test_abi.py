@@ -59,7 +59,7 @@ def test_queries_reject_a_null_handle(lib):
     from paper_2203_11875_gb300 import binding
     L = binding.load_library()
     f, nb = C.c_int(), C.c_int()
-    ms = (C.c_float * 9)()
+    ms = (C.c_float * 11)()
     assert L.opf_chol_choice(None, C.byref(f), C.byref(nb), ms) == -1
     k, k1 = C.c_int(), C.c_int()
     ms6 = (C.c_float * 6)()

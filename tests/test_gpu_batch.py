@@ -89,3 +89,19 @@ def test_small_batch_of_mixed_networks(pkg):
     b.close()
     assert hs[1].solve()["status"] == 0
     assert np.isfinite(hs[1].solution()[3]).all()
+
+
+def test_lockstep_redlin_batch_matches_single_solves(pkg):
+    """Reduce-then-linearize loops in lockstep: each iteration's condensation of
+    every instance still iterating goes through the batched call; every
+    instance reaches its own single-instance RedLin optimum."""
+    nets = [gridgen.tiny3(), gridgen.ring30(), gridgen.lattice(500, 7101, name="b500")]
+    ref = [pkg.Handle(n).solve("redlin") for n in nets]
+    hs = [pkg.Handle(n) for n in nets]
+    b = pkg.Batch(hs)
+    out, _ = b.solve(variant="redlin")
+    assert b.lockstep_calls() == max(o["iters"] for o in out)
+    for r, o in zip(ref, out):
+        assert r["status"] == 0 and o["status"] == 0
+        assert abs(r["obj"] - o["obj"]) <= TOL_OBJ * abs(r["obj"])
+    b.close()
