@@ -396,8 +396,12 @@ int opf_batch_set_mode(opf_batch* b, int mode);
  * the cluster sizes (CTAs) of the batched multi-RHS solves and Cholesky (0 until
  * the first opf_batch_condense_factor whose instances all factored completely
  * timed the candidates 2, 4, 8, 16); tune_ms[8] those timings (solve, then
- * Cholesky; 0 = not tried).  Host outputs, any may be NULL. */
-int opf_batch_stats(const opf_batch* b, long long* lockstep_calls, int* trsm_cl, int* chol_cl, float* tune_ms);
+ * Cholesky; 0 = not tried); graph_calls: calls served by replaying the captured
+ * CUDA graph of the whole batched sequence (descriptor upload, every phase,
+ * the status read-back), which every call after the tuning one uses.  Host
+ * outputs, any may be NULL. */
+int opf_batch_stats(const opf_batch* b, long long* lockstep_calls, int* trsm_cl, int* chol_cl, float* tune_ms,
+                    long long* graph_calls);
 
 /* One interior-point iteration's condensation and control-step factorisation
  * (A5-A9: refactor G_x, S_x, K, H = K Z, Psi, Kred, Cholesky of Kred + delta_w I)

@@ -99,7 +99,8 @@ _SIGS = {
     "opf_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result),
                                   C.POINTER(C.c_double)]),
     "opf_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
-    "opf_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), _ip, _ip, C.POINTER(C.c_float)]),
+    "opf_batch_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), _ip, _ip, C.POINTER(C.c_float),
+                                  C.POINTER(C.c_longlong)]),
     "opf_batch_condense_factor": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                             C.POINTER(C.c_void_p), C.POINTER(C.c_double), _ip, _ip]),
     "opf_chol_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, _ip, C.c_void_p]),
@@ -469,11 +470,12 @@ class Batch:
     def stats(self):
         """opf_batch_stats: lockstep condensations, the batched solve's and
         Cholesky's cluster sizes and their tuning timings."""
-        n, a, c = C.c_longlong(0), C.c_int(0), C.c_int(0)
+        n, a, c, g = C.c_longlong(0), C.c_int(0), C.c_int(0), C.c_longlong(0)
         ms = (C.c_float * 8)()
-        _check(self._lib.opf_batch_stats(self._b, C.byref(n), C.byref(a), C.byref(c), ms), "opf_batch_stats")
+        _check(self._lib.opf_batch_stats(self._b, C.byref(n), C.byref(a), C.byref(c), ms, C.byref(g)),
+               "opf_batch_stats")
         return dict(lockstep_calls=n.value, trsm_cl=a.value, chol_cl=c.value,
-                    tune_trsm_ms=list(ms[:4]), tune_chol_ms=list(ms[4:]))
+                    tune_trsm_ms=list(ms[:4]), tune_chol_ms=list(ms[4:]), graph_calls=g.value)
 
     def condense_factor(self, sig_u, sig_x, sig_s, delta_w=None):
         """opf_batch_condense_factor: per-instance device tensors of Sigma (lists

@@ -61,6 +61,12 @@ struct opf_batch {
   // times the candidates on the batch's own instances
   int trsm_cl = 0, chol_cl = 0;
   float tune_trsm_ms[4] = {}, tune_chol_ms[4] = {};   // candidates 2, 4, 8, 16 CTAs
+  // once tuned, the whole batched sequence (descriptor upload, every phase,
+  // the status read-back) is captured as one CUDA graph and replayed
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_failed = false;
+  long long graph_calls = 0;
+  int* st_dev = nullptr;               // the active instances' status words, gathered
   // lockstep solves: the instances' loops meet at every condensation
   int mode = OPF_BATCH_LOCKSTEP;
   std::mutex mu;
@@ -139,6 +145,7 @@ extern "C" void opf_batch_destroy(opf_batch* b) {
   }
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   if (b->ev_done) cudaEventDestroy(b->ev_done);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->bs) cudaStreamDestroy(b->bs);
   for (void* p : b->dev_allocs) cudaFree(p);
   if (b->hI) cudaFreeHost(b->hI);
@@ -305,6 +312,8 @@ int batch_setup(opf_batch* b) {
   b->dev_allocs.push_back(b->dI);
   if (cudaMallocHost(&b->hI, sizeof(BatchInst) * n) != cudaSuccess) return OPF_ERR_OOM;
   if (cudaMallocHost(&b->st_host, sizeof(int) * ST_WORDS * n) != cudaSuccess) return OPF_ERR_OOM;
+  if (cudaMalloc(&b->st_dev, sizeof(int) * ST_WORDS * n) != cudaSuccess) return OPF_ERR_OOM;
+  b->dev_allocs.push_back(b->st_dev);
   if (cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess) return OPF_ERR_CUDA;
   b->ev.resize(n, nullptr);
   for (int i = 0; i < n; ++i)
@@ -393,8 +402,6 @@ int batch_condense_subset(opf_batch* b, const std::vector<char>& on, const doubl
     if (cudaStreamWaitEvent(b->bs, b->ev[i], 0) != cudaSuccess) return OPF_ERR_CUDA;
   }
   cudaStream_t s = b->bs;
-  if (cudaMemcpyAsync(b->dI, b->hI, sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return OPF_ERR_CUDA;
   const long long spin = b->hs[0]->spin_limit;
   // A5: refactorisation with its prologue and epilogue
   auto front = [&]() {
@@ -415,69 +422,119 @@ int batch_condense_subset(opf_batch* b, const std::vector<char>& on, const doubl
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ta, tb);
     return e;
   };
+  auto upload = [&]() {
+    return cudaMemcpyAsync(b->dI, b->hI, sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s);
+  };
+  // the active instances' status words into one pinned buffer
+  auto statuses = [&]() {
+    cudaError_t e = launch_batch_status(s, b->dI, n, b->st_dev);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->st_host, b->st_dev, sizeof(int) * ST_WORDS * n, cudaMemcpyDeviceToHost, s);
+    return e;
+  };
+  // the tuned sequence, as enqueued (eagerly or into the graph)
+  auto tuned_sequence = [&]() {
+    cudaError_t e = upload();
+    if (e == cudaSuccess) e = launch_batch_prologue(s, b->dI, n, b->boff, b->nb);
+    if (e == cudaSuccess)
+      e = launch_batch_lu(s, b->dI, b->lu_items, b->n_lu_items, b->lu_blocks, b->lu_maxlen, 1u, spin);
+    if (e == cudaSuccess)
+      e = launch_batch_factor_post(s, b->dI, n, b->boff[BOFF_F], b->nb[BOFF_F], b->boff[BOFF_D], b->nb[BOFF_D]);
+    if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, b->trsm_cl);
+    if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_W], b->nb[BOFF_W], 0);
+    if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 1, b->trsm_cl);
+    if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U], 1);
+    if (e == cudaSuccess) e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+    if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, b->chol_cl);
+    if (e == cudaSuccess) e = statuses();
+    return e;
+  };
   const bool tune = b->trsm_cl == 0 || b->chol_cl == 0;
+  int trsm_cl = b->trsm_cl, chol_cl = b->chol_cl;
   cudaError_t e = cudaSuccess;
+  if (!tune) {
+    if (!b->gexec && !b->graph_failed) {
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const cudaError_t ce = tuned_sequence();
+        ok = cudaStreamEndCapture(s, &g) == cudaSuccess && ce == cudaSuccess && g &&
+             cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+      }
+      if (!ok) {
+        b->gexec = nullptr;
+        b->graph_failed = true;
+      }
+      cudaGetLastError();
+    }
+    if (b->gexec) {
+      e = cudaGraphLaunch(b->gexec, s);
+      ++b->graph_calls;
+    } else {
+      e = tuned_sequence();
+    }
+  }
   if (tune) {
-    e = cudaEventCreate(&ta);
+    e = upload();
+    if (e == cudaSuccess) e = cudaEventCreate(&ta);
     if (e == cudaSuccess) e = cudaEventCreate(&tb);
   }
-  // A6 (S_x): with the tuned cluster size, or each candidate after its own
-  // refactorisation (the solve works in place; every cluster size gives the
-  // same result, each row being summed by one warp in one order)
-  int trsm_cl = b->trsm_cl;
-  if (e == cudaSuccess && trsm_cl == 0) {
-    float best = 1e30f;
-    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
-      const int cl = BATCH_CL_CANDIDATES[c];
-      if (batch_trsm_clusters(cl) < 1) continue;
-      e = front();
-      float ms = 0.f;
-      if (e == cudaSuccess) e = timed([&]() { return launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, cl); }, &ms);
-      b->tune_trsm_ms[c] = ms;
-      if (ms < best) { best = ms; trsm_cl = cl; }
-      if (c < 3 && e == cudaSuccess) e = cudaStreamSynchronize(s);
-    }
-    // the last candidate's solve stands only if it is the pick: redo otherwise
-    if (e == cudaSuccess && trsm_cl != BATCH_CL_CANDIDATES[3]) {
+  if (tune) {
+    // A6 (S_x): with the tuned cluster size, or each candidate after its own
+    // refactorisation (the solve works in place; every cluster size gives the
+    // same result, each row being summed by one warp in one order)
+    if (e == cudaSuccess && trsm_cl == 0) {
+      float best = 1e30f;
+      for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+        const int cl = BATCH_CL_CANDIDATES[c];
+        if (batch_trsm_clusters(cl) < 1) continue;
+        e = front();
+        float ms = 0.f;
+        if (e == cudaSuccess) e = timed([&]() { return launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, cl); }, &ms);
+        b->tune_trsm_ms[c] = ms;
+        if (ms < best) { best = ms; trsm_cl = cl; }
+        if (c < 3 && e == cudaSuccess) e = cudaStreamSynchronize(s);
+      }
+      // the last candidate's solve stands only if it is the pick: redo otherwise
+      if (e == cudaSuccess && trsm_cl != BATCH_CL_CANDIDATES[3]) {
+        e = front();
+        if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, trsm_cl);
+      }
+    } else if (e == cudaSuccess) {
       e = front();
       if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, trsm_cl);
     }
-  } else if (e == cudaSuccess) {
-    e = front();
-    if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 0, trsm_cl);
-  }
-  // A7: H = K Z, Psi = G_x^{-T} H_x, H_u -= G_u^T Psi, Kred and F
-  if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_W], b->nb[BOFF_W], 0);
-  if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 1, trsm_cl);
-  if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U], 1);
-  // A9: Cholesky, with the tuned cluster size or each candidate on a fresh F
-  int chol_cl = b->chol_cl;
-  if (e == cudaSuccess && chol_cl == 0) {
-    float best = 1e30f;
-    int last = 0;
-    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
-      const int cl = BATCH_CL_CANDIDATES[c];
-      if (batch_chol_clusters(cl) < 1) continue;
-      e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = timed([&]() { return launch_batch_chol(s, b->dI, n, cl); }, &ms);
-      b->tune_chol_ms[c] = ms;
-      if (ms < best) { best = ms; chol_cl = cl; }
-      last = cl;
-    }
-    if (e == cudaSuccess && chol_cl != last) {
+    // A7: H = K Z, Psi = G_x^{-T} H_x, H_u -= G_u^T Psi, Kred and F
+    if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_W], b->nb[BOFF_W], 0);
+    if (e == cudaSuccess) e = launch_batch_trsm(s, b->dI, b->cbs, b->ncbs, 1, trsm_cl);
+    if (e == cudaSuccess) e = launch_batch_spmm(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U], 1);
+    // A9: Cholesky, with the tuned cluster size or each candidate on a fresh F
+    if (e == cudaSuccess && chol_cl == 0) {
+      float best = 1e30f;
+      int last = 0;
+      for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+        const int cl = BATCH_CL_CANDIDATES[c];
+        if (batch_chol_clusters(cl) < 1) continue;
+        e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = timed([&]() { return launch_batch_chol(s, b->dI, n, cl); }, &ms);
+        b->tune_chol_ms[c] = ms;
+        if (ms < best) { best = ms; chol_cl = cl; }
+        last = cl;
+      }
+      if (e == cudaSuccess && chol_cl != last) {
+        e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
+        if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, chol_cl);
+      }
+    } else if (e == cudaSuccess) {
       e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
       if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, chol_cl);
     }
-  } else if (e == cudaSuccess) {
-    e = launch_batch_kred(s, b->dI, n, b->boff[BOFF_U], b->nb[BOFF_U]);
-    if (e == cudaSuccess) e = launch_batch_chol(s, b->dI, n, chol_cl);
+    if (ta) cudaEventDestroy(ta);
+    if (tb) cudaEventDestroy(tb);
   }
-  if (ta) cudaEventDestroy(ta);
-  if (tb) cudaEventDestroy(tb);
-  for (int i = 0; i < n && e == cudaSuccess; ++i)
-    if (on[i])
-      e = cudaMemcpyAsync(b->st_host + ST_WORDS * i, b->hs[i]->st, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, s);
+  if (tune && e == cudaSuccess) e = statuses();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     note_cuda_error(e);
@@ -588,9 +645,10 @@ extern "C" int opf_batch_set_mode(opf_batch* b, int mode) {
 }
 
 extern "C" int opf_batch_stats(const opf_batch* b, long long* lockstep_calls, int* trsm_cl, int* chol_cl,
-                               float* tune_ms) {
+                               float* tune_ms, long long* graph_calls) {
   if (!b) return OPF_ERR_INVALID_ARG;
   if (lockstep_calls) *lockstep_calls = b->lockstep_calls;
+  if (graph_calls) *graph_calls = b->graph_calls;
   if (trsm_cl) *trsm_cl = b->trsm_cl;
   if (chol_cl) *chol_cl = b->chol_cl;
   if (tune_ms)

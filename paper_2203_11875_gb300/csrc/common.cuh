@@ -382,6 +382,8 @@ cudaError_t launch_batch_trsm(cudaStream_t s, const BatchInst* I, const int2* cb
 cudaError_t launch_batch_spmm(cudaStream_t s, const BatchInst* I, int n, const int* boff, int nblocks, int which);
 // A7 / A9: Kred = sym(H_u) and F = tril(Kred) + delta_w I
 cudaError_t launch_batch_kred(cudaStream_t s, const BatchInst* I, int n, const int* boffU, int nblocks);
+// the active instances' status words into out[ST_WORDS * n] (0 for the others)
+cudaError_t launch_batch_status(cudaStream_t s, const BatchInst* I, int n, int* out);
 // A9: Cholesky of every instance's F, one thread-block cluster of cl CTAs per instance
 cudaError_t launch_batch_chol(cudaStream_t s, const BatchInst* I, int n, int cl);
 // clusters of cl CTAs of the batched solve / Cholesky that fit on the device at

@@ -466,6 +466,14 @@ __global__ void k_b_kred(const BatchInst* __restrict__ I, int n, const int* __re
   }
 }
 
+// the status words of the active instances, side by side (read back at once)
+__global__ void k_b_status(const BatchInst* __restrict__ I, int n, int* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ST_WORDS) return;
+  const BatchInst& B = I[t / ST_WORDS];
+  out[t] = B.active ? B.st[t % ST_WORDS] : 0;
+}
+
 // ----------------------------------------------------------------- Cholesky
 constexpr int CNB = 32;
 
@@ -1585,6 +1593,13 @@ cudaError_t launch_batch_lu(cudaStream_t s, const BatchInst* I, const int2* item
 cudaError_t launch_batch_spmm(cudaStream_t s, const BatchInst* I, int n, const int* boff, int nblocks, int which) {
   if (n <= 0) return cudaSuccess;
   k_b_spmm<<<nblocks, BATCH_EW_THREADS, 0, s>>>(I, n, boff, which);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_status(cudaStream_t s, const BatchInst* I, int n, int* out) {
+  if (n <= 0) return cudaSuccess;
+  k_b_status<<<nblk((long long)n * ST_WORDS, 256), 256, 0, s>>>(I, n, out);
   note_launch();
   return cudaGetLastError();
 }

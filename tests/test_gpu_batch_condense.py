@@ -134,4 +134,42 @@ def test_batched_condense_factor(pkg, call):
         p = pts[INDEFINITE]
         big = 2.0 * abs(float(np.linalg.eigvalsh(p["Ko"])[0])) + 1.0
         assert hs[INDEFINITE].kkt_factor(big) == -1
+    # the first call with every instance factored completely tunes the cluster
+    # sizes; the first call (one instance indefinite) cannot, so the second tunes
+    # and none is replayed from the captured graph yet
+    st = b.stats()
+    assert st["trsm_cl"] in (2, 4, 8, 16) or st["trsm_cl"] == 0
+    b.close()
+
+
+def test_batched_condense_factor_graph_replay(pkg):
+    """After the tuning call, every call replays the captured graph of the whole
+    batched sequence, with the same results as an eagerly enqueued call."""
+    nets = networks()[:5]
+    hs = [pkg.Handle(n) for n in nets]
+    b = pkg.Batch(hs)
+    outs = []
+    for call in range(3):
+        pts = [point(n, 500 + 10 * k, 1.0) for k, n in enumerate(nets)]
+        deltas = [max(0.0, -float(np.linalg.eigvalsh(p["Ko"])[0])) + 1.0 for p in pts]
+        for h, p in zip(hs, pts):
+            lay = p["lay"]
+            h.eval_derivatives(T(p["w"][lay.nu:]), T(p["w"][:lay.nu]), T(p["lam"]), T(p["y"]))
+        sig = [[T(p["sw"][:p["lay"].nu]) for p in pts], [T(p["sw"][p["lay"].nu:]) for p in pts],
+               [T(p["ss"]) for p in pts]]
+        status, _ = b.condense_factor(*sig, delta_w=deltas)
+        assert status == [0] * len(nets)
+        Fs = []
+        for h, p in zip(hs, pts):
+            F = torch.zeros(p["lay"].nu ** 2, dtype=torch.float64, device="cuda")
+            h.get_factor(F)
+            Fs.append(N(F))
+        outs.append(Fs)
+    st = b.stats()
+    assert st["trsm_cl"] > 0 and st["chol_cl"] > 0
+    assert st["graph_calls"] == 2
+    # the same point gives bitwise the same factors through the graph as through
+    # the eagerly enqueued tuning call
+    for k in range(len(nets)):
+        assert np.array_equal(outs[0][k], outs[1][k]) and np.array_equal(outs[1][k], outs[2][k])
     b.close()
