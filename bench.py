@@ -476,7 +476,9 @@ def main():
     fl = path_flops(h)
     trsm_ms, trsm_n = phases["trsm"]
     per_launch_ms = trsm_ms / max(1, trsm_n)
-    achieved = (fl["trsm"] / 4) / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
+    launches_per_step = trsm_n / args.steps          # 4 (one triangle each) or 2 (both triangles)
+    flops_per_launch = fl["trsm"] / max(1.0, launches_per_step)
+    achieved = flops_per_launch / (per_launch_ms * 1e-3) / 1e9 if trsm_n else None
     trsm_base = {32: "k_trsm_cols", 64: "k_trsm_blk", 96: "k_trsm_df", 128: "k_trsm_blkc"}.get(
         trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
     trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)", 96: " (dataflow)",
@@ -529,7 +531,8 @@ def main():
            "roofline": {"bound": "alu", "kernel": trsm_name,
                         "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                        "flops_per_launch": fl["trsm"] / 4, "ms_per_launch": per_launch_ms,
+                        "flops_per_launch": flops_per_launch, "ms_per_launch": per_launch_ms,
+                        "launches_per_step": launches_per_step,
                         "peak_note": ("FP64 measured live in this run: the best of opf_fp64_peak's DFMA and f64 "
                                       "mma.sync probes (fp64_peaks_gflops); the measured-peak file has no FP64 entry"
                                       if peaks else

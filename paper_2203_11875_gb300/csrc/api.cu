@@ -689,15 +689,14 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     const int minb = BLK_MINB[h->blk_minb_i];
     if (timed) ph_begin(h, OPF_PHASE_TRSM);
     if (h->blk_cl > 0) {
-      CK(launch_trsm_blkc(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, h->blk_cl));
+      // both triangles in one launch of one cluster per column block
+      CK(launch_trsm_blkc(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, h->bkU, h->Up_ci, upv,
+                          trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, h->blk_cl));
     } else {
+      // one launch per triangle (measured faster than both in one launch)
       CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
                          h->st, h->spin_limit, minb));
-    }
-    if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
-    if (h->blk_cl > 0) {
-      CK(launch_trsm_blkc(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, h->blk_cl));
-    } else {
+      if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
       CK(launch_trsm_blk(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->cs_bar,
                          h->st, h->spin_limit, minb));
     }

@@ -170,16 +170,18 @@ struct DiagInvJob {
 cudaError_t launch_diag_inv4(cudaStream_t s, const DiagInvJob* jobs);
 // X, Y row-major with leading dimension ld (Y: scratch of the same shape);
 // ksplit CTAs per 32 columns, cooperative launch; bar holds ncb counters.
-// minb: the register bound's CTAs per SM (1, 6 or 8; see the kernel)
-constexpr int BLK_MINB[3] = {1, 6, 8};
+// minb: the register bound's CTAs per SM (5, 6 or 8; see the kernel)
+constexpr int BLK_MINB[3] = {5, 6, 8};
 cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
-                            long long spin_limit, int minb = 1);
-int trsm_blk_max_blocks(int minb = 1);
-// the level-blocked solve with one thread-block cluster of cl CTAs per 32-column
-// block (cluster barrier between phases); clusters of cl that fit at once (0: none)
-cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
-                             double* X, double* Y, long long ld, int ncols, int cl);
+                            long long spin_limit, int minb = 5);
+int trsm_blk_max_blocks(int minb = 5);
+// the level-blocked solve, both triangles, with one thread-block cluster of cl
+// CTAs per 32-column block (cluster barrier between phases); clusters of cl that
+// fit at once (0: none)
+cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& SL, const int* ciL, const double* valL,
+                             const double* DL, const BlkDev& SU, const int* ciU, const double* valU,
+                             const double* DU, double* X, double* Y, long long ld, int ncols, int cl);
 int trsm_blkc_clusters(int cl);
 // Dataflow (barrier-free) form of the level-blocked solve: task list of
 // phase-A (row >= 0) and phase-B (-1 - row) warp tasks in level order, each

@@ -819,9 +819,9 @@ __device__ __forceinline__ bool blk_solve(const BlkDev& S, const int* __restrict
   return true;
 }
 
-// MINB: CTAs per SM the register allocation must allow (1: the compiler's
-// choice, 48 registers, 5 CTAs; 6 and 8 trade a few spilled registers for more
-// resident warps); the autotuner times each
+// MINB: CTAs per SM the register allocation must allow (5: 48 registers, no
+// spills; 6 and 8 trade a few spilled registers for more resident warps); the
+// autotuner times each
 template <int MINB>
 __global__ void __launch_bounds__(BLK_THREADS, MINB) k_trsm_blk(BlkDev S, const int* __restrict__ ci,
                                                                 const double* __restrict__ val,
@@ -835,21 +835,28 @@ __global__ void __launch_bounds__(BLK_THREADS, MINB) k_trsm_blk(BlkDev S, const 
             [&]() { return group_barrier(ctr, ksplit * (++nbar), spin_limit, st); });
 }
 
-// The level-blocked solve with one thread-block cluster per 32-column block:
+
+// The level-blocked solve (both triangles) with one thread-block cluster per
+// 32-column block:
 // the cluster's CTAs share out a level's rows and meet at the hardware cluster
 // barrier between the phases (in place of k_trsm_blk's bounded group barrier
 // through global memory); the hardware co-schedules a cluster, so no wait can
 // be left without its partner.
-__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blkc(BlkDev S, const int* __restrict__ ci,
-                                                           const double* __restrict__ val,
-                                                           const double* __restrict__ D, double* X, double* Y,
+__global__ void __launch_bounds__(BLK_THREADS) k_trsm_blkc(BlkDev SL, const int* __restrict__ ciL,
+                                                           const double* __restrict__ valL,
+                                                           const double* __restrict__ DL, BlkDev SU,
+                                                           const int* __restrict__ ciU,
+                                                           const double* __restrict__ valU,
+                                                           const double* __restrict__ DU, double* X, double* Y,
                                                            long long ld, int ncols) {
   cg::cluster_group cl = cg::this_cluster();
   const int cb = blockIdx.x / cl.num_blocks();
-  blk_solve(S, ci, val, D, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), [&]() {
+  auto sync = [&]() {
     cl.sync();
     return true;
-  });
+  };
+  blk_solve(SL, ciL, valL, DL, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), sync);
+  blk_solve(SU, ciU, valU, DU, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), sync);
 }
 
 // Both triangles of a multi-RHS solve for every instance of a batch: one
@@ -1270,7 +1277,7 @@ cudaError_t launch_diag_inv4(cudaStream_t s, const DiagInvJob* jobs) {
 }
 
 static const void* trsm_blk_fn(int minb) {
-  return minb >= 8 ? (const void*)k_trsm_blk<8> : minb >= 6 ? (const void*)k_trsm_blk<6> : (const void*)k_trsm_blk<1>;
+  return minb >= 8 ? (const void*)k_trsm_blk<8> : minb >= 6 ? (const void*)k_trsm_blk<6> : (const void*)k_trsm_blk<5>;
 }
 int trsm_blk_max_blocks(int minb) {
   int a = 0;
@@ -1293,9 +1300,10 @@ static cudaLaunchConfig_t trsm_cluster_config(int nclusters, int cl, cudaStream_
   return cfg;
 }
 
-cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
-                             double* X, double* Y, long long ld, int ncols, int cl) {
-  if (ncols <= 0 || S.nlev <= 0) return cudaSuccess;
+cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& SL, const int* ciL, const double* valL,
+                             const double* DL, const BlkDev& SU, const int* ciU, const double* valU,
+                             const double* DU, double* X, double* Y, long long ld, int ncols, int cl) {
+  if (ncols <= 0) return cudaSuccess;
   if (cl > 8) {
     cudaError_t e = allow_cluster16((const void*)k_trsm_blkc);
     if (e != cudaSuccess) return e;
@@ -1304,7 +1312,7 @@ cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& S, const int* ci, con
   cudaLaunchAttribute at[1];
   const cudaLaunchConfig_t cfg = trsm_cluster_config(ncb, cl, s, at);
   note_launch();
-  return cudaLaunchKernelEx(&cfg, k_trsm_blkc, S, ci, val, D, X, Y, ld, ncols);
+  return cudaLaunchKernelEx(&cfg, k_trsm_blkc, SL, ciL, valL, DL, SU, ciU, valU, DU, X, Y, ld, ncols);
 }
 
 int trsm_blkc_clusters(int cl) {

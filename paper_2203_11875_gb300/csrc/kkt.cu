@@ -100,18 +100,31 @@ __global__ void k_dense_rows(int n, int ncol, int k, const double* __restrict__ 
                              double* __restrict__ out) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  // four passes of 32 columns in flight at once (their loads independent), each
+  // with its own accumulators, summed at the end
+  double acc[4][4] = {};
   const double* Mi = M + (long long)i * ld;
-  for (int cc = lane; cc < ncol; cc += 32) {
-    const double m = Mi[cc];
+  int cc = lane;
+  for (; cc + 96 < ncol; cc += 128) {
+    double m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m[u] = __ldcs(&Mi[cc + 32 * u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < k) acc[u][j] = fma(m[u], V[(long long)(cc + 32 * u) * k + j], acc[u][j]);
+  }
+  for (; cc < ncol; cc += 32) {
+    const double m = __ldcs(&Mi[cc]);
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (j < k) acc[j] = fma(m, V[(long long)cc * k + j], acc[j]);
+      if (j < k) acc[0][j] = fma(m, V[(long long)cc * k + j], acc[0][j]);
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (j < k) {
-      double a = acc[j];
+      double a = (acc[0][j] + acc[1][j]) + (acc[2][j] + acc[3][j]);
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       if (lane == 0) out[(long long)i * k + j] = (base ? base[(long long)i * k + j] : 0.0) + alpha * a;
     }
