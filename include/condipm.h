@@ -238,6 +238,46 @@ int opf_newton_step(opf_handle* h, const double* x, const double* u, const doubl
                     const double* sig_u, const double* sig_x, const double* sig_s, const double* rhs,
                     double delta_w, double delta_c, double* step, int* fail_col);
 
+/* ---- the hybrid full-space solver (Sec. 4.3; Table 2's full-space IPM) --------- */
+/* The comparison method of Sec. 4.3 solves the augmented system of
+ * Eq. kktmatrix:normal directly (the paper pairs its GPU model with MA27 on the
+ * CPU).  Here it is a GPU block LDL^T of the system with the slack step
+ * eliminated,
+ *   M = [[W + diag(Sigma_w) + delta_w E_u, G^T, A^T], [G, 0, 0],
+ *        [A, 0, -(Sigma_s^{-1} + delta_c) I]]   over [p_w; p_lambda; p_y],
+ * one dense diagonal block per bus (its unknowns with the multipliers of its
+ * rows, so the state / balance-row pairs are pivoted together) and one per
+ * flow-limit row, ordered by minimum degree; no pivoting across blocks.  The
+ * plan is built on the first call (host), the factor lives in the handle.
+ *
+ * Assemble M at the last opf_eval_derivatives with Sigma (device, natural order:
+ * sig_u[nu], sig_x[nx], sig_s[m]) and the regularisation delta_w (u block, the
+ * placement of K_cond + delta_w I) and delta_c (inequality rows), factorise it,
+ * and count its inertia from the diagonal blocks (Sylvester's law; host
+ * inertia[3] = (n+, n-, n0), may be NULL).  Returns OPF_OK when the inertia is
+ * (nu + nx, nx + m, 0) -- by Theorem 3 exactly when K_cond + delta_w I is
+ * positive definite --, NOT_PD when it is not (the factor is kept and can still
+ * solve), SINGULAR when a diagonal block is singular, TIMEOUT.  The condensed
+ * state of the handle is dropped (opf_kkt_solve needs a new opf_condense).
+ * Errors also: INVALID_ARG (no evaluation, NULL Sigma, negative delta). */
+int opf_fullspace_factor(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s,
+                         double delta_w, double delta_c, int* inertia);
+/* Solve K_aug p = -r with that factor for nrhs right-hand sides, same device
+ * layout as opf_kkt_solve ([r_u | r_x | r_s | r_lambda | r_y] in,
+ * [p_u | p_x | p_s | p_lambda | p_y] out), then up to `refine` corrections of
+ * iterative refinement against the full K_aug (0: the plain solve).  Host
+ * outputs (may be NULL): *steps the corrections taken, *residual the final
+ * relative max-norm residual (0 when refine = 0).  Errors: INVALID_ARG (no
+ * factor), TIMEOUT, CUDA, OOM. */
+int opf_fullspace_solve(opf_handle* h, const double* rhs, double* step, int nrhs, int refine, int* steps,
+                        double* residual);
+/* Statistics (host outputs, may be NULL): diagonal blocks, levels of the block
+ * elimination tree, scalar entries of the strict block lower factor,
+ * multiply-adds of one factorisation, log|det M| and the inertia of the last
+ * factorisation (0 and -1 before one).  Builds the plan if needed. */
+int opf_fullspace_stats(opf_handle* h, int* nblocks, int* levels, long long* nnz_l, long long* flops,
+                        double* logabsdet, int* inertia);
+
 /* ---- A11: reduce-then-linearize helpers (Algorithm 2, Sec. 4.4) -------------- */
 /* Newton-Raphson on g(x, u) = 0 for x at fixed u (device u[nu]; device x[nx]
  * in: start, out: solution) to ||g||_inf <= tol.  Errors: PF_FAILED. */
@@ -273,7 +313,16 @@ typedef struct opf_ipm_options {
                           defers to (no restoration phase: when the step length
                           runs out, a larger primal regularisation shortens the
                           step)                                                   */
+    int linear_solver; /* OPF_LINSOLVE_CONDENSED: the condensed step (LinRed, RedLin);
+                          OPF_LINSOLVE_FULLSPACE (LinRed only): the hybrid
+                          full-space IPM of Sec. 4.3 -- the same loop, model,
+                          derivatives and regularisation, each step from
+                          opf_fullspace_factor / opf_fullspace_solve (the inertia
+                          test of the block factor in place of the Cholesky test,
+                          equivalent by Theorem 3)                                 */
 } opf_ipm_options;
+#define OPF_LINSOLVE_CONDENSED 0
+#define OPF_LINSOLVE_FULLSPACE 1
 #define OPF_LINESEARCH_MERIT  0
 #define OPF_LINESEARCH_FILTER 1
 

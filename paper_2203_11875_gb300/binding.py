@@ -45,7 +45,8 @@ class opf_options(C.Structure):
 
 class opf_ipm_options(C.Structure):
     _fields_ = [("variant", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("mu0", C.c_double),
-                ("pf_tol", C.c_double), ("verbose", C.c_int), ("line_search", C.c_int)]
+                ("pf_tol", C.c_double), ("verbose", C.c_int), ("line_search", C.c_int),
+                ("linear_solver", C.c_int)]
 
 
 class opf_ipm_result(C.Structure):
@@ -84,6 +85,12 @@ _SIGS = {
     "opf_newton_step": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_void_p, _ip]),
     "opf_kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_kkt_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "opf_fullspace_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                       _ip]),
+    "opf_fullspace_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, _ip,
+                                      C.POINTER(C.c_double)]),
+    "opf_fullspace_stats": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_double), _ip]),
     "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
     "opf_reduced_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result)]),
@@ -347,12 +354,40 @@ class Handle:
         _check(self._lib.opf_kkt_solve_adjoint(self._h, _ptr(rhs), _ptr(sol), int(nrhs)),
                "opf_kkt_solve_adjoint")
 
+    def fullspace_factor(self, sig_u, sig_x, sig_s, delta_w=0.0, delta_c=0.0):
+        """opf_fullspace_factor: returns (status, (n+, n-, n0)); status is OPF_OK
+        or OPF_ERR_NOT_PD (wrong inertia), other codes raise."""
+        inert = (C.c_int * 3)()
+        rc = self._lib.opf_fullspace_factor(self._h, _ptr(sig_u), _ptr(sig_x), _ptr(sig_s), float(delta_w),
+                                            float(delta_c), inert)
+        if rc not in (OPF_OK, OPF_ERR_NOT_PD):
+            _check(rc, "opf_fullspace_factor")
+        return rc, tuple(inert)
+
+    def fullspace_solve(self, rhs, step, nrhs=1, refine=0):
+        """opf_fullspace_solve: returns (corrections taken, final relative residual)."""
+        st = C.c_int(0)
+        res = C.c_double(0.0)
+        _check(self._lib.opf_fullspace_solve(self._h, _ptr(rhs), _ptr(step), int(nrhs), int(refine), C.byref(st),
+                                             C.byref(res)), "opf_fullspace_solve")
+        return st.value, res.value
+
+    def fullspace_stats(self):
+        nb, lv = C.c_int(0), C.c_int(0)
+        nl, fl = C.c_longlong(0), C.c_longlong(0)
+        ld = C.c_double(0.0)
+        inert = (C.c_int * 3)()
+        _check(self._lib.opf_fullspace_stats(self._h, C.byref(nb), C.byref(lv), C.byref(nl), C.byref(fl),
+                                             C.byref(ld), inert), "opf_fullspace_stats")
+        return dict(nblocks=nb.value, levels=lv.value, nnz_l=nl.value, flops=fl.value, logabsdet=ld.value,
+                    inertia=tuple(inert))
+
     def solve(self, variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
-              line_search="merit"):
+              line_search="merit", linear_solver="condensed"):
         """opf_solve: the interior-point loop; returns the result fields as a dict.
-        line_search: "merit" or "filter" (LinRed)."""
-        o = opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
-                            int(bool(verbose)), 1 if line_search == "filter" else 0)
+        line_search: "merit" or "filter" (LinRed); linear_solver: "condensed" or
+        "fullspace" (the hybrid full-space IPM, LinRed)."""
+        o = _ipm_options(variant, tol, max_iter, mu0, pf_tol, verbose, line_search, linear_solver)
         r = opf_ipm_result()
         rc = self._lib.opf_solve(self._h, C.byref(o), C.byref(r))
         out = {f: getattr(r, f) for f, _ in opf_ipm_result._fields_}
@@ -425,9 +460,12 @@ class Handle:
 
 
 def _ipm_options(variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
-                 line_search="merit"):
+                 line_search="merit", linear_solver="condensed"):
+    if linear_solver not in ("condensed", "fullspace"):
+        raise ValueError(f"linear_solver: {linear_solver!r}")
     return opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
-                           int(bool(verbose)), 1 if line_search == "filter" else 0)
+                           int(bool(verbose)), 1 if line_search == "filter" else 0,
+                           1 if linear_solver == "fullspace" else 0)
 
 
 class Batch:

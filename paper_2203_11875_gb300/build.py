@@ -23,9 +23,9 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC"]
-CU_SOURCES = ["kernels_model.cu", "kernels_linalg.cu", "kernels_trsm.cu", "api.cu", "kkt.cu", "ipm.cu", "sens.cu", "batch.cu", "noalloc.cu", "peak.cu"]
-CXX_SOURCES = ["plan.cpp"]
-HEADERS = ["common.cuh", "plan.h", "opf_handle.h", "internal.h"]
+CU_SOURCES = ["kernels_model.cu", "kernels_linalg.cu", "kernels_trsm.cu", "api.cu", "kkt.cu", "ipm.cu", "sens.cu", "batch.cu", "noalloc.cu", "peak.cu", "fullspace.cu"]
+CXX_SOURCES = ["plan.cpp", "fsplan.cpp"]
+HEADERS = ["common.cuh", "plan.h", "fsplan.h", "opf_handle.h", "internal.h"]
 
 
 def _nvcc() -> str:

@@ -1184,6 +1184,7 @@ void opf_destroy(opf_handle* h) {
   for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->cf_exec) cudaGraphExecDestroy(h->cf_exec);
+  condipm::fs_release(h);
   for (void* p : h->allocs) cudaFree(p);
   if (h->ws) cudaFree(h->ws);
   if (h->ybuf) cudaFree(h->ybuf);

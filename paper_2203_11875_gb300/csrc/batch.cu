@@ -173,6 +173,8 @@ extern "C" int opf_batch_autotune(opf_batch* b) {
 extern "C" int opf_batch_solve(opf_batch* b, const opf_ipm_options* opt, opf_ipm_result* results,
                                double* wall_ms) {
   if (!b || !results) return OPF_ERR_INVALID_ARG;
+  // batches run the condensed step (their rendezvous is the batched condensation)
+  if (opt && opt->linear_solver != OPF_LINSOLVE_CONDENSED) return OPF_ERR_INVALID_ARG;
   const int n = int(b->hs.size());
   std::vector<int> rcs(n, OPF_OK);
   const auto t0 = std::chrono::steady_clock::now();

@@ -31,12 +31,26 @@ KB kb_at(const Plan& P, double* base, int k);
 // p = K_aug^{-1} b through the condensed system (b_l = 0 may be declared)
 int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, double* scratch);
 // R = b - K_aug z with the full sparse K_aug
-int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R);
+// (with delta_w > 0: + delta_w on the u block of K_aug's primal rows)
+int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R, double delta_w = 0.0);
 // z <- refined solution of K_aug z = b (solve_first: start from the condensed
 // solve, else from z); at most max_steps corrections; relative max-norm residual
 // and the corrections taken are returned
 int kkt_refine(opf_handle* h, int k, const KB& b, const KB& z, bool solve_first, bool bl_zero, int max_steps,
-               double* scratch, double* final_res, int* steps);
+               double* scratch, double* final_res, int* steps, bool fullspace = false);
+// the hybrid full-space solver (block LDL^T of the slack-eliminated augmented
+// matrix): Sigma of the next factorisations (device, natural order; drops the
+// condensed state), the assembly + factorisation + inertia count with
+// (delta_w, delta_c) (status word: SINGULAR, TIMEOUT, NOT_PD = wrong inertia),
+// the inertia read-back, p = K_aug^{-1} b in the KB layout, the natural-layout
+// solve with refinement, and the release of its state
+int fs_set_sigma(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s);
+int fs_factor_async(opf_handle* h, double delta_w, double delta_c);
+int fs_read_inertia(opf_handle* h, int* inertia, double* logdet);
+int fs_core(opf_handle* h, int k, const KB& b, const KB& p);
+int fs_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int refine, int* steps, double* res);
+void fs_release(opf_handle* h);
+double fs_delta_w(const opf_handle* h);   // delta_w of the last block factorisation
 int read_status(opf_handle* h, int* info = nullptr);
 // bracket the launches enqueued between the two calls with events (opf_profile)
 void ph_begin(opf_handle* h, int phase);

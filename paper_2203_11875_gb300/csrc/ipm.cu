@@ -245,6 +245,18 @@ int eval_fgh(opf_handle* h, Dev& d, const Vec& w, double& f, Vec& g, Vec& hv) {
   return OPF_OK;
 }
 
+// The factorisation with primal regularisation d on the u block: the Cholesky
+// of Kred + d I, or in the hybrid full-space mode the block LDL^T of the
+// augmented matrix with d on its u diagonal (its inertia test reports NOT_PD
+// exactly when Kred + d I is not positive definite, Theorem 3)
+int factor_delta(opf_handle* h, double d) { return h->ipm_fs ? fs_factor_async(h, d, 0.0) : factor_kred_async(h, d); }
+
+// K_aug p = -r for the loop's one right-hand side: the condensed recovery, or
+// the block factor with up to three refinement corrections
+int solve_step(opf_handle* h, const double* rhs, double* step) {
+  return h->ipm_fs ? fs_solve_impl(h, rhs, step, 1, 3, nullptr, nullptr) : kkt_solve_impl(h, rhs, step, 1, 0);
+}
+
 // Cholesky of Kred + delta I with the inertia-correction schedule; delta in/out.
 // skip_zero: the attempt with delta = 0 already failed (NOT_PD)
 int factor_with_correction(opf_handle* h, double& delta, double delta_last, int& attempts, bool skip_zero = false) {
@@ -252,9 +264,16 @@ int factor_with_correction(opf_handle* h, double& delta, double delta_last, int&
   double d = 0.0;
   if (skip_zero) d = delta_last > 0.0 ? std::max(1e-20, delta_last / 3.0) : 1e-4;
   for (;;) {
-    TRYD(factor_kred_async(h, d));
+    TRYD(factor_delta(h, d));
     ++attempts;
     int rc = read_status(h, nullptr);
+    if (h->ipm_fs && h->ipm_verbose) {
+      int in[3];
+      double ld = 0.0;
+      TRYD(fs_read_inertia(h, in, &ld));
+      std::printf("  full-space factor delta_w %.1e: status %d inertia (%d, %d, %d) want (%d, %d, 0)\n", d, rc, in[0],
+                  in[1], in[2], h->P.nw, h->P.nx + h->P.m);
+    }
     if (rc == OPF_OK) {
       h->have_factor = true;
       delta = d;
@@ -274,6 +293,14 @@ int factor_with_correction(opf_handle* h, double& delta, double delta_last, int&
 // is refused, or while phases are being profiled, the launches are enqueued
 // one by one.  Returns the device status (one synchronisation).
 int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
+  if (h->ipm_fs) {
+    // hybrid full-space mode: assemble and factor the augmented matrix
+    TRYD(fs_set_sigma(h, d.sig_u, d.sig_x, d.sig_s));
+    TRYD(fs_factor_async(h, 0.0, 0.0));
+    const int rc = read_status(h, nullptr);
+    h->have_factor = false;
+    return rc;
+  }
   if (h->batch) {
     // a lockstep batch: one batched call serves every instance still iterating
     const int rc = batch_join(h->batch, h->batch_idx, d.sig_u, d.sig_x, d.sig_s);
@@ -338,7 +365,17 @@ Vec flat_start(const Plan& P) {
 }  // namespace
 
 // ------------------------------------------------------------------ LinRed
+int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R);
+
 int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
+  h->ipm_fs = o.linear_solver == OPF_LINSOLVE_FULLSPACE;
+  h->ipm_verbose = o.verbose != 0;
+  const int rc = ipm_linred_body(h, o, R);
+  h->ipm_fs = false;
+  return rc;
+}
+
+int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
   const Plan& P = h->P;
   const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
   const int nkkt = nw + 2 * m + nx;
@@ -446,7 +483,7 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
     for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
       t0 = clk::now();
       TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
-      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
+      TRYD(solve_step(h, d.rhs, d.step));
       TRYD(d2h(h->s, step.data(), d.step, nkkt));
       CKD(cudaStreamSynchronize(h->s));
       R.ms_solve += ms_since(t0);
@@ -508,7 +545,7 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
             for (int k = 0; k < SOC_MAX && !accepted; ++k) {
               std::copy(csoc.begin(), csoc.end(), rs.begin() + nw + m);
               TRYD(h2d(h->s, d.rhs, rs.data(), nkkt));
-              TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
+              TRYD(solve_step(h, d.rhs, d.step));
               TRYD(d2h(h->s, q.data(), d.step, nkkt));
               CKD(cudaStreamSynchronize(h->s));
               Vec qw(q.begin(), q.begin() + nw), qs(q.begin() + nw, q.begin() + nw + m);
@@ -551,7 +588,7 @@ int ipm_linred(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
       if (!accepted) {
         // backtracking failed: shorten the step by a larger primal regularisation
         delta = std::max(1e-8, 10.0 * delta);
-        TRYD(factor_kred_async(h, delta));
+        TRYD(factor_delta(h, delta));
         ++R.n_factor;
         int rc = read_status(h, nullptr);
         if (rc == OPF_ERR_NOT_PD) { att = 0; TRYD(factor_with_correction(h, delta, delta, att)); R.n_factor += att; }
@@ -748,7 +785,7 @@ int ipm_redlin(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) {
     for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
       t0 = clk::now();
       TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
-      TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
+      TRYD(solve_step(h, d.rhs, d.step));
       TRYD(d2h(h->s, step.data(), d.step, nkkt));
       CKD(cudaStreamSynchronize(h->s));
       R.ms_solve += ms_since(t0);
@@ -989,7 +1026,9 @@ extern "C" int opf_solve(opf_handle* h, const opf_ipm_options* opt, opf_ipm_resu
   if (!(o.tol > 0) || o.max_iter < 0 || !(o.mu0 > 0) || !(o.pf_tol > 0) ||
       (o.variant != OPF_LINRED && o.variant != OPF_REDLIN) ||
       (o.line_search != OPF_LINESEARCH_MERIT && o.line_search != OPF_LINESEARCH_FILTER) ||
-      (o.line_search == OPF_LINESEARCH_FILTER && o.variant != OPF_LINRED))
+      (o.line_search == OPF_LINESEARCH_FILTER && o.variant != OPF_LINRED) ||
+      (o.linear_solver != OPF_LINSOLVE_CONDENSED && o.linear_solver != OPF_LINSOLVE_FULLSPACE) ||
+      (o.linear_solver == OPF_LINSOLVE_FULLSPACE && o.variant != OPF_LINRED))
     return OPF_ERR_INVALID_ARG;
   *res = opf_ipm_result{};
   h->have_solution = false;

@@ -239,13 +239,14 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   return OPF_OK;
 }
 
-int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R) {
+int kkt_residual(opf_handle* h, int k, const KB& b, const KB& z, const KB& R, double delta_w) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const int nw = P.nw, nx = P.nx, m = P.m;
-  // R_w = b_w - (W + Sigma_w) z_w - G^T z_l - A^T z_y
+  // R_w = b_w - (W + Sigma_w + delta_w E_u) z_w - G^T z_l - A^T z_y
   k_rows_scale_sub<<<nblk((long long)nw * k, 256), 256, 0, s>>>(nw, k, h->sig_c, z.w, b.w, R.w);
   TRYK(launched());
+  if (delta_w > 0.0) CKK(launch_axpby(s, (long long)P.nu * k, -delta_w, z.w, 1.0, R.w, R.w));
   CKK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Wval, nullptr, z.w, k, 1, R.w, k, 1, k, -1.0, 1.0));
   CKK(launch_spmm(s, nw, h->GcT_rp, h->GcT_ci, h->Gval, h->GcT_map, z.l, k, 1, R.w, k, 1, k, -1.0, 1.0));
   CKK(launch_spmm(s, nw, h->AT_rp, h->AT_ci, h->Aval, h->AT_map, z.y, k, 1, R.w, k, 1, k, -1.0, 1.0));
@@ -276,7 +277,7 @@ int device_absmax(opf_handle* h, const double* x, long long n, double* part, dou
 }
 
 int kkt_refine(opf_handle* h, int k, const KB& b, const KB& z, bool solve_first, bool bl_zero, int max_steps,
-               double* scratch, double* final_res, int* steps) {
+               double* scratch, double* final_res, int* steps, bool fullspace) {
   const Plan& P = h->P;
   const size_t N = kkt_rows(P) * (size_t)k;
   double* Rbase = scratch;
@@ -284,16 +285,16 @@ int kkt_refine(opf_handle* h, int k, const KB& b, const KB& z, bool solve_first,
   double* part = Dbase + N;
   double* core = part + ABSMAX_PARTS + 8;
   const KB R = kb_at(P, Rbase, k), D = kb_at(P, Dbase, k);
-  if (solve_first) TRYK(kkt_core(h, k, b, z, bl_zero, core));
+  if (solve_first) TRYK(fullspace ? fs_core(h, k, b, z) : kkt_core(h, k, b, z, bl_zero, core));
   double bn = 0.0, rn = 0.0, prev = INFINITY;
   TRYK(device_absmax(h, b.w, (long long)N, part, &bn));
   int it = 0;
   for (; it <= max_steps; ++it) {
-    TRYK(kkt_residual(h, k, b, z, R));
+    TRYK(kkt_residual(h, k, b, z, R, fullspace ? fs_delta_w(h) : 0.0));
     TRYK(device_absmax(h, Rbase, (long long)N, part, &rn));
     if (!(rn > 1e-15 * std::max(bn, 1e-300)) || rn > 0.5 * prev || it == max_steps) break;
     prev = rn;
-    TRYK(kkt_core(h, k, R, D, false, core));
+    TRYK(fullspace ? fs_core(h, k, R, D) : kkt_core(h, k, R, D, false, core));
     CKK(launch_axpby(h->s, (long long)N, 1.0, Dbase, 1.0, z.w, z.w));
   }
   if (final_res) *final_res = bn > 0 ? rn / bn : rn;

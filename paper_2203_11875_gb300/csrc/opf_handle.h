@@ -9,6 +9,9 @@
 #include "plan.h"
 
 struct opf_batch;
+namespace condipm {
+struct FsState;
+}
 
 struct opf_handle {
   condipm::Plan P;
@@ -157,6 +160,10 @@ struct opf_handle {
   double vjp_res = 0.0;
   int vjp_max_refine = 4;
   int* sens_pq = nullptr;        // [2 nb] elimination position of P_i / Q_i rows, -1 if none (in allocs)
+  // the hybrid full-space solver's plan, factor and buffers (built on first use)
+  condipm::FsState* fs = nullptr;
+  bool ipm_fs = false;           // the running interior-point loop is the hybrid full-space one
+  bool ipm_verbose = false;      // ... and prints its progress
   // phase timing (opf_profile)
   bool profiling = false;
   struct PhaseRec { int phase; cudaEvent_t a, b; };

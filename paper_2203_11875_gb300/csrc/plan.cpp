@@ -959,4 +959,8 @@ std::string build_cl_sched(const ColSched& C, int CL, ClSched& S) {
   }
   return "";
 }
+std::vector<int> min_degree_order(int n, const std::vector<std::vector<int>>& adj, const std::vector<int>& wt) {
+  return min_degree(n, adj, wt);
+}
+
 }  // namespace condipm

@@ -184,6 +184,10 @@ struct Plan {
 void build_sn_stream(const CSR& M, const SnSched& S, const std::vector<int>& start, bool upper,
                      bool unit, int budget, SnStream& out);
 
+// Minimum-degree ordering of a weighted graph (adjacency lists, weights =
+// unknowns per node); ties broken by node index.
+std::vector<int> min_degree_order(int n, const std::vector<std::vector<int>>& adj, const std::vector<int>& wt);
+
 // Builds the plan; returns an empty string on success, else the reason.
 std::string build_plan(Plan& P, int nb, int nl, int ng, int slack, const double* Pd,
                        const double* Qd, const double* Vmin, const double* Vmax,

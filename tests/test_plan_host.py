@@ -46,3 +46,35 @@ def test_cluster_solve_schedules(checker, tmp_path, name):
     _write(gridgen.WORKLOADS[name](), str(path))
     res = subprocess.run([str(checker), str(path)], capture_output=True, text=True, timeout=120)
     assert res.returncode == 0 and res.stdout.strip() == "ok", res.stdout + res.stderr
+
+
+@pytest.fixture(scope="module")
+def fs_checker(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    out = tmp_path_factory.mktemp("fsplan") / "fsplan_check"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, "-o", str(out),
+                    os.path.join(ROOT, "tests", "fsplan_check.cpp"), os.path.join(CSRC, "plan.cpp"),
+                    os.path.join(CSRC, "fsplan.cpp")], check=True, capture_output=True)
+    return out
+
+
+@pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000"])
+def test_fullspace_block_plan(fs_checker, tmp_path, name):
+    """The block LDL^T plan of the hybrid full-space system: a permutation of
+    the unknowns, a symmetric fill-closed block pattern in level order, and
+    assembly slots with one source each (tests/fsplan_check.cpp)."""
+    net = gridgen.WORKLOADS[name]()
+    path = tmp_path / f"{name}.bin"
+    _write(net, str(path))
+    res = subprocess.run([str(fs_checker), str(path)], capture_output=True, text=True, timeout=120)
+    out = res.stdout.split()
+    assert res.returncode == 0 and out and out[0] == "ok", res.stdout + res.stderr
+    n, nblk, bmax = int(out[1]), int(out[2]), int(out[3])
+    from oracle import model
+    lay = model.Layout(net)
+    assert n == lay.nw + lay.nx + lay.m
+    # one block per bus and one per flow-limit row; at most 5 unknowns per bus
+    assert nblk == net.nb + 2 * len(lay.lim)
+    assert 1 <= bmax <= 5
