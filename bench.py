@@ -365,6 +365,69 @@ def time_condense(h, D, delta, reps, stream, torch):
     return float(np.mean(ts))
 
 
+def run_fullspace(binding, net, it, delta, D, stream, flush, torch, split, no_solve, reps=20):
+    """The hybrid full-space IPM's linear algebra (Sec. 4.3, Table 2's comparison
+    method) on the same grid10k iterate: assembly + block LDL^T + inertia, then
+    the step, CUDA events on the handle's stream with an L2 flush before each
+    repetition; and whole solves of both IPMs."""
+    hf = binding.Handle(net)
+    hf.set_stream(stream)
+    step = torch.zeros(hf.n_kkt, dtype=torch.float64, device=D["x"].device)
+    for _ in range(3):
+        hf.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+        rc, inert = hf.fullspace_factor(D["sig_u"], D["sig_x"], D["sig_s"], delta_w=delta)
+        hf.fullspace_solve(D["r"], step, 1, 0)
+    assert rc == binding.OPF_OK, inert
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps)]
+    hf.profile(True)
+    for k in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        hf.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+        ev[k][0].record(stream)
+        hf.fullspace_factor(D["sig_u"], D["sig_x"], D["sig_s"], delta_w=delta)
+        ev[k][1].record(stream)
+        hf.fullspace_solve(D["r"], step, 1, 0)
+        ev[k][2].record(stream)
+        steps, res = hf.fullspace_solve(D["r"], step, 1, 3)
+        ev[k][3].record(stream)
+    torch.cuda.synchronize()
+    ph = hf.phase_times()
+    hf.profile(False)
+    st = hf.fullspace_stats()
+    t_fac = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    t_sol = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    t_ref = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+    linred = split["condense_cholesky"] + split["condensed_rhs"] + split["step_recovery"]
+    out = {"workload": "grid10k stored iterate: augmented system with the slack step eliminated, "
+                       f"{hf.nw + hf.nx + hf.m} unknowns, {st['nblocks']} diagonal blocks",
+           "factor_ms": t_fac, "solve_ms": t_sol, "solve_refined_ms": t_ref, "refine_steps": steps,
+           "refined_rel_residual": res, "per_iteration_ms": t_fac + t_sol,
+           "linred_per_iteration_ms": linred, "linred_over_fullspace": linred / (t_fac + t_sol),
+           "phases_ms_per_rep": {p: v[0] / reps for p, v in ph.items() if v[0] > 0},
+           "inertia": list(inert), "block_levels": st["levels"], "nnz_l": st["nnz_l"],
+           "tuning": hf.fullspace_tuning(),
+           "factor_gflops": 2.0 * st["flops"] / (ph["chol"][0] / reps * 1e-3) / 1e9,
+           "note": "LinRed's per-iteration linear algebra = condense + Cholesky + condensed RHS + step recovery "
+                   "(split_ms_per_step); the hybrid's = assembly + block LDL^T + inertia + one solve"}
+    del hf
+    if not no_solve:
+        for name, mk in (("grid2000", gridgen.grid2000), ("grid10k", gridgen.grid10k)):
+            row = {}
+            for ls in ("condensed", "fullspace"):
+                hs = binding.Handle(mk())
+                hs.set_stream(stream)
+                t0 = time.perf_counter()
+                r = hs.solve("linred", linear_solver=ls)
+                row[ls] = {"wall_s": time.perf_counter() - t0, "iters": r["iters"], "obj": r["obj"],
+                           "status": r["status"], "ms_condense_or_factor": r["ms_condense"] + r["ms_factor"],
+                           "ms_solve": r["ms_solve"]}
+                del hs
+            row["rel_obj_diff"] = abs(row["condensed"]["obj"] - row["fullspace"]["obj"]) / abs(row["condensed"]["obj"])
+            out[f"solve_{name}"] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,6 +440,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the whole-solve timing")
     ap.add_argument("--no-vjp", action="store_true", help="skip the 10,000-bus dispatch-derivative timing")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FP64 peak probes (derived peak instead)")
+    ap.add_argument("--no-fullspace", action="store_true", help="skip the hybrid full-space comparison")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
@@ -590,6 +654,9 @@ def main():
                               "solve_iters": r10["iters"], "solve_obj": r10["obj"], "prepare_ms": t_prep * 1e3,
                               "vjp_ms": float(np.median(reps)) * 1e3, "refine_steps": info["refine_steps"],
                               "rel_residual": info["rel_residual"], "polish_iters": info["polish_iters"]}
+    if not args.no_fullspace:
+        out["hybrid_fullspace"] = run_fullspace(binding, net, it, delta, D, stream, flush, torch,
+                                                out["split_ms_per_step"], args.no_solve)
     if not args.no_batch:
         out["batch96"] = run_batch(binding, args.batch_threads, rank, world, dist, dev)
     # one whole interior-point solve of the 2,000-bus network (LinRed), GPU path

@@ -277,6 +277,12 @@ int opf_fullspace_solve(opf_handle* h, const double* rhs, double* step, int nrhs
  * factorisation (0 and -1 before one).  Builds the plan if needed. */
 int opf_fullspace_stats(opf_handle* h, int* nblocks, int* levels, long long* nnz_l, long long* flops,
                         double* logabsdet, int* inertia);
+/* Launch shapes of the block factorisation and solves (host outputs, may be
+ * NULL): grids[2] = CTAs of the factorisation and of the solves (cooperative
+ * grids; fewer resident warps poll the dependency flags less), ms[8] = the
+ * timings of the first factorisation and the first solve at 1, 2, 4 and 8 CTAs
+ * per SM (0 = not tried).  INVALID_ARG before the plan exists. */
+int opf_fullspace_tuning(const opf_handle* h, int* grids, float* ms);
 
 /* ---- A11: reduce-then-linearize helpers (Algorithm 2, Sec. 4.4) -------------- */
 /* Newton-Raphson on g(x, u) = 0 for x at fixed u (device u[nu]; device x[nx]

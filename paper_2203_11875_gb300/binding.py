@@ -91,6 +91,7 @@ _SIGS = {
                                       C.POINTER(C.c_double)]),
     "opf_fullspace_stats": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_double), _ip]),
+    "opf_fullspace_tuning": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_powerflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, _ip]),
     "opf_reduced_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_solve": (C.c_int, [C.c_void_p, C.POINTER(opf_ipm_options), C.POINTER(opf_ipm_result)]),
@@ -381,6 +382,12 @@ class Handle:
                                              C.byref(ld), inert), "opf_fullspace_stats")
         return dict(nblocks=nb.value, levels=lv.value, nnz_l=nl.value, flops=fl.value, logabsdet=ld.value,
                     inertia=tuple(inert))
+
+    def fullspace_tuning(self):
+        g = (C.c_int * 2)()
+        ms = (C.c_float * 8)()
+        _check(self._lib.opf_fullspace_tuning(self._h, g, ms), "opf_fullspace_tuning")
+        return dict(grid_factor=g[0], grid_solve=g[1], factor_ms=list(ms[:4]), solve_ms=list(ms[4:]))
 
     def solve(self, variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
               line_search="merit", linear_solver="condensed"):

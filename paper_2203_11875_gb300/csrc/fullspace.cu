@@ -55,7 +55,11 @@ struct FsState {
   double* ldet = nullptr;        // [1] log|det M|
   double* X = nullptr;           // permuted right-hand sides (n x xcap)
   int xcap = 0;
-  int grid = 1;                  // CTAs of the cooperative row kernels
+  // CTAs of the cooperative row kernels (factorisation, solves): fewer resident
+  // warps poll the flags less; timed on first use over FS_GRIDS CTAs per SM
+  int grid_f = 1, grid_s = 1, per_f = 1, per_s = 1;
+  bool tuned_f = false, tuned_s = false;
+  float tune_f[4] = {}, tune_s[4] = {};
   bool sigma_set = false, factored = false;
   double delta_w = 0.0, delta_c = 0.0;
   int inertia[3] = {-1, -1, -1};
@@ -67,6 +71,7 @@ namespace {
 constexpr int FS_THREADS = 128;
 constexpr int FS_WARPS = FS_THREADS / 32;
 constexpr int FS_KC = 4;   // right-hand-side columns per solve pass (FS_BMAX * FS_KC <= 32)
+constexpr int FS_GRIDS[4] = {1, 2, 4, 8};   // CTAs per SM tried by the grid tuner
 static_assert(FS_BMAX * FS_KC <= 32, "one lane per (row, column) of a block");
 
 // lane 0 waits (bounded) until flags[k] == epoch with acquire semantics;
@@ -135,9 +140,24 @@ __global__ void __launch_bounds__(FS_THREADS) k_fs_factor(FsDev D, double* val, 
     const int I = D.rows[t];
     const int bI = D.bptr[I + 1] - D.bptr[I];
     const int qd = D.bdiag[I];
+    // the flags of the next 32 L columns are read at once (one acquire load per
+    // lane); only columns not yet published then cost a wait
+    unsigned ready = 0;
+    int win = -1;
     for (int q = D.brp[I]; q < qd; ++q) {
       const int K = D.bci[q], bK = D.bptr[K + 1] - D.bptr[K];
-      if (!fs_wait(flags, K, epoch, st, spin_limit, lane)) return;
+      if (win < 0 || q >= win + 32) {
+        win = q;
+        unsigned f = 0;
+        if (q + lane < qd)
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + D.bci[q + lane]) : "memory");
+        ready = __ballot_sync(0xffffffffu, q + lane < qd && f == epoch);
+      }
+      if (!((ready >> (q - win)) & 1u)) {
+        if (!fs_wait(flags, K, epoch, st, spin_limit, lane)) return;
+      } else {
+        __syncwarp();   // orders the reading lane's acquire before every lane's loads of row K
+      }
       double* Wik = val + D.voff[q];
       const double* Dk = dinv + D.doff[K];
       const int nIK = bI * bK;
@@ -150,40 +170,44 @@ __global__ void __launch_bounds__(FS_THREADS) k_fs_factor(FsDev D, double* val, 
       }
       __syncwarp();
       for (int e = lane; e < nIK; e += 32) Wik[e] = L[e];
-      // W_IJ -= L_IK U_KJ over the U blocks of row K; two updates in flight
+      // W_IJ -= L_IK U_KJ over the U blocks of row K, four updates in flight
       const long long u0 = D.upd_ptr[q], u1 = D.upd_ptr[q + 1];
-      long long u = u0;
-      for (; u + 1 < u1; u += 2) {
-        const int s0 = D.upd_src[u], d0 = D.upd_dst[u], s1 = D.upd_src[u + 1], d1 = D.upd_dst[u + 1];
-        const int J0 = D.bci[s0], J1 = D.bci[s1];
-        const int b0 = D.bptr[J0 + 1] - D.bptr[J0], b1 = D.bptr[J1 + 1] - D.bptr[J1];
-        const double* U0 = val + D.voff[s0];
-        const double* U1 = val + D.voff[s1];
-        double* W0 = val + D.voff[d0];
-        double* W1 = val + D.voff[d1];
-        const int n0 = bI * b0, n1 = bI * b1;
-        for (int e = lane; e < n0 || e < n1; e += 32) {
-          double a0 = 0.0, a1 = 0.0;
-          const int r0 = e / b0, c0 = e - r0 * b0, r1 = e / b1, c1 = e - r1 * b1;
-          const bool v0 = e < n0, v1 = e < n1;
-          for (int k = 0; k < bK; ++k) {
-            if (v0) a0 = fma(L[r0 * bK + k], __ldcg(&U0[k * b0 + c0]), a0);
-            if (v1) a1 = fma(L[r1 * bK + k], __ldcg(&U1[k * b1 + c1]), a1);
+      for (long long u = u0; u < u1; u += 4) {
+        const double* Ub[4];
+        double* Wb[4];
+        int bJ[4], nE[4];
+        int nmax = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (u + i < u1) {
+            const int sx = D.upd_src[u + i], dx = D.upd_dst[u + i], J = D.bci[sx];
+            bJ[i] = D.bptr[J + 1] - D.bptr[J];
+            nE[i] = bI * bJ[i];
+            Ub[i] = val + D.voff[sx];
+            Wb[i] = val + D.voff[dx];
+            nmax = max(nmax, nE[i]);
+          } else {
+            bJ[i] = 1;
+            nE[i] = 0;
+            Ub[i] = nullptr;
+            Wb[i] = nullptr;
           }
-          if (v0) W0[e] -= a0;
-          if (v1) W1[e] -= a1;
         }
-      }
-      if (u < u1) {
-        const int s0 = D.upd_src[u], d0 = D.upd_dst[u];
-        const int J0 = D.bci[s0], b0 = D.bptr[J0 + 1] - D.bptr[J0];
-        const double* U0 = val + D.voff[s0];
-        double* W0 = val + D.voff[d0];
-        for (int e = lane; e < bI * b0; e += 32) {
-          const int r0 = e / b0, c0 = e - r0 * b0;
-          double a0 = 0.0;
-          for (int k = 0; k < bK; ++k) a0 = fma(L[r0 * bK + k], __ldcg(&U0[k * b0 + c0]), a0);
-          W0[e] -= a0;
+        for (int e = lane; e < nmax; e += 32) {
+          double a[4] = {0.0, 0.0, 0.0, 0.0};
+          int r[4], c[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            r[i] = e / bJ[i];
+            c[i] = e - r[i] * bJ[i];
+          }
+          for (int k = 0; k < bK; ++k)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (e < nE[i]) a[i] = fma(L[r[i] * bK + k], __ldcg(&Ub[i][k * bJ[i] + c[i]]), a[i]);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (e < nE[i]) Wb[i][e] -= a[i];
         }
       }
       __syncwarp();
@@ -372,60 +396,103 @@ __global__ void k_fs_scatter_back(int nw, int nx, int m, int k, int j0, int kc, 
   }
 }
 
-// forward: y_I = x_I - sum_K L_IK y_K (unit block lower factor); X row-major n x kc
-__global__ void __launch_bounds__(FS_THREADS) k_fs_fwd(FsDev D, const double* val, double* X, int kc,
-                                                       unsigned* flags, unsigned epoch, int* st,
-                                                       long long spin_limit) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x + gridDim.x * wib, nwarp = gridDim.x * FS_WARPS;
-  for (int t = gw; t < D.nblk; t += nwarp) {
-    const int I = D.rows[t];
-    const int p0 = D.bptr[I], bI = D.bptr[I + 1] - p0;
-    const int r = lane / kc, j = lane - r * kc;
-    const bool act = r < bI;
-    double acc = act ? __ldcg(&X[(long long)(p0 + r) * kc + j]) : 0.0;
-    for (int q = D.brp[I]; q < D.bdiag[I]; ++q) {
-      const int K = D.bci[q];
-      if (!fs_wait(flags, K, epoch, st, spin_limit, lane)) return;
-      const int pK = D.bptr[K], bK = D.bptr[K + 1] - pK;
-      const double* Lik = val + D.voff[q];
-      if (act)
-        for (int c = 0; c < bK; ++c) acc = fma(-__ldcg(&Lik[r * bK + c]), __ldcg(&X[(long long)(pK + c) * kc + j]), acc);
-    }
-    if (act) X[(long long)(p0 + r) * kc + j] = acc;
-    fs_publish(flags, I, epoch, lane);
+// lane-level bounded wait on flags[k] == epoch (acquire); false on expiry
+__device__ __forceinline__ bool fs_wait_lane(const unsigned* flags, int k, unsigned epoch, int* st,
+                                             long long spin_limit) {
+  volatile int* vst = st;
+  unsigned f;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
+  long long it = 0;
+  unsigned ns = 32;
+  while (f != epoch) {
+    if (++it > spin_limit) { atomicExch(&st[ST_TIMEOUT], 1); return false; }
+    if ((it & 1023) == 0 && vst[ST_TIMEOUT]) return false;
+    __nanosleep(ns);
+    ns = ns < 256 ? 2 * ns : 256;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + k) : "memory");
   }
+  return true;
 }
 
-// backward: x_I = D_I^{-1} (y_I - sum_J U_IJ x_J), rows in reverse list order
-__global__ void __launch_bounds__(FS_THREADS) k_fs_bwd(FsDev D, const double* val, const double* dinv, double* X,
-                                                       int kc, unsigned* flags, unsigned epoch, int* st,
-                                                       long long spin_limit) {
-  __shared__ double Tsh[FS_WARPS][32];
+// The two block triangular solves, X row-major n x kc (kc <= KC).  A row's
+// dependency blocks are shared out over the lanes (lane t takes blocks t,
+// t + 32, ...; each lane waits for its own blocks' flags), every lane keeps
+// partial sums for the whole row block, and a butterfly reduction combines
+// them.  Forward (unit block lower factor): y_I = x_I - sum_K L_IK y_K.
+// Backward (U = D L^T, rows in reverse list order):
+// x_I = D_I^{-1} (y_I - sum_J U_IJ x_J).
+template <int KC, bool BWD>
+__global__ void __launch_bounds__(FS_THREADS) k_fs_trsv(FsDev D, const double* val, const double* dinv, double* X,
+                                                        int kc, unsigned* flags, unsigned epoch, int* st,
+                                                        long long spin_limit) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x + gridDim.x * wib, nwarp = gridDim.x * FS_WARPS;
-  double* T = Tsh[wib];
   for (int t = gw; t < D.nblk; t += nwarp) {
-    const int I = D.rows[D.nblk - 1 - t];
+    const int I = BWD ? D.rows[D.nblk - 1 - t] : D.rows[t];
     const int p0 = D.bptr[I], bI = D.bptr[I + 1] - p0;
-    const int r = lane / kc, j = lane - r * kc;
-    const bool act = r < bI;
-    double acc = act ? __ldcg(&X[(long long)(p0 + r) * kc + j]) : 0.0;
-    for (int q = D.bdiag[I] + 1; q < D.brp[I + 1]; ++q) {
-      const int J = D.bci[q];
-      if (!fs_wait(flags, J, epoch, st, spin_limit, lane)) return;
-      const int pJ = D.bptr[J], bJ = D.bptr[J + 1] - pJ;
-      const double* Uij = val + D.voff[q];
-      if (act)
-        for (int c = 0; c < bJ; ++c) acc = fma(-__ldcg(&Uij[r * bJ + c]), __ldcg(&X[(long long)(pJ + c) * kc + j]), acc);
+    const int q0 = BWD ? D.bdiag[I] + 1 : D.brp[I], q1 = BWD ? D.brp[I + 1] : D.bdiag[I];
+    double acc[FS_BMAX][KC];
+#pragma unroll
+    for (int r = 0; r < FS_BMAX; ++r)
+#pragma unroll
+      for (int j = 0; j < KC; ++j) acc[r][j] = 0.0;
+    bool ok = true;
+    for (int q = q0 + lane; q < q1; q += 32) {
+      const int K = D.bci[q];
+      if (!fs_wait_lane(flags, K, epoch, st, spin_limit)) { ok = false; break; }
+      const int pK = D.bptr[K], bK = D.bptr[K + 1] - pK;
+      const double* B = val + D.voff[q];
+      for (int c = 0; c < bK; ++c) {
+        double xv[KC];
+#pragma unroll
+        for (int j = 0; j < KC; ++j) xv[j] = j < kc ? __ldcg(&X[(long long)(pK + c) * kc + j]) : 0.0;
+#pragma unroll
+        for (int r = 0; r < FS_BMAX; ++r)
+          if (r < bI) {
+            const double l = __ldcg(&B[r * bK + c]);
+#pragma unroll
+            for (int j = 0; j < KC; ++j) acc[r][j] = fma(l, xv[j], acc[r][j]);
+          }
+      }
     }
-    T[lane] = acc;
-    __syncwarp();
-    if (act) {
-      const double* Dv = dinv + D.doff[I];
+    if (__any_sync(0xffffffffu, !ok)) return;
+    // sums over the lanes; afterwards every lane holds every row's sum
+#pragma unroll
+    for (int r = 0; r < FS_BMAX; ++r)
+      if (r < bI)
+#pragma unroll
+        for (int j = 0; j < KC; ++j)
+          for (int o = 16; o > 0; o >>= 1) acc[r][j] += __shfl_xor_sync(0xffffffffu, acc[r][j], o);
+    const int r = lane / kc, j = lane - r * kc;
+    const bool mine = r < bI;
+    if (!BWD) {
+      if (mine) {
+        double sum = 0.0;
+#pragma unroll
+        for (int rr = 0; rr < FS_BMAX; ++rr)
+#pragma unroll
+          for (int jj = 0; jj < KC; ++jj)
+            if (rr == r && jj == j) sum = acc[rr][jj];
+        const long long o = (long long)(p0 + r) * kc + j;
+        X[o] = __ldcg(&X[o]) - sum;
+      }
+    } else {
       double x = 0.0;
-      for (int c = 0; c < bI; ++c) x = fma(__ldcg(&Dv[r * bI + c]), T[c * kc + j], x);
-      X[(long long)(p0 + r) * kc + j] = x;
+      if (mine) {
+        const double* Dv = dinv + D.doff[I];
+#pragma unroll
+        for (int c = 0; c < FS_BMAX; ++c)
+          if (c < bI) {
+            double sc = 0.0;
+#pragma unroll
+            for (int jj = 0; jj < KC; ++jj)
+              if (jj == j) sc = acc[c][jj];
+            const double z = __ldcg(&X[(long long)(p0 + c) * kc + j]) - sc;
+            x = fma(__ldcg(&Dv[r * bI + c]), z, x);
+          }
+      }
+      __syncwarp();   // every lane has read y_I before it is overwritten
+      if (mine) X[(long long)(p0 + r) * kc + j] = x;
     }
     fs_publish(flags, I, epoch, lane);
   }
@@ -479,6 +546,12 @@ int coop(const void* fn, int grid, void** args, cudaStream_t s) {
                                                                                                    : OPF_ERR_CUDA;
 }
 
+// a cooperative grid of c CTAs per SM, within the occupancy and the rows
+int fs_grid(const FsState* S, int per, int c) {
+  const int need = (S->F.nblk + FS_WARPS - 1) / FS_WARPS;
+  return std::max(1, std::min(device_sms() * std::min(per, c), need));
+}
+
 // the plan, its device copy and the buffers, on first use
 int fs_ensure(opf_handle* h) {
   if (h->fs) return OPF_OK;
@@ -526,13 +599,16 @@ int fs_ensure(opf_handle* h) {
   FS_TRY(fs_alloc(h, &S->flags, (size_t)F.nblk));
   FS_TRY(fs_alloc(h, &S->cnt, 4));
   FS_TRY(fs_alloc(h, &S->ldet, 1));
-  int per = 0, per2 = 0, per3 = 0;
+  int per = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0;
   FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fs_factor, FS_THREADS, 0));
-  FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_fs_fwd, FS_THREADS, 0));
-  FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, k_fs_bwd, FS_THREADS, 0));
-  per = std::max(1, std::min(per, std::min(per2, per3)));
-  const int need = (F.nblk + FS_WARPS - 1) / FS_WARPS;
-  S->grid = std::max(1, std::min(device_sms() * std::min(per, 8), need));
+  FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_fs_trsv<FS_KC, false>, FS_THREADS, 0));
+  FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_fs_trsv<FS_KC, true>, FS_THREADS, 0));
+  FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_fs_trsv<1, false>, FS_THREADS, 0));
+  FS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p5, k_fs_trsv<1, true>, FS_THREADS, 0));
+  S->per_f = std::max(1, per);
+  S->per_s = std::max(1, std::min(std::min(p2, p3), std::min(p4, p5)));
+  S->grid_f = fs_grid(S, S->per_f, 2);
+  S->grid_s = fs_grid(S, S->per_s, 2);
   return OPF_OK;
 }
 
@@ -581,13 +657,13 @@ int fs_set_sigma(opf_handle* h, const double* sig_u, const double* sig_x, const 
 
 // assemble M with (delta_w, delta_c), factorise, count the inertia; the device
 // status reports SINGULAR, TIMEOUT or NOT_PD (wrong inertia)
-int fs_factor_async(opf_handle* h, double delta_w, double delta_c) {
+namespace {
+
+int fs_assemble(opf_handle* h, double delta_w, double delta_c) {
   FsState* S = h->fs;
-  if (!S || !S->sigma_set || !h->have_W) return OPF_ERR_INVALID_ARG;
   const Plan& P = h->P;
   const FsPlan& F = S->F;
   cudaStream_t s = h->s;
-  ph_begin(h, OPF_PHASE_ASSEMBLE);
   k_fs_zero<<<nb256(F.nval), 256, 0, s>>>(F.nval, S->val);
   FS_TRY(launched());
   const long long nW = (long long)F.w_slot.size(), nG = (long long)F.g_slot.size(), nA = (long long)F.a_slot.size();
@@ -596,14 +672,66 @@ int fs_factor_async(opf_handle* h, double delta_w, double delta_c) {
   if (nA) { k_fs_scatter<<<nb256(nA), 256, 0, s>>>(nA, S->a_slot, S->a_src, h->Aval, S->val); FS_TRY(launched()); }
   k_fs_diag<<<nb256(F.n), 256, 0, s>>>(P.nw, P.nu, P.nx, P.m, S->diag_slot, S->sig_w, h->sig_s, delta_w, delta_c,
                                        S->val);
-  FS_TRY(launched());
-  ph_end(h);
-  ph_begin(h, OPF_PHASE_CHOL);
+  return launched();
+}
+
+int fs_launch_factor(opf_handle* h, int grid) {
+  FsState* S = h->fs;
   unsigned ep = ++S->epoch;
   long long spin = h->spin_limit;
   FsDev d = S->d;
   void* args[] = {&d, &S->val, &S->dinv, &S->flags, &ep, &h->st, &spin};
-  FS_TRY(coop((const void*)k_fs_factor, S->grid, args, s));
+  return coop((const void*)k_fs_factor, grid, args, h->s);
+}
+
+// the factorisation at each candidate grid on the same matrix (re-assembled
+// before each), timed with events; the fastest is kept
+int fs_tune_factor(opf_handle* h, double delta_w, double delta_c) {
+  FsState* S = h->fs;
+  cudaEvent_t a = nullptr, b = nullptr;
+  FS_CK(cudaEventCreate(&a));
+  FS_CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  int pick = S->grid_f;
+  int rc = OPF_OK;
+  for (int i = 0; i < 4 && rc == OPF_OK; ++i) {
+    S->tune_f[i] = 0.f;
+    if (FS_GRIDS[i] > S->per_f) continue;
+    const int g = fs_grid(S, S->per_f, FS_GRIDS[i]);
+    rc = fs_assemble(h, delta_w, delta_c);
+    if (rc == OPF_OK && cudaEventRecord(a, h->s) != cudaSuccess) rc = OPF_ERR_CUDA;
+    if (rc == OPF_OK) rc = fs_launch_factor(h, g);
+    if (rc == OPF_OK && cudaEventRecord(b, h->s) != cudaSuccess) rc = OPF_ERR_CUDA;
+    if (rc == OPF_OK && cudaEventSynchronize(b) != cudaSuccess) rc = OPF_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == OPF_OK) cudaEventElapsedTime(&ms, a, b);
+    S->tune_f[i] = ms;
+    if (rc == OPF_OK && ms < best) { best = ms; pick = g; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  FS_TRY(rc);
+  S->grid_f = pick;
+  S->tuned_f = true;
+  return OPF_OK;
+}
+
+}  // namespace
+
+// assemble M with (delta_w, delta_c), factorise, count the inertia; the device
+// status reports SINGULAR, TIMEOUT or NOT_PD (wrong inertia)
+int fs_factor_async(opf_handle* h, double delta_w, double delta_c) {
+  FsState* S = h->fs;
+  if (!S || !S->sigma_set || !h->have_W) return OPF_ERR_INVALID_ARG;
+  const Plan& P = h->P;
+  const FsPlan& F = S->F;
+  cudaStream_t s = h->s;
+  if (!S->tuned_f && !h->profiling) FS_TRY(fs_tune_factor(h, delta_w, delta_c));
+  ph_begin(h, OPF_PHASE_ASSEMBLE);
+  FS_TRY(fs_assemble(h, delta_w, delta_c));
+  ph_end(h);
+  ph_begin(h, OPF_PHASE_CHOL);
+  FS_TRY(fs_launch_factor(h, S->grid_f));
   FS_CK(cudaMemsetAsync(S->cnt, 0, sizeof(int) * 4, s));
   FS_CK(cudaMemsetAsync(S->ldet, 0, sizeof(double), s));
   k_fs_inertia<<<nb256(F.nblk), 256, 0, s>>>(S->d, S->val, S->cnt, S->ldet);
@@ -635,6 +763,63 @@ int fs_read_inertia(opf_handle* h, int* inertia, double* logdet) {
   return OPF_OK;
 }
 
+namespace {
+
+int fs_launch_solves(opf_handle* h, int kc, int grid) {
+  FsState* S = h->fs;
+  long long spin = h->spin_limit;
+  FsDev d = S->d;
+  unsigned ep = ++S->epoch;
+  void* fa[] = {&d, &S->val, &S->dinv, &S->X, &kc, &S->flags, &ep, &h->st, &spin};
+  FS_TRY(coop(kc == 1 ? (const void*)k_fs_trsv<1, false> : (const void*)k_fs_trsv<FS_KC, false>, grid, fa, h->s));
+  unsigned ep2 = ++S->epoch;
+  void* ba[] = {&d, &S->val, &S->dinv, &S->X, &kc, &S->flags, &ep2, &h->st, &spin};
+  return coop(kc == 1 ? (const void*)k_fs_trsv<1, true> : (const void*)k_fs_trsv<FS_KC, true>, grid, ba, h->s);
+}
+
+int fs_gather(opf_handle* h, int k, int j0, int kc, const KB& b) {
+  FsState* S = h->fs;
+  const Plan& P = h->P;
+  const int rows = P.nw + P.nx + P.m;
+  k_fs_gather<<<nb256((long long)rows * kc), 256, 0, h->s>>>(P.nw, P.nx, P.m, k, j0, kc, S->kbpos, b.w, b.l, b.y,
+                                                              b.s, h->sig_s, S->X);
+  return launched();
+}
+
+// the two solves at each candidate grid on the first right-hand side, timed
+int fs_tune_solves(opf_handle* h, int k, const KB& b) {
+  FsState* S = h->fs;
+  const int kc = std::min(FS_KC, k);
+  cudaEvent_t a = nullptr, e = nullptr;
+  FS_CK(cudaEventCreate(&a));
+  FS_CK(cudaEventCreate(&e));
+  float best = 1e30f;
+  int pick = S->grid_s;
+  int rc = OPF_OK;
+  for (int i = 0; i < 4 && rc == OPF_OK; ++i) {
+    S->tune_s[i] = 0.f;
+    if (FS_GRIDS[i] > S->per_s) continue;
+    const int g = fs_grid(S, S->per_s, FS_GRIDS[i]);
+    rc = fs_gather(h, k, 0, kc, b);
+    if (rc == OPF_OK && cudaEventRecord(a, h->s) != cudaSuccess) rc = OPF_ERR_CUDA;
+    if (rc == OPF_OK) rc = fs_launch_solves(h, kc, g);
+    if (rc == OPF_OK && cudaEventRecord(e, h->s) != cudaSuccess) rc = OPF_ERR_CUDA;
+    if (rc == OPF_OK && cudaEventSynchronize(e) != cudaSuccess) rc = OPF_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == OPF_OK) cudaEventElapsedTime(&ms, a, e);
+    S->tune_s[i] = ms;
+    if (rc == OPF_OK && ms < best) { best = ms; pick = g; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(e);
+  FS_TRY(rc);
+  S->grid_s = pick;
+  S->tuned_s = true;
+  return OPF_OK;
+}
+
+}  // namespace
+
 // p = K_aug^{-1} b for k right-hand sides in the KB layout, through M
 int fs_core(opf_handle* h, int k, const KB& b, const KB& p) {
   FsState* S = h->fs;
@@ -643,20 +828,12 @@ int fs_core(opf_handle* h, int k, const KB& b, const KB& p) {
   cudaStream_t s = h->s;
   const int rows = P.nw + P.nx + P.m;
   FS_TRY(fs_xbuf(h, FS_KC));
+  if (!S->tuned_s && !h->profiling) FS_TRY(fs_tune_solves(h, k, b));
   ph_begin(h, OPF_PHASE_RECOVER);
   for (int j0 = 0; j0 < k; j0 += FS_KC) {
-    int kc = std::min(FS_KC, k - j0);
-    k_fs_gather<<<nb256((long long)rows * kc), 256, 0, s>>>(P.nw, P.nx, P.m, k, j0, kc, S->kbpos, b.w, b.l, b.y,
-                                                             b.s, h->sig_s, S->X);
-    FS_TRY(launched());
-    long long spin = h->spin_limit;
-    FsDev d = S->d;
-    unsigned ep = ++S->epoch;
-    void* fa[] = {&d, &S->val, &S->X, &kc, &S->flags, &ep, &h->st, &spin};
-    FS_TRY(coop((const void*)k_fs_fwd, S->grid, fa, s));
-    unsigned ep2 = ++S->epoch;
-    void* ba[] = {&d, &S->val, &S->dinv, &S->X, &kc, &S->flags, &ep2, &h->st, &spin};
-    FS_TRY(coop((const void*)k_fs_bwd, S->grid, ba, s));
+    const int kc = std::min(FS_KC, k - j0);
+    FS_TRY(fs_gather(h, k, j0, kc, b));
+    FS_TRY(fs_launch_solves(h, kc, S->grid_s));
     k_fs_scatter_back<<<nb256((long long)rows * kc), 256, 0, s>>>(P.nw, P.nx, P.m, k, j0, kc, S->kbpos, S->X, b.s,
                                                                    h->sig_s, p.w, p.l, p.y, p.s);
     FS_TRY(launched());
@@ -694,6 +871,13 @@ int fs_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int ref
   FS_CK(launch_permute_rows(s, m, k, nullptr, p.s, k, 0, step + nw, int(N), 1, 1.0, 0));
   FS_CK(launch_permute_rows(s, nx, k, h->perm, p.l, k, 0, step + nw + m, int(N), 1, 1.0, 1));
   FS_CK(launch_permute_rows(s, m, k, nullptr, p.y, k, 0, step + nw + m + nx, int(N), 1, 1.0, 0));
+  return OPF_OK;
+}
+
+int fs_tuning(const opf_handle* h, int* grids, float* ms) {
+  if (!h->fs) return OPF_ERR_INVALID_ARG;
+  if (grids) { grids[0] = h->fs->grid_f; grids[1] = h->fs->grid_s; }
+  if (ms) for (int i = 0; i < 4; ++i) { ms[i] = h->fs->tune_f[i]; ms[4 + i] = h->fs->tune_s[i]; }
   return OPF_OK;
 }
 
@@ -741,4 +925,9 @@ extern "C" int opf_fullspace_stats(opf_handle* h, int* nblocks, int* levels, lon
   if (logabsdet) *logabsdet = h->fs->factored ? h->fs->logdet : 0.0;
   if (inertia) for (int i = 0; i < 3; ++i) inertia[i] = h->fs->factored ? h->fs->inertia[i] : -1;
   return OPF_OK;
+}
+
+extern "C" int opf_fullspace_tuning(const opf_handle* h, int* grids, float* ms) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  return fs_tuning(h, grids, ms);
 }
