@@ -21,6 +21,7 @@ from __future__ import annotations
 import dataclasses
 
 import numpy as np
+import scipy.sparse as sp
 
 from . import kkt, model
 
@@ -41,6 +42,10 @@ ETA_PHI = 1e-4
 GAMMA_ALPHA = 0.05
 KAPPA_SOC = 0.99
 SOC_MAX = 4
+# feasibility restoration (Wachter and Biegler 2006, Sec. 3.3)
+RHO_RESTO = 1000.0    # weight of the relaxation variables' l1 norm
+KAPPA_RESTO = 0.9     # required reduction of the constraint violation
+RESTO_MAX_ITER = 100
 
 
 @dataclasses.dataclass
@@ -60,6 +65,7 @@ class Result:
     err: float = np.inf
     history: list = dataclasses.field(default_factory=list)
     soc_steps: int = 0          # accepted second-order corrections (filter line search)
+    restorations: int = 0       # feasibility restoration phases (filter line search)
 
 
 def _push(v, lo, hi, k1=1e-2, k2=1e-2):
@@ -194,14 +200,16 @@ def _regularized(step_fn, delta_last):
 
 
 def _filter_search(lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, zwu, zsl, zsu, mu, tau,
-                   pw, ps, plam, py, delta, theta_min, stats):
+                   pw, ps, plam, py, delta, theta_min, stats, restoration=False):
     """Filter line search with second-order corrections along the condensed
     step (Wachter and Biegler 2006, Algorithm A, steps A-5 to A-8).  theta is the
     l1 norm of c = [g; h + s], phi the barrier objective.  When the step length
     falls below alpha_min the step is shortened by a larger primal
-    regularization and the search starts again (in place of the restoration
-    phase).  Returns the primal-dual step, its primal and bound-multiplier
-    lengths, the bound-multiplier steps and the delta_w in use."""
+    regularization and the search starts again, unless restoration is on:
+    then the search gives up at once and returns None, and the caller runs the
+    feasibility restoration phase.  Returns the primal-dual step, its primal
+    and bound-multiplier lengths, the bound-multiplier steps and the delta_w in
+    use."""
     nw, m = lay.nw, lay.m
 
     def cons(wt, st):
@@ -255,6 +263,11 @@ def _filter_search(lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, z
             az = min(_max_step_z(zwl, dzwl, bw.fl, tau), _max_step_z(zwu, dzwu, bw.fu, tau),
                      _max_step_z(zsl, dzsl, bs.fl, tau), _max_step_z(zsu, dzsu, bs.fu, tau))
             return pw_acc, ps_acc, plam, py, a, az, dzwl, dzwu, dzsl, dzsu, delta
+        if restoration:
+            # out of step length: the current point goes into the filter and the
+            # restoration phase takes over (Algorithm A, step A-9)
+            filt.add(theta0, phi0)
+            return None
         # out of step length: shorten the step by a larger primal regularization
         delta = max(1e-8, 10.0 * delta)
         pw, ps, plam, py, Kc, ok = kkt.condensed_step(G, A, W, sig_w, sig_s, r, nu, delta_w=delta)
@@ -264,12 +277,128 @@ def _filter_search(lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, z
     raise RuntimeError("filter line search failed")
 
 
+def _restoration(lay, bw, bs, filt, w, s, mu, tol, stats, verbose=False):
+    """Feasibility restoration phase (Wachter and Biegler 2006, Sec. 3.3) with
+    the relaxation restricted to the inequality rows, as Sec. 4.3 describes for
+    LinRed: the equality rows g(w) = 0 stay exact (so G_x and the reduction
+    are unchanged) and each row of h + s = 0 gets two nonnegative variables,
+
+        min  rho sum(p + n) + zeta/2 ||D_R (w - w_R)||^2
+        s.t. g(w) = 0,  h(w) + s - p + n = 0,  bounds on w and s,  p, n >= 0,
+
+    zeta = sqrt(mu), D_R = diag(min(1, 1/|w_R|)).  Its barrier Newton step is the
+    condensed step of the same K_aug with W replaced by the Hessian of the
+    constraint terms plus zeta D_R^2, and -delta I in the (p_y, p_y) block with
+    delta_i = 1/Sigma_p,i + 1/Sigma_n,i: eliminating dp and dn folds the
+    relaxation into a dual regularisation of the inequality rows.  Steps are
+    accepted by backtracking on the l1 merit of the restoration barrier
+    problem.  The phase ends at the first point whose violation theta of
+    [g; h + s] is at most kappa theta(w_R, s_R) and that the original filter
+    accepts (the current point was added to it before the call).
+    Returns (w, s, lam, y, zwl, zwu, zsl, zsu) for the main loop or raises."""
+    nu, nx, m, nw = lay.nu, lay.nx, lay.m, lay.nw
+
+    def cons(wt, st):
+        return np.concatenate([model.cons_g(lay, wt), model.cons_h(lay, wt) + st])
+
+    def phi_main(wt, st):
+        return model.objective(lay, wt) + bw.barrier(wt, mu) + bs.barrier(st, mu)
+
+    theta_R = np.abs(cons(w, s)).sum()
+    wR = w.copy()
+    zeta = np.sqrt(mu)
+    dr2 = np.minimum(1.0, 1.0 / np.maximum(np.abs(wR), 1e-300)) ** 2
+    rho = RHO_RESTO
+    c = model.cons_h(lay, w) + s
+    mur = max(mu, np.abs(cons(w, s)).max())
+    # p and n minimising the relaxed barrier terms for the current c (closed form)
+    t = (mur - rho * c) / (2.0 * rho)
+    n = t + np.sqrt(t * t + mur * c / (2.0 * rho))
+    p = c + n
+    zp, zn = mur / p, mur / n
+    lam, y = np.zeros(nx), np.zeros(m)
+    zwl, zwu = np.where(bw.fl, mur / bw.dl(w), 0.0), np.where(bw.fu, mur / bw.du(w), 0.0)
+    zsl, zsu = np.where(bs.fl, mur / bs.dl(s), 0.0), np.where(bs.fu, mur / bs.du(s), 0.0)
+    nu_pen = 1.0
+    delta = 0.0
+    for it in range(RESTO_MAX_ITER):
+        gf, G, A = model.jacobians(lay, w)
+        g = model.cons_g(lay, w)
+        hv = model.cons_h(lay, w)
+        Wc = (model.lagrangian_hessian(lay, w, lam, y) - model.lagrangian_hessian(lay, w, 0.0 * lam, 0.0 * y)
+              + sp.diags(zeta * dr2))
+        sig_w = bw.sigma(w, zwl, zwu)
+        sig_s = bs.sigma(s, zsl, zsu)
+        sp_, sn_ = zp / p, zn / n
+        dcv = 1.0 / sp_ + 1.0 / sn_
+        r_w = zeta * dr2 * (w - wR) + G.T @ lam + A.T @ y + bw.barrier_grad(w, mur)
+        r_s = y + bs.barrier_grad(s, mur)
+        r_y = hv + s - p + n
+        r_p = rho - y - mur / p
+        r_n = rho + y - mur / n
+        r = np.concatenate([r_w, r_s, g, r_y + r_p / sp_ - r_n / sn_])
+        (pw, ps, plam, py, Kc, ok), delta = _regularized(
+            lambda d: kkt.condensed_step(G, A, Wc, sig_w, sig_s, r, nu, delta_w=d, delta_c=dcv), delta)
+        pp = (py - r_p) / sp_
+        pn = (-py - r_n) / sn_
+        tau = max(TAU_MIN, 1.0 - mur)
+        amax = min(bw.max_step(w, pw, tau), bs.max_step(s, ps, tau))
+        for v, dv in ((p, pp), (n, pn)):
+            neg = dv < 0
+            if neg.any():
+                amax = min(amax, np.min(-tau * v[neg] / dv[neg]))
+        dzwl, dzwu = bw.dz(w, zwl, zwu, pw, mur)
+        dzsl, dzsu = bs.dz(s, zsl, zsu, ps, mur)
+        dzp = mur / p - zp - sp_ * pp
+        dzn = mur / n - zn - sn_ * pn
+        ones = np.ones(m, bool)
+        az = min(_max_step_z(zwl, dzwl, bw.fl, tau), _max_step_z(zwu, dzwu, bw.fu, tau),
+                 _max_step_z(zsl, dzsl, bs.fl, tau), _max_step_z(zsu, dzsu, bs.fu, tau),
+                 _max_step_z(zp, dzp, ones, tau), _max_step_z(zn, dzn, ones, tau))
+        nu_pen = max(nu_pen, 1.1 * max(np.abs(lam + plam).max(initial=0), np.abs(y + py).max(initial=0)))
+
+        def merit(wt, st, pt, nt):
+            cr = np.concatenate([model.cons_g(lay, wt), model.cons_h(lay, wt) + st - pt + nt])
+            return (rho * np.sum(pt + nt) + 0.5 * zeta * np.sum(dr2 * (wt - wR) ** 2) + bw.barrier(wt, mur)
+                    + bs.barrier(st, mur) - mur * np.sum(np.log(pt) + np.log(nt)) + nu_pen * np.abs(cr).sum())
+        psi0 = merit(w, s, p, n)
+        dpsi = (rho * np.sum(pp + pn) + zeta * np.sum(dr2 * (w - wR) * pw) + bw.barrier_grad(w, mur) @ pw
+                + bs.barrier_grad(s, mur) @ ps - mur * np.sum(pp / p + pn / n)
+                - nu_pen * np.abs(np.concatenate([g, r_y])).sum())
+        a = amax
+        while a > 1e-8 * amax and not (merit(w + a * pw, s + a * ps, p + a * pp, n + a * pn)
+                                       <= psi0 + ETA * a * min(dpsi, 0.0)):
+            a *= 0.5
+        w, s, p, n = w + a * pw, s + a * ps, p + a * pp, n + a * pn
+        lam, y = lam + a * plam, y + a * py
+        zwl, zwu = bw.safeguard(w, zwl + az * dzwl, zwu + az * dzwu, mur)
+        zsl, zsu = bs.safeguard(s, zsl + az * dzsl, zsu + az * dzsu, mur)
+        zp = np.clip(zp + az * dzp, mur / (KAPPA_SIGMA * p), KAPPA_SIGMA * mur / p)
+        zn = np.clip(zn + az * dzn, mur / (KAPPA_SIGMA * n), KAPPA_SIGMA * mur / n)
+        theta = np.abs(cons(w, s)).sum()
+        if verbose:
+            print(f"  resto it {it:3d} theta {theta:.3e} (theta_R {theta_R:.3e}) mu_R {mur:.1e} a {a:.2e}")
+        stats["resto_iters"] = stats.get("resto_iters", 0) + 1
+        if theta <= KAPPA_RESTO * theta_R and filt.acceptable(theta, phi_main(w, s)):
+            return w, s, lam, y, zwl, zwu, zsl, zsu
+        # the restoration problem's own barrier parameter
+        dual = np.concatenate([r_w, r_s, r_p, r_n])
+        if np.abs(dual).max() <= KAPPA_EPS * mur and np.abs(np.concatenate([g, r_y])).max() <= KAPPA_EPS * mur:
+            mur = max(0.1 * mu, min(KAPPA_MU * mur, mur ** THETA_MU))
+    raise RuntimeError("feasibility restoration failed")
+
+
 # ------------------------------------------------------------------ LinRed
-def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, line_search="merit"):
+def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, line_search="merit",
+           restoration=False, start_with_resto=False):
     """Algorithm 1.  record_at: iteration index whose iterate (and the step
     inputs) is stored in Result.history as a dict.  line_search: "merit"
     (l1 exact-penalty backtracking) or "filter" (filter line search with
-    second-order corrections)."""
+    second-order corrections); with the filter, restoration=True runs the
+    feasibility restoration phase when the step length runs out (otherwise a
+    larger primal regularisation shortens the step), and start_with_resto=True
+    (Ipopt's option of that name) runs it once from the starting point before
+    the first step."""
     lay = model.Layout(net)
     nu, nx, m, nw = lay.nu, lay.nx, lay.m, lay.nw
     bw = _Bounds(lay.wl, lay.wu)
@@ -305,7 +434,8 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, 
                   f"inf_pr {np.abs(primal).max():.2e} delta {delta:.1e}")
         if err0 <= tol:
             return Result("converged", it, float(model.objective(lay, w)), w, s, lam, y,
-                          (zwl, zsl), (zwu, zsu), mu, err=err0, history=hist, soc_steps=stats["soc"])
+                          (zwl, zsl), (zwu, zsu), mu, err=err0, history=hist, soc_steps=stats["soc"],
+                          restorations=stats.get("restorations", 0))
         if it == max_iter:
             break
         while True:
@@ -329,9 +459,20 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, 
         if line_search == "filter":
             if filt is None or filt_mu != mu:      # a new barrier problem: a new filter
                 filt, filt_mu = Filter(theta_max), mu
-            pw, ps, plam, py, a, az, dzwl, dzwu, dzsl, dzsu, delta = _filter_search(
+            if start_with_resto and it == 0:
+                theta0 = np.abs(np.concatenate([g, h + s])).sum()
+                filt.add(theta0, model.objective(lay, w) + bw.barrier(w, mu) + bs.barrier(s, mu))
+                w, s, lam, y, zwl, zwu, zsl, zsu = _restoration(lay, bw, bs, filt, w, s, mu, tol, stats, verbose)
+                stats["restorations"] = stats.get("restorations", 0) + 1
+                continue
+            res = _filter_search(
                 lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, zwu, zsl, zsu, mu, tau,
-                pw, ps, plam, py, delta, theta_min, stats)
+                pw, ps, plam, py, delta, theta_min, stats, restoration)
+            if res is None:
+                w, s, lam, y, zwl, zwu, zsl, zsu = _restoration(lay, bw, bs, filt, w, s, mu, tol, stats, verbose)
+                stats["restorations"] = stats.get("restorations", 0) + 1
+                continue
+            pw, ps, plam, py, a, az, dzwl, dzwu, dzsl, dzsu, delta = res
         for attempt in range(40 if line_search == "merit" else 0):
             dzwl, dzwu = bw.dz(w, zwl, zwu, pw, mu)
             dzsl, dzsu = bs.dz(s, zsl, zsu, ps, mu)

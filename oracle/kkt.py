@@ -47,14 +47,16 @@ def kaug(G, A, W, sig_w, sig_s, delta_c=0.0):
     """K_aug of Eq. kktmatrix:normal (sparse), unknowns [p_w, p_s, p_lambda, p_y]
     with p_w = [p_u; p_x] and the +I slack coupling; delta_c > 0 puts
     -delta_c I in the (p_y, p_y) block (dual regularisation of the
-    inequalities, Sec. 4.3)."""
+    inequalities, Sec. 4.3); delta_c may also be one value per inequality row
+    (the restoration phase's relaxation, oracle/ipm.py)."""
     G = sp.csr_matrix(G)
     A = sp.csr_matrix(A)
     W = sp.csr_matrix(W)
     nx, nw = G.shape
     m = A.shape[0]
     I = sp.identity(m, format="csr")
-    Dyy = -delta_c * sp.identity(m, format="csr") if delta_c else None
+    dc = np.broadcast_to(np.asarray(delta_c, dtype=np.float64), (m,))
+    Dyy = sp.diags(-dc, format="csr") if np.any(dc) else None
     return sp.bmat([
         [W + sp.diags(sig_w), None, G.T, A.T],
         [None, sp.diags(sig_s), None, I],

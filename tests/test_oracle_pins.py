@@ -401,3 +401,81 @@ def test_filter_line_search_reaches_the_pinned_optima(case):
     assert np.abs(model.cons_g(lay, res.w)).max() <= 1e-8
     if case == "tiny3_loaded":
         assert res.soc_steps >= 1
+
+
+# ------------------------------------------------- feasibility restoration
+def _scaled_loads(net, f):
+    import dataclasses
+    return dataclasses.replace(net, Pd=net.Pd * f, Qd=net.Qd * f)
+
+
+def test_per_row_dual_regularisation_matches_kaug():
+    """The restoration phase relaxes each inequality row with its own dual
+    regularisation delta_i: the condensed step with Sigma_t,i = (Sigma_s,i^{-1}
+    + delta_i)^{-1} against the sparse solve of K_aug with -diag(delta) in its
+    (p_y, p_y) block."""
+    net = gridgen.ring30()
+    lay = model.Layout(net)
+    rng = np.random.default_rng(77)
+    w = lay.flat_start() + 0.02 * rng.standard_normal(lay.nw)
+    _, G, A = model.jacobians(lay, w)
+    W = model.lagrangian_hessian(lay, w, rng.standard_normal(lay.nx), rng.standard_normal(lay.m))
+    sw, ss = rng.uniform(0.5, 5.0, lay.nw), rng.uniform(0.5, 5.0, lay.m)
+    dc = rng.uniform(1e-3, 2.0, lay.m)
+    r = rng.standard_normal(lay.nw + 2 * lay.m + lay.nx)
+    Kc0 = kkt.kred_definition(G, A, W, sw, kkt.regularized_sigma(ss, dc), lay.nu)
+    dw = max(0.0, -np.linalg.eigvalsh(0.5 * (Kc0 + Kc0.T))[0]) + 1.0
+    pw, ps, pl, py, _, ok = kkt.condensed_step(G, A, W, sw, ss, r, lay.nu, delta_w=dw, delta_c=dc)
+    assert ok
+    Wd = W + sp.diags(np.r_[np.full(lay.nu, dw), np.zeros(lay.nx)])
+    ref = np.concatenate(kkt.full_space_step(G, A, Wd, sw, ss, r, delta_c=dc))
+    got = np.concatenate([pw, ps, pl, py])
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("make", [gridgen.tiny3, gridgen.ring30])
+def test_restoration_from_the_start_reaches_the_same_optimum(make):
+    """Ipopt's start-with-restoration: the restoration phase runs from the flat
+    start, hands an acceptable point back, and the loop converges to the
+    optimum of the plain filter solve."""
+    net = make()
+    a = ipm.linred(net, line_search="filter")
+    b = ipm.linred(net, line_search="filter", restoration=True, start_with_resto=True)
+    assert a.status == b.status == "converged"
+    assert b.restorations == 1
+    assert abs(a.obj - b.obj) <= 1e-8 * abs(a.obj)
+
+
+def test_restoration_endpoint_is_acceptable():
+    """The restoration phase returns a point whose violation of [g; h + s] is at
+    most 0.9 of the starting one and that the original filter (holding the
+    starting point) accepts; the bound multipliers are positive."""
+    net = gridgen.ring30()
+    lay = model.Layout(net)
+    bw = ipm._Bounds(lay.wl, lay.wu)
+    bs = ipm._Bounds(-lay.hu, -lay.hl)
+    w = ipm._push(lay.flat_start(), lay.wl, lay.wu)
+    s = ipm._push(-model.cons_h(lay, w), bs.lo, bs.hi)
+    mu = 0.1
+
+    def theta_phi(wt, st):
+        c = np.concatenate([model.cons_g(lay, wt), model.cons_h(lay, wt) + st])
+        return np.abs(c).sum(), model.objective(lay, wt) + bw.barrier(wt, mu) + bs.barrier(st, mu)
+    t0, p0 = theta_phi(w, s)
+    filt = ipm.Filter(1e4 * max(1.0, t0))
+    filt.add(t0, p0)
+    w2, s2, lam, y, zwl, zwu, zsl, zsu = ipm._restoration(lay, bw, bs, filt, w, s, mu, 1e-8, {})
+    t1, p1 = theta_phi(w2, s2)
+    assert t1 <= ipm.KAPPA_RESTO * t0 and filt.acceptable(t1, p1)
+    assert (zwl[bw.fl] > 0).all() and (zwu[bw.fu] > 0).all() and (zsl[bs.fl] > 0).all()
+    assert np.all(w2 >= lay.wl) and np.all(w2 <= lay.wu)
+
+
+def test_restoration_fails_on_an_infeasible_case():
+    """Loads of 1.7 x the 3-bus case exceed its generation capacity (total Pmax
+    2.0 against 2.04 of load; losses are nonnegative), so no feasible point
+    exists: the restoration phase cannot return one and the solve fails."""
+    net = _scaled_loads(gridgen.tiny3(), 1.7)
+    assert net.Pmax.sum() < net.Pd.sum()
+    with pytest.raises(RuntimeError, match="restoration failed"):
+        ipm.linred(net, line_search="filter", restoration=True)
