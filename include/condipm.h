@@ -51,6 +51,8 @@ extern "C" {
 #define OPF_ERR_TIMEOUT       -6   /* a bounded device wait expired              */
 #define OPF_ERR_OOM           -7   /* device allocation failed                   */
 #define OPF_ERR_NO_CONVERGENCE -8  /* interior-point loop hit its iteration cap  */
+#define OPF_ERR_INFEASIBLE    -9   /* feasibility restoration found no acceptable
+                                      point (the problem looks locally infeasible) */
 
 /* ---- network (host arrays, copied by opf_create) ---------------------------- */
 typedef struct opf_network {
@@ -319,6 +321,15 @@ typedef struct opf_ipm_options {
                           defers to (no restoration phase: when the step length
                           runs out, a larger primal regularisation shortens the
                           step)                                                   */
+    int restoration;   /* filter line search only: 1 = when the step length runs out,
+                          the feasibility restoration phase of Wachter and Biegler
+                          (2006, Sec. 3.3) with the relaxation on the inequality
+                          rows only (Sec. 4.3: there it is a dual regularisation
+                          of the inequality rows, so the condensation on G_x is
+                          unchanged); 0 = a larger primal regularisation
+                          shortens the step instead                             */
+    int start_with_resto; /* with restoration: run the phase once from the starting
+                          point before the first step (Ipopt's option of that name) */
     int linear_solver; /* OPF_LINSOLVE_CONDENSED: the condensed step (LinRed, RedLin);
                           OPF_LINSOLVE_FULLSPACE (LinRed only): the hybrid
                           full-space IPM of Sec. 4.3 -- the same loop, model,
@@ -341,6 +352,8 @@ typedef struct opf_ipm_result {
     int graph_iters;   /* iterations whose condensation + first Cholesky attempt ran as
                           a replayed CUDA graph (needs a non-default stream)           */
     int soc_steps;     /* accepted second-order corrections (filter line search)      */
+    int restorations;  /* feasibility restoration phases entered                      */
+    int resto_iters;   /* iterations spent inside them                                 */
 } opf_ipm_result;
 
 /* Solve the OPF of the handle's network from the flat start (theta = 0, Vm = 1 at

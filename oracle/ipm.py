@@ -445,6 +445,13 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, 
                 break
             mu = max(tol / 10, min(KAPPA_MU * mu, mu ** THETA_MU))
         tau = max(TAU_MIN, 1.0 - mu)
+        if line_search == "filter" and restoration and start_with_resto and it == 0:
+            # the restoration phase from the starting point, before any step
+            filt, filt_mu = Filter(theta_max), mu
+            filt.add(np.abs(primal).sum(), model.objective(lay, w) + bw.barrier(w, mu) + bs.barrier(s, mu))
+            w, s, lam, y, zwl, zwu, zsl, zsu = _restoration(lay, bw, bs, filt, w, s, mu, tol, stats, verbose)
+            stats["restorations"] = stats.get("restorations", 0) + 1
+            continue
         W = model.lagrangian_hessian(lay, w, lam, y)
         sig_w = bw.sigma(w, zwl, zwu)
         sig_s = bs.sigma(s, zsl, zsu)
@@ -459,12 +466,7 @@ def linred(net, tol=1e-8, max_iter=300, mu0=0.1, record_at=None, verbose=False, 
         if line_search == "filter":
             if filt is None or filt_mu != mu:      # a new barrier problem: a new filter
                 filt, filt_mu = Filter(theta_max), mu
-            if start_with_resto and it == 0:
-                theta0 = np.abs(np.concatenate([g, h + s])).sum()
-                filt.add(theta0, model.objective(lay, w) + bw.barrier(w, mu) + bs.barrier(s, mu))
-                w, s, lam, y, zwl, zwu, zsl, zsu = _restoration(lay, bw, bs, filt, w, s, mu, tol, stats, verbose)
-                stats["restorations"] = stats.get("restorations", 0) + 1
-                continue
+
             res = _filter_search(
                 lay, bw, bs, filt, G, A, W, sig_w, sig_s, r, nu, w, s, zwl, zwu, zsl, zsu, mu, tau,
                 pw, ps, plam, py, delta, theta_min, stats, restoration)

@@ -20,6 +20,8 @@ OPF_ERR_NOT_PD = -3
 OPF_ERR_SINGULAR = -4
 OPF_ERR_PF_FAILED = -5
 OPF_ERR_TIMEOUT = -6
+OPF_ERR_NO_CONVERGENCE = -8
+OPF_ERR_INFEASIBLE = -9
 OPF_ROUTE_ADJOINT = 0
 OPF_ROUTE_EXPLICIT = 1
 OPF_ROUTE_AUTO = 2
@@ -46,7 +48,7 @@ class opf_options(C.Structure):
 class opf_ipm_options(C.Structure):
     _fields_ = [("variant", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("mu0", C.c_double),
                 ("pf_tol", C.c_double), ("verbose", C.c_int), ("line_search", C.c_int),
-                ("linear_solver", C.c_int)]
+                ("restoration", C.c_int), ("start_with_resto", C.c_int), ("linear_solver", C.c_int)]
 
 
 class opf_ipm_result(C.Structure):
@@ -54,7 +56,7 @@ class opf_ipm_result(C.Structure):
                 ("mu", C.c_double), ("n_factor", C.c_int), ("ms_total", C.c_double), ("ms_eval", C.c_double),
                 ("ms_condense", C.c_double), ("ms_factor", C.c_double), ("ms_solve", C.c_double),
                 ("ms_linesearch", C.c_double), ("ms_pf", C.c_double), ("graph_iters", C.c_int),
-                ("soc_steps", C.c_int)]
+                ("soc_steps", C.c_int), ("restorations", C.c_int), ("resto_iters", C.c_int)]
 
 
 OPF_LINRED, OPF_REDLIN = 0, 1
@@ -390,16 +392,19 @@ class Handle:
         return dict(grid_factor=g[0], grid_solve=g[1], factor_ms=list(ms[:4]), solve_ms=list(ms[4:]))
 
     def solve(self, variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
-              line_search="merit", linear_solver="condensed"):
+              line_search="merit", linear_solver="condensed", restoration=False, start_with_resto=False):
         """opf_solve: the interior-point loop; returns the result fields as a dict.
         line_search: "merit" or "filter" (LinRed); linear_solver: "condensed" or
-        "fullspace" (the hybrid full-space IPM, LinRed)."""
-        o = _ipm_options(variant, tol, max_iter, mu0, pf_tol, verbose, line_search, linear_solver)
+        "fullspace" (the hybrid full-space IPM, LinRed); restoration /
+        start_with_resto: the feasibility restoration phase of the filter line
+        search."""
+        o = _ipm_options(variant, tol, max_iter, mu0, pf_tol, verbose, line_search, linear_solver, restoration,
+                         start_with_resto)
         r = opf_ipm_result()
         rc = self._lib.opf_solve(self._h, C.byref(o), C.byref(r))
         out = {f: getattr(r, f) for f, _ in opf_ipm_result._fields_}
         self.last_result = out
-        if rc not in (OPF_OK, -8):
+        if rc not in (OPF_OK, OPF_ERR_NO_CONVERGENCE, OPF_ERR_INFEASIBLE):
             raise OPFError(rc, "opf_solve")
         return out
 
@@ -467,12 +472,12 @@ class Handle:
 
 
 def _ipm_options(variant="linred", tol=1e-8, max_iter=300, mu0=0.1, pf_tol=1e-10, verbose=False,
-                 line_search="merit", linear_solver="condensed"):
+                 line_search="merit", linear_solver="condensed", restoration=False, start_with_resto=False):
     if linear_solver not in ("condensed", "fullspace"):
         raise ValueError(f"linear_solver: {linear_solver!r}")
     return opf_ipm_options(OPF_LINRED if variant == "linred" else OPF_REDLIN, tol, max_iter, mu0, pf_tol,
-                           int(bool(verbose)), 1 if line_search == "filter" else 0,
-                           1 if linear_solver == "fullspace" else 0)
+                           int(bool(verbose)), 1 if line_search == "filter" else 0, int(bool(restoration)),
+                           int(bool(start_with_resto)), 1 if linear_solver == "fullspace" else 0)
 
 
 class Batch:
@@ -499,7 +504,7 @@ class Batch:
         ms = C.c_double()
         rc = self._lib.opf_batch_solve(self._b, C.byref(o), res, C.byref(ms))
         out = [{f: getattr(r, f) for f, _ in opf_ipm_result._fields_} for r in res]
-        if rc not in (OPF_OK, -8):
+        if rc not in (OPF_OK, OPF_ERR_NO_CONVERGENCE, OPF_ERR_INFEASIBLE):
             raise OPFError(rc, "opf_batch_solve")
         return out, ms.value
 

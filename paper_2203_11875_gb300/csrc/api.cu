@@ -1114,6 +1114,7 @@ const char* opf_strerror(int code) {
     case OPF_ERR_TIMEOUT: return "a bounded device wait expired";
     case OPF_ERR_OOM: return "device allocation failed";
     case OPF_ERR_NO_CONVERGENCE: return "interior-point iteration cap reached";
+    case OPF_ERR_INFEASIBLE: return "feasibility restoration failed (locally infeasible)";
     default: return "unknown status";
   }
 }

@@ -37,6 +37,9 @@ constexpr double KAPPA_SIGMA = 1e10, SMAX = 100.0;
 constexpr double GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-8, SWITCH_DELTA = 1.0, S_THETA = 1.1, S_PHI = 2.3;
 constexpr double ETA_PHI = 1e-4, GAMMA_ALPHA = 0.05, KAPPA_SOC = 0.99;
 constexpr int SOC_MAX = 4;
+// feasibility restoration (Wachter and Biegler 2006, Sec. 3.3)
+constexpr double RHO_RESTO = 1000.0, KAPPA_RESTO = 0.9;
+constexpr int RESTO_MAX_ITER = 100;
 
 // The filter: a trial (theta, phi) is acceptable when no pair (theta_l, phi_l)
 // has theta >= theta_l and phi >= phi_l.  It starts as theta >= theta_max.
@@ -349,6 +352,224 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
   return rc;
 }
 
+// Feasibility restoration phase (Wachter and Biegler 2006, Sec. 3.3), the
+// relaxation restricted to the inequality rows as Sec. 4.3 describes for
+// LinRed:
+//   min rho sum(p + n) + zeta/2 |D_R (w - w_R)|^2
+//   s.t. g(w) = 0, h(w) + s - p + n = 0, bounds on w and s, p, n >= 0,
+// zeta = sqrt(mu), D_R = diag(min(1, 1/|w_R|)).  Its barrier Newton step is the
+// condensed step with W replaced by the Hessian of the constraint terms plus
+// zeta D_R^2 and the dual regularisation delta_i = 1/Sigma_p,i + 1/Sigma_n,i
+// on the inequality rows (dp, dn eliminated).  That regularisation is folded
+// into Sigma_t = Sigma_s / (1 + delta Sigma_s) with the slack row's right-hand
+// side moved into the inequality rows (the same p_w, p_lambda and p_y), and the
+// slack step taken from the slack row: the device path is the ordinary
+// condensation.  The constraint-term Hessian is the evaluation at (lambda, y)
+// minus the one at (0, 0).  Steps by backtracking on the l1 merit of the
+// restoration barrier problem; the phase ends at the first point whose
+// violation is at most kappa of the starting one and that the filter (holding
+// the starting point) accepts.  Returns OPF_ERR_INFEASIBLE when it does not
+// get there.
+int restoration(opf_handle* h, Dev& d, const Bounds& bw, const Bounds& bs, const Filter& filt, double mu, Vec& w,
+                Vec& s, Vec& lam, Vec& y, Vec& zwl, Vec& zwu, Vec& zsl, Vec& zsu, bool verbose, opf_ipm_result& R) {
+  const Plan& P = h->P;
+  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
+  const int nkkt = nw + 2 * m + nx;
+  const long long nK = P.K.nnz();
+  if (!h->resto_w0) {
+    if (cudaMalloc(&h->resto_w0, sizeof(double) * std::max<long long>(1, nK)) != cudaSuccess) {
+      h->resto_w0 = nullptr;
+      return OPF_ERR_OOM;
+    }
+    h->allocs.push_back(h->resto_w0);
+  }
+  double f0;
+  Vec g, hv;
+  TRYD(eval_fgh(h, d, w, f0, g, hv));
+  double theta_R = 0.0, cinf = 0.0;
+  for (int i = 0; i < nx; ++i) { theta_R += std::fabs(g[i]); cinf = std::max(cinf, std::fabs(g[i])); }
+  for (int i = 0; i < m; ++i) {
+    theta_R += std::fabs(hv[i] + s[i]);
+    cinf = std::max(cinf, std::fabs(hv[i] + s[i]));
+  }
+  const Vec wR = w;
+  const double zeta = std::sqrt(mu), rho = RHO_RESTO;
+  Vec dr2(nw);
+  for (int i = 0; i < nw; ++i) {
+    const double q = std::min(1.0, 1.0 / std::max(std::fabs(wR[i]), 1e-300));
+    dr2[i] = q * q;
+  }
+  double mur = std::max(mu, cinf);
+  Vec p(m), n(m), zp(m), zn(m);
+  for (int i = 0; i < m; ++i) {
+    // p and n minimising the relaxed barrier terms for the current c (closed form)
+    const double c = hv[i] + s[i], t = (mur - rho * c) / (2.0 * rho);
+    n[i] = t + std::sqrt(t * t + mur * c / (2.0 * rho));
+    p[i] = c + n[i];
+    zp[i] = mur / p[i];
+    zn[i] = mur / n[i];
+  }
+  std::fill(lam.begin(), lam.end(), 0.0);
+  std::fill(y.begin(), y.end(), 0.0);
+  for (int i = 0; i < nw; ++i) {
+    zwl[i] = bw.fl[i] ? mur / bw.dl(w, i) : 0.0;
+    zwu[i] = bw.fu[i] ? mur / bw.du(w, i) : 0.0;
+  }
+  for (int i = 0; i < m; ++i) {
+    zsl[i] = bs.fl[i] ? mur / bs.dl(s, i) : 0.0;
+    zsu[i] = bs.fu[i] ? mur / bs.du(s, i) : 0.0;
+  }
+  double nu_pen = 1.0, delta = 0.0;
+  Vec grad(nw), gradf(nw), sw, ss, st(m), sp(m), sn(m), r(nkkt), step(nkkt), rw(nw), rs(m), ry(m), rp(m), rn(m);
+  Vec pw(nw), ps(m), pl(nx), py(m), pp(m), pn(m), dzwl, dzwu, dzsl, dzsu, dzp(m), dzn(m), wt(nw), stt(m), pt(m),
+      nt(m);
+  std::vector<char> all(m, 1);
+  for (int it = 0; it < RESTO_MAX_ITER; ++it) {
+    ++R.resto_iters;
+    // derivatives; W of the constraint terms only: W(lambda, y) - W(0, 0)
+    TRYD(h2d(h->s, d.u, w.data(), nu));
+    TRYD(h2d(h->s, d.x, w.data() + nu, nx));
+    CKD(cudaMemsetAsync(d.lam, 0, sizeof(double) * std::max(1, nx), h->s));
+    CKD(cudaMemsetAsync(d.y, 0, sizeof(double) * std::max(1, m), h->s));
+    TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+    CKD(cudaMemcpyAsync(h->resto_w0, h->Wval, sizeof(double) * nK, cudaMemcpyDeviceToDevice, h->s));
+    TRYD(h2d(h->s, d.lam, lam.data(), nx));
+    TRYD(h2d(h->s, d.y, y.data(), m));
+    TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
+    CKD(launch_axpby(h->s, nK, -1.0, h->resto_w0, 1.0, h->Wval, h->Wval));
+    TRYD(lagrangian_gradient(h, d.lam, d.y, d.grad));
+    g.resize(nx);
+    hv.resize(m);
+    TRYD(d2h(h->s, g.data(), h->g, nx));
+    TRYD(d2h(h->s, hv.data(), h->hv, m));
+    TRYD(d2h(h->s, grad.data(), d.grad, nw));
+    TRYD(d2h(h->s, gradf.data(), h->gradf, nw));
+    CKD(cudaStreamSynchronize(h->s));
+    bw.sigma(w, zwl, zwu, sw);
+    bs.sigma(s, zsl, zsu, ss);
+    for (int i = 0; i < nw; ++i) {
+      sw[i] += zeta * dr2[i];
+      rw[i] = zeta * dr2[i] * (w[i] - wR[i]) + (grad[i] - gradf[i]) + bw.bgrad(w, i, mur);
+    }
+    double dual = 0.0, prim = 0.0;
+    for (int i = 0; i < nw; ++i) dual = std::max(dual, std::fabs(rw[i]));
+    for (int i = 0; i < nx; ++i) prim = std::max(prim, std::fabs(g[i]));
+    for (int i = 0; i < m; ++i) {
+      sp[i] = zp[i] / p[i];
+      sn[i] = zn[i] / n[i];
+      const double dc = 1.0 / sp[i] + 1.0 / sn[i];
+      st[i] = ss[i] / (1.0 + dc * ss[i]);
+      rs[i] = y[i] + bs.bgrad(s, i, mur);
+      ry[i] = hv[i] + s[i] - p[i] + n[i];
+      rp[i] = rho - y[i] - mur / p[i];
+      rn[i] = rho + y[i] - mur / n[i];
+      dual = std::max(dual, std::max(std::fabs(rs[i]), std::max(std::fabs(rp[i]), std::fabs(rn[i]))));
+      prim = std::max(prim, std::fabs(ry[i]));
+      // the relaxation folded into the inequality row, then the slack row too
+      r[nw + m + nx + i] = ry[i] + rp[i] / sp[i] - rn[i] / sn[i] - rs[i] / ss[i];
+      r[nw + i] = 0.0;
+    }
+    for (int i = 0; i < nw; ++i) r[i] = rw[i];
+    for (int i = 0; i < nx; ++i) r[nw + m + i] = g[i];
+    TRYD(h2d(h->s, d.sig_u, sw.data(), nu));
+    TRYD(h2d(h->s, d.sig_x, sw.data() + nu, nx));
+    TRYD(h2d(h->s, d.sig_s, st.data(), m));
+    int att = 1, gi = 0;
+    {
+      const int rc0 = condense_factor0(h, d, &gi);
+      if (rc0 == OPF_OK) delta = 0.0;
+      else if (rc0 == OPF_ERR_NOT_PD) { TRYD(factor_with_correction(h, delta, delta, att, true)); ++att; }
+      else return rc0;
+    }
+    R.n_factor += att;
+    TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
+    TRYD(solve_step(h, d.rhs, d.step));
+    TRYD(d2h(h->s, step.data(), d.step, nkkt));
+    CKD(cudaStreamSynchronize(h->s));
+    std::copy(step.begin(), step.begin() + nw, pw.begin());
+    std::copy(step.begin() + nw + m, step.begin() + nw + m + nx, pl.begin());
+    std::copy(step.begin() + nw + m + nx, step.end(), py.begin());
+    for (int i = 0; i < m; ++i) {
+      ps[i] = -(rs[i] + py[i]) / ss[i];    // the slack row of K_aug
+      pp[i] = (py[i] - rp[i]) / sp[i];
+      pn[i] = (-py[i] - rn[i]) / sn[i];
+    }
+    const double tau = std::max(TAU_MIN, 1.0 - mur);
+    double amax = std::min(bw.max_step(w, pw, tau), bs.max_step(s, ps, tau));
+    for (int i = 0; i < m; ++i) {
+      if (pp[i] < 0) amax = std::min(amax, -tau * p[i] / pp[i]);
+      if (pn[i] < 0) amax = std::min(amax, -tau * n[i] / pn[i]);
+    }
+    bw.dz(w, zwl, zwu, pw, mur, dzwl, dzwu);
+    bs.dz(s, zsl, zsu, ps, mur, dzsl, dzsu);
+    for (int i = 0; i < m; ++i) {
+      dzp[i] = mur / p[i] - zp[i] - sp[i] * pp[i];
+      dzn[i] = mur / n[i] - zn[i] - sn[i] * pn[i];
+    }
+    const double az = std::min(std::min(std::min(max_step_z(zwl, dzwl, bw.fl, tau), max_step_z(zwu, dzwu, bw.fu, tau)),
+                                        std::min(max_step_z(zsl, dzsl, bs.fl, tau), max_step_z(zsu, dzsu, bs.fu, tau))),
+                               std::min(max_step_z(zp, dzp, all, tau), max_step_z(zn, dzn, all, tau)));
+    double mmax = 0.0;
+    for (int i = 0; i < nx; ++i) mmax = std::max(mmax, std::fabs(lam[i] + pl[i]));
+    for (int i = 0; i < m; ++i) mmax = std::max(mmax, std::fabs(y[i] + py[i]));
+    nu_pen = std::max(nu_pen, 1.1 * mmax);
+    // l1 merit of the restoration barrier problem and its directional derivative
+    auto merit = [&](const Vec& wv, const Vec& sv, const Vec& pv, const Vec& nv, const Vec& gv, const Vec& hh) {
+      double v = bw.barrier(wv, mur) + bs.barrier(sv, mur), c1 = 0.0;
+      for (int i = 0; i < nw; ++i) v += 0.5 * zeta * dr2[i] * (wv[i] - wR[i]) * (wv[i] - wR[i]);
+      for (int i = 0; i < m; ++i) {
+        v += rho * (pv[i] + nv[i]) - mur * (std::log(pv[i]) + std::log(nv[i]));
+        c1 += std::fabs(hh[i] + sv[i] - pv[i] + nv[i]);
+      }
+      for (int i = 0; i < nx; ++i) c1 += std::fabs(gv[i]);
+      return v + nu_pen * c1;
+    };
+    const double psi0 = merit(w, s, p, n, g, hv);
+    double dpsi = 0.0, c1 = 0.0;
+    for (int i = 0; i < nw; ++i) dpsi += (zeta * dr2[i] * (w[i] - wR[i]) + bw.bgrad(w, i, mur)) * pw[i];
+    for (int i = 0; i < m; ++i) {
+      dpsi += rho * (pp[i] + pn[i]) + bs.bgrad(s, i, mur) * ps[i] - mur * (pp[i] / p[i] + pn[i] / n[i]);
+      c1 += std::fabs(ry[i]);
+    }
+    for (int i = 0; i < nx; ++i) c1 += std::fabs(g[i]);
+    dpsi -= nu_pen * c1;
+    double a = amax, ft = 0.0;
+    Vec gt, ht;
+    for (;;) {
+      for (int i = 0; i < nw; ++i) wt[i] = w[i] + a * pw[i];
+      for (int i = 0; i < m; ++i) { stt[i] = s[i] + a * ps[i]; pt[i] = p[i] + a * pp[i]; nt[i] = n[i] + a * pn[i]; }
+      TRYD(eval_fgh(h, d, wt, ft, gt, ht));
+      const double v = merit(wt, stt, pt, nt, gt, ht);
+      if ((std::isfinite(v) && v <= psi0 + ETA * a * std::min(dpsi, 0.0)) || a <= 1e-8 * amax) break;
+      a *= 0.5;
+    }
+    w = wt;
+    s = stt;
+    p = pt;
+    n = nt;
+    for (int i = 0; i < nx; ++i) lam[i] += a * pl[i];
+    for (int i = 0; i < m; ++i) y[i] += a * py[i];
+    for (int i = 0; i < nw; ++i) { zwl[i] += az * dzwl[i]; zwu[i] += az * dzwu[i]; }
+    for (int i = 0; i < m; ++i) { zsl[i] += az * dzsl[i]; zsu[i] += az * dzsu[i]; }
+    bw.safeguard(w, zwl, zwu, mur);
+    bs.safeguard(s, zsl, zsu, mur);
+    for (int i = 0; i < m; ++i) {
+      zp[i] = std::min(std::max(zp[i] + az * dzp[i], mur / (KAPPA_SIGMA * p[i])), KAPPA_SIGMA * mur / p[i]);
+      zn[i] = std::min(std::max(zn[i] + az * dzn[i], mur / (KAPPA_SIGMA * n[i])), KAPPA_SIGMA * mur / n[i]);
+    }
+    double theta = 0.0;
+    for (int i = 0; i < nx; ++i) theta += std::fabs(gt[i]);
+    for (int i = 0; i < m; ++i) theta += std::fabs(ht[i] + s[i]);
+    const double phi = ft + bw.barrier(w, mu) + bs.barrier(s, mu);
+    if (verbose)
+      std::printf("  resto it %3d theta %.3e (theta_R %.3e) mu_R %.1e a %.2e\n", it, theta, theta_R, mur, a);
+    if (theta <= KAPPA_RESTO * theta_R && filt.acceptable(theta, phi)) return OPF_OK;
+    if (dual <= KAPPA_EPS * mur && prim <= KAPPA_EPS * mur)
+      mur = std::max(0.1 * mu, std::min(KAPPA_MU * mur, std::pow(mur, THETA_MU)));
+  }
+  return OPF_ERR_INFEASIBLE;
+}
+
 // the initial primal point: theta = 0, Vm = 1 at load buses, 1.05 at generator
 // buses (clipped to bounds), non-slack Pg at the middle of its range
 Vec flat_start(const Plan& P) {
@@ -452,6 +673,15 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
       mu = std::max(o.tol / 10, std::min(KAPPA_MU * mu, std::pow(mu, THETA_MU)));
     }
     const double tau = std::max(TAU_MIN, 1.0 - mu);
+    if (o.line_search == OPF_LINESEARCH_FILTER && o.restoration && o.start_with_resto && it == 0) {
+      // the restoration phase from the starting point, before any step
+      filt.reset(theta_max);
+      filt_mu = mu;
+      filt.pairs.push_back({pl1, f + bw.barrier(w, mu) + bs.barrier(s, mu)});
+      TRYD(restoration(h, d, bw, bs, filt, mu, w, s, lam, y, zwl, zwu, zsl, zsu, o.verbose != 0, R));
+      ++R.restorations;
+      continue;
+    }
     bw.sigma(w, zwl, zwu, sw);
     bs.sigma(s, zsl, zsu, ss);
     // condense + factor with inertia correction
@@ -479,7 +709,7 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
     for (int i = 0; i < m; ++i) r[nw + m + nx + i] = hv[i] + s[i];
     Vec pw(nw), ps(m), plam(nx), py(m);
     double amax = 1.0, az = 1.0, a = 1.0;
-    bool accepted = false;
+    bool accepted = false, resto = false;
     for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
       t0 = clk::now();
       TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
@@ -569,6 +799,12 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
           if (!accepted) a *= 0.5;
         }
         if (accepted && !phi_type) filt.pairs.push_back({(1.0 - GAMMA_THETA) * theta0, ph0 - GAMMA_PHI * theta0});
+        if (!accepted && o.restoration) {
+          // out of step length: the current point goes into the filter and the
+          // restoration phase takes over
+          filt.pairs.push_back({theta0, ph0});
+          resto = true;
+        }
       } else {
         while (a > 1e-4 * amax) {
           for (int i = 0; i < nw; ++i) wt[i] = w[i] + a * pw[i];
@@ -585,6 +821,7 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
         }
       }
       R.ms_linesearch += ms_since(t0);
+      if (resto) break;
       if (!accepted) {
         // backtracking failed: shorten the step by a larger primal regularisation
         delta = std::max(1e-8, 10.0 * delta);
@@ -594,6 +831,11 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
         if (rc == OPF_ERR_NOT_PD) { att = 0; TRYD(factor_with_correction(h, delta, delta, att)); R.n_factor += att; }
         else if (rc != OPF_OK) return rc;
       }
+    }
+    if (resto) {
+      TRYD(restoration(h, d, bw, bs, filt, mu, w, s, lam, y, zwl, zwu, zsl, zsu, o.verbose != 0, R));
+      ++R.restorations;
+      continue;
     }
     for (int i = 0; i < nw; ++i) w[i] += a * pw[i];
     for (int i = 0; i < m; ++i) s[i] += a * ps[i];
@@ -1028,7 +1270,9 @@ extern "C" int opf_solve(opf_handle* h, const opf_ipm_options* opt, opf_ipm_resu
       (o.line_search != OPF_LINESEARCH_MERIT && o.line_search != OPF_LINESEARCH_FILTER) ||
       (o.line_search == OPF_LINESEARCH_FILTER && o.variant != OPF_LINRED) ||
       (o.linear_solver != OPF_LINSOLVE_CONDENSED && o.linear_solver != OPF_LINSOLVE_FULLSPACE) ||
-      (o.linear_solver == OPF_LINSOLVE_FULLSPACE && o.variant != OPF_LINRED))
+      (o.linear_solver == OPF_LINSOLVE_FULLSPACE && o.variant != OPF_LINRED) ||
+      ((o.restoration || o.start_with_resto) && o.line_search != OPF_LINESEARCH_FILTER) ||
+      (o.start_with_resto && !o.restoration))
     return OPF_ERR_INVALID_ARG;
   *res = opf_ipm_result{};
   h->have_solution = false;

@@ -146,6 +146,7 @@ struct opf_handle {
   double* ps_sc = nullptr;       // 1 / (1 + delta_c Sigma_s) (m)
   double* pf_ws = nullptr;       // power-flow step and norm (nx + 1)
   double* ipm_buf = nullptr;     // interior-point loop scratch (in allocs)
+  double* resto_w0 = nullptr;    // restoration phase: W at zero multipliers (K pattern; in allocs)
   // converged state of the last opf_solve (host), full-space form
   bool have_solution = false;
   std::vector<double> sol_w, sol_lam, sol_y, sol_s, sol_sig_w, sol_sig_s;

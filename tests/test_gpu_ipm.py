@@ -119,3 +119,32 @@ def test_filter_line_search_matches_oracle(pkg, name):
         assert ref.soc_steps >= 1 and res["soc_steps"] >= 1
     with pytest.raises(pkg.OPFError):
         pkg.Handle(net).solve("redlin", line_search="filter")
+
+
+@pytest.mark.parametrize("name", ["tiny3", "ring30", "grid2000"])
+def test_restoration_from_the_start_matches_oracle(pkg, name):
+    """The feasibility restoration phase (filter line search, relaxation on the
+    inequality rows as a per-row dual regularisation) run from the flat start
+    hands back an acceptable point, and the loop reaches the oracle's optimum
+    (which the non-GPU pins tie to the plain filter solve)."""
+    net = gridgen.WORKLOADS[name]()
+    ref = ipm.linred(net, line_search="filter", restoration=True, start_with_resto=True)
+    assert ref.status == "converged" and ref.restorations == 1
+    res = pkg.Handle(net).solve("linred", line_search="filter", restoration=True, start_with_resto=True)
+    assert res["status"] == 0, res
+    assert res["restorations"] == 1 and res["resto_iters"] >= 1
+    assert abs(res["obj"] - ref.obj) <= TOL_OBJ * abs(ref.obj)
+
+
+def test_restoration_reports_an_infeasible_case(pkg):
+    """Loads of 1.7 x the 3-bus case exceed its generation capacity: the filter
+    search runs out of step length, the restoration phase finds no acceptable
+    point, and the solve ends with OPF_ERR_INFEASIBLE (the oracle fails the
+    same way)."""
+    net = gridgen.tiny3()
+    net.Pd, net.Qd = 1.7 * net.Pd, 1.7 * net.Qd
+    assert net.Pmax.sum() < net.Pd.sum()
+    res = pkg.Handle(net).solve("linred", line_search="filter", restoration=True)
+    assert res["status"] == pkg.OPF_ERR_INFEASIBLE and res["restorations"] >= 1
+    with pytest.raises(RuntimeError, match="restoration failed"):
+        ipm.linred(net, line_search="filter", restoration=True)
