@@ -365,6 +365,74 @@ def time_condense(h, D, delta, reps, stream, torch):
     return float(np.mean(ts))
 
 
+def run_decay(binding, net, it, D, torch):
+    """The decay of the reduced Hessian with the bus distance between controls
+    (the structure Sec. 5 proposes to exploit), measured on the library's own
+    Kred and reduced gradient at the grid10k iterate: normalised entries
+    |K_ij| / sqrt(K_ii K_jj) by hop distance for the voltage and the dispatch
+    controls, with and without the rank-one coupling through the slack
+    generator (coefficient 2 c2_0 + Sigma_s,0 on v = Z^T grad P_slack), and the
+    error of a probing approximation (distance-2d colouring, entries kept within
+    distance d)."""
+    import scipy.sparse as sps
+    from scipy.sparse.csgraph import shortest_path
+    h = binding.Handle(net)
+    nu, nw = h.nu, h.nw
+    h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
+    K = torch.zeros(nu * nu, dtype=torch.float64, device=D["x"].device)
+    h.condense(D["sig_u"], D["sig_x"], D["sig_s"], K)
+    K = K.cpu().numpy().reshape(nu, nu)
+    K = 0.5 * (K + K.T)
+    nr, nc, rp, ci = h.get_csr_pattern(binding.OPF_MAT_A)
+    av = torch.zeros(len(ci), dtype=torch.float64, device=D["x"].device)
+    h.get_csr_values(binding.OPF_MAT_A, av)
+    av = av.cpu().numpy()
+    a0 = np.zeros(nw)
+    a0[ci[rp[0]:rp[1]]] = av[rp[0]:rp[1]]
+    v = torch.zeros(nu, dtype=torch.float64, device=D["x"].device)
+    h.reduced_gradient(torch.as_tensor(a0, device=D["x"].device), v)
+    v = v.cpu().numpy()
+    del h
+    ng = net.ng
+    busu = np.concatenate([net.gbus, net.gbus[1:]])
+    graph = sps.coo_matrix((np.ones(net.nl), (net.lf, net.lt)), shape=(net.nb, net.nb))
+    srcs = np.unique(busu)
+    hop = shortest_path(graph, directed=False, unweighted=True, indices=srcs)
+    row = {b: k for k, b in enumerate(srcs)}
+    Dh = hop[np.array([row[b] for b in busu])][:, busu]
+    coef = 2.0 * float(net.c2[0]) + float(it["sig_s"][0])
+
+    def profile(M, idx):
+        dg = np.sqrt(np.abs(np.diag(M)))
+        Nm = np.abs(M) / np.outer(dg, dg)
+        Nb, Db = Nm[np.ix_(idx, idx)], Dh[np.ix_(idx, idx)]
+        return {int(k): [float(np.median(Nb[Db == k])), float(np.percentile(Nb[Db == k], 99))]
+                for k in range(0, 31, 3) if (Db == k).any()}
+    vm, pg = np.arange(ng), np.arange(ng, nu)
+    K1 = K - coef * np.outer(v, v)
+    probe = {}
+    for d in (4, 8, 12):
+        order = np.argsort(-np.sum(Dh <= 2 * d, axis=1), kind="stable")
+        color = -np.ones(nu, int)
+        for j in order:
+            used = set(color[(Dh[j] <= 2 * d) & (color >= 0)].tolist())
+            c = 0
+            while c in used:
+                c += 1
+            color[j] = c
+        nc_ = int(color.max()) + 1
+        V = np.zeros((nu, nc_))
+        V[np.arange(nu), color] = 1.0
+        Kd = np.where(Dh <= d, (K @ V)[:, color], 0.0)
+        Kd = 0.5 * (Kd + Kd.T)
+        probe[d] = {"colors": nc_, "rel_err": float(np.linalg.norm(Kd - K) / np.linalg.norm(K))}
+    return {"workload": "grid10k iterate: Kred and the slack row's reduced gradient from the library",
+            "normalised_by_hops_median_p99": {"Vm-Vm": profile(K, vm), "Pg-Pg": profile(K, pg),
+                                              "Vm-Vm_without_slack_rank1": profile(K1, vm),
+                                              "Pg-Pg_without_slack_rank1": profile(K1, pg)},
+            "probing": probe}
+
+
 def run_fullspace(binding, net, it, delta, D, stream, flush, torch, split, no_solve, reps=20):
     """The hybrid full-space IPM's linear algebra (Sec. 4.3, Table 2's comparison
     method) on the same grid10k iterate: assembly + block LDL^T + inertia, then
@@ -441,6 +509,7 @@ def main():
     ap.add_argument("--no-vjp", action="store_true", help="skip the 10,000-bus dispatch-derivative timing")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FP64 peak probes (derived peak instead)")
     ap.add_argument("--no-fullspace", action="store_true", help="skip the hybrid full-space comparison")
+    ap.add_argument("--no-decay", action="store_true", help="skip the reduced-Hessian decay study")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
@@ -654,6 +723,8 @@ def main():
                               "solve_iters": r10["iters"], "solve_obj": r10["obj"], "prepare_ms": t_prep * 1e3,
                               "vjp_ms": float(np.median(reps)) * 1e3, "refine_steps": info["refine_steps"],
                               "rel_residual": info["rel_residual"], "polish_iters": info["polish_iters"]}
+    if not args.no_decay:
+        out["reduced_hessian_decay"] = run_decay(binding, net, it, D, torch)
     if not args.no_fullspace:
         out["hybrid_fullspace"] = run_fullspace(binding, net, it, delta, D, stream, flush, torch,
                                                 out["split_ms_per_step"], args.no_solve)
