@@ -557,14 +557,14 @@ def main():
 
     def hot_step(dl):
         h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
-        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        h.condense_rhs(D["sig_u"], D["sig_x"], D["sig_s"], D["r"])
         return h.kkt_factor(dl)
 
     torch.cuda.synchronize()
     for _ in range(max(args.warmup, 3)):
         while hot_step(delta) >= 0:
             delta = max(1e-4, 8 * delta)
-        h.kkt_solve(D["r"], step)
+        h.kkt_solve_condensed(step)
     torch.cuda.synchronize()
     trsm_kernel, trsm_tune, trsm_kernel1 = h.trsm_choice()
     chol_form, chol_grid, chol_tune = h.chol_choice()
@@ -582,10 +582,11 @@ def main():
             ev[k][0].record(stream)
         h.eval_derivatives(D["x"], D["u"], D["lam"], D["y"])
         ev[k][1].record(stream)
-        h.condense(D["sig_u"], D["sig_x"], D["sig_s"])
+        # A4-A9: condensation with the step's right-hand side as one extra column
+        h.condense_rhs(D["sig_u"], D["sig_x"], D["sig_s"], D["r"])
         assert h.kkt_factor(delta) == -1
         ev[k][2].record(stream)
-        h.kkt_solve(D["r"], step)
+        h.kkt_solve_condensed(step)
         ev[k][3].record(stream)
     torch.cuda.synchronize()
     n_launch = binding.launch_count() - n_launch0
@@ -646,8 +647,9 @@ def main():
            "config": {"workload": WORKLOAD, "inputs": "tests/golden/grid10k_iterate.npz (oracle LinRed iterate 3 "
                       "of the seeded 10,000-bus network)",
                       "l2": "inputs larger than L2 (Z, H 168 MB each) and a 256 MB flush written between timed steps",
-                      "timed": "A4-A9: G_x refactor, multi-RHS solves, K, H = K Z, Kred, one Cholesky attempt "
-                               "(events) + the condensed right-hand side of the step solve (phase events)",
+                      "timed": "A4-A9: G_x refactor, multi-RHS solves (the step's right-hand side as one extra "
+                               "column), K, H = K Z, Kred and the condensed right-hand side, one Cholesky attempt "
+                               "(events) + reading the condensed right-hand side out (phase events)",
                       "route": "adjoint", "delta_w": delta,
                       "trsm_kernel": KERNEL_NAMES.get(trsm_kernel, str(trsm_kernel)),
                       "trsm_kernel_1rhs": KERNEL_NAMES.get(trsm_kernel1, str(trsm_kernel1)),

@@ -220,6 +220,24 @@ int opf_get_factor(opf_handle* h, double* dst);
  * overlap.  K_aug carries Sigma of the last condense and delta_w, delta_c of the
  * last factor (-delta_c I in its (p_y, p_y) block). */
 int opf_kkt_solve(opf_handle* h, const double* rhs, double* step, int nrhs);
+/* A4-A8 in one pass: opf_condense together with the condensed right-hand side
+ * of K_aug p = -rhs (one right-hand side, device, n_kkt doubles in the layout
+ * of opf_kkt_solve).  The right-hand side rides along the condensation as one
+ * extra column (Theorem 1's reductions with the same factor): q = G_x^{-1} b_l
+ * in the S_x solve, K [0; q] in H = K Z, phi = G_x^{-T} (b_t - K [0; q])_x in
+ * the adjoint solve, and the condensed right-hand side in the G_u^T product
+ * (adjoint route; on the explicit route, or with no spare column, the
+ * right-hand side is only kept).  rhs is copied; Kred as in opf_condense.
+ * Errors as opf_condense, INVALID_ARG for a NULL rhs. */
+int opf_condense_rhs(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s,
+                     const double* rhs, double* Kred);
+/* The step for that right-hand side after opf_kkt_factor: the Cholesky solve
+ * and the recovery products only (step as in opf_kkt_solve, device).  With
+ * delta_c > 0 in the factor, or when the condensation could not carry the
+ * column, the plain recovery of opf_kkt_solve runs on the kept right-hand side.
+ * Errors: INVALID_ARG (no opf_condense_rhs since the last evaluation, or no
+ * factor), CUDA, TIMEOUT. */
+int opf_kkt_solve_condensed(opf_handle* h, double* step);
 /* Solve K_aug^T z = -r (K_aug is symmetric; this path applies the transposed
  * recovery, G_x^{-T} first), same layout.  Used by the dispatch derivative. */
 int opf_kkt_solve_adjoint(opf_handle* h, const double* rhs, double* sol, int nrhs);

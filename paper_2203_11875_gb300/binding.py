@@ -86,6 +86,8 @@ _SIGS = {
     "opf_get_factor": (C.c_int, [C.c_void_p, C.c_void_p]),
     "opf_newton_step": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8 + [C.c_double, C.c_double, C.c_void_p, _ip]),
     "opf_kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "opf_condense_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "opf_kkt_solve_condensed": (C.c_int, [C.c_void_p, C.c_void_p]),
     "opf_kkt_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "opf_fullspace_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                                        _ip]),
@@ -349,6 +351,13 @@ class Handle:
 
     def get_factor(self, dst):
         _check(self._lib.opf_get_factor(self._h, _ptr(dst)), "opf_get_factor")
+
+    def condense_rhs(self, sig_u, sig_x, sig_s, rhs, Kred=None):
+        _check(self._lib.opf_condense_rhs(self._h, _ptr(sig_u), _ptr(sig_x), _ptr(sig_s), _ptr(rhs), _ptr(Kred)),
+               "opf_condense_rhs")
+
+    def kkt_solve_condensed(self, step):
+        _check(self._lib.opf_kkt_solve_condensed(self._h, _ptr(step)), "opf_kkt_solve_condensed")
 
     def kkt_solve(self, rhs, step, nrhs=1):
         _check(self._lib.opf_kkt_solve(self._h, _ptr(rhs), _ptr(step), int(nrhs)), "opf_kkt_solve")

@@ -558,6 +558,8 @@ int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam
               bool derivs) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
+  h->fr_ready = false;   // a new point: the condensed right-hand side belongs to the old one
+  h->fr_have_b = false;
   CK(launch_bus_state(s, P.nb, P.nu, x, u, h->th_w, h->vm_w, h->Vm, h->Va));
   CK(launch_end_eval(s, P.ne, h->end_i, h->end_k, h->end_h, h->gs, h->bs, h->gm, h->bm, h->Vm, h->Va,
                      h->pq, h->dsrc, h->hpq, h->hv, derivs ? 1 : 0));
@@ -863,7 +865,7 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
 
 // A7 on the current K and Z = [I; S_x]: H = K Z, then Kred by the handle's route
 // (the x rows of H end up holding Psi = G_x^{-T} H_x on the adjoint route)
-static int reduce_route(opf_handle* h, int route) {
+static int reduce_route(opf_handle* h, int route, int nc) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const int nu = P.nu, nx = P.nx;
@@ -882,10 +884,11 @@ static int reduce_route(opf_handle* h, int route) {
     CK(launch_symmetrize(s, nu, h->F, nu, 1, h->Kred));
     ph_end(h);
   } else {
-    // Psi = G_x^{-T} H_x ; Kred = H_u - G_u^T Psi
-    TRY(lu_solve_perm(h, 1, Hx, ld, 1, nu, true));
+    // Psi = G_x^{-T} H_x ; Kred = H_u - G_u^T Psi  (nc = nu + 1: the condensed
+    // right-hand side's column rides along: phi = G_x^{-T} e_x, r_hat = e_u - G_u^T phi)
+    TRY(lu_solve_perm(h, 1, Hx, ld, 1, nc, true));
     ph_begin(h, OPF_PHASE_KRED);
-    CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Hx, ld, 1, h->H, ld, 1, nu, -1.0, 1.0));
+    CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Hx, ld, 1, h->H, ld, 1, nc, -1.0, 1.0));
     CK(launch_symmetrize(s, nu, h->H, ld, 1, h->Kred));
     ph_end(h);
   }
@@ -897,21 +900,24 @@ static int reduce_route(opf_handle* h, int route) {
 // OPF_ROUTE_AUTO the first call times both routes on this network (the explicit
 // one first: it leaves H intact) and keeps the faster; the adjoint route's
 // result stands for that call.
-static int reduce_async(opf_handle* h) {
+static int reduce_async(opf_handle* h, int nc = 0, const double* bt = nullptr) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const int nu = P.nu, nw = P.nw;
   const long long ld = h->ldp;
+  if (nc <= 0) nc = nu;
   ph_begin(h, OPF_PHASE_SPMM);
-  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, ld, 1, h->H, ld, 1, nu, 1.0, 0.0));
+  CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt, ld, 1, h->H, ld, 1, nc, 1.0, 0.0));
+  // the right-hand side's column: e = b_t - K [0; q]
+  if (bt) CK(launch_column_axpby(s, nw, -1.0, h->H + nu, ld, 1.0, bt, 1, h->H + nu, ld));
   ph_end(h);
-  if (h->route >= 0) return reduce_route(h, h->route);
+  if (h->route >= 0) return reduce_route(h, h->route, nc);
   cudaEvent_t ev[3];
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], s));
-  TRY(reduce_route(h, OPF_ROUTE_EXPLICIT));
+  TRY(reduce_route(h, OPF_ROUTE_EXPLICIT, nc));
   CK(cudaEventRecord(ev[1], s));
-  TRY(reduce_route(h, OPF_ROUTE_ADJOINT));
+  TRY(reduce_route(h, OPF_ROUTE_ADJOINT, nc));
   CK(cudaEventRecord(ev[2], s));
   CK(cudaEventSynchronize(ev[2]));
   CK(cudaEventElapsedTime(&h->route_ms[OPF_ROUTE_EXPLICIT], ev[0], ev[1]));
@@ -922,10 +928,45 @@ static int reduce_async(opf_handle* h) {
   return OPF_OK;
 }
 
-int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s) {
+// the right-hand side of the step into the handle's KB copy, and
+// b_t = b_w + A^T (Sigma_s b_y - b_s) (needs h->sig_s)
+int fr_reserve(opf_handle* h) {
+  if (!h->fr_kb) {
+    TRY(alloc(h, &h->fr_kb, kkt_rows(h->P)));
+    TRY(alloc(h, &h->fr_bt, (size_t)h->P.nw + h->P.m));
+  }
+  return OPF_OK;
+}
+
+static int fr_prepare(opf_handle* h, const double* rhs) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nw = P.nw, m = P.m, nx = P.nx;
+  const size_t N = kkt_rows(P);
+  TRY(fr_reserve(h));
+  const KB b = kb_at(P, h->fr_kb, 1);
+  CK(launch_permute_rows(s, nw, 1, h->c2w, rhs, int(N), 1, b.w, 1, 0, -1.0, 0));
+  CK(launch_permute_rows(s, m, 1, nullptr, rhs + nw, int(N), 1, b.s, 1, 0, -1.0, 0));
+  CK(launch_permute_rows(s, nx, 1, h->perm, rhs + nw + m, int(N), 1, b.l, 1, 0, -1.0, 0));
+  CK(launch_permute_rows(s, m, 1, nullptr, rhs + nw + m + nx, int(N), 1, b.y, 1, 0, -1.0, 0));
+  double* U = h->fr_bt + nw;   // Sigma_s b_y - b_s
+  CK(launch_scale_rows(s, m, 1, h->sig_s, b.y, U, -1.0, b.s));
+  CK(cudaMemcpyAsync(h->fr_bt, b.w, sizeof(double) * nw, cudaMemcpyDeviceToDevice, s));
+  CK(launch_spmm(s, nw, h->AT_rp, h->AT_ci, h->Aval, h->AT_map, U, 1, 1, h->fr_bt, 1, 1, 1, 1.0, 1.0));
+  h->fr_have_b = true;
+  return OPF_OK;
+}
+
+int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s,
+                   const double* rhs) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   const int nu = P.nu, nx = P.nx, nw = P.nw;
+  // the right-hand side in the same pass: needs a spare column (ldp > nu) and
+  // the adjoint route's Psi
+  const bool fused = rhs != nullptr && h->ldp > nu && h->opt.route != OPF_ROUTE_EXPLICIT;
+  h->fr_ready = false;
+  h->fr_have_b = false;
   h->psi_valid = false;
   h->finv_valid = false;   // the explicit route uses the factor's buffer as scratch
   h->delta_c = 0.0;
@@ -936,6 +977,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   CK(launch_assemble_K(s, P.K.nnz(), h->Wval, h->KAA_ptr, h->KAA_r, h->KAA_a, h->KAA_b, h->sig_s, h->Aval,
                        h->Kval));
   CK(launch_add_diag(s, nw, nu, h->K_diag, h->perm, sig_u, sig_x, h->Kval, h->sig_c));
+  if (rhs) TRY(fr_prepare(h, rhs));
   ph_end(h);
   // A6: Z = [I; S_x],  S_x = -(P G_x P^T)^{-1} P G_u   (perm rows); Z and H are
   // row-major with leading dimension ldp (nu rounded up to 32): lanes of a warp
@@ -945,13 +987,18 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s));
   CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
   if (h->trsm_mode < 0) TRY(autotune_trsm(h, Sx, ld));
-  TRY(lu_solve_perm(h, 0, Sx, ld, 1, nu, true));
+  // the right-hand side's column of the solve: b_l (then q = G_x^{-1} b_l; the
+  // identity rows of Zt are zero in this column, so H gets K [0; q])
+  const int nc = fused ? nu + 1 : nu;
+  if (fused) CK(launch_column_axpby(s, nx, 1.0, kb_at(P, h->fr_kb, 1).l, 1, 0.0, nullptr, 0, Sx + nu, ld));
+  TRY(lu_solve_perm(h, 0, Sx, ld, 1, nc, true));
   h->psi_last_adjoint = false;
-  TRY(reduce_async(h));
+  TRY(reduce_async(h, nc, fused ? h->fr_bt : nullptr));
   h->have_condense = true;
   h->have_factor = false;
   h->sens_ready = false;
   h->psi_valid = h->route != OPF_ROUTE_EXPLICIT || h->psi_last_adjoint;
+  h->fr_ready = fused && h->psi_valid;
   return OPF_OK;
 }
 
@@ -963,6 +1010,7 @@ int recondense_dc(opf_handle* h, double delta_c) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
   h->psi_valid = false;
+  h->fr_ready = false;   // K changes: the condensed right-hand side is recomputed by the plain path
   h->finv_valid = false;
   h->have_factor = false;
   const double* sig = h->sig_s;
@@ -1345,6 +1393,30 @@ int opf_condense(opf_handle* h, const double* sig_u, const double* sig_x, const 
     h->have_lu = false;
   }
   return rc;
+}
+
+int opf_condense_rhs(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s,
+                     const double* rhs, double* Kred) {
+  if (!h || !sig_u || !sig_x || !sig_s || !rhs || !h->have_W) return OPF_ERR_INVALID_ARG;
+  TRY(condense_async(h, sig_u, sig_x, sig_s, rhs));
+  if (Kred)
+    CK(cudaMemcpyAsync(Kred, h->Kred, sizeof(double) * (size_t)h->P.nu * h->P.nu, cudaMemcpyDeviceToDevice,
+                       h->s));
+  int rc = read_status(h);
+  if (rc != OPF_OK) {
+    h->have_condense = false;
+    h->have_lu = false;
+    h->fr_ready = false;
+    h->fr_have_b = false;
+  }
+  return rc;
+}
+
+int opf_kkt_solve_condensed(opf_handle* h, double* step) {
+  if (!h || !step || !h->have_factor || !h->fr_have_b) return OPF_ERR_INVALID_ARG;
+  TRY(kkt_solve_prepared(h, step));
+  CK(cudaStreamSynchronize(h->s));
+  return OPF_OK;
 }
 
 int opf_kkt_factor(opf_handle* h, double delta_w, double delta_c, int* fail_col) {

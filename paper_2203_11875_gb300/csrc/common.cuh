@@ -300,6 +300,9 @@ cudaError_t launch_scale_rows(cudaStream_t s, int n, int ncols, const double* d,
 cudaError_t launch_absmax(cudaStream_t s, long long n, const double* x, double* out);
 cudaError_t launch_fill(cudaStream_t s, long long n, double v, double* x);
 cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld);
+// dst[i * ldd] = a * src[i * lds] + b * y[i * ldy] for i < n (y may be NULL)
+cudaError_t launch_column_axpby(cudaStream_t s, int n, double a, const double* src, long long lds, double b,
+                                const double* y, long long ldy, double* dst, long long ldd);
 
 // ----------------------------------------------------------------- batches
 // One instance of a batched condensation (opf_batch_condense_factor): the device

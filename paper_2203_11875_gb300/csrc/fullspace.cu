@@ -652,6 +652,8 @@ int fs_set_sigma(opf_handle* h, const double* sig_u, const double* sig_x, const 
   h->have_factor = false;
   h->psi_valid = false;
   h->sens_ready = false;
+  h->fr_ready = false;
+  h->fr_have_b = false;
   return OPF_OK;
 }
 

@@ -6,7 +6,11 @@ namespace condipm {
 
 int eval_impl(opf_handle* h, const double* x, const double* u, const double* lam, const double* y, bool derivs);
 int factor_async(opf_handle* h);
-int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s);
+// rhs (device, natural layout, one right-hand side; may be NULL): condensed in
+// the same pass as one extra column (adjoint route; kept in the handle for
+// kkt_solve_prepared)
+int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s,
+                   const double* rhs = nullptr);
 int factor_kred_async(opf_handle* h, double delta_w);
 // fold the dual regularisation delta_c of the inequality rows into K, H and Kred
 int recondense_dc(opf_handle* h, double delta_c);
@@ -14,6 +18,11 @@ int recondense_dc(opf_handle* h, double delta_c);
 int chol_solve_async(opf_handle* h, double* X, int k);
 // K_aug p = -r (external layout), with up to `refine` refinement corrections
 int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int refine);
+// K_aug p = -r for the right-hand side given to the last condense_async (from
+// its extra column when it is still valid, else by the plain recovery)
+int kkt_solve_prepared(opf_handle* h, double* step);
+// the buffers of the condensed right-hand side (allocated before any capture)
+int fr_reserve(opf_handle* h);
 int polish_solution(opf_handle* h, double tol, int max_iter);
 int ipm_reserve(opf_handle* h);
 int autotune_at_flat_start(opf_handle* h);

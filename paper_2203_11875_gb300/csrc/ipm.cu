@@ -218,6 +218,7 @@ int alloc_dev(Dev& d, opf_handle* h) {
   for (int i = 0; i < 11; ++i) { *slots[i] = p; p += std::max<size_t>(sizes[i], 1); }
   // the single-right-hand-side K_aug solves of the loop use this much workspace
   if (!workspace(h, 2 * nkkt + kkt_refine_scratch(P, 1) + 8)) return OPF_ERR_OOM;
+  TRYD(fr_reserve(h));
   return OPF_OK;
 }
 
@@ -295,7 +296,7 @@ int factor_with_correction(opf_handle* h, double& delta, double delta_last, int&
 // sequence resets its own counters and flags).  Where capture or instantiation
 // is refused, or while phases are being profiled, the launches are enqueued
 // one by one.  Returns the device status (one synchronisation).
-int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
+int condense_factor0(opf_handle* h, Dev& d, int* graph_iters, bool with_rhs = false) {
   if (h->ipm_fs) {
     // hybrid full-space mode: assemble and factor the augmented matrix
     TRYD(fs_set_sigma(h, d.sig_u, d.sig_x, d.sig_s));
@@ -306,16 +307,24 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
   }
   if (h->batch) {
     // a lockstep batch: one batched call serves every instance still iterating
+    h->fr_ready = false;
+    h->fr_have_b = false;
     const int rc = batch_join(h->batch, h->batch_idx, d.sig_u, d.sig_x, d.sig_s);
     h->have_factor = rc == OPF_OK;
     return rc;
   }
   const bool graph_ok = h->use_graphs && !h->cf_failed && !h->profiling && h->trsm_mode >= 0 && h->chol_tuned &&
                         h->route >= 0;
+  if (h->cf_exec && h->cf_rhs != with_rhs) {
+    // captured for the other kind of call: capture again
+    cudaGraphExecDestroy(h->cf_exec);
+    h->cf_exec = nullptr;
+  }
   if (graph_ok && !h->cf_exec) {
+    h->cf_rhs = with_rhs;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      int rc = condense_async(h, d.sig_u, d.sig_x, d.sig_s);
+      int rc = condense_async(h, d.sig_u, d.sig_x, d.sig_s, with_rhs ? d.rhs : nullptr);
       if (rc == OPF_OK) rc = factor_kred_async(h, 0.0);
       const cudaError_t e = cudaStreamEndCapture(h->s, &g);
       if (rc == OPF_OK && e == cudaSuccess && g &&
@@ -343,8 +352,11 @@ int condense_factor0(opf_handle* h, Dev& d, int* graph_iters) {
     h->finv_valid = false;
     h->delta_w = 0.0;
     h->delta_c = 0.0;
+    // the captured condensation carried the right-hand side's column
+    h->fr_have_b = with_rhs;
+    h->fr_ready = with_rhs && h->psi_valid && h->ldp > h->P.nu;
   } else {
-    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+    TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s, with_rhs ? d.rhs : nullptr));
     TRYD(factor_kred_async(h, 0.0));
   }
   const int rc = read_status(h, nullptr);
@@ -474,16 +486,17 @@ int restoration(opf_handle* h, Dev& d, const Bounds& bw, const Bounds& bs, const
     TRYD(h2d(h->s, d.sig_u, sw.data(), nu));
     TRYD(h2d(h->s, d.sig_x, sw.data() + nu, nx));
     TRYD(h2d(h->s, d.sig_s, st.data(), m));
+    TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
     int att = 1, gi = 0;
     {
-      const int rc0 = condense_factor0(h, d, &gi);
+      const int rc0 = condense_factor0(h, d, &gi, !h->ipm_fs);
       if (rc0 == OPF_OK) delta = 0.0;
       else if (rc0 == OPF_ERR_NOT_PD) { TRYD(factor_with_correction(h, delta, delta, att, true)); ++att; }
       else return rc0;
     }
     R.n_factor += att;
-    TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
-    TRYD(solve_step(h, d.rhs, d.step));
+    if (h->fr_have_b && !h->ipm_fs) TRYD(kkt_solve_prepared(h, d.step));
+    else TRYD(solve_step(h, d.rhs, d.step));
     TRYD(d2h(h->s, step.data(), d.step, nkkt));
     CKD(cudaStreamSynchronize(h->s));
     std::copy(step.begin(), step.begin() + nw, pw.begin());
@@ -684,16 +697,23 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
     }
     bw.sigma(w, zwl, zwu, sw);
     bs.sigma(s, zsl, zsu, ss);
+    // right-hand side of the step (it does not depend on the factorisation, so
+    // the condensation below carries it as one extra column)
+    for (int i = 0; i < nw; ++i) r[i] = grad[i] + bw.bgrad(w, i, mu);
+    for (int i = 0; i < m; ++i) r[nw + i] = y[i] + bs.bgrad(s, i, mu);
+    for (int i = 0; i < nx; ++i) r[nw + m + i] = g[i];
+    for (int i = 0; i < m; ++i) r[nw + m + nx + i] = hv[i] + s[i];
     // condense + factor with inertia correction
     t0 = clk::now();
     TRYD(h2d(h->s, d.sig_u, sw.data(), nu));
     TRYD(h2d(h->s, d.sig_x, sw.data() + nu, nx));
     TRYD(h2d(h->s, d.sig_s, ss.data(), m));
+    TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
     // condensation + first Cholesky attempt (one graph); inertia correction
     // only when Kred is not positive definite
     int att = 1;
     {
-      const int rc0 = condense_factor0(h, d, &R.graph_iters);
+      const int rc0 = condense_factor0(h, d, &R.graph_iters, !h->ipm_fs);
       R.ms_condense += ms_since(t0);
       t0 = clk::now();
       if (rc0 == OPF_OK) delta = 0.0;
@@ -702,18 +722,19 @@ int ipm_linred_body(opf_handle* h, const opf_ipm_options& o, opf_ipm_result& R) 
     }
     R.n_factor += att;
     R.ms_factor += ms_since(t0);
-    // right-hand side and step
-    for (int i = 0; i < nw; ++i) r[i] = grad[i] + bw.bgrad(w, i, mu);
-    for (int i = 0; i < m; ++i) r[nw + i] = y[i] + bs.bgrad(s, i, mu);
-    for (int i = 0; i < nx; ++i) r[nw + m + i] = g[i];
-    for (int i = 0; i < m; ++i) r[nw + m + nx + i] = hv[i] + s[i];
     Vec pw(nw), ps(m), plam(nx), py(m);
     double amax = 1.0, az = 1.0, a = 1.0;
     bool accepted = false, resto = false;
     for (int attempt = 0; attempt < 40 && !accepted; ++attempt) {
       t0 = clk::now();
-      TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
-      TRYD(solve_step(h, d.rhs, d.step));
+      if (h->fr_have_b && !h->ipm_fs) {
+        // the right-hand side condensed with the condensation (any refactor
+        // since changed delta_w only)
+        TRYD(kkt_solve_prepared(h, d.step));
+      } else {
+        TRYD(h2d(h->s, d.rhs, r.data(), nkkt));
+        TRYD(solve_step(h, d.rhs, d.step));
+      }
       TRYD(d2h(h->s, step.data(), d.step, nkkt));
       CKD(cudaStreamSynchronize(h->s));
       R.ms_solve += ms_since(t0);
@@ -1320,7 +1341,8 @@ extern "C" int opf_newton_step(opf_handle* h, const double* x, const double* u, 
   TRYD(h2d(h->s, d.sig_s, sig_s, P.m));
   TRYD(h2d(h->s, d.rhs, rhs, nkkt));
   TRYD(eval_impl(h, d.x, d.u, d.lam, d.y, true));
-  TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s));
+  // the condensed right-hand side rides along the condensation (one extra column)
+  TRYD(condense_async(h, d.sig_u, d.sig_x, d.sig_s, d.rhs));
   if (delta_c > 0.0) TRYD(recondense_dc(h, delta_c));
   TRYD(factor_kred_async(h, delta_w));
   int info = -1;
@@ -1331,7 +1353,7 @@ extern "C" int opf_newton_step(opf_handle* h, const double* x, const double* u, 
     return rc;
   }
   h->have_factor = true;
-  TRYD(kkt_solve_impl(h, d.rhs, d.step, 1, 0));
+  TRYD(kkt_solve_prepared(h, d.step));
   TRYD(d2h(h->s, step, d.step, nkkt));
   CKD(cudaStreamSynchronize(h->s));
   return OPF_OK;

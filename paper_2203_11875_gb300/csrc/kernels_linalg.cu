@@ -1119,6 +1119,22 @@ cudaError_t launch_fill(cudaStream_t s, long long n, double v, double* x) {
   note_launch();
   return cudaGetLastError();
 }
+// dst[i * ldd] = a * src[i * lds] + b * y[i * ldy]  (strided columns; y may be NULL)
+__global__ void k_column_axpby(int n, double a, const double* __restrict__ src, long long lds, double b,
+                               const double* __restrict__ y, long long ldy, double* __restrict__ dst, long long ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = a * src[(long long)i * lds];
+  dst[(long long)i * ldd] = y ? fma(b, y[(long long)i * ldy], v) : v;
+}
+cudaError_t launch_column_axpby(cudaStream_t s, int n, double a, const double* src, long long lds, double b,
+                                const double* y, long long ldy, double* dst, long long ldd) {
+  if (n <= 0) return cudaSuccess;
+  k_column_axpby<<<(n + 255) / 256, 256, 0, s>>>(n, a, src, lds, b, y, ldy, dst, ldd);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_identity(cudaStream_t s, int n, double* X, int ld) {
   k_set_identity<<<nblk((long long)n * n, 256), 256, 0, s>>>(n, X, ld);
   note_launch();

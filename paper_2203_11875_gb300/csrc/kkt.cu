@@ -153,6 +153,8 @@ KB kb_at(const Plan& P, double* base, int k) {
   return b;
 }
 
+int kkt_recover(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, double* scratch);
+
 int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, double* scratch) {
   const Plan& P = h->P;
   cudaStream_t s = h->s;
@@ -190,6 +192,25 @@ int kkt_core(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, doubl
   CKK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, E + (size_t)nu * k, k, 1, p.w, k, 1, k, -1.0,
                   1.0));
   ph_end(h);
+  return kkt_recover(h, k, b, p, bl_zero, scratch);
+}
+
+// The recovery half of kkt_core: p_u from the condensed right-hand side in p.w
+// (Cholesky solves), then p_x, p_s, p_y, p_lambda, with q = G_x^{-1} b_l in
+// D0's x rows and phi = G_x^{-T} e_x in E's x rows (the scratch layout of
+// kkt_core) when the condensation's products are used
+int kkt_recover(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, double* scratch) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nx = P.nx, nw = P.nw, m = P.m;
+  double* Bt = scratch;
+  double* E = Bt + (size_t)nw * k;
+  double* D0 = E + (size_t)nw * k;
+  double* U = D0 + (size_t)nw * k;
+  double* Byr = U + (size_t)m * k;
+  const bool dc = h->delta_c > 0.0;
+  const double* sig = dc ? h->sig_se : h->sig_s;
+  const double* by = dc ? Byr : b.y;
   ph_begin(h, OPF_PHASE_RECOVER);
   TRYK(chol_solve_async(h, p.w, k));
   double* px = p.w + (size_t)nu * k;
@@ -327,6 +348,41 @@ int kkt_solve_impl(opf_handle* h, const double* rhs, double* step, int k, int re
   CKK(launch_permute_rows(s, m, k, nullptr, p.s, k, 0, step + nw, int(N), 1, 1.0, 0));
   CKK(launch_permute_rows(s, nx, k, h->perm, p.l, k, 0, step + nw + m, int(N), 1, 1.0, 1));
   CKK(launch_permute_rows(s, m, k, nullptr, p.y, k, 0, step + nw + m + nx, int(N), 1, 1.0, 0));
+  return OPF_OK;
+}
+
+// K_aug p = -r for the right-hand side condensed with the last condensation:
+// r_hat, q and phi are read from the extra column of H and Zt, so only the
+// Cholesky solve and the recovery products remain (the plain path on the kept
+// copy of the right-hand side when the column is no longer valid)
+int kkt_solve_prepared(opf_handle* h, double* step) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nw = P.nw, m = P.m, nx = P.nx, nu = P.nu;
+  if (!h->fr_have_b) return OPF_ERR_INVALID_ARG;
+  const size_t N = kkt_rows(P);
+  double* ws = workspace(h, N + kkt_core_scratch(P) + 8);
+  if (!ws) return OPF_ERR_OOM;
+  const KB b = kb_at(P, h->fr_kb, 1);
+  const KB p = kb_at(P, ws, 1);
+  double* scratch = ws + N;
+  if (h->fr_ready && h->delta_c == 0.0 && h->psi_valid) {
+    const long long ld = h->ldp;
+    double* E = scratch + nw;
+    double* D0 = E + nw;
+    ph_begin(h, OPF_PHASE_RHS);
+    CKK(launch_column_axpby(s, nu, 1.0, h->H + nu, ld, 0.0, nullptr, 0, p.w, 1));                        // r_hat
+    CKK(launch_column_axpby(s, nx, 1.0, h->Zt + (size_t)nu * ld + nu, ld, 0.0, nullptr, 0, D0 + nu, 1));  // q
+    CKK(launch_column_axpby(s, nx, 1.0, h->H + (size_t)nu * ld + nu, ld, 0.0, nullptr, 0, E + nu, 1));     // phi
+    ph_end(h);
+    TRYK(kkt_recover(h, 1, b, p, false, scratch));
+  } else {
+    TRYK(kkt_core(h, 1, b, p, false, scratch));
+  }
+  CKK(launch_permute_rows(s, nw, 1, h->c2w, p.w, 1, 0, step, int(N), 1, 1.0, 1));
+  CKK(launch_permute_rows(s, m, 1, nullptr, p.s, 1, 0, step + nw, int(N), 1, 1.0, 0));
+  CKK(launch_permute_rows(s, nx, 1, h->perm, p.l, 1, 0, step + nw + m, int(N), 1, 1.0, 1));
+  CKK(launch_permute_rows(s, m, 1, nullptr, p.y, 1, 0, step + nw + m + nx, int(N), 1, 1.0, 0));
   return OPF_OK;
 }
 

@@ -125,6 +125,7 @@ struct opf_handle {
   // graph (inputs in the loop's fixed device buffers)
   cudaGraphExec_t cf_exec = nullptr;
   bool cf_failed = false;        // capture or instantiation was refused: plain launches
+  bool cf_rhs = false;           // the captured condensation carries the step's right-hand side
   bool use_graphs = true;
   // condensation route in use: the option, or with OPF_ROUTE_AUTO the faster one
   // on the first condensation (-1 until then), and the two timings
@@ -138,6 +139,12 @@ struct opf_handle {
   // call-order state
   bool have_eval = false, have_W = false, have_lu = false, have_condense = false, have_factor = false;
   bool psi_valid = false;         // Zt holds S_x and H's x rows G_x^{-T} H_x of the last condensation
+  // the right-hand side condensed with the last condensation (one extra column
+  // of S_x, H and Psi): its KB copy, b_t = b_w + A^T (Sigma_s b_y - b_s), and
+  // whether column nu of Zt / H holds q, e - K [0; q] -> (r_hat; phi) for it
+  double* fr_kb = nullptr;       // kkt_rows doubles (in allocs)
+  double* fr_bt = nullptr;       // nw (in allocs)
+  bool fr_have_b = false, fr_ready = false;
   double delta_w = 0.0;
   // dual regularisation of the inequality rows folded into K, H and Kred
   // (-delta_c I in the (p_y, p_y) block of K_aug); 0 after every condensation
