@@ -651,6 +651,8 @@ def main():
                                "column), K, H = K Z, Kred and the condensed right-hand side, one Cholesky attempt "
                                "(events) + reading the condensed right-hand side out (phase events)",
                       "route": "adjoint", "delta_w": delta,
+                      "rhs_width": {"N": h.rhs_width()[0],
+                                    "autotune_ms_at_nu_512_256_128": h.rhs_width()[1]},
                       "trsm_kernel": KERNEL_NAMES.get(trsm_kernel, str(trsm_kernel)),
                       "trsm_kernel_1rhs": KERNEL_NAMES.get(trsm_kernel1, str(trsm_kernel1)),
                       "autotune_ms": trsm_tune,

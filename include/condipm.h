@@ -100,6 +100,13 @@ typedef struct opf_options {
                              CTA's shared memory (65 and 66 fall back to 64 when
                              they do not fit); 0 = autotune together with rhs_block
                              (until then: 1)                                       */
+    int rhs_width;        /* N, the right-hand sides per pass of the condensation
+                             (Sec. 3.3, Fig. 2b: the batch width of the multi-RHS
+                             products): the adjoint route runs the S_x solve, H = K Z,
+                             the adjoint solve and the G_u^T product over column
+                             chunks of N; N >= nu is one pass; 0 = autotune on the
+                             first condensation among nu, 512, 256, 128 (the
+                             explicit route always uses one pass)                */
 } opf_options;
 
 typedef struct opf_handle opf_handle;
@@ -130,6 +137,11 @@ int opf_stats(const opf_handle* h, long long* nnz_lu, int* levels_fwd, int* leve
  * memory, 66 level-blocked on a thread-block cluster -- 65 and 66 for one
  * right-hand side only, others then use 64 --, -1 not chosen yet). */
 int opf_trsm_choice(const opf_handle* h, int* kernel, float* ms, int* kernel1);
+/* Right-hand-side width of the condensation in use (host outputs, may be
+ * NULL): *width = N (nu for one pass; 0 before the autotuner ran), ms[4] the
+ * autotuner's timings of the condensation's products at N = nu, 512, 256, 128
+ * (0 = not tried). */
+int opf_rhs_width(const opf_handle* h, int* width, float* ms);
 /* Dense Cholesky kernel in use (host outputs, may be NULL): *form as in
  * opf_options.chol_form (0 before the first factorisation), *nblocks its grid,
  * ms[OPF_CHOL_CANDIDATES] the autotuner's timings of {barrier form at 1/4, 1/2,

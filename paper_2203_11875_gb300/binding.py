@@ -42,7 +42,7 @@ class opf_network(C.Structure):
 
 class opf_options(C.Structure):
     _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong),
-                ("chol_form", C.c_int), ("rhs1_kernel", C.c_int)]
+                ("chol_form", C.c_int), ("rhs1_kernel", C.c_int), ("rhs_width", C.c_int)]
 
 
 class opf_ipm_options(C.Structure):
@@ -73,6 +73,7 @@ _SIGS = {
     "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float), _ip]),
     "opf_chol_choice": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_float)]),
     "opf_route_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
+    "opf_rhs_width": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_eval_functions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "opf_get_vector": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -214,7 +215,7 @@ class Handle:
     """One network on one GPU: wraps opf_create / opf_destroy and every call."""
 
     def __init__(self, net, route: int = OPF_ROUTE_ADJOINT, rhs_block: int = 0, spin_limit: int = 0,
-                 chol_form: int = 0, rhs1_kernel: int = 0):
+                 chol_form: int = 0, rhs1_kernel: int = 0, rhs_width: int = 0):
         lib = load_library()
         self._keep = []
 
@@ -230,7 +231,7 @@ class Handle:
         n = opf_network(net.nb, net.nl, net.ng, net.slack, d(net.Pd), d(net.Qd), d(net.Vmin), d(net.Vmax),
                         i(net.lf), i(net.lt), d(net.r), d(net.x), d(net.b), d(net.rate), i(net.gbus),
                         d(net.Pmin), d(net.Pmax), d(net.Qmin), d(net.Qmax), d(net.c2), d(net.c1))
-        o = opf_options(route, rhs_block, spin_limit, chol_form, rhs1_kernel)
+        o = opf_options(route, rhs_block, spin_limit, chol_form, rhs1_kernel, rhs_width)
         h = C.c_void_p()
         _check(lib.opf_create(C.byref(n), C.byref(o), C.byref(h)), "opf_create")
         self._keep = []
@@ -393,6 +394,13 @@ class Handle:
                                              C.byref(ld), inert), "opf_fullspace_stats")
         return dict(nblocks=nb.value, levels=lv.value, nnz_l=nl.value, flops=fl.value, logabsdet=ld.value,
                     inertia=tuple(inert))
+
+    def rhs_width(self):
+        """opf_rhs_width: (N in use, autotuner timings at nu, 512, 256, 128)."""
+        w = C.c_int(0)
+        ms = (C.c_float * 4)()
+        _check(self._lib.opf_rhs_width(self._h, C.byref(w), ms), "opf_rhs_width")
+        return w.value, list(ms)
 
     def fullspace_tuning(self):
         g = (C.c_int * 2)()

@@ -957,6 +957,96 @@ static int fr_prepare(opf_handle* h, const double* rhs) {
   return OPF_OK;
 }
 
+// columns per pass of the adjoint-route condensation
+static int chunk_width(const opf_handle* h) {
+  const int N = h->opt.rhs_width > 0 ? h->opt.rhs_width : h->rhs_width;
+  return N > 0 ? N : h->P.nu;
+}
+
+// A6-A7 of the adjoint route in column chunks of N (Fig. 2b's batch width):
+// per chunk the S_x solve, H = K Z, Psi = G_x^{-T} H_x and H_u - G_u^T Psi;
+// the condensed right-hand side's column rides with the last chunk.  S_x holds
+// -P G_u (and b_l) on entry; Kred is symmetrised at the end.
+static int condense_chunked(opf_handle* h, int N, bool fused) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nw = P.nw;
+  const long long ld = h->ldp;
+  double* Sx = h->Zt + (size_t)nu * ld;
+  double* Hx = h->H + (size_t)nu * ld;
+  for (int c0 = 0; c0 < nu; c0 += N) {
+    const bool last = c0 + N >= nu;
+    const int ncc = std::min(N, nu - c0) + (fused && last ? 1 : 0);
+    TRY(lu_solve_perm(h, 0, Sx + c0, ld, 1, ncc, true));
+    ph_begin(h, OPF_PHASE_SPMM);
+    CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt + c0, ld, 1, h->H + c0, ld, 1, ncc, 1.0, 0.0));
+    if (fused && last) CK(launch_column_axpby(s, nw, -1.0, h->H + nu, ld, 1.0, h->fr_bt, 1, h->H + nu, ld));
+    ph_end(h);
+    TRY(lu_solve_perm(h, 1, Hx + c0, ld, 1, ncc, true));
+    ph_begin(h, OPF_PHASE_KRED);
+    CK(launch_spmm(s, nu, h->GuT_rp, h->GuT_ci, h->Gval, h->GuT_map, Hx + c0, ld, 1, h->H + c0, ld, 1, ncc, -1.0,
+                   1.0));
+    ph_end(h);
+  }
+  ph_begin(h, OPF_PHASE_KRED);
+  CK(launch_symmetrize(s, nu, h->H, ld, 1, h->Kred));
+  ph_end(h);
+  return OPF_OK;
+}
+
+// On the first adjoint-route condensation: the products at N = nu, 512, 256,
+// 128 (those below nu), each from the same S_x right-hand side (kept in Zt's
+// spare rows: re-scattered before every candidate), timed with events; the
+// fastest is kept.  The last candidate's results stand.
+static int tune_width(opf_handle* h, bool fused) {
+  const Plan& P = h->P;
+  cudaStream_t s = h->s;
+  const int nu = P.nu, nx = P.nx;
+  const long long ld = h->ldp;
+  double* Sx = h->Zt + (size_t)nu * ld;
+  const int cand[4] = {nu, 512, 256, 128};
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  int pick = nu, rc = OPF_OK, ran = 0;
+  for (int i = 0; i < 4 && rc == OPF_OK; ++i) {
+    h->width_ms[i] = 0.f;
+    if (i > 0 && cand[i] >= nu) continue;
+    if (ran > 0) {
+      // the right-hand side again (the previous candidate solved S_x in place)
+      if (cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s) != cudaSuccess) rc = OPF_ERR_CUDA;
+      if (rc == OPF_OK && launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1) !=
+                              cudaSuccess)
+        rc = OPF_ERR_CUDA;
+      if (rc == OPF_OK && fused &&
+          launch_column_axpby(s, nx, 1.0, kb_at(P, h->fr_kb, 1).l, 1, 0.0, nullptr, 0, Sx + nu, ld) != cudaSuccess)
+        rc = OPF_ERR_CUDA;
+    }
+    if (rc == OPF_OK && cudaEventRecord(a, s) != cudaSuccess) rc = OPF_ERR_CUDA;
+    if (rc == OPF_OK) {
+      if (cand[i] >= nu) {
+        rc = lu_solve_perm(h, 0, Sx, ld, 1, fused ? nu + 1 : nu, true);
+        if (rc == OPF_OK) rc = reduce_async(h, fused ? nu + 1 : nu, fused ? h->fr_bt : nullptr);
+      } else {
+        rc = condense_chunked(h, cand[i], fused);
+      }
+    }
+    if (rc == OPF_OK && cudaEventRecord(b, s) != cudaSuccess) rc = OPF_ERR_CUDA;
+    if (rc == OPF_OK && cudaEventSynchronize(b) != cudaSuccess) rc = OPF_ERR_CUDA;
+    float ms = 0.f;
+    if (rc == OPF_OK) cudaEventElapsedTime(&ms, a, b);
+    h->width_ms[i] = ms;
+    ++ran;
+    if (rc == OPF_OK && ms < best) { best = ms; pick = cand[i]; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  TRY(rc);
+  h->rhs_width = pick;
+  return OPF_OK;
+}
+
 int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, const double* sig_s,
                    const double* rhs) {
   const Plan& P = h->P;
@@ -991,9 +1081,15 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   // identity rows of Zt are zero in this column, so H gets K [0; q])
   const int nc = fused ? nu + 1 : nu;
   if (fused) CK(launch_column_axpby(s, nx, 1.0, kb_at(P, h->fr_kb, 1).l, 1, 0.0, nullptr, 0, Sx + nu, ld));
-  TRY(lu_solve_perm(h, 0, Sx, ld, 1, nc, true));
   h->psi_last_adjoint = false;
-  TRY(reduce_async(h, nc, fused ? h->fr_bt : nullptr));
+  if (h->route == OPF_ROUTE_ADJOINT && h->rhs_width == 0 && h->opt.rhs_width == 0 && !h->profiling) {
+    TRY(tune_width(h, fused));
+  } else if (h->route == OPF_ROUTE_ADJOINT && chunk_width(h) < nu) {
+    TRY(condense_chunked(h, chunk_width(h), fused));
+  } else {
+    TRY(lu_solve_perm(h, 0, Sx, ld, 1, nc, true));
+    TRY(reduce_async(h, nc, fused ? h->fr_bt : nullptr));
+  }
   h->have_condense = true;
   h->have_factor = false;
   h->sens_ready = false;
@@ -1173,7 +1269,8 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
   opf_handle* h = new (std::nothrow) opf_handle();
   if (!h) return OPF_ERR_OOM;
   if (opt) h->opt = *opt;
-  if (h->opt.route != OPF_ROUTE_ADJOINT && h->opt.route != OPF_ROUTE_EXPLICIT && h->opt.route != OPF_ROUTE_AUTO) {
+  if ((h->opt.route != OPF_ROUTE_ADJOINT && h->opt.route != OPF_ROUTE_EXPLICIT && h->opt.route != OPF_ROUTE_AUTO) ||
+      h->opt.rhs_width < 0) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
@@ -1210,6 +1307,13 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
     return rc;
   }
   *out = h;
+  return OPF_OK;
+}
+
+int opf_rhs_width(const opf_handle* h, int* width, float* ms) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (width) *width = h->opt.rhs_width > 0 ? std::min(h->opt.rhs_width, h->P.nu) : std::min(h->rhs_width, h->P.nu);
+  if (ms) for (int i = 0; i < 4; ++i) ms[i] = h->width_ms[i];
   return OPF_OK;
 }
 

@@ -131,6 +131,10 @@ struct opf_handle {
   // on the first condensation (-1 until then), and the two timings
   int route = -1;
   float route_ms[2] = {0.f, 0.f};
+  // right-hand sides per pass of the condensation (adjoint route): the option,
+  // or the autotuner's pick on the first condensation (0 until then)
+  int rhs_width = 0;
+  float width_ms[4] = {};
   bool psi_last_adjoint = false;   // the last condensation ended with the adjoint route's Psi
   // set while a lockstep batch solve runs this handle's loop: its condensation
   // and first Cholesky attempt go through the batch's rendezvous

@@ -113,3 +113,45 @@ def test_condensed_rhs_needs_the_condensation(pkg):
     step = torch.zeros(h.n_kkt, dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.OPFError):
         h.kkt_solve_condensed(step)
+
+
+@pytest.mark.parametrize("width", [128, 256, 512])
+def test_chunked_condensation_matches_one_pass(pkg, width):
+    """The adjoint-route condensation in column chunks of N (Sec. 3.3's batch
+    width) gives the one-pass Kred and the same step (grid2000, nu = 399: the
+    last chunk is ragged, and carries the right-hand side's column)."""
+    net = gridgen.grid2000()
+    p = point(net, 23)
+    lay = p["lay"]
+    out = []
+    for w in (0, width):
+        h = pkg.Handle(net, rhs_width=w if w else 10 ** 6)
+        h.eval_derivatives(T(p["w"][lay.nu:]), T(p["w"][:lay.nu]), T(p["lam"]), T(p["y"]))
+        K = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
+        h.condense_rhs(T(p["sw"][:lay.nu]), T(p["sw"][lay.nu:]), T(p["ss"]), T(p["r"]), K)
+        assert h.kkt_factor(p["dw"]) == -1
+        step = torch.zeros(len(p["r"]), dtype=torch.float64, device="cuda")
+        h.kkt_solve_condensed(step)
+        out.append((N(K), N(step), h.rhs_width()[0]))
+    assert out[0][2] == lay.nu and out[1][2] == min(width, lay.nu)
+    assert rel_err(out[1][0], out[0][0]) <= 1e-12
+    assert rel_err(out[1][1], ref_step(p, p["dw"])) <= 1e-9
+
+
+def test_width_autotune_on_grid10k(pkg):
+    """rhs_width = 0 times the products at N = nu, 512, 256, 128 on the first
+    condensation and keeps the fastest; the Kred is right whatever it picks."""
+    d = dict(np.load(GOLDEN))
+    net = gridgen.grid10k()
+    lay = model.Layout(net)
+    _, G, A = model.jacobians(lay, d["w"])
+    W = model.lagrangian_hessian(lay, d["w"], d["lam"], d["y"])
+    h = pkg.Handle(net)
+    h.eval_derivatives(T(d["w"][lay.nu:]), T(d["w"][:lay.nu]), T(d["lam"]), T(d["y"]))
+    sw, ss = d["sig_w"], d["sig_s"]
+    K = torch.zeros(lay.nu * lay.nu, dtype=torch.float64, device="cuda")
+    h.condense_rhs(T(sw[:lay.nu]), T(sw[lay.nu:]), T(ss), T(d["r"]), K)
+    width, ms = h.rhs_width()
+    assert width in (lay.nu, 512, 256, 128) and all(t > 0 for t in ms)
+    Ko = kkt.kred_definition(G, A, W, sw, ss, lay.nu)
+    assert rel_err(N(K).reshape(lay.nu, lay.nu), 0.5 * (Ko + Ko.T)) <= 1e-9
