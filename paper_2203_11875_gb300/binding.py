@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcondipm.so")
 
 OPF_OK = 0
+OPF_ERR_INVALID_ARG = -1
+OPF_ERR_CUDA = -2
 OPF_ERR_NOT_PD = -3
 OPF_ERR_SINGULAR = -4
 OPF_ERR_PF_FAILED = -5
