@@ -131,6 +131,29 @@ __global__ void k_dense_rows(int n, int ncol, int k, const double* __restrict__ 
   }
 }
 
+// the same for one right-hand side (the interior-point step): eight loads of
+// the row in flight per lane, each with its own accumulator
+__global__ void __launch_bounds__(256) k_dense_rows1(int n, int ncol, const double* __restrict__ M, long long ld,
+                                                     const double* __restrict__ V, const double* __restrict__ base,
+                                                     double alpha, double* __restrict__ out) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double acc[8] = {};
+  const double* Mi = M + (long long)i * ld;
+  int cc = lane;
+  for (; cc + 224 < ncol; cc += 256) {
+    double m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = __ldcs(&Mi[cc + 32 * u]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = fma(m[u], __ldg(&V[cc + 32 * u]), acc[u]);
+  }
+  for (; cc < ncol; cc += 32) acc[0] = fma(__ldcs(&Mi[cc]), __ldg(&V[cc]), acc[0]);
+  double a = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) out[i] = (base ? base[i] : 0.0) + alpha * a;
+}
+
 int launched() {
   note_launch();
   return cudaGetLastError() == cudaSuccess ? OPF_OK : OPF_ERR_CUDA;
@@ -219,9 +242,13 @@ int kkt_recover(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, do
     // H's x rows, H = K Z); with phi = G_x^{-T} e_x (already in E):
     //   p_x = q + S_x p_u,   p_l = phi - Psi p_u       (two products, no solves)
     const long long ld = h->ldp;
-    const int nb = (nx * 32 + 127) / 128;
-    k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->Zt + (size_t)nu * ld, ld, p.w,
-                                    bl_zero ? nullptr : D0 + (size_t)nu * k, 1.0, px);
+    const int nb = (nx * 32 + 127) / 128, nb1 = (nx * 32 + 255) / 256;
+    if (k == 1)
+      k_dense_rows1<<<nb1, 256, 0, s>>>(nx, nu, h->Zt + (size_t)nu * ld, ld, p.w, bl_zero ? nullptr : D0 + nu, 1.0,
+                                         px);
+    else
+      k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->Zt + (size_t)nu * ld, ld, p.w,
+                                      bl_zero ? nullptr : D0 + (size_t)nu * k, 1.0, px);
     TRYK(launched());
     CKK(launch_spmm(s, m, h->A_rp, h->A_ci_c, h->Aval, nullptr, p.w, k, 1, p.s, k, 1, k, -1.0, 0.0));
     CKK(launch_axpby(s, (long long)m * k, 1.0, by, 1.0, p.s, p.s));
@@ -231,7 +258,10 @@ int kkt_recover(opf_handle* h, int k, const KB& b, const KB& p, bool bl_zero, do
       k_rows_scale_inplace<<<nblk((long long)m * k, 256), 256, 0, s>>>(m, k, h->ps_sc, p.s);
       TRYK(launched());
     }
-    k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->H + (size_t)nu * ld, ld, p.w, E + (size_t)nu * k, -1.0, p.l);
+    if (k == 1)
+      k_dense_rows1<<<nb1, 256, 0, s>>>(nx, nu, h->H + (size_t)nu * ld, ld, p.w, E + nu, -1.0, p.l);
+    else
+      k_dense_rows<<<nb, 128, 0, s>>>(nx, nu, k, h->H + (size_t)nu * ld, ld, p.w, E + (size_t)nu * k, -1.0, p.l);
     TRYK(launched());
     ph_end(h);
     return OPF_OK;
