@@ -568,6 +568,7 @@ def main():
     torch.cuda.synchronize()
     trsm_kernel, trsm_tune, trsm_kernel1 = h.trsm_choice()
     chol_form, chol_grid, chol_tune = h.chol_choice()
+    cs_cluster, cs_tune = h.chol_solve_choice()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     h.profile(True)
@@ -657,7 +658,9 @@ def main():
                       "trsm_kernel_1rhs": KERNEL_NAMES.get(trsm_kernel1, str(trsm_kernel1)),
                       "autotune_ms": trsm_tune,
                       "cholesky": {"form": {1: "barrier", 2: "dataflow"}.get(chol_form, str(chol_form)),
-                                   "ctas": chol_grid, "autotune_ms": chol_tune}},
+                                   "ctas": chol_grid, "autotune_ms": chol_tune,
+                                   "solve_cluster": cs_cluster,
+                                   "solve_cluster_autotune_ms": {str(c): v for c, v in cs_tune.items()}}},
            "clocks": clocks, "gpu_launches": int(n_launch),
            "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                    "includes": "opf_newton_step from pinned host buffers: H2D of x, u, lambda, y, Sigma, r + "

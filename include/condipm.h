@@ -151,6 +151,12 @@ int opf_rhs_width(const opf_handle* h, int* width, float* ms);
  * a candidate with more CTAs than fit at once is not tried). */
 #define OPF_CHOL_CANDIDATES 11
 int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms);
+/* Cluster size of the dense solve with L and L^T for one to eight right-hand
+ * sides (host outputs, may be NULL): *cluster the CTAs of one thread-block
+ * cluster per right-hand side, ms[3] the timings of 4, 8 and 16 CTAs taken on
+ * the first one-vector solve (0 = not timed yet; the size chosen from nu is in
+ * use until then). */
+int opf_chol_solve_choice(const opf_handle* h, int* cluster, float* ms);
 /* Condensation route in use (host outputs, may be NULL): *route as in
  * opf_options.route (-1: OPF_ROUTE_AUTO before its first opf_condense), ms[2]
  * the AUTO timings of {adjoint, explicit} (0 = not timed). */

@@ -74,6 +74,7 @@ _SIGS = {
     "opf_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float), _ip]),
     "opf_chol_choice": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_float)]),
+    "opf_chol_solve_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_route_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_rhs_width": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -283,6 +284,14 @@ class Handle:
                  "dataflow_half_sm", "dataflow_1_per_sm", "dataflow_2_per_sm", "dataflow_1_per_sm_wide_panel",
                  "dataflow_2_per_sm_wide_panel", "dataflow_4_per_sm", "dataflow_4_per_sm_wide_panel")
         return f.value, nb.value, dict(zip(names, ms))
+
+    def chol_solve_choice(self):
+        """(cluster size of the few-right-hand-side dense solve; {4, 8, 16: ms}
+        of its timing on the first one-vector solve, 0 = not timed)."""
+        c = C.c_int()
+        ms = (C.c_float * 3)()
+        _check(self._lib.opf_chol_solve_choice(self._h, C.byref(c), ms), "opf_chol_solve_choice")
+        return c.value, dict(zip((4, 8, 16), ms))
 
     def route_choice(self):
         """(route in use: 0 adjoint, 1 explicit, -1 auto before its first

@@ -429,6 +429,7 @@ int upload_all(opf_handle* h) {
   TRY(alloc(h, &h->chol_cnt, 2 * (size_t)((P.nu + 31) / 32 + 1)));
   TRY(alloc(h, &h->Finv, (size_t)std::max(1, (P.nu + 31) / 32) * 32 * 32));
   h->chol_solve_cl = (P.nu + 31) / 32 > 8 ? 16 : 8;
+  TRY(alloc(h, &h->cs_tmp, (size_t)P.nu));
   CK(launch_set_identity(0, P.nu, h->Zt, h->ldp));
   // launch shapes
   int maxlen = 1;
@@ -1235,6 +1236,34 @@ int chol_solve_async(opf_handle* h, double* X, int k) {
       CK(launch_tile_inv(h->s, nu, h->F, h->Fdinv, h->Finv));
       h->finv_valid = true;
     }
+    if (k == 1 && !h->cs_tuned && !h->profiling && nu > 8 * 32) {
+      // the cluster size: a tile step costs one cluster barrier, a larger
+      // cluster shares the update out wider; time 4, 8, 16 CTAs on this
+      // right-hand side (restored before each) and keep the fastest
+      cudaEvent_t a = nullptr, b = nullptr;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      CK(cudaMemcpyAsync(h->cs_tmp, X, sizeof(double) * nu, cudaMemcpyDeviceToDevice, h->s));
+      const int cand[3] = {4, 8, 16};
+      float best = 1e30f;
+      int pick = h->chol_solve_cl;
+      for (int c = 0; c < 3; ++c) {
+        CK(cudaMemcpyAsync(X, h->cs_tmp, sizeof(double) * nu, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaEventRecord(a, h->s));
+        CK(launch_chol_solve_cl(h->s, nu, h->F, h->Finv, X, 1, cand[c]));
+        CK(cudaEventRecord(b, h->s));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        h->cs_ms[c] = ms;
+        if (ms < best) { best = ms; pick = cand[c]; }
+      }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      CK(cudaMemcpyAsync(X, h->cs_tmp, sizeof(double) * nu, cudaMemcpyDeviceToDevice, h->s));
+      h->chol_solve_cl = pick;
+      h->cs_tuned = true;
+    }
     CK(launch_chol_solve_cl(h->s, nu, h->F, h->Finv, X, k, h->chol_solve_cl));
     return OPF_OK;
   }
@@ -1329,6 +1358,13 @@ int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms) {
   if (form) *form = h->chol_tuned ? 1 + h->chol_df : 0;
   if (nblocks) *nblocks = h->chol_blocks;
   if (ms) for (int c = 0; c < OPF_CHOL_CANDIDATES; ++c) ms[c] = h->chol_ms[c];
+  return OPF_OK;
+}
+
+int opf_chol_solve_choice(const opf_handle* h, int* cluster, float* ms) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (cluster) *cluster = h->chol_solve_cl;
+  if (ms) for (int c = 0; c < 3; ++c) ms[c] = h->cs_ms[c];
   return OPF_OK;
 }
 

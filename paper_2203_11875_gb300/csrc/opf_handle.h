@@ -119,6 +119,9 @@ struct opf_handle {
   double* Finv = nullptr;        // inverses of the factor's 32 x 32 diagonal tiles (few-RHS solves)
   bool finv_valid = false;       // Finv belongs to the current factor
   int chol_solve_cl = 0;         // cluster size of the few-RHS solve (0: one CTA per column)
+  bool cs_tuned = false;         // ... timed at 4, 8, 16 CTAs on the first one-vector solve
+  float cs_ms[3] = {};
+  double* cs_tmp = nullptr;      // its copy of the right-hand side (nu; in allocs)
   float chol_ms[OPF_CHOL_CANDIDATES] = {};   // tuner timings
   unsigned* chol_cnt = nullptr;  // its step counters (2 x tile columns)
   // condensation + first Cholesky attempt of the interior-point loop as a CUDA

@@ -105,6 +105,12 @@ def test_condensed_rhs_step_grid10k(pkg):
     Wd = W + sp.diags(np.r_[np.full(lay.nu, delta), np.zeros(lay.nx)])
     ref = np.concatenate(kkt.full_space_step(G, A, Wd, sw, ss, d["r"]))
     assert rel_err(N(step), ref) <= 1e-9
+    # the first one-vector solve timed the solve's cluster at 4, 8, 16 CTAs on
+    # a copy of its right-hand side; the second runs on the size it kept
+    cl, ms = h.chol_solve_choice()
+    assert cl in (4, 8, 16) and all(t > 0 for t in ms.values())
+    h.kkt_solve_condensed(step)
+    assert rel_err(N(step), ref) <= 1e-9
 
 
 def test_condensed_rhs_needs_the_condensation(pkg):
