@@ -345,6 +345,14 @@ def path_flops(h):
     _, _, _, ci = h.get_csr_pattern(0)        # G = [G_u G_x], columns [u; x]
     nnz_gu = int((ci < h.nu).sum())
     trsm = 4 * 2 * S * h.nu + 2 * h.nx * h.nu
+    # the forward sweep over P G_u on the level-blocked kernels solves, in each
+    # full 32-column block, only the rows of its reach list: that sweep's share
+    # of the count above, scaled by the listed fraction of those blocks' work
+    nblk, work = h.forward_reach()
+    kern = h.trsm_choice()[0]
+    if nblk > 0 and kern in (64, 128) and work["all"] > 0:
+        sweep = 2 * S * h.nu + h.nx * h.nu / 2
+        trsm -= sweep * (32 * nblk / h.nu) * (1.0 - work["listed"] / work["all"])
     return {"trsm": trsm, "refactor": 2 * st["lu_flops"], "spmm": 2 * st["nnz_k"] * h.nu,
             "kred": 2 * nnz_gu * h.nu, "chol": h.nu ** 3 / 3.0, "S": S}
 

@@ -107,6 +107,13 @@ typedef struct opf_options {
                              chunks of N; N >= nu is one pass; 0 = autotune on the
                              first condensation among nu, 512, 256, 128 (the
                              explicit route always uses one pass)                */
+    int dense_forward;    /* the forward sweep L Y = P G_u of the condensation (Sec.
+                             3.3): 0 = the level-blocked kernels solve, in each
+                             full 32-column block of G_u (also in column chunks),
+                             only the rows where Y can be nonzero (the etree paths
+                             from the block's rows of G_u to the root, found at
+                             opf_create; every other row of Y is exactly zero) and
+                             pass by the levels without any; 1 = every row     */
 } opf_options;
 
 typedef struct opf_handle opf_handle;
@@ -157,6 +164,12 @@ int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms);
  * the first one-vector solve (0 = not timed yet; the size chosen from nu is in
  * use until then). */
 int opf_chol_solve_choice(const opf_handle* h, int* cluster, float* ms);
+/* The condensation's forward sweep over P G_u (host outputs, may be NULL):
+ * *nblocks the 32-column blocks with a reach list (nu / 32; 0 when
+ * opf_options.dense_forward is set), work[2] the multiply-adds per sweep of the
+ * listed rows and of all rows of those blocks (external L entries plus the
+ * diagonal-block row). */
+int opf_forward_reach(const opf_handle* h, int* nblocks, double* work);
 /* Condensation route in use (host outputs, may be NULL): *route as in
  * opf_options.route (-1: OPF_ROUTE_AUTO before its first opf_condense), ms[2]
  * the AUTO timings of {adjoint, explicit} (0 = not timed). */

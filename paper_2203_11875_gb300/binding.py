@@ -44,7 +44,8 @@ class opf_network(C.Structure):
 
 class opf_options(C.Structure):
     _fields_ = [("route", C.c_int), ("rhs_block", C.c_int), ("spin_limit", C.c_longlong),
-                ("chol_form", C.c_int), ("rhs1_kernel", C.c_int), ("rhs_width", C.c_int)]
+                ("chol_form", C.c_int), ("rhs1_kernel", C.c_int), ("rhs_width", C.c_int),
+                ("dense_forward", C.c_int)]
 
 
 class opf_ipm_options(C.Structure):
@@ -75,6 +76,7 @@ _SIGS = {
     "opf_trsm_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float), _ip]),
     "opf_chol_choice": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_float)]),
     "opf_chol_solve_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
+    "opf_forward_reach": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_double)]),
     "opf_route_choice": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_rhs_width": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_float)]),
     "opf_eval_derivatives": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -218,7 +220,7 @@ class Handle:
     """One network on one GPU: wraps opf_create / opf_destroy and every call."""
 
     def __init__(self, net, route: int = OPF_ROUTE_ADJOINT, rhs_block: int = 0, spin_limit: int = 0,
-                 chol_form: int = 0, rhs1_kernel: int = 0, rhs_width: int = 0):
+                 chol_form: int = 0, rhs1_kernel: int = 0, rhs_width: int = 0, dense_forward: int = 0):
         lib = load_library()
         self._keep = []
 
@@ -234,7 +236,7 @@ class Handle:
         n = opf_network(net.nb, net.nl, net.ng, net.slack, d(net.Pd), d(net.Qd), d(net.Vmin), d(net.Vmax),
                         i(net.lf), i(net.lt), d(net.r), d(net.x), d(net.b), d(net.rate), i(net.gbus),
                         d(net.Pmin), d(net.Pmax), d(net.Qmin), d(net.Qmax), d(net.c2), d(net.c1))
-        o = opf_options(route, rhs_block, spin_limit, chol_form, rhs1_kernel, rhs_width)
+        o = opf_options(route, rhs_block, spin_limit, chol_form, rhs1_kernel, rhs_width, dense_forward)
         h = C.c_void_p()
         _check(lib.opf_create(C.byref(n), C.byref(o), C.byref(h)), "opf_create")
         self._keep = []
@@ -292,6 +294,14 @@ class Handle:
         ms = (C.c_float * 3)()
         _check(self._lib.opf_chol_solve_choice(self._h, C.byref(c), ms), "opf_chol_solve_choice")
         return c.value, dict(zip((4, 8, 16), ms))
+
+    def forward_reach(self):
+        """(32-column blocks of the forward sweep with a reach list; {"listed":
+        multiply-adds of their listed rows, "all": of all their rows})."""
+        nb = C.c_int()
+        wk = (C.c_double * 2)()
+        _check(self._lib.opf_forward_reach(self._h, C.byref(nb), wk), "opf_forward_reach")
+        return nb.value, {"listed": wk[0], "all": wk[1]}
 
     def route_choice(self):
         """(route in use: 0 adjoint, 1 explicit, -1 auto before its first

@@ -320,6 +320,17 @@ int upload_all(opf_handle* h) {
     if (k == 0) { TRY(alloc(h, &h->D_L, nd)); TRY(alloc(h, &h->D_Ut, nd)); }
     else { TRY(alloc(h, &h->D_U, nd)); TRY(alloc(h, &h->D_Lt, nd)); }
   }
+  // the forward sweep's reach lists per full 32-column block of P G_u
+  if (h->opt.dense_forward == 0 && P.nu >= 32) {
+    std::vector<int> rptr, rq;
+    build_forward_reach(P, P.csL, rptr, rq, h->rch_work);
+    int *a, *b;
+    TRY(upload(h, &a, rptr));
+    TRY(upload(h, &b, rq.empty() ? std::vector<int>(1, 0) : rq));
+    h->bkL.rch_ptr = a;
+    h->bkL.rch_q = b;
+    h->bkL.rch_nblk = P.nu / 32;
+  }
   h->lu1s_ok = sizeof(double) * ((size_t)P.nx + (size_t)h->lu1s_ymax) <= trsm_lu1s_max_smem();
   // the cluster form of the one-right-hand-side solve, for 4, 8 and 16 CTAs
   for (int c = 0; c < 3; ++c) {
@@ -628,8 +639,12 @@ int factor_async(opf_handle* h) {
 }
 
 // X (perm space, n x ncols, element (i, c) at X[i*xr + c*xc]) <- (LU)^{-1} X or (LU)^{-T} X
-int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols, bool timed) {
+int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols, bool timed,
+                  int gu_c0) {
   const Plan& P = h->P;
+  // X holds P G_u's columns from gu_c0 on: the level-blocked forward sweep may
+  // use the reach lists (its 32-column blocks must line up with G_u's)
+  const int rch = (trans == 0 && gu_c0 >= 0 && gu_c0 % 32 == 0 && xc == 1) ? gu_c0 / 32 : -1;
   cudaStream_t s = h->s;
   const double* lov = trans ? h->Ut_val : h->Lo_val;
   const double* upv = trans ? h->Lt_val : h->Up_val;
@@ -694,11 +709,11 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
     if (h->blk_cl > 0) {
       // both triangles in one launch of one cluster per column block
       CK(launch_trsm_blkc(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, h->bkU, h->Up_ci, upv,
-                          trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, h->blk_cl));
+                          trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, h->blk_cl, rch));
     } else {
       // one launch per triangle (measured faster than both in one launch)
       CK(launch_trsm_blk(s, h->bkL, h->Lo_ci, lov, trans ? h->D_Ut : h->D_L, X, Y, xr, ncols, ksplit, h->cs_bar,
-                         h->st, h->spin_limit, minb));
+                         h->st, h->spin_limit, minb, rch));
       if (timed) { ph_end(h); ph_begin(h, OPF_PHASE_TRSM); }
       CK(launch_trsm_blk(s, h->bkU, h->Up_ci, upv, trans ? h->D_Lt : h->D_U, X, Y, xr, ncols, ksplit, h->cs_bar,
                          h->st, h->spin_limit, minb));
@@ -737,6 +752,15 @@ int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long x
   return OPF_OK;
 }
 
+// S_x <- -P G_u, the rest of its nx x ld block zero (the forward sweep's
+// reach lists rely on those exact zeros)
+static int scatter_gu(opf_handle* h, double* Sx, long long ld) {
+  const Plan& P = h->P;
+  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)P.nx * ld, h->s));
+  CK(launch_scatter_rows(h->s, P.nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
+  return OPF_OK;
+}
+
 // Pick the fastest multi-RHS solve kernel for this network on the device at hand:
 // each candidate solves the real right-hand side (in the H buffer, which the
 // condensation overwrites afterwards) twice, the second run timed with events.
@@ -755,7 +779,7 @@ int autotune_trsm(opf_handle* h, const double* Sx, long long ld) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaMemcpyAsync(trial, Sx, sizeof(double) * (size_t)nx * ld, cudaMemcpyDeviceToDevice, h->s));
       CK(cudaEventRecord(a, h->s));
-      TRY(lu_solve_perm(h, 0, trial, ld, 1, ncols));
+      TRY(lu_solve_perm(h, 0, trial, ld, 1, ncols, false, 0));
       CK(cudaEventRecord(b, h->s));
       CK(cudaEventSynchronize(b));
       CK(cudaEventElapsedTime(&ms, a, b));
@@ -978,7 +1002,7 @@ static int condense_chunked(opf_handle* h, int N, bool fused) {
   for (int c0 = 0; c0 < nu; c0 += N) {
     const bool last = c0 + N >= nu;
     const int ncc = std::min(N, nu - c0) + (fused && last ? 1 : 0);
-    TRY(lu_solve_perm(h, 0, Sx + c0, ld, 1, ncc, true));
+    TRY(lu_solve_perm(h, 0, Sx + c0, ld, 1, ncc, true, c0));
     ph_begin(h, OPF_PHASE_SPMM);
     CK(launch_spmm(s, nw, h->K_rp, h->K_ci, h->Kval, nullptr, h->Zt + c0, ld, 1, h->H + c0, ld, 1, ncc, 1.0, 0.0));
     if (fused && last) CK(launch_column_axpby(s, nw, -1.0, h->H + nu, ld, 1.0, h->fr_bt, 1, h->H + nu, ld));
@@ -1016,10 +1040,7 @@ static int tune_width(opf_handle* h, bool fused) {
     if (i > 0 && cand[i] >= nu) continue;
     if (ran > 0) {
       // the right-hand side again (the previous candidate solved S_x in place)
-      if (cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s) != cudaSuccess) rc = OPF_ERR_CUDA;
-      if (rc == OPF_OK && launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1) !=
-                              cudaSuccess)
-        rc = OPF_ERR_CUDA;
+      rc = scatter_gu(h, Sx, ld);
       if (rc == OPF_OK && fused &&
           launch_column_axpby(s, nx, 1.0, kb_at(P, h->fr_kb, 1).l, 1, 0.0, nullptr, 0, Sx + nu, ld) != cudaSuccess)
         rc = OPF_ERR_CUDA;
@@ -1027,7 +1048,7 @@ static int tune_width(opf_handle* h, bool fused) {
     if (rc == OPF_OK && cudaEventRecord(a, s) != cudaSuccess) rc = OPF_ERR_CUDA;
     if (rc == OPF_OK) {
       if (cand[i] >= nu) {
-        rc = lu_solve_perm(h, 0, Sx, ld, 1, fused ? nu + 1 : nu, true);
+        rc = lu_solve_perm(h, 0, Sx, ld, 1, fused ? nu + 1 : nu, true, 0);
         if (rc == OPF_OK) rc = reduce_async(h, fused ? nu + 1 : nu, fused ? h->fr_bt : nullptr);
       } else {
         rc = condense_chunked(h, cand[i], fused);
@@ -1075,8 +1096,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   // hold consecutive right-hand-side columns
   const long long ld = h->ldp;
   double* Sx = h->Zt + (size_t)nu * ld;
-  CK(cudaMemsetAsync(Sx, 0, sizeof(double) * (size_t)nx * ld, s));
-  CK(launch_scatter_rows(s, nx, h->PGu_rp, h->PGu_ci, h->PGu_map, h->Gval, -1.0, Sx, ld, 1));
+  TRY(scatter_gu(h, Sx, ld));
   if (h->trsm_mode < 0) TRY(autotune_trsm(h, Sx, ld));
   // the right-hand side's column of the solve: b_l (then q = G_x^{-1} b_l; the
   // identity rows of Zt are zero in this column, so H gets K [0; q])
@@ -1088,7 +1108,7 @@ int condense_async(opf_handle* h, const double* sig_u, const double* sig_x, cons
   } else if (h->route == OPF_ROUTE_ADJOINT && chunk_width(h) < nu) {
     TRY(condense_chunked(h, chunk_width(h), fused));
   } else {
-    TRY(lu_solve_perm(h, 0, Sx, ld, 1, nc, true));
+    TRY(lu_solve_perm(h, 0, Sx, ld, 1, nc, true, 0));
     TRY(reduce_async(h, nc, fused ? h->fr_bt : nullptr));
   }
   h->have_condense = true;
@@ -1299,7 +1319,7 @@ int opf_create(const opf_network* net, const opf_options* opt, opf_handle** out)
   if (!h) return OPF_ERR_OOM;
   if (opt) h->opt = *opt;
   if ((h->opt.route != OPF_ROUTE_ADJOINT && h->opt.route != OPF_ROUTE_EXPLICIT && h->opt.route != OPF_ROUTE_AUTO) ||
-      h->opt.rhs_width < 0) {
+      h->opt.rhs_width < 0 || h->opt.dense_forward < 0 || h->opt.dense_forward > 1) {
     delete h;
     return OPF_ERR_INVALID_ARG;
   }
@@ -1358,6 +1378,13 @@ int opf_chol_choice(const opf_handle* h, int* form, int* nblocks, float* ms) {
   if (form) *form = h->chol_tuned ? 1 + h->chol_df : 0;
   if (nblocks) *nblocks = h->chol_blocks;
   if (ms) for (int c = 0; c < OPF_CHOL_CANDIDATES; ++c) ms[c] = h->chol_ms[c];
+  return OPF_OK;
+}
+
+int opf_forward_reach(const opf_handle* h, int* nblocks, double* work) {
+  if (!h) return OPF_ERR_INVALID_ARG;
+  if (nblocks) *nblocks = h->bkL.rch_ptr ? h->bkL.rch_nblk : 0;
+  if (work) { work[0] = h->rch_work[0]; work[1] = h->rch_work[1]; }
   return OPF_OK;
 }
 

@@ -159,6 +159,11 @@ struct BlkDev {
   // the factor's pattern is upper triangular: the diagonal-block inverses D_s
   // are upper triangular (else lower), so row r of D_s is zero left (right) of r
   int upper;
+  // forward sweeps on P G_u: per full 32-column block of G_u (rch_nblk of
+  // them) the positions in rows of the rows where the solution can be nonzero,
+  // nlev + 1 offsets per block into rch_q (null: no lists)
+  const int *rch_ptr, *rch_q;
+  int rch_nblk;
 };
 // inverse of every (split) supernode's diagonal block of one factor
 struct DiagInvJob {
@@ -172,16 +177,20 @@ cudaError_t launch_diag_inv4(cudaStream_t s, const DiagInvJob* jobs);
 // ksplit CTAs per 32 columns, cooperative launch; bar holds ncb counters.
 // minb: the register bound's CTAs per SM (5, 6 or 8; see the kernel)
 constexpr int BLK_MINB[3] = {5, 6, 8};
+// rch_cb0 >= 0: X's columns are those of P G_u from column 32 rch_cb0 on (with
+// exact zeros outside its pattern): the full blocks pass by the rows outside
+// their reach lists (S.rch_*) and the levels without such rows
 cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
-                            long long spin_limit, int minb = 5);
+                            long long spin_limit, int minb = 5, int rch_cb0 = -1);
 int trsm_blk_max_blocks(int minb = 5);
 // the level-blocked solve, both triangles, with one thread-block cluster of cl
 // CTAs per 32-column block (cluster barrier between phases); clusters of cl that
 // fit at once (0: none)
 cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& SL, const int* ciL, const double* valL,
                              const double* DL, const BlkDev& SU, const int* ciU, const double* valU,
-                             const double* DU, double* X, double* Y, long long ld, int ncols, int cl);
+                             const double* DU, double* X, double* Y, long long ld, int ncols, int cl,
+                             int rch_cb0 = -1);
 int trsm_blkc_clusters(int cl);
 // Dataflow (barrier-free) form of the level-blocked solve: task list of
 // phase-A (row >= 0) and phase-B (-1 - row) warp tasks in level order, each

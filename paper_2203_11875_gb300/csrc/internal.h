@@ -67,8 +67,10 @@ void ph_end(opf_handle* h);
 double* workspace(opf_handle* h, size_t n);
 double* ybuf_reserve(opf_handle* h, size_t n);
 int lagrangian_gradient(opf_handle* h, const double* lam, const double* y, double* out);
+// gu_c0 >= 0 (trans = 0): X's columns are P G_u's from column gu_c0 on, exact
+// zeros outside its pattern (the forward sweep's reach lists apply)
 int lu_solve_perm(opf_handle* h, int trans, double* X, long long xr, long long xc, int ncols,
-                  bool timed = false);
+                  bool timed = false, int gu_c0 = -1);
 int sens_prepare(opf_handle* h, const double* w, const double* lam, const double* y, const double* sig_w,
                  const double* sig_s);
 int powerflow_impl(opf_handle* h, const double* u, double* x, double tol, int max_iter, int* iters);

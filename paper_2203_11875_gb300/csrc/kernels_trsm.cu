@@ -753,19 +753,27 @@ __global__ void __launch_bounds__(128, 4) k_b_diag_inv(const BatchInst* __restri
 // The level-blocked solve of one 32-column block (columns cb * 32 ..), by the
 // ksplit CTAs of its group (this one is p); sync() separates the phases (a
 // bounded group barrier, or __syncthreads when one CTA has the block).
+// rch_cb0 >= 0: the block is block rch_cb0 + cb of P G_u's columns, and when
+// that block has a reach list only the listed rows are solved (the others are
+// zero in X and stay so) and the levels without any are passed by (every CTA
+// of the group reads the same list, so all of them skip the same barriers).
 // Returns false when a barrier wait expired.
 template <class Sync>
 __device__ __forceinline__ bool blk_solve(const BlkDev& S, const int* __restrict__ ci, const double* __restrict__ val,
                                           const double* __restrict__ D, double* X, double* Y, long long ld,
-                                          int ncols, int cb, int p, int ksplit, Sync&& sync) {
+                                          int ncols, int cb, int p, int ksplit, Sync&& sync, int rch_cb0 = -1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int c = cb * 32 + lane;
   const bool on = c < ncols;
   const int gw = p * nwarps + warp, W = ksplit * nwarps;
+  const int rb = rch_cb0 >= 0 && S.rch_ptr ? rch_cb0 + cb : -1;
+  const int* __restrict__ rp = rb >= 0 && rb < S.rch_nblk ? S.rch_ptr + (size_t)rb * (S.nlev + 1) : nullptr;
   for (int lev = 0; lev < S.nlev; ++lev) {
-    const int q0 = S.lvl_rptr[lev], q1 = S.lvl_rptr[lev + 1];
+    const int q0 = rp ? rp[lev] : S.lvl_rptr[lev], q1 = rp ? rp[lev + 1] : S.lvl_rptr[lev + 1];
+    if (q0 == q1) continue;
     // A: Y_r = X_r - external part of row r
-    for (int q = q0 + gw; q < q1; q += W) {
+    for (int k = q0 + gw; k < q1; k += W) {
+      const int q = rp ? S.rch_q[k] : k;
       const int r = S.rows[q];
       const int e0 = S.ext_beg[r], e1 = S.ext_end[r];
       double a0 = on ? X[(long long)r * ld + c] : 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -798,7 +806,8 @@ __device__ __forceinline__ bool blk_solve(const BlkDev& S, const int* __restrict
     }
     if (!sync()) return false;
     // B: X_r = D_s(r, :) Y_s over the nonzero half of the triangular D_s row
-    for (int q = q0 + gw; q < q1; q += W) {
+    for (int k = q0 + gw; k < q1; k += W) {
+      const int q = rp ? S.rch_q[k] : k;
       const int r = S.rows[q], s = S.row_sn[q];
       const int f = S.sn_first[s], w = S.sn_w[s];
       const double* Dr = D + S.d_off[s] + (r - f) * w;
@@ -827,12 +836,12 @@ __global__ void __launch_bounds__(BLK_THREADS, MINB) k_trsm_blk(BlkDev S, const 
                                                                 const double* __restrict__ val,
                                                                 const double* __restrict__ D, double* X, double* Y,
                                                                 long long ld, int ncols, int ksplit, unsigned* bar,
-                                                                int* st, long long spin_limit) {
+                                                                int* st, long long spin_limit, int rch_cb0) {
   const int cb = blockIdx.x / ksplit, p = blockIdx.x % ksplit;
   unsigned* ctr = bar + cb;
   unsigned nbar = 0;
   blk_solve(S, ci, val, D, X, Y, ld, ncols, cb, p, ksplit,
-            [&]() { return group_barrier(ctr, ksplit * (++nbar), spin_limit, st); });
+            [&]() { return group_barrier(ctr, ksplit * (++nbar), spin_limit, st); }, rch_cb0);
 }
 
 
@@ -848,14 +857,14 @@ __global__ void __launch_bounds__(BLK_THREADS) k_trsm_blkc(BlkDev SL, const int*
                                                            const int* __restrict__ ciU,
                                                            const double* __restrict__ valU,
                                                            const double* __restrict__ DU, double* X, double* Y,
-                                                           long long ld, int ncols) {
+                                                           long long ld, int ncols, int rch_cb0) {
   cg::cluster_group cl = cg::this_cluster();
   const int cb = blockIdx.x / cl.num_blocks();
   auto sync = [&]() {
     cl.sync();
     return true;
   };
-  blk_solve(SL, ciL, valL, DL, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), sync);
+  blk_solve(SL, ciL, valL, DL, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), sync, rch_cb0);
   blk_solve(SU, ciU, valU, DU, X, Y, ld, ncols, cb, (int)cl.block_rank(), (int)cl.num_blocks(), sync);
 }
 
@@ -1302,7 +1311,8 @@ static cudaLaunchConfig_t trsm_cluster_config(int nclusters, int cl, cudaStream_
 
 cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& SL, const int* ciL, const double* valL,
                              const double* DL, const BlkDev& SU, const int* ciU, const double* valU,
-                             const double* DU, double* X, double* Y, long long ld, int ncols, int cl) {
+                             const double* DU, double* X, double* Y, long long ld, int ncols, int cl,
+                             int rch_cb0) {
   if (ncols <= 0) return cudaSuccess;
   if (cl > 8) {
     cudaError_t e = allow_cluster16((const void*)k_trsm_blkc);
@@ -1312,7 +1322,7 @@ cudaError_t launch_trsm_blkc(cudaStream_t s, const BlkDev& SL, const int* ciL, c
   cudaLaunchAttribute at[1];
   const cudaLaunchConfig_t cfg = trsm_cluster_config(ncb, cl, s, at);
   note_launch();
-  return cudaLaunchKernelEx(&cfg, k_trsm_blkc, SL, ciL, valL, DL, SU, ciU, valU, DU, X, Y, ld, ncols);
+  return cudaLaunchKernelEx(&cfg, k_trsm_blkc, SL, ciL, valL, DL, SU, ciU, valU, DU, X, Y, ld, ncols, rch_cb0);
 }
 
 int trsm_blkc_clusters(int cl) {
@@ -1329,13 +1339,13 @@ int trsm_blkc_clusters(int cl) {
 
 cudaError_t launch_trsm_blk(cudaStream_t s, const BlkDev& S, const int* ci, const double* val, const double* D,
                             double* X, double* Y, long long ld, int ncols, int ksplit, unsigned* bar, int* st,
-                            long long spin_limit, int minb) {
+                            long long spin_limit, int minb, int rch_cb0) {
   if (ncols <= 0 || S.nlev <= 0) return cudaSuccess;
   const int ncb = (ncols + 31) / 32;
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned) * ncb, s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&S, (void*)&ci, (void*)&val, (void*)&D, (void*)&X, (void*)&Y, (void*)&ld,
-                  (void*)&ncols, (void*)&ksplit, (void*)&bar, (void*)&st, (void*)&spin_limit};
+                  (void*)&ncols, (void*)&ksplit, (void*)&bar, (void*)&st, (void*)&spin_limit, (void*)&rch_cb0};
   note_launch();
   return cudaLaunchCooperativeKernel(trsm_blk_fn(minb), dim3(ncb * ksplit), dim3(BLK_THREADS), args, 0, s);
 }

@@ -83,6 +83,7 @@ struct opf_handle {
   int trsm_mode1 = -1;           // kernel of the solves with fewer than 32 right-hand sides
                                  // (-1 autotune, 1 staged, 64 level-blocked)
   condipm::BlkDev bkL{}, bkU{};  // level-blocked schedules of the lower / upper solves
+  double rch_work[2] = {};         // forward sweep on P G_u: multiply-adds of the reach lists / of all rows
   double *D_L = nullptr, *D_Ut = nullptr, *D_U = nullptr, *D_Lt = nullptr;  // diagonal-block inverses
   double* ybuf = nullptr;        // level-blocked solve scratch (rows x leading dimension)
   size_t ybuf_cap = 0;

@@ -959,6 +959,51 @@ std::string build_cl_sched(const ColSched& C, int CL, ClSched& S) {
   }
   return "";
 }
+void build_forward_reach(const Plan& P, const ColSched& C, std::vector<int>& ptr, std::vector<int>& q,
+                         double work[2]) {
+  const int n = P.nx, nblk = P.nu / 32, nlev = C.nlev;
+  ptr.assign((size_t)nblk * (nlev + 1), 0);
+  q.clear();
+  work[0] = work[1] = 0.0;
+  // rows in level order, with their supernode
+  std::vector<int> rows, rsn;
+  for (int l = 0; l < nlev; ++l)
+    for (int s = C.lvl_ptr[l]; s < C.lvl_ptr[l + 1]; ++s)
+      for (int r = C.sn_first[s]; r < C.sn_first[s] + C.sn_w[s]; ++r) { rows.push_back(r); rsn.push_back(s); }
+  auto row_work = [&](int r, int s) {
+    return double(C.ext_end[r] - C.ext_beg[r]) + double(r - C.sn_first[s] + 1);
+  };
+  for (size_t t = 0; t < rows.size(); ++t) work[1] += row_work(rows[t], rsn[t]);
+  work[1] *= 32.0 * nblk;
+  std::vector<char> in(n);
+  for (int b = 0; b < nblk; ++b) {
+    std::fill(in.begin(), in.end(), 0);
+    // rows ascend in the elimination order, so one pass reaches every row
+    for (int i = 0; i < n; ++i) {
+      char v = 0;
+      for (int e = P.PGu.rp[i]; e < P.PGu.rp[i + 1] && !v; ++e) v = P.PGu.ci[e] / 32 == b;
+      for (int e = P.Lo.rp[i]; e < P.Lo.rp[i + 1] && !v; ++e) v = in[P.Lo.ci[e]];
+      in[i] = v;
+    }
+    int* bp = &ptr[(size_t)b * (nlev + 1)];
+    bp[0] = int(q.size());
+    size_t t = 0;
+    for (int l = 0; l < nlev; ++l) {
+      for (int s = C.lvl_ptr[l]; s < C.lvl_ptr[l + 1]; ++s) {
+        const int f = C.sn_first[s], w = C.sn_w[s];
+        bool any = false;
+        for (int r = f; r < f + w; ++r) any = any || in[r];
+        for (int r = f; r < f + w; ++r, ++t)
+          if (any) {
+            q.push_back(int(t));
+            work[0] += 32.0 * row_work(r, s);
+          }
+      }
+      bp[l + 1] = int(q.size());
+    }
+  }
+}
+
 std::vector<int> min_degree_order(int n, const std::vector<std::vector<int>>& adj, const std::vector<int>& wt) {
   return min_degree(n, adj, wt);
 }

@@ -112,6 +112,7 @@ struct ClSched {
 };
 std::string build_cl_sched(const ColSched& C, int CL, ClSched& S);
 
+
 struct Plan {
   // ---- sizes
   int nb = 0, nl = 0, ng = 0, slack = 0, nx = 0, nu = 0, nw = 0, m = 0, nlim = 0, ne = 0;
@@ -183,6 +184,19 @@ struct Plan {
 // upper), unit or non-unit diagonal, chunks of at most budget bytes.
 void build_sn_stream(const CSR& M, const SnSched& S, const std::vector<int>& start, bool upper,
                      bool unit, int budget, SnStream& out);
+
+// The forward sweep L Y = P G_u, one 32-column block of G_u at a time (the
+// nu / 32 full blocks): the rows where Y can be nonzero in a block's columns
+// are the rows of P G_u's pattern there and every row with an L entry in a
+// column already reached (the union of the etree paths from those rows up);
+// every other row of Y is exactly zero and the solve can pass it by.  Per
+// block, the positions of those rows in C's level order (each level's
+// supernodes in turn, each supernode's rows in turn), a supernode listed whole
+// or not at all; ptr holds nblk x (C.nlev + 1) offsets into q.  work[0] and
+// work[1]: multiply-adds per column of the listed rows and of all rows (their
+// external L entries plus their row of the diagonal block's inverse).
+void build_forward_reach(const Plan& P, const ColSched& C, std::vector<int>& ptr, std::vector<int>& q,
+                         double work[2]);
 
 // Minimum-degree ordering of a weighted graph (adjacency lists, weights =
 // unknowns per node); ties broken by node index.

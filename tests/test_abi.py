@@ -62,6 +62,8 @@ def test_queries_reject_a_null_handle(lib):
     ms = (C.c_float * 11)()
     assert L.opf_chol_choice(None, C.byref(f), C.byref(nb), ms) == -1
     assert L.opf_chol_solve_choice(None, C.byref(f), ms) == -1
+    wk = (C.c_double * 2)()
+    assert L.opf_forward_reach(None, C.byref(f), wk) == -1
     k, k1 = C.c_int(), C.c_int()
     ms6 = (C.c_float * 6)()
     assert L.opf_trsm_choice(None, C.byref(k), ms6, C.byref(k1)) == -1

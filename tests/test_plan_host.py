@@ -78,3 +78,36 @@ def test_fullspace_block_plan(fs_checker, tmp_path, name):
     # one block per bus and one per flow-limit row; at most 5 unknowns per bus
     assert nblk == net.nb + 2 * len(lay.lim)
     assert 1 <= bmax <= 5
+
+
+@pytest.fixture(scope="module")
+def reach_checker(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    out = tmp_path_factory.mktemp("reach") / "reach_check"
+    subprocess.run([gxx, "-O2", "-std=c++17", "-I", CSRC, "-o", str(out),
+                    os.path.join(ROOT, "tests", "reach_check.cpp"), os.path.join(CSRC, "plan.cpp")],
+                   check=True, capture_output=True)
+    return out
+
+
+@pytest.mark.parametrize("name,make", [("ring30", gridgen.ring30),
+                                       ("b1500", lambda: gridgen.lattice(1500, 7002, name="b1500")),
+                                       ("grid2000", gridgen.grid2000)])
+def test_forward_sweep_reach_lists(reach_checker, tmp_path, name, make):
+    """The reach lists the forward sweep L Y = P G_u passes rows by: a numeric
+    forward solve with random values on both patterns is nonzero only on
+    listed rows, every listed row is nonzero or shares a supernode with one,
+    and the lists hold only part of the rows (tests/reach_check.cpp)."""
+    net = make()
+    path = tmp_path / f"{name}.bin"
+    _write(net, str(path))
+    res = subprocess.run([str(reach_checker), str(path)], capture_output=True, text=True, timeout=300)
+    out = res.stdout.split()
+    assert res.returncode == 0 and out and out[0] == "ok", res.stdout + res.stderr
+    from oracle import model
+    nblk, listed, allr, frac = int(out[1]), int(out[2]), int(out[3]), float(out[4])
+    assert nblk == model.Layout(net).nu // 32
+    if nblk:
+        assert 0 < listed < allr and 0 < frac < 0.9
