@@ -437,7 +437,7 @@ int upload_all(opf_handle* h) {
   TRY(alloc(h, &h->st, ST_WORDS));
   TRY(alloc(h, &h->pf_ws, (size_t)P.nx + 1));
   TRY(alloc(h, &h->bar, 4));
-  TRY(alloc(h, &h->chol_cnt, 2 * (size_t)((P.nu + 31) / 32 + 1)));
+  TRY(alloc(h, &h->chol_cnt, 3 * (size_t)((P.nu + 31) / 32 + 1)));
   TRY(alloc(h, &h->Finv, (size_t)std::max(1, (P.nu + 31) / 32) * 32 * 32));
   h->chol_solve_cl = (P.nu + 31) / 32 > 8 ? 16 : 8;
   TRY(alloc(h, &h->cs_tmp, (size_t)P.nu));

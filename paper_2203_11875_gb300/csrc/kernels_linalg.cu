@@ -1193,6 +1193,7 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
   const int nt = (n + CNB - 1) / CNB;
   unsigned* pdone = cnt;          // [nt]
   unsigned* cdone = cnt + nt;     // [nt]
+  unsigned* ccol = cnt + 2 * nt;  // [nt] full-tile mode: tiles of column k+2 updated at step k
   fill_pairs(pairs);
   __syncthreads();
   const bool panel = (int)blockIdx.x < np;
@@ -1206,9 +1207,11 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
       if (tid == 0) {
         int ok = 1;
         if (k > 0) {
-          // (sub-)tiles of column k below its diagonal, counted at step k-1
-          const int gmax = sub_mode ? (n + 15) / 16 : nt;
-          const unsigned need = sub_mode ? (unsigned)((gmax - 2 * k) + (gmax - 2 * k - 1)) : (unsigned)(nt - k);
+          // the 16 x 16 sub-tiles of column k on and below its diagonal,
+          // counted at step k-1 (in both modes column k's last update is done
+          // in sub-tiles)
+          const int g16 = (n + 15) / 16;
+          const unsigned need = (unsigned)((g16 - 2 * k) + (g16 - 2 * k - 1));
           ok = chol_wait(cdone + (k - 1), need, spin_limit, st);
         }
         ok_s = ok;
@@ -1282,10 +1285,47 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
     const int g = sub_mode ? 2 : 1;                   // (sub-)tiles per tile side
     const int gmax = sub_mode ? (n + 15) / 16 : nt;   // (sub-)rows in the matrix
     if (!sub_mode) {
-      // whole 32 x 32 tiles: the owned tiles of this step in order (columns
-      // k+1 .., rows of the CTA's residue class), the next tile's panels fetched
+      // Column k+1 first, as 16 x 16 sub-tiles shared out over all update CTAs
+      // (the next panel waits on it: four CTAs per tile shorten that wait).
+      // This is the last update of those entries, so it needs only their
+      // owners' step k-1 updates done (counted in ccol[k-1]).
+      {
+        const int g16 = (n + 15) / 16, sc0 = 2 * (k + 1);
+        const int n0 = g16 - sc0, n1 = g16 - sc0 - 1, nsub = n0 + n1;
+        if (ub < nsub) {
+          __syncthreads();   // every thread has read ok_s of the pdone wait
+          if (tid == 0) ok_s = k == 0 || chol_wait(ccol + (k - 1), (unsigned)(nt - k - 1), spin_limit, st);
+          __syncthreads();
+          if (!ok_s) return;
+        }
+        for (int sidx = ub; sidx < nsub; sidx += nU) {
+          const int sc = sidx < n0 ? sc0 : sc0 + 1;
+          const int sr = sidx < n0 ? sc0 + sidx : sc0 + 1 + (sidx - n0);
+          const int i0 = sr * 16, j0 = sc * 16;
+          for (int t = tid; t < 16 * CNB; t += blockDim.x) {
+            const int rr = t / CNB, l = t % CNB;
+            Ta[rr][l] = (i0 + rr < n && l < kb) ? __ldcg(&F[(size_t)(i0 + rr) * n + k0 + l]) : 0.0;
+            Tb[rr][l] = (j0 + rr < n && l < kb) ? __ldcg(&F[(size_t)(j0 + rr) * n + k0 + l]) : 0.0;
+          }
+          __syncthreads();
+          const int rr = tid >> 4, cc = tid & 15;
+          double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+          for (int l = 0; l < CNB; l += 2) {
+            acc0 = fma(Ta[rr][l], Tb[cc][l], acc0);
+            acc1 = fma(Ta[rr][l + 1], Tb[cc][l + 1], acc1);
+          }
+          const int gr = i0 + rr, gc = j0 + cc;
+          if (gr < n && gc < n && gc <= gr) F[(size_t)gr * n + gc] -= acc0 + acc1;
+          __syncthreads();
+          if (tid == 0) red_add_release(cdone + k, 1u);
+        }
+      }
+      // whole 32 x 32 tiles of columns k+2 ..: the owned tiles of this step in
+      // order (rows of the CTA's residue class), the next tile's panels fetched
       // into registers while this one is computed (each thread moves rows
-      // t / 32 + 8 q, column t % 32 of both panels)
+      // t / 32 + 8 q, column t % 32 of both panels); column k+2's are counted
+      // into ccol[k] for the next step's sub-tiles
       auto first_row = [&](int gj) { return gj + (((ub - (gj * gmax - gj * (gj - 1) / 2)) % nU) + nU) % nU; };
       auto advance = [&](int& gi, int& gj) {
         gi += nU;
@@ -1294,7 +1334,7 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
           gi = first_row(gj);
         }
       };
-      int gj = k + 1, gi = first_row(gj);
+      int gj = k + 2, gi = gj < gmax ? first_row(gj) : gmax;
       if (gi >= gmax) { gi -= nU; advance(gi, gj); }
       double pa[4], pb[4];
       auto fetch = [&](int ti, int tj) {
@@ -1335,7 +1375,7 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
         if (r1g < n && c0g <= r1g) F[(size_t)r1g * n + c0g] -= c10;
         if (r1g < n && c1g < n && c1g <= r1g) F[(size_t)r1g * n + c1g] -= c11;
         __syncthreads();
-        if (tid == 0 && gj == k + 1) red_add_release(cdone + k, 1u);
+        if (tid == 0 && gj == k + 2) red_add_release(ccol + k, 1u);
         gi = ni;
         gj = nj;
       }
@@ -1410,7 +1450,7 @@ int chol_df_max_blocks() {
 cudaError_t launch_chol_df(cudaStream_t s, int n, double* F, double* dinv, int* st, unsigned* cnt,
                            long long spin_limit, int nblocks, int np) {
   const int nt = (n + CNB - 1) / CNB;
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 2 * (size_t)nt, s);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 3 * (size_t)nt, s);
   if (e != cudaSuccess) return e;
   const int nU = std::max(1, nblocks - np);
   const int sub_mode = (nt * (nt - 1) / 2 < 2 * nU) ? 1 : 0;

@@ -124,7 +124,7 @@ struct opf_handle {
   float cs_ms[3] = {};
   double* cs_tmp = nullptr;      // its copy of the right-hand side (nu; in allocs)
   float chol_ms[OPF_CHOL_CANDIDATES] = {};   // tuner timings
-  unsigned* chol_cnt = nullptr;  // its step counters (2 x tile columns)
+  unsigned* chol_cnt = nullptr;  // its step counters (3 x tile columns)
   // condensation + first Cholesky attempt of the interior-point loop as a CUDA
   // graph (inputs in the loop's fixed device buffers)
   cudaGraphExec_t cf_exec = nullptr;
