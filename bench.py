@@ -11,7 +11,7 @@ columns, K assembly, H = K Z and the condensed matrix (A4-A7), the condensed
 right-hand side (A8), one Cholesky attempt (A9) and the step recovery (A10).
 ``value`` is A4-A9 (the metric); ``ms_per_step`` the whole step.
 
-Z and H (168 MB each) exceed L2 (129 MB); a 256 MB buffer is still written on
+Z and H (339 MB each) exceed L2 (129 MB); a 256 MB buffer is still written on
 the stream between timed steps, so the factors and K start cold too.  Device
 time comes from CUDA events on the library's stream.  ``e2e`` times the same
 step through opf_newton_step with pinned HOST buffers (copies inside).
@@ -519,6 +519,9 @@ def main():
     ap.add_argument("--no-fullspace", action="store_true", help="skip the hybrid full-space comparison")
     ap.add_argument("--no-decay", action="store_true", help="skip the reduced-Hessian decay study")
     ap.add_argument("--batch-threads", type=int, default=0, help="host threads of the batch (0 = auto)")
+    ap.add_argument("--workload", default="grid10k", choices=["grid10k", "grid2000"],
+                    help="network of the timed loop: grid10k (the bench line, at the stored oracle iterate) or "
+                         "grid2000 (for profiling the 2,000-bus case, at a synthetic iterate)")
     ap.add_argument("--chol-form", type=int, default=0, choices=[0, 1, 2],
                     help="dense Cholesky of Kred: 0 autotune, 1 barrier form, 2 dataflow form")
     ap.add_argument("--rhs-block", type=int, default=0, choices=[0, 1, 2, 4, 32, 64, 96, 128],
@@ -554,11 +557,14 @@ def main():
     # the best FP64 rate the device delivers among the probes (DFMA and the f64
     # mma.sync shapes measure within a few per cent of each other)
     peak = max(peaks[k] for k in ("dfma", "dmma_m8n8k4", "dmma_m16n8k4", "dmma_m16n8k16")) if peaks else derived
-    net = gridgen.grid10k()
+    net = gridgen.grid10k() if args.workload == "grid10k" else gridgen.grid2000()
     h = binding.Handle(net, chol_form=args.chol_form, rhs_block=args.rhs_block, rhs1_kernel=args.rhs1_kernel)
     stream = torch.cuda.Stream(device=dev)
     h.set_stream(stream)
-    it, delta = stored_iterate()
+    if args.workload == "grid10k":
+        it, delta = stored_iterate()
+    else:
+        it, delta = synthetic_iterate(net, h.nx, h.nu, h.m), 0.0
     D = {k: torch.as_tensor(v, dtype=torch.float64, device=dev) for k, v in it.items()}
     step = torch.zeros(h.n_kkt, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -626,7 +632,7 @@ def main():
         trsm_kernel, f"k_trsm_st<{trsm_kernel}>")
     trsm_name = trsm_base + {32: " (column-parallel)", 64: " (level-blocked)", 96: " (dataflow)",
                              128: " (level-blocked, clusters)"}.get(trsm_kernel, " (staged)")
-    traffic = measured_traffic(trsm_base, "grid10k")
+    traffic = measured_traffic(trsm_base, args.workload)
     fl_path = sum(v for k, v in fl.items() if k != "S")
     cf_ms = float(np.mean(cf))
     # end to end through the public API with pinned host buffers: opf_newton_step
@@ -653,9 +659,12 @@ def main():
     out = {"metric": METRIC, "value": t_cf, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_full, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "inputs": "tests/golden/grid10k_iterate.npz (oracle LinRed iterate 3 "
-                      "of the seeded 10,000-bus network)",
-                      "l2": "inputs larger than L2 (Z, H 168 MB each) and a 256 MB flush written between timed steps",
+           "config": {"workload": WORKLOAD if args.workload == "grid10k" else
+                      "grid2000: 2,000-bus lattice, 200 generators, nu=399, nx=3,799, FP64, synthetic iterate",
+                      "inputs": "tests/golden/grid10k_iterate.npz (oracle LinRed iterate 3 of the seeded 10,000-bus "
+                                "network)" if args.workload == "grid10k" else "bench.synthetic_iterate(grid2000)",
+                      "l2": ("inputs larger than L2 (Z, H 339 MB each) and " if args.workload == "grid10k" else "")
+                      + "a 256 MB flush written between timed steps",
                       "timed": "A4-A9: G_x refactor, multi-RHS solves (the step's right-hand side as one extra "
                                "column), K, H = K Z, Kred and the condensed right-hand side, one Cholesky attempt "
                                "(events) + reading the condensed right-hand side out (phase events)",
