@@ -551,10 +551,20 @@ __device__ __forceinline__ double pivot_rcp(double d) {
 // the pivots are taken once, all together, at the end.  Writes 1 / L_jj to
 // dv[j]; returns the first failing local column (non-positive or non-finite
 // pivot) or -1.
-// R (optional, nr = 8 rows) holds panel rows below the tile: they are
-// eliminated along with it, as further rows of the column block, and leave as
-// rows of L (R L_kk^T = the rows given), so the panel solve costs no separate
-// sequence of dependent steps.
+// R (optional, nr = 8, 16 or 24 rows) holds panel rows below the tile: they
+// are eliminated along with it, as further rows of the column block, and leave
+// as rows of L (R L_kk^T = the rows given), so the panel solve costs no
+// separate sequence of dependent steps.
+template <int NR>
+__device__ __forceinline__ void tile_rows_update(double (*R)[CNB + 1], const double (*T)[CNB + 1], int j, double rj,
+                                                 int wk, int nwk) {
+  // R_rl -= R_rj T_lj / d_j for l > j (row index fastest)
+  for (int q = wk; q < NR * (CNB - 1 - j); q += nwk) {
+    const int rr = q % NR, l = j + 1 + q / NR;
+    R[rr][l] = fma(-R[rr][j] * rj, T[l][j], R[rr][l]);
+  }
+}
+
 __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const unsigned short* pairs,
                                double (*R)[CNB + 1] = nullptr, int nr = 0) {
   const int tid = threadIdx.x;
@@ -592,11 +602,9 @@ __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const u
       }
     }
     if (nr > 0 && wk >= 0) {
-      // panel rows: R_rl -= R_rj T_lj / d_j for l > j (eight rows, row index fastest)
-      for (int q = wk; q < 8 * (CNB - 1 - j); q += nwk) {
-        const int rr = q & 7, l = j + 1 + (q >> 3);
-        R[rr][l] = fma(-R[rr][j] * rj, T[l][j], R[rr][l]);
-      }
+      if (nr == 8) tile_rows_update<8>(R, T, j, rj, wk, nwk);
+      else if (nr == 16) tile_rows_update<16>(R, T, j, rj, wk, nwk);
+      else tile_rows_update<24>(R, T, j, rj, wk, nwk);
     }
     __syncthreads();
   }
@@ -612,7 +620,7 @@ __device__ int block_chol_tile(double (*T)[CNB + 1], double* dv, int kb, const u
     if (j < kb && i > j) T[i][j] *= dv[j];
   }
   if (nr > 0)
-    for (int t = tid; t < 8 * CNB; t += blockDim.x) {
+    for (int t = tid; t < nr * CNB; t += blockDim.x) {
       const int rr = t / CNB, j = t % CNB;
       if (j < kb) R[rr][j] *= dv[j];
     }
@@ -1181,11 +1189,15 @@ __device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// row groups of the panel each panel CTA eliminates along with its diagonal
+// tile (the rest are solved by substitution with the factored tile)
+constexpr int CHOL_FUSED_GROUPS = 3;
+
 __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_out, int* st, unsigned* cnt,
                                                  int np, int sub_mode, long long spin_limit) {
   __shared__ double Ta[CNB][CNB + 1];
   __shared__ double Tb[CNB][CNB + 1];
-  __shared__ double Tr[8][CNB + 1];   // the panel rows eliminated with the diagonal tile
+  __shared__ double Tr[8 * CHOL_FUSED_GROUPS][CNB + 1];   // the panel rows eliminated with the diagonal tile
   __shared__ double dv[CNB];
   __shared__ unsigned short pairs[CNB * (CNB + 1) / 2];
   __shared__ int ok_s;
@@ -1225,16 +1237,17 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
           const int i = t / CNB, j = t % CNB;
           Ta[i][j] = (i < kb && j <= i) ? __ldcg(&F[(size_t)(k0 + i) * n + k0 + j]) : (i == j ? 1.0 : 0.0);
         }
-        // the first row group of this CTA (rows r0 + 8 blockIdx.x ..) rides along
-        const bool fused = (int)blockIdx.x < row_blocks;
-        const int rf0 = r0 + (int)blockIdx.x * nwarps;
-        if (fused)
-          for (int t = tid; t < 8 * CNB; t += blockDim.x) {
-            const int rr = t / CNB, j = t % CNB;
-            Tr[rr][j] = (rf0 + rr < n && j < kb) ? __ldcg(&F[(size_t)(rf0 + rr) * n + k0 + j]) : 0.0;
-          }
+        // this CTA's first row groups (groups blockIdx.x + g np, g < 3: rows
+        // r0 + 8 (blockIdx.x + g np) ..) ride along in the tile's elimination
+        int nfg = 0;
+        while (nfg < CHOL_FUSED_GROUPS && (int)blockIdx.x + nfg * np < row_blocks) ++nfg;
+        auto frow = [&](int rr) { return r0 + ((int)blockIdx.x + (rr >> 3) * np) * 8 + (rr & 7); };
+        for (int t = tid; t < 8 * nfg * CNB; t += blockDim.x) {
+          const int rr = t / CNB, j = t % CNB, r = frow(rr);
+          Tr[rr][j] = (r < n && j < kb) ? __ldcg(&F[(size_t)r * n + k0 + j]) : 0.0;
+        }
         __syncthreads();
-        const int fail = block_chol_tile(Ta, dv, kb, pairs, Tr, fused ? 8 : 0);
+        const int fail = block_chol_tile(Ta, dv, kb, pairs, Tr, 8 * nfg);
         if (fail >= 0) {
           if (tid == 0) set_status(st, DEV_NOT_PD, k0 + fail);
           return;
@@ -1245,16 +1258,13 @@ __global__ void __launch_bounds__(256) k_chol_df(double* F, int n, double* dinv_
           for (int t = tid; t < CNB * CNB; t += blockDim.x) Tb[t / CNB][t % CNB] = Ta[t / CNB][t % CNB];
           if (tid < kb) dinv_out[k0 + tid] = dv[tid];
         }
-        int mine = 0;
-        if (fused) {
-          ++mine;
-          for (int t = tid; t < 8 * CNB; t += blockDim.x) {
-            const int rr = t / CNB, j = t % CNB;
-            if (rf0 + rr < n && j < kb) F[(size_t)(rf0 + rr) * n + k0 + j] = Tr[rr][j];
-          }
+        int mine = nfg;
+        for (int t = tid; t < 8 * nfg * CNB; t += blockDim.x) {
+          const int rr = t / CNB, j = t % CNB, r = frow(rr);
+          if (r < n && j < kb) F[(size_t)r * n + k0 + j] = Tr[rr][j];
         }
         // further row groups: one row per warp, forward substitution with L_kk
-        for (int rb = blockIdx.x + np; rb < row_blocks; rb += np) {
+        for (int rb = blockIdx.x + nfg * np; rb < row_blocks; rb += np) {
           ++mine;
           const int r = r0 + rb * nwarps + warp;
           if (r < n) {
