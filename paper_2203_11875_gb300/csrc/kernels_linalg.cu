@@ -237,6 +237,9 @@ __global__ void k_row_absmax(int n, const int* __restrict__ rp, const double* __
 // One row i of the up-looking LU, factored by the calling warp into its
 // shared-memory row buffer w (the body of k_lu_refactor and of the batched
 // refactorisation).  Returns false when a bounded wait expired.
+// entries per lane of a dependency row's update fetched at once
+constexpr int LU_PF = 4;
+
 __device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const int* __restrict__ ci,
                                        const int* __restrict__ diag, const long long* __restrict__ upd_ptr,
                                        const int* __restrict__ upd_pos, double* LU, double* inv_diag,
@@ -248,12 +251,15 @@ __device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const 
   __syncwarp();
   for (int q = r0; q < dpos; ++q) {
     const int k = ci[q];
-    // the structure of row k's update needs no wait: fetch it first, so that
-    // after the flag only the values cost a round trip
+    // the structure of row k's update needs no wait: fetch it first (its first
+    // LU_PF x 32 positions), so that after the flag only the values cost a
+    // round trip, all of them in flight together
     const int ub = diag[k] + 1, ue = rp[k + 1];
     const long long base = upd_ptr[q];
     const int j0 = ub + lane;
-    const int pos0 = j0 < ue ? upd_pos[base + lane] - r0 : 0;
+    int pos[LU_PF];
+#pragma unroll
+    for (int t = 0; t < LU_PF; ++t) pos[t] = j0 + 32 * t < ue ? upd_pos[base + lane + 32 * t] - r0 : 0;
     int expired = 0;
     if (lane == 0) {
       // acquire load: row k's values and inverse pivot are visible once the
@@ -274,11 +280,15 @@ __device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const 
     if (__shfl_sync(0xffffffffu, expired, 0)) return false;
     __syncwarp();   // orders lane 0's acquire before every lane's loads of row k
     const double dk = __ldcg(&inv_diag[k]);
-    const double u0 = j0 < ue ? __ldcg(&LU[j0]) : 0.0;
+    double u[LU_PF];
+#pragma unroll
+    for (int t = 0; t < LU_PF; ++t) u[t] = j0 + 32 * t < ue ? __ldcg(&LU[j0 + 32 * t]) : 0.0;
     const double lik = w[q - r0] * dk;
     __syncwarp();
-    if (j0 < ue) w[pos0] = fma(-lik, u0, w[pos0]);
-    for (int j = j0 + 32; j < ue; j += 32) {
+#pragma unroll
+    for (int t = 0; t < LU_PF; ++t)
+      if (j0 + 32 * t < ue) w[pos[t]] = fma(-lik, u[t], w[pos[t]]);
+    for (int j = j0 + 32 * LU_PF; j < ue; j += 32) {
       const int pos = upd_pos[base + (j - ub)] - r0;
       w[pos] = fma(-lik, __ldcg(&LU[j]), w[pos]);
     }
