@@ -240,6 +240,24 @@ __global__ void k_row_absmax(int n, const int* __restrict__ rp, const double* __
 // entries per lane of a dependency row's update fetched at once
 constexpr int LU_PF = 4;
 
+// Reciprocal of an LU pivot (either sign) whose magnitude lies in
+// [2^-1000, 2^1000]: the hardware estimate rcp.approx.ftz.f64 and one
+// third-order step, r (1 + e + e^2) with e = 1 - d r (relative error e^3,
+// from the geometric series of 1 / (1 - e)) -- three dependent FP64
+// operations where the IEEE division takes a longer sequence, and each row's
+// inverse pivot sits on the refactorisation's hand-off chain.  Other
+// magnitudes use the division.
+__device__ __forceinline__ double lu_rcp(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFULL;
+  if (b >= (23ULL << 52) && b < (2023ULL << 52)) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+  }
+  return 1.0 / d;
+}
+
 __device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const int* __restrict__ ci,
                                        const int* __restrict__ diag, const long long* __restrict__ upd_ptr,
                                        const int* __restrict__ upd_pos, double* LU, double* inv_diag,
@@ -247,6 +265,9 @@ __device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const 
                                        long long spin_limit, double* w, int lane) {
   volatile int* vst = st;
   const int r0 = rp[i], r1 = rp[i + 1], dpos = diag[i];
+  // the pivot threshold, off the hand-off chain: non-negative doubles order
+  // like their bit patterns, so the test at the end is an integer compare
+  const unsigned long long thr_bits = lane == 0 ? (unsigned long long)__double_as_longlong(1e-14 * rmax[i]) : 0ULL;
   for (int j = r0 + lane; j < r1; j += 32) w[j - r0] = __ldcg(&LU[j]);
   __syncwarp();
   for (int q = r0; q < dpos; ++q) {
@@ -299,9 +320,12 @@ __device__ __forceinline__ bool lu_row(int i, const int* __restrict__ rp, const 
   __syncwarp();
   if (lane == 0) {
     const double u = w[dpos - r0];
+    const unsigned long long ub = (unsigned long long)__double_as_longlong(u) & 0x7FFFFFFFFFFFFFFFULL;
     double inv = 0.0;
-    if (!(fabs(u) > 1e-14 * rmax[i]) || !isfinite(u)) set_status(st, DEV_SINGULAR, i);
-    else inv = 1.0 / u;
+    // |u| <= 1e-14 max|row| (or NaN threshold), or u not finite: singular
+    if (!(ub > thr_bits) || ub >= 0x7FF0000000000000ULL || thr_bits > 0x7FF0000000000000ULL)
+      set_status(st, DEV_SINGULAR, i);
+    else inv = lu_rcp(u);
     inv_diag[i] = inv;
     // release: the row's values (ordered before lane 0 by __syncwarp) and its
     // inverse pivot are visible to whoever acquires the flag
