@@ -975,15 +975,22 @@ void build_forward_reach(const Plan& P, const ColSched& C, std::vector<int>& ptr
   };
   for (size_t t = 0; t < rows.size(); ++t) work[1] += row_work(rows[t], rsn[t]);
   work[1] *= 32.0 * nblk;
-  std::vector<char> in(n);
+  // the reach of 64 blocks at a time, one bit per block: rows ascend in the
+  // elimination order, so one pass over L's rows reaches every row
+  std::vector<unsigned long long> in(n);
   for (int b = 0; b < nblk; ++b) {
-    std::fill(in.begin(), in.end(), 0);
-    // rows ascend in the elimination order, so one pass reaches every row
-    for (int i = 0; i < n; ++i) {
-      char v = 0;
-      for (int e = P.PGu.rp[i]; e < P.PGu.rp[i + 1] && !v; ++e) v = P.PGu.ci[e] / 32 == b;
-      for (int e = P.Lo.rp[i]; e < P.Lo.rp[i + 1] && !v; ++e) v = in[P.Lo.ci[e]];
-      in[i] = v;
+    const unsigned long long bit = 1ULL << (b & 63);
+    if ((b & 63) == 0) {
+      const int b0 = b;
+      for (int i = 0; i < n; ++i) {
+        unsigned long long v = 0;
+        for (int e = P.PGu.rp[i]; e < P.PGu.rp[i + 1]; ++e) {
+          const int cb = P.PGu.ci[e] / 32 - b0;
+          if (cb >= 0 && cb < 64) v |= 1ULL << cb;
+        }
+        for (int e = P.Lo.rp[i]; e < P.Lo.rp[i + 1]; ++e) v |= in[P.Lo.ci[e]];
+        in[i] = v;
+      }
     }
     int* bp = &ptr[(size_t)b * (nlev + 1)];
     bp[0] = int(q.size());
@@ -992,7 +999,7 @@ void build_forward_reach(const Plan& P, const ColSched& C, std::vector<int>& ptr
       for (int s = C.lvl_ptr[l]; s < C.lvl_ptr[l + 1]; ++s) {
         const int f = C.sn_first[s], w = C.sn_w[s];
         bool any = false;
-        for (int r = f; r < f + w; ++r) any = any || in[r];
+        for (int r = f; r < f + w; ++r) any = any || (in[r] & bit) != 0;
         for (int r = f; r < f + w; ++r, ++t)
           if (any) {
             q.push_back(int(t));
